@@ -1,0 +1,239 @@
+/*
+ * efe.h - C ABI of libefe: the hot path of all-electron real-time TDDFT in an
+ * orthogonalised enriched finite element (EFE) basis, after Kanungo, Rufus &
+ * Gavini, "Efficient all-electron time-dependent density functional theory
+ * calculations using an enriched finite element basis" (arXiv 2210.14421),
+ * written for one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units: atomic units (bohr, hartree, a.u. of time).
+ * Mesh: an axis-aligned rectilinear hexahedral mesh of [xb0, xbN] x [yb0, ybN]
+ *   x [zb0, zbN]; cells c = cx + ncx (cy + ncy cz).  Classical nodes are the
+ *   tensor-product Gauss-Lobatto-Legendre (GLL) nodes of degree p; node
+ *   g = ix + Nx (iy + Ny iz), Nx = ncx p + 1.  Every node is stored; boundary
+ *   nodes carry the homogeneous Dirichlet condition of the orbitals and are
+ *   held at zero by the operators.
+ * DOFs: n_dof = n_nodes + n_enrich; rows 0..n_nodes-1 are classical nodes,
+ *   rows n_nodes.. are enrichment functions in the order they were given.
+ * Orbitals: psi_bar is the Loewdin-basis coefficient block of Eq.
+ *   TDKSDiscrete2 (psi_bar = M^1/2 psi), stored as complex128, row-major
+ *   [n_dof][n_cols] with re/im interleaved, n_cols = n_orb * batch, column
+ *   b * n_orb + alpha = orbital alpha of batch member b.
+ * Quadrature fields (rho, v_xc, v_H): float64 [batch][n_cells][n_q^3],
+ *   point q = q1 + n_q (q2 + n_q q3) of the n_q-point Gauss-Legendre rule.
+ * Pointers: every array argument named *_dev is device memory of the device
+ *   that was current at efe_setup; *_host is host memory.  The caller owns all
+ *   arrays it passes and keeps them alive until the stream work completes; the
+ *   context owns only its internal tables and workspaces.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
+ *   calls enqueue work on `stream` and return without waiting, except
+ *   efe_setup, efe_destroy and the host-visible outputs documented below
+ *   (efe_step_info, iteration counts), which synchronise `stream`.
+ * Errors: every call returns an efe_status; a non-OK status leaves a message
+ *   that efe_last_error(ctx) returns until the next call on that context.
+ *   EFE_WARN_KRYLOV_CAP is a warning: the step was completed with k_max
+ *   Lanczos vectors for at least one column.
+ */
+#ifndef EFE_H
+#define EFE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct efe_ctx efe_ctx;
+
+typedef enum {
+  EFE_OK = 0,
+  EFE_ERR_ARG = 1,          /* invalid argument (sizes, pointers, unsupported degree) */
+  EFE_ERR_NOMEM = 2,        /* device allocation failed */
+  EFE_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  EFE_ERR_NOT_SPD = 4,      /* the enrichment overlap M^ee is not positive definite */
+  EFE_WARN_KRYLOV_CAP = 5,  /* Lanczos reached k_max before its error estimate met tol */
+  EFE_ERR_CG_NOCONV = 6,    /* Hartree CG did not reach cg_tol within cg_max_it */
+  EFE_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
+  EFE_ERR_STATE = 8         /* call out of order (e.g. apply before a potential was set) */
+} efe_status;
+
+typedef enum {
+  EFE_FP64 = 0,   /* every step in float64 */
+  EFE_MIXED = 1   /* cell contraction and enrichment coupling in float32 with float32
+                     accumulation; gather/scatter, Lanczos, tridiagonal exponential,
+                     density, Hartree residuals, norms and dipole in float64 */
+} efe_precision;
+
+/* Radial shapes of the atomic part N^A (Eq. EFEAtomic), divided by r^l:
+ * SLATER r^(n-1-l) e^(-zeta r); HYDROGENIC zeta^l L_{n-l-1}^{(2l+1)}(2 zeta r / n)
+ * e^(-zeta r / n); GAUSSIAN e^(-zeta r^2).  Angular part: real solid harmonics
+ * l <= 2 (l = 1: m = -1, 0, 1 -> y, z, x; l = 2: xy, yz, 2z^2-x^2-y^2, xz, x^2-y^2). */
+enum { EFE_RADIAL_SLATER = 0, EFE_RADIAL_HYDROGENIC = 1, EFE_RADIAL_GAUSSIAN = 2 };
+
+/* External field E(t) of Eq. VField, v_f = -E(t) . x. */
+enum {
+  EFE_FIELD_NONE = 0,
+  EFE_FIELD_GAUSS = 1,       /* amp exp(-(t-t0)^2 / (2 sigma^2)) dir */
+  EFE_FIELD_SINE_GAUSS = 2,  /* amp sin(omega t) exp(-(t-t0)^2 / (2 sigma^2)) dir */
+  EFE_FIELD_SINE_TRAP = 3,   /* amp sin(omega t) env(t) dir; env ramps linearly over `ramp`
+                                at both ends of [0, period], zero outside */
+  EFE_FIELD_SINE_SINE = 4    /* amp sin(pi t / period) sin(omega t) dir on [0, period] */
+};
+
+typedef struct {
+  int32_t ncx, ncy, ncz;      /* cells per axis, >= 1 */
+  const double* xb_host;      /* ncx + 1 strictly increasing cell boundaries */
+  const double* yb_host;      /* ncy + 1 */
+  const double* zb_host;      /* ncz + 1 */
+  int32_t degree;             /* p in [2, 5] */
+  int32_t n_quad;             /* Gauss-Legendre points per direction; must be p + 2 */
+} efe_mesh_desc;
+
+typedef struct {
+  double Z;                   /* nuclear charge */
+  double R[3];                /* position */
+} efe_atom;
+
+typedef struct {
+  int32_t atom;               /* index into the atom array */
+  int32_t n, l, m;            /* quantum numbers, l <= 2, |m| <= l */
+  int32_t radial;             /* EFE_RADIAL_* */
+  double zeta;                /* exponent / effective charge */
+} efe_enrich_fn;
+
+typedef struct {
+  int32_t n_fn;
+  const efe_enrich_fn* fns_host;
+  double r0;                  /* cutoff radius: N^A = 0 for r >= r0 */
+  double s;                   /* cutoff width: N^A untouched for r <= r0 - s */
+} efe_enrich_desc;
+
+typedef struct {
+  int32_t kind;               /* EFE_FIELD_* */
+  double amp, omega, t0, sigma, period, ramp;
+  double dir[3];
+  double kick;                /* delta-kick strength used by efe_kick (0: none) */
+} efe_field;
+
+typedef struct {
+  int32_t n_orb;              /* orbitals per batch member */
+  int32_t batch;              /* independent propagations (own density, potential, field) */
+  const double* occ_host;     /* n_orb occupations (2.0 for doubly occupied) */
+  double krylov_tol;          /* Lanczos stop threshold on eps_k of Eq. AdaptiveKrylovErr */
+  int32_t k_max;              /* Lanczos cap, 1 <= k_max <= 32 */
+  int32_t fixed_k;            /* > 0: take exactly fixed_k Lanczos steps (tests) */
+  double cg_tol;              /* Hartree PCG relative residual target */
+  int32_t cg_max_it;
+  int32_t precision;          /* efe_precision used by efe_magnus_step and efe_kick */
+} efe_options;
+
+typedef struct {
+  int32_t k_pred_max;         /* largest Lanczos dimension used in the predictor */
+  int32_t k_corr_max;         /* ... and in the corrector */
+  int32_t krylov_cap_hit;     /* columns that reached k_max */
+  int32_t cg_iters;           /* total Hartree PCG iterations in the step */
+  double eps_max;             /* largest final Krylov error estimate */
+} efe_step_info;
+
+/* ---- set-up (Secs. "Enriched finite element discretization", "Spectral finite
+ * elements"): builds the GLL basis, Gauss-Legendre quadrature, the lumped
+ * diagonal M^cc, the enrichment functions at every quadrature point of the
+ * cells their support reaches, the orthogonalisation coefficients
+ * c = b / M^cc (Eq. EFEOrtho), M^ee and (M^ee)^(+-1/2) (Eq. MSquareRoot), the
+ * kinetic coupling blocks, the nuclear potential v_N (Eq. VN) at the quadrature
+ * points and the Dirichlet data of the Hartree problem.  All host inputs are
+ * copied.  Runs on the current CUDA device and synchronises it.
+ * Errors: EFE_ERR_ARG, EFE_ERR_NOMEM, EFE_ERR_CUDA, EFE_ERR_NOT_SPD.  On error
+ * *out is NULL and the message is available from efe_last_error(NULL). */
+efe_status efe_setup(const efe_mesh_desc* mesh, const efe_atom* atoms_host, int32_t n_atoms,
+                     const efe_enrich_desc* enrich, const efe_options* opts, efe_ctx** out);
+
+/* Frees every device allocation of the context (synchronises the device). */
+efe_status efe_destroy(efe_ctx* ctx);
+
+/* Last error message of ctx (or of the last failed efe_setup when ctx is NULL). */
+const char* efe_last_error(const efe_ctx* ctx);
+
+/* Sizes: n_nodes, n_enrich, n_cells, n_q (points per cell), n_pairs (cell-function
+ * pairs of the enrichment support).  Any pointer may be NULL. */
+efe_status efe_sizes(const efe_ctx* ctx, int64_t* n_nodes, int64_t* n_enrich, int64_t* n_cells,
+                     int64_t* n_q, int64_t* n_pairs);
+
+/* Node coordinates [n_nodes][3] (float64, device) and quadrature point
+ * coordinates [n_cells][n_q][3] (device; either may be NULL). */
+efe_status efe_coords(efe_ctx* ctx, double* node_xyz_dev, double* quad_xyz_dev, void* stream);
+
+/* Builds the operator Hbar = M^-1/2 P^T H_ext P M^-1/2 (Eqs. Hmn, TDKSDiscrete2)
+ * for `batch` potentials v_dev [batch][n_cells][n_q] given at the quadrature
+ * points: H = kin_scale * (1/2) int grad N . grad N + int v N N.  The operator
+ * is held by the context and used by efe_apply_H until the next build. */
+efe_status efe_set_potential(efe_ctx* ctx, const double* v_dev, int32_t batch, double kin_scale,
+                             void* stream);
+
+/* Y = Hbar X (Eq. TDKSDiscrete2) for the operator of the last efe_set_potential.
+ * X_dev, Y_dev: complex128 [n_dof][ld] (ld >= n_cols complex entries per row);
+ * the first n_cols columns are used, n_cols = n_orb_per_member * batch of that
+ * operator.  The four steps run on the device: gather (with M^-1/2), cell
+ * contraction (kinetic + v-weighted mass), scatter-add (with M^-1/2) and the
+ * enrichment coupling.  X and Y must not overlap. */
+efe_status efe_apply_H(efe_ctx* ctx, const double* X_dev, double* Y_dev, int64_t n_cols, int64_t ld,
+                       int32_t precision, void* stream);
+
+/* One second-order Magnus step (Eq. ApproxMagnus) evaluated by the adaptive
+ * Lanczos exponential (Eqs. AdaptiveKrylov, AdaptiveKrylovErr) with the
+ * predictor-corrector for the mid-point Hamiltonian:
+ *   S1 psi^p = Kexp(Hbar[v(rho_n), E(t+dt/2)]) psi_n;  S2 rho^p = rho(psi^p);
+ *   S3 rho_mid = (rho_n + rho^p)/2;  S4 v_mid = v_N + v_H[rho_mid] + v_xc[rho_mid]
+ *   - E(t+dt/2).x;  S5 psi_n+1 = Kexp(Hbar[v_mid]) psi_n;  S6 rho_n+1, v_H, v_xc,
+ *   dipole.
+ * psi_bar_dev is overwritten with psi_n+1.  fields_host: `batch` field
+ * descriptions.  mu_dev: NULL or device float64 [batch][3] receiving the dipole
+ * at t + dt.  info_host: NULL, or filled after synchronising `stream`.
+ * The density-derived potentials of step n are kept in the context from the
+ * previous step; the first step after efe_setup, efe_kick or efe_reset_state
+ * recomputes them from psi_bar. */
+efe_status efe_magnus_step(efe_ctx* ctx, double* psi_bar_dev, double t, double dt,
+                           const efe_field* fields_host, double* mu_dev, efe_step_info* info_host,
+                           void* stream);
+
+/* Forgets the cached density-derived potentials (call after changing psi_bar). */
+efe_status efe_reset_state(efe_ctx* ctx);
+
+/* Density rho_q = sum_alpha occ_alpha |psi_alpha(x_q)|^2 per batch member
+ * (Sec. "Time dependent Kohn-Sham equations"), psi(x_q) from Eq. PsiEFE, and
+ * the LDA v_xc (Slater exchange + PW92 correlation) and eps_xc at the same
+ * points.  vxc_dev / exc_dev may be NULL. */
+efe_status efe_density_vxc(efe_ctx* ctx, const double* psi_bar_dev, double* rho_dev, double* vxc_dev,
+                           double* exc_dev, void* stream);
+
+/* Hartree potential (Eqs. Hartree_possion, DiscretePoisson): Jacobi-preconditioned
+ * CG for (1/4pi) K phi = d, d_i = int rho N_i, phi = sum Z_I / |x - R_I| on the
+ * boundary, warm-started from the previous solution held by the context;
+ * vH_dev receives phi interpolated to the quadrature points [batch][n_cells][n_q].
+ * iters_host: NULL or receives the iteration count (synchronises `stream`).
+ * Returns EFE_ERR_CG_NOCONV (after writing the last iterate) if tol is not met. */
+efe_status efe_hartree(efe_ctx* ctx, const double* rho_dev, double* vH_dev, double tol, int32_t max_it,
+                       int32_t* iters_host, void* stream);
+
+/* Dipole mu = sum_I Z_I R_I - int x rho for each batch member; mu_dev [batch][3]. */
+efe_status efe_dipole(efe_ctx* ctx, const double* rho_dev, double* mu_dev, void* stream);
+
+/* Delta kick psi_bar <- exp(i kick d.Xbar) psi_bar per batch member, with Xbar the
+ * Loewdin-transformed position operator, by the same Lanczos exponential. */
+efe_status efe_kick(efe_ctx* ctx, double* psi_bar_dev, const efe_field* fields_host, void* stream);
+
+/* Initial orbitals from Gaussian descriptors: classical coefficients
+ * psi^C_i = sum_g coef[a][g] exp(-expo[a][g] |x_i - center[a][g]|^2) (zero on
+ * the boundary), enrichment coefficients enr[a][nu]; psi_bar = M^1/2 psi, the
+ * same for every batch member.  Host arrays: centers [n_orb][G][3], expo
+ * [n_orb][G], coef and enr complex128 interleaved [n_orb][G] / [n_orb][n_enrich]. */
+efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss, const double* centers_host,
+                             const double* expo_host, const double* coef_host, const double* enr_host,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EFE_H */

@@ -1,0 +1,248 @@
+"""ctypes binding of libefe (include/efe.h): the same entry points, with torch
+tensors marshalled to device pointers.  No numerical step runs here: every
+call goes to the CUDA library, and loading fails loudly if it is missing."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libefe.so")
+
+EFE_OK, EFE_ERR_ARG, EFE_ERR_NOMEM, EFE_ERR_CUDA, EFE_ERR_NOT_SPD = 0, 1, 2, 3, 4
+EFE_WARN_KRYLOV_CAP, EFE_ERR_CG_NOCONV, EFE_ERR_TIMEOUT, EFE_ERR_STATE = 5, 6, 7, 8
+EFE_FP64, EFE_MIXED = 0, 1
+STATUS_NAMES = {0: "EFE_OK", 1: "EFE_ERR_ARG", 2: "EFE_ERR_NOMEM", 3: "EFE_ERR_CUDA", 4: "EFE_ERR_NOT_SPD",
+                5: "EFE_WARN_KRYLOV_CAP", 6: "EFE_ERR_CG_NOCONV", 7: "EFE_ERR_TIMEOUT", 8: "EFE_ERR_STATE"}
+
+EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coords", "efe_set_potential",
+            "efe_apply_H", "efe_magnus_step", "efe_reset_state", "efe_density_vxc", "efe_hartree", "efe_dipole",
+            "efe_kick", "efe_init_orbitals"]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("ncx", C.c_int32), ("ncy", C.c_int32), ("ncz", C.c_int32), ("xb_host", C.POINTER(C.c_double)),
+                ("yb_host", C.POINTER(C.c_double)), ("zb_host", C.POINTER(C.c_double)), ("degree", C.c_int32),
+                ("n_quad", C.c_int32)]
+
+
+class Atom(C.Structure):
+    _fields_ = [("Z", C.c_double), ("R", C.c_double * 3)]
+
+
+class EnrichFn(C.Structure):
+    _fields_ = [("atom", C.c_int32), ("n", C.c_int32), ("l", C.c_int32), ("m", C.c_int32), ("radial", C.c_int32),
+                ("zeta", C.c_double)]
+
+
+class EnrichDesc(C.Structure):
+    _fields_ = [("n_fn", C.c_int32), ("fns_host", C.POINTER(EnrichFn)), ("r0", C.c_double), ("s", C.c_double)]
+
+
+class Field(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("amp", C.c_double), ("omega", C.c_double), ("t0", C.c_double),
+                ("sigma", C.c_double), ("period", C.c_double), ("ramp", C.c_double), ("dir", C.c_double * 3),
+                ("kick", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("n_orb", C.c_int32), ("batch", C.c_int32), ("occ_host", C.POINTER(C.c_double)),
+                ("krylov_tol", C.c_double), ("k_max", C.c_int32), ("fixed_k", C.c_int32), ("cg_tol", C.c_double),
+                ("cg_max_it", C.c_int32), ("precision", C.c_int32)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("k_pred_max", C.c_int32), ("k_corr_max", C.c_int32), ("krylov_cap_hit", C.c_int32),
+                ("cg_iters", C.c_int32), ("eps_max", C.c_double)]
+
+
+_lib = None
+
+
+def lib(path: str = LIB_PATH):
+    """Loads libefe.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libefe.so not found at %s: build it with `python -c \"import __graft_entry__ as g; "
+                           "g.build()\"`; there is no CPU fallback" % path)
+    L = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    pdbl = C.POINTER(C.c_double)
+    L.efe_setup.argtypes = [C.POINTER(MeshDesc), C.POINTER(Atom), i32, C.POINTER(EnrichDesc), C.POINTER(Options),
+                            C.POINTER(vp)]
+    L.efe_destroy.argtypes = [vp]
+    L.efe_last_error.argtypes = [vp]
+    L.efe_last_error.restype = C.c_char_p
+    L.efe_sizes.argtypes = [vp] + [C.POINTER(i64)] * 5
+    L.efe_coords.argtypes = [vp, vp, vp, vp]
+    L.efe_set_potential.argtypes = [vp, vp, i32, dbl, vp]
+    L.efe_apply_H.argtypes = [vp, vp, vp, i64, i64, i32, vp]
+    L.efe_magnus_step.argtypes = [vp, vp, dbl, dbl, C.POINTER(Field), vp, C.POINTER(StepInfo), vp]
+    L.efe_reset_state.argtypes = [vp]
+    L.efe_density_vxc.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.efe_hartree.argtypes = [vp, vp, vp, dbl, i32, C.POINTER(i32), vp]
+    L.efe_dipole.argtypes = [vp, vp, vp, vp]
+    L.efe_kick.argtypes = [vp, vp, C.POINTER(Field), vp]
+    L.efe_init_orbitals.argtypes = [vp, vp, i32, pdbl, pdbl, pdbl, pdbl, vp]
+    for name in EXPORTED:
+        if name != "efe_last_error":
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+class EfeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def fields_array(fields):
+    arr = (Field * len(fields))()
+    for i, f in enumerate(fields):
+        arr[i].kind = int(f.kind)
+        arr[i].amp, arr[i].omega, arr[i].t0 = float(f.amp), float(f.omega), float(f.t0)
+        arr[i].sigma, arr[i].period, arr[i].ramp = float(f.sigma), float(f.period), float(f.ramp)
+        for k in range(3):
+            arr[i].dir[k] = float(f.direction[k])
+        arr[i].kick = float(f.kick)
+    return arr
+
+
+class Context:
+    """Owns one efe_ctx built from an `efe_workloads.Workload`."""
+
+    def __init__(self, wl, precision: int = EFE_FP64, krylov_tol=None, k_max=None, fixed_k: int = 0,
+                 cg_tol: float = 1e-12, cg_max_it: int = 5000):
+        L = lib()
+        self.wl = wl
+        self._keep = []
+        xb, yb, zb = (np.ascontiguousarray(b, dtype=np.float64) for b in (wl.xb, wl.yb, wl.zb))
+        self._keep += [xb, yb, zb]
+        mesh = MeshDesc(len(xb) - 1, len(yb) - 1, len(zb) - 1, _dptr(xb), _dptr(yb), _dptr(zb), int(wl.degree),
+                        int(wl.n_quad))
+        na = len(wl.Z)
+        atoms = (Atom * max(na, 1))()
+        for i in range(na):
+            atoms[i].Z = float(wl.Z[i])
+            for k in range(3):
+                atoms[i].R[k] = float(wl.R[i][k])
+        fns = (EnrichFn * max(len(wl.enrich), 1))()
+        for i, f in enumerate(wl.enrich):
+            fns[i] = EnrichFn(int(f.atom), int(f.n), int(f.l), int(f.m), int(f.radial), float(f.zeta))
+        enr = EnrichDesc(len(wl.enrich), fns, float(wl.r0), float(wl.s))
+        occ = np.ascontiguousarray(wl.occ, dtype=np.float64)
+        self._keep.append(occ)
+        opts = Options(int(wl.n_orb), int(wl.batch), _dptr(occ),
+                       float(wl.krylov_tol if krylov_tol is None else krylov_tol),
+                       int(wl.k_max if k_max is None else k_max), int(fixed_k), float(cg_tol), int(cg_max_it),
+                       int(precision))
+        h = C.c_void_p()
+        st = L.efe_setup(C.byref(mesh), atoms, na, C.byref(enr), C.byref(opts), C.byref(h))
+        if st != EFE_OK:
+            raise EfeError(st, L.efe_last_error(None).decode())
+        self.h = h
+        v = [C.c_int64() for _ in range(5)]
+        L.efe_sizes(self.h, *[C.byref(x) for x in v])
+        self.n_nodes, self.n_enrich, self.n_cells, self.n_q, self.n_pairs = (x.value for x in v)
+        self.n_dof = self.n_nodes + self.n_enrich
+        self.n_cols = wl.n_orb * wl.batch
+
+    def _check(self, st, allow=(EFE_OK,)):
+        if st not in allow:
+            raise EfeError(st, lib().efe_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().efe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- entry points (same names as the C ABI, without the prefix)
+    def coords(self):
+        import torch
+        nodes = torch.empty((self.n_nodes, 3), dtype=torch.float64, device="cuda")
+        quad = torch.empty((self.n_cells, self.n_q, 3), dtype=torch.float64, device="cuda")
+        self._check(lib().efe_coords(self.h, _ptr(nodes), _ptr(quad), _stream()))
+        return nodes, quad
+
+    def set_potential(self, v, kin_scale: float = 1.0):
+        assert v.is_cuda and v.dtype.is_floating_point and v.is_contiguous()
+        batch = v.shape[0] if v.dim() == 3 else 1
+        self._check(lib().efe_set_potential(self.h, _ptr(v), int(batch), float(kin_scale), _stream()))
+
+    def apply_H(self, X, Y, precision: int = EFE_FP64):
+        """X, Y: complex128 [n_dof, n_cols] (or any ld >= n_cols) on the device."""
+        n_cols = X.shape[1]
+        ld = X.stride(0)
+        assert Y.stride(0) == ld and X.dtype == Y.dtype
+        self._check(lib().efe_apply_H(self.h, _ptr(X), _ptr(Y), int(n_cols), int(ld), int(precision), _stream()))
+        return Y
+
+    def magnus_step(self, psi, t, dt, fields, mu=None):
+        info = StepInfo()
+        arr = fields_array(fields)
+        st = lib().efe_magnus_step(self.h, _ptr(psi), float(t), float(dt), arr, _ptr(mu), C.byref(info), _stream())
+        self._check(st, allow=(EFE_OK, EFE_WARN_KRYLOV_CAP))
+        return {"k_pred": info.k_pred_max, "k_corr": info.k_corr_max, "cap": info.krylov_cap_hit,
+                "cg_iters": info.cg_iters, "eps_max": info.eps_max, "status": st}
+
+    def magnus_step_async(self, psi, t, dt, fields_arr, mu=None):
+        """Same as magnus_step with a prepared field array and no host-visible info."""
+        st = lib().efe_magnus_step(self.h, _ptr(psi), float(t), float(dt), fields_arr, _ptr(mu), None, _stream())
+        return self._check(st, allow=(EFE_OK, EFE_WARN_KRYLOV_CAP))
+
+    def reset_state(self):
+        self._check(lib().efe_reset_state(self.h))
+
+    def density_vxc(self, psi, rho, vxc=None, exc=None):
+        self._check(lib().efe_density_vxc(self.h, _ptr(psi), _ptr(rho), _ptr(vxc), _ptr(exc), _stream()))
+
+    def hartree(self, rho, vH, tol=1e-12, max_it=5000):
+        its = C.c_int32()
+        st = lib().efe_hartree(self.h, _ptr(rho), _ptr(vH), float(tol), int(max_it), C.byref(its), _stream())
+        self._check(st)
+        return its.value
+
+    def dipole(self, rho, mu):
+        self._check(lib().efe_dipole(self.h, _ptr(rho), _ptr(mu), _stream()))
+
+    def kick(self, psi, fields):
+        st = lib().efe_kick(self.h, _ptr(psi), fields_array(fields), _stream())
+        return self._check(st, allow=(EFE_OK, EFE_WARN_KRYLOV_CAP))
+
+    def init_orbitals(self, psi):
+        wl = self.wl
+        G = wl.orb_centers.shape[1]
+        cen = np.ascontiguousarray(wl.orb_centers, dtype=np.float64)
+        ex = np.ascontiguousarray(wl.orb_exps, dtype=np.float64)
+        co = np.ascontiguousarray(np.stack([wl.orb_coefs.real, wl.orb_coefs.imag], axis=-1), dtype=np.float64)
+        en = np.ascontiguousarray(np.stack([wl.enr_coefs.real, wl.enr_coefs.imag], axis=-1), dtype=np.float64)
+        if en.size == 0:
+            en = np.zeros(2)
+        self._check(lib().efe_init_orbitals(self.h, _ptr(psi), int(G), _dptr(cen), _dptr(ex), _dptr(co), _dptr(en),
+                                            _stream()))
+        return psi

@@ -1,0 +1,188 @@
+// Internal declarations of libefe (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/efe.h"
+
+namespace efe {
+
+constexpr int kMaxP1 = 6;    // degree <= 5
+constexpr int kMaxNQ1 = 7;   // n_quad = p + 2
+constexpr int kMaxK = 32;    // Lanczos cap
+constexpr int kThreads = 256;
+
+// 1D reference tables on [-1, 1], passed to kernels by value (parameter space is
+// the constant bank, so warp-uniform reads broadcast).
+struct RefTables {
+  double B1[kMaxNQ1 * kMaxP1];   // l_i(xg_q), [q][i]
+  double D1[kMaxNQ1 * kMaxP1];   // l_i'(xg_q)
+  double K1[kMaxP1 * kMaxP1];    // int l_i' l_j'
+  double M1[kMaxP1 * kMaxP1];    // int l_i l_j
+  double wg[kMaxNQ1];            // GL weights
+  double xg[kMaxNQ1];            // GL points
+  float B1f[kMaxNQ1 * kMaxP1];
+  float D1f[kMaxNQ1 * kMaxP1];
+  float K1f[kMaxP1 * kMaxP1];
+  float M1f[kMaxP1 * kMaxP1];
+};
+
+// Rectilinear mesh, device view (pointers to per-axis arrays).
+struct MeshView {
+  int ncx, ncy, ncz;
+  int Nx, Ny, Nz;
+  int p;
+  int nc;
+  long long n_h;
+  const double* x0;   // cell origins, x then y then z, size ncx + ncy + ncz
+  const double* h;    // cell sizes, same layout
+};
+
+__host__ __device__ inline void cell_ijk(const MeshView& m, int c, int& cx, int& cy, int& cz) {
+  cx = c % m.ncx;
+  int t = c / m.ncx;
+  cy = t % m.ncy;
+  cz = t / m.ncy;
+}
+
+__host__ __device__ inline long long node_index(const MeshView& m, int cx, int cy, int cz, int i1, int i2, int i3) {
+  return (long long)(cx * m.p + i1) + (long long)m.Nx * ((long long)(cy * m.p + i2) + (long long)m.Ny * (cz * m.p + i3));
+}
+
+// Operator held by the context (one per batch member for the v-dependent parts).
+struct Operator {
+  int batch = 0;
+  double kin = 1.0;
+  double* W64 = nullptr;    // [batch][nc][nq]  w_q |J| v(x_q)
+  float* W32 = nullptr;
+  double* E64 = nullptr;    // [batch][n_pairs][nn] classical-enriched coupling E_c
+  float* E32 = nullptr;
+  double* HEE = nullptr;    // [batch][nE][nE] enriched-enriched block (before M^ee^-1/2 scaling)
+  bool valid = false;
+};
+
+struct Ctx {
+  int device = 0;
+  std::string err;
+  // sizes
+  int p = 0, P1 = 0, NQ1 = 0, nn = 0, nq = 0;
+  int ncx = 0, ncy = 0, ncz = 0, nc = 0;
+  int Nx = 0, Ny = 0, Nz = 0;
+  long long n_h = 0;
+  int nE = 0;
+  long long n_dof = 0;
+  int n_atoms = 0;
+  std::vector<double> Z, R;               // host copies
+  std::vector<efe_enrich_fn> fns;
+  double r0 = 0, s = 0;
+  std::vector<double> xb, yb, zb;
+  RefTables tab{};
+  MeshView mesh{};
+  // options
+  int n_orb = 0, batch = 0;
+  std::vector<double> occ;
+  double krylov_tol = 1e-12;
+  int k_max = 16, fixed_k = 0;
+  double cg_tol = 1e-12;
+  int cg_max_it = 2000;
+  int precision = EFE_FP64;
+  // device tables
+  double* d_geo = nullptr;     // x0 (ncx+ncy+ncz) then h (ncx+ncy+ncz)
+  double* d_Dsc = nullptr;     // [n_h] mask / sqrt(M)
+  double* d_M = nullptr;       // [n_h] lumped mass
+  double* d_occ = nullptr;     // [n_orb]
+  double* d_vN = nullptr;      // [nc][nq]
+  double* d_wJ = nullptr;      // [nc][nq]
+  double* d_xq = nullptr;      // [nc][nq][3]
+  // enrichment support: pairs (cell, function), CSR by cell
+  long long n_pairs = 0;
+  int* d_pair_start = nullptr; // [nc + 1]
+  int* d_pair_fn = nullptr;    // [n_pairs]
+  int* d_pair_cell = nullptr;  // [n_pairs]
+  double* d_Atil = nullptr;    // [n_pairs][nq] values of N^E at quadrature points
+  double* d_KE = nullptr;      // [n_pairs][nn] 1/2 int grad N_i . grad N^E
+  double* d_KEE = nullptr;     // [nE][nE] 1/2 int grad N^E . grad N^E
+  double* d_S = nullptr;       // [nE][nE] (M^ee)^-1/2
+  double* d_Shalf = nullptr;   // [nE][nE] (M^ee)^1/2
+  std::vector<double> Mee, S, Shalf;
+  int max_pairs_per_cell = 0;
+  // Poisson
+  double* d_diagA = nullptr;   // [n_h] diagonal of (1/4pi) K at interior nodes (1 elsewhere)
+  double* d_phiB = nullptr;    // [n_h] Dirichlet data (zero inside)
+  double* d_phi = nullptr;     // [n_h][batch] warm start / last solution
+  // operators
+  Operator op;                 // current operator (efe_set_potential / magnus)
+  // state (density-derived potentials of the current step)
+  bool state_valid = false;
+  double* d_rho = nullptr;     // [batch][nc][nq]
+  double* d_vH = nullptr;
+  double* d_vxc = nullptr;
+  // workspaces
+  long long ws_cols = 0;       // complex columns the workspaces are sized for
+  double* d_Q = nullptr;       // [(k_max + 1)][n_dof][cols] complex
+  double* d_psi_p = nullptr;   // [n_dof][cols] complex
+  double* d_xE = nullptr;      // [nE][2 cols] S x^E
+  double* d_yE = nullptr;      // [nE][2 cols] enriched accumulator
+  double* d_lz = nullptr;      // Lanczos scalars per column (see k_vector.cu)
+  int* d_lzi = nullptr;        // Lanczos integer state per column
+  double* h_lz = nullptr;      // pinned mirror for step info
+  int* h_flag = nullptr;       // pinned flag
+  double* d_rho2 = nullptr;    // [batch][nc][nq] scratch densities
+  double* d_v = nullptr;       // [batch][nc][nq] potential scratch
+  double* d_cg = nullptr;      // CG vectors [5][n_h][batch] + scalars
+  double* d_red = nullptr;     // reduction scratch
+  ~Ctx();
+};
+
+// ---- host math (host_math.cu)
+void gauss_legendre(int n, double* x, double* w);
+void gauss_lobatto(int p, double* x, double* w);
+void lagrange_tables(int n_nodes, const double* nodes, int n_pts, const double* pts, double* L, double* dL);
+bool jacobi_eigen(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& lam);
+
+// ---- launch wrappers (k_*.cu); all return cudaGetLastError() of the launch
+cudaError_t launch_geometry(const Ctx& c, cudaStream_t s);                       // wJ, xq, vN
+cudaError_t launch_enrich_setup(Ctx& c, cudaStream_t s);                         // Atil, KE, KEE, Mee parts
+cudaError_t launch_poisson_setup(Ctx& c, cudaStream_t s);                        // diagA, phiB
+cudaError_t launch_coords(const Ctx& c, double* nodes, double* quad, cudaStream_t s);
+cudaError_t launch_init_orbitals(const Ctx& c, double* psi, int n_gauss, const double* d_centers,
+                                 const double* d_expo, const double* d_coef, const double* d_enr, cudaStream_t s);
+
+// operator build: W = wJ * v (per member), E = kin*KE + B^T (W Atil), HEE = kin*KEE + Atil^T W Atil
+cudaError_t launch_build_operator(Ctx& c, const double* v, int batch, double kin, cudaStream_t s);
+// Y = Hbar X on n_cols complex columns (per member operator), ld in complex entries
+cudaError_t launch_apply(Ctx& c, const double* X, double* Y, long long n_cols, long long ld, int precision,
+                         cudaStream_t s);
+
+// Lanczos exponential: out = Kexp(-i dt_col Hbar) in for every complex column, with the
+// operator held in Ctx::op; dts_host [n_cols]; host-visible statistics after a stream sync.
+cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* dts_host, int precision,
+                          int* kmax_used, int* cap_hits, double* eps_max, cudaStream_t s);
+
+// density / xc / dipole
+cudaError_t launch_density(Ctx& c, const double* psi, double* rho, cudaStream_t s);
+cudaError_t launch_lda(const Ctx& c, const double* rho, double* vxc, double* exc, long long n, cudaStream_t s);
+cudaError_t launch_dipole(const Ctx& c, const double* rho, double* mu, cudaStream_t s);
+double field_amp(const efe_field& f, double t);
+cudaError_t launch_potential_sum(const Ctx& c, const double* vH, const double* vxc, const double* E_host,
+                                 bool nuclear, double* v, cudaStream_t s);
+cudaError_t launch_laplace(const Ctx& c, const double* x, double* y, int nb, int mask_in, double scale,
+                           cudaStream_t s);
+cudaError_t launch_load_vector(const Ctx& c, const double* f, double* d, int nb, cudaStream_t s);
+cudaError_t launch_interp(const Ctx& c, const double* x, double* out, int nb, cudaStream_t s);
+cudaError_t launch_axpby(double* y, const double* a, const double* b, double ca, double cb, long long n,
+                         cudaStream_t s);
+// Hartree PCG; iters returned (synchronises)
+efe_status run_hartree(Ctx& c, const double* rho, double* vH, double tol, int max_it, int* iters, cudaStream_t s);
+
+}  // namespace efe
+
+#define EFE_CUDA_TRY(expr)                                                   \
+  do {                                                                       \
+    cudaError_t _e = (expr);                                                 \
+    if (_e != cudaSuccess) return _e;                                        \
+  } while (0)

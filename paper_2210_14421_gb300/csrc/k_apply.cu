@@ -1,0 +1,516 @@
+// The EFE Hamiltonian apply and the cell-local operators built on it.
+//
+// Hbar = M^-1/2 H M^-1/2 (Eq. TDKSDiscrete2) with H = P^T H_ext P (Eqs. Hmn,
+// EFESplit, EFEOrtho) is applied as
+//   x^C = D x_bar^C, x^E = S x_bar^E                 D = mask / sqrt(M^cc), S = (M^ee)^-1/2
+//   y^C = sum_c G_c^T (H_c G_c x^C + E_c x^E)        cell gather / contraction / scatter-add
+//   y^E = sum_c E_c^T G_c x^C + H_EE x^E              enrichment coupling
+//   y_bar^C = D y^C, y_bar^E = S y^E
+// where H_c is the classical cell matrix (kinetic + v-weighted mass, applied by
+// sum factorisation), E_c = 1/2 int grad N_i . grad N^E_nu + int v N_i N^E_nu is
+// the cell's classical-enriched block for the orthogonalised enrichment
+// functions N^E = N^A - sum_l c_l N^C_l, and H_EE the enriched-enriched block.
+// These are P^T H_ext P written out block by block, so no P is applied at run time.
+#include <cstdio>
+#include <type_traits>
+
+#include "efe_internal.h"
+#include "sumfact.cuh"
+
+namespace efe {
+
+// Slots per tile from the shared-memory budget: four tile buffers of
+// NQ1^3 * RT entries of T in ~110 KB, so two blocks fit on one SM.
+template <typename T, int NQ1>
+constexpr int tile_rt() {
+  return (110 * 1024) / (4 * NQ1 * NQ1 * NQ1 * (int)sizeof(T)) >= 32   ? 32
+         : (110 * 1024) / (4 * NQ1 * NQ1 * NQ1 * (int)sizeof(T)) >= 16 ? 16
+         : (110 * 1024) / (4 * NQ1 * NQ1 * NQ1 * (int)sizeof(T)) >= 8  ? 8
+                                                                         : 4;
+}
+
+template <typename T, int NQ1>
+constexpr size_t tile_smem() {
+  return (size_t)4 * NQ1 * NQ1 * NQ1 * tile_rt<T, NQ1>() * sizeof(T) + 3 * 32 * sizeof(T);
+}
+
+// ----------------------------------------------------------------------------
+// cell apply: one block per (cell, batch member); the block walks the member's
+// real columns in tiles of RT slots.
+// ----------------------------------------------------------------------------
+template <typename T, int P1, int NQ1, bool ENR>
+__global__ void __launch_bounds__(kThreads)
+k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ X,
+             double* __restrict__ Y, long long ld2, int cols_member, const double* __restrict__ Dsc,
+             const T* __restrict__ W, double kin, const int* __restrict__ pair_start,
+             const int* __restrict__ pair_fn, const T* __restrict__ E, long long n_pairs,
+             const double* __restrict__ xE, double* __restrict__ yE) {
+  constexpr int RT = tile_rt<T, NQ1>();
+  constexpr int S3 = NQ1 * NQ1 * NQ1;
+  constexpr int NN = P1 * P1 * P1;
+  constexpr int NQ = S3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* B = A + S3 * RT;
+  T* C = B + S3 * RT;
+  T* D = C + S3 * RT;
+  T* ax = D + S3 * RT;
+  T* ay = ax + 32;
+  T* az = ay + 32;
+
+  const int c = blockIdx.x;
+  const int member = blockIdx.y;
+  int cx, cy, cz;
+  cell_ijk(mesh, c, cx, cy, cz);
+  const double hx = mesh.h[cx], hy = mesh.h[mesh.ncx + cy], hz = mesh.h[mesh.ncx + mesh.ncy + cz];
+  if (threadIdx.x < RT) {
+    ax[threadIdx.x] = (T)(kin * hy * hz / (4.0 * hx));
+    ay[threadIdx.x] = (T)(kin * hx * hz / (4.0 * hy));
+    az[threadIdx.x] = (T)(kin * hx * hy / (4.0 * hz));
+  }
+  const T* Wc = W + ((long long)member * mesh.nc + c) * NQ;
+  int p0 = 0, np = 0;
+  if (ENR) {
+    p0 = pair_start[c];
+    np = pair_start[c + 1] - p0;
+  }
+  const T* Ec = ENR ? E + ((long long)member * n_pairs + p0) * NN : nullptr;
+  const int col0 = member * cols_member;
+  const int n_tiles = (cols_member + RT - 1) / RT;
+
+  for (int tile = 0; tile < n_tiles; ++tile) {
+    const int cbase = tile * RT;
+    // gather x^C = D x_bar^C into A
+    for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
+      const int r = it % RT, l = it / RT;
+      const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
+      const long long g = node_index(mesh, cx, cy, cz, i1, i2, i3);
+      T v = T(0);
+      if (cbase + r < cols_member) v = (T)(Dsc[g] * X[g * ld2 + col0 + cbase + r]);
+      A[l * RT + r] = v;
+    }
+    __syncthreads();
+    // kinetic part into B
+    kinetic_tile<T, P1, RT>(tab, A, B, C, D, ax, ay, az);
+    // v-weighted mass: B += B1^T diag(W) B1 X
+    interp_fwd<T, P1, NQ1, RT>(tab, A, C, D);
+    for (int it = threadIdx.x; it < NQ * RT; it += blockDim.x) C[it] *= Wc[it / RT];
+    __syncthreads();
+    interp_bwd<T, P1, NQ1, RT, true>(tab, C, B, D, C);
+    if (ENR && np > 0) {
+      // y^C += E_c x^E  and  y^E += E_c^T x^C
+      for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
+        const int r = it % RT, l = it / RT;
+        if (cbase + r >= cols_member) continue;
+        T acc = T(0);
+        for (int k = 0; k < np; ++k) acc = fma(Ec[(long long)k * NN + l], (T)xE[(long long)pair_fn[p0 + k] * ld2 + col0 + cbase + r], acc);
+        B[l * RT + r] += acc;
+      }
+      for (int it = threadIdx.x; it < np * RT; it += blockDim.x) {
+        const int r = it % RT, k = it / RT;
+        if (cbase + r >= cols_member) continue;
+        const T* e = Ec + (long long)k * NN;
+        T acc = T(0);
+        for (int l = 0; l < NN; ++l) acc = fma(e[l], A[l * RT + r], acc);
+        atomicAdd(&yE[(long long)pair_fn[p0 + k] * ld2 + col0 + cbase + r], (double)acc);
+      }
+      __syncthreads();
+    }
+    // scatter-add y_bar^C += D y^C
+    for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
+      const int r = it % RT, l = it / RT;
+      if (cbase + r >= cols_member) continue;
+      const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
+      const long long g = node_index(mesh, cx, cy, cz, i1, i2, i3);
+      const double d = Dsc[g];
+      if (d != 0.0) atomicAdd(&Y[g * ld2 + col0 + cbase + r], d * (double)B[l * RT + r]);
+    }
+    __syncthreads();
+  }
+}
+
+// xE[nu][col] = sum_mu S[nu][mu] X[n_h + mu][col]
+__global__ void k_enr_pre(const double* __restrict__ S, const double* __restrict__ X, long long n_h, long long ld2,
+                          int ncols2, int nE, double* __restrict__ xE) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)nE * ncols2) return;
+  int nu = idx / ncols2, col = idx % ncols2;
+  double acc = 0.0;
+  for (int mu = 0; mu < nE; ++mu) acc += S[nu * nE + mu] * X[(n_h + mu) * ld2 + col];
+  xE[nu * ld2 + col] = acc;
+}
+
+// yE[mu][col] += sum_k HEE[member][mu][k] xE[k][col]
+__global__ void k_enr_post1(const double* __restrict__ HEE, const double* __restrict__ xE, double* __restrict__ yE,
+                            long long ld2, int ncols2, int cols_member, int nE) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)nE * ncols2) return;
+  int mu = idx / ncols2, col = idx % ncols2;
+  int member = col / cols_member;
+  const double* H = HEE + (long long)member * nE * nE + (long long)mu * nE;
+  double acc = 0.0;
+  for (int k = 0; k < nE; ++k) acc += H[k] * xE[k * ld2 + col];
+  yE[mu * ld2 + col] += acc;
+}
+
+// Y[n_h + nu][col] = sum_mu S[nu][mu] yE[mu][col]
+__global__ void k_enr_post2(const double* __restrict__ S, const double* __restrict__ yE, double* __restrict__ Y,
+                            long long n_h, long long ld2, int ncols2, int nE) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)nE * ncols2) return;
+  int nu = idx / ncols2, col = idx % ncols2;
+  double acc = 0.0;
+  for (int mu = 0; mu < nE; ++mu) acc += S[nu * nE + mu] * yE[mu * ld2 + col];
+  Y[(n_h + nu) * ld2 + col] = acc;
+}
+
+// ----------------------------------------------------------------------------
+// operator build
+// ----------------------------------------------------------------------------
+__global__ void k_op_W(const double* __restrict__ wJ, const double* __restrict__ v, double* __restrict__ W64,
+                       float* __restrict__ W32, long long n_per_member, int batch) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n_per_member * batch) return;
+  double w = wJ[idx % n_per_member] * v[idx];
+  W64[idx] = w;
+  W32[idx] = (float)w;
+}
+
+// E[member][k][l] = kin * KE[k][l] + sum_q B[q][l] W[member][cell_k][q] Atil[k][q]
+// slots = pairs (RT per block), sum-factorised B^T.
+template <int P1, int NQ1>
+__global__ void __launch_bounds__(kThreads)
+k_op_pairs(const __grid_constant__ RefTables tab, const int* __restrict__ pair_cell, long long n_pairs, int nc,
+           const double* __restrict__ Atil, const double* __restrict__ KE, const double* __restrict__ W,
+           double kin, double* __restrict__ E64, float* __restrict__ E32) {
+  constexpr int RT = tile_rt<double, NQ1>();
+  constexpr int S3 = NQ1 * NQ1 * NQ1;
+  constexpr int NN = P1 * P1 * P1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Bt = reinterpret_cast<double*>(smem_raw);
+  double* C = Bt + S3 * RT;
+  double* D = C + S3 * RT;
+  const int member = blockIdx.y;
+  const long long k0 = (long long)blockIdx.x * RT;
+  for (int it = threadIdx.x; it < S3 * RT; it += blockDim.x) {
+    const int r = it % RT, q = it / RT;
+    const long long k = k0 + r;
+    double v = 0.0;
+    if (k < n_pairs) v = W[((long long)member * nc + pair_cell[k]) * S3 + q] * Atil[k * S3 + q];
+    C[it] = v;
+  }
+  __syncthreads();
+  interp_bwd<double, P1, NQ1, RT, false>(tab, C, Bt, D, C);
+  for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
+    const int r = it % RT, l = it / RT;
+    const long long k = k0 + r;
+    if (k >= n_pairs) continue;
+    const double e = kin * KE[k * NN + l] + Bt[l * RT + r];
+    const long long o = ((long long)member * n_pairs + k) * NN + l;
+    E64[o] = e;
+    E32[o] = (float)e;
+  }
+}
+
+// HEE[member] = kin * KEE + sum_cells Atil_c^T diag(W) Atil_c
+__global__ void k_op_hee_init(const double* __restrict__ KEE, double kin, double* __restrict__ HEE, int nE, int batch) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)batch * nE * nE) return;
+  HEE[idx] = kin * KEE[idx % ((long long)nE * nE)];
+}
+
+__global__ void k_op_hee(const int* __restrict__ pair_start, const int* __restrict__ pair_fn,
+                         const double* __restrict__ Atil, const double* __restrict__ W, int nc, int nq, int nE,
+                         double* __restrict__ HEE) {
+  const int c = blockIdx.x, member = blockIdx.y;
+  const int p0 = pair_start[c], np = pair_start[c + 1] - p0;
+  if (np == 0) return;
+  const double* Wc = W + ((long long)member * nc + c) * nq;
+  for (int it = threadIdx.x; it < np * np; it += blockDim.x) {
+    const int a = it / np, b = it % np;
+    if (b < a) continue;
+    const double* fa = Atil + (long long)(p0 + a) * nq;
+    const double* fb = Atil + (long long)(p0 + b) * nq;
+    double acc = 0.0;
+    for (int q = 0; q < nq; ++q) acc += Wc[q] * fa[q] * fb[q];
+    const int ia = pair_fn[p0 + a], ib = pair_fn[p0 + b];
+    double* H = HEE + (long long)member * nE * nE;
+    atomicAdd(&H[(long long)ia * nE + ib], acc);
+    if (ia != ib) atomicAdd(&H[(long long)ib * nE + ia], acc);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// multi-cell tiles (one real column per cell and batch member): Laplacian,
+// Poisson load vector, nodal -> quadrature interpolation.  Slot s of the
+// launch covers cell s / nb and member s % nb.
+// ----------------------------------------------------------------------------
+template <int P1, int NQ1>
+__global__ void __launch_bounds__(kThreads)
+k_laplace(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ x,
+          double* __restrict__ y, int nb, const double* __restrict__ Dsc, int mask_in, double scale) {
+  constexpr int RT = tile_rt<double, NQ1>();
+  constexpr int S3 = NQ1 * NQ1 * NQ1;
+  constexpr int NN = P1 * P1 * P1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* A = reinterpret_cast<double*>(smem_raw);
+  double* B = A + S3 * RT;
+  double* C = B + S3 * RT;
+  double* D = C + S3 * RT;
+  double* ax = D + S3 * RT;
+  double* ay = ax + 32;
+  double* az = ay + 32;
+  const long long s0 = (long long)blockIdx.x * RT;
+  const long long n_slots = (long long)mesh.nc * nb;
+  if (threadIdx.x < RT) {
+    const long long s = s0 + threadIdx.x;
+    double a1 = 0, a2 = 0, a3 = 0;
+    if (s < n_slots) {
+      int cx, cy, cz;
+      cell_ijk(mesh, (int)(s / nb), cx, cy, cz);
+      const double hx = mesh.h[cx], hy = mesh.h[mesh.ncx + cy], hz = mesh.h[mesh.ncx + mesh.ncy + cz];
+      a1 = scale * hy * hz / (4.0 * hx);
+      a2 = scale * hx * hz / (4.0 * hy);
+      a3 = scale * hx * hy / (4.0 * hz);
+    }
+    ax[threadIdx.x] = a1;
+    ay[threadIdx.x] = a2;
+    az[threadIdx.x] = a3;
+  }
+  for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
+    const int r = it % RT, l = it / RT;
+    const long long s = s0 + r;
+    double v = 0.0;
+    if (s < n_slots) {
+      int cx, cy, cz;
+      cell_ijk(mesh, (int)(s / nb), cx, cy, cz);
+      const long long g = node_index(mesh, cx, cy, cz, l % P1, (l / P1) % P1, l / (P1 * P1));
+      v = x[g * nb + s % nb];
+      if (mask_in && Dsc[g] == 0.0) v = 0.0;
+    }
+    A[it] = v;
+  }
+  __syncthreads();
+  kinetic_tile<double, P1, RT>(tab, A, B, C, D, ax, ay, az);
+  for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
+    const int r = it % RT, l = it / RT;
+    const long long s = s0 + r;
+    if (s >= n_slots) continue;
+    int cx, cy, cz;
+    cell_ijk(mesh, (int)(s / nb), cx, cy, cz);
+    const long long g = node_index(mesh, cx, cy, cz, l % P1, (l / P1) % P1, l / (P1 * P1));
+    if (Dsc[g] != 0.0) atomicAdd(&y[g * nb + s % nb], B[it]);
+  }
+}
+
+// d[g][m] += sum_q B[q][l] wJ[c][q] f[m][c][q]
+template <int P1, int NQ1>
+__global__ void __launch_bounds__(kThreads)
+k_load_vector(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ wJ,
+              const double* __restrict__ f, double* __restrict__ d, int nb) {
+  constexpr int RT = tile_rt<double, NQ1>();
+  constexpr int S3 = NQ1 * NQ1 * NQ1;
+  constexpr int NN = P1 * P1 * P1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Bt = reinterpret_cast<double*>(smem_raw);
+  double* C = Bt + S3 * RT;
+  double* D = C + S3 * RT;
+  const long long s0 = (long long)blockIdx.x * RT;
+  const long long n_slots = (long long)mesh.nc * nb;
+  for (int it = threadIdx.x; it < S3 * RT; it += blockDim.x) {
+    const int r = it % RT, q = it / RT;
+    const long long s = s0 + r;
+    double v = 0.0;
+    if (s < n_slots) {
+      const long long c = s / nb, m = s % nb;
+      v = wJ[c * S3 + q] * f[(m * mesh.nc + c) * S3 + q];
+    }
+    C[it] = v;
+  }
+  __syncthreads();
+  interp_bwd<double, P1, NQ1, RT, false>(tab, C, Bt, D, C);
+  for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
+    const int r = it % RT, l = it / RT;
+    const long long s = s0 + r;
+    if (s >= n_slots) continue;
+    int cx, cy, cz;
+    cell_ijk(mesh, (int)(s / nb), cx, cy, cz);
+    const long long g = node_index(mesh, cx, cy, cz, l % P1, (l / P1) % P1, l / (P1 * P1));
+    atomicAdd(&d[g * nb + s % nb], Bt[it]);
+  }
+}
+
+// out[m][c][q] = sum_l B[q][l] x[g(c,l)][m]
+template <int P1, int NQ1>
+__global__ void __launch_bounds__(kThreads)
+k_interp(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ x,
+         double* __restrict__ out, int nb) {
+  constexpr int RT = tile_rt<double, NQ1>();
+  constexpr int S3 = NQ1 * NQ1 * NQ1;
+  constexpr int NN = P1 * P1 * P1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* A = reinterpret_cast<double*>(smem_raw);
+  double* C = A + S3 * RT;
+  double* D = C + S3 * RT;
+  const long long s0 = (long long)blockIdx.x * RT;
+  const long long n_slots = (long long)mesh.nc * nb;
+  for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
+    const int r = it % RT, l = it / RT;
+    const long long s = s0 + r;
+    double v = 0.0;
+    if (s < n_slots) {
+      int cx, cy, cz;
+      cell_ijk(mesh, (int)(s / nb), cx, cy, cz);
+      v = x[node_index(mesh, cx, cy, cz, l % P1, (l / P1) % P1, l / (P1 * P1)) * nb + s % nb];
+    }
+    A[it] = v;
+  }
+  __syncthreads();
+  interp_fwd<double, P1, NQ1, RT>(tab, A, C, D);
+  for (int it = threadIdx.x; it < S3 * RT; it += blockDim.x) {
+    const int r = it % RT, q = it / RT;
+    const long long s = s0 + r;
+    if (s >= n_slots) continue;
+    const long long c = s / nb, m = s % nb;
+    out[(m * mesh.nc + c) * S3 + q] = C[it];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// host wrappers
+// ----------------------------------------------------------------------------
+template <typename F>
+static cudaError_t set_smem(F f, size_t bytes) {
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int P1, int NQ1>
+static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_cols, long long ld, cudaStream_t s) {
+  const long long ld2 = 2 * ld;
+  const int batch = c.op.batch;
+  const int cols_member = (int)(2 * n_cols / batch);
+  const int ncols2 = (int)(2 * n_cols);
+  EFE_CUDA_TRY(cudaMemset2DAsync(Y, sizeof(double) * ld2, 0, sizeof(double) * ncols2, c.n_dof, s));
+  if (c.nE > 0) {
+    EFE_CUDA_TRY(cudaMemsetAsync(c.d_yE, 0, sizeof(double) * c.nE * ld2, s));
+    long long n = (long long)c.nE * ncols2;
+    k_enr_pre<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, X, c.n_h, ld2, ncols2, c.nE, c.d_xE);
+    EFE_CUDA_TRY(cudaGetLastError());
+  }
+  const T* W = std::is_same<T, float>::value ? (const T*)c.op.W32 : (const T*)c.op.W64;
+  const T* E = std::is_same<T, float>::value ? (const T*)c.op.E32 : (const T*)c.op.E64;
+  const size_t sm = tile_smem<T, NQ1>();
+  dim3 grid(c.nc, batch);
+  if (c.n_pairs > 0) {
+    auto f = k_cell_apply<T, P1, NQ1, true>;
+    EFE_CUDA_TRY(set_smem(f, sm));
+    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, c.d_Dsc, W, c.op.kin, c.d_pair_start,
+                                 c.d_pair_fn, E, c.n_pairs, c.d_xE, c.d_yE);
+  } else {
+    auto f = k_cell_apply<T, P1, NQ1, false>;
+    EFE_CUDA_TRY(set_smem(f, sm));
+    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, c.d_Dsc, W, c.op.kin, nullptr, nullptr,
+                                 nullptr, 0, nullptr, nullptr);
+  }
+  EFE_CUDA_TRY(cudaGetLastError());
+  if (c.nE > 0) {
+    long long n = (long long)c.nE * ncols2;
+    k_enr_post1<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.op.HEE, c.d_xE, c.d_yE, ld2, ncols2, cols_member, c.nE);
+    k_enr_post2<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, c.d_yE, Y, c.n_h, ld2, ncols2, c.nE);
+    EFE_CUDA_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+template <int P1, int NQ1>
+static cudaError_t build_impl(Ctx& c, const double* v, int batch, double kin, cudaStream_t s) {
+  const long long per = (long long)c.nc * c.nq;
+  k_op_W<<<(unsigned)((per * batch + 255) / 256), 256, 0, s>>>(c.d_wJ, v, c.op.W64, c.op.W32, per, batch);
+  EFE_CUDA_TRY(cudaGetLastError());
+  if (c.nE > 0) {
+    if (c.n_pairs > 0) {
+      constexpr int RT = tile_rt<double, NQ1>();
+      const size_t sm = tile_smem<double, NQ1>();
+      auto f = k_op_pairs<P1, NQ1>;
+      EFE_CUDA_TRY(set_smem(f, sm));
+      dim3 grid((unsigned)((c.n_pairs + RT - 1) / RT), batch);
+      f<<<grid, kThreads, sm, s>>>(c.tab, c.d_pair_cell, c.n_pairs, c.nc, c.d_Atil, c.d_KE, c.op.W64, kin, c.op.E64,
+                                   c.op.E32);
+      EFE_CUDA_TRY(cudaGetLastError());
+    }
+    long long n = (long long)batch * c.nE * c.nE;
+    k_op_hee_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_KEE, kin, c.op.HEE, c.nE, batch);
+    dim3 g2(c.nc, batch);
+    k_op_hee<<<g2, 128, 0, s>>>(c.d_pair_start, c.d_pair_fn, c.d_Atil, c.op.W64, c.nc, c.nq, c.nE, c.op.HEE);
+    EFE_CUDA_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+#define EFE_DISPATCH_P(P, CALL)                         \
+  switch (P) {                                          \
+    case 2: { constexpr int P1 = 3, NQ1 = 4; CALL; }    \
+    case 3: { constexpr int P1 = 4, NQ1 = 5; CALL; }    \
+    case 4: { constexpr int P1 = 5, NQ1 = 6; CALL; }    \
+    case 5: { constexpr int P1 = 6, NQ1 = 7; CALL; }    \
+    default: return cudaErrorInvalidValue;              \
+  }
+
+cudaError_t launch_apply(Ctx& c, const double* X, double* Y, long long n_cols, long long ld, int precision,
+                         cudaStream_t s) {
+  if (precision == EFE_MIXED) {
+    EFE_DISPATCH_P(c.p, return (apply_impl<float, P1, NQ1>(c, X, Y, n_cols, ld, s)));
+  }
+  EFE_DISPATCH_P(c.p, return (apply_impl<double, P1, NQ1>(c, X, Y, n_cols, ld, s)));
+}
+
+cudaError_t launch_build_operator(Ctx& c, const double* v, int batch, double kin, cudaStream_t s) {
+  EFE_DISPATCH_P(c.p, return (build_impl<P1, NQ1>(c, v, batch, kin, s)));
+}
+
+template <int P1, int NQ1>
+static cudaError_t laplace_impl(const Ctx& c, const double* x, double* y, int nb, int mask_in, double scale,
+                                cudaStream_t s) {
+  constexpr int RT = tile_rt<double, NQ1>();
+  const size_t sm = tile_smem<double, NQ1>();
+  auto f = k_laplace<P1, NQ1>;
+  EFE_CUDA_TRY(set_smem(f, sm));
+  const long long slots = (long long)c.nc * nb;
+  f<<<(unsigned)((slots + RT - 1) / RT), kThreads, sm, s>>>(c.tab, c.mesh, x, y, nb, c.d_Dsc, mask_in, scale);
+  return cudaGetLastError();
+}
+
+template <int P1, int NQ1>
+static cudaError_t loadvec_impl(const Ctx& c, const double* f, double* d, int nb, cudaStream_t s) {
+  constexpr int RT = tile_rt<double, NQ1>();
+  const size_t sm = tile_smem<double, NQ1>();
+  auto k = k_load_vector<P1, NQ1>;
+  EFE_CUDA_TRY(set_smem(k, sm));
+  const long long slots = (long long)c.nc * nb;
+  k<<<(unsigned)((slots + RT - 1) / RT), kThreads, sm, s>>>(c.tab, c.mesh, c.d_wJ, f, d, nb);
+  return cudaGetLastError();
+}
+
+template <int P1, int NQ1>
+static cudaError_t interp_impl(const Ctx& c, const double* x, double* out, int nb, cudaStream_t s) {
+  constexpr int RT = tile_rt<double, NQ1>();
+  const size_t sm = tile_smem<double, NQ1>();
+  auto k = k_interp<P1, NQ1>;
+  EFE_CUDA_TRY(set_smem(k, sm));
+  const long long slots = (long long)c.nc * nb;
+  k<<<(unsigned)((slots + RT - 1) / RT), kThreads, sm, s>>>(c.tab, c.mesh, x, out, nb);
+  return cudaGetLastError();
+}
+
+// y (+)= mask_out * scale * (1/2 int grad N . grad N) x  (atomically added; caller zeroes y)
+cudaError_t launch_laplace(const Ctx& c, const double* x, double* y, int nb, int mask_in, double scale, cudaStream_t s) {
+  EFE_DISPATCH_P(c.p, return (laplace_impl<P1, NQ1>(c, x, y, nb, mask_in, scale, s)));
+}
+cudaError_t launch_load_vector(const Ctx& c, const double* f, double* d, int nb, cudaStream_t s) {
+  EFE_DISPATCH_P(c.p, return (loadvec_impl<P1, NQ1>(c, f, d, nb, s)));
+}
+cudaError_t launch_interp(const Ctx& c, const double* x, double* out, int nb, cudaStream_t s) {
+  EFE_DISPATCH_P(c.p, return (interp_impl<P1, NQ1>(c, x, out, nb, s)));
+}
+
+}  // namespace efe

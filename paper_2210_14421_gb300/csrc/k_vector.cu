@@ -1,0 +1,768 @@
+// Lanczos exponential (Eqs. AdaptiveKrylov, AdaptiveKrylovErr), density
+// (Sec. "Time dependent Kohn-Sham equations"), LDA, dipole, potential
+// assembly and the Hartree PCG (Eqs. Hartree_possion, DiscretePoisson).
+// Everything here is float64 and bound by HBM bandwidth or by the FP64 pipe.
+#include <cmath>
+#include <cstdio>
+
+#include "efe_internal.h"
+#include "sumfact.cuh"
+
+namespace efe {
+
+cudaError_t launch_laplace(const Ctx& c, const double* x, double* y, int nb, int mask_in, double scale,
+                           cudaStream_t s);
+cudaError_t launch_load_vector(const Ctx& c, const double* f, double* d, int nb, cudaStream_t s);
+cudaError_t launch_interp(const Ctx& c, const double* x, double* out, int nb, cudaStream_t s);
+
+static unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// Lanczos scalar layout in Ctx::d_lz for C complex columns.
+struct LzView {
+  double *nrm, *alpha, *beta, *yre, *yim, *eps, *red, *red2, *dt, *invb;
+  int *active, *kused, *cap, *n_active;
+};
+static LzView lz_view(const Ctx& c, long long C) {
+  LzView v;
+  double* b = c.d_lz;
+  v.nrm = b;
+  v.alpha = b + C;
+  v.beta = v.alpha + kMaxK * C;
+  v.yre = v.beta + kMaxK * C;
+  v.yim = v.yre + kMaxK * C;
+  v.eps = v.yim + kMaxK * C;
+  v.red = v.eps + C;
+  v.red2 = v.red + C;
+  v.dt = v.red2 + C;
+  v.invb = v.dt + C;
+  int* ib = c.d_lzi;
+  v.active = ib;
+  v.kused = ib + C;
+  v.cap = ib + 2 * C;
+  v.n_active = ib + 3 * C;
+  return v;
+}
+
+// Flat grid over (row, column) with a fixed column per thread: the thread
+// count used is the largest multiple of C not above the launch size.
+struct FlatIter {
+  long long row0, rstride;
+  int col;
+  bool ok;
+};
+__device__ __forceinline__ FlatIter flat_iter(int C) {
+  const long long T = (long long)gridDim.x * blockDim.x;
+  const long long Tc = (T / C) * C;
+  const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  FlatIter f;
+  f.ok = gt < Tc;
+  f.col = (int)(gt % C);
+  f.row0 = gt / C;
+  f.rstride = Tc / C;
+  return f;
+}
+
+// block-level reduction of one value per thread into out[col] (atomics)
+__device__ __forceinline__ void block_col_reduce(double v, int col, bool ok, int C, double* sred, double* out) {
+  for (int i = threadIdx.x; i < C; i += blockDim.x) sred[i] = 0.0;
+  __syncthreads();
+  if (ok && v != 0.0) atomicAdd(&sred[col], v);
+  __syncthreads();
+  for (int i = threadIdx.x; i < C; i += blockDim.x)
+    if (sred[i] != 0.0) atomicAdd(&out[i], sred[i]);
+}
+
+// out[col] += sum_rows |X[row][col]|^2 (complex)
+__global__ void k_norm2(const double* __restrict__ X, long long n_rows, int C, long long ld2, double* __restrict__ out) {
+  extern __shared__ double sred[];
+  FlatIter f = flat_iter(C);
+  double acc = 0.0;
+  if (f.ok)
+    for (long long r = f.row0; r < n_rows; r += f.rstride) {
+      const double2 v = *reinterpret_cast<const double2*>(X + r * ld2 + 2 * f.col);
+      acc += v.x * v.x + v.y * v.y;
+    }
+  block_col_reduce(acc, f.col, f.ok, C, sred, out);
+}
+
+// Q0 = X / nrm, set up the per-column state
+__global__ void k_lz_init(const double* __restrict__ X, double* __restrict__ Q0, long long n_rows, int C, long long ld2,
+                          const double* __restrict__ red) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n_rows * C) return;
+  const long long r = idx / C;
+  const int col = (int)(idx % C);
+  const double n = sqrt(red[col]);
+  const double inv = n > 0.0 ? 1.0 / n : 0.0;
+  const double2 v = *reinterpret_cast<const double2*>(X + r * ld2 + 2 * col);
+  *reinterpret_cast<double2*>(Q0 + r * 2 * C + 2 * col) = make_double2(v.x * inv, v.y * inv);
+}
+
+__global__ void k_lz_state(LzView v, int C, const double* __restrict__ dts) {
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= C) return;
+  const double n = sqrt(v.red[col]);
+  v.nrm[col] = n;
+  v.active[col] = n > 0.0 ? 1 : 0;
+  v.kused[col] = 0;
+  v.cap[col] = 0;
+  v.eps[col] = 0.0;
+  v.dt[col] = dts[col];
+}
+
+// red[col] += Re <Qj, W>
+__global__ void k_lz_dot(const double* __restrict__ Qj, const double* __restrict__ W, long long n_rows, int C,
+                         const int* __restrict__ active, double* __restrict__ out) {
+  extern __shared__ double sred[];
+  FlatIter f = flat_iter(C);
+  double acc = 0.0;
+  if (f.ok && active[f.col])
+    for (long long r = f.row0; r < n_rows; r += f.rstride) {
+      const double2 a = *reinterpret_cast<const double2*>(Qj + r * 2 * C + 2 * f.col);
+      const double2 b = *reinterpret_cast<const double2*>(W + r * 2 * C + 2 * f.col);
+      acc += a.x * b.x + a.y * b.y;
+    }
+  block_col_reduce(acc, f.col, f.ok, C, sred, out);
+}
+
+// W -= alpha Qj + beta_prev Qjm1 ; red2[col] += |W|^2
+__global__ void k_lz_update(double* __restrict__ W, const double* __restrict__ Qj, const double* __restrict__ Qjm1,
+                            long long n_rows, int C, const int* __restrict__ active, const double* __restrict__ alpha,
+                            const double* __restrict__ beta_prev, double* __restrict__ out) {
+  extern __shared__ double sred[];
+  FlatIter f = flat_iter(C);
+  double acc = 0.0;
+  if (f.ok && active[f.col]) {
+    const double a = alpha[f.col];
+    const double b = Qjm1 ? beta_prev[f.col] : 0.0;
+    for (long long r = f.row0; r < n_rows; r += f.rstride) {
+      const long long o = r * 2 * C + 2 * f.col;
+      double2 w = *reinterpret_cast<double2*>(W + o);
+      const double2 q = *reinterpret_cast<const double2*>(Qj + o);
+      w.x -= a * q.x;
+      w.y -= a * q.y;
+      if (Qjm1) {
+        const double2 p = *reinterpret_cast<const double2*>(Qjm1 + o);
+        w.x -= b * p.x;
+        w.y -= b * p.y;
+      }
+      *reinterpret_cast<double2*>(W + o) = w;
+      acc += w.x * w.x + w.y * w.y;
+    }
+  }
+  block_col_reduce(acc, f.col, f.ok, C, sred, out);
+}
+
+// Symmetric eigendecomposition of the small tridiagonal T by cyclic Jacobi,
+// then y = exp(-i dt T) e_1 and the error estimate; one thread per column.
+__global__ void k_lz_tri(LzView v, int C, int j, int k_max, int fixed_k, double tol) {
+  extern __shared__ double tri_sh[];
+  const int col = blockIdx.x;
+  if (threadIdx.x != 0 || col >= C) return;
+  if (!v.active[col]) return;
+  const double a_j = v.red[col];
+  const double b_j = sqrt(v.red2[col]);
+  v.alpha[(long long)j * C + col] = a_j;
+  v.beta[(long long)j * C + col] = b_j;
+  const int m = j + 1;
+  double* A = tri_sh;
+  double* V = tri_sh + m * m;
+  for (int r = 0; r < m; ++r)
+    for (int s = 0; s < m; ++s) {
+      A[r * m + s] = 0.0;
+      V[r * m + s] = (r == s) ? 1.0 : 0.0;
+    }
+  for (int r = 0; r < m; ++r) A[r * m + r] = v.alpha[(long long)r * C + col];
+  for (int r = 0; r + 1 < m; ++r) {
+    const double b = v.beta[(long long)r * C + col];
+    A[r * m + r + 1] = b;
+    A[(r + 1) * m + r] = b;
+  }
+  double total = 0.0;
+  for (int r = 0; r < m * m; ++r) total += A[r] * A[r];
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) off += A[p * m + q] * A[p * m + q];
+    if (off <= 1e-34 * total || off == 0.0) break;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[p * m + q];
+        if (apq == 0.0) continue;
+        const double theta = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < m; ++k) {
+          const double akp = A[k * m + p], akq = A[k * m + q];
+          A[k * m + p] = cs * akp - sn * akq;
+          A[k * m + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double apk = A[p * m + k], aqk = A[q * m + k];
+          A[p * m + k] = cs * apk - sn * aqk;
+          A[q * m + k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[k * m + p], vkq = V[k * m + q];
+          V[k * m + p] = cs * vkp - sn * vkq;
+          V[k * m + q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+  const double dt = v.dt[col];
+  double ylast_re = 0.0, ylast_im = 0.0;
+  for (int r = 0; r < m; ++r) {
+    double yr = 0.0, yi = 0.0;
+    for (int k = 0; k < m; ++k) {
+      double sn, cs;
+      sincos(dt * A[k * m + k], &sn, &cs);
+      const double w = V[r * m + k] * V[0 * m + k];
+      yr += w * cs;
+      yi -= w * sn;
+    }
+    v.yre[(long long)r * C + col] = yr;
+    v.yim[(long long)r * C + col] = yi;
+    ylast_re = yr;
+    ylast_im = yi;
+  }
+  const double eps = fabs(dt) * b_j * v.nrm[col] * sqrt(ylast_re * ylast_re + ylast_im * ylast_im);
+  v.eps[col] = eps;
+  bool stop = false;
+  if (fixed_k > 0) {
+    stop = (m >= fixed_k);
+  } else if (eps <= tol || b_j == 0.0) {
+    stop = true;
+  }
+  if (!stop && m >= k_max) {
+    stop = true;
+    if (fixed_k <= 0) v.cap[col] = 1;
+  }
+  if (stop) {
+    v.active[col] = 0;
+    v.kused[col] = m;
+  } else {
+    v.invb[col] = 1.0 / b_j;
+    atomicAdd(v.n_active, 1);
+  }
+}
+
+// Q_{j+1} = W / beta_j for columns still running, zero for finished ones
+__global__ void k_lz_scale(double* __restrict__ W, long long n_rows, int C, const int* __restrict__ active,
+                           const double* __restrict__ invb) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n_rows * C) return;
+  const int col = (int)(idx % C);
+  double2* p = reinterpret_cast<double2*>(W) + idx;
+  if (active[col]) {
+    const double s = invb[col];
+    double2 w = *p;
+    w.x *= s;
+    w.y *= s;
+    *p = w;
+  } else {
+    *p = make_double2(0.0, 0.0);
+  }
+}
+
+// out = nrm * sum_{j < kused} y_j Q_j
+__global__ void k_lz_combine(const double* __restrict__ Q, long long qstride, long long n_rows, int C,
+                             LzView v, double* __restrict__ out, long long ld2) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n_rows * C) return;
+  const long long r = idx / C;
+  const int col = (int)(idx % C);
+  const int k = v.kused[col];
+  double re = 0.0, im = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double2 q = reinterpret_cast<const double2*>(Q + j * qstride)[idx];
+    const double yr = v.yre[(long long)j * C + col], yi = v.yim[(long long)j * C + col];
+    re += yr * q.x - yi * q.y;
+    im += yr * q.y + yi * q.x;
+  }
+  const double n = v.nrm[col];
+  *reinterpret_cast<double2*>(out + r * ld2 + 2 * col) = make_double2(n * re, n * im);
+}
+
+__global__ void k_lz_stats(LzView v, int C, int* __restrict__ stats_i, double* __restrict__ stats_d) {
+  // stats_i: [max k, cap hits]; stats_d: [max eps]  (single block)
+  __shared__ int smax, scap;
+  __shared__ double seps;
+  if (threadIdx.x == 0) { smax = 0; scap = 0; seps = 0.0; }
+  __syncthreads();
+  for (int col = threadIdx.x; col < C; col += blockDim.x) {
+    atomicMax(&smax, v.kused[col]);
+    atomicAdd(&scap, v.cap[col]);
+    const double e = v.eps[col];
+    unsigned long long* a = reinterpret_cast<unsigned long long*>(&seps);
+    unsigned long long old = *a, assumed;
+    do {
+      assumed = old;
+      if (__longlong_as_double(assumed) >= e) break;
+      old = atomicCAS(a, assumed, __double_as_longlong(e));
+    } while (old != assumed);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    stats_i[0] = smax;
+    stats_i[1] = scap;
+    stats_d[0] = seps;
+  }
+}
+
+static size_t red_smem(long long C) { return sizeof(double) * (size_t)C; }
+static unsigned red_grid(long long n_rows, long long C) {
+  long long want = (n_rows * C + 255) / 256;
+  long long cap = 152LL * 8;
+  long long g = want < cap ? want : cap;
+  if (g * 256 < C) g = (C + 255) / 256;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h_dts, int precision, int* kmax_used,
+                          int* cap_hits, double* eps_max, cudaStream_t s) {
+  const long long C = (long long)c.n_orb * c.op.batch;
+  const long long n = c.n_dof;
+  const long long ld2 = 2 * C;
+  const long long qstride = n * 2 * C;
+  LzView v = lz_view(c, C);
+  double* d_dts = v.invb;   // temporarily hold dts in invb, copied by k_lz_state
+  EFE_CUDA_TRY(cudaMemcpyAsync(d_dts, h_dts, sizeof(double) * C, cudaMemcpyHostToDevice, s));
+  EFE_CUDA_TRY(cudaMemsetAsync(v.red, 0, sizeof(double) * C, s));
+  const unsigned rg = red_grid(n, C);
+  const size_t rs = red_smem(C);
+  k_norm2<<<rg, 256, rs, s>>>(in, n, (int)C, ld2, v.red);
+  k_lz_init<<<nblk(n * C), 256, 0, s>>>(in, c.d_Q, n, (int)C, ld2, v.red);
+  k_lz_state<<<nblk(C), 256, 0, s>>>(v, (int)C, d_dts);
+  EFE_CUDA_TRY(cudaGetLastError());
+  for (int j = 0; j < c.k_max; ++j) {
+    double* Qj = c.d_Q + j * qstride;
+    double* W = c.d_Q + (j + 1) * qstride;
+    EFE_CUDA_TRY(launch_apply(c, Qj, W, C, C, precision, s));
+    EFE_CUDA_TRY(cudaMemsetAsync(v.red, 0, sizeof(double) * 2 * C, s));   // red and red2
+    EFE_CUDA_TRY(cudaMemsetAsync(v.n_active, 0, sizeof(int), s));
+    k_lz_dot<<<rg, 256, rs, s>>>(Qj, W, n, (int)C, v.active, v.red);
+    k_lz_update<<<rg, 256, rs, s>>>(W, Qj, j > 0 ? c.d_Q + (j - 1) * qstride : nullptr, n, (int)C, v.active, v.red,
+                                    j > 0 ? v.beta + (long long)(j - 1) * C : nullptr, v.red2);
+    k_lz_tri<<<(unsigned)C, 32, sizeof(double) * 2 * (j + 1) * (j + 1), s>>>(v, (int)C, j, c.k_max, c.fixed_k,
+                                                                          c.krylov_tol);
+    k_lz_scale<<<nblk(n * C), 256, 0, s>>>(W, n, (int)C, v.active, v.invb);
+    EFE_CUDA_TRY(cudaGetLastError());
+    EFE_CUDA_TRY(cudaMemcpyAsync(c.h_flag, v.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    EFE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (*c.h_flag == 0) break;
+  }
+  k_lz_combine<<<nblk(n * C), 256, 0, s>>>(c.d_Q, qstride, n, (int)C, v, out, ld2);
+  int* d_si = v.n_active;   // reuse: [0] max k, [1] caps
+  double* d_sd = v.red;
+  k_lz_stats<<<1, 256, 0, s>>>(v, (int)C, d_si, d_sd);
+  EFE_CUDA_TRY(cudaGetLastError());
+  int hi[2];
+  double hd;
+  EFE_CUDA_TRY(cudaMemcpyAsync(hi, d_si, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+  EFE_CUDA_TRY(cudaMemcpyAsync(&hd, d_sd, sizeof(double), cudaMemcpyDeviceToHost, s));
+  EFE_CUDA_TRY(cudaStreamSynchronize(s));
+  if (kmax_used) *kmax_used = hi[0];
+  if (cap_hits) *cap_hits = hi[1];
+  if (eps_max) *eps_max = hd;
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------- density
+template <int P1, int NQ1>
+__global__ void __launch_bounds__(kThreads)
+k_density(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ X, long long ld2,
+          int n_orb, const double* __restrict__ occ, const double* __restrict__ Dsc,
+          const int* __restrict__ pair_start, const int* __restrict__ pair_fn, const double* __restrict__ Atil,
+          const double* __restrict__ xE, double* __restrict__ rho) {
+  constexpr int RT = 16;
+  constexpr int S3 = NQ1 * NQ1 * NQ1;
+  constexpr int NN = P1 * P1 * P1;
+  extern __shared__ __align__(16) double dsm[];
+  double* A = dsm;
+  double* C = A + S3 * RT;
+  double* D = C + S3 * RT;
+  double* racc = D + S3 * RT;
+  const int c = blockIdx.x, member = blockIdx.y;
+  int cx, cy, cz;
+  cell_ijk(mesh, c, cx, cy, cz);
+  const int cols_member = 2 * n_orb;
+  const int col0 = member * cols_member;
+  const int p0 = pair_start ? pair_start[c] : 0;
+  const int np = pair_start ? pair_start[c + 1] - p0 : 0;
+  for (int q = threadIdx.x; q < S3; q += blockDim.x) racc[q] = 0.0;
+  for (int cbase = 0; cbase < cols_member; cbase += RT) {
+    for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
+      const int r = it % RT, l = it / RT;
+      const long long g = node_index(mesh, cx, cy, cz, l % P1, (l / P1) % P1, l / (P1 * P1));
+      A[it] = (cbase + r < cols_member) ? Dsc[g] * X[g * ld2 + col0 + cbase + r] : 0.0;
+    }
+    __syncthreads();
+    interp_fwd<double, P1, NQ1, RT>(tab, A, C, D);
+    for (int it = threadIdx.x; it < S3 * RT; it += blockDim.x) {
+      const int r = it % RT, q = it / RT;
+      if (cbase + r >= cols_member) continue;
+      double acc = C[it];
+      for (int k = 0; k < np; ++k)
+        acc += Atil[(long long)(p0 + k) * S3 + q] * xE[(long long)pair_fn[p0 + k] * ld2 + col0 + cbase + r];
+      C[it] = acc;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < S3; q += blockDim.x) {
+      double s = 0.0;
+      for (int r = 0; r < RT; ++r) {
+        if (cbase + r >= cols_member) break;
+        const double u = C[q * RT + r];
+        s += occ[((cbase + r) / 2) % n_orb] * u * u;
+      }
+      racc[q] += s;
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < S3; q += blockDim.x) rho[((long long)member * mesh.nc + c) * S3 + q] = racc[q];
+}
+
+__global__ void k_enr_pre_d(const double* __restrict__ S, const double* __restrict__ X, long long n_h, long long ld2,
+                            int ncols2, int nE, double* __restrict__ xE) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)nE * ncols2) return;
+  int nu = idx / ncols2, col = idx % ncols2;
+  double acc = 0.0;
+  for (int mu = 0; mu < nE; ++mu) acc += S[nu * nE + mu] * X[(n_h + mu) * ld2 + col];
+  xE[nu * ld2 + col] = acc;
+}
+
+template <int P1, int NQ1>
+static cudaError_t density_impl(Ctx& c, const double* psi, double* rho, cudaStream_t s) {
+  const long long C = (long long)c.n_orb * c.batch;
+  const long long ld2 = 2 * C;
+  if (c.nE > 0) {
+    long long n = (long long)c.nE * ld2;
+    k_enr_pre_d<<<nblk(n), 256, 0, s>>>(c.d_S, psi, c.n_h, ld2, (int)ld2, c.nE, c.d_xE);
+  }
+  dim3 grid(c.nc, c.batch);
+  const size_t sm = sizeof(double) * (3 * 16 * NQ1 * NQ1 * NQ1 + NQ1 * NQ1 * NQ1);
+  EFE_CUDA_TRY(cudaFuncSetAttribute(k_density<P1, NQ1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_density<P1, NQ1><<<grid, kThreads, sm, s>>>(c.tab, c.mesh, psi, ld2, c.n_orb, c.d_occ, c.d_Dsc,
+                                                c.n_pairs ? c.d_pair_start : nullptr, c.d_pair_fn, c.d_Atil, c.d_xE,
+                                                rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_density(Ctx& c, const double* psi, double* rho, cudaStream_t s) {
+  switch (c.p) {
+    case 2: return density_impl<3, 4>(c, psi, rho, s);
+    case 3: return density_impl<4, 5>(c, psi, rho, s);
+    case 4: return density_impl<5, 6>(c, psi, rho, s);
+    case 5: return density_impl<6, 7>(c, psi, rho, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------- LDA
+__global__ void k_lda(const double* __restrict__ rho, double* __restrict__ vxc, double* __restrict__ exc, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double r = rho[i];
+  double e = 0.0, v = 0.0;
+  if (r > 1e-14) {
+    const double pi = 3.14159265358979323846;
+    const double c13 = cbrt(3.0 * r / pi);
+    const double ex = -0.75 * c13, vx = -c13;
+    // Perdew-Wang 1992 unpolarised correlation
+    const double A = 0.031091, a1 = 0.21370, b1 = 7.5957, b2 = 3.5876, b3 = 1.6382, b4 = 0.49294;
+    const double rs = cbrt(3.0 / (4.0 * pi * r));
+    const double srs = sqrt(rs);
+    const double Q = 2.0 * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs);
+    const double dQ = 2.0 * A * (0.5 * b1 / srs + b2 + 1.5 * b3 * srs + 2.0 * b4 * rs);
+    const double lg = log1p(1.0 / Q);
+    const double ec = -2.0 * A * (1.0 + a1 * rs) * lg;
+    const double dec = -2.0 * A * a1 * lg + 2.0 * A * (1.0 + a1 * rs) * dQ / (Q * (Q + 1.0));
+    const double vc = ec - rs / 3.0 * dec;
+    e = ex + ec;
+    v = vx + vc;
+  }
+  if (vxc) vxc[i] = v;
+  if (exc) exc[i] = e;
+}
+
+cudaError_t launch_lda(const Ctx& c, const double* rho, double* vxc, double* exc, long long n, cudaStream_t s) {
+  k_lda<<<nblk(n), 256, 0, s>>>(rho, vxc, exc, n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- dipole
+__global__ void k_dipole(const double* __restrict__ rho, const double* __restrict__ wJ, const double* __restrict__ xq,
+                         long long npts, double* __restrict__ mu) {
+  const int member = blockIdx.y;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
+    const double w = wJ[i] * rho[member * npts + i];
+    a0 += w * xq[3 * i];
+    a1 += w * xq[3 * i + 1];
+    a2 += w * xq[3 * i + 2];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_down_sync(0xffffffffu, a0, o);
+    a1 += __shfl_down_sync(0xffffffffu, a1, o);
+    a2 += __shfl_down_sync(0xffffffffu, a2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&mu[member * 3 + 0], -a0);
+    atomicAdd(&mu[member * 3 + 1], -a1);
+    atomicAdd(&mu[member * 3 + 2], -a2);
+  }
+}
+
+__global__ void k_dipole_init(double* mu, int batch, double n0, double n1, double n2) {
+  int m = threadIdx.x;
+  if (m < batch) {
+    mu[3 * m] = n0;
+    mu[3 * m + 1] = n1;
+    mu[3 * m + 2] = n2;
+  }
+}
+
+cudaError_t launch_dipole(const Ctx& c, const double* rho, double* mu, cudaStream_t s) {
+  double n[3] = {0, 0, 0};
+  for (int a = 0; a < c.n_atoms; ++a)
+    for (int k = 0; k < 3; ++k) n[k] += c.Z[a] * c.R[3 * a + k];
+  for (int b0 = 0; b0 < c.batch; b0 += 1024) {
+    int nb = std::min(1024, c.batch - b0);
+    k_dipole_init<<<1, 1024, 0, s>>>(mu + 3 * b0, nb, n[0], n[1], n[2]);
+  }
+  const long long npts = (long long)c.nc * c.nq;
+  dim3 grid(std::min<long long>(nblk(npts), 608), c.batch);
+  k_dipole<<<grid, 256, 0, s>>>(rho, c.d_wJ, c.d_xq, npts, mu);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- potentials
+__global__ void k_potential(const double* __restrict__ vN, const double* __restrict__ vH, const double* __restrict__ vxc,
+                            const double* __restrict__ xq, const double* __restrict__ E, long long npts, int batch,
+                            double* __restrict__ v) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= npts * batch) return;
+  const long long i = idx % npts;
+  const int m = (int)(idx / npts);
+  double val = vN ? vN[i] : 0.0;
+  if (vH) val += vH[idx];
+  if (vxc) val += vxc[idx];
+  val -= E[3 * m] * xq[3 * i] + E[3 * m + 1] * xq[3 * i + 1] + E[3 * m + 2] * xq[3 * i + 2];
+  v[idx] = val;
+}
+
+double field_amp(const efe_field& f, double t) {
+  const double pi = 3.14159265358979323846;
+  switch (f.kind) {
+    case EFE_FIELD_GAUSS: return f.amp * std::exp(-(t - f.t0) * (t - f.t0) / (2.0 * f.sigma * f.sigma));
+    case EFE_FIELD_SINE_GAUSS:
+      return f.amp * std::sin(f.omega * t) * std::exp(-(t - f.t0) * (t - f.t0) / (2.0 * f.sigma * f.sigma));
+    case EFE_FIELD_SINE_TRAP: {
+      if (t < 0.0 || t > f.period) return 0.0;
+      double env = 1.0;
+      if (f.ramp > 0.0) env = std::min(1.0, std::min(t / f.ramp, (f.period - t) / f.ramp));
+      if (env < 0.0) env = 0.0;
+      return f.amp * std::sin(f.omega * t) * env;
+    }
+    case EFE_FIELD_SINE_SINE:
+      if (t < 0.0 || t > f.period) return 0.0;
+      return f.amp * std::sin(pi * t / f.period) * std::sin(f.omega * t);
+    default: return 0.0;
+  }
+}
+
+struct FieldVec {
+  double e[3 * 64];
+};
+
+__global__ void k_potential_v(const double* __restrict__ vN, const double* __restrict__ vH,
+                              const double* __restrict__ vxc, const double* __restrict__ xq, const FieldVec E,
+                              long long npts, int batch, double* __restrict__ v) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= npts * batch) return;
+  const long long i = idx % npts;
+  const int m = (int)(idx / npts);
+  double val = vN ? vN[i] : 0.0;
+  if (vH) val += vH[idx];
+  if (vxc) val += vxc[idx];
+  val -= E.e[3 * m] * xq[3 * i] + E.e[3 * m + 1] * xq[3 * i + 1] + E.e[3 * m + 2] * xq[3 * i + 2];
+  v[idx] = val;
+}
+
+// v[m] = (nuclear ? v_N : 0) + vH[m] + vxc[m] - E[m] . x   (vH / vxc may be NULL); E_host [batch][3]
+cudaError_t launch_potential_sum(const Ctx& c, const double* vH, const double* vxc, const double* E_host,
+                                 bool nuclear, double* v, cudaStream_t s) {
+  const long long npts = (long long)c.nc * c.nq;
+  if (c.batch <= 64) {
+    FieldVec E{};
+    for (int k = 0; k < 3 * c.batch; ++k) E.e[k] = E_host[k];
+    k_potential_v<<<nblk(npts * c.batch), 256, 0, s>>>(nuclear ? c.d_vN : nullptr, vH, vxc, c.d_xq, E, npts,
+                                                       c.batch, v);
+    return cudaGetLastError();
+  }
+  EFE_CUDA_TRY(cudaMemcpyAsync(c.d_red, E_host, sizeof(double) * 3 * c.batch, cudaMemcpyHostToDevice, s));
+  k_potential<<<nblk(npts * c.batch), 256, 0, s>>>(nuclear ? c.d_vN : nullptr, vH, vxc, c.d_xq, c.d_red, npts,
+                                                   c.batch, v);
+  EFE_CUDA_TRY(cudaGetLastError());
+  return cudaStreamSynchronize(s);
+}
+
+__global__ void k_axpby(double* __restrict__ y, const double* __restrict__ a, const double* __restrict__ b, double ca,
+                        double cb, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = ca * a[i] + cb * b[i];
+}
+
+cudaError_t launch_axpby(double* y, const double* a, const double* b, double ca, double cb, long long n, cudaStream_t s) {
+  k_axpby<<<nblk(n), 256, 0, s>>>(y, a, b, ca, cb, n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- Hartree PCG
+// vectors are [n_h][nb]; per-member scalars
+__global__ void k_coldot(const double* __restrict__ a, const double* __restrict__ b, long long n_rows, int C,
+                         double* __restrict__ out) {
+  extern __shared__ double sred[];
+  FlatIter f = flat_iter(C);
+  double acc = 0.0;
+  if (f.ok)
+    for (long long r = f.row0; r < n_rows; r += f.rstride) acc += a[r * C + f.col] * b[r * C + f.col];
+  block_col_reduce(acc, f.col, f.ok, C, sred, out);
+}
+
+// phi boundary values <- phiB (once, or after a reset)
+__global__ void k_cg_bc(double* __restrict__ phi, const double* __restrict__ phiB, const double* __restrict__ Dsc,
+                        long long n_h, int nb) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n_h * nb) return;
+  const long long g = idx / nb;
+  if (Dsc[g] == 0.0) phi[idx] = phiB[g];
+}
+
+// r = d - Ap (interior), z = r / diag, p = z; zero on the boundary
+__global__ void k_cg_start(const double* __restrict__ d, const double* __restrict__ Ap, const double* __restrict__ diag,
+                           const double* __restrict__ Dsc, long long n_h, int nb, double* __restrict__ r,
+                           double* __restrict__ z, double* __restrict__ p, double* __restrict__ dm) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n_h * nb) return;
+  const long long g = idx / nb;
+  if (Dsc[g] == 0.0) {
+    r[idx] = z[idx] = p[idx] = 0.0;
+    dm[idx] = 0.0;
+    return;
+  }
+  const double rr = d[idx] - Ap[idx];
+  r[idx] = rr;
+  z[idx] = rr / diag[g];
+  p[idx] = z[idx];
+  dm[idx] = d[idx];
+}
+
+// scalars per member: [0] rz, [1] rz_new, [2] pAp, [3] rr, [4] dd
+__global__ void k_cg_update(double* __restrict__ phi, double* __restrict__ r, double* __restrict__ z,
+                            const double* __restrict__ p, const double* __restrict__ Ap, const double* __restrict__ diag,
+                            const double* __restrict__ Dsc, long long n_h, int nb, const double* __restrict__ sc,
+                            double* __restrict__ rz_new, double* __restrict__ rr) {
+  extern __shared__ double sred[];   // 2 * nb
+  FlatIter f = flat_iter(nb);
+  double a_rz = 0.0, a_rr = 0.0;
+  if (f.ok) {
+    const double pAp = sc[2 * nb + f.col];
+    const double alpha = pAp != 0.0 ? sc[0 * nb + f.col] / pAp : 0.0;
+    for (long long g = f.row0; g < n_h; g += f.rstride) {
+      const long long i = g * nb + f.col;
+      if (Dsc[g] == 0.0) continue;
+      phi[i] += alpha * p[i];
+      const double rv = r[i] - alpha * Ap[i];
+      r[i] = rv;
+      const double zv = rv / diag[g];
+      z[i] = zv;
+      a_rz += rv * zv;
+      a_rr += rv * rv;
+    }
+  }
+  block_col_reduce(a_rz, f.col, f.ok, nb, sred, rz_new);
+  __syncthreads();
+  block_col_reduce(a_rr, f.col, f.ok, nb, sred, rr);
+}
+
+__global__ void k_cg_dir(double* __restrict__ p, const double* __restrict__ z, long long n, int nb,
+                         const double* __restrict__ sc) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n * nb) return;
+  const int m = (int)(idx % nb);
+  const double rz = sc[m], rzn = sc[nb + m];
+  const double beta = rz != 0.0 ? rzn / rz : 0.0;
+  p[idx] = z[idx] + beta * p[idx];
+}
+
+__global__ void k_cg_rot(double* sc, int nb) {
+  int m = threadIdx.x + blockIdx.x * blockDim.x;
+  if (m >= nb) return;
+  sc[m] = sc[nb + m];   // rz <- rz_new
+  sc[nb + m] = 0.0;
+  sc[2 * nb + m] = 0.0;  // pAp (rr is cleared before each update)
+}
+
+efe_status run_hartree(Ctx& c, const double* rho, double* vH, double tol, int max_it, int* iters, cudaStream_t s) {
+  const int nb = c.batch;
+  const long long n = c.n_h;
+  const long long N = n * nb;
+  double* d = c.d_cg;
+  double* r = d + N;
+  double* z = r + N;
+  double* p = z + N;
+  double* Ap = p + N;
+  double* dm = Ap + N;
+  double* sc = dm + N;   // 5 * nb scalars
+  const double scale = 1.0 / (2.0 * 3.14159265358979323846);
+  const size_t rs = sizeof(double) * nb;
+  const unsigned rg = red_grid(n, nb);
+#define CK(x)                                              \
+  do {                                                     \
+    cudaError_t _e = (x);                                  \
+    if (_e != cudaSuccess) {                               \
+      c.err = std::string("CUDA: ") + cudaGetErrorString(_e); \
+      return EFE_ERR_CUDA;                                 \
+    }                                                      \
+  } while (0)
+  CK(cudaMemsetAsync(d, 0, sizeof(double) * N, s));
+  CK(launch_load_vector(c, rho, d, nb, s));
+  k_cg_bc<<<nblk(N), 256, 0, s>>>(c.d_phi, c.d_phiB, c.d_Dsc, n, nb);
+  CK(cudaMemsetAsync(Ap, 0, sizeof(double) * N, s));
+  CK(launch_laplace(c, c.d_phi, Ap, nb, 0, scale, s));
+  k_cg_start<<<nblk(N), 256, 0, s>>>(d, Ap, c.d_diagA, c.d_Dsc, n, nb, r, z, p, dm);
+  CK(cudaMemsetAsync(sc, 0, sizeof(double) * 5 * nb, s));
+  k_coldot<<<rg, 256, rs, s>>>(r, z, n, nb, sc);            // rz
+  k_coldot<<<rg, 256, rs, s>>>(r, r, n, nb, sc + 3 * nb);   // rr
+  k_coldot<<<rg, 256, rs, s>>>(dm, dm, n, nb, sc + 4 * nb); // dd
+  CK(cudaGetLastError());
+  std::vector<double> hs(5 * (size_t)nb);
+  int it = 0;
+  bool conv = false;
+  for (;;) {
+    if (it % 8 == 0 || it >= max_it) {
+      CK(cudaMemcpyAsync(hs.data(), sc, sizeof(double) * 5 * nb, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      conv = true;
+      for (int m = 0; m < nb; ++m)
+        if (!(std::sqrt(hs[3 * nb + m]) <= tol * std::sqrt(hs[4 * nb + m]) || hs[3 * nb + m] == 0.0)) conv = false;
+      if (conv || it >= max_it) break;
+    }
+    CK(cudaMemsetAsync(Ap, 0, sizeof(double) * N, s));
+    CK(launch_laplace(c, p, Ap, nb, 1, scale, s));
+    k_coldot<<<rg, 256, rs, s>>>(p, Ap, n, nb, sc + 2 * nb);
+    CK(cudaMemsetAsync(sc + 3 * nb, 0, sizeof(double) * nb, s));
+    k_cg_update<<<rg, 256, rs, s>>>(c.d_phi, r, z, p, Ap, c.d_diagA, c.d_Dsc, n, nb, sc, sc + nb, sc + 3 * nb);
+    k_cg_dir<<<nblk(N), 256, 0, s>>>(p, z, n, nb, sc);
+    k_cg_rot<<<1, 1024, 0, s>>>(sc, nb);
+    CK(cudaGetLastError());
+    ++it;
+  }
+  CK(launch_interp(c, c.d_phi, vH, nb, s));
+  if (iters) *iters = it;
+#undef CK
+  return conv ? EFE_OK : EFE_ERR_CG_NOCONV;
+}
+
+}  // namespace efe

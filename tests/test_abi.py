@@ -1,0 +1,53 @@
+"""The C-ABI library loads and exports every entry point include/efe.h
+declares (no compute calls: runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "efe.h")).read()
+    return sorted(set(re.findall(r"^(?:efe_status|const char\*)\s+(efe_\w+)\(", txt, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["efe_setup", "efe_apply_H", "efe_magnus_step", "efe_density_vxc", "efe_hartree",
+                     "efe_dipole", "efe_destroy", "efe_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    import shutil
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available to build the library")
+    from paper_2210_14421_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    from paper_2210_14421_gb300 import EXPORTED
+    assert sorted(EXPORTED) == _declared()
+
+
+def test_setup_rejects_bad_arguments_without_gpu_work():
+    """Argument validation happens before any device call."""
+    import numpy as np
+    from paper_2210_14421_gb300 import _binding as B
+    lib = B.lib()
+    xb = np.linspace(-1, 1, 3)
+    mesh = B.MeshDesc(2, 2, 2, B._dptr(xb), B._dptr(xb), B._dptr(xb), 7, 9)   # degree 7 unsupported
+    occ = np.ones(1)
+    opts = B.Options(1, 1, B._dptr(occ), 1e-8, 8, 0, 1e-10, 100, 0)
+    h = ctypes.c_void_p()
+    st = lib.efe_setup(ctypes.byref(mesh), None, 0, None, ctypes.byref(opts), ctypes.byref(h))
+    assert st == B.EFE_ERR_ARG
+    assert b"degree" in lib.efe_last_error(None)
+    mesh = B.MeshDesc(2, 2, 2, B._dptr(xb), B._dptr(xb), B._dptr(xb), 4, 6)
+    opts = B.Options(1, 1, B._dptr(occ), 1e-8, 99, 0, 1e-10, 100, 0)                # k_max too large
+    st = lib.efe_setup(ctypes.byref(mesh), None, 0, None, ctypes.byref(opts), ctypes.byref(h))
+    assert st == B.EFE_ERR_ARG
