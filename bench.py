@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Throughput of the EFE real-time TDDFT hot path on GB300.
+
+A step is one second-order Magnus predictor-corrector step (two adaptive
+Lanczos exponentials of Hbar, two densities, three Hartree solves, LDA, the
+dipole) of the sodium-cluster-like workload: 8 atoms with Z = 11, 44 doubly
+occupied orbitals, a 40-bohr cube with 31^3 graded cells of degree 4
+(~1.92M classical nodes) and 48 enrichment functions, dt = 0.05 a.u., delta
+kick 1e-3 along x.  Inputs are synthetic and seeded (efe_workloads.na8); the
+orbital block (1.35 GB) is larger than L2, so no flush is needed between
+steps.  One JSON line is printed by rank 0.
+
+  python bench.py [--gpus N --steps K --warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TDDFT steps/s & H.X TFLOP/s (% peak), mixed vs FP64 at dipole err<=1e-5"
+WORKLOAD = "Na8-like cluster (Z=11 x 8, 44 doubly occupied orbitals), 31^3 graded hex cells degree 4, " \
+           "GL 6^3, 48 enrichment fns (1s,2s,2p,3s per atom, cutoff 6 bohr), dt=0.05, kick 1e-3"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="efe", choices=["efe", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64 steps reported beside the main number")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=31, help="cells per axis (31 = the Na8-like workload)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def workload(cells, rank):
+    import efe_workloads as W
+    wl = W.na8() if cells == 31 else W.na_cluster(n_atoms=8, L=40.0, cells_per_axis=cells)
+    # independent problems per rank (weak scaling): the kick direction cycles x, y, z
+    d = [(1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0)][rank % 3]
+    wl.fields[0].direction = d
+    return wl
+
+
+def apply_model(ctx, wl, precision):
+    """Algorithmic work of one cell-apply launch (the dominant kernel).
+    bytes: read X and write Y once (complex128), the quadrature weights, the
+    coupling blocks and D; flops: the sum-factorised cell operator
+    (7 (p+1)^4 FMA kinetic + 2 (nq (p+1)^3 + nq^2 (p+1)^2 + nq^3 (p+1)) + nq^3
+    potential per real column) plus 2 (p+1)^3 FMA per real column per
+    cell-function pair of the enrichment coupling; dense-equivalent flops
+    N_c 2 N_n^2 cols for the H.X rate."""
+    p1, nq1 = wl.degree + 1, wl.n_quad
+    R = 2 * wl.n_orb * wl.batch
+    ts = 4 if precision == "mixed" else 8
+    bytes_ = 2 * ctx.n_dof * R * 8 + ctx.n_cells * nq1 ** 3 * ts + ctx.n_pairs * p1 ** 3 * ts + ctx.n_nodes * 8
+    fma_cell = 7 * p1 ** 4 + 2 * (nq1 * p1 ** 3 + nq1 ** 2 * p1 ** 2 + nq1 ** 3 * p1) + nq1 ** 3
+    flops = 2.0 * (ctx.n_cells * fma_cell * R + 2 * p1 ** 3 * ctx.n_pairs * R)
+    dense = ctx.n_cells * 2.0 * (p1 ** 3) ** 2 * R
+    return bytes_, flops, dense
+
+
+def cpu_baseline(wl_full, k_hint, budget_s=25.0):
+    """The FP64 oracle as it stands, timed on the host cores on a bounded sample:
+    one predictor-corrector step on a crop of the same mesh (n^3 cells around
+    the first atom, all orbitals, the enrichment functions of the atoms inside
+    the crop, the same Krylov tolerance), scaled to the full mesh by the cell
+    count."""
+    import numpy as np
+    from oracle import operators, tdks
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    n = 4
+    while True:
+        sub = []
+        centre = np.asarray(wl_full.R[0])
+        for a, b in enumerate((wl_full.xb, wl_full.yb, wl_full.zb)):
+            mid = int(np.searchsorted(b, centre[a])) - 1
+            lo = min(max(0, mid - n // 2), len(b) - 1 - n)
+            sub.append(b[lo:lo + n + 1].copy())
+        lo_c = np.array([b[0] for b in sub])
+        hi_c = np.array([b[-1] for b in sub])
+        # the enrichment functions of the atoms inside the crop
+        keep = [f for f in wl_full.enrich
+                if np.all(np.asarray(wl_full.R[f.atom]) > lo_c) and np.all(np.asarray(wl_full.R[f.atom]) < hi_c)]
+        idx = [wl_full.enrich.index(f) for f in keep]
+        wl = wl_full.with_(xb=sub[0], yb=sub[1], zb=sub[2], enrich=keep, enr_coefs=wl_full.enr_coefs[:, idx])
+        S = operators.System(wl)
+        psi = S.initial_orbitals()
+        psi = tdks.kick(S, psi, wl.fields, wl.n_orb, tol=wl.krylov_tol, k_max=wl.k_max)
+        st = tdks.make_state(S, psi, wl.occ, 1)
+        t0 = time.perf_counter()
+        tdks.magnus_step(S, psi, st, 0.0, wl.dt, wl.fields, wl.occ, wl.krylov_tol, wl.k_max)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or n >= 8:
+            break
+        n += 2
+    scale = wl_full.n_cells / S.mesh.n_cells
+    sec_per_step = dt * scale
+    return {"value": 1.0 / sec_per_step, "unit": "steps/s", "cores": int(cores), "kind": "oracle",
+            "sample": "one predictor-corrector step on a %dx%dx%d-cell crop of the same mesh (%d of %d cells, all "
+                      "%d orbitals, the %d enrichment functions of the atoms inside it), %.2f s, scaled by "
+                      "the cell count" % (n, n, n, S.mesh.n_cells, wl_full.n_cells, wl.n_orb, len(wl.enrich), dt)}
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = workload(args.cells, 0)
+    # each timed unit is one oracle sample step (bounded so the run ends in minutes)
+    vals = []
+    info = None
+    for i in range(max(1, min(args.steps, 3))):
+        info = cpu_baseline(wl, None, budget_s=20.0)
+        vals.append(info["value"])
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": len(vals), "warmup": 0, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": 1, "flush": "inputs larger than L2"},
+            "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"], "value": value,
+                             "unit": "steps/s"},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_efe(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as g
+    from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED, Context, fields_array
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    g.build()
+    dev = torch.cuda.current_device()
+    prec = EFE_MIXED if args.precision == "mixed" else EFE_FP64
+    wl = workload(args.cells, rank)
+    t_setup = time.perf_counter()
+    ctx = Context(wl, precision=prec, cg_tol=1e-10, cg_max_it=20000)
+    t_setup = time.perf_counter() - t_setup
+    psi = torch.zeros((ctx.n_dof, ctx.n_cols), dtype=torch.complex128, device="cuda")
+    ctx.init_orbitals(psi)
+    ctx.kick(psi, wl.fields)
+    psi_start = psi.clone()
+    arr = fields_array(wl.fields)
+    mu = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up (untimed); the first step also builds the state
+    infos = []
+    mus_mixed = []
+    t = 0.0
+    for _ in range(args.warmup):
+        infos.append(ctx.magnus_step(psi, t, wl.dt, wl.fields, mu))
+        mus_mixed.append(mu.cpu().numpy().copy())
+        t += wl.dt
+    # timed region
+    clocks = Clocks(dev)
+    ctx.profile(True)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.magnus_step_async(psi, t, wl.dt, arr, mu)
+        t += wl.dt
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_step = ms / args.steps
+    value = world * args.steps / (ms / 1000.0)
+
+    # dominant kernel: cell apply, timed by CUDA events on its stream inside the timed region
+    bytes_, flops, dense = apply_model(ctx, wl, args.precision)
+    t_apply = prof["apply_ms"] / max(prof["apply_launches"], 1) / 1000.0
+    peaks, src = measured_peaks()
+    gbs = bytes_ / t_apply / 1e9
+    tfl = flops / t_apply / 1e12
+    sm_mhz = (ck or {}).get("sm_mhz") or 1900.0
+    fp_lanes = 128 if args.precision == "mixed" else 2   # FP32 FMA lanes / FP64 FMA per clock per SM
+    alu_peak = 152 * fp_lanes * 2 * sm_mhz * 1e6 / 1e12
+    hbm_frac = gbs / peaks["hbm_gbs"]
+    alu_frac = tfl / alu_peak
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+                "frac": round(alu_frac, 4), "traffic": None,
+                "peak_source": "152 SMs x %d %s FMA/clk x 2 x %.0f MHz (median SM clock sampled in the timed region)"
+                               % (fp_lanes, "FP32" if fp_lanes == 128 else "FP64", sm_mhz),
+                "hbm_frac_of_measured": round(hbm_frac, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "traffic": None, "peak_source": src, "alu_frac": round(alu_frac, 4)}
+    roof.update({"kernel": "k_cell_apply<%s,5,6,ENR>" % ("float" if args.precision == "mixed" else "double"),
+                 "launches": prof["apply_launches"], "avg_ms": round(t_apply * 1000.0, 4),
+                 "algorithmic_bytes": int(bytes_), "algorithmic_flops": flops})
+    hx_tflops = dense / t_apply / 1e12
+
+    line = {"metric": METRIC, "value": round(value, 4), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32-contraction/f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic (seeded efe_workloads.na8)",
+            "config": {"workload": WORKLOAD, "precision": args.precision, "global_batch": world,
+                       "n_cells": ctx.n_cells, "n_nodes": ctx.n_nodes, "n_enrich": ctx.n_enrich,
+                       "n_pairs": ctx.n_pairs, "n_orb": wl.n_orb, "krylov_tol": wl.krylov_tol, "k_max": wl.k_max,
+                       "parallelism": "independent problem per GPU" if world > 1 else "1 GPU",
+                       "flush": "inputs larger than L2 (orbital block %.2f GB)" % (ctx.n_dof * ctx.n_cols * 16 / 1e9)},
+            "roofline": roof,
+            "hx": {"tflops_dense_equivalent": round(hx_tflops, 3),
+                   "note": "N_c * 2 N_n^2 * cols per H.X over the cell-apply time; the kernel does the "
+                           "sum-factorised equivalent"},
+            "gpu_launches": prof["launches"], "clocks": ck,
+            "krylov": {"k_pred": [i["k_pred"] for i in infos], "k_corr": [i["k_corr"] for i in infos],
+                       "cg_iters": [i["cg_iters"] for i in infos]},
+            "setup_s": round(t_setup, 2)}
+
+    if rank == 0 and args.fp64_steps > 0 and args.precision == "mixed":
+        # FP64 side by side from the same kicked state, and the mixed-vs-FP64 dipole error
+        ctx64 = Context(wl, precision=EFE_FP64, cg_tol=1e-10, cg_max_it=20000)
+        psi64 = psi_start.clone()
+        mus64 = []
+        t64 = 0.0
+        n_cmp = min(args.warmup, 1 + args.fp64_steps)
+        ctx64.magnus_step(psi64, t64, wl.dt, wl.fields, mu)
+        mus64.append(mu.cpu().numpy().copy())
+        t64 += wl.dt
+        torch.cuda.synchronize()
+        a0 = time.perf_counter()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            ctx64.magnus_step_async(psi64, t64, wl.dt, arr, mu)
+            t64 += wl.dt
+            if len(mus64) < n_cmp:
+                mus64.append(mu.cpu().numpy().copy())
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / args.fp64_steps
+        k = min(len(mus64), len(mus_mixed))
+        derr = float(np.max(np.abs(np.array(mus64[:k]) - np.array(mus_mixed[:k])))) if k else None
+        line["fp64"] = {"steps_per_s": round(1000.0 / ms64, 4), "ms_per_step": round(ms64, 1),
+                        "steps": args.fp64_steps, "dipole_err_mixed_vs_fp64": derr, "compared_steps": k}
+        ctx64.close()
+
+    # end to end through the public API with host buffers: H2D of the orbital
+    # block from pinned memory, the step, D2H of the dipole, every step
+    if rank == 0 and args.e2e_steps > 0:
+        host_psi = psi.cpu().pin_memory()
+        host_mu = torch.zeros((1, 3), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        a0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            psi.copy_(host_psi, non_blocking=True)
+            ctx.magnus_step_async(psi, t, wl.dt, arr, mu)
+            host_mu.copy_(mu, non_blocking=True)
+            torch.cuda.synchronize()
+            t += wl.dt
+        el = time.perf_counter() - a0
+        line["e2e"] = {"value": round(args.e2e_steps / el, 4), "unit": "steps/s",
+                       "h2d_bytes_per_step": int(psi.numel() * 16), "d2h_bytes_per_step": int(mu.numel() * 8)}
+
+    ctx.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        k_hint = max([i["k_corr"] for i in infos] or [wl.k_max])
+        line["cpu_baseline"] = cpu_baseline(workload(args.cells, 0), k_hint)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_efe(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

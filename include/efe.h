@@ -232,6 +232,16 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
                              const double* expo_host, const double* coef_host, const double* enr_host,
                              void* stream);
 
+/* Diagnostics (not part of the method).  efe_profile(ctx, 1) synchronises the
+ * device, resets a process-wide counter of kernel launches made by the library,
+ * and from then on brackets every launch of the cell-apply kernel with a pair of
+ * CUDA events recorded on the launching stream; efe_profile(ctx, 0) stops the
+ * timing.  efe_profile_read synchronises the device and returns the launches
+ * counted since the last efe_profile call, the cell-apply launches timed, and
+ * their summed device time in milliseconds (any pointer may be NULL). */
+efe_status efe_profile(efe_ctx* ctx, int32_t enable);
+efe_status efe_profile_read(efe_ctx* ctx, int64_t* launches, int64_t* apply_launches, double* apply_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "EFE_OK", 1: "EFE_ERR_ARG", 2: "EFE_ERR_NOMEM", 3: "EFE_ERR_C
 
 EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coords", "efe_set_potential",
             "efe_apply_H", "efe_magnus_step", "efe_reset_state", "efe_density_vxc", "efe_hartree", "efe_dipole",
-            "efe_kick", "efe_init_orbitals"]
+            "efe_kick", "efe_init_orbitals", "efe_profile", "efe_profile_read"]
 
 
 class MeshDesc(C.Structure):
@@ -88,6 +88,8 @@ def lib(path: str = LIB_PATH):
     L.efe_dipole.argtypes = [vp, vp, vp, vp]
     L.efe_kick.argtypes = [vp, vp, C.POINTER(Field), vp]
     L.efe_init_orbitals.argtypes = [vp, vp, i32, pdbl, pdbl, pdbl, pdbl, vp]
+    L.efe_profile.argtypes = [vp, i32]
+    L.efe_profile_read.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl)]
     for name in EXPORTED:
         if name != "efe_last_error":
             getattr(L, name).restype = C.c_int
@@ -233,6 +235,14 @@ class Context:
     def kick(self, psi, fields):
         st = lib().efe_kick(self.h, _ptr(psi), fields_array(fields), _stream())
         return self._check(st, allow=(EFE_OK, EFE_WARN_KRYLOV_CAP))
+
+    def profile(self, enable: bool = True):
+        self._check(lib().efe_profile(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        a, b, ms = C.c_int64(), C.c_int64(), C.c_double()
+        self._check(lib().efe_profile_read(self.h, C.byref(a), C.byref(b), C.byref(ms)))
+        return {"launches": a.value, "apply_launches": b.value, "apply_ms": ms.value}
 
     def init_orbitals(self, psi):
         wl = self.wl

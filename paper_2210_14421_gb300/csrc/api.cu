@@ -15,9 +15,32 @@ struct efe_ctx {
   efe::Ctx c;
 };
 
+#include <atomic>
+
 namespace efe {
 
 static thread_local std::string g_setup_err;
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void reset_launch_count() { g_launches.store(0); }
+
+void prof_pair(Ctx& c, cudaEvent_t& a, cudaEvent_t& b) {
+  a = b = nullptr;
+  if (!c.prof.on) return;
+  if (c.prof.used + 2 > c.prof.pool.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      c.prof.pool.push_back(e);
+    }
+  }
+  a = c.prof.pool[c.prof.used];
+  b = c.prof.pool[c.prof.used + 1];
+  c.prof.used += 2;
+  c.prof.apply_launches += 1;
+}
 
 template <typename T>
 static void dfree(T*& p) {
@@ -35,6 +58,7 @@ Ctx::~Ctx() {
   dfree(op.W64); dfree(op.W32); dfree(op.E64); dfree(op.E32); dfree(op.HEE);
   dfree(d_rho); dfree(d_vH); dfree(d_vxc); dfree(d_Q); dfree(d_psi_p); dfree(d_xE); dfree(d_yE);
   dfree(d_lz); dfree(d_lzi); dfree(d_rho2); dfree(d_v); dfree(d_cg); dfree(d_red);
+  for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
   if (h_flag) cudaFreeHost(h_flag);
   h_flag = nullptr;
   if (prev >= 0) cudaSetDevice(prev);
@@ -623,6 +647,33 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
   dfree(dc); dfree(de); dfree(dk); dfree(dn);
   if (e != cudaSuccess) return cuda_fail(c, e, "initial orbitals");
   c.state_valid = false;
+  return EFE_OK;
+}
+
+efe_status efe_profile(efe_ctx* ctx, int32_t enable) {
+  CHECK_CTX(ctx);
+  Ctx& c = ctx->c;
+  TRY_CUDA(c, cudaDeviceSynchronize(), "profile");
+  c.prof.on = enable != 0;
+  c.prof.used = 0;
+  c.prof.apply_launches = 0;
+  reset_launch_count();
+  return EFE_OK;
+}
+
+efe_status efe_profile_read(efe_ctx* ctx, int64_t* launches, int64_t* apply_launches, double* apply_ms) {
+  CHECK_CTX(ctx);
+  Ctx& c = ctx->c;
+  TRY_CUDA(c, cudaDeviceSynchronize(), "profile");
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < c.prof.used; i += 2) {
+    float ms = 0.0f;
+    TRY_CUDA(c, cudaEventElapsedTime(&ms, c.prof.pool[i], c.prof.pool[i + 1]), "profile events");
+    total += ms;
+  }
+  if (launches) *launches = launch_count();
+  if (apply_launches) *apply_launches = c.prof.apply_launches;
+  if (apply_ms) *apply_ms = total;
   return EFE_OK;
 }
 

@@ -65,8 +65,17 @@ struct Operator {
   bool valid = false;
 };
 
+// Per-launch timing of the cell-apply kernel (enabled by efe_profile).
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;   // pairs (start, stop)
+  size_t used = 0;                 // events used since the last read
+  long long apply_launches = 0;
+};
+
 struct Ctx {
   int device = 0;
+  Prof prof;
   std::string err;
   // sizes
   int p = 0, P1 = 0, NQ1 = 0, nn = 0, nq = 0;
@@ -137,6 +146,13 @@ struct Ctx {
   double* d_red = nullptr;     // reduction scratch
   ~Ctx();
 };
+
+// process-wide count of kernel launches (diagnostics)
+void note_launch();
+long long launch_count();
+void reset_launch_count();
+// returns (start, stop) events to bracket one cell-apply launch, or nulls when timing is off
+void prof_pair(Ctx& c, cudaEvent_t& a, cudaEvent_t& b);
 
 // ---- host math (host_math.cu)
 void gauss_legendre(int n, double* x, double* w);

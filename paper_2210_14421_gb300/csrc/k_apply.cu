@@ -395,28 +395,37 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
     EFE_CUDA_TRY(cudaMemsetAsync(c.d_yE, 0, sizeof(double) * c.nE * ld2, s));
     long long n = (long long)c.nE * ncols2;
     k_enr_pre<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, X, c.n_h, ld2, ncols2, c.nE, c.d_xE);
+    note_launch();
     EFE_CUDA_TRY(cudaGetLastError());
   }
   const T* W = std::is_same<T, float>::value ? (const T*)c.op.W32 : (const T*)c.op.W64;
   const T* E = std::is_same<T, float>::value ? (const T*)c.op.E32 : (const T*)c.op.E64;
   const size_t sm = tile_smem<T, NQ1>();
   dim3 grid(c.nc, batch);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  prof_pair(c, e0, e1);
+  if (e0) EFE_CUDA_TRY(cudaEventRecord(e0, s));
   if (c.n_pairs > 0) {
     auto f = k_cell_apply<T, P1, NQ1, true>;
     EFE_CUDA_TRY(set_smem(f, sm));
     f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, c.d_Dsc, W, c.op.kin, c.d_pair_start,
                                  c.d_pair_fn, E, c.n_pairs, c.d_xE, c.d_yE);
+    note_launch();
   } else {
     auto f = k_cell_apply<T, P1, NQ1, false>;
     EFE_CUDA_TRY(set_smem(f, sm));
     f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, c.d_Dsc, W, c.op.kin, nullptr, nullptr,
                                  nullptr, 0, nullptr, nullptr);
+    note_launch();
   }
   EFE_CUDA_TRY(cudaGetLastError());
+  if (e1) EFE_CUDA_TRY(cudaEventRecord(e1, s));
   if (c.nE > 0) {
     long long n = (long long)c.nE * ncols2;
     k_enr_post1<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.op.HEE, c.d_xE, c.d_yE, ld2, ncols2, cols_member, c.nE);
+    note_launch();
     k_enr_post2<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, c.d_yE, Y, c.n_h, ld2, ncols2, c.nE);
+    note_launch();
     EFE_CUDA_TRY(cudaGetLastError());
   }
   return cudaSuccess;
@@ -426,6 +435,7 @@ template <int P1, int NQ1>
 static cudaError_t build_impl(Ctx& c, const double* v, int batch, double kin, cudaStream_t s) {
   const long long per = (long long)c.nc * c.nq;
   k_op_W<<<(unsigned)((per * batch + 255) / 256), 256, 0, s>>>(c.d_wJ, v, c.op.W64, c.op.W32, per, batch);
+  note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   if (c.nE > 0) {
     if (c.n_pairs > 0) {
@@ -436,12 +446,15 @@ static cudaError_t build_impl(Ctx& c, const double* v, int batch, double kin, cu
       dim3 grid((unsigned)((c.n_pairs + RT - 1) / RT), batch);
       f<<<grid, kThreads, sm, s>>>(c.tab, c.d_pair_cell, c.n_pairs, c.nc, c.d_Atil, c.d_KE, c.op.W64, kin, c.op.E64,
                                    c.op.E32);
+      note_launch();
       EFE_CUDA_TRY(cudaGetLastError());
     }
     long long n = (long long)batch * c.nE * c.nE;
     k_op_hee_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_KEE, kin, c.op.HEE, c.nE, batch);
+    note_launch();
     dim3 g2(c.nc, batch);
     k_op_hee<<<g2, 128, 0, s>>>(c.d_pair_start, c.d_pair_fn, c.d_Atil, c.op.W64, c.nc, c.nq, c.nE, c.op.HEE);
+    note_launch();
     EFE_CUDA_TRY(cudaGetLastError());
   }
   return cudaSuccess;
@@ -477,6 +490,7 @@ static cudaError_t laplace_impl(const Ctx& c, const double* x, double* y, int nb
   EFE_CUDA_TRY(set_smem(f, sm));
   const long long slots = (long long)c.nc * nb;
   f<<<(unsigned)((slots + RT - 1) / RT), kThreads, sm, s>>>(c.tab, c.mesh, x, y, nb, c.d_Dsc, mask_in, scale);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -488,6 +502,7 @@ static cudaError_t loadvec_impl(const Ctx& c, const double* f, double* d, int nb
   EFE_CUDA_TRY(set_smem(k, sm));
   const long long slots = (long long)c.nc * nb;
   k<<<(unsigned)((slots + RT - 1) / RT), kThreads, sm, s>>>(c.tab, c.mesh, c.d_wJ, f, d, nb);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -499,6 +514,7 @@ static cudaError_t interp_impl(const Ctx& c, const double* x, double* out, int n
   EFE_CUDA_TRY(set_smem(k, sm));
   const long long slots = (long long)c.nc * nb;
   k<<<(unsigned)((slots + RT - 1) / RT), kThreads, sm, s>>>(c.tab, c.mesh, x, out, nb);
+  note_launch();
   return cudaGetLastError();
 }
 

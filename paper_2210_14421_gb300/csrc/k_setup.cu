@@ -158,16 +158,8 @@ __global__ void k_enr_b(const __grid_constant__ RefTables tab, const MeshView me
   atomicAdd(&bmat[(long long)pair_fn[k] * mesh.n_h + g], acc);
 }
 
-// c = b / M on interior nodes, 0 on the boundary (only interior classical
-// functions exist), kept in place in bmat's copy cmat.
-__global__ void k_enr_c(const double* __restrict__ bmat, const double* __restrict__ Dsc, double* __restrict__ cmat,
-                        long long n) {
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= n) return;
-  // Dsc = 1/sqrt(M) inside, 0 on the boundary -> 1/M = Dsc^2
-  cmat[idx] = 0.0;
-}
-
+// c = b / M on interior nodes (1/M = D^2 with D = mask / sqrt(M)), 0 on the boundary
+// where no classical function exists.
 __global__ void k_enr_c2(const double* __restrict__ bmat, const double* __restrict__ Dsc, double* __restrict__ cmat,
                          long long n_h, int nE) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -404,6 +396,7 @@ cudaError_t launch_geometry(const Ctx& c, cudaStream_t s) {
   EFE_CUDA_TRY(cudaMemcpyAsync(d_at, at.data(), sizeof(double) * at.size(), cudaMemcpyHostToDevice, s));
   k_geometry<<<nblk((long long)c.nc * c.nq), 256, 0, s>>>(c.tab, c.mesh, c.NQ1, d_at, c.n_atoms, c.d_xq, c.d_wJ,
                                                         c.d_vN);
+  note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   EFE_CUDA_TRY(cudaStreamSynchronize(s));
   cudaFree(d_at);
@@ -418,6 +411,7 @@ cudaError_t launch_coords(const Ctx& c, double* nodes, double* quad, cudaStream_
     EFE_CUDA_TRY(cudaMalloc(&d_xi, sizeof(xi)));
     EFE_CUDA_TRY(cudaMemcpyAsync(d_xi, xi, sizeof(xi), cudaMemcpyHostToDevice, s));
     k_node_coords<<<nblk(c.n_h), 256, 0, s>>>(c.tab, c.mesh, d_xi, nodes);
+    note_launch();
     EFE_CUDA_TRY(cudaGetLastError());
     EFE_CUDA_TRY(cudaStreamSynchronize(s));
     cudaFree(d_xi);
@@ -451,19 +445,25 @@ cudaError_t launch_enrich_setup(Ctx& c, cudaStream_t s) {
   if (np > 0) {
     k_enr_eval<<<nblk(np * c.nq), 256, 0, s>>>(c.d_pair_cell, c.d_pair_fn, np, c.nq, c.d_xq, d_fns, c.r0, c.s,
                                                d_Aval, d_Agrad);
+    note_launch();
     k_enr_b<<<nblk(np * c.nn), 256, 0, s>>>(c.tab, c.mesh, c.NQ1, c.d_pair_cell, c.d_pair_fn, np, c.d_wJ, d_Aval, d_b);
+    note_launch();
     EFE_CUDA_TRY(cudaGetLastError());
   }
   k_enr_c2<<<nblk(c.n_h * nE), 256, 0, s>>>(d_b, c.d_Dsc, d_cm, c.n_h, nE);
+  note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   if (np > 0) {
     const size_t sm = sizeof(double) * (c.nn + 3 * c.nq);
     k_enr_orth<<<(unsigned)np, 128, sm, s>>>(c.tab, c.mesh, c.NQ1, c.d_pair_cell, c.d_pair_fn, np, c.d_wJ, d_cm,
                                              d_Aval, d_Agrad, c.d_Atil, c.d_KE);
+    note_launch();
     k_enr_gram<<<c.nc, 128, 0, s>>>(c.d_pair_start, c.d_pair_fn, c.nq, nE, c.d_wJ, d_Aval, d_Agrad, d_MAA, c.d_KEE);
+    note_launch();
     EFE_CUDA_TRY(cudaGetLastError());
   }
   k_mee<<<nE * nE, kThreads, 0, s>>>(d_b, c.d_Dsc, c.n_h, nE, d_MAA, d_Mee);
+  note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   c.Mee.assign((size_t)nE * nE, 0.0);
   EFE_CUDA_TRY(cudaMemcpyAsync(c.Mee.data(), d_Mee, sizeof(double) * nE * nE, cudaMemcpyDeviceToHost, s));
@@ -482,6 +482,7 @@ cudaError_t launch_poisson_setup(Ctx& c, cudaStream_t s) {
   EFE_CUDA_TRY(cudaMemsetAsync(c.d_diagA, 0, sizeof(double) * c.n_h, s));
   const double scale = 1.0 / (2.0 * 3.14159265358979323846);   // (1/4pi) int grad.grad = (1/2pi) * kinetic
   k_laplace_diag<<<nblk((long long)c.nc * c.nn), 256, 0, s>>>(c.tab, c.mesh, scale, c.d_diagA);
+  note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   double* d_nodes = nullptr;
   EFE_CUDA_TRY(cudaMalloc(&d_nodes, sizeof(double) * 3 * c.n_h));
@@ -497,6 +498,7 @@ cudaError_t launch_poisson_setup(Ctx& c, cudaStream_t s) {
   EFE_CUDA_TRY(cudaMalloc(&d_at, sizeof(double) * std::max<size_t>(at.size(), 4)));
   EFE_CUDA_TRY(cudaMemcpyAsync(d_at, at.data(), sizeof(double) * at.size(), cudaMemcpyHostToDevice, s));
   k_poisson_bc<<<nblk(c.n_h), 256, 0, s>>>(c.mesh, d_nodes, c.d_Dsc, d_at, c.n_atoms, c.d_phiB, c.d_diagA);
+  note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   EFE_CUDA_TRY(cudaStreamSynchronize(s));
   cudaFree(d_nodes);
@@ -512,9 +514,11 @@ cudaError_t launch_init_orbitals(const Ctx& c, double* psi, int G, const double*
   const long long ld2 = 2LL * c.n_orb * c.batch;
   k_init_orb<<<nblk(c.n_h * c.n_orb), 256, 0, s>>>(d_nodes, c.d_Dsc, c.n_h, c.n_orb, c.batch, G, d_centers, d_expo,
                                                   d_coef, psi, ld2);
+  note_launch();
   if (c.nE > 0)
     k_init_enr<<<nblk((long long)c.nE * c.n_orb), 256, 0, s>>>(c.d_Shalf, d_enr, c.n_h, c.nE, c.n_orb, c.batch, psi,
                                                                ld2);
+    note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   EFE_CUDA_TRY(cudaStreamSynchronize(s));
   cudaFree(d_nodes);

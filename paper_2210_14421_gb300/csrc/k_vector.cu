@@ -331,8 +331,11 @@ cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h
   const unsigned rg = red_grid(n, C);
   const size_t rs = red_smem(C);
   k_norm2<<<rg, 256, rs, s>>>(in, n, (int)C, ld2, v.red);
+  note_launch();
   k_lz_init<<<nblk(n * C), 256, 0, s>>>(in, c.d_Q, n, (int)C, ld2, v.red);
+  note_launch();
   k_lz_state<<<nblk(C), 256, 0, s>>>(v, (int)C, d_dts);
+  note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   for (int j = 0; j < c.k_max; ++j) {
     double* Qj = c.d_Q + j * qstride;
@@ -341,20 +344,26 @@ cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h
     EFE_CUDA_TRY(cudaMemsetAsync(v.red, 0, sizeof(double) * 2 * C, s));   // red and red2
     EFE_CUDA_TRY(cudaMemsetAsync(v.n_active, 0, sizeof(int), s));
     k_lz_dot<<<rg, 256, rs, s>>>(Qj, W, n, (int)C, v.active, v.red);
+    note_launch();
     k_lz_update<<<rg, 256, rs, s>>>(W, Qj, j > 0 ? c.d_Q + (j - 1) * qstride : nullptr, n, (int)C, v.active, v.red,
                                     j > 0 ? v.beta + (long long)(j - 1) * C : nullptr, v.red2);
+    note_launch();
     k_lz_tri<<<(unsigned)C, 32, sizeof(double) * 2 * (j + 1) * (j + 1), s>>>(v, (int)C, j, c.k_max, c.fixed_k,
                                                                           c.krylov_tol);
+    note_launch();
     k_lz_scale<<<nblk(n * C), 256, 0, s>>>(W, n, (int)C, v.active, v.invb);
+    note_launch();
     EFE_CUDA_TRY(cudaGetLastError());
     EFE_CUDA_TRY(cudaMemcpyAsync(c.h_flag, v.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
     EFE_CUDA_TRY(cudaStreamSynchronize(s));
     if (*c.h_flag == 0) break;
   }
   k_lz_combine<<<nblk(n * C), 256, 0, s>>>(c.d_Q, qstride, n, (int)C, v, out, ld2);
+  note_launch();
   int* d_si = v.n_active;   // reuse: [0] max k, [1] caps
   double* d_sd = v.red;
   k_lz_stats<<<1, 256, 0, s>>>(v, (int)C, d_si, d_sd);
+  note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   int hi[2];
   double hd;
@@ -438,6 +447,7 @@ static cudaError_t density_impl(Ctx& c, const double* psi, double* rho, cudaStre
   if (c.nE > 0) {
     long long n = (long long)c.nE * ld2;
     k_enr_pre_d<<<nblk(n), 256, 0, s>>>(c.d_S, psi, c.n_h, ld2, (int)ld2, c.nE, c.d_xE);
+    note_launch();
   }
   dim3 grid(c.nc, c.batch);
   const size_t sm = sizeof(double) * (3 * 16 * NQ1 * NQ1 * NQ1 + NQ1 * NQ1 * NQ1);
@@ -445,6 +455,7 @@ static cudaError_t density_impl(Ctx& c, const double* psi, double* rho, cudaStre
   k_density<P1, NQ1><<<grid, kThreads, sm, s>>>(c.tab, c.mesh, psi, ld2, c.n_orb, c.d_occ, c.d_Dsc,
                                                 c.n_pairs ? c.d_pair_start : nullptr, c.d_pair_fn, c.d_Atil, c.d_xE,
                                                 rho);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -487,6 +498,7 @@ __global__ void k_lda(const double* __restrict__ rho, double* __restrict__ vxc, 
 
 cudaError_t launch_lda(const Ctx& c, const double* rho, double* vxc, double* exc, long long n, cudaStream_t s) {
   k_lda<<<nblk(n), 256, 0, s>>>(rho, vxc, exc, n);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -529,10 +541,12 @@ cudaError_t launch_dipole(const Ctx& c, const double* rho, double* mu, cudaStrea
   for (int b0 = 0; b0 < c.batch; b0 += 1024) {
     int nb = std::min(1024, c.batch - b0);
     k_dipole_init<<<1, 1024, 0, s>>>(mu + 3 * b0, nb, n[0], n[1], n[2]);
+    note_launch();
   }
   const long long npts = (long long)c.nc * c.nq;
   dim3 grid(std::min<long long>(nblk(npts), 608), c.batch);
   k_dipole<<<grid, 256, 0, s>>>(rho, c.d_wJ, c.d_xq, npts, mu);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -598,11 +612,13 @@ cudaError_t launch_potential_sum(const Ctx& c, const double* vH, const double* v
     for (int k = 0; k < 3 * c.batch; ++k) E.e[k] = E_host[k];
     k_potential_v<<<nblk(npts * c.batch), 256, 0, s>>>(nuclear ? c.d_vN : nullptr, vH, vxc, c.d_xq, E, npts,
                                                        c.batch, v);
+    note_launch();
     return cudaGetLastError();
   }
   EFE_CUDA_TRY(cudaMemcpyAsync(c.d_red, E_host, sizeof(double) * 3 * c.batch, cudaMemcpyHostToDevice, s));
   k_potential<<<nblk(npts * c.batch), 256, 0, s>>>(nuclear ? c.d_vN : nullptr, vH, vxc, c.d_xq, c.d_red, npts,
                                                    c.batch, v);
+  note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   return cudaStreamSynchronize(s);
 }
@@ -615,6 +631,7 @@ __global__ void k_axpby(double* __restrict__ y, const double* __restrict__ a, co
 
 cudaError_t launch_axpby(double* y, const double* a, const double* b, double ca, double cb, long long n, cudaStream_t s) {
   k_axpby<<<nblk(n), 256, 0, s>>>(y, a, b, ca, cb, n);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -729,14 +746,17 @@ efe_status run_hartree(Ctx& c, const double* rho, double* vH, double tol, int ma
   CK(cudaMemsetAsync(d, 0, sizeof(double) * N, s));
   CK(launch_load_vector(c, rho, d, nb, s));
   k_cg_bc<<<nblk(N), 256, 0, s>>>(c.d_phi, c.d_phiB, c.d_Dsc, n, nb);
+  note_launch();
   CK(cudaMemsetAsync(Ap, 0, sizeof(double) * N, s));
   CK(launch_laplace(c, c.d_phi, Ap, nb, 0, scale, s));
   k_cg_start<<<nblk(N), 256, 0, s>>>(d, Ap, c.d_diagA, c.d_Dsc, n, nb, r, z, p, dm);
+  note_launch();
   CK(cudaMemsetAsync(sc, 0, sizeof(double) * 5 * nb, s));
   k_coldot<<<rg, 256, rs, s>>>(r, z, n, nb, sc);            // rz
   k_coldot<<<rg, 256, rs, s>>>(r, r, n, nb, sc + 3 * nb);   // rr
   k_coldot<<<rg, 256, rs, s>>>(dm, dm, n, nb, sc + 4 * nb); // dd
   CK(cudaGetLastError());
+  note_launch();
   std::vector<double> hs(5 * (size_t)nb);
   int it = 0;
   bool conv = false;
@@ -752,10 +772,14 @@ efe_status run_hartree(Ctx& c, const double* rho, double* vH, double tol, int ma
     CK(cudaMemsetAsync(Ap, 0, sizeof(double) * N, s));
     CK(launch_laplace(c, p, Ap, nb, 1, scale, s));
     k_coldot<<<rg, 256, rs, s>>>(p, Ap, n, nb, sc + 2 * nb);
+    note_launch();
     CK(cudaMemsetAsync(sc + 3 * nb, 0, sizeof(double) * nb, s));
     k_cg_update<<<rg, 256, rs, s>>>(c.d_phi, r, z, p, Ap, c.d_diagA, c.d_Dsc, n, nb, sc, sc + nb, sc + 3 * nb);
+    note_launch();
     k_cg_dir<<<nblk(N), 256, 0, s>>>(p, z, n, nb, sc);
+    note_launch();
     k_cg_rot<<<1, 1024, 0, s>>>(sc, nb);
+    note_launch();
     CK(cudaGetLastError());
     ++it;
   }
