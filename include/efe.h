@@ -121,12 +121,19 @@ typedef struct {
   int32_t batch;              /* independent propagations (own density, potential, field) */
   const double* occ_host;     /* n_orb occupations (2.0 for doubly occupied) */
   double krylov_tol;          /* Lanczos stop threshold on eps_k of Eq. AdaptiveKrylovErr */
-  int32_t k_max;              /* Lanczos cap, 1 <= k_max <= 32 */
+  int32_t k_max;              /* Lanczos cap, 1 <= k_max <= 64 */
   int32_t fixed_k;            /* > 0: take exactly fixed_k Lanczos steps (tests) */
   double cg_tol;              /* Hartree PCG relative residual target */
   int32_t cg_max_it;
-  int32_t precision;          /* efe_precision used by efe_magnus_step and efe_kick */
+  int32_t precision;          /* efe_precision used by efe_magnus_step (efe_kick is always FP64) */
+  int32_t hartree_method;     /* EFE_HARTREE_FDM (direct) or EFE_HARTREE_PCG */
 } efe_options;
+
+/* Hartree solvers for the same discrete system (Eq. DiscretePoisson):
+ * FDM  - direct solve by fast diagonalisation of the Kronecker-sum stiffness of
+ *        the rectilinear mesh (exact to rounding; cg_tol / cg_max_it unused);
+ * PCG  - Jacobi-preconditioned conjugate gradients to cg_tol. */
+enum { EFE_HARTREE_FDM = 0, EFE_HARTREE_PCG = 1 };
 
 typedef struct {
   int32_t k_pred_max;         /* largest Lanczos dimension used in the predictor */
@@ -207,12 +214,14 @@ efe_status efe_reset_state(efe_ctx* ctx);
 efe_status efe_density_vxc(efe_ctx* ctx, const double* psi_bar_dev, double* rho_dev, double* vxc_dev,
                            double* exc_dev, void* stream);
 
-/* Hartree potential (Eqs. Hartree_possion, DiscretePoisson): Jacobi-preconditioned
- * CG for (1/4pi) K phi = d, d_i = int rho N_i, phi = sum Z_I / |x - R_I| on the
- * boundary, warm-started from the previous solution held by the context;
- * vH_dev receives phi interpolated to the quadrature points [batch][n_cells][n_q].
- * iters_host: NULL or receives the iteration count (synchronises `stream`).
- * Returns EFE_ERR_CG_NOCONV (after writing the last iterate) if tol is not met. */
+/* Hartree potential (Eqs. Hartree_possion, DiscretePoisson): solves
+ * (1/4pi) K phi = d, d_i = int rho N_i, with phi = sum Z_I / |x - R_I| on the
+ * boundary, by the context's hartree_method (FDM: direct; PCG: Jacobi-preconditioned
+ * CG to relative residual tol, warm-started from the previous solution held by
+ * the context); vH_dev receives phi interpolated to the quadrature points
+ * [batch][n_cells][n_q].  iters_host: NULL or receives the PCG iteration count
+ * (1 for FDM; PCG synchronises `stream`).  Returns EFE_ERR_CG_NOCONV (after
+ * writing the last iterate) if PCG does not meet tol. */
 efe_status efe_hartree(efe_ctx* ctx, const double* rho_dev, double* vH_dev, double tol, int32_t max_it,
                        int32_t* iters_host, void* stream);
 
@@ -220,7 +229,8 @@ efe_status efe_hartree(efe_ctx* ctx, const double* rho_dev, double* vH_dev, doub
 efe_status efe_dipole(efe_ctx* ctx, const double* rho_dev, double* mu_dev, void* stream);
 
 /* Delta kick psi_bar <- exp(i kick d.Xbar) psi_bar per batch member, with Xbar the
- * Loewdin-transformed position operator, by the same Lanczos exponential. */
+ * Loewdin-transformed position operator, by the same Lanczos exponential with
+ * float64 applies (the initial condition carries no float32 rounding). */
 efe_status efe_kick(efe_ctx* ctx, double* psi_bar_dev, const efe_field* fields_host, void* stream);
 
 /* Initial orbitals from Gaussian descriptors: classical coefficients
@@ -240,6 +250,14 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
  * counted since the last efe_profile call, the cell-apply launches timed, and
  * their summed device time in milliseconds (any pointer may be NULL). */
 efe_status efe_profile(efe_ctx* ctx, int32_t enable);
+
+/* Diagnostics (not part of the method): checks, on the current device, the
+ * integer-pipe binary64 <-> binary32 conversions the mixed-precision kernels
+ * use against the hardware conversions, bit for bit, on n seeded patterns per
+ * direction (normal binary32 range, a quarter of the doubles exact
+ * round-to-nearest ties).  *mismatches_host receives the count (0 expected).
+ * Synchronises the device. */
+efe_status efe_selftest(int64_t n, int64_t* mismatches_host);
 efe_status efe_profile_read(efe_ctx* ctx, int64_t* launches, int64_t* apply_launches, double* apply_ms);
 
 #ifdef __cplusplus

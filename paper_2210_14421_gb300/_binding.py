@@ -14,12 +14,13 @@ LIB_PATH = os.path.join(_HERE, "_build", "libefe.so")
 EFE_OK, EFE_ERR_ARG, EFE_ERR_NOMEM, EFE_ERR_CUDA, EFE_ERR_NOT_SPD = 0, 1, 2, 3, 4
 EFE_WARN_KRYLOV_CAP, EFE_ERR_CG_NOCONV, EFE_ERR_TIMEOUT, EFE_ERR_STATE = 5, 6, 7, 8
 EFE_FP64, EFE_MIXED = 0, 1
+EFE_HARTREE_FDM, EFE_HARTREE_PCG = 0, 1
 STATUS_NAMES = {0: "EFE_OK", 1: "EFE_ERR_ARG", 2: "EFE_ERR_NOMEM", 3: "EFE_ERR_CUDA", 4: "EFE_ERR_NOT_SPD",
                 5: "EFE_WARN_KRYLOV_CAP", 6: "EFE_ERR_CG_NOCONV", 7: "EFE_ERR_TIMEOUT", 8: "EFE_ERR_STATE"}
 
 EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coords", "efe_set_potential",
             "efe_apply_H", "efe_magnus_step", "efe_reset_state", "efe_density_vxc", "efe_hartree", "efe_dipole",
-            "efe_kick", "efe_init_orbitals", "efe_profile", "efe_profile_read"]
+            "efe_kick", "efe_init_orbitals", "efe_profile", "efe_profile_read", "efe_selftest"]
 
 
 class MeshDesc(C.Structure):
@@ -50,7 +51,7 @@ class Field(C.Structure):
 class Options(C.Structure):
     _fields_ = [("n_orb", C.c_int32), ("batch", C.c_int32), ("occ_host", C.POINTER(C.c_double)),
                 ("krylov_tol", C.c_double), ("k_max", C.c_int32), ("fixed_k", C.c_int32), ("cg_tol", C.c_double),
-                ("cg_max_it", C.c_int32), ("precision", C.c_int32)]
+                ("cg_max_it", C.c_int32), ("precision", C.c_int32), ("hartree_method", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -89,12 +90,22 @@ def lib(path: str = LIB_PATH):
     L.efe_kick.argtypes = [vp, vp, C.POINTER(Field), vp]
     L.efe_init_orbitals.argtypes = [vp, vp, i32, pdbl, pdbl, pdbl, pdbl, vp]
     L.efe_profile.argtypes = [vp, i32]
+    L.efe_selftest.argtypes = [i64, C.POINTER(i64)]
     L.efe_profile_read.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl)]
     for name in EXPORTED:
         if name != "efe_last_error":
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
+
+
+def selftest(n: int = 1 << 24) -> int:
+    """Mismatches of the integer-pipe float conversions against the hardware ones."""
+    m = C.c_int64()
+    st = lib().efe_selftest(int(n), C.byref(m))
+    if st != EFE_OK:
+        raise EfeError(st, lib().efe_last_error(None).decode())
+    return m.value
 
 
 class EfeError(RuntimeError):
@@ -132,7 +143,7 @@ class Context:
     """Owns one efe_ctx built from an `efe_workloads.Workload`."""
 
     def __init__(self, wl, precision: int = EFE_FP64, krylov_tol=None, k_max=None, fixed_k: int = 0,
-                 cg_tol: float = 1e-12, cg_max_it: int = 5000):
+                 cg_tol: float = 1e-12, cg_max_it: int = 5000, hartree_method: int = EFE_HARTREE_FDM):
         L = lib()
         self.wl = wl
         self._keep = []
@@ -155,7 +166,7 @@ class Context:
         opts = Options(int(wl.n_orb), int(wl.batch), _dptr(occ),
                        float(wl.krylov_tol if krylov_tol is None else krylov_tol),
                        int(wl.k_max if k_max is None else k_max), int(fixed_k), float(cg_tol), int(cg_max_it),
-                       int(precision))
+                       int(precision), int(hartree_method))
         h = C.c_void_p()
         st = L.efe_setup(C.byref(mesh), atoms, na, C.byref(enr), C.byref(opts), C.byref(h))
         if st != EFE_OK:

@@ -52,9 +52,13 @@ Ctx::~Ctx() {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(device);
-  dfree(d_geo); dfree(d_Dsc); dfree(d_M); dfree(d_occ); dfree(d_vN); dfree(d_wJ); dfree(d_xq);
+  dfree(d_geo); dfree(d_Dsc); dfree(d_Dsc32); dfree(d_M); dfree(d_xE32); dfree(d_occ); dfree(d_vN); dfree(d_wJ); dfree(d_xq);
   dfree(d_pair_start); dfree(d_pair_fn); dfree(d_pair_cell); dfree(d_Atil); dfree(d_KE); dfree(d_KEE);
+  if (d_phiB_nb != d_phiB) dfree(d_phiB_nb);
+  d_phiB_nb = nullptr;
   dfree(d_S); dfree(d_Shalf); dfree(d_diagA); dfree(d_phiB); dfree(d_phi);
+  for (int a = 0; a < 3; ++a) { dfree(d_fdmV[a]); dfree(d_fdmL[a]); }
+  dfree(d_fdmT);
   dfree(op.W64); dfree(op.W32); dfree(op.E64); dfree(op.E32); dfree(op.HEE);
   dfree(d_rho); dfree(d_vH); dfree(d_vxc); dfree(d_Q); dfree(d_psi_p); dfree(d_xE); dfree(d_yE);
   dfree(d_lz); dfree(d_lzi); dfree(d_rho2); dfree(d_v); dfree(d_cg); dfree(d_red);
@@ -96,6 +100,7 @@ static efe_status ensure_ws(Ctx& c, long long C, long long ld) {
   TRY_CUDA(c, dalloc(c.d_lz, (size_t)(4 * kMaxK + 8) * need_ld), "allocating Lanczos scalars");
   TRY_CUDA(c, dalloc(c.d_lzi, (size_t)3 * need_ld + 8), "allocating Lanczos state");
   TRY_CUDA(c, dalloc(c.d_xE, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
+  TRY_CUDA(c, dalloc(c.d_xE32, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
   TRY_CUDA(c, dalloc(c.d_yE, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
   c.ws_cols = need_ld;
   return EFE_OK;
@@ -166,9 +171,13 @@ static bool validate(const efe_mesh_desc* mesh, const efe_atom* atoms, int n_ato
     }
   }
   if (o->n_orb < 1 || o->batch < 1 || !o->occ_host) { why = "n_orb, batch >= 1 and occupations required"; return false; }
-  if (o->k_max < 1 || o->k_max > kMaxK) { why = "k_max must be in [1, 32]"; return false; }
+  if (o->k_max < 1 || o->k_max > kMaxK) { why = "k_max must be in [1, 64]"; return false; }
   if (o->fixed_k < 0 || o->fixed_k > o->k_max) { why = "fixed_k must be in [0, k_max]"; return false; }
   if (o->precision != EFE_FP64 && o->precision != EFE_MIXED) { why = "unknown precision"; return false; }
+  if (o->hartree_method != EFE_HARTREE_FDM && o->hartree_method != EFE_HARTREE_PCG) {
+    why = "unknown Hartree method";
+    return false;
+  }
   return true;
 }
 
@@ -209,6 +218,7 @@ static efe_status setup_impl(Ctx& c, const efe_mesh_desc* mesh, const efe_atom* 
   c.cg_tol = o->cg_tol > 0 ? o->cg_tol : 1e-12;
   c.cg_max_it = o->cg_max_it > 0 ? o->cg_max_it : 2000;
   c.precision = o->precision;
+  c.hartree_method = o->hartree_method;
 
   // reference tables
   double xi[kMaxP1], wl[kMaxP1], xg[kMaxNQ1], wg[kMaxNQ1];
@@ -276,6 +286,9 @@ static efe_status setup_impl(Ctx& c, const efe_mesh_desc* mesh, const efe_atom* 
         }
     TRY_CUDA(c, dalloc(c.d_Dsc, Dsc.size()), "allocating D");
     TRY_CUDA(c, cudaMemcpy(c.d_Dsc, Dsc.data(), sizeof(double) * Dsc.size(), cudaMemcpyHostToDevice), "copy");
+    std::vector<float> D32(Dsc.begin(), Dsc.end());
+    TRY_CUDA(c, dalloc(c.d_Dsc32, D32.size()), "allocating D");
+    TRY_CUDA(c, cudaMemcpy(c.d_Dsc32, D32.data(), sizeof(float) * D32.size(), cudaMemcpyHostToDevice), "copy");
   }
   TRY_CUDA(c, dalloc(c.d_occ, c.occ.size()), "allocating occupations");
   TRY_CUDA(c, cudaMemcpy(c.d_occ, c.occ.data(), sizeof(double) * c.occ.size(), cudaMemcpyHostToDevice), "copy");
@@ -383,6 +396,24 @@ static efe_status setup_impl(Ctx& c, const efe_mesh_desc* mesh, const efe_atom* 
   TRY_CUDA(c, dalloc(c.d_diagA, (size_t)c.n_h), "allocating Poisson data");
   TRY_CUDA(c, dalloc(c.d_phiB, (size_t)c.n_h), "allocating Poisson data");
   TRY_CUDA(c, launch_poisson_setup(c, s), "Poisson set-up");
+  if (c.batch == 1) {
+    c.d_phiB_nb = c.d_phiB;
+  } else {
+    TRY_CUDA(c, dalloc(c.d_phiB_nb, (size_t)c.n_h * c.batch), "allocating Dirichlet data");
+    std::vector<double> hb((size_t)c.n_h), hbn((size_t)c.n_h * c.batch);
+    TRY_CUDA(c, cudaMemcpy(hb.data(), c.d_phiB, sizeof(double) * c.n_h, cudaMemcpyDeviceToHost), "copy");
+    for (long long g = 0; g < c.n_h; ++g)
+      for (int m = 0; m < c.batch; ++m) hbn[(size_t)g * c.batch + m] = hb[(size_t)g];
+    TRY_CUDA(c, cudaMemcpy(c.d_phiB_nb, hbn.data(), sizeof(double) * hbn.size(), cudaMemcpyHostToDevice), "copy");
+  }
+  {
+    cudaError_t e = setup_fdm(c);
+    if (e == cudaErrorInvalidValue) {
+      c.err = "fast-diagonalisation set-up failed (1D mass matrix not positive definite)";
+      return EFE_ERR_NOT_SPD;
+    }
+    TRY_CUDA(c, e, "fast-diagonalisation set-up");
+  }
   TRY_CUDA(c, dalloc(c.d_red, (size_t)std::max(64, 3 * c.batch + 64)), "allocating scratch");
   TRY_CUDA(c, cudaMallocHost((void**)&c.h_flag, sizeof(int) * 4), "allocating pinned flag");
   efe_status st = ensure_batch_buffers(c);
@@ -616,7 +647,7 @@ efe_status efe_kick(efe_ctx* ctx, double* psi_bar_dev, const efe_field* fields_h
   if (st != EFE_OK) return st;
   int k = 0, cap = 0;
   double e = 0.0;
-  TRY_CUDA(c, run_kexp_cols(c, psi_bar_dev, psi_bar_dev, dts.data(), c.precision, &k, &cap, &e, s), "kick");
+  TRY_CUDA(c, run_kexp_cols(c, psi_bar_dev, psi_bar_dev, dts.data(), EFE_FP64, &k, &cap, &e, s), "kick");
   c.state_valid = false;
   c.op.valid = false;
   return cap > 0 ? EFE_WARN_KRYLOV_CAP : EFE_OK;
@@ -647,6 +678,18 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
   dfree(dc); dfree(de); dfree(dk); dfree(dn);
   if (e != cudaSuccess) return cuda_fail(c, e, "initial orbitals");
   c.state_valid = false;
+  return EFE_OK;
+}
+
+efe_status efe_selftest(int64_t n, int64_t* mismatches_host) {
+  if (n < 0 || !mismatches_host) return EFE_ERR_ARG;
+  long long m = 0;
+  cudaError_t e = run_selftest_cvt(n, &m);
+  if (e != cudaSuccess) {
+    g_setup_err = std::string("self-test: ") + cudaGetErrorString(e);
+    return EFE_ERR_CUDA;
+  }
+  *mismatches_host = m;
   return EFE_OK;
 }
 

@@ -13,7 +13,7 @@ namespace efe {
 
 constexpr int kMaxP1 = 6;    // degree <= 5
 constexpr int kMaxNQ1 = 7;   // n_quad = p + 2
-constexpr int kMaxK = 32;    // Lanczos cap
+constexpr int kMaxK = 64;    // Lanczos cap
 constexpr int kThreads = 256;
 
 // 1D reference tables on [-1, 1], passed to kernels by value (parameter space is
@@ -99,9 +99,11 @@ struct Ctx {
   double cg_tol = 1e-12;
   int cg_max_it = 2000;
   int precision = EFE_FP64;
+  int hartree_method = EFE_HARTREE_FDM;
   // device tables
   double* d_geo = nullptr;     // x0 (ncx+ncy+ncz) then h (ncx+ncy+ncz)
   double* d_Dsc = nullptr;     // [n_h] mask / sqrt(M)
+  float* d_Dsc32 = nullptr;    // float copy for the mixed apply
   double* d_M = nullptr;       // [n_h] lumped mass
   double* d_occ = nullptr;     // [n_orb]
   double* d_vN = nullptr;      // [nc][nq]
@@ -123,6 +125,11 @@ struct Ctx {
   double* d_diagA = nullptr;   // [n_h] diagonal of (1/4pi) K at interior nodes (1 elsewhere)
   double* d_phiB = nullptr;    // [n_h] Dirichlet data (zero inside)
   double* d_phi = nullptr;     // [n_h][batch] warm start / last solution
+  double* d_phiB_nb = nullptr; // [n_h][batch] Dirichlet data per member
+  int fdm_n[3] = {0, 0, 0};    // interior 1D sizes
+  double* d_fdmV[3] = {nullptr, nullptr, nullptr};   // 1D generalised eigenvectors
+  double* d_fdmL[3] = {nullptr, nullptr, nullptr};   // 1D eigenvalues
+  double* d_fdmT = nullptr;    // [2][batch][nx ny nz] transform scratch
   // operators
   Operator op;                 // current operator (efe_set_potential / magnus)
   // state (density-derived potentials of the current step)
@@ -135,6 +142,7 @@ struct Ctx {
   double* d_Q = nullptr;       // [(k_max + 1)][n_dof][cols] complex
   double* d_psi_p = nullptr;   // [n_dof][cols] complex
   double* d_xE = nullptr;      // [nE][2 cols] S x^E
+  float* d_xE32 = nullptr;     // float copy
   double* d_yE = nullptr;      // [nE][2 cols] enriched accumulator
   double* d_lz = nullptr;      // Lanczos scalars per column (see k_vector.cu)
   int* d_lzi = nullptr;        // Lanczos integer state per column
@@ -153,6 +161,8 @@ long long launch_count();
 void reset_launch_count();
 // returns (start, stop) events to bracket one cell-apply launch, or nulls when timing is off
 void prof_pair(Ctx& c, cudaEvent_t& a, cudaEvent_t& b);
+
+cudaError_t run_selftest_cvt(long long n, long long* mismatches);
 
 // ---- host math (host_math.cu)
 void gauss_legendre(int n, double* x, double* w);
@@ -192,7 +202,10 @@ cudaError_t launch_load_vector(const Ctx& c, const double* f, double* d, int nb,
 cudaError_t launch_interp(const Ctx& c, const double* x, double* out, int nb, cudaStream_t s);
 cudaError_t launch_axpby(double* y, const double* a, const double* b, double ca, double cb, long long n,
                          cudaStream_t s);
-// Hartree PCG; iters returned (synchronises)
+// fast-diagonalisation Hartree solve (k_poisson.cu)
+cudaError_t setup_fdm(Ctx& c);
+cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, cudaStream_t s);
+// Hartree solve (direct or PCG); iters returned (synchronises for PCG)
 efe_status run_hartree(Ctx& c, const double* rho, double* vH, double tol, int max_it, int* iters, cudaStream_t s);
 
 }  // namespace efe

@@ -41,14 +41,16 @@ constexpr size_t tile_smem() {
 template <typename T, int P1, int NQ1, bool ENR>
 __global__ void __launch_bounds__(kThreads)
 k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ X,
-             double* __restrict__ Y, long long ld2, int cols_member, const double* __restrict__ Dsc,
+             double* __restrict__ Y, long long ld2, int cols_member, const T* __restrict__ Dsc,
              const T* __restrict__ W, double kin, const int* __restrict__ pair_start,
              const int* __restrict__ pair_fn, const T* __restrict__ E, long long n_pairs,
-             const double* __restrict__ xE, double* __restrict__ yE) {
+             const T* __restrict__ xE, double* __restrict__ yE) {
   constexpr int RT = tile_rt<T, NQ1>();
   constexpr int S3 = NQ1 * NQ1 * NQ1;
   constexpr int NN = P1 * P1 * P1;
   constexpr int NQ = S3;
+  // coupling rows staged per chunk: kc * NN entries of E_c in C and kc * RT of x^E in D
+  constexpr int KCAP = (S3 * RT) / NN < S3 ? (S3 * RT) / NN : S3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   T* B = A + S3 * RT;
@@ -62,8 +64,8 @@ k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const d
   const int member = blockIdx.y;
   int cx, cy, cz;
   cell_ijk(mesh, c, cx, cy, cz);
-  const double hx = mesh.h[cx], hy = mesh.h[mesh.ncx + cy], hz = mesh.h[mesh.ncx + mesh.ncy + cz];
   if (threadIdx.x < RT) {
+    const double hx = mesh.h[cx], hy = mesh.h[mesh.ncx + cy], hz = mesh.h[mesh.ncx + mesh.ncy + cz];
     ax[threadIdx.x] = (T)(kin * hy * hz / (4.0 * hx));
     ay[threadIdx.x] = (T)(kin * hx * hz / (4.0 * hy));
     az[threadIdx.x] = (T)(kin * hx * hy / (4.0 * hz));
@@ -86,8 +88,8 @@ k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const d
       const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
       const long long g = node_index(mesh, cx, cy, cz, i1, i2, i3);
       T v = T(0);
-      if (cbase + r < cols_member) v = (T)(Dsc[g] * X[g * ld2 + col0 + cbase + r]);
-      A[l * RT + r] = v;
+      if (cbase + r < cols_member) v = from_f64<T>(X[g * ld2 + col0 + cbase + r]) * Dsc[g];
+      A[it] = v;
     }
     __syncthreads();
     // kinetic part into B
@@ -98,23 +100,32 @@ k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const d
     __syncthreads();
     interp_bwd<T, P1, NQ1, RT, true>(tab, C, B, D, C);
     if (ENR && np > 0) {
-      // y^C += E_c x^E  and  y^E += E_c^T x^C
-      for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
-        const int r = it % RT, l = it / RT;
-        if (cbase + r >= cols_member) continue;
-        T acc = T(0);
-        for (int k = 0; k < np; ++k) acc = fma(Ec[(long long)k * NN + l], (T)xE[(long long)pair_fn[p0 + k] * ld2 + col0 + cbase + r], acc);
-        B[l * RT + r] += acc;
+      // y^C += E_c x^E  and  y^E += E_c^T x^C, with E_c rows and x^E staged in C and D
+      for (int k0 = 0; k0 < np; k0 += KCAP) {
+        const int kc = np - k0 < KCAP ? np - k0 : KCAP;
+        for (int i = threadIdx.x; i < kc * NN; i += blockDim.x) C[i] = Ec[(long long)k0 * NN + i];
+        for (int i = threadIdx.x; i < kc * RT; i += blockDim.x) {
+          const int r = i % RT, k = i / RT;
+          D[i] = (cbase + r < cols_member) ? xE[(long long)pair_fn[p0 + k0 + k] * ld2 + col0 + cbase + r] : T(0);
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
+          const int r = it % RT, l = it / RT;
+          T acc = T(0);
+          for (int k = 0; k < kc; ++k) acc = fma(C[k * NN + l], D[k * RT + r], acc);
+          B[it] += acc;
+        }
+        for (int it = threadIdx.x; it < kc * RT; it += blockDim.x) {
+          const int r = it % RT, k = it / RT;
+          if (cbase + r >= cols_member) continue;
+          const T* e = C + k * NN;
+          T acc = T(0);
+#pragma unroll 5
+          for (int l = 0; l < NN; ++l) acc = fma(e[l], A[l * RT + r], acc);
+          atomicAdd(&yE[(long long)pair_fn[p0 + k0 + k] * ld2 + col0 + cbase + r], to_f64<T>(acc));
+        }
+        __syncthreads();
       }
-      for (int it = threadIdx.x; it < np * RT; it += blockDim.x) {
-        const int r = it % RT, k = it / RT;
-        if (cbase + r >= cols_member) continue;
-        const T* e = Ec + (long long)k * NN;
-        T acc = T(0);
-        for (int l = 0; l < NN; ++l) acc = fma(e[l], A[l * RT + r], acc);
-        atomicAdd(&yE[(long long)pair_fn[p0 + k] * ld2 + col0 + cbase + r], (double)acc);
-      }
-      __syncthreads();
     }
     // scatter-add y_bar^C += D y^C
     for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
@@ -122,22 +133,23 @@ k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const d
       if (cbase + r >= cols_member) continue;
       const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
       const long long g = node_index(mesh, cx, cy, cz, i1, i2, i3);
-      const double d = Dsc[g];
-      if (d != 0.0) atomicAdd(&Y[g * ld2 + col0 + cbase + r], d * (double)B[l * RT + r]);
+      const T d = Dsc[g];
+      if (d != T(0)) atomicAdd(&Y[g * ld2 + col0 + cbase + r], to_f64<T>(d * B[it]));
     }
     __syncthreads();
   }
 }
 
-// xE[nu][col] = sum_mu S[nu][mu] X[n_h + mu][col]
+// xE[nu][col] = sum_mu S[nu][mu] X[n_h + mu][col]  (and a float copy)
 __global__ void k_enr_pre(const double* __restrict__ S, const double* __restrict__ X, long long n_h, long long ld2,
-                          int ncols2, int nE, double* __restrict__ xE) {
+                          int ncols2, int nE, double* __restrict__ xE, float* __restrict__ xE32) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)nE * ncols2) return;
   int nu = idx / ncols2, col = idx % ncols2;
   double acc = 0.0;
   for (int mu = 0; mu < nE; ++mu) acc += S[nu * nE + mu] * X[(n_h + mu) * ld2 + col];
   xE[nu * ld2 + col] = acc;
+  xE32[nu * ld2 + col] = (float)acc;
 }
 
 // yE[mu][col] += sum_k HEE[member][mu][k] xE[k][col]
@@ -377,8 +389,51 @@ k_interp(const __grid_constant__ RefTables tab, const MeshView mesh, const doubl
 }
 
 // ----------------------------------------------------------------------------
+// self-test of the integer-pipe conversions against the hardware ones, on
+// seeded bit patterns: doubles in the binary32 normal range (a quarter of them
+// exact round-to-nearest ties) and binary32 normal floats.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_selftest_cvt(long long n, unsigned long long* __restrict__ bad) {
+  unsigned long long local = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long h = splitmix64((unsigned long long)i);
+    const unsigned long long sign = (h >> 63) << 63;
+    const unsigned long long e = 897ull + (h >> 40) % 253ull;            // binary32 exponents 1..253
+    unsigned long long mant = splitmix64(h) & 0xFFFFFFFFFFFFFull;
+    if ((i & 3) == 0) mant = (mant & ~0x1FFFFFFFull) | 0x10000000ull;    // exact tie
+    const double x = __longlong_as_double((long long)(sign | (e << 52) | mant));
+    if (__float_as_uint(f64_to_f32_rn(x)) != __float_as_uint(__double2float_rn(x))) ++local;
+    const unsigned fb = (unsigned)(h & 0x807FFFFFu) | ((unsigned)(1u + (h >> 32) % 254u) << 23);
+    const float f = __uint_as_float(fb);
+    if (__double_as_longlong(f32_to_f64(f)) != __double_as_longlong((double)f)) ++local;
+  }
+  if (local) atomicAdd(bad, local);
+}
+
+// ----------------------------------------------------------------------------
 // host wrappers
 // ----------------------------------------------------------------------------
+cudaError_t run_selftest_cvt(long long n, long long* mismatches) {
+  unsigned long long* d = nullptr;
+  EFE_CUDA_TRY(cudaMalloc(&d, sizeof(unsigned long long)));
+  EFE_CUDA_TRY(cudaMemset(d, 0, sizeof(unsigned long long)));
+  k_selftest_cvt<<<1216, 256>>>(n, d);
+  note_launch();
+  EFE_CUDA_TRY(cudaGetLastError());
+  unsigned long long h = 0;
+  EFE_CUDA_TRY(cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost));
+  cudaFree(d);
+  *mismatches = (long long)h;
+  return cudaSuccess;
+}
+
 template <typename F>
 static cudaError_t set_smem(F f, size_t bytes) {
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -394,12 +449,15 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
   if (c.nE > 0) {
     EFE_CUDA_TRY(cudaMemsetAsync(c.d_yE, 0, sizeof(double) * c.nE * ld2, s));
     long long n = (long long)c.nE * ncols2;
-    k_enr_pre<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, X, c.n_h, ld2, ncols2, c.nE, c.d_xE);
+    k_enr_pre<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, X, c.n_h, ld2, ncols2, c.nE, c.d_xE, c.d_xE32);
     note_launch();
     EFE_CUDA_TRY(cudaGetLastError());
   }
-  const T* W = std::is_same<T, float>::value ? (const T*)c.op.W32 : (const T*)c.op.W64;
-  const T* E = std::is_same<T, float>::value ? (const T*)c.op.E32 : (const T*)c.op.E64;
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const T* W = F32 ? (const T*)c.op.W32 : (const T*)c.op.W64;
+  const T* E = F32 ? (const T*)c.op.E32 : (const T*)c.op.E64;
+  const T* Dt = F32 ? (const T*)c.d_Dsc32 : (const T*)c.d_Dsc;
+  const T* xEt = F32 ? (const T*)c.d_xE32 : (const T*)c.d_xE;
   const size_t sm = tile_smem<T, NQ1>();
   dim3 grid(c.nc, batch);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -408,13 +466,13 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
   if (c.n_pairs > 0) {
     auto f = k_cell_apply<T, P1, NQ1, true>;
     EFE_CUDA_TRY(set_smem(f, sm));
-    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, c.d_Dsc, W, c.op.kin, c.d_pair_start,
-                                 c.d_pair_fn, E, c.n_pairs, c.d_xE, c.d_yE);
+    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, c.d_pair_start,
+                                 c.d_pair_fn, E, c.n_pairs, xEt, c.d_yE);
     note_launch();
   } else {
     auto f = k_cell_apply<T, P1, NQ1, false>;
     EFE_CUDA_TRY(set_smem(f, sm));
-    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, c.d_Dsc, W, c.op.kin, nullptr, nullptr,
+    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, nullptr, nullptr,
                                  nullptr, 0, nullptr, nullptr);
     note_launch();
   }

@@ -153,79 +153,157 @@ __global__ void k_lz_update(double* __restrict__ W, const double* __restrict__ Q
   block_col_reduce(acc, f.col, f.ok, C, sred, out);
 }
 
-// Symmetric eigendecomposition of the small tridiagonal T by cyclic Jacobi,
-// then y = exp(-i dt T) e_1 and the error estimate; one thread per column.
+// y = exp(-i dt T) e_1 for the real symmetric tridiagonal T_j of one column
+// and the error estimate of Eq. AdaptiveKrylovErr, one warp per column.
+// The exponential is the Chebyshev (Jacobi-Anger) series on the Gershgorin
+// interval [c - e, c + e] of T:
+//   exp(-i dt T) = exp(-i dt c) [J_0(z) + 2 sum_k (-i)^k J_k(z) T_k((T - c)/e)],  z = dt e,
+// with the Bessel values J_k(z) from Miller's backward recurrence (normalised
+// by J_0 + 2 sum J_2k = 1) and T_k(.) e_1 from the three-term recurrence, so a
+// step costs O(K m) with K ~ 1.3 z + 40 terms (truncation below 1e-17).
 __global__ void k_lz_tri(LzView v, int C, int j, int k_max, int fixed_k, double tol) {
   extern __shared__ double tri_sh[];
   const int col = blockIdx.x;
-  if (threadIdx.x != 0 || col >= C) return;
+  const int lane = threadIdx.x;   // 32 lanes
+  if (col >= C) return;
   if (!v.active[col]) return;
-  const double a_j = v.red[col];
-  const double b_j = sqrt(v.red2[col]);
-  v.alpha[(long long)j * C + col] = a_j;
-  v.beta[(long long)j * C + col] = b_j;
   const int m = j + 1;
-  double* A = tri_sh;
-  double* V = tri_sh + m * m;
-  for (int r = 0; r < m; ++r)
-    for (int s = 0; s < m; ++s) {
-      A[r * m + s] = 0.0;
-      V[r * m + s] = (r == s) ? 1.0 : 0.0;
-    }
-  for (int r = 0; r < m; ++r) A[r * m + r] = v.alpha[(long long)r * C + col];
-  for (int r = 0; r + 1 < m; ++r) {
-    const double b = v.beta[(long long)r * C + col];
-    A[r * m + r + 1] = b;
-    A[(r + 1) * m + r] = b;
+  double* al = tri_sh;            // [kMaxK]
+  double* be = al + kMaxK;        // [kMaxK]
+  double* u0 = be + kMaxK;        // [kMaxK + 2] T_{k-1} e1 (padded)
+  double* u1 = u0 + kMaxK + 2;    // [kMaxK + 2] T_k e1
+  double* jb = u1 + kMaxK + 2;    // Bessel values, [kMaxBessel]
+  constexpr int kMaxBessel = 1200;
+  __shared__ double sc[4];        // c, e, z
+  __shared__ int sK;
+  if (lane == 0) {
+    v.alpha[(long long)j * C + col] = v.red[col];
+    v.beta[(long long)j * C + col] = sqrt(v.red2[col]);
   }
-  double total = 0.0;
-  for (int r = 0; r < m * m; ++r) total += A[r] * A[r];
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0;
-    for (int p = 0; p < m; ++p)
-      for (int q = p + 1; q < m; ++q) off += A[p * m + q] * A[p * m + q];
-    if (off <= 1e-34 * total || off == 0.0) break;
-    for (int p = 0; p < m; ++p)
-      for (int q = p + 1; q < m; ++q) {
-        const double apq = A[p * m + q];
-        if (apq == 0.0) continue;
-        const double theta = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
-        for (int k = 0; k < m; ++k) {
-          const double akp = A[k * m + p], akq = A[k * m + q];
-          A[k * m + p] = cs * akp - sn * akq;
-          A[k * m + q] = sn * akp + cs * akq;
-        }
-        for (int k = 0; k < m; ++k) {
-          const double apk = A[p * m + k], aqk = A[q * m + k];
-          A[p * m + k] = cs * apk - sn * aqk;
-          A[q * m + k] = sn * apk + cs * aqk;
-        }
-        for (int k = 0; k < m; ++k) {
-          const double vkp = V[k * m + p], vkq = V[k * m + q];
-          V[k * m + p] = cs * vkp - sn * vkq;
-          V[k * m + q] = sn * vkp + cs * vkq;
+  __syncwarp();
+  for (int r = lane; r < m; r += 32) {
+    al[r] = v.alpha[(long long)r * C + col];
+    be[r] = v.beta[(long long)r * C + col];   // be[m-1] = beta_j (not part of T_m)
+  }
+  __syncwarp();
+  const double dt = v.dt[col];
+  if (lane == 0) {
+    double lo = 1e300, hi = -1e300;
+    for (int r = 0; r < m; ++r) {
+      const double off = (r > 0 ? fabs(be[r - 1]) : 0.0) + (r + 1 < m ? fabs(be[r]) : 0.0);
+      lo = fmin(lo, al[r] - off);
+      hi = fmax(hi, al[r] + off);
+    }
+    const double c = 0.5 * (hi + lo), e = fmax(0.5 * (hi - lo), 1e-300);
+    const double z = fabs(dt) * e;
+    int K = (int)(1.3 * z + 40.0);
+    if (K > kMaxBessel - 40) K = kMaxBessel - 40;
+    // Miller: J_{n-1} = (2n / z) J_n - J_{n+1} from n0 well above K, then normalise
+    if (z < 1e-280) {
+      for (int n = 0; n < K; ++n) jb[n] = (n == 0) ? 1.0 : 0.0;
+    } else {
+      const int n0 = K + 30;
+      double jp1 = 0.0, jn = 1e-300, norm = 0.0;
+      for (int n = n0; n >= 1; --n) {
+        const double jm1 = (2.0 * n / z) * jn - jp1;
+        jp1 = jn;
+        jn = jm1;
+        if (n - 1 < K) jb[n - 1] = jn;
+        if (((n - 1) & 1) == 0) norm += ((n - 1) == 0 ? 1.0 : 2.0) * jn;
+        if (fabs(jn) > 1e250) {   // rescale the running values
+          jp1 *= 1e-250;
+          jn *= 1e-250;
+          norm *= 1e-250;
+          for (int q = n - 1; q < K; ++q) jb[q] *= 1e-250;
         }
       }
-  }
-  const double dt = v.dt[col];
-  double ylast_re = 0.0, ylast_im = 0.0;
-  for (int r = 0; r < m; ++r) {
-    double yr = 0.0, yi = 0.0;
-    for (int k = 0; k < m; ++k) {
-      double sn, cs;
-      sincos(dt * A[k * m + k], &sn, &cs);
-      const double w = V[r * m + k] * V[0 * m + k];
-      yr += w * cs;
-      yi -= w * sn;
+      const double inv = 1.0 / norm;
+      for (int n = 0; n < K; ++n) jb[n] *= inv;
     }
-    v.yre[(long long)r * C + col] = yr;
-    v.yim[(long long)r * C + col] = yi;
-    ylast_re = yr;
-    ylast_im = yi;
+    sc[0] = c;
+    sc[1] = e;
+    sc[2] = z;
+    sK = K;
   }
-  const double eps = fabs(dt) * b_j * v.nrm[col] * sqrt(ylast_re * ylast_re + ylast_im * ylast_im);
+  __syncwarp();
+  const double c = sc[0], e = sc[1];
+  const int K = sK;
+  const double sgn = dt >= 0 ? 1.0 : -1.0;    // exp(-i dt T): for dt < 0 the series of |dt| with conjugated phases
+  // lane-owned components r = lane, lane + 32
+  double yr[2] = {0.0, 0.0}, yi[2] = {0.0, 0.0};
+  for (int t = 0; t < 2; ++t) {
+    const int r = lane + 32 * t;
+    if (r < m) {
+      u0[r + 1] = (r == 0) ? 1.0 : 0.0;
+      u1[r + 1] = 0.0;
+    }
+  }
+  if (lane == 0) { u0[0] = u0[m + 1] = 0.0; u1[0] = u1[m + 1] = 0.0; }
+  __syncwarp();
+  // k = 0 term
+  for (int t = 0; t < 2; ++t) {
+    const int r = lane + 32 * t;
+    if (r < m) yr[t] += jb[0] * u0[r + 1];
+  }
+  // T_1 e1 = ((T - c) / e) e1
+  for (int t = 0; t < 2; ++t) {
+    const int r = lane + 32 * t;
+    if (r < m) {
+      const double bl = r > 0 ? be[r - 1] : 0.0, br = r + 1 < m ? be[r] : 0.0;
+      u1[r + 1] = ((al[r] - c) * u0[r + 1] + bl * u0[r] + br * u0[r + 2]) / e;
+    }
+  }
+  __syncwarp();
+  for (int k = 1; k < K; ++k) {
+    // coefficient 2 (-i)^k J_k (sign of the imaginary unit follows dt)
+    const double cf = 2.0 * jb[k];
+    const int ph = k & 3;   // (-i)^k: 1, -i, -1, i
+    for (int t = 0; t < 2; ++t) {
+      const int r = lane + 32 * t;
+      if (r < m) {
+        const double w = cf * u1[r + 1];
+        if (ph == 0) yr[t] += w;
+        else if (ph == 1) yi[t] -= sgn * w;
+        else if (ph == 2) yr[t] -= w;
+        else yi[t] += sgn * w;
+      }
+    }
+    // next: T_{k+1} = 2 X T_k - T_{k-1}, stored in u0
+    double nx[2] = {0.0, 0.0};
+    for (int t = 0; t < 2; ++t) {
+      const int r = lane + 32 * t;
+      if (r < m) {
+        const double bl = r > 0 ? be[r - 1] : 0.0, br = r + 1 < m ? be[r] : 0.0;
+        nx[t] = 2.0 * ((al[r] - c) * u1[r + 1] + bl * u1[r] + br * u1[r + 2]) / e - u0[r + 1];
+      }
+    }
+    __syncwarp();
+    for (int t = 0; t < 2; ++t) {
+      const int r = lane + 32 * t;
+      if (r < m) {
+        u0[r + 1] = u1[r + 1];
+        u1[r + 1] = nx[t];
+      }
+    }
+    __syncwarp();
+  }
+  // global phase exp(-i dt c)
+  double sp, cp;
+  sincos(dt * c, &sp, &cp);
+  for (int t = 0; t < 2; ++t) {
+    const int r = lane + 32 * t;
+    if (r < m) {
+      const double re = yr[t] * cp + yi[t] * sp;
+      const double im = yi[t] * cp - yr[t] * sp;
+      v.yre[(long long)r * C + col] = re;
+      v.yim[(long long)r * C + col] = im;
+      if (r == m - 1) { u0[0] = re; u1[0] = im; }
+    }
+  }
+  __syncwarp();
+  if (lane != 0) return;
+  const double b_j = be[m - 1];
+  const double eps = fabs(dt) * b_j * v.nrm[col] * sqrt(u0[0] * u0[0] + u1[0] * u1[0]);
   v.eps[col] = eps;
   bool stop = false;
   if (fixed_k > 0) {
@@ -348,8 +426,8 @@ cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h
     k_lz_update<<<rg, 256, rs, s>>>(W, Qj, j > 0 ? c.d_Q + (j - 1) * qstride : nullptr, n, (int)C, v.active, v.red,
                                     j > 0 ? v.beta + (long long)(j - 1) * C : nullptr, v.red2);
     note_launch();
-    k_lz_tri<<<(unsigned)C, 32, sizeof(double) * 2 * (j + 1) * (j + 1), s>>>(v, (int)C, j, c.k_max, c.fixed_k,
-                                                                          c.krylov_tol);
+    k_lz_tri<<<(unsigned)C, 32, sizeof(double) * (4 * kMaxK + 4 + 1200), s>>>(v, (int)C, j, c.k_max, c.fixed_k,
+                                                                            c.krylov_tol);
     note_launch();
     k_lz_scale<<<nblk(n * C), 256, 0, s>>>(W, n, (int)C, v.active, v.invb);
     note_launch();
@@ -745,6 +823,12 @@ efe_status run_hartree(Ctx& c, const double* rho, double* vH, double tol, int ma
   } while (0)
   CK(cudaMemsetAsync(d, 0, sizeof(double) * N, s));
   CK(launch_load_vector(c, rho, d, nb, s));
+  if (c.hartree_method == EFE_HARTREE_FDM) {
+    CK(fdm_solve(c, d, Ap, c.d_phi, nb, s));
+    CK(launch_interp(c, c.d_phi, vH, nb, s));
+    if (iters) *iters = 1;
+    return EFE_OK;
+  }
   k_cg_bc<<<nblk(N), 256, 0, s>>>(c.d_phi, c.d_phiB, c.d_Dsc, n, nb);
   note_launch();
   CK(cudaMemsetAsync(Ap, 0, sizeof(double) * N, s));

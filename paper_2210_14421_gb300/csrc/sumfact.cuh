@@ -4,8 +4,9 @@
 // one cell), the values on a 3D tensor grid laid out [n3][n2][n1][RT] with the
 // slot index fastest.  A 1D matrix Mat[mout][min] is applied along one axis;
 // the three 1D factors of B = B1 (x) B1 (x) B1 (basis at Gauss-Legendre
-// points), of the derivative tables and of the exact 1D stiffness/mass
-// matrices reproduce the cell matrices of Eq. Hmn without forming them.
+// points) and the exact 1D stiffness/mass matrices reproduce the cell
+// matrices of Eq. Hmn without forming them.  All extents are compile-time so
+// the work-item decomposition costs no integer division.
 #pragma once
 
 #include "efe_internal.h"
@@ -27,99 +28,139 @@ template <> struct Tab<float> {
 };
 
 // out[..o..] (=|+=) rs[r] * sum_m Mat[o * MIN + m] * in[..m..]   (TRANS: Mat[m * MOUT + o])
-// Work items are (a, b, r) over the two untouched axes and the slot.
-template <typename T, int MIN, int MOUT, int RT, bool TRANS, bool ACC>
-__device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict__ out, const T* mat, int nA,
-                                         int nB, int sA_in, int sB_in, int sM_in, int sA_out, int sB_out,
-                                         int sM_out, const T* rs) {
-  const int items = nA * nB * RT;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+// Work items are (a, b, r) over the two untouched axes (extents NA, NB) and the slot.
+template <typename T, int MIN, int MOUT, int RT, bool TRANS, bool ACC, int NA, int NB, int SA_IN, int SB_IN,
+          int SM_IN, int SA_OUT, int SB_OUT, int SM_OUT>
+__device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict__ out, const T* mat, const T* rs) {
+  constexpr int ITEMS = NA * NB * RT;
+  for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
     const int r = it % RT;
     const int ab = it / RT;
-    const int a = ab % nA, b = ab / nA;
-    const T* src = in + a * sA_in + b * sB_in + r;
+    const int a = ab % NA, b = ab / NA;
+    const T* src = in + a * SA_IN + b * SB_IN + r;
     T v[MIN];
 #pragma unroll
-    for (int m = 0; m < MIN; ++m) v[m] = src[m * sM_in];
+    for (int m = 0; m < MIN; ++m) v[m] = src[m * SM_IN];
     const T scale = rs ? rs[r] : T(1);
-    T* dst = out + a * sA_out + b * sB_out + r;
+    T* dst = out + a * SA_OUT + b * SB_OUT + r;
 #pragma unroll
     for (int o = 0; o < MOUT; ++o) {
       T acc = T(0);
 #pragma unroll
       for (int m = 0; m < MIN; ++m) acc = fma(TRANS ? mat[m * MOUT + o] : mat[o * MIN + m], v[m], acc);
       if (ACC)
-        dst[o * sM_out] += scale * acc;
+        dst[o * SM_OUT] += scale * acc;
       else
-        dst[o * sM_out] = scale * acc;
+        dst[o * SM_OUT] = scale * acc;
     }
   }
 }
 
 // Apply a 1D operator along axis 1 (fastest), 2 or 3 of a tile with dims
 // (N3, N2, N1) where the contracted axis has extent MIN -> MOUT.
-template <typename T, int MIN, int MOUT, int RT, bool TRANS, bool ACC>
-__device__ __forceinline__ void along1(const T* in, T* out, const T* mat, int N2, int N3, const T* rs = nullptr) {
-  contract<T, MIN, MOUT, RT, TRANS, ACC>(in, out, mat, N2, N3, MIN * RT, N2 * MIN * RT, RT, MOUT * RT,
-                                         N2 * MOUT * RT, RT, rs);
+template <typename T, int MIN, int MOUT, int RT, bool TRANS, bool ACC, int N2, int N3>
+__device__ __forceinline__ void along1(const T* in, T* out, const T* mat, const T* rs = nullptr) {
+  contract<T, MIN, MOUT, RT, TRANS, ACC, N2, N3, MIN * RT, N2 * MIN * RT, RT, MOUT * RT, N2 * MOUT * RT, RT>(in, out,
+                                                                                                          mat, rs);
 }
-template <typename T, int MIN, int MOUT, int RT, bool TRANS, bool ACC>
-__device__ __forceinline__ void along2(const T* in, T* out, const T* mat, int N1, int N3, const T* rs = nullptr) {
-  contract<T, MIN, MOUT, RT, TRANS, ACC>(in, out, mat, N1, N3, RT, MIN * N1 * RT, N1 * RT, RT, MOUT * N1 * RT,
-                                         N1 * RT, rs);
+template <typename T, int MIN, int MOUT, int RT, bool TRANS, bool ACC, int N1, int N3>
+__device__ __forceinline__ void along2(const T* in, T* out, const T* mat, const T* rs = nullptr) {
+  contract<T, MIN, MOUT, RT, TRANS, ACC, N1, N3, RT, MIN * N1 * RT, N1 * RT, RT, MOUT * N1 * RT, N1 * RT>(in, out,
+                                                                                                        mat, rs);
 }
-template <typename T, int MIN, int MOUT, int RT, bool TRANS, bool ACC>
-__device__ __forceinline__ void along3(const T* in, T* out, const T* mat, int N1, int N2, const T* rs = nullptr) {
-  contract<T, MIN, MOUT, RT, TRANS, ACC>(in, out, mat, N1, N2, RT, N1 * RT, N2 * N1 * RT, RT, N1 * RT,
-                                         N2 * N1 * RT, rs);
+template <typename T, int MIN, int MOUT, int RT, bool TRANS, bool ACC, int N1, int N2>
+__device__ __forceinline__ void along3(const T* in, T* out, const T* mat, const T* rs = nullptr) {
+  contract<T, MIN, MOUT, RT, TRANS, ACC, N1, N2, RT, N1 * RT, N2 * N1 * RT, RT, N1 * RT, N2 * N1 * RT>(in, out, mat,
+                                                                                                     rs);
 }
 
 // Kinetic part of a box cell, 1/2 int grad N_I . grad N_J applied to X:
 //   Y = ax K1(x)M1(x)M1 X + ay M1(x)K1(x)M1 X + az M1(x)M1(x)K1 X   (axis order x, y, z)
-// with ax = hy hz / (4 hx) etc. given per slot.  Buffers: X in A, result in B,
-// C and D scratch; all P1^3 * RT.  ACC_OUT adds into B instead of overwriting.
+// with ax = hy hz / (4 hx) etc. given per slot.  X in A, result in B, C and D
+// scratch; all P1^3 * RT.
 template <typename T, int P1, int RT>
 __device__ __forceinline__ void kinetic_tile(const RefTables& tab, const T* A, T* B, T* C, T* D, const T* ax,
                                              const T* ay, const T* az) {
   const T* K1 = Tab<T>::K1(tab);
   const T* M1 = Tab<T>::M1(tab);
-  along3<T, P1, P1, RT, false, false>(A, B, M1, P1, P1);            // B = M_3 X
-  along3<T, P1, P1, RT, false, false>(A, C, K1, P1, P1);            // C = K_3 X
+  along3<T, P1, P1, RT, false, false, P1, P1>(A, B, M1);            // B = M_3 X
+  along3<T, P1, P1, RT, false, false, P1, P1>(A, C, K1);            // C = K_3 X
   __syncthreads();
-  along2<T, P1, P1, RT, false, false>(B, D, K1, P1, P1, ay);        // D = ay K_2 M_3 X
+  along2<T, P1, P1, RT, false, false, P1, P1>(B, D, K1, ay);        // D = ay K_2 M_3 X
   __syncthreads();
-  along2<T, P1, P1, RT, false, true>(C, D, M1, P1, P1, az);         // D += az M_2 K_3 X
+  along2<T, P1, P1, RT, false, true, P1, P1>(C, D, M1, az);         // D += az M_2 K_3 X
   __syncthreads();
-  along2<T, P1, P1, RT, false, false>(B, C, M1, P1, P1);            // C = M_2 M_3 X
+  along2<T, P1, P1, RT, false, false, P1, P1>(B, C, M1);            // C = M_2 M_3 X
   __syncthreads();
-  along1<T, P1, P1, RT, false, false>(D, B, M1, P1, P1);            // B = M_1 D
+  along1<T, P1, P1, RT, false, false, P1, P1>(D, B, M1);            // B = M_1 D
   __syncthreads();
-  along1<T, P1, P1, RT, false, true>(C, B, K1, P1, P1, ax);         // B += ax K_1 M_2 M_3 X
+  along1<T, P1, P1, RT, false, true, P1, P1>(C, B, K1, ax);         // B += ax K_1 M_2 M_3 X
   __syncthreads();
 }
 
-// Values at the Gauss-Legendre points: U = B X (A -> C via D), then optional
-// pointwise weights, then B^T back and accumulated into B.
+// Values at the Gauss-Legendre points: A (P1^3 slots) -> C (NQ1^3), D scratch.
 template <typename T, int P1, int NQ1, int RT>
 __device__ __forceinline__ void interp_fwd(const RefTables& tab, const T* A, T* C, T* D) {
   const T* B1 = Tab<T>::B1(tab);
-  along1<T, P1, NQ1, RT, false, false>(A, C, B1, P1, P1);           // (P1, P1, NQ1)
+  along1<T, P1, NQ1, RT, false, false, P1, P1>(A, C, B1);           // (P1, P1, NQ1)
   __syncthreads();
-  along2<T, P1, NQ1, RT, false, false>(C, D, B1, NQ1, P1);          // (P1, NQ1, NQ1)
+  along2<T, P1, NQ1, RT, false, false, NQ1, P1>(C, D, B1);          // (P1, NQ1, NQ1)
   __syncthreads();
-  along3<T, P1, NQ1, RT, false, false>(D, C, B1, NQ1, NQ1);         // (NQ1, NQ1, NQ1)
+  along3<T, P1, NQ1, RT, false, false, NQ1, NQ1>(D, C, B1);         // (NQ1, NQ1, NQ1)
   __syncthreads();
 }
 
+// Projection back: C (NQ1^3) -> B (P1^3), added when ACC; D and E scratch
+// (E may alias C).
 template <typename T, int P1, int NQ1, int RT, bool ACC>
 __device__ __forceinline__ void interp_bwd(const RefTables& tab, const T* C, T* B, T* D, T* E) {
   const T* B1 = Tab<T>::B1(tab);
-  along3<T, NQ1, P1, RT, true, false>(C, D, B1, NQ1, NQ1);          // (P1, NQ1, NQ1)
+  along3<T, NQ1, P1, RT, true, false, NQ1, NQ1>(C, D, B1);          // (P1, NQ1, NQ1)
   __syncthreads();
-  along2<T, NQ1, P1, RT, true, false>(D, E, B1, NQ1, P1);           // (P1, P1, NQ1)
+  along2<T, NQ1, P1, RT, true, false, NQ1, P1>(D, E, B1);           // (P1, P1, NQ1)
   __syncthreads();
-  along1<T, NQ1, P1, RT, true, ACC>(E, B, B1, P1, P1);              // (P1, P1, P1)
+  along1<T, NQ1, P1, RT, true, ACC, P1, P1>(E, B, B1);              // (P1, P1, P1)
   __syncthreads();
 }
+
+// IEEE-754 conversions between binary64 and binary32 on the integer pipes
+// (the FP64 unit of this GPU issues two operations per clock per SM, so the
+// hardware conversions would bind the float32 kernels).  Both follow the bit
+// layouts of the formats: f64_to_f32_rn rounds to nearest even, flushes
+// results below the smallest normal float to signed zero and saturates to
+// infinity; f32_to_f64 is exact for normal floats and maps subnormal floats to
+// signed zero.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu) - 896;          // binary32 biased exponent
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);   // top 23 mantissa bits
+  const unsigned rest = lo & 0x1FFFFFFFu;                   // 29 dropped bits
+  unsigned r = ((unsigned)e << 23) + m;
+  r += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  r = e <= 0 ? 0u : r;
+  r = (e >= 255 || r >= 0x7F800000u) ? 0x7F800000u : r;
+  return __uint_as_float(sign | r);
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned m = u & 0x7FFFFFu;
+  unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+  unsigned lo = m << 29;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  if (e == 255u) hi = sign | 0x7FF00000u | (m >> 3);
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
+template <typename T> __device__ __forceinline__ T from_f64(double x);
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return f64_to_f32_rn(x); }
+template <typename T> __device__ __forceinline__ double to_f64(T x);
+template <> __device__ __forceinline__ double to_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ double to_f64<float>(float x) { return f32_to_f64(x); }
 
 }  // namespace efe

@@ -48,6 +48,6 @@ def test_setup_rejects_bad_arguments_without_gpu_work():
     assert st == B.EFE_ERR_ARG
     assert b"degree" in lib.efe_last_error(None)
     mesh = B.MeshDesc(2, 2, 2, B._dptr(xb), B._dptr(xb), B._dptr(xb), 4, 6)
-    opts = B.Options(1, 1, B._dptr(occ), 1e-8, 99, 0, 1e-10, 100, 0)                # k_max too large
+    opts = B.Options(1, 1, B._dptr(occ), 1e-8, 99, 0, 1e-10, 100, 0, 0)                # k_max too large
     st = lib.efe_setup(ctypes.byref(mesh), None, 0, None, ctypes.byref(opts), ctypes.byref(h))
     assert st == B.EFE_ERR_ARG

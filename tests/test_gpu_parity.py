@@ -62,6 +62,11 @@ def test_geometry_and_initial_state(name):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
+def test_integer_pipe_conversions_match_hardware():
+    from paper_2210_14421_gb300 import _binding
+    assert _binding.selftest(1 << 24) == 0
+
+
 def _rounding_bound(H, X):
     return abs(H) @ np.abs(X)
 
@@ -115,12 +120,15 @@ def test_apply_H_batched_potentials():
     assert np.all(np.abs(Yd.cpu().numpy() - ref) <= 1e-12 * bound + 1e-300)
 
 
-@pytest.mark.parametrize("name", ["h2", "small2_p3", "small1_p2_11orb"])
-def test_density_lda_hartree_dipole(name):
+@pytest.mark.parametrize("name,method", [("h2", 0), ("small2_p3", 0), ("small1_p2_11orb", 0), ("h2", 1),
+                                         ("small2_p3", 1)])
+def test_density_lda_hartree_dipole(name, method):
+    """Density, LDA, Hartree (method 0: fast diagonalisation, 1: Jacobi PCG)
+    and dipole against the oracle's definitions (Hartree: sparse LU)."""
     wl = WORKLOADS[name]()
     S = _sys(wl)
     from oracle import poisson, tdks, xc
-    ctx = _ctx(wl, cg_tol=1e-14)
+    ctx = _ctx(wl, cg_tol=1e-14, hartree_method=method)
     psi0 = S.initial_orbitals()
     psi = _to_dev(psi0)
     rho = torch.empty((1, S.mesh.n_cells, S.mesh.nq), dtype=torch.float64, device="cuda")
@@ -184,6 +192,24 @@ def test_magnus_steps_fixed_k_match_oracle(name):
     got_psi, got_mu, _ = _gpu_run(wl, psi0, 3, fixed_k=8, tol=1e-14, kmax=8)
     assert np.linalg.norm(got_psi - ref_psi) <= 1e-10 * np.linalg.norm(ref_psi)
     assert np.max(np.abs(got_mu - ref_mu)) <= 1e-10 * max(np.max(np.abs(ref_mu)), 1e-3)
+
+
+def test_hartree_batched_members():
+    """Two densities solved in one call (both Hartree methods) against the
+    oracle member by member."""
+    wl = W.small_cluster(n_atoms=2, cells_per_axis=4, degree=3, n_quad=5, n_orb=2, batch=2)
+    S = _sys(wl)
+    from oracle import poisson, tdks
+    psi0 = S.initial_orbitals()
+    rho0 = tdks.density(S, psi0, wl.occ, 1)[0]
+    rho = np.stack([rho0, 0.5 * rho0 + 0.01 * np.exp(-np.sum(S.mesh.xq ** 2, axis=2))])
+    for method in (0, 1):
+        ctx = _ctx(wl, hartree_method=method)
+        vH = torch.empty((2, S.mesh.n_cells, S.mesh.nq), dtype=torch.float64, device="cuda")
+        ctx.hartree(_to_dev(rho), vH, tol=1e-14, max_it=20000)
+        for m in range(2):
+            ref = poisson.solve(S, rho[m])[1]
+            assert np.max(np.abs(vH.cpu().numpy()[m] - ref)) <= 1e-10 * np.max(np.abs(ref))
 
 
 def test_magnus_adaptive_k_and_batch():
