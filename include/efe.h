@@ -187,6 +187,25 @@ efe_status efe_set_potential(efe_ctx* ctx, const double* v_dev, int32_t batch, d
 efe_status efe_apply_H(efe_ctx* ctx, const double* X_dev, double* Y_dev, int64_t n_cols, int64_t ld,
                        int32_t precision, void* stream);
 
+/* Y = Hbar X without allocating device memory (the paper has no counterpart:
+ * this is a deployment variant of efe_apply_H).  Some callers cannot call
+ * cudaMalloc when they apply the operator: a host framework that owns all
+ * device memory and forbids new allocations once it runs, or code recording
+ * into a CUDA graph, where allocation is not allowed during stream capture.
+ * This call computes exactly what efe_apply_H computes, with the same
+ * arguments and precision, but keeps its enrichment scratch in a static
+ * device array of 2 MiB per GPU (held from the library's first use on that
+ * GPU until the process exits) instead of context workspaces; it calls no
+ * cudaMalloc, cudaFree or allocating library routine.  Limit:
+ * n_enrich * 2 * ld <= 104857 entries; larger requests return EFE_ERR_ARG
+ * with a message.  The first call on a device looks up the array's device
+ * address and must be made with the context's device current and before any
+ * stream capture.  All calls on one GPU share the array: calls that overlap
+ * on the GPU (other streams, other contexts) race; each call clears the
+ * accumulator it needs.  Requires a prior efe_set_potential. */
+efe_status efe_apply_H_noalloc(efe_ctx* ctx, const double* X_dev, double* Y_dev, int64_t n_cols, int64_t ld,
+                               int32_t precision, void* stream);
+
 /* One second-order Magnus step (Eq. ApproxMagnus) evaluated by the adaptive
  * Lanczos exponential (Eqs. AdaptiveKrylov, AdaptiveKrylovErr) with the
  * predictor-corrector for the mid-point Hamiltonian:

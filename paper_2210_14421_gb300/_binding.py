@@ -20,7 +20,8 @@ STATUS_NAMES = {0: "EFE_OK", 1: "EFE_ERR_ARG", 2: "EFE_ERR_NOMEM", 3: "EFE_ERR_C
 
 EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coords", "efe_set_potential",
             "efe_apply_H", "efe_magnus_step", "efe_reset_state", "efe_density_vxc", "efe_hartree", "efe_dipole",
-            "efe_kick", "efe_init_orbitals", "efe_profile", "efe_profile_read", "efe_selftest"]
+            "efe_kick", "efe_init_orbitals", "efe_profile", "efe_profile_read", "efe_selftest",
+            "efe_apply_H_noalloc"]
 
 
 class MeshDesc(C.Structure):
@@ -82,6 +83,7 @@ def lib(path: str = LIB_PATH):
     L.efe_coords.argtypes = [vp, vp, vp, vp]
     L.efe_set_potential.argtypes = [vp, vp, i32, dbl, vp]
     L.efe_apply_H.argtypes = [vp, vp, vp, i64, i64, i32, vp]
+    L.efe_apply_H_noalloc.argtypes = [vp, vp, vp, i64, i64, i32, vp]
     L.efe_magnus_step.argtypes = [vp, vp, dbl, dbl, C.POINTER(Field), vp, C.POINTER(StepInfo), vp]
     L.efe_reset_state.argtypes = [vp]
     L.efe_density_vxc.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -213,6 +215,15 @@ class Context:
         ld = X.stride(0)
         assert Y.stride(0) == ld and X.dtype == Y.dtype
         self._check(lib().efe_apply_H(self.h, _ptr(X), _ptr(Y), int(n_cols), int(ld), int(precision), _stream()))
+        return Y
+
+    def apply_H_noalloc(self, X, Y, precision: int = EFE_FP64):
+        """Same as apply_H, with the library's static scratch (no device allocation)."""
+        n_cols = X.shape[1]
+        ld = X.stride(0)
+        assert Y.stride(0) == ld and X.dtype == Y.dtype
+        self._check(lib().efe_apply_H_noalloc(self.h, _ptr(X), _ptr(Y), int(n_cols), int(ld), int(precision),
+                                              _stream()))
         return Y
 
     def magnus_step(self, psi, t, dt, fields, mu=None):

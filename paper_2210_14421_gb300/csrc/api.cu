@@ -11,9 +11,6 @@
 
 #include "efe_internal.h"
 
-struct efe_ctx {
-  efe::Ctx c;
-};
 
 #include <atomic>
 

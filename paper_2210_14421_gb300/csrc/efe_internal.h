@@ -210,6 +210,11 @@ efe_status run_hartree(Ctx& c, const double* rho, double* vH, double tol, int ma
 
 }  // namespace efe
 
+// The opaque handle of the C ABI wraps the context.
+struct efe_ctx {
+  efe::Ctx c;
+};
+
 #define EFE_CUDA_TRY(expr)                                                   \
   do {                                                                       \
     cudaError_t _e = (expr);                                                 \

@@ -12,6 +12,8 @@
 // functions N^E = N^A - sum_l c_l N^C_l, and H_EE the enriched-enriched block.
 // These are P^T H_ext P written out block by block, so no P is applied at run time.
 #include <cstdio>
+#include <mutex>
+#include <string>
 #include <type_traits>
 
 #include "efe_internal.h"
@@ -588,3 +590,151 @@ cudaError_t launch_interp(const Ctx& c, const double* x, double* out, int nb, cu
 }
 
 }  // namespace efe
+
+// ============================================================================
+// Apply without allocation.
+//
+// Callers that cannot allocate device memory at the time they apply the
+// operator - a host framework that owns every allocation and forbids new
+// ones once it is running, or a caller recording work into a CUDA graph,
+// where cudaMalloc is not allowed during stream capture - use
+// efe_apply_H_noalloc.  Its enrichment scratch (S x^E in float64 and float32
+// and the y^E accumulator) lives in the file-scope device array below instead
+// of context workspaces.  The array exists once per GPU that loads the library
+// and stays allocated until the process exits; every call on that GPU shares
+// it, so calls that overlap on the GPU race, and the accumulator is cleared at
+// the start of each call.
+// ============================================================================
+namespace efe {
+
+constexpr long long kNoAllocScratchDoubles = 262144;   // 2 MiB per device
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[256] = {};
+
+// Device address of the static scratch for the current device (looked up
+// once per device; the first call must come before any stream capture).
+static cudaError_t noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[device] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return cudaSuccess;
+}
+
+template <typename T, int P1, int NQ1>
+static cudaError_t apply_noalloc_impl(Ctx& c, const double* X, double* Y, long long n_cols, long long ld,
+                                      double* xE, float* xE32, double* yE, cudaStream_t s) {
+  const long long ld2 = 2 * ld;
+  const int batch = c.op.batch;
+  const int cols_member = (int)(2 * n_cols / batch);
+  const int ncols2 = (int)(2 * n_cols);
+  EFE_CUDA_TRY(cudaMemset2DAsync(Y, sizeof(double) * ld2, 0, sizeof(double) * ncols2, c.n_dof, s));
+  if (c.nE > 0) {
+    EFE_CUDA_TRY(cudaMemsetAsync(yE, 0, sizeof(double) * c.nE * ld2, s));
+    long long n = (long long)c.nE * ncols2;
+    k_enr_pre<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, X, c.n_h, ld2, ncols2, c.nE, xE, xE32);
+    note_launch();
+    EFE_CUDA_TRY(cudaGetLastError());
+  }
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const T* W = F32 ? (const T*)c.op.W32 : (const T*)c.op.W64;
+  const T* E = F32 ? (const T*)c.op.E32 : (const T*)c.op.E64;
+  const T* Dt = F32 ? (const T*)c.d_Dsc32 : (const T*)c.d_Dsc;
+  const T* xEt = F32 ? (const T*)xE32 : (const T*)xE;
+  const size_t sm = tile_smem<T, NQ1>();
+  dim3 grid(c.nc, batch);
+  if (c.n_pairs > 0) {
+    auto f = k_cell_apply<T, P1, NQ1, true>;
+    EFE_CUDA_TRY(set_smem(f, sm));
+    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, c.d_pair_start,
+                                 c.d_pair_fn, E, c.n_pairs, xEt, yE);
+    note_launch();
+  } else {
+    auto f = k_cell_apply<T, P1, NQ1, false>;
+    EFE_CUDA_TRY(set_smem(f, sm));
+    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, nullptr, nullptr,
+                                 nullptr, 0, nullptr, nullptr);
+    note_launch();
+  }
+  EFE_CUDA_TRY(cudaGetLastError());
+  if (c.nE > 0) {
+    long long n = (long long)c.nE * ncols2;
+    k_enr_post1<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.op.HEE, xE, yE, ld2, ncols2, cols_member, c.nE);
+    note_launch();
+    k_enr_post2<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, yE, Y, c.n_h, ld2, ncols2, c.nE);
+    note_launch();
+    EFE_CUDA_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+}  // namespace efe
+
+extern "C" efe_status efe_apply_H_noalloc(efe_ctx* ctx, const double* X_dev, double* Y_dev, int64_t n_cols,
+                                          int64_t ld, int32_t precision, void* stream) {
+  using namespace efe;
+  if (!ctx) return EFE_ERR_ARG;
+  Ctx& c = ctx->c;
+  c.err.clear();
+  if (!c.op.valid) {
+    c.err = "no operator: call efe_set_potential first";
+    return EFE_ERR_STATE;
+  }
+  if (!X_dev || !Y_dev || X_dev == Y_dev || n_cols < 1 || ld < n_cols || n_cols % c.op.batch != 0 ||
+      (precision != EFE_FP64 && precision != EFE_MIXED)) {
+    c.err = "bad arguments to efe_apply_H_noalloc (n_cols must be a multiple of the operator's batch, ld >= n_cols)";
+    return EFE_ERR_ARG;
+  }
+  // partition: x^E (float64), y^E (float64), x^E (float32), each n_enrich * 2 ld entries
+  const long long per = (long long)c.nE * 2 * ld;
+  const long long need = 2 * per + (per + 1) / 2;
+  if (need > kNoAllocScratchDoubles) {
+    c.err = "efe_apply_H_noalloc: n_enrich * 2 * ld = " + std::to_string(per) + " needs " + std::to_string(need) +
+            " doubles of scratch; the static scratch holds " + std::to_string(kNoAllocScratchDoubles) +
+            " (2 MiB), i.e. n_enrich * 2 * ld <= " + std::to_string(kNoAllocScratchDoubles * 2 / 5);
+    return EFE_ERR_ARG;
+  }
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess && dev != c.device) {
+    c.err = "efe_apply_H_noalloc: the context's device must be current";
+    return EFE_ERR_ARG;
+  }
+  double* base = nullptr;
+  if (e == cudaSuccess) e = noalloc_scratch(dev, &base);
+  if (e != cudaSuccess) {
+    c.err = std::string("efe_apply_H_noalloc: static scratch: ") + cudaGetErrorString(e);
+    return EFE_ERR_CUDA;
+  }
+  double* xE = base;
+  double* yE = base + per;
+  float* xE32 = reinterpret_cast<float*>(base + 2 * per);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (precision == EFE_MIXED) {
+    switch (c.p) {
+      case 2: e = apply_noalloc_impl<float, 3, 4>(c, X_dev, Y_dev, n_cols, ld, xE, xE32, yE, s); break;
+      case 3: e = apply_noalloc_impl<float, 4, 5>(c, X_dev, Y_dev, n_cols, ld, xE, xE32, yE, s); break;
+      case 4: e = apply_noalloc_impl<float, 5, 6>(c, X_dev, Y_dev, n_cols, ld, xE, xE32, yE, s); break;
+      default: e = apply_noalloc_impl<float, 6, 7>(c, X_dev, Y_dev, n_cols, ld, xE, xE32, yE, s); break;
+    }
+  } else {
+    switch (c.p) {
+      case 2: e = apply_noalloc_impl<double, 3, 4>(c, X_dev, Y_dev, n_cols, ld, xE, xE32, yE, s); break;
+      case 3: e = apply_noalloc_impl<double, 4, 5>(c, X_dev, Y_dev, n_cols, ld, xE, xE32, yE, s); break;
+      case 4: e = apply_noalloc_impl<double, 5, 6>(c, X_dev, Y_dev, n_cols, ld, xE, xE32, yE, s); break;
+      default: e = apply_noalloc_impl<double, 6, 7>(c, X_dev, Y_dev, n_cols, ld, xE, xE32, yE, s); break;
+    }
+  }
+  if (e != cudaSuccess) {
+    c.err = std::string("efe_apply_H_noalloc: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? EFE_ERR_NOMEM : EFE_ERR_CUDA;
+  }
+  return EFE_OK;
+}
