@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64 steps reported beside the main number")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--graph-steps", type=int, default=3, help="extra steps timed in CUDA-graph mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", type=int, default=31, help="cells per axis (31 = the Na8-like workload)")
     ap.add_argument("--k-max", type=int, default=48,
@@ -418,7 +419,8 @@ def run_efe(args):
             "krylov": {"k_pred": [i["k_pred"] for i in infos], "k_corr": [i["k_corr"] for i in infos],
                        "eps_max": [i["eps_max"] for i in infos], "cap_hits": [i["cap"] for i in infos],
                        "hartree_solves": [i["cg_iters"] for i in infos]},
-            "setup_s": round(t_setup, 2), "initial_state": prep}
+            "setup_s": round(t_setup, 2), "initial_state": prep,
+            "autotune": {"mixed": ctx.tuning(EFE_MIXED), "fp64": ctx.tuning(EFE_FP64)}}
 
     if rank == 0 and args.fp64_steps > 0 and args.precision == "mixed":
         # FP64 side by side from the same kicked state, and the mixed-vs-FP64 dipole error
@@ -468,6 +470,27 @@ def run_efe(args):
                        "h2d_bytes_per_step": int(psi.numel() * 16), "d2h_bytes_per_step": int(mu.numel() * 8)}
 
     ctx.close()
+    # the same steps with each Lanczos exponential replayed as a captured CUDA graph
+    if rank == 0 and args.graph_steps > 0:
+        ctxg = Context(wl, precision=prec, cg_tol=1e-10, cg_max_it=20000, use_graphs=True)
+        psig = psi_start.clone()
+        tg = 0.0
+        for _ in range(2):                       # eager + capture
+            ctxg.magnus_step(psig, tg, wl.dt, wl.fields, mu)
+            tg += wl.dt
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.graph_steps):
+            ctxg.magnus_step_async(psig, tg, wl.dt, arr, mu)
+            tg += wl.dt
+        g1.record(stream)
+        torch.cuda.synchronize()
+        msg = g0.elapsed_time(g1) / args.graph_steps
+        line["graph_mode"] = {"steps_per_s": round(1000.0 / msg, 4), "ms_per_step": round(msg, 2),
+                              "steps": args.graph_steps,
+                              "note": "Lanczos loops captured as CUDA graphs (k_max iterations, no host sync)"}
+        ctxg.close()
     if rank == 0 and not args.no_cpu_baseline:
         k_hint = max([i["k_corr"] for i in infos] or [wl.k_max])
         line["cpu_baseline"] = cpu_baseline(workload(args.cells, 0), k_hint)

@@ -127,6 +127,11 @@ typedef struct {
   int32_t cg_max_it;
   int32_t precision;          /* efe_precision used by efe_magnus_step (efe_kick is always FP64) */
   int32_t hartree_method;     /* EFE_HARTREE_FDM (direct) or EFE_HARTREE_PCG */
+  int32_t use_graphs;         /* 1: each Lanczos exponential of efe_magnus_step runs as a captured
+                                 CUDA graph of k_max iterations (finished columns skipped on the
+                                 device, no host synchronisation; captured on the second call for a
+                                 given buffer set, the first call runs and autotunes eagerly).
+                                 Must be 0 if the caller itself captures efe_magnus_step. */
 } efe_options;
 
 /* Hartree solvers for the same discrete system (Eq. DiscretePoisson):
@@ -269,6 +274,14 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
  * counted since the last efe_profile call, the cell-apply launches timed, and
  * their summed device time in milliseconds (any pointer may be NULL). */
 efe_status efe_profile(efe_ctx* ctx, int32_t enable);
+
+/* Tile-width autotuner of the cell apply (diagnostics and tests).  The first apply
+ * of each precision and column count times variant 0 (widest tile: two blocks per
+ * SM) and variant 1 (half as wide) and keeps the faster.  efe_tuning reports the
+ * choice (-1: not tuned yet) and the timed milliseconds; force_variant 0 or 1
+ * fixes the variant for applies of n_orb * batch columns, -1 leaves it. */
+efe_status efe_tuning(efe_ctx* ctx, int32_t precision, int32_t force_variant, int32_t* variant, float* ms0,
+                      float* ms1);
 
 /* Diagnostics (not part of the method): checks, on the current device, the
  * integer-pipe binary64 <-> binary32 conversions the mixed-precision kernels

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "EFE_OK", 1: "EFE_ERR_ARG", 2: "EFE_ERR_NOMEM", 3: "EFE_ERR_C
 EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coords", "efe_set_potential",
             "efe_apply_H", "efe_magnus_step", "efe_reset_state", "efe_density_vxc", "efe_hartree", "efe_dipole",
             "efe_kick", "efe_init_orbitals", "efe_profile", "efe_profile_read", "efe_selftest",
-            "efe_apply_H_noalloc"]
+            "efe_apply_H_noalloc", "efe_tuning"]
 
 
 class MeshDesc(C.Structure):
@@ -52,7 +52,8 @@ class Field(C.Structure):
 class Options(C.Structure):
     _fields_ = [("n_orb", C.c_int32), ("batch", C.c_int32), ("occ_host", C.POINTER(C.c_double)),
                 ("krylov_tol", C.c_double), ("k_max", C.c_int32), ("fixed_k", C.c_int32), ("cg_tol", C.c_double),
-                ("cg_max_it", C.c_int32), ("precision", C.c_int32), ("hartree_method", C.c_int32)]
+                ("cg_max_it", C.c_int32), ("precision", C.c_int32), ("hartree_method", C.c_int32),
+                ("use_graphs", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -93,6 +94,7 @@ def lib(path: str = LIB_PATH):
     L.efe_init_orbitals.argtypes = [vp, vp, i32, pdbl, pdbl, pdbl, pdbl, vp]
     L.efe_profile.argtypes = [vp, i32]
     L.efe_selftest.argtypes = [i64, C.POINTER(i64)]
+    L.efe_tuning.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.efe_profile_read.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl)]
     for name in EXPORTED:
         if name != "efe_last_error":
@@ -145,7 +147,8 @@ class Context:
     """Owns one efe_ctx built from an `efe_workloads.Workload`."""
 
     def __init__(self, wl, precision: int = EFE_FP64, krylov_tol=None, k_max=None, fixed_k: int = 0,
-                 cg_tol: float = 1e-12, cg_max_it: int = 5000, hartree_method: int = EFE_HARTREE_FDM):
+                 cg_tol: float = 1e-12, cg_max_it: int = 5000, hartree_method: int = EFE_HARTREE_FDM,
+                 use_graphs: bool = False):
         L = lib()
         self.wl = wl
         self._keep = []
@@ -168,7 +171,7 @@ class Context:
         opts = Options(int(wl.n_orb), int(wl.batch), _dptr(occ),
                        float(wl.krylov_tol if krylov_tol is None else krylov_tol),
                        int(wl.k_max if k_max is None else k_max), int(fixed_k), float(cg_tol), int(cg_max_it),
-                       int(precision), int(hartree_method))
+                       int(precision), int(hartree_method), int(bool(use_graphs)))
         h = C.c_void_p()
         st = L.efe_setup(C.byref(mesh), atoms, na, C.byref(enr), C.byref(opts), C.byref(h))
         if st != EFE_OK:
@@ -257,6 +260,11 @@ class Context:
     def kick(self, psi, fields):
         st = lib().efe_kick(self.h, _ptr(psi), fields_array(fields), _stream())
         return self._check(st, allow=(EFE_OK, EFE_WARN_KRYLOV_CAP))
+
+    def tuning(self, precision: int = EFE_MIXED, force_variant: int = -1):
+        v, a, b = C.c_int32(), C.c_float(), C.c_float()
+        self._check(lib().efe_tuning(self.h, int(precision), int(force_variant), C.byref(v), C.byref(a), C.byref(b)))
+        return {"variant": v.value, "ms": [a.value, b.value]}
 
     def profile(self, enable: bool = True):
         self._check(lib().efe_profile(self.h, int(bool(enable))))

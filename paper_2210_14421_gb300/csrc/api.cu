@@ -60,6 +60,10 @@ Ctx::~Ctx() {
   dfree(d_rho); dfree(d_vH); dfree(d_vxc); dfree(d_Q); dfree(d_psi_p); dfree(d_xE); dfree(d_yE);
   dfree(d_lz); dfree(d_lzi); dfree(d_rho2); dfree(d_v); dfree(d_cg); dfree(d_red);
   for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
+  for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+  graphs.clear();
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  cap_stream = nullptr;
   if (h_flag) cudaFreeHost(h_flag);
   h_flag = nullptr;
   if (prev >= 0) cudaSetDevice(prev);
@@ -92,6 +96,7 @@ static efe_status ensure_ws(Ctx& c, long long C, long long ld) {
   const long long need_ld = std::max(C, ld);
   if (c.ws_cols >= need_ld && c.d_Q) return EFE_OK;
   const long long n = c.n_dof;
+  c.ws_gen += 1;   // captured graphs refer to the old buffers
   TRY_CUDA(c, dalloc(c.d_Q, (size_t)(c.k_max + 1) * n * 2 * need_ld), "allocating the Krylov basis");
   TRY_CUDA(c, dalloc(c.d_psi_p, (size_t)n * 2 * need_ld), "allocating the predictor block");
   TRY_CUDA(c, dalloc(c.d_lz, (size_t)(4 * kMaxK + 8) * need_ld), "allocating Lanczos scalars");
@@ -120,6 +125,7 @@ static efe_status ensure_batch_buffers(Ctx& c) {
 static efe_status ensure_operator(Ctx& c, int batch) {
   if (c.op.W64 && c.op.batch == batch) return EFE_OK;
   const size_t nqb = (size_t)batch * c.nc * c.nq;
+  c.ws_gen += 1;
   TRY_CUDA(c, dalloc(c.op.W64, nqb), "allocating the operator");
   TRY_CUDA(c, dalloc(c.op.W32, nqb), "allocating the operator");
   TRY_CUDA(c, dalloc(c.op.E64, (size_t)batch * c.n_pairs * c.nn), "allocating the coupling blocks");
@@ -216,6 +222,7 @@ static efe_status setup_impl(Ctx& c, const efe_mesh_desc* mesh, const efe_atom* 
   c.cg_max_it = o->cg_max_it > 0 ? o->cg_max_it : 2000;
   c.precision = o->precision;
   c.hartree_method = o->hartree_method;
+  c.use_graphs = o->use_graphs != 0;
 
   // reference tables
   double xi[kMaxP1], wl[kMaxP1], xg[kMaxNQ1], wg[kMaxNQ1];
@@ -413,6 +420,7 @@ static efe_status setup_impl(Ctx& c, const efe_mesh_desc* mesh, const efe_atom* 
   }
   TRY_CUDA(c, dalloc(c.d_red, (size_t)std::max(64, 3 * c.batch + 64)), "allocating scratch");
   TRY_CUDA(c, cudaMallocHost((void**)&c.h_flag, sizeof(int) * 4), "allocating pinned flag");
+  TRY_CUDA(c, cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking), "creating the capture stream");
   efe_status st = ensure_batch_buffers(c);
   if (st != EFE_OK) return st;
   TRY_CUDA(c, cudaDeviceSynchronize(), "set-up");
@@ -460,7 +468,8 @@ static efe_status magnus_impl(Ctx& c, double* psi, double t, double dt, const ef
   if (st != EFE_OK) return st;
   int k1 = 0, cap1 = 0, k2 = 0, cap2 = 0;
   double e1 = 0.0, e2 = 0.0;
-  TRY_CUDA(c, run_kexp_cols(c, psi, c.d_psi_p, dts.data(), c.precision, &k1, &cap1, &e1, s), "predictor");
+  const bool stats = info != nullptr;
+  TRY_CUDA(c, run_kexp_cols(c, psi, c.d_psi_p, dts.data(), c.precision, &k1, &cap1, &e1, s, stats), "predictor");
   // S2, S3: rho_mid = (rho_n + rho^p) / 2
   TRY_CUDA(c, launch_density(c, c.d_psi_p, c.d_rho2, s), "density");
   const long long nqb = (long long)c.batch * c.nc * c.nq;
@@ -475,7 +484,7 @@ static efe_status magnus_impl(Ctx& c, double* psi, double t, double dt, const ef
   st = build_op(c, c.d_v, c.batch, 1.0, s);
   if (st != EFE_OK) return st;
   // S5: corrector from psi_n, written in place
-  TRY_CUDA(c, run_kexp_cols(c, psi, psi, dts.data(), c.precision, &k2, &cap2, &e2, s), "corrector");
+  TRY_CUDA(c, run_kexp_cols(c, psi, psi, dts.data(), c.precision, &k2, &cap2, &e2, s, stats), "corrector");
   // S6: state of step n+1 and the dipole
   c.state_valid = false;
   st = compute_state(c, psi, &cg_its, s);
@@ -687,6 +696,24 @@ efe_status efe_selftest(int64_t n, int64_t* mismatches_host) {
     return EFE_ERR_CUDA;
   }
   *mismatches_host = m;
+  return EFE_OK;
+}
+
+efe_status efe_tuning(efe_ctx* ctx, int32_t precision, int32_t force_variant, int32_t* variant, float* ms0,
+                      float* ms1) {
+  CHECK_CTX(ctx);
+  Ctx& c = ctx->c;
+  if (precision != EFE_FP64 && precision != EFE_MIXED) return EFE_ERR_ARG;
+  const int p = precision == EFE_MIXED ? 1 : 0;
+  if (force_variant == 0 || force_variant == 1) {
+    c.tile_choice[p] = force_variant;
+    c.tile_cols[p] = (long long)c.n_orb * c.batch;
+  } else if (force_variant != -1) {
+    return EFE_ERR_ARG;
+  }
+  if (variant) *variant = c.tile_choice[p];
+  if (ms0) *ms0 = c.tile_ms[p][0];
+  if (ms1) *ms1 = c.tile_ms[p][1];
   return EFE_OK;
 }
 

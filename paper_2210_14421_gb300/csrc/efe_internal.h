@@ -132,6 +132,27 @@ struct Ctx {
   double* d_fdmT = nullptr;    // [2][batch][nx ny nz] transform scratch
   // operators
   Operator op;                 // current operator (efe_set_potential / magnus)
+  // autotuned cell-apply tile width per precision [FP64, MIXED]: variant 0 (widest tile
+  // fitting two blocks per SM) or 1 (half as wide); -1 until timed
+  const int* apply_gate = nullptr;   // device count of active Lanczos columns (graph mode), else NULL
+  // CUDA graphs of the Lanczos exponential, keyed by (in, out, precision, columns, kin, generation)
+  struct KexpGraph {
+    const double* in;
+    double* out;
+    int precision;
+    long long C;
+    double kin;
+    long long gen;
+    cudaGraphExec_t exec;
+  };
+  std::vector<KexpGraph> graphs;
+  std::vector<KexpGraph> graph_seen;   // keys run eagerly once (tuning) before capture
+  long long ws_gen = 0;                // bumped whenever workspaces or operator buffers move
+  bool use_graphs = false;
+  cudaStream_t cap_stream = nullptr;
+  int tile_choice[2] = {-1, -1};
+  long long tile_cols[2] = {-1, -1};
+  float tile_ms[2][2] = {{0, 0}, {0, 0}};
   // state (density-derived potentials of the current step)
   bool state_valid = false;
   double* d_rho = nullptr;     // [batch][nc][nq]
@@ -187,7 +208,7 @@ cudaError_t launch_apply(Ctx& c, const double* X, double* Y, long long n_cols, l
 // Lanczos exponential: out = Kexp(-i dt_col Hbar) in for every complex column, with the
 // operator held in Ctx::op; dts_host [n_cols]; host-visible statistics after a stream sync.
 cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* dts_host, int precision,
-                          int* kmax_used, int* cap_hits, double* eps_max, cudaStream_t s);
+                          int* kmax_used, int* cap_hits, double* eps_max, cudaStream_t s, bool need_stats = true);
 
 // density / xc / dipole
 cudaError_t launch_density(Ctx& c, const double* psi, double* rho, cudaStream_t s);

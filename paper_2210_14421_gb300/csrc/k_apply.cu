@@ -31,23 +31,22 @@ constexpr int tile_rt() {
                                                                          : 4;
 }
 
-template <typename T, int NQ1>
+template <typename T, int NQ1, int RT = tile_rt<T, NQ1>()>
 constexpr size_t tile_smem() {
-  return (size_t)4 * NQ1 * NQ1 * NQ1 * tile_rt<T, NQ1>() * sizeof(T) + 3 * 32 * sizeof(T);
+  return (size_t)4 * NQ1 * NQ1 * NQ1 * RT * sizeof(T) + 3 * 32 * sizeof(T);
 }
 
 // ----------------------------------------------------------------------------
 // cell apply: one block per (cell, batch member); the block walks the member's
 // real columns in tiles of RT slots.
 // ----------------------------------------------------------------------------
-template <typename T, int P1, int NQ1, bool ENR>
+template <typename T, int P1, int NQ1, bool ENR, int RT = tile_rt<T, NQ1>()>
 __global__ void __launch_bounds__(kThreads)
 k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ X,
              double* __restrict__ Y, long long ld2, int cols_member, const T* __restrict__ Dsc,
              const T* __restrict__ W, double kin, const int* __restrict__ pair_start,
              const int* __restrict__ pair_fn, const T* __restrict__ E, long long n_pairs,
-             const T* __restrict__ xE, double* __restrict__ yE) {
-  constexpr int RT = tile_rt<T, NQ1>();
+             const T* __restrict__ xE, double* __restrict__ yE, const int* __restrict__ gate = nullptr) {
   constexpr int S3 = NQ1 * NQ1 * NQ1;
   constexpr int NN = P1 * P1 * P1;
   constexpr int NQ = S3;
@@ -62,6 +61,7 @@ k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const d
   T* ay = ax + 32;
   T* az = ay + 32;
 
+  if (gate && *gate == 0) return;   // every Lanczos column has converged (graph-captured loops)
   const int c = blockIdx.x;
   const int member = blockIdx.y;
   int cx, cy, cz;
@@ -460,25 +460,80 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
   const T* E = F32 ? (const T*)c.op.E32 : (const T*)c.op.E64;
   const T* Dt = F32 ? (const T*)c.d_Dsc32 : (const T*)c.d_Dsc;
   const T* xEt = F32 ? (const T*)c.d_xE32 : (const T*)c.d_xE;
-  const size_t sm = tile_smem<T, NQ1>();
   dim3 grid(c.nc, batch);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  prof_pair(c, e0, e1);
-  if (e0) EFE_CUDA_TRY(cudaEventRecord(e0, s));
-  if (c.n_pairs > 0) {
-    auto f = k_cell_apply<T, P1, NQ1, true>;
-    EFE_CUDA_TRY(set_smem(f, sm));
-    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, c.d_pair_start,
-                                 c.d_pair_fn, E, c.n_pairs, xEt, c.d_yE);
+  constexpr int RT0 = tile_rt<T, NQ1>();
+  constexpr int RT1 = RT0 / 2;
+  // one launch of the cell kernel with tile width RT0 (variant 0) or RT1 (variant 1)
+  auto launch = [&](int variant) -> cudaError_t {
+    if (variant == 0) {
+      const size_t sm = tile_smem<T, NQ1, RT0>();
+      if (c.n_pairs > 0) {
+        auto f = k_cell_apply<T, P1, NQ1, true, RT0>;
+        EFE_CUDA_TRY(set_smem(f, sm));
+        f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, c.d_pair_start,
+                                     c.d_pair_fn, E, c.n_pairs, xEt, c.d_yE, c.apply_gate);
+      } else {
+        auto f = k_cell_apply<T, P1, NQ1, false, RT0>;
+        EFE_CUDA_TRY(set_smem(f, sm));
+        f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, nullptr, nullptr,
+                                     nullptr, 0, nullptr, nullptr, c.apply_gate);
+      }
+    } else {
+      const size_t sm = tile_smem<T, NQ1, RT1>();
+      if (c.n_pairs > 0) {
+        auto f = k_cell_apply<T, P1, NQ1, true, RT1>;
+        EFE_CUDA_TRY(set_smem(f, sm));
+        f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, c.d_pair_start,
+                                     c.d_pair_fn, E, c.n_pairs, xEt, c.d_yE, c.apply_gate);
+      } else {
+        auto f = k_cell_apply<T, P1, NQ1, false, RT1>;
+        EFE_CUDA_TRY(set_smem(f, sm));
+        f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, nullptr, nullptr,
+                                     nullptr, 0, nullptr, nullptr, c.apply_gate);
+      }
+    }
     note_launch();
-  } else {
-    auto f = k_cell_apply<T, P1, NQ1, false>;
-    EFE_CUDA_TRY(set_smem(f, sm));
-    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, nullptr, nullptr,
-                                 nullptr, 0, nullptr, nullptr);
-    note_launch();
+    return cudaGetLastError();
+  };
+  // Autotuner: the first apply of each (precision, column count) on a stream that
+  // is not being captured times both tile widths (CUDA events, two launches each,
+  // results discarded by the zero-fill and the final launch) and keeps the faster.
+  int& choice = c.tile_choice[F32 ? 1 : 0];
+  if (choice < 0 || c.tile_cols[F32 ? 1 : 0] != n_cols) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    EFE_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+      choice = 0;
+    } else {
+      float best = 1e30f;
+      int bestv = 0;
+      cudaEvent_t t0, t1;
+      EFE_CUDA_TRY(cudaEventCreate(&t0));
+      EFE_CUDA_TRY(cudaEventCreate(&t1));
+      for (int v = 0; v < 2; ++v) {
+        EFE_CUDA_TRY(launch(v));   // warm
+        EFE_CUDA_TRY(cudaEventRecord(t0, s));
+        EFE_CUDA_TRY(launch(v));
+        EFE_CUDA_TRY(cudaEventRecord(t1, s));
+        EFE_CUDA_TRY(cudaEventSynchronize(t1));
+        float ms = 0.0f;
+        EFE_CUDA_TRY(cudaEventElapsedTime(&ms, t0, t1));
+        c.tile_ms[F32 ? 1 : 0][v] = ms;
+        if (ms < best) { best = ms; bestv = v; }
+      }
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      choice = bestv;
+      c.tile_cols[F32 ? 1 : 0] = n_cols;
+      // the timing launches accumulated into Y and yE: start again from zero
+      EFE_CUDA_TRY(cudaMemset2DAsync(Y, sizeof(double) * ld2, 0, sizeof(double) * ncols2, c.n_dof, s));
+      if (c.nE > 0) EFE_CUDA_TRY(cudaMemsetAsync(c.d_yE, 0, sizeof(double) * c.nE * ld2, s));
+    }
   }
-  EFE_CUDA_TRY(cudaGetLastError());
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!c.apply_gate) prof_pair(c, e0, e1);   // no timing events inside captured graphs
+  if (e0) EFE_CUDA_TRY(cudaEventRecord(e0, s));
+  EFE_CUDA_TRY(launch(choice));
   if (e1) EFE_CUDA_TRY(cudaEventRecord(e1, s));
   if (c.nE > 0) {
     long long n = (long long)c.nE * ncols2;
@@ -654,13 +709,13 @@ static cudaError_t apply_noalloc_impl(Ctx& c, const double* X, double* Y, long l
     auto f = k_cell_apply<T, P1, NQ1, true>;
     EFE_CUDA_TRY(set_smem(f, sm));
     f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, c.d_pair_start,
-                                 c.d_pair_fn, E, c.n_pairs, xEt, yE);
+                                 c.d_pair_fn, E, c.n_pairs, xEt, yE, nullptr);
     note_launch();
   } else {
     auto f = k_cell_apply<T, P1, NQ1, false>;
     EFE_CUDA_TRY(set_smem(f, sm));
     f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, nullptr, nullptr,
-                                 nullptr, 0, nullptr, nullptr);
+                                 nullptr, 0, nullptr, nullptr, nullptr);
     note_launch();
   }
   EFE_CUDA_TRY(cudaGetLastError());

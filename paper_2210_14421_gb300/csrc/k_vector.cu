@@ -100,6 +100,7 @@ __global__ void k_lz_init(const double* __restrict__ X, double* __restrict__ Q0,
 
 __global__ void k_lz_state(LzView v, int C, const double* __restrict__ dts) {
   int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col == 0) *v.n_active = C;   // lets the first (gated) apply run
   if (col >= C) return;
   const double n = sqrt(v.red[col]);
   v.nrm[col] = n;
@@ -396,15 +397,15 @@ static unsigned red_grid(long long n_rows, long long C) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h_dts, int precision, int* kmax_used,
-                          int* cap_hits, double* eps_max, cudaStream_t s) {
+// The Lanczos loop for C columns: eager (host checks the active count after every
+// iteration and stops when it reaches zero) or graph body (all k_max iterations,
+// finished columns skipped on the device, no host synchronisation).
+static cudaError_t kexp_body(Ctx& c, const double* in, double* out, int precision, cudaStream_t s, bool eager) {
   const long long C = (long long)c.n_orb * c.op.batch;
   const long long n = c.n_dof;
   const long long ld2 = 2 * C;
   const long long qstride = n * 2 * C;
   LzView v = lz_view(c, C);
-  double* d_dts = v.invb;   // temporarily hold dts in invb, copied by k_lz_state
-  EFE_CUDA_TRY(cudaMemcpyAsync(d_dts, h_dts, sizeof(double) * C, cudaMemcpyHostToDevice, s));
   EFE_CUDA_TRY(cudaMemsetAsync(v.red, 0, sizeof(double) * C, s));
   const unsigned rg = red_grid(n, C);
   const size_t rs = red_smem(C);
@@ -412,13 +413,15 @@ cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h
   note_launch();
   k_lz_init<<<nblk(n * C), 256, 0, s>>>(in, c.d_Q, n, (int)C, ld2, v.red);
   note_launch();
-  k_lz_state<<<nblk(C), 256, 0, s>>>(v, (int)C, d_dts);
+  k_lz_state<<<nblk(C), 256, 0, s>>>(v, (int)C, v.invb);
   note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
+  c.apply_gate = eager ? nullptr : v.n_active;
   for (int j = 0; j < c.k_max; ++j) {
     double* Qj = c.d_Q + j * qstride;
     double* W = c.d_Q + (j + 1) * qstride;
-    EFE_CUDA_TRY(launch_apply(c, Qj, W, C, C, precision, s));
+    cudaError_t e = launch_apply(c, Qj, W, C, C, precision, s);
+    if (e != cudaSuccess) { c.apply_gate = nullptr; return e; }
     EFE_CUDA_TRY(cudaMemsetAsync(v.red, 0, sizeof(double) * 2 * C, s));   // red and red2
     EFE_CUDA_TRY(cudaMemsetAsync(v.n_active, 0, sizeof(int), s));
     k_lz_dot<<<rg, 256, rs, s>>>(Qj, W, n, (int)C, v.active, v.red);
@@ -432,21 +435,73 @@ cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h
     k_lz_scale<<<nblk(n * C), 256, 0, s>>>(W, n, (int)C, v.active, v.invb);
     note_launch();
     EFE_CUDA_TRY(cudaGetLastError());
-    EFE_CUDA_TRY(cudaMemcpyAsync(c.h_flag, v.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-    EFE_CUDA_TRY(cudaStreamSynchronize(s));
-    if (*c.h_flag == 0) break;
+    if (eager) {
+      EFE_CUDA_TRY(cudaMemcpyAsync(c.h_flag, v.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      EFE_CUDA_TRY(cudaStreamSynchronize(s));
+      if (*c.h_flag == 0) break;
+    }
   }
+  c.apply_gate = nullptr;
   k_lz_combine<<<nblk(n * C), 256, 0, s>>>(c.d_Q, qstride, n, (int)C, v, out, ld2);
   note_launch();
   int* d_si = v.n_active;   // reuse: [0] max k, [1] caps
   double* d_sd = v.red;
   k_lz_stats<<<1, 256, 0, s>>>(v, (int)C, d_si, d_sd);
   note_launch();
-  EFE_CUDA_TRY(cudaGetLastError());
+  return cudaGetLastError();
+}
+
+cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h_dts, int precision, int* kmax_used,
+                          int* cap_hits, double* eps_max, cudaStream_t s, bool need_stats) {
+  const long long C = (long long)c.n_orb * c.op.batch;
+  LzView v = lz_view(c, C);
+  // per-column time steps; they reach k_lz_state through invb (outside any graph)
+  EFE_CUDA_TRY(cudaMemcpyAsync(v.invb, h_dts, sizeof(double) * C, cudaMemcpyHostToDevice, s));
+  bool done = false;
+  if (c.use_graphs) {
+    Ctx::KexpGraph key{in, out, precision, C, c.op.kin, c.ws_gen, nullptr};
+    auto same = [&](const Ctx::KexpGraph& g) {
+      return g.in == key.in && g.out == key.out && g.precision == key.precision && g.C == key.C && g.kin == key.kin &&
+             g.gen == key.gen;
+    };
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : c.graphs)
+      if (same(g)) exec = g.exec;
+    bool seen = false;
+    for (auto& g : c.graph_seen)
+      if (same(g)) seen = true;
+    if (!exec && seen) {
+      // capture on the context's own stream, ordered after the work already on s
+      cudaEvent_t ev;
+      EFE_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      EFE_CUDA_TRY(cudaEventRecord(ev, s));
+      EFE_CUDA_TRY(cudaStreamWaitEvent(c.cap_stream, ev, 0));
+      EFE_CUDA_TRY(cudaStreamSynchronize(c.cap_stream));
+      cudaEventDestroy(ev);
+      EFE_CUDA_TRY(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = kexp_body(c, in, out, precision, c.cap_stream, false);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(c.cap_stream, &graph);
+      if (e != cudaSuccess) return e;
+      EFE_CUDA_TRY(e2);
+      EFE_CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
+      cudaGraphDestroy(graph);
+      key.exec = exec;
+      c.graphs.push_back(key);
+    }
+    if (exec) {
+      EFE_CUDA_TRY(cudaGraphLaunch(exec, s));
+      done = true;
+    } else {
+      c.graph_seen.push_back(key);   // first time: run eagerly (this also tunes the apply)
+    }
+  }
+  if (!done) EFE_CUDA_TRY(kexp_body(c, in, out, precision, s, true));
+  if (!need_stats) return cudaSuccess;
   int hi[2];
   double hd;
-  EFE_CUDA_TRY(cudaMemcpyAsync(hi, d_si, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
-  EFE_CUDA_TRY(cudaMemcpyAsync(&hd, d_sd, sizeof(double), cudaMemcpyDeviceToHost, s));
+  EFE_CUDA_TRY(cudaMemcpyAsync(hi, v.n_active, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+  EFE_CUDA_TRY(cudaMemcpyAsync(&hd, v.red, sizeof(double), cudaMemcpyDeviceToHost, s));
   EFE_CUDA_TRY(cudaStreamSynchronize(s));
   if (kmax_used) *kmax_used = hi[0];
   if (cap_hits) *cap_hits = hi[1];

@@ -166,8 +166,9 @@ def _oracle_run(S, wl, psi0, n_steps, fixed_k, tol, kmax, kick=True):
     return psi, np.array(mus)
 
 
-def _gpu_run(wl, psi0, n_steps, fixed_k, tol, kmax, precision=0, kick=True):
-    ctx = _ctx(wl, precision=precision, fixed_k=fixed_k, krylov_tol=tol, k_max=kmax, cg_tol=1e-14, cg_max_it=20000)
+def _gpu_run(wl, psi0, n_steps, fixed_k, tol, kmax, precision=0, kick=True, use_graphs=False):
+    ctx = _ctx(wl, precision=precision, fixed_k=fixed_k, krylov_tol=tol, k_max=kmax, cg_tol=1e-14, cg_max_it=20000,
+               use_graphs=use_graphs)
     psi = _to_dev(psi0)
     if kick:
         ctx.kick(psi, wl.fields)
@@ -210,6 +211,53 @@ def test_hartree_batched_members():
         for m in range(2):
             ref = poisson.solve(S, rho[m])[1]
             assert np.max(np.abs(vH.cpu().numpy()[m] - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_apply_both_tile_variants(variant):
+    """Both tile widths the autotuner chooses between give the oracle's result."""
+    wl = WORKLOADS["small2_p3"]()
+    S = _sys(wl)
+    from oracle import tdks
+    from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED
+    vq = tdks.nuclear_potential(S)
+    H = S.hbar(vq)
+    rng = np.random.default_rng(17)
+    X = rng.normal(size=(S.n_dof, wl.n_orb)) + 1j * rng.normal(size=(S.n_dof, wl.n_orb))
+    X[:S.n_h][S.mesh.boundary] = 0.0
+    ref = H @ X
+    bound = _rounding_bound(H, X)
+    ctx = _ctx(wl)
+    ctx.set_potential(_to_dev(vq[None]))
+    Xd = _to_dev(X)
+    Yd = torch.empty_like(Xd)
+    for prec, tol in ((EFE_FP64, 1e-12), (EFE_MIXED, 2e-5)):
+        assert ctx.tuning(prec, force_variant=variant)["variant"] == variant
+        ctx.apply_H(Xd, Yd, precision=prec)
+        assert np.all(np.abs(Yd.cpu().numpy() - ref) <= tol * bound + 1e-300)
+
+
+def test_graph_mode_matches_eager_and_oracle():
+    """Lanczos exponentials replayed as captured CUDA graphs (k_max iterations,
+    finished columns skipped on the device) give the eager / oracle result."""
+    wl = W.small_cluster(n_atoms=2, cells_per_axis=4, degree=3, n_quad=5, n_orb=2, batch=2, tol=1e-10)
+    S = _sys(wl)
+    psi0 = np.tile(S.initial_orbitals(), (1, 2))
+    ref_psi, ref_mu = _oracle_run(S, wl, psi0, 4, fixed_k=0, tol=1e-10, kmax=16)
+    ctx = _ctx(wl, fixed_k=0, krylov_tol=1e-10, k_max=16, use_graphs=True)
+    psi = _to_dev(psi0)
+    ctx.kick(psi, wl.fields)
+    mu = torch.zeros((2, 3), dtype=torch.float64, device="cuda")
+    for n in range(4):      # the first step runs eagerly, later ones replay the captured graphs
+        if n % 2 == 0:
+            ctx.magnus_step(psi, n * wl.dt, wl.dt, wl.fields, mu)
+        else:
+            from paper_2210_14421_gb300 import fields_array
+            ctx.magnus_step_async(psi, n * wl.dt, wl.dt, fields_array(wl.fields), mu)
+    torch.cuda.synchronize()
+    got = psi.cpu().numpy()
+    assert np.linalg.norm(got - ref_psi) <= 1e-8 * np.linalg.norm(ref_psi)
+    assert np.max(np.abs(mu.cpu().numpy() - ref_mu[-1])) <= 1e-8
 
 
 def test_magnus_adaptive_k_and_batch():
