@@ -266,6 +266,33 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
                              const double* expo_host, const double* coef_host, const double* enr_host,
                              void* stream);
 
+/* Gradient of a windowed dipole signal with respect to the field parameters.
+ * The paper has no adjoint; this is the exact reverse sweep (the adjoint of
+ * each operation, in reverse order) of n_steps calls of efe_magnus_step's
+ * predictor-corrector step (Eq. ApproxMagnus with the mid-point density of
+ * the predictor, field at t_n + dt/2, t_n = n dt), all in float64:
+ *   J = (1/|W|) sum_{n in W} d . mu(rho_n),   W = [window_first, window_last],
+ *   grad = dJ / d(amp, omega, sigma)   (omega entry 0 for EFE_FIELD_GAUSS).
+ * The derivative of each exponential exp(-i dt Hbar) is its Frechet derivative,
+ * integrated over s in [0, 1] with n_quad_s Gauss-Legendre nodes, each node two
+ * Lanczos exponentials; the Hartree map enters transposed (the direct solve
+ * with zero boundary data) and v_xc through d v_xc / d rho.  States are kept
+ * every checkpoint_every steps and a segment is recomputed before its reverse
+ * sweep (memory (n_steps / K + K + 10) blocks of psi).
+ * psi0_dev: device [n_dof][n_orb] complex128 (not modified).  field_host: kind
+ * EFE_FIELD_GAUSS or EFE_FIELD_SINE_GAUSS with sigma > 0; direction_host: host
+ * double[3] (d).  J_host: receives J; grad_host: host double[3].  The context
+ * needs batch = 1; the Lanczos tolerance and k_max of its options apply, and
+ * its state is invalidated (the next efe_magnus_step recomputes rho).  Allocates
+ * device memory per call and synchronises `stream`.  Returns EFE_WARN_KRYLOV_CAP
+ * (J and grad written) if any exponential stopped at k_max.  Errors: EFE_ERR_ARG
+ * (bad sizes, window outside [1, n_steps], n_quad_s outside [1, 64], batch != 1,
+ * unsupported field), EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_steps, double dt,
+                              const efe_field* field_host, const double* direction_host, int32_t window_first,
+                              int32_t window_last, int32_t checkpoint_every, int32_t n_quad_s, double* J_host,
+                              double* grad_host, void* stream);
+
 /* Diagnostics (not part of the method).  efe_profile(ctx, 1) synchronises the
  * device, resets a process-wide counter of kernel launches made by the library,
  * and from then on brackets every launch of the cell-apply kernel with a pair of

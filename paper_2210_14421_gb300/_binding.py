@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "EFE_OK", 1: "EFE_ERR_ARG", 2: "EFE_ERR_NOMEM", 3: "EFE_ERR_C
 EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coords", "efe_set_potential",
             "efe_apply_H", "efe_magnus_step", "efe_reset_state", "efe_density_vxc", "efe_hartree", "efe_dipole",
             "efe_kick", "efe_init_orbitals", "efe_profile", "efe_profile_read", "efe_selftest",
-            "efe_apply_H_noalloc", "efe_tuning"]
+            "efe_apply_H_noalloc", "efe_tuning", "efe_adjoint_dipole"]
 
 
 class MeshDesc(C.Structure):
@@ -96,6 +96,8 @@ def lib(path: str = LIB_PATH):
     L.efe_selftest.argtypes = [i64, C.POINTER(i64)]
     L.efe_tuning.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.efe_profile_read.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl)]
+    L.efe_adjoint_dipole.argtypes = [vp, vp, i32, dbl, C.POINTER(Field), pdbl, i32, i32, i32, i32, C.POINTER(dbl),
+                                     pdbl, vp]
     for name in EXPORTED:
         if name != "efe_last_error":
             getattr(L, name).restype = C.c_int
@@ -260,6 +262,19 @@ class Context:
     def kick(self, psi, fields):
         st = lib().efe_kick(self.h, _ptr(psi), fields_array(fields), _stream())
         return self._check(st, allow=(EFE_OK, EFE_WARN_KRYLOV_CAP))
+
+    def adjoint_dipole(self, psi0, n_steps, dt, field, direction, window, checkpoint_every: int = 4,
+                       n_quad_s: int = 8):
+        """(J, dJ/d(amp, omega, sigma)) of the window-averaged dipole d . mu over steps
+        window = (first, last) from psi0 (device complex128 [n_dof, n_orb])."""
+        d = np.ascontiguousarray(direction, dtype=np.float64)
+        g = np.zeros(3)
+        J = C.c_double()
+        st = lib().efe_adjoint_dipole(self.h, _ptr(psi0), int(n_steps), float(dt), fields_array([field]), _dptr(d),
+                                      int(window[0]), int(window[1]), int(checkpoint_every), int(n_quad_s),
+                                      C.byref(J), _dptr(g), _stream())
+        self._check(st, allow=(EFE_OK, EFE_WARN_KRYLOV_CAP))
+        return J.value, g
 
     def tuning(self, precision: int = EFE_MIXED, force_variant: int = -1):
         v, a, b = C.c_int32(), C.c_float(), C.c_float()

@@ -92,7 +92,7 @@ static cudaError_t dalloc(T*& p, size_t n) {
 }
 
 // Workspaces for C complex columns (Krylov basis, scratch, scalars).
-static efe_status ensure_ws(Ctx& c, long long C, long long ld) {
+efe_status ensure_ws(Ctx& c, long long C, long long ld) {
   const long long need_ld = std::max(C, ld);
   if (c.ws_cols >= need_ld && c.d_Q) return EFE_OK;
   const long long n = c.n_dof;
@@ -136,7 +136,7 @@ static efe_status ensure_operator(Ctx& c, int batch) {
   return EFE_OK;
 }
 
-static efe_status build_op(Ctx& c, const double* v, int batch, double kin, cudaStream_t s) {
+efe_status build_op(Ctx& c, const double* v, int batch, double kin, cudaStream_t s) {
   efe_status st = ensure_operator(c, batch);
   if (st != EFE_OK) return st;
   c.op.kin = kin;
@@ -685,6 +685,30 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
   if (e != cudaSuccess) return cuda_fail(c, e, "initial orbitals");
   c.state_valid = false;
   return EFE_OK;
+}
+
+efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_steps, double dt,
+                              const efe_field* field_host, const double* direction_host, int32_t window_first,
+                              int32_t window_last, int32_t checkpoint_every, int32_t n_quad_s, double* J_host,
+                              double* grad_host, void* stream) {
+  CHECK_CTX(ctx);
+  Ctx& c = ctx->c;
+  if (!psi0_dev || !field_host || !direction_host || !J_host || !grad_host || n_steps < 1 || !(dt != 0.0) ||
+      !std::isfinite(dt) || window_first < 1 || window_last < window_first || window_last > n_steps ||
+      checkpoint_every < 1 || n_quad_s < 1 || n_quad_s > 64) {
+    c.err = "efe_adjoint_dipole: invalid argument";
+    return EFE_ERR_ARG;
+  }
+  if (c.batch != 1) {
+    c.err = "efe_adjoint_dipole needs a context with batch = 1";
+    return EFE_ERR_ARG;
+  }
+  if ((field_host->kind != EFE_FIELD_GAUSS && field_host->kind != EFE_FIELD_SINE_GAUSS) || !(field_host->sigma > 0.0)) {
+    c.err = "efe_adjoint_dipole: the field must be EFE_FIELD_GAUSS or EFE_FIELD_SINE_GAUSS with sigma > 0";
+    return EFE_ERR_ARG;
+  }
+  return adjoint_dipole(c, psi0_dev, n_steps, dt, *field_host, direction_host, window_first, window_last,
+                        checkpoint_every, n_quad_s, J_host, grad_host, as_stream(stream));
 }
 
 efe_status efe_selftest(int64_t n, int64_t* mismatches_host) {

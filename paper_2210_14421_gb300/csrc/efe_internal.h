@@ -225,7 +225,14 @@ cudaError_t launch_axpby(double* y, const double* a, const double* b, double ca,
                          cudaStream_t s);
 // fast-diagonalisation Hartree solve (k_poisson.cu)
 cudaError_t setup_fdm(Ctx& c);
-cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, cudaStream_t s);
+cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, cudaStream_t s,
+                      bool homogeneous = false);
+// context workspaces for C complex columns of leading dimension ld; the operator of v (api.cu)
+efe_status ensure_ws(Ctx& c, long long C, long long ld);
+efe_status build_op(Ctx& c, const double* v, int batch, double kin, cudaStream_t s);
+// reverse sweep of the dipole objective through n_steps Magnus steps (adjoint.cu)
+efe_status adjoint_dipole(Ctx& c, const double* psi0, int n_steps, double dt, const efe_field& f, const double dir[3],
+                          int w_first, int w_last, int K, int n_s, double* J_out, double grad[3], cudaStream_t s);
 // Hartree solve (direct or PCG); iters returned (synchronises for PCG)
 efe_status run_hartree(Ctx& c, const double* rho, double* vH, double tol, int max_it, int* iters, cudaStream_t s);
 

@@ -119,7 +119,7 @@ __global__ void k_fdm_scatter(const double* __restrict__ u, const double* __rest
   const long long g = idx / nb;
   const int m = (int)(idx % nb);
   const long long ix = g % Nx, iy = (g / Nx) % Ny, iz = g / (Nx * Ny);
-  double v = phiB[g];
+  double v = phiB ? phiB[g] : 0.0;
   if (ix > 0 && iy > 0 && iz > 0 && ix < nx + 1 && iy < ny + 1 && iz < nz + 1) {
     const long long i = (ix - 1) + nx * ((iy - 1) + (long long)ny * (iz - 1));
     v = u[(long long)m * nx * ny * nz + i];
@@ -213,7 +213,7 @@ cudaError_t setup_fdm(Ctx& c) {
 
 // phi (n_h x nb) <- solution of the Dirichlet problem for the load vector d;
 // Ap is scratch (n_h x nb).
-cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, cudaStream_t s) {
+cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, cudaStream_t s, bool homogeneous) {
   const double scale = 1.0 / (2.0 * 3.14159265358979323846);
   const int nx = c.fdm_n[0], ny = c.fdm_n[1], nz = c.fdm_n[2];
   const long long n = (long long)nx * ny * nz;
@@ -222,7 +222,7 @@ cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, 
   const double *Vx = c.d_fdmV[0], *Vy = c.d_fdmV[1], *Vz = c.d_fdmV[2];
   // Ap = A phi_B (output on interior nodes only)
   EFE_CUDA_TRY(cudaMemsetAsync(Ap, 0, sizeof(double) * c.n_h * nb, s));
-  EFE_CUDA_TRY(launch_laplace(c, c.d_phiB_nb, Ap, nb, 0, scale, s));
+  if (!homogeneous) EFE_CUDA_TRY(launch_laplace(c, c.d_phiB_nb, Ap, nb, 0, scale, s));
   const unsigned g1 = (unsigned)((n * nb + 255) / 256);
   k_fdm_gather<<<g1, 256, 0, s>>>(d, Ap, c.Nx, c.Ny, nx, ny, nz, nb, t0);
   note_launch();
@@ -246,8 +246,8 @@ cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, 
                                       nz, s)));                                                         // y
     EFE_CUDA_TRY((dgemm<false, true>(ny * nz, nx, nx, b, nx, 0, Vx, nx, 0, a, nx, 0, 1, s)));           // x
   }
-  k_fdm_scatter<<<(unsigned)((c.n_h * nb + 255) / 256), 256, 0, s>>>(t0, c.d_phiB, c.n_h, c.Nx, c.Ny, nx, ny, nz,
-                                                                    nb, phi);
+  k_fdm_scatter<<<(unsigned)((c.n_h * nb + 255) / 256), 256, 0, s>>>(t0, homogeneous ? nullptr : c.d_phiB, c.n_h,
+                                                                    c.Nx, c.Ny, nx, ny, nz, nb, phi);
   note_launch();
   return cudaGetLastError();
 }
