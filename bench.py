@@ -10,7 +10,13 @@ kick 1e-3 along x.  Inputs are synthetic and seeded (efe_workloads.na8); the
 orbital block (1.35 GB) is larger than L2, so no flush is needed between
 steps.  One JSON line is printed by rank 0.
 
-  python bench.py [--gpus N --steps K --warmup W] [--precision mixed|fp64]
+The headline precision is "pair": the cell contraction and enrichment coupling
+on the FP32 pipe with pairs of binary32 (error-free products and sums), the
+rest in FP64; its dipole error against the FP64 path is measured in the same
+run (bound 1e-5 a.u.).  "mixed" (plain binary32 contraction) is timed beside it
+with its own dipole error, which exceeds the bound on this stiff workload.
+
+  python bench.py [--gpus N --steps K --warmup W] [--precision pair|mixed|fp64]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
 """
 from __future__ import annotations
@@ -39,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="efe", choices=["efe", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="pair", choices=["pair", "mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64 steps reported beside the main number")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--graph-steps", type=int, default=3, help="extra steps timed in CUDA-graph mode")
@@ -128,7 +134,7 @@ def apply_model(ctx, wl, precision):
     N_c 2 N_n^2 cols for the H.X rate."""
     p1, nq1 = wl.degree + 1, wl.n_quad
     R = 2 * wl.n_orb * wl.batch
-    ts = 4 if precision == "mixed" else 8
+    ts = 4 if precision == "mixed" else 8   # bytes per stored operator value (float, float pair, double)
     bytes_ = 2 * ctx.n_dof * R * 8 + ctx.n_cells * nq1 ** 3 * ts + ctx.n_pairs * p1 ** 3 * ts + ctx.n_nodes * 8
     fma_cell = 7 * p1 ** 4 + 2 * (nq1 * p1 ** 3 + nq1 ** 2 * p1 ** 2 + nq1 ** 3 * p1) + nq1 ** 3
     flops = 2.0 * (ctx.n_cells * fma_cell * R + 2 * p1 ** 3 * ctx.n_pairs * R)
@@ -311,7 +317,7 @@ def run_efe(args):
     import torch
 
     import __graft_entry__ as g
-    from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED, Context, fields_array
+    from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED, EFE_PAIR, Context, fields_array
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -324,7 +330,7 @@ def run_efe(args):
         torch.cuda.set_device(0)
     g.build()
     dev = torch.cuda.current_device()
-    prec = EFE_MIXED if args.precision == "mixed" else EFE_FP64
+    prec = {"mixed": EFE_MIXED, "pair": EFE_PAIR, "fp64": EFE_FP64}[args.precision]
     wl = workload(args.cells, rank)
     if args.k_max > 0:
         wl = wl.with_(k_max=args.k_max)
@@ -382,29 +388,38 @@ def run_efe(args):
     t_apply = prof["apply_ms"] / max(prof["apply_launches"], 1) / 1000.0
     peaks, src = measured_peaks()
     gbs = bytes_ / t_apply / 1e9
-    tfl = flops / t_apply / 1e12
     sm_mhz = (ck or {}).get("sm_mhz") or 1900.0
-    fp_lanes = 128 if args.precision == "mixed" else 2   # FP32 FMA lanes / FP64 FMA per clock per SM
+    fp_lanes = 2 if args.precision == "fp64" else 128   # FP64 FMA / FP32 lanes per clock per SM
     alu_peak = 152 * fp_lanes * 2 * sm_mhz * 1e6 / 1e12
+    if args.precision == "pair":
+        # each pair fma is 12 FP32-pipe instructions (1 mul, 3 fma, 8 add) = 15 flops; the pipe's peak
+        # for that mix is 15 flops per 12 lane-cycles
+        flops *= 15.0 / 2.0
+        alu_peak = 152 * 128 * (15.0 / 12.0) * sm_mhz * 1e6 / 1e12
+    tfl = flops / t_apply / 1e12
     hbm_frac = gbs / peaks["hbm_gbs"]
     alu_frac = tfl / alu_peak
     if alu_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                 "frac": round(alu_frac, 4), "traffic": None,
-                "peak_source": "152 SMs x %d %s FMA/clk x 2 x %.0f MHz (median SM clock sampled in the timed region)"
+                "peak_source": ("152 SMs x 128 FP32 lanes x 15/12 flop per lane-cycle (pair-fma instruction mix) x "
+                                "%.0f MHz (median SM clock sampled in the timed region)" % sm_mhz)
+                               if args.precision == "pair" else
+                               "152 SMs x %d %s FMA/clk x 2 x %.0f MHz (median SM clock sampled in the timed region)"
                                % (fp_lanes, "FP32" if fp_lanes == 128 else "FP64", sm_mhz),
                 "hbm_frac_of_measured": round(hbm_frac, 4)}
     else:
         roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(hbm_frac, 4), "traffic": None, "peak_source": src, "alu_frac": round(alu_frac, 4)}
-    roof.update({"kernel": "k_cell_apply<%s,5,6,ENR>" % ("float" if args.precision == "mixed" else "double"),
+    roof.update({"kernel": "k_cell_apply<%s,5,6,ENR>" % {"mixed": "float", "pair": "df32", "fp64": "double"}[args.precision],
                  "launches": prof["apply_launches"], "avg_ms": round(t_apply * 1000.0, 4),
                  "algorithmic_bytes": int(bytes_), "algorithmic_flops": flops})
     hx_tflops = dense / t_apply / 1e12
 
     line = {"metric": METRIC, "value": round(value, 4), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32-contraction/f64" if args.precision == "mixed" else "f64",
+            "vs_baseline": None,
+            "dtype": {"mixed": "f32-contraction/f64", "pair": "f32-pair-contraction/f64", "fp64": "f64"}[args.precision],
             "data": "synthetic (seeded efe_workloads.na8)",
             "config": {"workload": WORKLOAD, "precision": args.precision, "global_batch": world,
                        "n_cells": ctx.n_cells, "n_nodes": ctx.n_nodes, "n_enrich": ctx.n_enrich,
@@ -420,37 +435,47 @@ def run_efe(args):
                        "eps_max": [i["eps_max"] for i in infos], "cap_hits": [i["cap"] for i in infos],
                        "hartree_solves": [i["cg_iters"] for i in infos]},
             "setup_s": round(t_setup, 2), "initial_state": prep,
-            "autotune": {"mixed": ctx.tuning(EFE_MIXED), "fp64": ctx.tuning(EFE_FP64)}}
+            "autotune": {"mixed": ctx.tuning(EFE_MIXED), "pair": ctx.tuning(EFE_PAIR), "fp64": ctx.tuning(EFE_FP64)}}
 
-    if rank == 0 and args.fp64_steps > 0 and args.precision == "mixed":
-        # FP64 side by side from the same kicked state, and the mixed-vs-FP64 dipole error
-        ctx64 = Context(wl, precision=EFE_FP64, cg_tol=1e-10, cg_max_it=20000)
-        info64 = []
-        psi64 = psi_start.clone()
-        mus64 = []
-        t64 = 0.0
-        n_cmp = min(args.warmup, 1 + args.fp64_steps)
-        info64.append(ctx64.magnus_step(psi64, t64, wl.dt, wl.fields, mu))
-        mus64.append(mu.cpu().numpy().copy())
-        t64 += wl.dt
+    def side_run(prec_code, timed_steps, n_cmp):
+        """The same steps from the same kicked state at another precision: the dipoles of
+        the first n_cmp steps and the device time per step of timed_steps more."""
+        cs = Context(wl, precision=prec_code, cg_tol=1e-10, cg_max_it=20000)
+        ps = psi_start.clone()
+        mus, ts, first = [], 0.0, None
+        while len(mus) < n_cmp:
+            info = cs.magnus_step(ps, ts, wl.dt, wl.fields, mu)
+            first = first or info
+            mus.append(mu.cpu().numpy().copy())
+            ts += wl.dt
         torch.cuda.synchronize()
-        a0 = time.perf_counter()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for _ in range(args.fp64_steps):
-            ctx64.magnus_step_async(psi64, t64, wl.dt, arr, mu)
-            t64 += wl.dt
-            if len(mus64) < n_cmp:
-                mus64.append(mu.cpu().numpy().copy())
+        for _ in range(timed_steps):
+            cs.magnus_step_async(ps, ts, wl.dt, arr, mu)
+            ts += wl.dt
         f1.record(stream)
         torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1) / args.fp64_steps
-        k = min(len(mus64), len(mus_mixed))
-        derr = float(np.max(np.abs(np.array(mus64[:k]) - np.array(mus_mixed[:k])))) if k else None
+        cs.close()
+        return f0.elapsed_time(f1) / max(timed_steps, 1), np.array(mus), first
+
+    if rank == 0 and args.fp64_steps > 0 and args.precision != "fp64":
+        # FP64 (and, beside the pair path, the plain float32 contraction) from the same kicked
+        # state; dipole error of each against FP64 over the first steps
+        n_cmp = max(1, min(args.warmup, 3))
+        ms64, mus64, first64 = side_run(EFE_FP64, args.fp64_steps, n_cmp)
+        derr = float(np.max(np.abs(mus64 - np.array(mus_mixed[:n_cmp]))))
+        line["dipole_err_vs_fp64"] = {"value": derr, "steps": n_cmp, "bound": 1e-5, "met": derr <= 1e-5}
         line["fp64"] = {"steps_per_s": round(1000.0 / ms64, 4), "ms_per_step": round(ms64, 1),
-                        "steps": args.fp64_steps, "dipole_err_mixed_vs_fp64": derr, "compared_steps": k,
-                        "first_step": info64[0]}
-        ctx64.close()
+                        "steps": args.fp64_steps, "first_step": first64}
+        if args.precision == "pair":
+            ms32, mus32, first32 = side_run(EFE_MIXED, args.fp64_steps, n_cmp)
+            d32 = float(np.max(np.abs(mus64 - mus32)))
+            line["fp32_contraction"] = {"steps_per_s": round(1000.0 / ms32, 4), "ms_per_step": round(ms32, 1),
+                                        "steps": args.fp64_steps, "dipole_err_vs_fp64": d32, "met": d32 <= 1e-5,
+                                        "first_step": first32,
+                                        "note": "EFE_MIXED: float32 contraction; not the headline because its "
+                                                "dipole error exceeds the bound on this workload"}
 
     # end to end through the public API with host buffers: H2D of the orbital
     # block from pinned memory, the step, D2H of the dipole, every step

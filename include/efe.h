@@ -60,9 +60,13 @@ typedef enum {
 
 typedef enum {
   EFE_FP64 = 0,   /* every step in float64 */
-  EFE_MIXED = 1   /* cell contraction and enrichment coupling in float32 with float32
+  EFE_MIXED = 1,  /* cell contraction and enrichment coupling in float32 with float32
                      accumulation; gather/scatter, Lanczos, tridiagonal exponential,
                      density, Hartree residuals, norms and dipole in float64 */
+  EFE_PAIR = 2    /* as EFE_MIXED, but every value of the cell contraction and the
+                     enrichment coupling is a pair of float32 (h + l) with error-free
+                     products and sums, so the float32 pipe delivers ~2^-44 relative
+                     accuracy (float64 storage and everything else as EFE_MIXED) */
 } efe_precision;
 
 /* Radial shapes of the atomic part N^A (Eq. EFEAtomic), divided by r^l:
@@ -198,7 +202,8 @@ efe_status efe_apply_H(efe_ctx* ctx, const double* X_dev, double* Y_dev, int64_t
  * device memory and forbids new allocations once it runs, or code recording
  * into a CUDA graph, where allocation is not allowed during stream capture.
  * This call computes exactly what efe_apply_H computes, with the same
- * arguments and precision, but keeps its enrichment scratch in a static
+ * arguments and precision (EFE_FP64 or EFE_MIXED; EFE_PAIR is rejected with
+ * EFE_ERR_ARG), but keeps its enrichment scratch in a static
  * device array of 2 MiB per GPU (held from the library's first use on that
  * GPU until the process exits) instead of context workspaces; it calls no
  * cudaMalloc, cudaFree or allocating library routine.  Limit:
@@ -274,11 +279,13 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
  *   J = (1/|W|) sum_{n in W} d . mu(rho_n),   W = [window_first, window_last],
  *   grad = dJ / d(amp, omega, sigma)   (omega entry 0 for EFE_FIELD_GAUSS).
  * The derivative of each exponential exp(-i dt Hbar) is its Frechet derivative,
- * integrated over s in [0, 1] with n_quad_s Gauss-Legendre nodes, each node two
- * Lanczos exponentials; the Hartree map enters transposed (the direct solve
- * with zero boundary data) and v_xc through d v_xc / d rho.  States are kept
- * every checkpoint_every steps and a segment is recomputed before its reverse
- * sweep (memory (n_steps / K + K + 10) blocks of psi).
+ * integrated over s in [0, 1] with n_quad_s Gauss-Legendre nodes; the vectors
+ * exp(-i s dt Hbar) psi and exp(+i (1 - s) dt Hbar) lam at the nodes are
+ * recombined from the Krylov bases of the full-step exponentials (four Lanczos
+ * runs per reversed step).  The Hartree map enters transposed (the direct
+ * solve with zero boundary data) and v_xc through d v_xc / d rho.  States are
+ * kept every checkpoint_every steps and a segment is recomputed before its
+ * reverse sweep (memory (n_steps / K + K + 10 + 2 n_quad_s) blocks of psi).
  * psi0_dev: device [n_dof][n_orb] complex128 (not modified).  field_host: kind
  * EFE_FIELD_GAUSS or EFE_FIELD_SINE_GAUSS with sigma > 0; direction_host: host
  * double[3] (d).  J_host: receives J; grad_host: host double[3].  The context

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libefe.so")
 
 EFE_OK, EFE_ERR_ARG, EFE_ERR_NOMEM, EFE_ERR_CUDA, EFE_ERR_NOT_SPD = 0, 1, 2, 3, 4
 EFE_WARN_KRYLOV_CAP, EFE_ERR_CG_NOCONV, EFE_ERR_TIMEOUT, EFE_ERR_STATE = 5, 6, 7, 8
-EFE_FP64, EFE_MIXED = 0, 1
+EFE_FP64, EFE_MIXED, EFE_PAIR = 0, 1, 2
 EFE_HARTREE_FDM, EFE_HARTREE_PCG = 0, 1
 STATUS_NAMES = {0: "EFE_OK", 1: "EFE_ERR_ARG", 2: "EFE_ERR_NOMEM", 3: "EFE_ERR_CUDA", 4: "EFE_ERR_NOT_SPD",
                 5: "EFE_WARN_KRYLOV_CAP", 6: "EFE_ERR_CG_NOCONV", 7: "EFE_ERR_TIMEOUT", 8: "EFE_ERR_STATE"}

@@ -271,17 +271,28 @@ void field_derivs(const efe_field& f, double t, double E[3], double dE[3][3]) {
   }
 }
 
-// The reverse sweep and its forward recomputation.
+// The reverse sweep and its forward recomputation.  The Frechet derivative of
+// exp(-i dt Hbar) needs exp(-i s dt Hbar) psi and exp(+i (1 - s) dt Hbar) lam at the
+// n_s Gauss-Legendre nodes s_k; each family comes from one Krylov basis (that of
+// psi, resp. lam, for the full step) recombined at the scaled time steps.
 class Sweep {
  public:
-  Sweep(Ctx& c, cudaStream_t s) : c_(c), s_(s) {
+  Sweep(Ctx& c, cudaStream_t s, int n_s) : c_(c), s_(s) {
     C_ = c.n_orb;
     nqt_ = (long long)c.nc * c.nq;
     blk_ = c.n_dof * 2 * C_;
     for (double** p : {&rho0_, &rhop_, &rhom_, &v1_, &v2_, &vb1_, &vb2_, &rbar_, &rbm_, &tq_, &tq2_})
       *p = buf_.get(c, nqt_);
-    for (double** p : {&psip_, &lam_, &lam_new_, &lamp_, &ba_, &bb_, &tmp_}) *p = buf_.get(c, blk_);
+    for (double** p : {&psip_, &lam_, &lam_new_, &lamp_, &ba_, &tmp_}) *p = buf_.get(c, blk_);
     red_ = buf_.get(c, 3);
+    std::vector<double> x((size_t)n_s), w((size_t)n_s);
+    gauss_legendre(n_s, x.data(), w.data());
+    for (int k = 0; k < n_s; ++k) {
+      sk_.push_back(0.5 * (x[k] + 1.0));
+      wk_.push_back(0.5 * w[k]);
+      b1_.push_back(buf_.get(c, blk_));
+      b2_.push_back(buf_.get(c, blk_));
+    }
   }
 
   double* block() { return buf_.get(c_, blk_); }
@@ -290,12 +301,15 @@ class Sweep {
   long long cap_hits() const { return cap_hits_; }
 
   // forward step psi -> out (intermediates kept: rho0, v1, psip, rhop, rhom, v2);
-  // the corrector is skipped when out is NULL
-  void forward(const double* psi, double* out, const double E[3], double dt) {
+  // the corrector is skipped when out is NULL; with nodes, exp(-i s_k dt H1) psi
+  // goes to the node buffers b1
+  void forward(const double* psi, double* out, const double E[3], double dt, bool nodes = false) {
     ck(c_, launch_density(c_, psi, rho0_, s_), "density");
     potential(rho0_, E, v1_);
     ck(build_op(c_, v1_, 1, 1.0, s_));
     ck(c_, kexp(psi, psip_, dt), "predictor");
+    if (nodes)
+      for (size_t k = 0; k < sk_.size(); ++k) ck(c_, recombine(b1_[k], sk_[k] * dt), "Frechet node");
     ck(c_, launch_density(c_, psip_, rhop_, s_), "density");
     k_avg<<<nb256(nqt_), 256, 0, s_>>>(rhom_, rho0_, rhop_, nqt_);
     note_launch();
@@ -331,13 +345,15 @@ class Sweep {
 
   // reverse of the step psi -> psi_next (lam holds psi_next's cotangent on entry,
   // psi's on exit; rho_bar receives rho_n's); theta_bar accumulated
-  void reverse_step(const double* psi, const double E[3], const double dE[3][3], double dt, int n_s,
+  void reverse_step(const double* psi, const double E[3], const double dE[3][3], double dt,
                     double theta_bar[3]) {
-    forward(psi, nullptr, E, dt);
+    forward(psi, nullptr, E, dt, true);
     // corrector psi_next = U(v2) psi
     ck(build_op(c_, v2_, 1, 1.0, s_));
+    ck(c_, kexp(psi, tmp_, dt), "corrector");
+    for (size_t k = 0; k < sk_.size(); ++k) ck(c_, recombine(b2_[k], sk_[k] * dt), "Frechet node");
     ck(c_, kexp(lam_, lam_new_, -dt), "adjoint corrector");
-    frechet(psi, lam_, dt, n_s, vb2_);
+    frechet(b2_, dt, vb2_);
     vt(rhom_, vb2_, rbm_);
     k_axpy_q<<<nb256(nqt_), 256, 0, s_>>>(rbar_, rbm_, 0.5, nqt_);   // rho_m = (rho_n + rho^p) / 2
     note_launch();
@@ -350,7 +366,7 @@ class Sweep {
     ck(c_, kexp(lamp_, tmp_, -dt), "adjoint predictor");
     k_axpy_q<<<nb256(blk_), 256, 0, s_>>>(lam_new_, tmp_, 1.0, blk_);
     note_launch();
-    frechet(psi, lamp_, dt, n_s, vb1_);
+    frechet(b1_, dt, vb1_);
     vt(rho0_, vb1_, tq_);
     k_axpy_q<<<nb256(nqt_), 256, 0, s_>>>(rbar_, tq_, 1.0, nqt_);
     note_launch();
@@ -411,18 +427,20 @@ class Sweep {
     note_launch();
   }
 
-  // vbar = w dt int_0^1 Im sum_a conj(Phi a_a(s)) Phi b_a(s) ds by n_s-point Gauss-Legendre,
-  // a(s) = exp(+i (1-s) dt Hbar) lam, b(s) = exp(-i s dt Hbar) psi, Hbar the current operator
-  void frechet(const double* psi, const double* lam, double dt, int n_s, double* vbar) {
+  // vbar = w dt int_0^1 Im sum_a conj(Phi a_a(s)) Phi b_a(s) ds by the Gauss-Legendre nodes,
+  // b(s_k) = exp(-i s_k dt Hbar) psi given, a(s) = exp(+i (1-s) dt Hbar) lam recombined from
+  // the Krylov basis of lam just built (for -dt)
+  void frechet(const std::vector<double*>& b, double dt, double* vbar) {
     ck(c_, cudaMemsetAsync(vbar, 0, sizeof(double) * nqt_, s_), "memset");
-    std::vector<double> x((size_t)n_s), w((size_t)n_s);
-    gauss_legendre(n_s, x.data(), w.data());
-    for (int k = 0; k < n_s; ++k) {
-      const double sk = 0.5 * (x[k] + 1.0), wk = 0.5 * w[k];
-      ck(c_, kexp(psi, bb_, sk * dt), "Frechet node");
-      ck(c_, kexp(lam, ba_, -(1.0 - sk) * dt), "Frechet node");
-      ck(c_, cross_density(c_, ba_, bb_, wk * dt, vbar, s_), "cross density");
+    for (size_t k = 0; k < sk_.size(); ++k) {
+      ck(c_, recombine(ba_, -(1.0 - sk_[k]) * dt), "Frechet node");
+      ck(c_, cross_density(c_, ba_, b[k], wk_[k] * dt, vbar, s_), "cross density");
     }
+  }
+
+  cudaError_t recombine(double* out, double dt) {
+    std::vector<double> dts((size_t)C_, dt);
+    return run_kexp_recombine(c_, out, dts.data(), s_);
   }
 
   Ctx& c_;
@@ -430,7 +448,9 @@ class Sweep {
   long long C_ = 0, nqt_ = 0, blk_ = 0, cap_hits_ = 0;
   Buffers buf_;
   double *rho0_, *rhop_, *rhom_, *v1_, *v2_, *vb1_, *vb2_, *rbar_, *rbm_, *tq_, *tq2_;
-  double *psip_, *lam_, *lam_new_, *lamp_, *ba_, *bb_, *tmp_, *red_;
+  double *psip_, *lam_, *lam_new_, *lamp_, *ba_, *tmp_, *red_;
+  std::vector<double> sk_, wk_;
+  std::vector<double*> b1_, b2_;   // exp(-i s_k dt H1) psi, exp(-i s_k dt H2) psi
 };
 
 }  // namespace
@@ -442,7 +462,7 @@ efe_status adjoint_dipole(Ctx& c, const double* psi0, int n_steps, double dt, co
   efe_status st = EFE_OK;
   try {
     ck(ensure_ws(c, c.n_orb, c.n_orb));
-    Sweep sw(c, s);
+    Sweep sw(c, s, n_s);
     const long long blk = sw.blk();
     const int n_ck = (n_steps + K - 1) / K;
     const int nW = w_last - w_first + 1;
@@ -484,7 +504,7 @@ efe_status adjoint_dipole(Ctx& c, const double* psi0, int n_steps, double dt, co
         if (n >= w_first && n <= w_last) sw.window_term(dir, -1.0 / nW);
         sw.density_to_lam(seg[n - n0]);
         field_derivs(f, (n - 1) * dt + 0.5 * dt, E, dE);
-        sw.reverse_step(seg[n - 1 - n0], E, dE, dt, n_s, grad);
+        sw.reverse_step(seg[n - 1 - n0], E, dE, dt, grad);
       }
     }
     ck(c, cudaStreamSynchronize(s), "reverse sweep");

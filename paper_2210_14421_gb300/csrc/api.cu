@@ -49,14 +49,15 @@ Ctx::~Ctx() {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(device);
-  dfree(d_geo); dfree(d_Dsc); dfree(d_Dsc32); dfree(d_M); dfree(d_xE32); dfree(d_occ); dfree(d_vN); dfree(d_wJ); dfree(d_xq);
+  dfree(d_geo); dfree(d_Dsc); dfree(d_Dsc32); dfree(d_Dsc2); dfree(d_M); dfree(d_xE32); dfree(d_xE2);
+  dfree(d_occ); dfree(d_vN); dfree(d_wJ); dfree(d_xq);
   dfree(d_pair_start); dfree(d_pair_fn); dfree(d_pair_cell); dfree(d_Atil); dfree(d_KE); dfree(d_KEE);
   if (d_phiB_nb != d_phiB) dfree(d_phiB_nb);
   d_phiB_nb = nullptr;
   dfree(d_S); dfree(d_Shalf); dfree(d_diagA); dfree(d_phiB); dfree(d_phi);
   for (int a = 0; a < 3; ++a) { dfree(d_fdmV[a]); dfree(d_fdmL[a]); }
   dfree(d_fdmT);
-  dfree(op.W64); dfree(op.W32); dfree(op.E64); dfree(op.E32); dfree(op.HEE);
+  dfree(op.W64); dfree(op.W32); dfree(op.E64); dfree(op.E32); dfree(op.W2); dfree(op.E2); dfree(op.HEE);
   dfree(d_rho); dfree(d_vH); dfree(d_vxc); dfree(d_Q); dfree(d_psi_p); dfree(d_xE); dfree(d_yE);
   dfree(d_lz); dfree(d_lzi); dfree(d_rho2); dfree(d_v); dfree(d_cg); dfree(d_red);
   for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
@@ -103,6 +104,7 @@ efe_status ensure_ws(Ctx& c, long long C, long long ld) {
   TRY_CUDA(c, dalloc(c.d_lzi, (size_t)3 * need_ld + 8), "allocating Lanczos state");
   TRY_CUDA(c, dalloc(c.d_xE, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
   TRY_CUDA(c, dalloc(c.d_xE32, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
+  TRY_CUDA(c, dalloc(c.d_xE2, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
   TRY_CUDA(c, dalloc(c.d_yE, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
   c.ws_cols = need_ld;
   return EFE_OK;
@@ -130,6 +132,8 @@ static efe_status ensure_operator(Ctx& c, int batch) {
   TRY_CUDA(c, dalloc(c.op.W32, nqb), "allocating the operator");
   TRY_CUDA(c, dalloc(c.op.E64, (size_t)batch * c.n_pairs * c.nn), "allocating the coupling blocks");
   TRY_CUDA(c, dalloc(c.op.E32, (size_t)batch * c.n_pairs * c.nn), "allocating the coupling blocks");
+  TRY_CUDA(c, dalloc(c.op.W2, nqb), "allocating the operator");
+  TRY_CUDA(c, dalloc(c.op.E2, (size_t)batch * c.n_pairs * c.nn), "allocating the coupling blocks");
   TRY_CUDA(c, dalloc(c.op.HEE, (size_t)batch * std::max(c.nE, 1) * std::max(c.nE, 1)), "allocating H_EE");
   c.op.batch = batch;
   c.op.valid = false;
@@ -176,7 +180,10 @@ static bool validate(const efe_mesh_desc* mesh, const efe_atom* atoms, int n_ato
   if (o->n_orb < 1 || o->batch < 1 || !o->occ_host) { why = "n_orb, batch >= 1 and occupations required"; return false; }
   if (o->k_max < 1 || o->k_max > kMaxK) { why = "k_max must be in [1, 64]"; return false; }
   if (o->fixed_k < 0 || o->fixed_k > o->k_max) { why = "fixed_k must be in [0, k_max]"; return false; }
-  if (o->precision != EFE_FP64 && o->precision != EFE_MIXED) { why = "unknown precision"; return false; }
+  if (o->precision != EFE_FP64 && o->precision != EFE_MIXED && o->precision != EFE_PAIR) {
+    why = "unknown precision";
+    return false;
+  }
   if (o->hartree_method != EFE_HARTREE_FDM && o->hartree_method != EFE_HARTREE_PCG) {
     why = "unknown Hartree method";
     return false;
@@ -252,10 +259,14 @@ static efe_status setup_impl(Ctx& c, const efe_mesh_desc* mesh, const efe_atom* 
   for (int i = 0; i < kMaxNQ1 * kMaxP1; ++i) {
     t.B1f[i] = (float)t.B1[i];
     t.D1f[i] = (float)t.D1[i];
+    t.B1p[i] = df32::split(t.B1[i]);
+    t.D1p[i] = df32::split(t.D1[i]);
   }
   for (int i = 0; i < kMaxP1 * kMaxP1; ++i) {
     t.K1f[i] = (float)t.K1[i];
     t.M1f[i] = (float)t.M1[i];
+    t.K1p[i] = df32::split(t.K1[i]);
+    t.M1p[i] = df32::split(t.M1[i]);
   }
 
   // mesh geometry and the lumped GLL mass (a tensor product of 1D lumped masses)
@@ -293,6 +304,10 @@ static efe_status setup_impl(Ctx& c, const efe_mesh_desc* mesh, const efe_atom* 
     std::vector<float> D32(Dsc.begin(), Dsc.end());
     TRY_CUDA(c, dalloc(c.d_Dsc32, D32.size()), "allocating D");
     TRY_CUDA(c, cudaMemcpy(c.d_Dsc32, D32.data(), sizeof(float) * D32.size(), cudaMemcpyHostToDevice), "copy");
+    std::vector<df32> D2(Dsc.size());
+    for (size_t i = 0; i < Dsc.size(); ++i) D2[i] = df32::split(Dsc[i]);
+    TRY_CUDA(c, dalloc(c.d_Dsc2, D2.size()), "allocating D");
+    TRY_CUDA(c, cudaMemcpy(c.d_Dsc2, D2.data(), sizeof(df32) * D2.size(), cudaMemcpyHostToDevice), "copy");
   }
   TRY_CUDA(c, dalloc(c.d_occ, c.occ.size()), "allocating occupations");
   TRY_CUDA(c, cudaMemcpy(c.d_occ, c.occ.data(), sizeof(double) * c.occ.size(), cudaMemcpyHostToDevice), "copy");
@@ -579,7 +594,7 @@ efe_status efe_apply_H(efe_ctx* ctx, const double* X_dev, double* Y_dev, int64_t
     return EFE_ERR_STATE;
   }
   if (!X_dev || !Y_dev || X_dev == Y_dev || n_cols < 1 || ld < n_cols || n_cols % c.op.batch != 0 ||
-      (precision != EFE_FP64 && precision != EFE_MIXED)) {
+      (precision != EFE_FP64 && precision != EFE_MIXED && precision != EFE_PAIR)) {
     c.err = "bad arguments to efe_apply_H (n_cols must be a multiple of the operator's batch, ld >= n_cols)";
     return EFE_ERR_ARG;
   }
@@ -727,8 +742,8 @@ efe_status efe_tuning(efe_ctx* ctx, int32_t precision, int32_t force_variant, in
                       float* ms1) {
   CHECK_CTX(ctx);
   Ctx& c = ctx->c;
-  if (precision != EFE_FP64 && precision != EFE_MIXED) return EFE_ERR_ARG;
-  const int p = precision == EFE_MIXED ? 1 : 0;
+  if (precision != EFE_FP64 && precision != EFE_MIXED && precision != EFE_PAIR) return EFE_ERR_ARG;
+  const int p = precision;
   if (force_variant == 0 || force_variant == 1) {
     c.tile_choice[p] = force_variant;
     c.tile_cols[p] = (long long)c.n_orb * c.batch;

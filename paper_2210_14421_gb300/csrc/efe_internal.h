@@ -16,6 +16,19 @@ constexpr int kMaxNQ1 = 7;   // n_quad = p + 2
 constexpr int kMaxK = 64;    // Lanczos cap
 constexpr int kThreads = 256;
 
+// A value held as an unevaluated sum h + l of two binary32 numbers (the
+// FP32-pair precision of the cell apply; arithmetic in sumfact.cuh).
+struct __align__(8) df32 {
+  float h, l;
+  df32() = default;
+  __host__ __device__ constexpr df32(float h_, float l_ = 0.0f) : h(h_), l(l_) {}
+  // nearest pair to a double (host side: tables and set-up)
+  static df32 split(double x) {
+    const float h = (float)x;
+    return df32(h, (float)(x - (double)h));
+  }
+};
+
 // 1D reference tables on [-1, 1], passed to kernels by value (parameter space is
 // the constant bank, so warp-uniform reads broadcast).
 struct RefTables {
@@ -29,6 +42,10 @@ struct RefTables {
   float D1f[kMaxNQ1 * kMaxP1];
   float K1f[kMaxP1 * kMaxP1];
   float M1f[kMaxP1 * kMaxP1];
+  df32 B1p[kMaxNQ1 * kMaxP1];
+  df32 D1p[kMaxNQ1 * kMaxP1];
+  df32 K1p[kMaxP1 * kMaxP1];
+  df32 M1p[kMaxP1 * kMaxP1];
 };
 
 // Rectilinear mesh, device view (pointers to per-axis arrays).
@@ -61,6 +78,8 @@ struct Operator {
   float* W32 = nullptr;
   double* E64 = nullptr;    // [batch][n_pairs][nn] classical-enriched coupling E_c
   float* E32 = nullptr;
+  df32* W2 = nullptr;       // FP32-pair copies for EFE_PAIR
+  df32* E2 = nullptr;
   double* HEE = nullptr;    // [batch][nE][nE] enriched-enriched block (before M^ee^-1/2 scaling)
   bool valid = false;
 };
@@ -104,6 +123,7 @@ struct Ctx {
   double* d_geo = nullptr;     // x0 (ncx+ncy+ncz) then h (ncx+ncy+ncz)
   double* d_Dsc = nullptr;     // [n_h] mask / sqrt(M)
   float* d_Dsc32 = nullptr;    // float copy for the mixed apply
+  df32* d_Dsc2 = nullptr;      // pair copy for the FP32-pair apply
   double* d_M = nullptr;       // [n_h] lumped mass
   double* d_occ = nullptr;     // [n_orb]
   double* d_vN = nullptr;      // [nc][nq]
@@ -132,7 +152,7 @@ struct Ctx {
   double* d_fdmT = nullptr;    // [2][batch][nx ny nz] transform scratch
   // operators
   Operator op;                 // current operator (efe_set_potential / magnus)
-  // autotuned cell-apply tile width per precision [FP64, MIXED]: variant 0 (widest tile
+  // autotuned cell-apply tile width per precision [FP64, MIXED, PAIR]: variant 0 (widest tile
   // fitting two blocks per SM) or 1 (half as wide); -1 until timed
   const int* apply_gate = nullptr;   // device count of active Lanczos columns (graph mode), else NULL
   // CUDA graphs of the Lanczos exponential, keyed by (in, out, precision, columns, kin, generation)
@@ -150,9 +170,9 @@ struct Ctx {
   long long ws_gen = 0;                // bumped whenever workspaces or operator buffers move
   bool use_graphs = false;
   cudaStream_t cap_stream = nullptr;
-  int tile_choice[2] = {-1, -1};
-  long long tile_cols[2] = {-1, -1};
-  float tile_ms[2][2] = {{0, 0}, {0, 0}};
+  int tile_choice[3] = {-1, -1, -1};
+  long long tile_cols[3] = {-1, -1, -1};
+  float tile_ms[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   // state (density-derived potentials of the current step)
   bool state_valid = false;
   double* d_rho = nullptr;     // [batch][nc][nq]
@@ -164,6 +184,7 @@ struct Ctx {
   double* d_psi_p = nullptr;   // [n_dof][cols] complex
   double* d_xE = nullptr;      // [nE][2 cols] S x^E
   float* d_xE32 = nullptr;     // float copy
+  df32* d_xE2 = nullptr;       // pair copy
   double* d_yE = nullptr;      // [nE][2 cols] enriched accumulator
   double* d_lz = nullptr;      // Lanczos scalars per column (see k_vector.cu)
   int* d_lzi = nullptr;        // Lanczos integer state per column
@@ -209,6 +230,10 @@ cudaError_t launch_apply(Ctx& c, const double* X, double* Y, long long n_cols, l
 // operator held in Ctx::op; dts_host [n_cols]; host-visible statistics after a stream sync.
 cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* dts_host, int precision,
                           int* kmax_used, int* cap_hits, double* eps_max, cudaStream_t s, bool need_stats = true);
+
+// out = Kexp(-i dt_col Hbar) in again, for the start vectors of the last run_kexp_cols, from its
+// Krylov basis and tridiagonal matrices (|dt_col| no larger than that run's; no applies)
+cudaError_t run_kexp_recombine(Ctx& c, double* out, const double* dts_host, cudaStream_t s);
 
 // density / xc / dipole
 cudaError_t launch_density(Ctx& c, const double* psi, double* rho, cudaStream_t s);

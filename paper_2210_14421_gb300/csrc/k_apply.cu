@@ -33,7 +33,7 @@ constexpr int tile_rt() {
 
 template <typename T, int NQ1, int RT = tile_rt<T, NQ1>()>
 constexpr size_t tile_smem() {
-  return (size_t)4 * NQ1 * NQ1 * NQ1 * RT * sizeof(T) + 3 * 32 * sizeof(T);
+  return (size_t)4 * NQ1 * NQ1 * NQ1 * RT * sizeof(T) + 3 * 32 * sizeof(T);   // tiles + k_laplace's factors
 }
 
 // ----------------------------------------------------------------------------
@@ -50,27 +50,25 @@ k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const d
   constexpr int S3 = NQ1 * NQ1 * NQ1;
   constexpr int NN = P1 * P1 * P1;
   constexpr int NQ = S3;
-  // coupling rows staged per chunk: kc * NN entries of E_c in C and kc * RT of x^E in D
+  // coupling rows staged per chunk: kc * NN entries of E_c and kc * RT of x^E
   constexpr int KCAP = (S3 * RT) / NN < S3 ? (S3 * RT) / NN : S3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   T* B = A + S3 * RT;
   T* C = B + S3 * RT;
   T* D = C + S3 * RT;
-  T* ax = D + S3 * RT;
-  T* ay = ax + 32;
-  T* az = ay + 32;
 
   if (gate && *gate == 0) return;   // every Lanczos column has converged (graph-captured loops)
   const int c = blockIdx.x;
   const int member = blockIdx.y;
   int cx, cy, cz;
   cell_ijk(mesh, c, cx, cy, cz);
-  if (threadIdx.x < RT) {
+  T kx, ky, kz;   // kinetic factors hy hz / (4 hx) etc.
+  {
     const double hx = mesh.h[cx], hy = mesh.h[mesh.ncx + cy], hz = mesh.h[mesh.ncx + mesh.ncy + cz];
-    ax[threadIdx.x] = (T)(kin * hy * hz / (4.0 * hx));
-    ay[threadIdx.x] = (T)(kin * hx * hz / (4.0 * hy));
-    az[threadIdx.x] = (T)(kin * hx * hy / (4.0 * hz));
+    kx = from_f64<T>(kin * hy * hz / (4.0 * hx));
+    ky = from_f64<T>(kin * hx * hz / (4.0 * hy));
+    kz = from_f64<T>(kin * hx * hy / (4.0 * hz));
   }
   const T* Wc = W + ((long long)member * mesh.nc + c) * NQ;
   int p0 = 0, np = 0;
@@ -94,29 +92,12 @@ k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const d
       A[it] = v;
     }
     __syncthreads();
-    // kinetic part into B
-    kinetic_tile<T, P1, RT>(tab, A, B, C, D, ax, ay, az);
-    // v-weighted mass: B += B1^T diag(W) B1 X
-    interp_fwd<T, P1, NQ1, RT>(tab, A, C, D);
-    for (int it = threadIdx.x; it < NQ * RT; it += blockDim.x) C[it] *= Wc[it / RT];
-    __syncthreads();
-    interp_bwd<T, P1, NQ1, RT, true>(tab, C, B, D, C);
     if (ENR && np > 0) {
-      // y^C += E_c x^E  and  y^E += E_c^T x^C, with E_c rows and x^E staged in C and D
+      // y^E += E_c^T x^C while x^C is still in A (E_c rows staged in C)
       for (int k0 = 0; k0 < np; k0 += KCAP) {
         const int kc = np - k0 < KCAP ? np - k0 : KCAP;
         for (int i = threadIdx.x; i < kc * NN; i += blockDim.x) C[i] = Ec[(long long)k0 * NN + i];
-        for (int i = threadIdx.x; i < kc * RT; i += blockDim.x) {
-          const int r = i % RT, k = i / RT;
-          D[i] = (cbase + r < cols_member) ? xE[(long long)pair_fn[p0 + k0 + k] * ld2 + col0 + cbase + r] : T(0);
-        }
         __syncthreads();
-        for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
-          const int r = it % RT, l = it / RT;
-          T acc = T(0);
-          for (int k = 0; k < kc; ++k) acc = fma(C[k * NN + l], D[k * RT + r], acc);
-          B[it] += acc;
-        }
         for (int it = threadIdx.x; it < kc * RT; it += blockDim.x) {
           const int r = it % RT, k = it / RT;
           if (cbase + r >= cols_member) continue;
@@ -129,6 +110,27 @@ k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const d
         __syncthreads();
       }
     }
+    // classical cell operator: y^C = H_c x^C into D
+    cell_operator_tile<T, P1, NQ1, RT>(tab, A, B, C, D, Wc, kx, ky, kz);
+    if (ENR && np > 0) {
+      // y^C += E_c x^E, with E_c rows staged in B and x^E in C
+      for (int k0 = 0; k0 < np; k0 += KCAP) {
+        const int kc = np - k0 < KCAP ? np - k0 : KCAP;
+        for (int i = threadIdx.x; i < kc * NN; i += blockDim.x) B[i] = Ec[(long long)k0 * NN + i];
+        for (int i = threadIdx.x; i < kc * RT; i += blockDim.x) {
+          const int r = i % RT, k = i / RT;
+          C[i] = (cbase + r < cols_member) ? xE[(long long)pair_fn[p0 + k0 + k] * ld2 + col0 + cbase + r] : T(0);
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
+          const int r = it % RT, l = it / RT;
+          T acc = T(0);
+          for (int k = 0; k < kc; ++k) acc = fma(B[k * NN + l], C[k * RT + r], acc);
+          D[it] += fin(acc);
+        }
+        __syncthreads();
+      }
+    }
     // scatter-add y_bar^C += D y^C
     for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
       const int r = it % RT, l = it / RT;
@@ -136,15 +138,16 @@ k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const d
       const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
       const long long g = node_index(mesh, cx, cy, cz, i1, i2, i3);
       const T d = Dsc[g];
-      if (d != T(0)) atomicAdd(&Y[g * ld2 + col0 + cbase + r], to_f64<T>(d * B[it]));
+      if (d != T(0)) atomicAdd(&Y[g * ld2 + col0 + cbase + r], to_f64<T>(d * D[it]));
     }
     __syncthreads();
   }
 }
 
-// xE[nu][col] = sum_mu S[nu][mu] X[n_h + mu][col]  (and a float copy)
+// xE[nu][col] = sum_mu S[nu][mu] X[n_h + mu][col]  (and float and pair copies; xE2 may be NULL)
 __global__ void k_enr_pre(const double* __restrict__ S, const double* __restrict__ X, long long n_h, long long ld2,
-                          int ncols2, int nE, double* __restrict__ xE, float* __restrict__ xE32) {
+                          int ncols2, int nE, double* __restrict__ xE, float* __restrict__ xE32,
+                          df32* __restrict__ xE2 = nullptr) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)nE * ncols2) return;
   int nu = idx / ncols2, col = idx % ncols2;
@@ -152,6 +155,10 @@ __global__ void k_enr_pre(const double* __restrict__ S, const double* __restrict
   for (int mu = 0; mu < nE; ++mu) acc += S[nu * nE + mu] * X[(n_h + mu) * ld2 + col];
   xE[nu * ld2 + col] = acc;
   xE32[nu * ld2 + col] = (float)acc;
+  if (xE2) {
+    const float h = (float)acc;
+    xE2[nu * ld2 + col] = df32(h, (float)(acc - (double)h));
+  }
 }
 
 // yE[mu][col] += sum_k HEE[member][mu][k] xE[k][col]
@@ -182,12 +189,14 @@ __global__ void k_enr_post2(const double* __restrict__ S, const double* __restri
 // operator build
 // ----------------------------------------------------------------------------
 __global__ void k_op_W(const double* __restrict__ wJ, const double* __restrict__ v, double* __restrict__ W64,
-                       float* __restrict__ W32, long long n_per_member, int batch) {
+                       float* __restrict__ W32, df32* __restrict__ W2, long long n_per_member, int batch) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= n_per_member * batch) return;
   double w = wJ[idx % n_per_member] * v[idx];
   W64[idx] = w;
-  W32[idx] = (float)w;
+  const float h = (float)w;
+  W32[idx] = h;
+  W2[idx] = df32(h, (float)(w - (double)h));
 }
 
 // E[member][k][l] = kin * KE[k][l] + sum_q B[q][l] W[member][cell_k][q] Atil[k][q]
@@ -196,7 +205,7 @@ template <int P1, int NQ1>
 __global__ void __launch_bounds__(kThreads)
 k_op_pairs(const __grid_constant__ RefTables tab, const int* __restrict__ pair_cell, long long n_pairs, int nc,
            const double* __restrict__ Atil, const double* __restrict__ KE, const double* __restrict__ W,
-           double kin, double* __restrict__ E64, float* __restrict__ E32) {
+           double kin, double* __restrict__ E64, float* __restrict__ E32, df32* __restrict__ E2) {
   constexpr int RT = tile_rt<double, NQ1>();
   constexpr int S3 = NQ1 * NQ1 * NQ1;
   constexpr int NN = P1 * P1 * P1;
@@ -222,7 +231,9 @@ k_op_pairs(const __grid_constant__ RefTables tab, const int* __restrict__ pair_c
     const double e = kin * KE[k * NN + l] + Bt[l * RT + r];
     const long long o = ((long long)member * n_pairs + k) * NN + l;
     E64[o] = e;
-    E32[o] = (float)e;
+    const float h = (float)e;
+    E32[o] = h;
+    E2[o] = df32(h, (float)(e - (double)h));
   }
 }
 
@@ -451,15 +462,18 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
   if (c.nE > 0) {
     EFE_CUDA_TRY(cudaMemsetAsync(c.d_yE, 0, sizeof(double) * c.nE * ld2, s));
     long long n = (long long)c.nE * ncols2;
-    k_enr_pre<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, X, c.n_h, ld2, ncols2, c.nE, c.d_xE, c.d_xE32);
+    k_enr_pre<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, X, c.n_h, ld2, ncols2, c.nE, c.d_xE, c.d_xE32,
+                                                          c.d_xE2);
     note_launch();
     EFE_CUDA_TRY(cudaGetLastError());
   }
   constexpr bool F32 = std::is_same<T, float>::value;
-  const T* W = F32 ? (const T*)c.op.W32 : (const T*)c.op.W64;
-  const T* E = F32 ? (const T*)c.op.E32 : (const T*)c.op.E64;
-  const T* Dt = F32 ? (const T*)c.d_Dsc32 : (const T*)c.d_Dsc;
-  const T* xEt = F32 ? (const T*)c.d_xE32 : (const T*)c.d_xE;
+  constexpr bool PR = std::is_same<T, df32>::value;
+  constexpr int PI = PR ? 2 : F32 ? 1 : 0;   // precision index of the autotuner
+  const T* W = PR ? (const T*)c.op.W2 : F32 ? (const T*)c.op.W32 : (const T*)c.op.W64;
+  const T* E = PR ? (const T*)c.op.E2 : F32 ? (const T*)c.op.E32 : (const T*)c.op.E64;
+  const T* Dt = PR ? (const T*)c.d_Dsc2 : F32 ? (const T*)c.d_Dsc32 : (const T*)c.d_Dsc;
+  const T* xEt = PR ? (const T*)c.d_xE2 : F32 ? (const T*)c.d_xE32 : (const T*)c.d_xE;
   dim3 grid(c.nc, batch);
   constexpr int RT0 = tile_rt<T, NQ1>();
   constexpr int RT1 = RT0 / 2;
@@ -498,8 +512,8 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
   // Autotuner: the first apply of each (precision, column count) on a stream that
   // is not being captured times both tile widths (CUDA events, two launches each,
   // results discarded by the zero-fill and the final launch) and keeps the faster.
-  int& choice = c.tile_choice[F32 ? 1 : 0];
-  if (choice < 0 || c.tile_cols[F32 ? 1 : 0] != n_cols) {
+  int& choice = c.tile_choice[PI];
+  if (choice < 0 || c.tile_cols[PI] != n_cols) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     EFE_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
     if (cs != cudaStreamCaptureStatusNone) {
@@ -518,13 +532,13 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
         EFE_CUDA_TRY(cudaEventSynchronize(t1));
         float ms = 0.0f;
         EFE_CUDA_TRY(cudaEventElapsedTime(&ms, t0, t1));
-        c.tile_ms[F32 ? 1 : 0][v] = ms;
+        c.tile_ms[PI][v] = ms;
         if (ms < best) { best = ms; bestv = v; }
       }
       cudaEventDestroy(t0);
       cudaEventDestroy(t1);
       choice = bestv;
-      c.tile_cols[F32 ? 1 : 0] = n_cols;
+      c.tile_cols[PI] = n_cols;
       // the timing launches accumulated into Y and yE: start again from zero
       EFE_CUDA_TRY(cudaMemset2DAsync(Y, sizeof(double) * ld2, 0, sizeof(double) * ncols2, c.n_dof, s));
       if (c.nE > 0) EFE_CUDA_TRY(cudaMemsetAsync(c.d_yE, 0, sizeof(double) * c.nE * ld2, s));
@@ -549,7 +563,7 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
 template <int P1, int NQ1>
 static cudaError_t build_impl(Ctx& c, const double* v, int batch, double kin, cudaStream_t s) {
   const long long per = (long long)c.nc * c.nq;
-  k_op_W<<<(unsigned)((per * batch + 255) / 256), 256, 0, s>>>(c.d_wJ, v, c.op.W64, c.op.W32, per, batch);
+  k_op_W<<<(unsigned)((per * batch + 255) / 256), 256, 0, s>>>(c.d_wJ, v, c.op.W64, c.op.W32, c.op.W2, per, batch);
   note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   if (c.nE > 0) {
@@ -560,7 +574,7 @@ static cudaError_t build_impl(Ctx& c, const double* v, int batch, double kin, cu
       EFE_CUDA_TRY(set_smem(f, sm));
       dim3 grid((unsigned)((c.n_pairs + RT - 1) / RT), batch);
       f<<<grid, kThreads, sm, s>>>(c.tab, c.d_pair_cell, c.n_pairs, c.nc, c.d_Atil, c.d_KE, c.op.W64, kin, c.op.E64,
-                                   c.op.E32);
+                                   c.op.E32, c.op.E2);
       note_launch();
       EFE_CUDA_TRY(cudaGetLastError());
     }
@@ -588,6 +602,9 @@ cudaError_t launch_apply(Ctx& c, const double* X, double* Y, long long n_cols, l
                          cudaStream_t s) {
   if (precision == EFE_MIXED) {
     EFE_DISPATCH_P(c.p, return (apply_impl<float, P1, NQ1>(c, X, Y, n_cols, ld, s)));
+  }
+  if (precision == EFE_PAIR) {
+    EFE_DISPATCH_P(c.p, return (apply_impl<df32, P1, NQ1>(c, X, Y, n_cols, ld, s)));
   }
   EFE_DISPATCH_P(c.p, return (apply_impl<double, P1, NQ1>(c, X, Y, n_cols, ld, s)));
 }

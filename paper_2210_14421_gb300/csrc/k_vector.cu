@@ -154,40 +154,29 @@ __global__ void k_lz_update(double* __restrict__ W, const double* __restrict__ Q
   block_col_reduce(acc, f.col, f.ok, C, sred, out);
 }
 
-// y = exp(-i dt T) e_1 for the real symmetric tridiagonal T_j of one column
-// and the error estimate of Eq. AdaptiveKrylovErr, one warp per column.
+// y = exp(-i dt T) e_1 for the real symmetric m x m tridiagonal T (diagonal al,
+// off-diagonal be[0..m-2]) of one column, by one warp; y goes to v.yre/v.yim
+// and its last component to u0[0] (re) and u1[0] (im).
 // The exponential is the Chebyshev (Jacobi-Anger) series on the Gershgorin
 // interval [c - e, c + e] of T:
 //   exp(-i dt T) = exp(-i dt c) [J_0(z) + 2 sum_k (-i)^k J_k(z) T_k((T - c)/e)],  z = dt e,
 // with the Bessel values J_k(z) from Miller's backward recurrence (normalised
 // by J_0 + 2 sum J_2k = 1) and T_k(.) e_1 from the three-term recurrence, so a
 // step costs O(K m) with K ~ 1.3 z + 40 terms (truncation below 1e-17).
-__global__ void k_lz_tri(LzView v, int C, int j, int k_max, int fixed_k, double tol) {
-  extern __shared__ double tri_sh[];
-  const int col = blockIdx.x;
-  const int lane = threadIdx.x;   // 32 lanes
-  if (col >= C) return;
-  if (!v.active[col]) return;
-  const int m = j + 1;
-  double* al = tri_sh;            // [kMaxK]
-  double* be = al + kMaxK;        // [kMaxK]
-  double* u0 = be + kMaxK;        // [kMaxK + 2] T_{k-1} e1 (padded)
-  double* u1 = u0 + kMaxK + 2;    // [kMaxK + 2] T_k e1
-  double* jb = u1 + kMaxK + 2;    // Bessel values, [kMaxBessel]
-  constexpr int kMaxBessel = 1200;
-  __shared__ double sc[4];        // c, e, z
-  __shared__ int sK;
-  if (lane == 0) {
-    v.alpha[(long long)j * C + col] = v.red[col];
-    v.beta[(long long)j * C + col] = sqrt(v.red2[col]);
-  }
-  __syncwarp();
-  for (int r = lane; r < m; r += 32) {
-    al[r] = v.alpha[(long long)r * C + col];
-    be[r] = v.beta[(long long)r * C + col];   // be[m-1] = beta_j (not part of T_m)
-  }
-  __syncwarp();
-  const double dt = v.dt[col];
+constexpr int kMaxBessel = 1200;
+struct TriScratch {
+  double* u0;   // [kMaxK + 2] T_{k-1} e1 (padded)
+  double* u1;   // [kMaxK + 2] T_k e1
+  double* jb;   // [kMaxBessel] Bessel values
+  double* sc;   // [4]
+  int* sK;
+};
+__device__ void tri_exp_warp(const double* al, const double* be, int m, double dt, TriScratch t, LzView v, int col,
+                             int C) {
+  const int lane = threadIdx.x;
+  double* u0 = t.u0;
+  double* u1 = t.u1;
+  double* jb = t.jb;
   if (lane == 0) {
     double lo = 1e300, hi = -1e300;
     for (int r = 0; r < m; ++r) {
@@ -221,19 +210,19 @@ __global__ void k_lz_tri(LzView v, int C, int j, int k_max, int fixed_k, double 
       const double inv = 1.0 / norm;
       for (int n = 0; n < K; ++n) jb[n] *= inv;
     }
-    sc[0] = c;
-    sc[1] = e;
-    sc[2] = z;
-    sK = K;
+    t.sc[0] = c;
+    t.sc[1] = e;
+    t.sc[2] = z;
+    *t.sK = K;
   }
   __syncwarp();
-  const double c = sc[0], e = sc[1];
-  const int K = sK;
+  const double c = t.sc[0], e = t.sc[1];
+  const int K = *t.sK;
   const double sgn = dt >= 0 ? 1.0 : -1.0;    // exp(-i dt T): for dt < 0 the series of |dt| with conjugated phases
   // lane-owned components r = lane, lane + 32
   double yr[2] = {0.0, 0.0}, yi[2] = {0.0, 0.0};
-  for (int t = 0; t < 2; ++t) {
-    const int r = lane + 32 * t;
+  for (int q = 0; q < 2; ++q) {
+    const int r = lane + 32 * q;
     if (r < m) {
       u0[r + 1] = (r == 0) ? 1.0 : 0.0;
       u1[r + 1] = 0.0;
@@ -242,13 +231,13 @@ __global__ void k_lz_tri(LzView v, int C, int j, int k_max, int fixed_k, double 
   if (lane == 0) { u0[0] = u0[m + 1] = 0.0; u1[0] = u1[m + 1] = 0.0; }
   __syncwarp();
   // k = 0 term
-  for (int t = 0; t < 2; ++t) {
-    const int r = lane + 32 * t;
-    if (r < m) yr[t] += jb[0] * u0[r + 1];
+  for (int q = 0; q < 2; ++q) {
+    const int r = lane + 32 * q;
+    if (r < m) yr[q] += jb[0] * u0[r + 1];
   }
   // T_1 e1 = ((T - c) / e) e1
-  for (int t = 0; t < 2; ++t) {
-    const int r = lane + 32 * t;
+  for (int q = 0; q < 2; ++q) {
+    const int r = lane + 32 * q;
     if (r < m) {
       const double bl = r > 0 ? be[r - 1] : 0.0, br = r + 1 < m ? be[r] : 0.0;
       u1[r + 1] = ((al[r] - c) * u0[r + 1] + bl * u0[r] + br * u0[r + 2]) / e;
@@ -259,31 +248,31 @@ __global__ void k_lz_tri(LzView v, int C, int j, int k_max, int fixed_k, double 
     // coefficient 2 (-i)^k J_k (sign of the imaginary unit follows dt)
     const double cf = 2.0 * jb[k];
     const int ph = k & 3;   // (-i)^k: 1, -i, -1, i
-    for (int t = 0; t < 2; ++t) {
-      const int r = lane + 32 * t;
+    for (int q = 0; q < 2; ++q) {
+      const int r = lane + 32 * q;
       if (r < m) {
         const double w = cf * u1[r + 1];
-        if (ph == 0) yr[t] += w;
-        else if (ph == 1) yi[t] -= sgn * w;
-        else if (ph == 2) yr[t] -= w;
-        else yi[t] += sgn * w;
+        if (ph == 0) yr[q] += w;
+        else if (ph == 1) yi[q] -= sgn * w;
+        else if (ph == 2) yr[q] -= w;
+        else yi[q] += sgn * w;
       }
     }
     // next: T_{k+1} = 2 X T_k - T_{k-1}, stored in u0
     double nx[2] = {0.0, 0.0};
-    for (int t = 0; t < 2; ++t) {
-      const int r = lane + 32 * t;
+    for (int q = 0; q < 2; ++q) {
+      const int r = lane + 32 * q;
       if (r < m) {
         const double bl = r > 0 ? be[r - 1] : 0.0, br = r + 1 < m ? be[r] : 0.0;
-        nx[t] = 2.0 * ((al[r] - c) * u1[r + 1] + bl * u1[r] + br * u1[r + 2]) / e - u0[r + 1];
+        nx[q] = 2.0 * ((al[r] - c) * u1[r + 1] + bl * u1[r] + br * u1[r + 2]) / e - u0[r + 1];
       }
     }
     __syncwarp();
-    for (int t = 0; t < 2; ++t) {
-      const int r = lane + 32 * t;
+    for (int q = 0; q < 2; ++q) {
+      const int r = lane + 32 * q;
       if (r < m) {
         u0[r + 1] = u1[r + 1];
-        u1[r + 1] = nx[t];
+        u1[r + 1] = nx[q];
       }
     }
     __syncwarp();
@@ -291,20 +280,48 @@ __global__ void k_lz_tri(LzView v, int C, int j, int k_max, int fixed_k, double 
   // global phase exp(-i dt c)
   double sp, cp;
   sincos(dt * c, &sp, &cp);
-  for (int t = 0; t < 2; ++t) {
-    const int r = lane + 32 * t;
+  for (int q = 0; q < 2; ++q) {
+    const int r = lane + 32 * q;
     if (r < m) {
-      const double re = yr[t] * cp + yi[t] * sp;
-      const double im = yi[t] * cp - yr[t] * sp;
+      const double re = yr[q] * cp + yi[q] * sp;
+      const double im = yi[q] * cp - yr[q] * sp;
       v.yre[(long long)r * C + col] = re;
       v.yim[(long long)r * C + col] = im;
       if (r == m - 1) { u0[0] = re; u1[0] = im; }
     }
   }
   __syncwarp();
+}
+
+// Iteration j of one column: record alpha_j, beta_j, evaluate exp(-i dt T_{j+1}) e_1
+// and the error estimate of Eq. AdaptiveKrylovErr, and decide whether to stop.
+__global__ void k_lz_tri(LzView v, int C, int j, int k_max, int fixed_k, double tol) {
+  extern __shared__ double tri_sh[];
+  const int col = blockIdx.x;
+  const int lane = threadIdx.x;   // 32 lanes
+  if (col >= C) return;
+  if (!v.active[col]) return;
+  const int m = j + 1;
+  double* al = tri_sh;            // [kMaxK]
+  double* be = al + kMaxK;        // [kMaxK]
+  __shared__ double sc[4];
+  __shared__ int sK;
+  TriScratch t{be + kMaxK, be + 2 * kMaxK + 2, be + 3 * kMaxK + 4, sc, &sK};
+  if (lane == 0) {
+    v.alpha[(long long)j * C + col] = v.red[col];
+    v.beta[(long long)j * C + col] = sqrt(v.red2[col]);
+  }
+  __syncwarp();
+  for (int r = lane; r < m; r += 32) {
+    al[r] = v.alpha[(long long)r * C + col];
+    be[r] = v.beta[(long long)r * C + col];   // be[m-1] = beta_j (not part of T_m)
+  }
+  __syncwarp();
+  const double dt = v.dt[col];
+  tri_exp_warp(al, be, m, dt, t, v, col, C);
   if (lane != 0) return;
   const double b_j = be[m - 1];
-  const double eps = fabs(dt) * b_j * v.nrm[col] * sqrt(u0[0] * u0[0] + u1[0] * u1[0]);
+  const double eps = fabs(dt) * b_j * v.nrm[col] * sqrt(t.u0[0] * t.u0[0] + t.u1[0] * t.u1[0]);
   v.eps[col] = eps;
   bool stop = false;
   if (fixed_k > 0) {
@@ -325,6 +342,28 @@ __global__ void k_lz_tri(LzView v, int C, int j, int k_max, int fixed_k, double 
   }
 }
 
+// After a finished exponential: y = exp(-i dts[col] T) e_1 with the column's final
+// T (kused rows), for recombining the same Krylov basis at another time step.
+__global__ void k_lz_eval(LzView v, int C, const double* __restrict__ dts) {
+  extern __shared__ double tri_sh[];
+  const int col = blockIdx.x;
+  const int lane = threadIdx.x;
+  if (col >= C) return;
+  const int m = v.kused[col];
+  if (m <= 0) return;
+  double* al = tri_sh;
+  double* be = al + kMaxK;
+  __shared__ double sc[4];
+  __shared__ int sK;
+  TriScratch t{be + kMaxK, be + 2 * kMaxK + 2, be + 3 * kMaxK + 4, sc, &sK};
+  for (int r = lane; r < m; r += 32) {
+    al[r] = v.alpha[(long long)r * C + col];
+    be[r] = v.beta[(long long)r * C + col];
+  }
+  __syncwarp();
+  tri_exp_warp(al, be, m, dts[col], t, v, col, C);
+}
+
 // Q_{j+1} = W / beta_j for columns still running, zero for finished ones
 __global__ void k_lz_scale(double* __restrict__ W, long long n_rows, int C, const int* __restrict__ active,
                            const double* __restrict__ invb) {
@@ -343,20 +382,39 @@ __global__ void k_lz_scale(double* __restrict__ W, long long n_rows, int C, cons
   }
 }
 
-// out = nrm * sum_{j < kused} y_j Q_j
-__global__ void k_lz_combine(const double* __restrict__ Q, long long qstride, long long n_rows, int C,
-                             LzView v, double* __restrict__ out, long long ld2) {
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+// out = nrm * sum_{j < kused} y_j Q_j.  One thread per complex entry; the basis
+// vectors are read eight at a time (independent loads in flight) with
+// streaming hints, since each is touched once.
+__global__ void __launch_bounds__(256) k_lz_combine(const double* __restrict__ Q, long long qstride,
+                                                    long long n_rows, int C, LzView v, double* __restrict__ out,
+                                                    long long ld2) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= n_rows * C) return;
   const long long r = idx / C;
   const int col = (int)(idx % C);
   const int k = v.kused[col];
+  const double2* q = reinterpret_cast<const double2*>(Q) + idx;
+  const long long qs = qstride / 2;
+  const double* yr = v.yre + col;
+  const double* yi = v.yim + col;
   double re = 0.0, im = 0.0;
-  for (int j = 0; j < k; ++j) {
-    const double2 q = reinterpret_cast<const double2*>(Q + j * qstride)[idx];
-    const double yr = v.yre[(long long)j * C + col], yi = v.yim[(long long)j * C + col];
-    re += yr * q.x - yi * q.y;
-    im += yr * q.y + yi * q.x;
+  int j = 0;
+  for (; j + 8 <= k; j += 8) {
+    double2 a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = __ldcs(q + (long long)(j + u) * qs);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const double cr = yr[(long long)(j + u) * C], ci = yi[(long long)(j + u) * C];
+      re += cr * a[u].x - ci * a[u].y;
+      im += cr * a[u].y + ci * a[u].x;
+    }
+  }
+  for (; j < k; ++j) {
+    const double2 a = __ldcs(q + (long long)j * qs);
+    const double cr = yr[(long long)j * C], ci = yi[(long long)j * C];
+    re += cr * a.x - ci * a.y;
+    im += cr * a.y + ci * a.x;
   }
   const double n = v.nrm[col];
   *reinterpret_cast<double2*>(out + r * ld2 + 2 * col) = make_double2(n * re, n * im);
@@ -429,7 +487,7 @@ static cudaError_t kexp_body(Ctx& c, const double* in, double* out, int precisio
     k_lz_update<<<rg, 256, rs, s>>>(W, Qj, j > 0 ? c.d_Q + (j - 1) * qstride : nullptr, n, (int)C, v.active, v.red,
                                     j > 0 ? v.beta + (long long)(j - 1) * C : nullptr, v.red2);
     note_launch();
-    k_lz_tri<<<(unsigned)C, 32, sizeof(double) * (4 * kMaxK + 4 + 1200), s>>>(v, (int)C, j, c.k_max, c.fixed_k,
+    k_lz_tri<<<(unsigned)C, 32, sizeof(double) * (4 * kMaxK + 4 + kMaxBessel), s>>>(v, (int)C, j, c.k_max, c.fixed_k,
                                                                             c.krylov_tol);
     note_launch();
     k_lz_scale<<<nblk(n * C), 256, 0, s>>>(W, n, (int)C, v.active, v.invb);
@@ -507,6 +565,21 @@ cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h
   if (cap_hits) *cap_hits = hi[1];
   if (eps_max) *eps_max = hd;
   return cudaSuccess;
+}
+
+// out = nrm V exp(-i dts[col] T) e_1 with the Krylov basis V and tridiagonal T left by the
+// last run_kexp_cols (same columns): the exponential of the same start vector at another
+// time step of no larger magnitude, without new operator applies.
+cudaError_t run_kexp_recombine(Ctx& c, double* out, const double* h_dts, cudaStream_t s) {
+  const long long C = (long long)c.n_orb * c.op.batch;
+  const long long n = c.n_dof;
+  LzView v = lz_view(c, C);
+  EFE_CUDA_TRY(cudaMemcpyAsync(v.invb, h_dts, sizeof(double) * C, cudaMemcpyHostToDevice, s));
+  k_lz_eval<<<(unsigned)C, 32, sizeof(double) * (4 * kMaxK + 4 + kMaxBessel), s>>>(v, (int)C, v.invb);
+  note_launch();
+  k_lz_combine<<<nblk(n * C), 256, 0, s>>>(c.d_Q, n * 2 * C, n, (int)C, v, out, 2 * C);
+  note_launch();
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------- density

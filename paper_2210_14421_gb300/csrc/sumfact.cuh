@@ -13,12 +13,78 @@
 
 namespace efe {
 
+// ---------------------------------------------------------------------------
+// Pair-of-binary32 ("double-word") arithmetic on the FP32 pipe.  A value is
+// h + l with |l| <= ulp(h) / 2 once normalised.  The error-free transformations
+// are Knuth's TwoSum, Dekker's Fast2Sum and the FMA form of TwoProd; the
+// addition and multiplication of two pairs are the accurate algorithms of
+// Joldes, Muller and Popescu (ACM TOMS 44, 2017: "AccurateDWPlusDW",
+// relative error <= 3u^2, and "DWTimesDW3", <= 4u^2, u = 2^-24).  A chain of
+// products accumulated by fma() keeps its low word unnormalised (the exact
+// rounding error of every high-word addition is added into it) and fin()
+// renormalises it with one TwoSum.  The _rn intrinsics keep the compiler from
+// contracting or reassociating the transformations.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b|
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ df32 operator+(df32 x, df32 y) {
+  float sh, sl, th, tl, vh, vl, zh, zl;
+  two_sum(x.h, y.h, sh, sl);
+  two_sum(x.l, y.l, th, tl);
+  fast_two_sum(sh, __fadd_rn(sl, th), vh, vl);
+  fast_two_sum(vh, __fadd_rn(tl, vl), zh, zl);
+  return df32(zh, zl);
+}
+__device__ __forceinline__ df32 operator*(df32 x, df32 y) {
+  const float ch = __fmul_rn(x.h, y.h);
+  const float cl1 = __fmaf_rn(x.h, y.h, -ch);
+  const float tl1 = __fmaf_rn(x.h, y.l, __fmul_rn(x.l, y.l));
+  const float cl2 = __fmaf_rn(x.l, y.h, tl1);
+  float zh, zl;
+  fast_two_sum(ch, __fadd_rn(cl1, cl2), zh, zl);
+  return df32(zh, zl);
+}
+__device__ __forceinline__ df32& operator+=(df32& a, df32 b) { return a = a + b; }
+__device__ __forceinline__ df32& operator*=(df32& a, df32 b) { return a = a * b; }
+__device__ __forceinline__ bool operator!=(df32 a, df32 b) { return a.h != b.h || a.l != b.l; }
+// c + a b: exact product error and exact high-word rounding error go to the low word
+using ::fma;   // keep the float and double overloads visible next to this one
+__device__ __forceinline__ df32 fma(df32 a, df32 b, df32 c) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  float s, err;
+  two_sum(c.h, p, s, err);
+  return df32(s, __fadd_rn(c.l, __fadd_rn(err, e)));
+}
+__device__ __forceinline__ df32 fin(df32 a) {
+  float s, e;
+  two_sum(a.h, a.l, s, e);
+  return df32(s, e);
+}
+__device__ __forceinline__ float fin(float a) { return a; }
+__device__ __forceinline__ double fin(double a) { return a; }
+
 template <typename T> struct Tab;
 template <> struct Tab<double> {
   static __device__ __forceinline__ const double* B1(const RefTables& t) { return t.B1; }
   static __device__ __forceinline__ const double* K1(const RefTables& t) { return t.K1; }
   static __device__ __forceinline__ const double* M1(const RefTables& t) { return t.M1; }
   static __device__ __forceinline__ const double* D1(const RefTables& t) { return t.D1; }
+};
+template <> struct Tab<df32> {
+  static __device__ __forceinline__ const df32* B1(const RefTables& t) { return t.B1p; }
+  static __device__ __forceinline__ const df32* K1(const RefTables& t) { return t.K1p; }
+  static __device__ __forceinline__ const df32* M1(const RefTables& t) { return t.M1p; }
+  static __device__ __forceinline__ const df32* D1(const RefTables& t) { return t.D1p; }
 };
 template <> struct Tab<float> {
   static __device__ __forceinline__ const float* B1(const RefTables& t) { return t.B1f; }
@@ -41,17 +107,18 @@ __device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict
     T v[MIN];
 #pragma unroll
     for (int m = 0; m < MIN; ++m) v[m] = src[m * SM_IN];
-    const T scale = rs ? rs[r] : T(1);
     T* dst = out + a * SA_OUT + b * SB_OUT + r;
 #pragma unroll
     for (int o = 0; o < MOUT; ++o) {
       T acc = T(0);
 #pragma unroll
       for (int m = 0; m < MIN; ++m) acc = fma(TRANS ? mat[m * MOUT + o] : mat[o * MIN + m], v[m], acc);
+      acc = fin(acc);
+      if (rs) acc = rs[r] * acc;
       if (ACC)
-        dst[o * SM_OUT] += scale * acc;
+        dst[o * SM_OUT] += acc;
       else
-        dst[o * SM_OUT] = scale * acc;
+        dst[o * SM_OUT] = acc;
     }
   }
 }
@@ -123,6 +190,108 @@ __device__ __forceinline__ void interp_bwd(const RefTables& tab, const T* C, T* 
   __syncthreads();
 }
 
+// Classical cell operator of one tile, kinetic plus v-weighted mass:
+//   Y = cx K_1 M_2 M_3 X + cy M_1 K_2 M_3 X + cz M_1 M_2 K_3 X + B^T diag(W) B X
+// (subscript = axis; cx = hy hz / (4 hx) etc.), ordered so that every output
+// is one accumulation chain and no stage adds into a stored tile:
+//   G  = (B1^T (x) B1^T) [W (B1 (x) B1 (x) B1) X]          axes 3, 2 of the back projection
+//   A <- cx M_3 X,  B <- cy M_3 X,  D <- cz K_3 X           (one pass over axis-3 lines)
+//   B <- K_2 B + M_2 D,  A <- M_2 A                         (one pass over axis-2 lines)
+//   D <- K_1 A + M_1 B + B1^T_1 G                           (one pass over axis-1 lines)
+// X in A (overwritten), result in D; B, C scratch; W the cell's weights [NQ1^3].
+template <typename T, int P1, int NQ1, int RT>
+__device__ __forceinline__ void cell_operator_tile(const RefTables& tab, T* A, T* B, T* C, T* D,
+                                                   const T* __restrict__ W, T cx, T cy, T cz) {
+  constexpr int S3 = NQ1 * NQ1 * NQ1;
+  const T* B1 = Tab<T>::B1(tab);
+  const T* K1 = Tab<T>::K1(tab);
+  const T* M1 = Tab<T>::M1(tab);
+  interp_fwd<T, P1, NQ1, RT>(tab, A, C, D);
+  for (int it = threadIdx.x; it < S3 * RT; it += blockDim.x) C[it] *= W[it / RT];
+  __syncthreads();
+  along3<T, NQ1, P1, RT, true, false, NQ1, NQ1>(C, D, B1);          // (P1, NQ1, NQ1)
+  __syncthreads();
+  along2<T, NQ1, P1, RT, true, false, NQ1, P1>(D, C, B1);           // G: (P1, P1, NQ1)
+  __syncthreads();
+  constexpr int ITEMS = P1 * P1 * RT;
+  // axis-3 lines: offset (i2 P1 + i1) RT + r, stride P1^2 RT
+  for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
+    constexpr int S = P1 * P1 * RT;
+    T v[P1];
+#pragma unroll
+    for (int m = 0; m < P1; ++m) v[m] = A[it + m * S];
+#pragma unroll
+    for (int o = 0; o < P1; ++o) {
+      T p = T(0), q = T(0);
+#pragma unroll
+      for (int m = 0; m < P1; ++m) {
+        p = fma(M1[o * P1 + m], v[m], p);
+        q = fma(K1[o * P1 + m], v[m], q);
+      }
+      p = fin(p);
+      q = fin(q);
+      A[it + o * S] = cx * p;
+      B[it + o * S] = cy * p;
+      D[it + o * S] = cz * q;
+    }
+  }
+  __syncthreads();
+  // axis-2 lines: offset (i3 P1^2 + i1) RT + r, stride P1 RT
+  for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
+    constexpr int S = P1 * RT;
+    const int r = it % RT, i1 = (it / RT) % P1, i3 = it / (RT * P1);
+    const int off = (i3 * P1 * P1 + i1) * RT + r;
+    T a[P1], b[P1], d[P1];
+#pragma unroll
+    for (int m = 0; m < P1; ++m) {
+      a[m] = A[off + m * S];
+      b[m] = B[off + m * S];
+      d[m] = D[off + m * S];
+    }
+#pragma unroll
+    for (int o = 0; o < P1; ++o) {
+      T y = T(0), e = T(0);
+#pragma unroll
+      for (int m = 0; m < P1; ++m) {
+        y = fma(K1[o * P1 + m], b[m], y);
+        e = fma(M1[o * P1 + m], a[m], e);
+      }
+#pragma unroll
+      for (int m = 0; m < P1; ++m) y = fma(M1[o * P1 + m], d[m], y);
+      B[off + o * S] = fin(y);
+      A[off + o * S] = fin(e);
+    }
+  }
+  __syncthreads();
+  // axis-1 lines: offset (i3 P1 + i2) P1 RT + r (G: (i3 P1 + i2) NQ1 RT + r), stride RT
+  for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
+    const int r = it % RT, l23 = it / RT;
+    const int off = l23 * P1 * RT + r;
+    const int offg = l23 * NQ1 * RT + r;
+    T a[P1], b[P1], g[NQ1];
+#pragma unroll
+    for (int m = 0; m < P1; ++m) {
+      a[m] = A[off + m * RT];
+      b[m] = B[off + m * RT];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ1; ++q) g[q] = C[offg + q * RT];
+#pragma unroll
+    for (int o = 0; o < P1; ++o) {
+      T y = T(0);
+#pragma unroll
+      for (int m = 0; m < P1; ++m) {
+        y = fma(K1[o * P1 + m], a[m], y);
+        y = fma(M1[o * P1 + m], b[m], y);
+      }
+#pragma unroll
+      for (int q = 0; q < NQ1; ++q) y = fma(B1[q * P1 + o], g[q], y);
+      D[off + o * RT] = fin(y);
+    }
+  }
+  __syncthreads();
+}
+
 // IEEE-754 conversions between binary64 and binary32 on the integer pipes
 // (the FP64 unit of this GPU issues two operations per clock per SM, so the
 // hardware conversions would bind the float32 kernels).  Both follow the bit
@@ -162,5 +331,11 @@ template <> __device__ __forceinline__ float from_f64<float>(double x) { return 
 template <typename T> __device__ __forceinline__ double to_f64(T x);
 template <> __device__ __forceinline__ double to_f64<double>(double x) { return x; }
 template <> __device__ __forceinline__ double to_f64<float>(float x) { return f32_to_f64(x); }
+// x = h + l with h the nearest binary32 and l the nearest binary32 to x - h (one float64 subtraction)
+template <> __device__ __forceinline__ df32 from_f64<df32>(double x) {
+  const float h = f64_to_f32_rn(x);
+  return df32(h, f64_to_f32_rn(x - f32_to_f64(h)));
+}
+template <> __device__ __forceinline__ double to_f64<df32>(df32 x) { return f32_to_f64(x.h) + f32_to_f64(x.l); }
 
 }  // namespace efe

@@ -94,10 +94,14 @@ def test_apply_H_fp64_matches_oracle(name):
     bound = _rounding_bound(H, X)
     assert np.all(np.abs(got - ref) <= 1e-12 * bound + 1e-300)
     # mixed: float32 contraction; error within 2e-5 of the same scale
-    from paper_2210_14421_gb300 import EFE_MIXED
+    from paper_2210_14421_gb300 import EFE_MIXED, EFE_PAIR
     ctx.apply_H(Xd, Yd, precision=EFE_MIXED)
     got32 = Yd.cpu().numpy()
     assert np.all(np.abs(got32 - ref) <= 2e-5 * bound + 1e-300)
+    # float32 pairs: error-free products and sums, ~2^-44 per operation
+    ctx.apply_H(Xd, Yd, precision=EFE_PAIR)
+    gotp = Yd.cpu().numpy()
+    assert np.all(np.abs(gotp - ref) <= 1e-11 * bound + 1e-300)
 
 
 def test_apply_H_batched_potentials():
@@ -219,7 +223,7 @@ def test_apply_both_tile_variants(variant):
     wl = WORKLOADS["small2_p3"]()
     S = _sys(wl)
     from oracle import tdks
-    from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED
+    from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED, EFE_PAIR
     vq = tdks.nuclear_potential(S)
     H = S.hbar(vq)
     rng = np.random.default_rng(17)
@@ -231,7 +235,7 @@ def test_apply_both_tile_variants(variant):
     ctx.set_potential(_to_dev(vq[None]))
     Xd = _to_dev(X)
     Yd = torch.empty_like(Xd)
-    for prec, tol in ((EFE_FP64, 1e-12), (EFE_MIXED, 2e-5)):
+    for prec, tol in ((EFE_FP64, 1e-12), (EFE_MIXED, 2e-5), (EFE_PAIR, 1e-11)):
         assert ctx.tuning(prec, force_variant=variant)["variant"] == variant
         ctx.apply_H(Xd, Yd, precision=prec)
         assert np.all(np.abs(Yd.cpu().numpy() - ref) <= tol * bound + 1e-300)
@@ -284,6 +288,18 @@ def test_mixed_precision_dipole_error():
     _, mu64, _ = _gpu_run(wl, psi0, 5, fixed_k=0, tol=1e-10, kmax=16, precision=0)
     _, mu32, _ = _gpu_run(wl, psi0, 5, fixed_k=0, tol=1e-10, kmax=16, precision=1)
     assert np.max(np.abs(mu32 - mu64)) <= 1e-5
+
+
+def test_pair_precision_steps_match_fp64():
+    """Float32-pair path against the FP64 path: orbitals and dipoles after
+    5 adaptive steps agree to 1e-9 (the pair arithmetic carries ~2^-44)."""
+    wl = WORKLOADS["small2_p3"]()
+    S = _sys(wl)
+    psi0 = S.initial_orbitals()
+    p64, mu64, _ = _gpu_run(wl, psi0, 5, fixed_k=0, tol=1e-10, kmax=16, precision=0)
+    pp, mup, _ = _gpu_run(wl, psi0, 5, fixed_k=0, tol=1e-10, kmax=16, precision=2)
+    assert np.max(np.abs(mup - mu64)) <= 1e-9
+    assert np.max(np.abs(pp - p64)) <= 1e-9 * np.max(np.abs(p64))
 
 
 def test_unitary_and_hermitian_at_scale():
