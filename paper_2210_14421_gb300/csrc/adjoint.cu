@@ -13,7 +13,8 @@
 //            lam_p      = 2 occ Phi^T (rho_bar_p * Phi psi^p)   (the potential-only operator)
 //            theta_bar += -(dE/dtheta)(t_mid) . sum_q x_q (v_bar1 + v_bar2)_q
 // with checkpoints of psi every K steps and the states of a segment recomputed
-// before its reverse sweep.  Everything in float64.
+// before its reverse sweep.  Applies in float64, or in float32 pairs when the
+// context's precision is EFE_PAIR; everything else in float64.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -278,6 +279,7 @@ void field_derivs(const efe_field& f, double t, double E[3], double dE[3][3]) {
 class Sweep {
  public:
   Sweep(Ctx& c, cudaStream_t s, int n_s) : c_(c), s_(s) {
+    prec_ = c.precision == EFE_PAIR ? EFE_PAIR : EFE_FP64;
     C_ = c.n_orb;
     nqt_ = (long long)c.nc * c.nq;
     blk_ = c.n_dof * 2 * C_;
@@ -388,7 +390,7 @@ class Sweep {
     std::vector<double> dts((size_t)C_, dt);
     int k = 0, caps = 0;
     double eps = 0.0;
-    cudaError_t e = run_kexp_cols(c_, in, out, dts.data(), EFE_FP64, &k, &caps, &eps, s_, true);
+    cudaError_t e = run_kexp_cols(c_, in, out, dts.data(), prec_, &k, &caps, &eps, s_, true);
     cap_hits_ += caps;
     return e;
   }
@@ -422,7 +424,7 @@ class Sweep {
     k_div_w<<<nb256(nqt_), 256, 0, s_>>>(rho_bar, c_.d_wJ, tq2_, 1.0, nqt_);
     note_launch();
     ck(build_op(c_, tq2_, 1, 0.0, s_));
-    ck(c_, launch_apply(c_, psi, tmp_, C_, C_, EFE_FP64, s_), "apply");
+    ck(c_, launch_apply(c_, psi, tmp_, C_, C_, prec_, s_), "apply");
     k_occ_axpy<<<nb256(c_.n_dof * C_), 256, 0, s_>>>(acc, tmp_, c_.d_occ, c_.n_dof, (int)C_, c_.n_orb);
     note_launch();
   }
@@ -445,6 +447,7 @@ class Sweep {
 
   Ctx& c_;
   cudaStream_t s_;
+  int prec_ = EFE_FP64;
   long long C_ = 0, nqt_ = 0, blk_ = 0, cap_hits_ = 0;
   Buffers buf_;
   double *rho0_, *rhop_, *rhom_, *v1_, *v2_, *vb1_, *vb2_, *rbar_, *rbm_, *tq_, *tq2_;

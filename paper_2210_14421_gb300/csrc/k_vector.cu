@@ -583,20 +583,25 @@ cudaError_t run_kexp_recombine(Ctx& c, double* out, const double* h_dts, cudaStr
 }
 
 // ---------------------------------------------------------------------------- density
-template <int P1, int NQ1>
+// rho_q = sum_a f_a |psi_a(x_q)|^2.  The classical values Phi^C psi are interpolated in T
+// (float64, or float32 pairs: both 8 bytes, so a tile entry of T is overwritten in place by
+// the float64 value), the enrichment values and the squares are float64.
+template <typename T, int P1, int NQ1>
 __global__ void __launch_bounds__(kThreads)
 k_density(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ X, long long ld2,
           int n_orb, const double* __restrict__ occ, const double* __restrict__ Dsc,
           const int* __restrict__ pair_start, const int* __restrict__ pair_fn, const double* __restrict__ Atil,
           const double* __restrict__ xE, double* __restrict__ rho) {
+  static_assert(sizeof(T) == sizeof(double), "tile entries are reused as float64");
   constexpr int RT = 16;
   constexpr int S3 = NQ1 * NQ1 * NQ1;
   constexpr int NN = P1 * P1 * P1;
   extern __shared__ __align__(16) double dsm[];
-  double* A = dsm;
-  double* C = A + S3 * RT;
-  double* D = C + S3 * RT;
-  double* racc = D + S3 * RT;
+  T* A = reinterpret_cast<T*>(dsm);
+  T* Ct = A + S3 * RT;
+  T* D = Ct + S3 * RT;
+  double* C = reinterpret_cast<double*>(Ct);
+  double* racc = dsm + 3 * S3 * RT;
   const int c = blockIdx.x, member = blockIdx.y;
   int cx, cy, cz;
   cell_ijk(mesh, c, cx, cy, cz);
@@ -609,14 +614,14 @@ k_density(const __grid_constant__ RefTables tab, const MeshView mesh, const doub
     for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
       const int r = it % RT, l = it / RT;
       const long long g = node_index(mesh, cx, cy, cz, l % P1, (l / P1) % P1, l / (P1 * P1));
-      A[it] = (cbase + r < cols_member) ? Dsc[g] * X[g * ld2 + col0 + cbase + r] : 0.0;
+      A[it] = from_f64<T>((cbase + r < cols_member) ? Dsc[g] * X[g * ld2 + col0 + cbase + r] : 0.0);
     }
     __syncthreads();
-    interp_fwd<double, P1, NQ1, RT>(tab, A, C, D);
+    interp_fwd<T, P1, NQ1, RT>(tab, A, Ct, D);
     for (int it = threadIdx.x; it < S3 * RT; it += blockDim.x) {
       const int r = it % RT, q = it / RT;
       if (cbase + r >= cols_member) continue;
-      double acc = C[it];
+      double acc = to_f64<T>(Ct[it]);
       for (int k = 0; k < np; ++k)
         acc += Atil[(long long)(p0 + k) * S3 + q] * xE[(long long)pair_fn[p0 + k] * ld2 + col0 + cbase + r];
       C[it] = acc;
@@ -646,7 +651,7 @@ __global__ void k_enr_pre_d(const double* __restrict__ S, const double* __restri
   xE[nu * ld2 + col] = acc;
 }
 
-template <int P1, int NQ1>
+template <typename T, int P1, int NQ1>
 static cudaError_t density_impl(Ctx& c, const double* psi, double* rho, cudaStream_t s) {
   const long long C = (long long)c.n_orb * c.batch;
   const long long ld2 = 2 * C;
@@ -657,20 +662,30 @@ static cudaError_t density_impl(Ctx& c, const double* psi, double* rho, cudaStre
   }
   dim3 grid(c.nc, c.batch);
   const size_t sm = sizeof(double) * (3 * 16 * NQ1 * NQ1 * NQ1 + NQ1 * NQ1 * NQ1);
-  EFE_CUDA_TRY(cudaFuncSetAttribute(k_density<P1, NQ1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_density<P1, NQ1><<<grid, kThreads, sm, s>>>(c.tab, c.mesh, psi, ld2, c.n_orb, c.d_occ, c.d_Dsc,
+  EFE_CUDA_TRY(cudaFuncSetAttribute(k_density<T, P1, NQ1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_density<T, P1, NQ1><<<grid, kThreads, sm, s>>>(c.tab, c.mesh, psi, ld2, c.n_orb, c.d_occ, c.d_Dsc,
                                                 c.n_pairs ? c.d_pair_start : nullptr, c.d_pair_fn, c.d_Atil, c.d_xE,
                                                 rho);
   note_launch();
   return cudaGetLastError();
 }
 
+// Float32 pairs for the interpolation unless the context computes in float64.
 cudaError_t launch_density(Ctx& c, const double* psi, double* rho, cudaStream_t s) {
+  if (c.precision != EFE_FP64) {
+    switch (c.p) {
+      case 2: return density_impl<df32, 3, 4>(c, psi, rho, s);
+      case 3: return density_impl<df32, 4, 5>(c, psi, rho, s);
+      case 4: return density_impl<df32, 5, 6>(c, psi, rho, s);
+      case 5: return density_impl<df32, 6, 7>(c, psi, rho, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (c.p) {
-    case 2: return density_impl<3, 4>(c, psi, rho, s);
-    case 3: return density_impl<4, 5>(c, psi, rho, s);
-    case 4: return density_impl<5, 6>(c, psi, rho, s);
-    case 5: return density_impl<6, 7>(c, psi, rho, s);
+    case 2: return density_impl<double, 3, 4>(c, psi, rho, s);
+    case 3: return density_impl<double, 4, 5>(c, psi, rho, s);
+    case 4: return density_impl<double, 5, 6>(c, psi, rho, s);
+    case 5: return density_impl<double, 6, 7>(c, psi, rho, s);
   }
   return cudaErrorInvalidValue;
 }
