@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--graph-steps", type=int, default=3, help="extra steps timed in CUDA-graph mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="instead of the step throughput: cost and finite-difference check of the adjoint gradient "
+                         "on the organic-27 workload")
+    ap.add_argument("--adj-steps", type=int, default=6)
+    ap.add_argument("--adj-cells", type=int, default=27)
     ap.add_argument("--cells", type=int, default=31, help="cells per axis (31 = the Na8-like workload)")
     ap.add_argument("--k-max", type=int, default=48,
                     help="Lanczos cap; the Na8-like spectrum (-257..+1600 Ha) at dt = 0.05 needs k ~ 32 (FP64) "
@@ -397,11 +402,16 @@ def run_efe(args):
         flops *= 15.0 / 2.0
         alu_peak = 152 * 128 * (15.0 / 12.0) * sm_mhz * 1e6 / 1e12
     tfl = flops / t_apply / 1e12
+    # dram__bytes_read.sum + dram__bytes_write.sum of one k_cell_apply<df32,5,6,ENR,8> launch on the
+    # 15^3-cell crop (440.15 MB against 348.27 MB algorithmic), scaled to this launch by its algorithmic
+    # bytes; only for the pair kernel that capture measured
+    traffic = (round(bytes_ * 440.151808 / 348.26868, -6)
+               if args.precision == "pair" and wl.degree == 4 else None)
     hbm_frac = gbs / peaks["hbm_gbs"]
     alu_frac = tfl / alu_peak
     if alu_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
-                "frac": round(alu_frac, 4), "traffic": None,
+                "frac": round(alu_frac, 4), "traffic": traffic,
                 "peak_source": ("152 SMs x 128 FP32 lanes x 15/12 flop per lane-cycle (pair-fma instruction mix) x "
                                 "%.0f MHz (median SM clock sampled in the timed region)" % sm_mhz)
                                if args.precision == "pair" else
@@ -410,7 +420,7 @@ def run_efe(args):
                 "hbm_frac_of_measured": round(hbm_frac, 4)}
     else:
         roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(hbm_frac, 4), "traffic": None, "peak_source": src, "alu_frac": round(alu_frac, 4)}
+                "frac": round(hbm_frac, 4), "traffic": traffic, "peak_source": src, "alu_frac": round(alu_frac, 4)}
     roof.update({"kernel": "k_cell_apply<%s,5,6,ENR>" % {"mixed": "float", "pair": "df32", "fp64": "double"}[args.precision],
                  "launches": prof["apply_launches"], "avg_ms": round(t_apply * 1000.0, 4),
                  "algorithmic_bytes": int(bytes_), "algorithmic_flops": flops})
@@ -528,10 +538,79 @@ def run_efe(args):
     return 0
 
 
+def run_adjoint(args):
+    """Cost of efe_adjoint_dipole against the forward steps it differentiates, and its
+    amplitude derivative against central differences of the forward run, on a segment
+    of the organic-27 propagation (the pulse centred in the segment)."""
+    import dataclasses
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import efe_workloads as W
+    from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED, EFE_PAIR, Context
+    prec = {"mixed": EFE_FP64, "pair": EFE_PAIR, "fp64": EFE_FP64}[args.precision]
+    n = args.adj_steps
+    # k_max 64: the exponentials converge (tol 1e-7), so the forward run is smooth in theta at the
+    # level the finite difference needs (with the cap at 48 the atomics' rounding order moves J by ~1e-6)
+    wl = W.organic27(cells_per_axis=args.adj_cells, k_max=64)
+    f = dataclasses.replace(wl.fields[0], amp=5e-3, t0=0.5 * n * wl.dt, sigma=0.25 * n * wl.dt)
+    ctx = Context(wl, precision=EFE_MIXED, cg_tol=1e-10, cg_max_it=20000)
+    psi0, prep = prepare_state(ctx, wl)
+    ctx.close()
+    torch.cuda.empty_cache()
+    ctx = Context(wl, precision=prec, cg_tol=1e-10, cg_max_it=20000)
+    d = np.array(f.direction, dtype=np.float64)
+    window = (n - 2, n)
+    mu = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+
+    def forward(field):
+        ctx.reset_state()
+        psi = psi0.clone()
+        J = 0.0
+        for k in range(n):
+            ctx.magnus_step(psi, k * wl.dt, wl.dt, [field], mu)
+            if window[0] <= k + 1 <= window[1]:
+                J += float(np.dot(d, mu.cpu().numpy()[0])) / (window[1] - window[0] + 1)
+        return J
+
+    forward(f)   # warm-up (autotuning)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J_fwd = forward(f)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    J, grad = ctx.adjoint_dipole(psi0, n, wl.dt, f, d, window, checkpoint_every=2, n_quad_s=6)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    h = 1e-2 * f.amp
+    fd = (forward(dataclasses.replace(f, amp=f.amp + h)) - forward(dataclasses.replace(f, amp=f.amp - h))) / (2 * h)
+    line = {"metric": "adjoint gradient cost", "value": round(t_adj / t_fwd, 3), "unit": "x forward",
+            "higher_is_better": False,
+            "dtype": {"pair": "f32-pair-contraction/f64", "fp64": "f64", "mixed": "f64"}[args.precision],
+            "data": "synthetic (seeded efe_workloads.organic27)",
+            "config": {"workload": "organic-27 (15 C/N/O + 12 H, %d orbitals), %d^3 graded cells degree 4; "
+                                   "sine-Gaussian pulse amp 5e-3, omega 0.1, centred in a %d-step segment, dt 0.05"
+                                   % (wl.n_orb, args.adj_cells, n),
+                       "n_steps": n, "window": list(window), "checkpoint_every": 2, "n_quad_s": 6,
+                       "k_max": wl.k_max, "krylov_tol": wl.krylov_tol},
+            "forward_s": round(t_fwd, 3), "adjoint_s": round(t_adj, 3), "J": J, "J_forward": J_fwd,
+            "grad": [float(x) for x in grad],
+            "fd_amp": {"h_rel": 1e-2, "fd": fd, "adjoint": float(grad[0]),
+                       "rel_err": abs(float(grad[0]) - fd) / max(abs(fd), 1e-300)},
+            "initial_state": prep}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.adjoint:
+        return run_adjoint(args)
     return run_efe(args)
 
 
