@@ -61,12 +61,14 @@ typedef enum {
 typedef enum {
   EFE_FP64 = 0,   /* every step in float64 */
   EFE_MIXED = 1,  /* cell contraction and enrichment coupling in float32 with float32
-                     accumulation; gather/scatter, Lanczos, tridiagonal exponential,
-                     density, Hartree residuals, norms and dipole in float64 */
+                     accumulation; the density interpolation, the Lanczos vector update
+                     and the Krylov combination in float32 pairs (as EFE_PAIR); gather/
+                     scatter accumulation, tridiagonal exponential, Hartree, norms and
+                     dipole in float64; storage float64 */
   EFE_PAIR = 2    /* as EFE_MIXED, but every value of the cell contraction and the
                      enrichment coupling is a pair of float32 (h + l) with error-free
                      products and sums, so the float32 pipe delivers ~2^-44 relative
-                     accuracy (float64 storage and everything else as EFE_MIXED) */
+                     accuracy */
 } efe_precision;
 
 /* Radial shapes of the atomic part N^A (Eq. EFEAtomic), divided by r^l:

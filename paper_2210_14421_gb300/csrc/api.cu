@@ -100,7 +100,7 @@ efe_status ensure_ws(Ctx& c, long long C, long long ld) {
   c.ws_gen += 1;   // captured graphs refer to the old buffers
   TRY_CUDA(c, dalloc(c.d_Q, (size_t)(c.k_max + 1) * n * 2 * need_ld), "allocating the Krylov basis");
   TRY_CUDA(c, dalloc(c.d_psi_p, (size_t)n * 2 * need_ld), "allocating the predictor block");
-  TRY_CUDA(c, dalloc(c.d_lz, (size_t)(4 * kMaxK + 8) * need_ld), "allocating Lanczos scalars");
+  TRY_CUDA(c, dalloc(c.d_lz, (size_t)(6 * kMaxK + 8) * need_ld), "allocating Lanczos scalars");
   TRY_CUDA(c, dalloc(c.d_lzi, (size_t)3 * need_ld + 8), "allocating Lanczos state");
   TRY_CUDA(c, dalloc(c.d_xE, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
   TRY_CUDA(c, dalloc(c.d_xE32, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");

@@ -20,6 +20,7 @@ static unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) /
 // Lanczos scalar layout in Ctx::d_lz for C complex columns.
 struct LzView {
   double *nrm, *alpha, *beta, *yre, *yim, *eps, *red, *red2, *dt, *invb;
+  df32* wp;   // [kMaxK][C][2] combination weights nrm y_j as float32 pairs (re, im)
   int *active, *kused, *cap, *n_active;
 };
 static LzView lz_view(const Ctx& c, long long C) {
@@ -35,6 +36,7 @@ static LzView lz_view(const Ctx& c, long long C) {
   v.red2 = v.red + C;
   v.dt = v.red2 + C;
   v.invb = v.dt + C;
+  v.wp = reinterpret_cast<df32*>(v.invb + C);
   int* ib = c.d_lzi;
   v.active = ib;
   v.kused = ib + C;
@@ -152,6 +154,39 @@ __global__ void k_lz_update(double* __restrict__ W, const double* __restrict__ Q
     }
   }
   block_col_reduce(acc, f.col, f.ok, C, sred, out);
+}
+
+// The same update in float32 pairs on the FP32 pipe (the float64 form is bound by the FP64
+// pipe: 6 FMA per entry): inputs split exactly on the integer pipes, W written back as float64.
+__global__ void k_lz_update_pair(double* __restrict__ W, const double* __restrict__ Qj,
+                                 const double* __restrict__ Qjm1, long long n_rows, int C,
+                                 const int* __restrict__ active, const double* __restrict__ alpha,
+                                 const double* __restrict__ beta_prev, double* __restrict__ out) {
+  extern __shared__ double sred[];
+  FlatIter f = flat_iter(C);
+  df32 acc(0.0f);
+  if (f.ok && active[f.col]) {
+    const df32 a = split_f64(-alpha[f.col]);
+    const df32 b = split_f64(Qjm1 ? -beta_prev[f.col] : 0.0);
+    for (long long r = f.row0; r < n_rows; r += f.rstride) {
+      const long long o = r * 2 * C + 2 * f.col;
+      const double2 w = *reinterpret_cast<const double2*>(W + o);
+      const double2 q = *reinterpret_cast<const double2*>(Qj + o);
+      df32 wr = fma(a, split_f64(q.x), split_f64(w.x));
+      df32 wi = fma(a, split_f64(q.y), split_f64(w.y));
+      if (Qjm1) {
+        const double2 p = *reinterpret_cast<const double2*>(Qjm1 + o);
+        wr = fma(b, split_f64(p.x), wr);
+        wi = fma(b, split_f64(p.y), wi);
+      }
+      wr = fin(wr);
+      wi = fin(wi);
+      *reinterpret_cast<double2*>(W + o) = make_double2(to_f64<df32>(wr), to_f64<df32>(wi));
+      acc = fma(wr, wr, acc);
+      acc = fma(wi, wi, acc);
+    }
+  }
+  block_col_reduce(to_f64<df32>(fin(acc)), f.col, f.ok, C, sred, out);
 }
 
 // y = exp(-i dt T) e_1 for the real symmetric m x m tridiagonal T (diagonal al,
@@ -420,6 +455,75 @@ __global__ void __launch_bounds__(256) k_lz_combine(const double* __restrict__ Q
   *reinterpret_cast<double2*>(out + r * ld2 + 2 * col) = make_double2(n * re, n * im);
 }
 
+// Weights of the pair combination: wp[j][col] = split(nrm y_j) for j < kused, zero beyond.
+__global__ void k_lz_wpair(LzView v, int C, int K) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= K * C) return;
+  const int j = i / C, col = i % C;
+  const double w = j < v.kused[col] ? v.nrm[col] : 0.0;
+  v.wp[2 * i] = split_f64(w * v.yre[i]);
+  v.wp[2 * i + 1] = split_f64(w * v.yim[i]);
+}
+
+// out = sum_{j < kused} wp_j Q_j in float32 pairs on the FP32 pipe (the float64 form needs four
+// FP64 FMA per entry and basis vector and is bound by the FP64 pipe, not by HBM).
+__global__ void __launch_bounds__(256) k_lz_combine_pair(const double* __restrict__ Q, long long qstride,
+                                                         long long n_rows, int C, LzView v,
+                                                         double* __restrict__ out, long long ld2) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n_rows * C) return;
+  const long long r = idx / C;
+  const int col = (int)(idx % C);
+  const int k = v.kused[col];
+  const double2* q = reinterpret_cast<const double2*>(Q) + idx;
+  const long long qs = qstride / 2;
+  const float4* wp = reinterpret_cast<const float4*>(v.wp) + col;
+  df32 re(0.0f), im(0.0f);
+  int j = 0;
+  for (; j + 4 <= k; j += 4) {
+    double2 a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] = __ldcs(q + (long long)(j + u) * qs);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 w = wp[(long long)(j + u) * C];
+      const df32 wr(w.x, w.y), wi(w.z, w.w), mwi(-w.z, -w.w);
+      const df32 ar = split_f64(a[u].x), ai = split_f64(a[u].y);
+      re = fma(wr, ar, re);
+      re = fma(mwi, ai, re);
+      im = fma(wr, ai, im);
+      im = fma(wi, ar, im);
+    }
+  }
+  for (; j < k; ++j) {
+    const double2 a = __ldcs(q + (long long)j * qs);
+    const float4 w = wp[(long long)j * C];
+    const df32 wr(w.x, w.y), wi(w.z, w.w), mwi(-w.z, -w.w);
+    const df32 ar = split_f64(a.x), ai = split_f64(a.y);
+    re = fma(wr, ar, re);
+    re = fma(mwi, ai, re);
+    im = fma(wr, ai, im);
+    im = fma(wi, ar, im);
+  }
+  *reinterpret_cast<double2*>(out + r * ld2 + 2 * col) =
+      make_double2(to_f64<df32>(fin(re)), to_f64<df32>(fin(im)));
+}
+
+// The Krylov combination in the precision of the run: float64 for EFE_FP64, float32 pairs otherwise.
+static cudaError_t launch_combine(const Ctx& c, const LzView& v, long long n, long long C, double* out, long long ld2,
+                                  int precision, cudaStream_t s) {
+  if (precision == EFE_FP64) {
+    k_lz_combine<<<nblk(n * C), 256, 0, s>>>(c.d_Q, n * 2 * C, n, (int)C, v, out, ld2);
+    note_launch();
+  } else {
+    k_lz_wpair<<<nblk((long long)c.k_max * C), 256, 0, s>>>(v, (int)C, c.k_max);
+    note_launch();
+    k_lz_combine_pair<<<nblk(n * C), 256, 0, s>>>(c.d_Q, n * 2 * C, n, (int)C, v, out, ld2);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
 __global__ void k_lz_stats(LzView v, int C, int* __restrict__ stats_i, double* __restrict__ stats_d) {
   // stats_i: [max k, cap hits]; stats_d: [max eps]  (single block)
   __shared__ int smax, scap;
@@ -484,8 +588,13 @@ static cudaError_t kexp_body(Ctx& c, const double* in, double* out, int precisio
     EFE_CUDA_TRY(cudaMemsetAsync(v.n_active, 0, sizeof(int), s));
     k_lz_dot<<<rg, 256, rs, s>>>(Qj, W, n, (int)C, v.active, v.red);
     note_launch();
-    k_lz_update<<<rg, 256, rs, s>>>(W, Qj, j > 0 ? c.d_Q + (j - 1) * qstride : nullptr, n, (int)C, v.active, v.red,
-                                    j > 0 ? v.beta + (long long)(j - 1) * C : nullptr, v.red2);
+    if (precision == EFE_FP64)
+      k_lz_update<<<rg, 256, rs, s>>>(W, Qj, j > 0 ? c.d_Q + (j - 1) * qstride : nullptr, n, (int)C, v.active,
+                                      v.red, j > 0 ? v.beta + (long long)(j - 1) * C : nullptr, v.red2);
+    else
+      k_lz_update_pair<<<rg, 256, rs, s>>>(W, Qj, j > 0 ? c.d_Q + (j - 1) * qstride : nullptr, n, (int)C,
+                                           v.active, v.red, j > 0 ? v.beta + (long long)(j - 1) * C : nullptr,
+                                           v.red2);
     note_launch();
     k_lz_tri<<<(unsigned)C, 32, sizeof(double) * (4 * kMaxK + 4 + kMaxBessel), s>>>(v, (int)C, j, c.k_max, c.fixed_k,
                                                                             c.krylov_tol);
@@ -500,8 +609,7 @@ static cudaError_t kexp_body(Ctx& c, const double* in, double* out, int precisio
     }
   }
   c.apply_gate = nullptr;
-  k_lz_combine<<<nblk(n * C), 256, 0, s>>>(c.d_Q, qstride, n, (int)C, v, out, ld2);
-  note_launch();
+  EFE_CUDA_TRY(launch_combine(c, v, n, C, out, ld2, precision, s));
   int* d_si = v.n_active;   // reuse: [0] max k, [1] caps
   double* d_sd = v.red;
   k_lz_stats<<<1, 256, 0, s>>>(v, (int)C, d_si, d_sd);
@@ -577,9 +685,7 @@ cudaError_t run_kexp_recombine(Ctx& c, double* out, const double* h_dts, cudaStr
   EFE_CUDA_TRY(cudaMemcpyAsync(v.invb, h_dts, sizeof(double) * C, cudaMemcpyHostToDevice, s));
   k_lz_eval<<<(unsigned)C, 32, sizeof(double) * (4 * kMaxK + 4 + kMaxBessel), s>>>(v, (int)C, v.invb);
   note_launch();
-  k_lz_combine<<<nblk(n * C), 256, 0, s>>>(c.d_Q, n * 2 * C, n, (int)C, v, out, 2 * C);
-  note_launch();
-  return cudaGetLastError();
+  return launch_combine(c, v, n, C, out, 2 * C, c.precision == EFE_FP64 ? EFE_FP64 : EFE_PAIR, s);
 }
 
 // ---------------------------------------------------------------------------- density

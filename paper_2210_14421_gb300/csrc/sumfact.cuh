@@ -338,4 +338,26 @@ template <> __device__ __forceinline__ df32 from_f64<df32>(double x) {
 }
 template <> __device__ __forceinline__ double to_f64<df32>(df32 x) { return f32_to_f64(x.h) + f32_to_f64(x.l); }
 
+// x = h + l on the integer pipes, without rounding: h holds the leading 24 significant bits of x,
+// l the next 24 (truncated), so |x - (h + l)| < 2^-47 |x| for |x| > 1e-23; parts below the binary32
+// normal range are flushed to zero (absolute error < 1e-37), magnitudes beyond it become infinite.  One float64 value costs ~15 integer operations and no FP64-pipe work.
+__device__ __forceinline__ df32 split_f64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);                 // biased binary64 exponent
+  const unsigned mh = ((hi & 0xFFFFFu) << 3) | (lo >> 29);   // next 23 bits after the leading one
+  const unsigned rest = lo & 0x1FFFFFFFu;                    // the 29 bits below them
+  const int eh = e - 896;                                    // binary32 biased exponent of h
+  const float h = eh <= 0 ? 0.0f : __uint_as_float(sign | (eh < 255 ? ((unsigned)eh << 23) | mh : 0x7F800000u));
+  float l = 0.0f;
+  if (rest != 0u) {
+    const int pm = 31 - __clz((int)rest);                    // position of the leading one of rest
+    const unsigned m = pm <= 23 ? rest << (23 - pm) : rest >> (pm - 23);
+    const int el = pm + e - 948;                             // rest * 2^(e - 1075) in binary32
+    if (el > 0 && el < 255) l = __uint_as_float(sign | ((unsigned)el << 23) | (m & 0x7FFFFFu));
+  }
+  return df32(h, l);
+}
+
 }  // namespace efe
