@@ -61,9 +61,9 @@ typedef enum {
 typedef enum {
   EFE_FP64 = 0,   /* every step in float64 */
   EFE_MIXED = 1,  /* cell contraction and enrichment coupling in float32 with float32
-                     accumulation; the density interpolation, the Lanczos vector update
-                     and the Krylov combination in float32 pairs (as EFE_PAIR); gather/
-                     scatter accumulation, tridiagonal exponential, Hartree, norms and
+                     accumulation; the density interpolation and the Krylov combination
+                     in float32 pairs (as EFE_PAIR); gather/scatter accumulation,
+                     Lanczos recurrence, tridiagonal exponential, Hartree, norms and
                      dipole in float64; storage float64 */
   EFE_PAIR = 2    /* as EFE_MIXED, but every value of the cell contraction and the
                      enrichment coupling is a pair of float32 (h + l) with error-free

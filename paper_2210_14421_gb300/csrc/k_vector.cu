@@ -156,39 +156,6 @@ __global__ void k_lz_update(double* __restrict__ W, const double* __restrict__ Q
   block_col_reduce(acc, f.col, f.ok, C, sred, out);
 }
 
-// The same update in float32 pairs on the FP32 pipe (the float64 form is bound by the FP64
-// pipe: 6 FMA per entry): inputs split exactly on the integer pipes, W written back as float64.
-__global__ void k_lz_update_pair(double* __restrict__ W, const double* __restrict__ Qj,
-                                 const double* __restrict__ Qjm1, long long n_rows, int C,
-                                 const int* __restrict__ active, const double* __restrict__ alpha,
-                                 const double* __restrict__ beta_prev, double* __restrict__ out) {
-  extern __shared__ double sred[];
-  FlatIter f = flat_iter(C);
-  df32 acc(0.0f);
-  if (f.ok && active[f.col]) {
-    const df32 a = split_f64(-alpha[f.col]);
-    const df32 b = split_f64(Qjm1 ? -beta_prev[f.col] : 0.0);
-    for (long long r = f.row0; r < n_rows; r += f.rstride) {
-      const long long o = r * 2 * C + 2 * f.col;
-      const double2 w = *reinterpret_cast<const double2*>(W + o);
-      const double2 q = *reinterpret_cast<const double2*>(Qj + o);
-      df32 wr = fma(a, split_f64(q.x), split_f64(w.x));
-      df32 wi = fma(a, split_f64(q.y), split_f64(w.y));
-      if (Qjm1) {
-        const double2 p = *reinterpret_cast<const double2*>(Qjm1 + o);
-        wr = fma(b, split_f64(p.x), wr);
-        wi = fma(b, split_f64(p.y), wi);
-      }
-      wr = fin(wr);
-      wi = fin(wi);
-      *reinterpret_cast<double2*>(W + o) = make_double2(to_f64<df32>(wr), to_f64<df32>(wi));
-      acc = fma(wr, wr, acc);
-      acc = fma(wi, wi, acc);
-    }
-  }
-  block_col_reduce(to_f64<df32>(fin(acc)), f.col, f.ok, C, sred, out);
-}
-
 // y = exp(-i dt T) e_1 for the real symmetric m x m tridiagonal T (diagonal al,
 // off-diagonal be[0..m-2]) of one column, by one warp; y goes to v.yre/v.yim
 // and its last component to u0[0] (re) and u1[0] (im).
@@ -588,13 +555,8 @@ static cudaError_t kexp_body(Ctx& c, const double* in, double* out, int precisio
     EFE_CUDA_TRY(cudaMemsetAsync(v.n_active, 0, sizeof(int), s));
     k_lz_dot<<<rg, 256, rs, s>>>(Qj, W, n, (int)C, v.active, v.red);
     note_launch();
-    if (precision == EFE_FP64)
-      k_lz_update<<<rg, 256, rs, s>>>(W, Qj, j > 0 ? c.d_Q + (j - 1) * qstride : nullptr, n, (int)C, v.active,
-                                      v.red, j > 0 ? v.beta + (long long)(j - 1) * C : nullptr, v.red2);
-    else
-      k_lz_update_pair<<<rg, 256, rs, s>>>(W, Qj, j > 0 ? c.d_Q + (j - 1) * qstride : nullptr, n, (int)C,
-                                           v.active, v.red, j > 0 ? v.beta + (long long)(j - 1) * C : nullptr,
-                                           v.red2);
+    k_lz_update<<<rg, 256, rs, s>>>(W, Qj, j > 0 ? c.d_Q + (j - 1) * qstride : nullptr, n, (int)C, v.active, v.red,
+                                    j > 0 ? v.beta + (long long)(j - 1) * C : nullptr, v.red2);
     note_launch();
     k_lz_tri<<<(unsigned)C, 32, sizeof(double) * (4 * kMaxK + 4 + kMaxBessel), s>>>(v, (int)C, j, c.k_max, c.fixed_k,
                                                                             c.krylov_tol);
