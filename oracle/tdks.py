@@ -14,6 +14,12 @@ Readings (the paper defers the predictor-corrector to its references):
   S4  v_mid   = v_N + v_H[rho_mid] + v_xc[rho_mid] - E(t_n + dt/2) . x
   S5  psi_n+1 = Kexp(Hbar[v_mid]) psi_n
   S6  rho_n+1, v_H[rho_n+1], v_xc[rho_n+1] (reused by the next S1), mu(t_n+1)
+Potential-extrapolation variant (scheme "extrapolated", one exponential per
+step): the Hartree + xc potential at the mid-point is the linear
+extrapolation from the two latest steps, v_Hxc(t_n + dt/2) ~
+(3 v_Hxc(t_n) - v_Hxc(t_n-1)) / 2, and psi_n+1 = Kexp(Hbar[v_N + v_Hxc +
+v_f(t_n + dt/2)]) psi_n; a step without history (the first of a run) is a
+predictor-corrector step.  Both schemes are second order in dt (pinned).
 v_N = -sum Z_I / |x - R_I| is evaluated in closed form at the quadrature
 points (the nuclear Poisson problem with point sources needs the
 electrostatic enrichment, which is not used).  Eq. VField: v_f = -E(t) . x.
@@ -89,22 +95,23 @@ class State:
     vH: np.ndarray     # (batch, n_cells, nq)
     vxc: np.ndarray    # (batch, n_cells, nq)
     phi: np.ndarray    # (batch, n_h) nodal Hartree potential
+    vhxc_prev: np.ndarray = None   # v_H + v_xc of the previous step (None: no history)
 
 
-def potentials(system: System, rho: np.ndarray):
+def potentials(system: System, rho: np.ndarray, xc_kind: str = "pw92"):
     """v_H and v_xc for a batch of densities."""
     vH = np.zeros_like(rho)
     vxc = np.zeros_like(rho)
     phi = np.zeros((rho.shape[0], system.n_h))
     for b in range(rho.shape[0]):
         phi[b], vH[b] = poisson.solve(system, rho[b])
-        vxc[b] = xc.lda(rho[b])[1]
+        vxc[b] = xc.lda(rho[b], xc_kind)[1]
     return vH, vxc, phi
 
 
-def make_state(system: System, psi_bar: np.ndarray, occ: np.ndarray, batch: int) -> State:
+def make_state(system: System, psi_bar: np.ndarray, occ: np.ndarray, batch: int, xc_kind: str = "pw92") -> State:
     rho = density(system, psi_bar, occ, batch)
-    vH, vxc, phi = potentials(system, rho)
+    vH, vxc, phi = potentials(system, rho, xc_kind)
     return State(rho=rho, vH=vH, vxc=vxc, phi=phi)
 
 
@@ -124,22 +131,33 @@ def kexp_members(system: System, psi_bar, v_members, n_orb, dt, tol, k_max, fixe
 
 
 def magnus_step(system: System, psi_bar: np.ndarray, state: State, t: float, dt: float, fields, occ,
-                tol: float, k_max: int, fixed_k: int = 0, vN=None):
-    """One predictor-corrector step S1..S6; returns (psi_new, state_new, mu
+                tol: float, k_max: int, fixed_k: int = 0, vN=None, scheme: str = "pc", xc_kind: str = "pw92"):
+    """One step: predictor-corrector S1..S6 (scheme "pc"), or the
+    potential-extrapolation step (scheme "extrapolated"; predictor-corrector
+    while the state has no history).  Returns (psi_new, state_new, mu
     (batch, 3), info dict)."""
     batch = len(fields)
     n_orb = len(occ)
     if vN is None:
         vN = nuclear_potential(system)
     Emid = [field_value(f, t + 0.5 * dt) for f in fields]
-    v1 = [vN + state.vH[b] + state.vxc[b] + field_potential(system, Emid[b]) for b in range(batch)]
-    psi_p, k1 = kexp_members(system, psi_bar, v1, n_orb, dt, tol, k_max, fixed_k)
-    rho_p = density(system, psi_p, occ, batch)
-    rho_mid = 0.5 * (state.rho + rho_p)
-    vH_mid, vxc_mid, _ = potentials(system, rho_mid)
-    v2 = [vN + vH_mid[b] + vxc_mid[b] + field_potential(system, Emid[b]) for b in range(batch)]
+    vhxc = state.vH + state.vxc
+    if scheme == "extrapolated" and state.vhxc_prev is not None:
+        vx = 1.5 * vhxc - 0.5 * state.vhxc_prev
+        v2 = [vN + vx[b] + field_potential(system, Emid[b]) for b in range(batch)]
+        k1 = np.zeros(0, dtype=int)
+    elif scheme in ("pc", "extrapolated"):
+        v1 = [vN + vhxc[b] + field_potential(system, Emid[b]) for b in range(batch)]
+        psi_p, k1 = kexp_members(system, psi_bar, v1, n_orb, dt, tol, k_max, fixed_k)
+        rho_p = density(system, psi_p, occ, batch)
+        rho_mid = 0.5 * (state.rho + rho_p)
+        vH_mid, vxc_mid, _ = potentials(system, rho_mid, xc_kind)
+        v2 = [vN + vH_mid[b] + vxc_mid[b] + field_potential(system, Emid[b]) for b in range(batch)]
+    else:
+        raise ValueError("unknown scheme")
     psi_new, k2 = kexp_members(system, psi_bar, v2, n_orb, dt, tol, k_max, fixed_k)
-    new_state = make_state(system, psi_new, occ, batch)
+    new_state = make_state(system, psi_new, occ, batch, xc_kind)
+    new_state.vhxc_prev = vhxc
     mu = np.stack([dipole(system, new_state.rho[b]) for b in range(batch)])
     return psi_new, new_state, mu, {"k_pred": k1, "k_corr": k2}
 
