@@ -138,7 +138,16 @@ typedef struct {
                                  device, no host synchronisation; captured on the second call for a
                                  given buffer set, the first call runs and autotunes eagerly).
                                  Must be 0 if the caller itself captures efe_magnus_step. */
+  int32_t xc;                 /* EFE_XC_PW92 (Slater + Perdew-Wang 1992) or EFE_XC_PZ81 (Slater +
+                                 Perdew-Zunger 1981 fit of Ceperley-Alder, the paper's functional) */
+  int32_t scheme;             /* EFE_STEP_PC: predictor-corrector (two exponentials per step);
+                                 EFE_STEP_EXTRAPOLATED: v_Hxc at the mid-point extrapolated
+                                 linearly from the last two steps, one exponential per step (the
+                                 first step after set-up, a kick or a reset is predictor-corrector) */
 } efe_options;
+
+enum { EFE_XC_PW92 = 0, EFE_XC_PZ81 = 1 };
+enum { EFE_STEP_PC = 0, EFE_STEP_EXTRAPOLATED = 1 };
 
 /* Hartree solvers for the same discrete system (Eq. DiscretePoisson):
  * FDM  - direct solve by fast diagonalisation of the Kronecker-sum stiffness of
@@ -292,12 +301,13 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
  * psi0_dev: device [n_dof][n_orb] complex128 (not modified).  field_host: kind
  * EFE_FIELD_GAUSS or EFE_FIELD_SINE_GAUSS with sigma > 0; direction_host: host
  * double[3] (d).  J_host: receives J; grad_host: host double[3].  The context
- * needs batch = 1; the Lanczos tolerance and k_max of its options apply, and
+ * needs batch = 1, xc = EFE_XC_PW92 and scheme = EFE_STEP_PC; the Lanczos
+ * tolerance and k_max of its options apply, and
  * its state is invalidated (the next efe_magnus_step recomputes rho).  Allocates
  * device memory per call and synchronises `stream`.  Returns EFE_WARN_KRYLOV_CAP
  * (J and grad written) if any exponential stopped at k_max.  Errors: EFE_ERR_ARG
  * (bad sizes, window outside [1, n_steps], n_quad_s outside [1, 64], batch != 1,
- * unsupported field), EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+ * another functional or step scheme, unsupported field), EFE_ERR_NOMEM, EFE_ERR_CUDA. */
 efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_steps, double dt,
                               const efe_field* field_host, const double* direction_host, int32_t window_first,
                               int32_t window_last, int32_t checkpoint_every, int32_t n_quad_s, double* J_host,

@@ -15,6 +15,8 @@ EFE_OK, EFE_ERR_ARG, EFE_ERR_NOMEM, EFE_ERR_CUDA, EFE_ERR_NOT_SPD = 0, 1, 2, 3, 
 EFE_WARN_KRYLOV_CAP, EFE_ERR_CG_NOCONV, EFE_ERR_TIMEOUT, EFE_ERR_STATE = 5, 6, 7, 8
 EFE_FP64, EFE_MIXED, EFE_PAIR = 0, 1, 2
 EFE_HARTREE_FDM, EFE_HARTREE_PCG = 0, 1
+EFE_XC_PW92, EFE_XC_PZ81 = 0, 1
+EFE_STEP_PC, EFE_STEP_EXTRAPOLATED = 0, 1
 STATUS_NAMES = {0: "EFE_OK", 1: "EFE_ERR_ARG", 2: "EFE_ERR_NOMEM", 3: "EFE_ERR_CUDA", 4: "EFE_ERR_NOT_SPD",
                 5: "EFE_WARN_KRYLOV_CAP", 6: "EFE_ERR_CG_NOCONV", 7: "EFE_ERR_TIMEOUT", 8: "EFE_ERR_STATE"}
 
@@ -53,7 +55,7 @@ class Options(C.Structure):
     _fields_ = [("n_orb", C.c_int32), ("batch", C.c_int32), ("occ_host", C.POINTER(C.c_double)),
                 ("krylov_tol", C.c_double), ("k_max", C.c_int32), ("fixed_k", C.c_int32), ("cg_tol", C.c_double),
                 ("cg_max_it", C.c_int32), ("precision", C.c_int32), ("hartree_method", C.c_int32),
-                ("use_graphs", C.c_int32)]
+                ("use_graphs", C.c_int32), ("xc", C.c_int32), ("scheme", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -150,7 +152,7 @@ class Context:
 
     def __init__(self, wl, precision: int = EFE_FP64, krylov_tol=None, k_max=None, fixed_k: int = 0,
                  cg_tol: float = 1e-12, cg_max_it: int = 5000, hartree_method: int = EFE_HARTREE_FDM,
-                 use_graphs: bool = False):
+                 use_graphs: bool = False, xc: int = EFE_XC_PW92, scheme: int = EFE_STEP_PC):
         L = lib()
         self.wl = wl
         self._keep = []
@@ -173,7 +175,7 @@ class Context:
         opts = Options(int(wl.n_orb), int(wl.batch), _dptr(occ),
                        float(wl.krylov_tol if krylov_tol is None else krylov_tol),
                        int(wl.k_max if k_max is None else k_max), int(fixed_k), float(cg_tol), int(cg_max_it),
-                       int(precision), int(hartree_method), int(bool(use_graphs)))
+                       int(precision), int(hartree_method), int(bool(use_graphs)), int(xc), int(scheme))
         h = C.c_void_p()
         st = L.efe_setup(C.byref(mesh), atoms, na, C.byref(enr), C.byref(opts), C.byref(h))
         if st != EFE_OK:

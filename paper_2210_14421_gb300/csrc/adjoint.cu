@@ -517,6 +517,7 @@ efe_status adjoint_dipole(Ctx& c, const double* psi0, int n_steps, double dt, co
   }
   c.use_graphs = graphs;
   c.state_valid = false;
+  c.has_prev = false;
   c.op.valid = false;
   return st;
 }

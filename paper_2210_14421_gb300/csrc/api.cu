@@ -58,7 +58,7 @@ Ctx::~Ctx() {
   for (int a = 0; a < 3; ++a) { dfree(d_fdmV[a]); dfree(d_fdmL[a]); }
   dfree(d_fdmT);
   dfree(op.W64); dfree(op.W32); dfree(op.E64); dfree(op.E32); dfree(op.W2); dfree(op.E2); dfree(op.HEE);
-  dfree(d_rho); dfree(d_vH); dfree(d_vxc); dfree(d_Q); dfree(d_psi_p); dfree(d_xE); dfree(d_yE);
+  dfree(d_rho); dfree(d_vH); dfree(d_vxc); dfree(d_vprev); dfree(d_Q); dfree(d_psi_p); dfree(d_xE); dfree(d_yE);
   dfree(d_lz); dfree(d_lzi); dfree(d_rho2); dfree(d_v); dfree(d_cg); dfree(d_red);
   for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
   for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
@@ -114,6 +114,7 @@ static efe_status ensure_batch_buffers(Ctx& c) {
   if (c.d_rho) return EFE_OK;
   const size_t nqb = (size_t)c.batch * c.nc * c.nq;
   TRY_CUDA(c, dalloc(c.d_rho, nqb), "allocating densities");
+  TRY_CUDA(c, dalloc(c.d_vprev, nqb), "allocating the potential history");
   TRY_CUDA(c, dalloc(c.d_vH, nqb), "allocating potentials");
   TRY_CUDA(c, dalloc(c.d_vxc, nqb), "allocating potentials");
   TRY_CUDA(c, dalloc(c.d_rho2, nqb), "allocating densities");
@@ -184,6 +185,8 @@ static bool validate(const efe_mesh_desc* mesh, const efe_atom* atoms, int n_ato
     why = "unknown precision";
     return false;
   }
+  if (o->xc != EFE_XC_PW92 && o->xc != EFE_XC_PZ81) { why = "unknown xc"; return false; }
+  if (o->scheme != EFE_STEP_PC && o->scheme != EFE_STEP_EXTRAPOLATED) { why = "unknown step scheme"; return false; }
   if (o->hartree_method != EFE_HARTREE_FDM && o->hartree_method != EFE_HARTREE_PCG) {
     why = "unknown Hartree method";
     return false;
@@ -229,6 +232,8 @@ static efe_status setup_impl(Ctx& c, const efe_mesh_desc* mesh, const efe_atom* 
   c.cg_max_it = o->cg_max_it > 0 ? o->cg_max_it : 2000;
   c.precision = o->precision;
   c.hartree_method = o->hartree_method;
+  c.xc = o->xc;
+  c.scheme = o->scheme;
   c.use_graphs = o->use_graphs != 0;
 
   // reference tables
@@ -477,25 +482,34 @@ static efe_status magnus_impl(Ctx& c, double* psi, double t, double dt, const ef
   std::vector<double> E;
   field_vectors(c, fields, t + 0.5 * dt, E);
   std::vector<double> dts((size_t)C, dt);
-  // S1: predictor with v(rho_n) and the mid-point field
-  TRY_CUDA(c, launch_potential_sum(c, c.d_vH, c.d_vxc, E.data(), true, c.d_v, s), "potential");
-  st = build_op(c, c.d_v, c.batch, 1.0, s);
-  if (st != EFE_OK) return st;
   int k1 = 0, cap1 = 0, k2 = 0, cap2 = 0;
   double e1 = 0.0, e2 = 0.0;
   const bool stats = info != nullptr;
-  TRY_CUDA(c, run_kexp_cols(c, psi, c.d_psi_p, dts.data(), c.precision, &k1, &cap1, &e1, s, stats), "predictor");
-  // S2, S3: rho_mid = (rho_n + rho^p) / 2
-  TRY_CUDA(c, launch_density(c, c.d_psi_p, c.d_rho2, s), "density");
   const long long nqb = (long long)c.batch * c.nc * c.nq;
-  TRY_CUDA(c, launch_axpby(c.d_rho2, c.d_rho, c.d_rho2, 0.5, 0.5, nqb, s), "mid-point density");
-  // S4: v_mid
-  TRY_CUDA(c, launch_lda(c, c.d_rho2, c.d_vxc, nullptr, nqb, s), "LDA");
-  int its = 0;
-  st = run_hartree(c, c.d_rho2, c.d_vH, c.cg_tol, c.cg_max_it, &its, s);
-  cg_its += its;
-  if (st == EFE_ERR_CG_NOCONV) warn = st; else if (st != EFE_OK) return st;
-  TRY_CUDA(c, launch_potential_sum(c, c.d_vH, c.d_vxc, E.data(), true, c.d_v, s), "potential");
+  if (c.scheme == EFE_STEP_EXTRAPOLATED && c.has_prev) {
+    // v_mid = v_N + (3 v_Hxc(t_n) - v_Hxc(t_n-1)) / 2 - E(t_n + dt/2) . x, then keep v_Hxc(t_n)
+    TRY_CUDA(c, launch_axpby(c.d_rho2, c.d_vH, c.d_vxc, 1.5, 1.5, nqb, s), "extrapolation");
+    TRY_CUDA(c, launch_axpby(c.d_rho2, c.d_rho2, c.d_vprev, 1.0, -0.5, nqb, s), "extrapolation");
+    TRY_CUDA(c, launch_potential_sum(c, c.d_rho2, nullptr, E.data(), true, c.d_v, s), "potential");
+    TRY_CUDA(c, launch_axpby(c.d_vprev, c.d_vH, c.d_vxc, 1.0, 1.0, nqb, s), "potential history");
+  } else {
+    TRY_CUDA(c, launch_axpby(c.d_vprev, c.d_vH, c.d_vxc, 1.0, 1.0, nqb, s), "potential history");
+    // S1: predictor with v(rho_n) and the mid-point field
+    TRY_CUDA(c, launch_potential_sum(c, c.d_vH, c.d_vxc, E.data(), true, c.d_v, s), "potential");
+    st = build_op(c, c.d_v, c.batch, 1.0, s);
+    if (st != EFE_OK) return st;
+    TRY_CUDA(c, run_kexp_cols(c, psi, c.d_psi_p, dts.data(), c.precision, &k1, &cap1, &e1, s, stats), "predictor");
+    // S2, S3: rho_mid = (rho_n + rho^p) / 2
+    TRY_CUDA(c, launch_density(c, c.d_psi_p, c.d_rho2, s), "density");
+    TRY_CUDA(c, launch_axpby(c.d_rho2, c.d_rho, c.d_rho2, 0.5, 0.5, nqb, s), "mid-point density");
+    // S4: v_mid
+    TRY_CUDA(c, launch_lda(c, c.d_rho2, c.d_vxc, nullptr, nqb, s), "LDA");
+    int its = 0;
+    st = run_hartree(c, c.d_rho2, c.d_vH, c.cg_tol, c.cg_max_it, &its, s);
+    cg_its += its;
+    if (st == EFE_ERR_CG_NOCONV) warn = st; else if (st != EFE_OK) return st;
+    TRY_CUDA(c, launch_potential_sum(c, c.d_vH, c.d_vxc, E.data(), true, c.d_v, s), "potential");
+  }
   st = build_op(c, c.d_v, c.batch, 1.0, s);
   if (st != EFE_OK) return st;
   // S5: corrector from psi_n, written in place
@@ -504,6 +518,7 @@ static efe_status magnus_impl(Ctx& c, double* psi, double t, double dt, const ef
   c.state_valid = false;
   st = compute_state(c, psi, &cg_its, s);
   if (st == EFE_ERR_CG_NOCONV) warn = st; else if (st != EFE_OK) return st;
+  c.has_prev = true;
   if (mu) TRY_CUDA(c, launch_dipole(c, c.d_rho, mu, s), "dipole");
   if (info) {
     TRY_CUDA(c, cudaStreamSynchronize(s), "step");
@@ -614,6 +629,7 @@ efe_status efe_magnus_step(efe_ctx* ctx, double* psi_bar_dev, double t, double d
 efe_status efe_reset_state(efe_ctx* ctx) {
   CHECK_CTX(ctx);
   ctx->c.state_valid = false;
+  ctx->c.has_prev = false;
   return EFE_OK;
 }
 
@@ -670,6 +686,7 @@ efe_status efe_kick(efe_ctx* ctx, double* psi_bar_dev, const efe_field* fields_h
   double e = 0.0;
   TRY_CUDA(c, run_kexp_cols(c, psi_bar_dev, psi_bar_dev, dts.data(), EFE_FP64, &k, &cap, &e, s), "kick");
   c.state_valid = false;
+  c.has_prev = false;
   c.op.valid = false;
   return cap > 0 ? EFE_WARN_KRYLOV_CAP : EFE_OK;
 }
@@ -699,6 +716,7 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
   dfree(dc); dfree(de); dfree(dk); dfree(dn);
   if (e != cudaSuccess) return cuda_fail(c, e, "initial orbitals");
   c.state_valid = false;
+  c.has_prev = false;
   return EFE_OK;
 }
 
@@ -716,6 +734,10 @@ efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_st
   }
   if (c.batch != 1) {
     c.err = "efe_adjoint_dipole needs a context with batch = 1";
+    return EFE_ERR_ARG;
+  }
+  if (c.xc != EFE_XC_PW92 || c.scheme != EFE_STEP_PC) {
+    c.err = "efe_adjoint_dipole differentiates the predictor-corrector step with the PW92 functional";
     return EFE_ERR_ARG;
   }
   if ((field_host->kind != EFE_FIELD_GAUSS && field_host->kind != EFE_FIELD_SINE_GAUSS) || !(field_host->sigma > 0.0)) {

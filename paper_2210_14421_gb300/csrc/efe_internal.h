@@ -119,6 +119,8 @@ struct Ctx {
   int cg_max_it = 2000;
   int precision = EFE_FP64;
   int hartree_method = EFE_HARTREE_FDM;
+  int xc = EFE_XC_PW92;
+  int scheme = EFE_STEP_PC;
   // device tables
   double* d_geo = nullptr;     // x0 (ncx+ncy+ncz) then h (ncx+ncy+ncz)
   double* d_Dsc = nullptr;     // [n_h] mask / sqrt(M)
@@ -175,6 +177,8 @@ struct Ctx {
   float tile_ms[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   // state (density-derived potentials of the current step)
   bool state_valid = false;
+  bool has_prev = false;       // d_vprev holds v_H + v_xc of the previous step
+  double* d_vprev = nullptr;   // [batch][nc][nq]
   double* d_rho = nullptr;     // [batch][nc][nq]
   double* d_vH = nullptr;
   double* d_vxc = nullptr;

@@ -759,7 +759,10 @@ cudaError_t launch_density(Ctx& c, const double* psi, double* rho, cudaStream_t 
 }
 
 // ---------------------------------------------------------------------------- LDA
-__global__ void k_lda(const double* __restrict__ rho, double* __restrict__ vxc, double* __restrict__ exc, long long n) {
+// Slater exchange plus PW92 (kind EFE_XC_PW92) or Perdew-Zunger 1981 (EFE_XC_PZ81)
+// unpolarised correlation; zero below rho = 1e-14.
+__global__ void k_lda(const double* __restrict__ rho, double* __restrict__ vxc, double* __restrict__ exc, long long n,
+                      int kind) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double r = rho[i];
@@ -768,15 +771,29 @@ __global__ void k_lda(const double* __restrict__ rho, double* __restrict__ vxc, 
     const double pi = 3.14159265358979323846;
     const double c13 = cbrt(3.0 * r / pi);
     const double ex = -0.75 * c13, vx = -c13;
-    // Perdew-Wang 1992 unpolarised correlation
-    const double A = 0.031091, a1 = 0.21370, b1 = 7.5957, b2 = 3.5876, b3 = 1.6382, b4 = 0.49294;
     const double rs = cbrt(3.0 / (4.0 * pi * r));
     const double srs = sqrt(rs);
-    const double Q = 2.0 * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs);
-    const double dQ = 2.0 * A * (0.5 * b1 / srs + b2 + 1.5 * b3 * srs + 2.0 * b4 * rs);
-    const double lg = log1p(1.0 / Q);
-    const double ec = -2.0 * A * (1.0 + a1 * rs) * lg;
-    const double dec = -2.0 * A * a1 * lg + 2.0 * A * (1.0 + a1 * rs) * dQ / (Q * (Q + 1.0));
+    double ec, dec;
+    if (kind == EFE_XC_PZ81) {
+      if (rs >= 1.0) {
+        const double g = -0.1423, b1 = 1.0529, b2 = 0.3334;
+        const double den = 1.0 + b1 * srs + b2 * rs;
+        ec = g / den;
+        dec = -g * (0.5 * b1 / srs + b2) / (den * den);
+      } else {
+        const double A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
+        const double lr = log(rs);
+        ec = A * lr + B + C * rs * lr + D * rs;
+        dec = A / rs + C * (lr + 1.0) + D;
+      }
+    } else {
+      const double A = 0.031091, a1 = 0.21370, b1 = 7.5957, b2 = 3.5876, b3 = 1.6382, b4 = 0.49294;
+      const double Q = 2.0 * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs);
+      const double dQ = 2.0 * A * (0.5 * b1 / srs + b2 + 1.5 * b3 * srs + 2.0 * b4 * rs);
+      const double lg = log1p(1.0 / Q);
+      ec = -2.0 * A * (1.0 + a1 * rs) * lg;
+      dec = -2.0 * A * a1 * lg + 2.0 * A * (1.0 + a1 * rs) * dQ / (Q * (Q + 1.0));
+    }
     const double vc = ec - rs / 3.0 * dec;
     e = ex + ec;
     v = vx + vc;
@@ -786,7 +803,7 @@ __global__ void k_lda(const double* __restrict__ rho, double* __restrict__ vxc, 
 }
 
 cudaError_t launch_lda(const Ctx& c, const double* rho, double* vxc, double* exc, long long n, cudaStream_t s) {
-  k_lda<<<nblk(n), 256, 0, s>>>(rho, vxc, exc, n);
+  k_lda<<<nblk(n), 256, 0, s>>>(rho, vxc, exc, n, c.xc);
   note_launch();
   return cudaGetLastError();
 }
