@@ -447,10 +447,10 @@ def run_efe(args):
             "setup_s": round(t_setup, 2), "initial_state": prep,
             "autotune": {"mixed": ctx.tuning(EFE_MIXED), "pair": ctx.tuning(EFE_PAIR), "fp64": ctx.tuning(EFE_FP64)}}
 
-    def side_run(prec_code, timed_steps, n_cmp):
-        """The same steps from the same kicked state at another precision: the dipoles of
-        the first n_cmp steps and the device time per step of timed_steps more."""
-        cs = Context(wl, precision=prec_code, cg_tol=1e-10, cg_max_it=20000)
+    def side_run(prec_code, timed_steps, n_cmp, scheme=0):
+        """The same steps from the same kicked state at another precision (or step scheme): the
+        dipoles of the first n_cmp steps and the device time per step of timed_steps more."""
+        cs = Context(wl, precision=prec_code, cg_tol=1e-10, cg_max_it=20000, scheme=scheme)
         ps = psi_start.clone()
         mus, ts, first = [], 0.0, None
         while len(mus) < n_cmp:
@@ -486,6 +486,15 @@ def run_efe(args):
                                         "first_step": first32,
                                         "note": "EFE_MIXED: float32 contraction; not the headline because its "
                                                 "dipole error exceeds the bound on this workload"}
+        # the potential-extrapolation variant of the step (one exponential per step; not the paper's
+        # predictor-corrector, so not the headline): its time per step and its dipole deviation
+        # from the predictor-corrector run over the same first steps
+        mse, muse, _ = side_run(prec, args.fp64_steps, n_cmp, scheme=1)
+        dse = float(np.max(np.abs(muse - np.array(mus_mixed[:n_cmp]))))
+        line["extrapolated_scheme"] = {"steps_per_s": round(1000.0 / mse, 4), "ms_per_step": round(mse, 1),
+                                       "steps": args.fp64_steps, "dipole_diff_vs_pc": dse, "compared_steps": n_cmp,
+                                       "note": "EFE_STEP_EXTRAPOLATED: v_Hxc at the mid-point extrapolated from the "
+                                               "last two steps, one exponential per step (second order, as PC)"}
 
     # end to end through the public API with host buffers: H2D of the orbital
     # block from pinned memory, the step, D2H of the dipole, every step
