@@ -313,6 +313,30 @@ efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_st
                               int32_t window_last, int32_t checkpoint_every, int32_t n_quad_s, double* J_host,
                               double* grad_host, void* stream);
 
+/* Spectra of dipole traces (Sec. Results: the absorption spectrum of the weak
+ * perturbation study and the power spectrum of the high-harmonic study); no
+ * context needed.  Samples at t_n = n dt, n = 0 .. n_t - 1, on the device;
+ * time integrals by the trapezoid rule, F[f](w) = dt sum_n c_n f_n e^{i w t_n}
+ * with c_0 = c_{n_t-1} = 1/2.  omega_dev: n_omega frequencies (a.u.).
+ *
+ * Absorption: S(w) = (4 w / (3 pi)) sum_j Im alpha_jj(w) with
+ * alpha_jj = F[e^{-t/tau} (mu_j^(j)(t) - mu_j^(j)(0))] / F[E_0], mu^(j) the trace of
+ * the run perturbed along axis j, read at mu_dev[j * stride_dir + n * stride_t + j]
+ * (the j-th dipole component); F[E_0] from the n_t field samples field_dev, or
+ * equal to kick (a delta kick of that strength) when field_dev is NULL.
+ *
+ * Power: P(w) = |dt sum_{n=1}^{n_t-2} e^{-i w t_n} a_n e^{-t_n^2/tau}|^2 with a_n the
+ * central second difference of mu_dev[n * stride_t] (the dipole acceleration).
+ *
+ * Outputs S_dev / P_dev: n_omega doubles.  Errors: EFE_ERR_ARG (NULL pointers,
+ * too few samples, dt or tau not positive, no field and kick 0), EFE_ERR_CUDA;
+ * the message is read with efe_last_error(NULL). */
+efe_status efe_absorption_spectrum(const double* mu_dev, int64_t n_t, int64_t stride_dir, int64_t stride_t, double dt,
+                                   const double* field_dev, double kick, const double* omega_dev, int64_t n_omega,
+                                   double tau, double* S_dev, void* stream);
+efe_status efe_power_spectrum(const double* mu_dev, int64_t n_t, int64_t stride_t, double dt, const double* omega_dev,
+                              int64_t n_omega, double tau, double* P_dev, void* stream);
+
 /* Diagnostics (not part of the method).  efe_profile(ctx, 1) synchronises the
  * device, resets a process-wide counter of kernel launches made by the library,
  * and from then on brackets every launch of the cell-apply kernel with a pair of

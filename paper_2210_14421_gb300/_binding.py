@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "EFE_OK", 1: "EFE_ERR_ARG", 2: "EFE_ERR_NOMEM", 3: "EFE_ERR_C
 EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coords", "efe_set_potential",
             "efe_apply_H", "efe_magnus_step", "efe_reset_state", "efe_density_vxc", "efe_hartree", "efe_dipole",
             "efe_kick", "efe_init_orbitals", "efe_profile", "efe_profile_read", "efe_selftest",
-            "efe_apply_H_noalloc", "efe_tuning", "efe_adjoint_dipole"]
+            "efe_apply_H_noalloc", "efe_tuning", "efe_adjoint_dipole",
+            "efe_absorption_spectrum", "efe_power_spectrum"]
 
 
 class MeshDesc(C.Structure):
@@ -98,6 +99,8 @@ def lib(path: str = LIB_PATH):
     L.efe_selftest.argtypes = [i64, C.POINTER(i64)]
     L.efe_tuning.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.efe_profile_read.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl)]
+    L.efe_absorption_spectrum.argtypes = [vp, i64, i64, i64, dbl, vp, dbl, vp, i64, dbl, vp, vp]
+    L.efe_power_spectrum.argtypes = [vp, i64, i64, dbl, vp, i64, dbl, vp, vp]
     L.efe_adjoint_dipole.argtypes = [vp, vp, i32, dbl, C.POINTER(Field), pdbl, i32, i32, i32, i32, C.POINTER(dbl),
                                      pdbl, vp]
     for name in EXPORTED:
@@ -145,6 +148,33 @@ def fields_array(fields):
             arr[i].dir[k] = float(f.direction[k])
         arr[i].kick = float(f.kick)
     return arr
+
+
+def absorption_spectrum(mu, dt, omegas, tau, field=None, kick=None):
+    """S(w) from three dipole traces on the device: mu[j, n, k] = component k of the
+    dipole at t = n dt of the run perturbed along axis j (float64, any strides with
+    the component innermost); field: E_0 samples [n_t] or None with kick."""
+    import torch
+    assert mu.dtype == torch.float64 and mu.is_cuda and mu.dim() == 3 and mu.shape[0] == 3 and mu.stride(2) == 1
+    out = torch.empty(omegas.shape[0], dtype=torch.float64, device=mu.device)
+    st = lib().efe_absorption_spectrum(_ptr(mu), int(mu.shape[1]), int(mu.stride(0)), int(mu.stride(1)), float(dt),
+                                       _ptr(field), float(kick or 0.0), _ptr(omegas), int(omegas.shape[0]),
+                                       float(tau), _ptr(out), _stream())
+    if st != EFE_OK:
+        raise EfeError(st, lib().efe_last_error(None).decode())
+    return out
+
+
+def power_spectrum(mu_x, dt, omegas, tau):
+    """P(w) of the dipole acceleration from one trace mu_x[n] on the device."""
+    import torch
+    assert mu_x.dtype == torch.float64 and mu_x.is_cuda and mu_x.dim() == 1
+    out = torch.empty(omegas.shape[0], dtype=torch.float64, device=mu_x.device)
+    st = lib().efe_power_spectrum(_ptr(mu_x), int(mu_x.shape[0]), int(mu_x.stride(0)), float(dt), _ptr(omegas),
+                                  int(omegas.shape[0]), float(tau), _ptr(out), _stream())
+    if st != EFE_OK:
+        raise EfeError(st, lib().efe_last_error(None).decode())
+    return out
 
 
 class Context:

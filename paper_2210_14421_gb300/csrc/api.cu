@@ -748,6 +748,40 @@ efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_st
                         checkpoint_every, n_quad_s, J_host, grad_host, as_stream(stream));
 }
 
+efe_status efe_absorption_spectrum(const double* mu_dev, int64_t n_t, int64_t stride_dir, int64_t stride_t, double dt,
+                                   const double* field_dev, double kick, const double* omega_dev, int64_t n_omega,
+                                   double tau, double* S_dev, void* stream) {
+  g_setup_err.clear();
+  if (!mu_dev || !omega_dev || !S_dev || n_t < 2 || n_omega < 1 || n_omega > 2147483647LL || !(dt > 0.0) ||
+      !(tau > 0.0) || (!field_dev && kick == 0.0)) {
+    g_setup_err = "efe_absorption_spectrum: invalid argument";
+    return EFE_ERR_ARG;
+  }
+  const cudaError_t e = launch_absorption(mu_dev, n_t, stride_dir, stride_t, dt, field_dev, kick, omega_dev, n_omega,
+                                          tau, S_dev, as_stream(stream));
+  if (e != cudaSuccess) {
+    g_setup_err = std::string("absorption spectrum: ") + cudaGetErrorString(e);
+    return EFE_ERR_CUDA;
+  }
+  return EFE_OK;
+}
+
+efe_status efe_power_spectrum(const double* mu_dev, int64_t n_t, int64_t stride_t, double dt, const double* omega_dev,
+                              int64_t n_omega, double tau, double* P_dev, void* stream) {
+  g_setup_err.clear();
+  if (!mu_dev || !omega_dev || !P_dev || n_t < 3 || n_omega < 1 || n_omega > 2147483647LL || !(dt > 0.0) ||
+      !(tau > 0.0)) {
+    g_setup_err = "efe_power_spectrum: invalid argument";
+    return EFE_ERR_ARG;
+  }
+  const cudaError_t e = launch_power(mu_dev, n_t, stride_t, dt, omega_dev, n_omega, tau, P_dev, as_stream(stream));
+  if (e != cudaSuccess) {
+    g_setup_err = std::string("power spectrum: ") + cudaGetErrorString(e);
+    return EFE_ERR_CUDA;
+  }
+  return EFE_OK;
+}
+
 efe_status efe_selftest(int64_t n, int64_t* mismatches_host) {
   if (n < 0 || !mismatches_host) return EFE_ERR_ARG;
   long long m = 0;

@@ -262,6 +262,12 @@ efe_status build_op(Ctx& c, const double* v, int batch, double kin, cudaStream_t
 // reverse sweep of the dipole objective through n_steps Magnus steps (adjoint.cu)
 efe_status adjoint_dipole(Ctx& c, const double* psi0, int n_steps, double dt, const efe_field& f, const double dir[3],
                           int w_first, int w_last, int K, int n_s, double* J_out, double grad[3], cudaStream_t s);
+// spectra of dipole traces (spectra.cu)
+cudaError_t launch_absorption(const double* mu, long long n_t, long long sdir, long long st, double dt,
+                              const double* E, double kick, const double* om, long long n_om, double tau, double* S,
+                              cudaStream_t s);
+cudaError_t launch_power(const double* mu, long long n_t, long long st, double dt, const double* om, long long n_om,
+                         double tau, double* P, cudaStream_t s);
 // Hartree solve (direct or PCG); iters returned (synchronises for PCG)
 efe_status run_hartree(Ctx& c, const double* rho, double* vH, double tol, int max_it, int* iters, cudaStream_t s);
 
