@@ -39,7 +39,7 @@ WORKLOAD = "Na8-like cluster (Z=11 x 8, 44 doubly occupied orbitals), 31^3 grade
            "GL 6^3, 48 enrichment fns (1s,2s,2p,3s per atom, cutoff 6 bohr), dt=0.05, kick 1e-3"
 
 
-def parse():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--k-max", type=int, default=48,
                     help="Lanczos cap; the Na8-like spectrum (-257..+1600 Ha) at dt = 0.05 needs k ~ 32 (FP64) "
                          "to 48 (mixed) for eps_k <= 1e-7")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -109,6 +109,23 @@ class Clocks:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- multi-rank bookkeeping
+def max_over_ranks(ms, device=None):
+    """The largest of the ranks' times (the job's time); the value itself with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    tt = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(world, steps, ms):
+    """Whole-job steps/s: every rank propagates its own problem (weak scaling)."""
+    return world * steps / (ms / 1000.0)
 
 
 # ---------------------------------------------------------------------------- helpers
@@ -380,13 +397,9 @@ def run_efe(args):
     ck = clocks.stop()
     prof = ctx.profile_read()
     ctx.profile(False)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, device="cuda")
     ms_step = ms / args.steps
-    value = world * args.steps / (ms / 1000.0)
+    value = job_throughput(world, args.steps, ms)
 
     # dominant kernel: cell apply, timed by CUDA events on its stream inside the timed region
     bytes_, flops, dense = apply_model(ctx, wl, args.precision)
@@ -615,7 +628,7 @@ def run_adjoint(args):
 
 
 def main():
-    args = parse()
+    args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.adjoint:
