@@ -27,8 +27,11 @@ namespace efe {
 
 static unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
 
-// out[c][q] += scale * wJ[c][q] * sum_a Im(conj(Phi a_a)(x_q) (Phi b_a)(x_q))   (batch member 0)
-template <int P1, int NQ1>
+// out[c][q] += scale * wJ[c][q] * sum_a Im(conj(Phi a_a)(x_q) (Phi b_a)(x_q))   (batch member 0).
+// The classical values are interpolated in T (float64, or float32 pairs: 8 bytes either way, a
+// tile entry of T is overwritten in place by its float64 value); enrichment values and the
+// products are float64.
+template <typename T, int P1, int NQ1>
 __global__ void __launch_bounds__(kThreads)
 k_cross_density(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ Xa,
                 const double* __restrict__ Xb, long long ld2, int n_orb, const double* __restrict__ Dsc,
@@ -38,12 +41,13 @@ k_cross_density(const __grid_constant__ RefTables tab, const MeshView mesh, cons
   constexpr int RT = 16;
   constexpr int S3 = NQ1 * NQ1 * NQ1;
   constexpr int NN = P1 * P1 * P1;
+  static_assert(sizeof(T) == sizeof(double), "tile entries are reused as float64");
   extern __shared__ __align__(16) double xsm[];
-  double* A = xsm;
-  double* Ca = A + S3 * RT;
-  double* D = Ca + S3 * RT;
-  double* Cb = D + S3 * RT;
-  double* racc = Cb + S3 * RT;
+  T* A = reinterpret_cast<T*>(xsm);
+  double* Ca = xsm + S3 * RT;
+  T* D = reinterpret_cast<T*>(xsm + 2 * S3 * RT);
+  double* Cb = xsm + 3 * S3 * RT;
+  double* racc = xsm + 4 * S3 * RT;
   const int c = blockIdx.x;
   int cx, cy, cz;
   cell_ijk(mesh, c, cx, cy, cz);
@@ -59,14 +63,14 @@ k_cross_density(const __grid_constant__ RefTables tab, const MeshView mesh, cons
       for (int it = threadIdx.x; it < NN * RT; it += blockDim.x) {
         const int r = it % RT, l = it / RT;
         const long long g = node_index(mesh, cx, cy, cz, l % P1, (l / P1) % P1, l / (P1 * P1));
-        A[it] = (cbase + r < cols) ? Dsc[g] * X[g * ld2 + cbase + r] : 0.0;
+        A[it] = from_f64<T>((cbase + r < cols) ? Dsc[g] * X[g * ld2 + cbase + r] : 0.0);
       }
       __syncthreads();
-      interp_fwd<double, P1, NQ1, RT>(tab, A, Cq, D);
+      interp_fwd<T, P1, NQ1, RT>(tab, A, reinterpret_cast<T*>(Cq), D);
       for (int it = threadIdx.x; it < S3 * RT; it += blockDim.x) {
         const int r = it % RT, q = it / RT;
         if (cbase + r >= cols) continue;
-        double acc = Cq[it];
+        double acc = to_f64<T>(reinterpret_cast<const T*>(Cq)[it]);
         for (int k = 0; k < np; ++k)
           acc += Atil[(long long)(p0 + k) * S3 + q] * xE[(long long)pair_fn[p0 + k] * ld2 + cbase + r];
         Cq[it] = acc;
@@ -219,7 +223,7 @@ struct Buffers {
   }
 };
 
-template <int P1, int NQ1>
+template <typename T, int P1, int NQ1>
 cudaError_t cross_impl(Ctx& c, const double* a, const double* b, double scale, double* out, cudaStream_t s) {
   const long long ld2 = 2LL * c.n_orb;
   if (c.nE > 0) {
@@ -231,8 +235,8 @@ cudaError_t cross_impl(Ctx& c, const double* a, const double* b, double scale, d
   }
   constexpr int S3 = NQ1 * NQ1 * NQ1;
   const size_t sm = sizeof(double) * (4 * 16 * S3 + S3);
-  EFE_CUDA_TRY(cudaFuncSetAttribute(k_cross_density<P1, NQ1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_cross_density<P1, NQ1><<<c.nc, kThreads, sm, s>>>(c.tab, c.mesh, a, b, ld2, c.n_orb, c.d_Dsc,
+  EFE_CUDA_TRY(cudaFuncSetAttribute(k_cross_density<T, P1, NQ1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_cross_density<T, P1, NQ1><<<c.nc, kThreads, sm, s>>>(c.tab, c.mesh, a, b, ld2, c.n_orb, c.d_Dsc,
                                                      c.n_pairs ? c.d_pair_start : nullptr, c.d_pair_fn, c.d_Atil,
                                                      c.d_xE, c.d_yE, c.d_wJ, scale, out);
   note_launch();
@@ -241,11 +245,20 @@ cudaError_t cross_impl(Ctx& c, const double* a, const double* b, double scale, d
 
 // out += scale * w Im(conj(Phi a) Phi b), summed over the orbitals
 cudaError_t cross_density(Ctx& c, const double* a, const double* b, double scale, double* out, cudaStream_t s) {
+  if (c.precision != EFE_FP64) {
+    switch (c.p) {
+      case 2: return cross_impl<df32, 3, 4>(c, a, b, scale, out, s);
+      case 3: return cross_impl<df32, 4, 5>(c, a, b, scale, out, s);
+      case 4: return cross_impl<df32, 5, 6>(c, a, b, scale, out, s);
+      case 5: return cross_impl<df32, 6, 7>(c, a, b, scale, out, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (c.p) {
-    case 2: return cross_impl<3, 4>(c, a, b, scale, out, s);
-    case 3: return cross_impl<4, 5>(c, a, b, scale, out, s);
-    case 4: return cross_impl<5, 6>(c, a, b, scale, out, s);
-    case 5: return cross_impl<6, 7>(c, a, b, scale, out, s);
+    case 2: return cross_impl<double, 3, 4>(c, a, b, scale, out, s);
+    case 3: return cross_impl<double, 4, 5>(c, a, b, scale, out, s);
+    case 4: return cross_impl<double, 5, 6>(c, a, b, scale, out, s);
+    case 5: return cross_impl<double, 6, 7>(c, a, b, scale, out, s);
   }
   return cudaErrorInvalidValue;
 }

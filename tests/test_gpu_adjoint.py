@@ -127,3 +127,15 @@ def test_adjoint_rejects_bad_arguments(case):
     with pytest.raises(EfeError):
         bad = dataclasses.replace(cs["field"], kind=W.FIELD_SINE_TRAP)
         cs["ctx"].adjoint_dipole(cs["psi0"], cs["n"], cs["dt"], bad, cs["d"], cs["window"])
+
+
+def test_pair_precision_adjoint_matches_oracle(case):
+    """The adjoint of a context computing in float32 pairs (pair applies, pair
+    interpolation in the cross densities) reaches the oracle's gradient to the
+    same 1e-8."""
+    from paper_2210_14421_gb300 import EFE_PAIR, Context
+    ctx = Context(case["wl"], precision=EFE_PAIR, krylov_tol=1e-13, k_max=40)
+    J, g = ctx.adjoint_dipole(case["psi0"], case["n"], case["dt"], case["field"], case["d"], case["window"],
+                              checkpoint_every=2, n_quad_s=6)
+    assert abs(J - case["J"]) <= 1e-10 * abs(case["J"])
+    assert np.max(np.abs(g - case["g"])) <= 1e-8 * np.max(np.abs(case["g"]))
