@@ -416,9 +416,9 @@ def run_efe(args):
         alu_peak = 152 * 128 * (15.0 / 12.0) * sm_mhz * 1e6 / 1e12
     tfl = flops / t_apply / 1e12
     # dram__bytes_read.sum + dram__bytes_write.sum of one k_cell_apply<df32,5,6,ENR,8> launch on the
-    # 15^3-cell crop (440.15 MB against 348.27 MB algorithmic), scaled to this launch by its algorithmic
+    # 15^3-cell crop (438.95 MB against 348.27 MB algorithmic), scaled to this launch by its algorithmic
     # bytes; only for the pair kernel that capture measured
-    traffic = (round(bytes_ * 440.151808 / 348.26868, -6)
+    traffic = (round(bytes_ * 438.948096 / 348.26868, -6)
                if args.precision == "pair" and wl.degree == 4 else None)
     hbm_frac = gbs / peaks["hbm_gbs"]
     alu_frac = tfl / alu_peak

@@ -54,7 +54,10 @@ __device__ __forceinline__ df32 operator*(df32 x, df32 y) {
 __device__ __forceinline__ df32& operator+=(df32& a, df32 b) { return a = a + b; }
 __device__ __forceinline__ df32& operator*=(df32& a, df32 b) { return a = a * b; }
 __device__ __forceinline__ bool operator!=(df32 a, df32 b) { return a.h != b.h || a.l != b.l; }
-// c + a b: exact product error and exact high-word rounding error go to the low word
+// c + a b: exact product error and exact high-word rounding error go to the low word.
+// a, b and c may be unnormalised results of earlier chains of m terms (|l| <= m ulp(h)):
+// the products a.h b.l and a.l b.h then still carry ~m 2^-48 relative error, so values
+// that only feed further chains skip fin(); values that meet operator+ do not.
 using ::fma;   // keep the float and double overloads visible next to this one
 __device__ __forceinline__ df32 fma(df32 a, df32 b, df32 c) {
   const float p = __fmul_rn(a.h, b.h);
@@ -113,8 +116,8 @@ __device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict
       T acc = T(0);
 #pragma unroll
       for (int m = 0; m < MIN; ++m) acc = fma(TRANS ? mat[m * MOUT + o] : mat[o * MIN + m], v[m], acc);
-      acc = fin(acc);
-      if (rs) acc = rs[r] * acc;
+      // outputs that only feed later fma chains stay unnormalised (see fma)
+      if (rs) acc = rs[r] * fin(acc);
       if (ACC)
         dst[o * SM_OUT] += acc;
       else
@@ -258,8 +261,8 @@ __device__ __forceinline__ void cell_operator_tile(const RefTables& tab, T* A, T
       }
 #pragma unroll
       for (int m = 0; m < P1; ++m) y = fma(M1[o * P1 + m], d[m], y);
-      B[off + o * S] = fin(y);
-      A[off + o * S] = fin(e);
+      B[off + o * S] = y;
+      A[off + o * S] = e;
     }
   }
   __syncthreads();
