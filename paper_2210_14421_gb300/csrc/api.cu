@@ -49,7 +49,7 @@ Ctx::~Ctx() {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(device);
-  dfree(d_geo); dfree(d_Dsc); dfree(d_Dsc32); dfree(d_Dsc2); dfree(d_M); dfree(d_xE32); dfree(d_xE2);
+  dfree(d_geo); dfree(d_Dsc); dfree(d_M); dfree(d_xE32); dfree(d_xE2);
   dfree(d_occ); dfree(d_vN); dfree(d_wJ); dfree(d_xq);
   dfree(d_pair_start); dfree(d_pair_fn); dfree(d_pair_cell); dfree(d_Atil); dfree(d_KE); dfree(d_KEE);
   if (d_phiB_nb != d_phiB) dfree(d_phiB_nb);
@@ -306,13 +306,6 @@ static efe_status setup_impl(Ctx& c, const efe_mesh_desc* mesh, const efe_atom* 
         }
     TRY_CUDA(c, dalloc(c.d_Dsc, Dsc.size()), "allocating D");
     TRY_CUDA(c, cudaMemcpy(c.d_Dsc, Dsc.data(), sizeof(double) * Dsc.size(), cudaMemcpyHostToDevice), "copy");
-    std::vector<float> D32(Dsc.begin(), Dsc.end());
-    TRY_CUDA(c, dalloc(c.d_Dsc32, D32.size()), "allocating D");
-    TRY_CUDA(c, cudaMemcpy(c.d_Dsc32, D32.data(), sizeof(float) * D32.size(), cudaMemcpyHostToDevice), "copy");
-    std::vector<df32> D2(Dsc.size());
-    for (size_t i = 0; i < Dsc.size(); ++i) D2[i] = df32::split(Dsc[i]);
-    TRY_CUDA(c, dalloc(c.d_Dsc2, D2.size()), "allocating D");
-    TRY_CUDA(c, cudaMemcpy(c.d_Dsc2, D2.data(), sizeof(df32) * D2.size(), cudaMemcpyHostToDevice), "copy");
   }
   TRY_CUDA(c, dalloc(c.d_occ, c.occ.size()), "allocating occupations");
   TRY_CUDA(c, cudaMemcpy(c.d_occ, c.occ.data(), sizeof(double) * c.occ.size(), cudaMemcpyHostToDevice), "copy");

@@ -124,8 +124,6 @@ struct Ctx {
   // device tables
   double* d_geo = nullptr;     // x0 (ncx+ncy+ncz) then h (ncx+ncy+ncz)
   double* d_Dsc = nullptr;     // [n_h] mask / sqrt(M)
-  float* d_Dsc32 = nullptr;    // float copy for the mixed apply
-  df32* d_Dsc2 = nullptr;      // pair copy for the FP32-pair apply
   double* d_M = nullptr;       // [n_h] lumped mass
   double* d_occ = nullptr;     // [n_orb]
   double* d_vN = nullptr;      // [nc][nq]

@@ -43,8 +43,8 @@ constexpr size_t tile_smem() {
 template <typename T, int P1, int NQ1, bool ENR, int RT = tile_rt<T, NQ1>()>
 __global__ void __launch_bounds__(kThreads)
 k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ X,
-             double* __restrict__ Y, long long ld2, int cols_member, const T* __restrict__ Dsc,
-             const T* __restrict__ W, double kin, const int* __restrict__ pair_start,
+             double* __restrict__ Y, long long ld2, int cols_member,
+             const double* __restrict__ Dsc, const T* __restrict__ W, double kin, const int* __restrict__ pair_start,
              const int* __restrict__ pair_fn, const T* __restrict__ E, long long n_pairs,
              const T* __restrict__ xE, double* __restrict__ yE, const int* __restrict__ gate = nullptr) {
   constexpr int S3 = NQ1 * NQ1 * NQ1;
@@ -88,7 +88,7 @@ k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const d
       const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
       const long long g = node_index(mesh, cx, cy, cz, i1, i2, i3);
       T v = T(0);
-      if (cbase + r < cols_member) v = from_f64<T>(X[g * ld2 + col0 + cbase + r]) * Dsc[g];
+      if (cbase + r < cols_member) v = from_f64_split<T>(X[g * ld2 + col0 + cbase + r] * Dsc[g]);
       A[it] = v;
     }
     __syncthreads();
@@ -137,8 +137,8 @@ k_cell_apply(const __grid_constant__ RefTables tab, const MeshView mesh, const d
       if (cbase + r >= cols_member) continue;
       const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
       const long long g = node_index(mesh, cx, cy, cz, i1, i2, i3);
-      const T d = Dsc[g];
-      if (d != T(0)) atomicAdd(&Y[g * ld2 + col0 + cbase + r], to_f64<T>(d * D[it]));
+      const double d = Dsc[g];
+      if (d != 0.0) atomicAdd(&Y[g * ld2 + col0 + cbase + r], d * to_f64<T>(D[it]));
     }
     __syncthreads();
   }
@@ -472,7 +472,6 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
   constexpr int PI = PR ? 2 : F32 ? 1 : 0;   // precision index of the autotuner
   const T* W = PR ? (const T*)c.op.W2 : F32 ? (const T*)c.op.W32 : (const T*)c.op.W64;
   const T* E = PR ? (const T*)c.op.E2 : F32 ? (const T*)c.op.E32 : (const T*)c.op.E64;
-  const T* Dt = PR ? (const T*)c.d_Dsc2 : F32 ? (const T*)c.d_Dsc32 : (const T*)c.d_Dsc;
   const T* xEt = PR ? (const T*)c.d_xE2 : F32 ? (const T*)c.d_xE32 : (const T*)c.d_xE;
   dim3 grid(c.nc, batch);
   constexpr int RT0 = tile_rt<T, NQ1>();
@@ -484,12 +483,12 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
       if (c.n_pairs > 0) {
         auto f = k_cell_apply<T, P1, NQ1, true, RT0>;
         EFE_CUDA_TRY(set_smem(f, sm));
-        f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, c.d_pair_start,
+        f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, c.d_Dsc, W, c.op.kin, c.d_pair_start,
                                      c.d_pair_fn, E, c.n_pairs, xEt, c.d_yE, c.apply_gate);
       } else {
         auto f = k_cell_apply<T, P1, NQ1, false, RT0>;
         EFE_CUDA_TRY(set_smem(f, sm));
-        f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, nullptr, nullptr,
+        f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, c.d_Dsc, W, c.op.kin, nullptr, nullptr,
                                      nullptr, 0, nullptr, nullptr, c.apply_gate);
       }
     } else {
@@ -497,12 +496,12 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
       if (c.n_pairs > 0) {
         auto f = k_cell_apply<T, P1, NQ1, true, RT1>;
         EFE_CUDA_TRY(set_smem(f, sm));
-        f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, c.d_pair_start,
+        f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, c.d_Dsc, W, c.op.kin, c.d_pair_start,
                                      c.d_pair_fn, E, c.n_pairs, xEt, c.d_yE, c.apply_gate);
       } else {
         auto f = k_cell_apply<T, P1, NQ1, false, RT1>;
         EFE_CUDA_TRY(set_smem(f, sm));
-        f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, nullptr, nullptr,
+        f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, c.d_Dsc, W, c.op.kin, nullptr, nullptr,
                                      nullptr, 0, nullptr, nullptr, c.apply_gate);
       }
     }
@@ -718,20 +717,19 @@ static cudaError_t apply_noalloc_impl(Ctx& c, const double* X, double* Y, long l
   constexpr bool F32 = std::is_same<T, float>::value;
   const T* W = F32 ? (const T*)c.op.W32 : (const T*)c.op.W64;
   const T* E = F32 ? (const T*)c.op.E32 : (const T*)c.op.E64;
-  const T* Dt = F32 ? (const T*)c.d_Dsc32 : (const T*)c.d_Dsc;
   const T* xEt = F32 ? (const T*)xE32 : (const T*)xE;
   const size_t sm = tile_smem<T, NQ1>();
   dim3 grid(c.nc, batch);
   if (c.n_pairs > 0) {
     auto f = k_cell_apply<T, P1, NQ1, true>;
     EFE_CUDA_TRY(set_smem(f, sm));
-    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, c.d_pair_start,
+    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, c.d_Dsc, W, c.op.kin, c.d_pair_start,
                                  c.d_pair_fn, E, c.n_pairs, xEt, yE, nullptr);
     note_launch();
   } else {
     auto f = k_cell_apply<T, P1, NQ1, false>;
     EFE_CUDA_TRY(set_smem(f, sm));
-    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, Dt, W, c.op.kin, nullptr, nullptr,
+    f<<<grid, kThreads, sm, s>>>(c.tab, c.mesh, X, Y, ld2, cols_member, c.d_Dsc, W, c.op.kin, nullptr, nullptr,
                                  nullptr, 0, nullptr, nullptr, nullptr);
     note_launch();
   }

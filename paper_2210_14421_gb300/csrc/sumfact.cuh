@@ -57,7 +57,8 @@ __device__ __forceinline__ bool operator!=(df32 a, df32 b) { return a.h != b.h |
 // c + a b: exact product error and exact high-word rounding error go to the low word.
 // a, b and c may be unnormalised results of earlier chains of m terms (|l| <= m ulp(h)):
 // the products a.h b.l and a.l b.h then still carry ~m 2^-48 relative error, so values
-// that only feed further chains skip fin(); values that meet operator+ do not.
+// that only feed further chains or a multiplication skip fin() (operator* leaves its
+// result normalised); values that meet operator+ do not.
 using ::fma;   // keep the float and double overloads visible next to this one
 __device__ __forceinline__ df32 fma(df32 a, df32 b, df32 c) {
   const float p = __fmul_rn(a.h, b.h);
@@ -117,7 +118,7 @@ __device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict
 #pragma unroll
       for (int m = 0; m < MIN; ++m) acc = fma(TRANS ? mat[m * MOUT + o] : mat[o * MIN + m], v[m], acc);
       // outputs that only feed later fma chains stay unnormalised (see fma)
-      if (rs) acc = rs[r] * fin(acc);
+      if (rs) acc = rs[r] * acc;
       if (ACC)
         dst[o * SM_OUT] += acc;
       else
@@ -231,8 +232,6 @@ __device__ __forceinline__ void cell_operator_tile(const RefTables& tab, T* A, T
         p = fma(M1[o * P1 + m], v[m], p);
         q = fma(K1[o * P1 + m], v[m], q);
       }
-      p = fin(p);
-      q = fin(q);
       A[it + o * S] = cx * p;
       B[it + o * S] = cy * p;
       D[it + o * S] = cz * q;
@@ -362,5 +361,11 @@ __device__ __forceinline__ df32 split_f64(double x) {
   }
   return df32(h, l);
 }
+
+// Gathered operands: FP64 products enter the fma chains through the exact split for pairs.
+template <typename T> __device__ __forceinline__ T from_f64_split(double x);
+template <> __device__ __forceinline__ double from_f64_split<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_f64_split<float>(double x) { return f64_to_f32_rn(x); }
+template <> __device__ __forceinline__ df32 from_f64_split<df32>(double x) { return split_f64(x); }
 
 }  // namespace efe
