@@ -65,10 +65,22 @@ typedef enum {
                      in float32 pairs (as EFE_PAIR); gather/scatter accumulation,
                      Lanczos recurrence, tridiagonal exponential, Hartree, norms and
                      dipole in float64; storage float64 */
-  EFE_PAIR = 2    /* as EFE_MIXED, but every value of the cell contraction and the
+  EFE_PAIR = 2,   /* as EFE_MIXED, but every value of the cell contraction and the
                      enrichment coupling is a pair of float32 (h + l) with error-free
                      products and sums, so the float32 pipe delivers ~2^-44 relative
                      accuracy */
+  EFE_TC = 3      /* as EFE_MIXED, but the cell contraction runs densely (H_c x_c with
+                     the dense cell matrix, rebuilt in float64 whenever the potential
+                     changes) on the tensor cores, together with the enrichment coupling:
+                     every operand is scaled by a power of two per row or column,
+                     rounded to 31 bits and split into four bf16 slices whose products
+                     are exact; slice products are summed in float32 tensor-memory
+                     accumulators (the leading group exactly) and combined in float64.
+                     Error per element ~2^-29 sum_k |H_ik| max_k |x_k|.  Supported for
+                     degree <= 4, at most 48 enrichment functions touching one cell and
+                     at most 96 real columns (48 orbitals) per batch member; otherwise
+                     efe_setup / efe_apply_H return EFE_ERR_ARG.  Holds 128 KB of slices
+                     per cell and batch member in device memory. */
 } efe_precision;
 
 /* Radial shapes of the atomic part N^A (Eq. EFEAtomic), divided by r^l:

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libefe.so")
 
 EFE_OK, EFE_ERR_ARG, EFE_ERR_NOMEM, EFE_ERR_CUDA, EFE_ERR_NOT_SPD = 0, 1, 2, 3, 4
 EFE_WARN_KRYLOV_CAP, EFE_ERR_CG_NOCONV, EFE_ERR_TIMEOUT, EFE_ERR_STATE = 5, 6, 7, 8
-EFE_FP64, EFE_MIXED, EFE_PAIR = 0, 1, 2
+EFE_FP64, EFE_MIXED, EFE_PAIR, EFE_TC = 0, 1, 2, 3
 EFE_HARTREE_FDM, EFE_HARTREE_PCG = 0, 1
 EFE_XC_PW92, EFE_XC_PZ81 = 0, 1
 EFE_STEP_PC, EFE_STEP_EXTRAPOLATED = 0, 1

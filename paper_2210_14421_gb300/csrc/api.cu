@@ -58,6 +58,7 @@ Ctx::~Ctx() {
   for (int a = 0; a < 3; ++a) { dfree(d_fdmV[a]); dfree(d_fdmL[a]); }
   dfree(d_fdmT);
   dfree(op.W64); dfree(op.W32); dfree(op.E64); dfree(op.E32); dfree(op.W2); dfree(op.E2); dfree(op.HEE);
+  tc_free(tc);
   dfree(d_rho); dfree(d_vH); dfree(d_vxc); dfree(d_vprev); dfree(d_Q); dfree(d_psi_p); dfree(d_xE); dfree(d_yE);
   dfree(d_lz); dfree(d_lzi); dfree(d_rho2); dfree(d_v); dfree(d_cg); dfree(d_red);
   for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
@@ -146,6 +147,7 @@ efe_status build_op(Ctx& c, const double* v, int batch, double kin, cudaStream_t
   if (st != EFE_OK) return st;
   c.op.kin = kin;
   TRY_CUDA(c, launch_build_operator(c, v, batch, kin, s), "building the operator");
+  if (c.tc_on) TRY_CUDA(c, launch_tc_build(c, batch, s), "building the tensor-core operator");
   c.op.valid = true;
   return EFE_OK;
 }
@@ -181,7 +183,7 @@ static bool validate(const efe_mesh_desc* mesh, const efe_atom* atoms, int n_ato
   if (o->n_orb < 1 || o->batch < 1 || !o->occ_host) { why = "n_orb, batch >= 1 and occupations required"; return false; }
   if (o->k_max < 1 || o->k_max > kMaxK) { why = "k_max must be in [1, 64]"; return false; }
   if (o->fixed_k < 0 || o->fixed_k > o->k_max) { why = "fixed_k must be in [0, k_max]"; return false; }
-  if (o->precision != EFE_FP64 && o->precision != EFE_MIXED && o->precision != EFE_PAIR) {
+  if (o->precision != EFE_FP64 && o->precision != EFE_MIXED && o->precision != EFE_PAIR && o->precision != EFE_TC) {
     why = "unknown precision";
     return false;
   }
@@ -436,6 +438,14 @@ static efe_status setup_impl(Ctx& c, const efe_mesh_desc* mesh, const efe_atom* 
   TRY_CUDA(c, cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking), "creating the capture stream");
   efe_status st = ensure_batch_buffers(c);
   if (st != EFE_OK) return st;
+  if (c.precision == EFE_TC) {
+    const char* why = tc_unsupported(c, 2 * c.n_orb);
+    if (why) {
+      c.err = why;
+      return EFE_ERR_ARG;
+    }
+    c.tc_on = true;
+  }
   TRY_CUDA(c, cudaDeviceSynchronize(), "set-up");
   return EFE_OK;
 }
@@ -515,6 +525,14 @@ static efe_status magnus_impl(Ctx& c, double* psi, double t, double dt, const ef
   if (mu) TRY_CUDA(c, launch_dipole(c, c.d_rho, mu, s), "dipole");
   if (info) {
     TRY_CUDA(c, cudaStreamSynchronize(s), "step");
+    if (c.tc.err) {
+      int h = 0;
+      TRY_CUDA(c, cudaMemcpy(&h, c.tc.err, sizeof(int), cudaMemcpyDeviceToHost), "tensor-core status");
+      if (h) {
+        c.err = "a tensor-core completion wait gave up";
+        return EFE_ERR_TIMEOUT;
+      }
+    }
     info->k_pred_max = k1;
     info->k_corr_max = k2;
     info->krylov_cap_hit = cap1 + cap2;
@@ -602,12 +620,23 @@ efe_status efe_apply_H(efe_ctx* ctx, const double* X_dev, double* Y_dev, int64_t
     return EFE_ERR_STATE;
   }
   if (!X_dev || !Y_dev || X_dev == Y_dev || n_cols < 1 || ld < n_cols || n_cols % c.op.batch != 0 ||
-      (precision != EFE_FP64 && precision != EFE_MIXED && precision != EFE_PAIR)) {
+      (precision != EFE_FP64 && precision != EFE_MIXED && precision != EFE_PAIR && precision != EFE_TC)) {
     c.err = "bad arguments to efe_apply_H (n_cols must be a multiple of the operator's batch, ld >= n_cols)";
     return EFE_ERR_ARG;
   }
   efe_status st = ensure_ws(c, n_cols, ld);
   if (st != EFE_OK) return st;
+  if (precision == EFE_TC) {
+    const char* why = tc_unsupported(c, (int)(2 * n_cols / c.op.batch));
+    if (why) {
+      c.err = why;
+      return EFE_ERR_ARG;
+    }
+    if (!c.tc_on) {   // first tensor-core apply of this context: slices of the current operator
+      c.tc_on = true;
+      TRY_CUDA(c, launch_tc_build(c, c.op.batch, as_stream(stream)), "building the tensor-core operator");
+    }
+  }
   TRY_CUDA(c, launch_apply(c, X_dev, Y_dev, n_cols, ld, precision, as_stream(stream)), "apply");
   return EFE_OK;
 }

@@ -84,6 +84,19 @@ struct Operator {
   bool valid = false;
 };
 
+// Tensor-core form of the operator (EFE_TC): bf16 slices of the dense cell matrices and
+// of the enrichment coupling in the shared-memory image the MMA reads (k_tc.cu).
+struct TcState {
+  int batch = 0;                  // members the slices are allocated for
+  unsigned char* H = nullptr;     // [batch][nc][4 slices][128 x 128 bf16]
+  int* rexp = nullptr;            // [batch][nc][128] row exponents of [H_c E_c]
+  unsigned char* E = nullptr;     // [batch][e_total][2048 B]: E_c then E_c^T slices per cell
+  int* hexp = nullptr;            // [batch][n_pairs] row exponents of E_c^T
+  long long* eoff = nullptr;      // [nc + 1] prefix sums of the padded function counts
+  long long e_total = 0;
+  int* err = nullptr;             // set by a tensor-core wait that gave up
+};
+
 // Per-launch timing of the cell-apply kernel (enabled by efe_profile).
 struct Prof {
   bool on = false;
@@ -152,6 +165,8 @@ struct Ctx {
   double* d_fdmT = nullptr;    // [2][batch][nx ny nz] transform scratch
   // operators
   Operator op;                 // current operator (efe_set_potential / magnus)
+  TcState tc;                  // its tensor-core slices, rebuilt with it while tc_on
+  bool tc_on = false;
   // autotuned cell-apply tile width per precision [FP64, MIXED, PAIR]: variant 0 (widest tile
   // fitting two blocks per SM) or 1 (half as wide); -1 until timed
   const int* apply_gate = nullptr;   // device count of active Lanczos columns (graph mode), else NULL
@@ -227,6 +242,15 @@ cudaError_t launch_build_operator(Ctx& c, const double* v, int batch, double kin
 // Y = Hbar X on n_cols complex columns (per member operator), ld in complex entries
 cudaError_t launch_apply(Ctx& c, const double* X, double* Y, long long n_cols, long long ld, int precision,
                          cudaStream_t s);
+
+// enrichment pre/post steps of an apply: xE = S X^E (and float copies); Y^E = S (yE + HEE xE)
+cudaError_t launch_enr_pre(Ctx& c, const double* X, long long ld2, int ncols2, cudaStream_t s);
+cudaError_t launch_enr_post(Ctx& c, double* Y, long long ld2, int ncols2, int cols_member, cudaStream_t s);
+// tensor-core operator (k_tc.cu): reason EFE_TC cannot serve this context, or NULL
+const char* tc_unsupported(const Ctx& c, int cols_member);
+cudaError_t launch_tc_build(Ctx& c, int batch, cudaStream_t s);
+cudaError_t launch_tc_apply(Ctx& c, const double* X, double* Y, long long n_cols, long long ld, cudaStream_t s);
+void tc_free(TcState& t);
 
 // Lanczos exponential: out = Kexp(-i dt_col Hbar) in for every complex column, with the
 // operator held in Ctx::op; dts_host [n_cols]; host-visible statistics after a stream sync.

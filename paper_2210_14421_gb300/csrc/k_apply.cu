@@ -461,11 +461,7 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
   EFE_CUDA_TRY(cudaMemset2DAsync(Y, sizeof(double) * ld2, 0, sizeof(double) * ncols2, c.n_dof, s));
   if (c.nE > 0) {
     EFE_CUDA_TRY(cudaMemsetAsync(c.d_yE, 0, sizeof(double) * c.nE * ld2, s));
-    long long n = (long long)c.nE * ncols2;
-    k_enr_pre<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, X, c.n_h, ld2, ncols2, c.nE, c.d_xE, c.d_xE32,
-                                                          c.d_xE2);
-    note_launch();
-    EFE_CUDA_TRY(cudaGetLastError());
+    EFE_CUDA_TRY(launch_enr_pre(c, X, ld2, ncols2, s));
   }
   constexpr bool F32 = std::is_same<T, float>::value;
   constexpr bool PR = std::is_same<T, df32>::value;
@@ -548,15 +544,24 @@ static cudaError_t apply_impl(Ctx& c, const double* X, double* Y, long long n_co
   if (e0) EFE_CUDA_TRY(cudaEventRecord(e0, s));
   EFE_CUDA_TRY(launch(choice));
   if (e1) EFE_CUDA_TRY(cudaEventRecord(e1, s));
-  if (c.nE > 0) {
-    long long n = (long long)c.nE * ncols2;
-    k_enr_post1<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.op.HEE, c.d_xE, c.d_yE, ld2, ncols2, cols_member, c.nE);
-    note_launch();
-    k_enr_post2<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, c.d_yE, Y, c.n_h, ld2, ncols2, c.nE);
-    note_launch();
-    EFE_CUDA_TRY(cudaGetLastError());
-  }
+  if (c.nE > 0) EFE_CUDA_TRY(launch_enr_post(c, Y, ld2, ncols2, cols_member, s));
   return cudaSuccess;
+}
+
+cudaError_t launch_enr_pre(Ctx& c, const double* X, long long ld2, int ncols2, cudaStream_t s) {
+  const long long n = (long long)c.nE * ncols2;
+  k_enr_pre<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, X, c.n_h, ld2, ncols2, c.nE, c.d_xE, c.d_xE32, c.d_xE2);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_enr_post(Ctx& c, double* Y, long long ld2, int ncols2, int cols_member, cudaStream_t s) {
+  const long long n = (long long)c.nE * ncols2;
+  k_enr_post1<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.op.HEE, c.d_xE, c.d_yE, ld2, ncols2, cols_member, c.nE);
+  note_launch();
+  k_enr_post2<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.d_S, c.d_yE, Y, c.n_h, ld2, ncols2, c.nE);
+  note_launch();
+  return cudaGetLastError();
 }
 
 template <int P1, int NQ1>
@@ -599,6 +604,7 @@ static cudaError_t build_impl(Ctx& c, const double* v, int batch, double kin, cu
 
 cudaError_t launch_apply(Ctx& c, const double* X, double* Y, long long n_cols, long long ld, int precision,
                          cudaStream_t s) {
+  if (precision == EFE_TC) return launch_tc_apply(c, X, Y, n_cols, ld, s);
   if (precision == EFE_MIXED) {
     EFE_DISPATCH_P(c.p, return (apply_impl<float, P1, NQ1>(c, X, Y, n_cols, ld, s)));
   }
