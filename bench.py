@@ -16,7 +16,7 @@ rest in FP64; its dipole error against the FP64 path is measured in the same
 run (bound 1e-5 a.u.).  "mixed" (plain binary32 contraction) is timed beside it
 with its own dipole error, which exceeds the bound on this stiff workload.
 
-  python bench.py [--gpus N --steps K --warmup W] [--precision pair|mixed|fp64]
+  python bench.py [--gpus N --steps K --warmup W] [--precision pair|tc|mixed|fp64]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
 """
 from __future__ import annotations
@@ -45,7 +45,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="efe", choices=["efe", "reference"])
-    ap.add_argument("--precision", default="pair", choices=["pair", "mixed", "fp64"])
+    ap.add_argument("--precision", default="pair", choices=["pair", "tc", "mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64 steps reported beside the main number")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--graph-steps", type=int, default=3, help="extra steps timed in CUDA-graph mode")
@@ -158,6 +158,16 @@ def apply_model(ctx, wl, precision):
     N_c 2 N_n^2 cols for the H.X rate."""
     p1, nq1 = wl.degree + 1, wl.n_quad
     R = 2 * wl.n_orb * wl.batch
+    if precision == "tc":
+        # dense form on the tensor cores: X read and Y written once, the four bf16 slices of
+        # every 128 x 128 cell matrix and of the cell's E_c and E_c^T blocks (125 values per
+        # cell-function pair each); flops: the 13 slice-pair products of the dense cell
+        # product H_c x^C, of E_c x^E and of E_c^T x^C (bf16 products, f32 accumulation)
+        nn = p1 ** 3
+        bytes_ = 2 * ctx.n_dof * R * 8 + ctx.n_cells * 4 * 128 * 128 * 2 + ctx.n_pairs * 2 * 4 * nn * 2
+        flops = 13 * 2.0 * R * (ctx.n_cells * nn * nn + 2 * nn * ctx.n_pairs)
+        dense = ctx.n_cells * 2.0 * nn ** 2 * R
+        return bytes_, flops, dense
     ts = 4 if precision == "mixed" else 8   # bytes per stored operator value (float, float pair, double)
     bytes_ = 2 * ctx.n_dof * R * 8 + ctx.n_cells * nq1 ** 3 * ts + ctx.n_pairs * p1 ** 3 * ts + ctx.n_nodes * 8
     fma_cell = 7 * p1 ** 4 + 2 * (nq1 * p1 ** 3 + nq1 ** 2 * p1 ** 2 + nq1 ** 3 * p1) + nq1 ** 3
@@ -341,7 +351,7 @@ def run_efe(args):
     import torch
 
     import __graft_entry__ as g
-    from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED, EFE_PAIR, Context, fields_array
+    from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED, EFE_PAIR, EFE_TC, Context, fields_array
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -354,7 +364,7 @@ def run_efe(args):
         torch.cuda.set_device(0)
     g.build()
     dev = torch.cuda.current_device()
-    prec = {"mixed": EFE_MIXED, "pair": EFE_PAIR, "fp64": EFE_FP64}[args.precision]
+    prec = {"mixed": EFE_MIXED, "pair": EFE_PAIR, "fp64": EFE_FP64, "tc": EFE_TC}[args.precision]
     wl = workload(args.cells, rank)
     if args.k_max > 0:
         wl = wl.with_(k_max=args.k_max)
@@ -424,7 +434,14 @@ def run_efe(args):
                if args.precision == "pair" and wl.degree == 4 else None)
     hbm_frac = gbs / peaks["hbm_gbs"]
     alu_frac = tfl / alu_peak
-    if alu_frac >= hbm_frac:
+    if args.precision == "tc":
+        # bf16 slice products on the tensor cores, timed inside a long step: the sustained peak
+        tpk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": round(tfl, 2), "peak": tpk, "unit": "TFLOP/s",
+                "frac": round(tfl / tpk, 4), "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (%s)" % src,
+                "hbm_frac_of_measured": round(hbm_frac, 4)}
+    elif alu_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                 "frac": round(alu_frac, 4), "traffic": traffic,
                 "peak_source": ("152 SMs x 128 FP32 lanes x 15/12 flop per lane-cycle (pair-fma instruction mix) x "
@@ -436,7 +453,8 @@ def run_efe(args):
     else:
         roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(hbm_frac, 4), "traffic": traffic, "peak_source": src, "alu_frac": round(alu_frac, 4)}
-    roof.update({"kernel": "k_cell_apply<%s,5,6,ENR>" % {"mixed": "float", "pair": "df32", "fp64": "double"}[args.precision],
+    roof.update({"kernel": "k_tc_apply<5>" if args.precision == "tc" else
+                 "k_cell_apply<%s,5,6,ENR>" % {"mixed": "float", "pair": "df32", "fp64": "double"}[args.precision],
                  "launches": prof["apply_launches"], "avg_ms": round(t_apply * 1000.0, 4),
                  "algorithmic_bytes": int(bytes_), "algorithmic_flops": flops})
     hx_tflops = dense / t_apply / 1e12
@@ -444,7 +462,8 @@ def run_efe(args):
     line = {"metric": METRIC, "value": round(value, 4), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {"mixed": "f32-contraction/f64", "pair": "f32-pair-contraction/f64", "fp64": "f64"}[args.precision],
+            "dtype": {"mixed": "f32-contraction/f64", "pair": "f32-pair-contraction/f64", "fp64": "f64",
+                      "tc": "bf16x4-split-tensor-contraction/f64"}[args.precision],
             "data": "synthetic (seeded efe_workloads.na8)",
             "config": {"workload": WORKLOAD, "precision": args.precision, "global_batch": world,
                        "n_cells": ctx.n_cells, "n_nodes": ctx.n_nodes, "n_enrich": ctx.n_enrich,
@@ -493,6 +512,14 @@ def run_efe(args):
         line["dipole_err_vs_fp64"] = {"value": derr, "steps": n_cmp, "bound": 1e-5, "met": derr <= 1e-5}
         line["fp64"] = {"steps_per_s": round(1000.0 / ms64, 4), "ms_per_step": round(ms64, 1),
                         "steps": args.fp64_steps, "first_step": first64}
+        if args.precision == "tc":
+            msp, musp, firstp = side_run(EFE_PAIR, args.fp64_steps, n_cmp)
+            dp = float(np.max(np.abs(mus64 - musp)))
+            line["fp32_pair_contraction"] = {"steps_per_s": round(1000.0 / msp, 4), "ms_per_step": round(msp, 1),
+                                             "steps": args.fp64_steps, "dipole_err_vs_fp64": dp, "met": dp <= 1e-5,
+                                             "first_step": firstp,
+                                             "note": "EFE_PAIR: the sum-factorised contraction in float32 pairs "
+                                                     "on the FP32 pipe"}
         if args.precision == "pair":
             ms32, mus32, first32 = side_run(EFE_MIXED, args.fp64_steps, n_cmp)
             d32 = float(np.max(np.abs(mus64 - mus32)))
@@ -573,7 +600,7 @@ def run_adjoint(args):
     g.build()
     import efe_workloads as W
     from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED, EFE_PAIR, Context
-    prec = {"mixed": EFE_FP64, "pair": EFE_PAIR, "fp64": EFE_FP64}[args.precision]
+    prec = {"mixed": EFE_FP64, "pair": EFE_PAIR, "fp64": EFE_FP64, "tc": EFE_PAIR}[args.precision]
     n = args.adj_steps
     # k_max 64: the exponentials converge (tol 1e-7), so the forward run is smooth in theta at the
     # level the finite difference needs (with the cap at 48 the atomics' rounding order moves J by ~1e-6)
@@ -612,7 +639,8 @@ def run_adjoint(args):
     fd = (forward(dataclasses.replace(f, amp=f.amp + h)) - forward(dataclasses.replace(f, amp=f.amp - h))) / (2 * h)
     line = {"metric": "adjoint gradient cost", "value": round(t_adj / t_fwd, 3), "unit": "x forward",
             "higher_is_better": False,
-            "dtype": {"pair": "f32-pair-contraction/f64", "fp64": "f64", "mixed": "f64"}[args.precision],
+            "dtype": {"pair": "f32-pair-contraction/f64", "fp64": "f64", "mixed": "f64",
+                      "tc": "f32-pair-contraction/f64"}[args.precision],
             "data": "synthetic (seeded efe_workloads.organic27)",
             "config": {"workload": "organic-27 (15 C/N/O + 12 H, %d orbitals), %d^3 graded cells degree 4; "
                                    "sine-Gaussian pulse amp 5e-3, omega 0.1, centred in a %d-step segment, dt 0.05"
