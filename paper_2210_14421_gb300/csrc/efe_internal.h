@@ -93,8 +93,6 @@ struct TcState {
   unsigned char* E = nullptr;     // [batch][e_total][2048 B]: E_c then E_c^T slices per cell
   int* hexp = nullptr;            // [batch][n_pairs] row exponents of E_c^T
   long long* eoff = nullptr;      // [nc + 1] prefix sums of the padded function counts
-  int* lam = nullptr;             // [nE] log2 bound of the rows of (M^ee)^-1/2
-  int* sig = nullptr;             // [batch][n_pairs] power of two moved from x^E to E_c per pair
   long long e_total = 0;
   int* err = nullptr;             // set by a tensor-core wait that gave up
 };

@@ -37,8 +37,6 @@
 //       mbarrier; all threads wait (bounded)
 //   epilogue: accumulators -> exact 64-bit fixed point -> float64 -> y_bar^C, y^E
 //   (atomic adds)
-#include <algorithm>
-#include <cmath>
 #include <cstdio>
 #include <vector>
 
@@ -66,7 +64,7 @@ constexpr int kAH = kXEs + kSlices * kXEslice;           // H_c slice i
 constexpr int kAEA = kAH + kSliceBytes;                  // E_c slice i      (128 x KEp)
 constexpr int kAET = kAEA + 128 * kMaxKE * 2;            // E_c^T slice i    (KEp x 128)
 constexpr int kMisc = kAET + kMaxKE * kK * 2;
-constexpr int kApplySmem = kMisc + 128 * 8 * 2 + 128 * 4 + (96 + 96 + 128 + 48 + 48 + 48) * 4 + 16;
+constexpr int kApplySmem = kMisc + 128 * 8 * 2 + 128 * 4 + (96 + 96 + 128 + 48 + 48) * 4 + 16;
 constexpr int kApplyThreads = 512;
 constexpr int kMaxPer = 26;                     // nodes gathered per thread (even; 512 / 96 >= 5 groups)
 
@@ -106,9 +104,8 @@ __global__ void __launch_bounds__(256)
 k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ W64, double kin,
            const int* __restrict__ pair_start, const double* __restrict__ E64, long long n_pairs,
            const double* __restrict__ Dsc, const long long* __restrict__ eoff, long long e_total,
-           const int* __restrict__ pair_fn, const int* __restrict__ lam, unsigned char* __restrict__ tcH,
-           int* __restrict__ tcRexp, unsigned char* __restrict__ tcE, int* __restrict__ tcHexp,
-           int* __restrict__ tcSig) {
+           unsigned char* __restrict__ tcH,
+           int* __restrict__ tcRexp, unsigned char* __restrict__ tcE, int* __restrict__ tcHexp) {
   constexpr int NN = P1 * P1 * P1;
   constexpr int S3 = NQ1 * NQ1 * NQ1;
   constexpr int PP = P1 * P1;
@@ -121,7 +118,6 @@ k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const dou
   double* Dn = H + NN * NN;           // D = mask / sqrt(M) at the cell's nodes
   int* rexp = reinterpret_cast<int*>(Dn + 128);
   int* hexp = rexp + 128;
-  int* sig = hexp + 48;               // per function of the cell: E_c column scaled by 2^sig
   const int c = blockIdx.x, m = blockIdx.y, tid = threadIdx.x;
   int cx, cy, cz;
   cell_ijk(mesh, c, cx, cy, cz);
@@ -167,26 +163,12 @@ k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const dou
   }
   const double* Ec = E64 + ((long long)m * n_pairs + p0) * NN;
   __syncthreads();
-  // Balance of x^E against x^C: x^E_f = S x_bar^E is up to 2^lam_f and x^C = D x_bar^C up to
-  // 2^delta in this cell; E_c's column f takes 2^(lam_f - delta) and x^E_f gives it back
-  // (exact powers of two), so one column scale serves [x^C; x^E] without costing x^C bits.
-  if (tid == 0 && np > 0) {
-    double dmax = 0.0;
-    for (int l = 0; l < NN; ++l) dmax = fmax(dmax, Dn[l]);
-    int delta = 0;
-    if (dmax > 0.0) frexp(dmax, &delta);
-    for (int f = 0; f < np; ++f) {
-      sig[f] = lam[pair_fn[p0 + f]] - delta;
-      tcSig[(long long)m * n_pairs + p0 + f] = sig[f];
-    }
-  }
-  __syncthreads();
   // row exponents, joint over the row of H_c and the row of E_c (one accumulator)
   for (int i = tid; i < 128; i += blockDim.x) {
     double mx = 0.0;
     if (i < NN) {
       for (int j = 0; j < NN; ++j) mx = fmax(mx, fabs(H[i * NN + j]));
-      for (int f = 0; f < np; ++f) mx = fmax(mx, fabs(ldexp(Dn[i] * Ec[(long long)f * NN + i], sig[f])));
+      for (int f = 0; f < np; ++f) mx = fmax(mx, fabs(Dn[i] * Ec[(long long)f * NN + i]));
     }
     rexp[i] = i < NN ? exp_of_max(mx) : kZero;
     tcRexp[((long long)m * mesh.nc + c) * 128 + i] = rexp[i];
@@ -225,7 +207,7 @@ k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const dou
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int f = fc * 8 + t;
-        v[t] = (i < NN && f < np) ? ldexp(Dn[i] * Ec[(long long)f * NN + i], sig[f]) : 0.0;
+        v[t] = (i < NN && f < np) ? Dn[i] * Ec[(long long)f * NN + i] : 0.0;
       }
       store_slices8(v, rexp[i], Eb + tc::kmajor_offset(i, fc * 8, 16 * KEp), eb);
     }
@@ -254,7 +236,7 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
            const int* __restrict__ tcRexp, const unsigned char* __restrict__ tcE, long long e_total,
            const long long* __restrict__ eoff, const int* __restrict__ tcHexp, const int* __restrict__ pair_start,
            const int* __restrict__ pair_fn, long long n_pairs, const double* __restrict__ xE, double* __restrict__ yE,
-           const int* __restrict__ tcSig, int* __restrict__ err, const int* __restrict__ gate) {
+           int* __restrict__ err, const int* __restrict__ gate) {
   constexpr int NN = P1 * P1 * P1;
   constexpr int NT = kApplyThreads;
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -266,8 +248,7 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
   int* rexp = fexp + 96;                                      // [128] row exponents
   int* hexp = rexp + 128;                                     // [48] E_c^T row exponents
   int* fns = hexp + 48;                                       // [48] enrichment functions of the cell
-  int* sig = fns + 48;                                        // [48] x^E_f scaled by 2^-sig
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sig + 48);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(fns + 48);
   uint32_t* tbase = reinterpret_cast<uint32_t*>(mbar + 1);
   int* abort_flag = reinterpret_cast<int*>(tbase + 1);
   if (gate && *gate == 0) return;   // every Lanczos column has converged (graph-captured loops)
@@ -344,7 +325,6 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
     for (int f = tid; f < np; f += NT) {
       fns[f] = pair_fn[p0 + f];
       hexp[f] = tcHexp[(long long)m * n_pairs + p0 + f];
-      sig[f] = tcSig[(long long)m * n_pairs + p0 + f];
     }
     for (int n = tid; n < 96; n += NT) colmax[n] = 0;
     if (np > 0)
@@ -365,11 +345,8 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
     for (int j = 0; j < kMaxPer; ++j)
       if (active && j < per && l0 + j < NN)
         kmax = max(kmax, tc::wide_key(tc::wide_mul(tc::wide_of(xv[j]), dm[l0 + j], de[l0 + j])));
-    for (int f = gg; active && f < np; f += G) {
-      tc::Wide x = tc::wide_of(xE[(long long)fns[f] * ld2 + col0 + gn]);
-      x.e -= sig[f];
-      kmax = max(kmax, tc::wide_key(x));
-    }
+    for (int f = gg; active && f < np; f += G)
+      kmax = max(kmax, tc::wide_key(tc::wide_of(xE[(long long)fns[f] * ld2 + col0 + gn])));
     if (active) atomicMax(&colmax[gn], kmax);
     __syncthreads();
     for (int n = tid; n < 96; n += NT) {
@@ -402,9 +379,7 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
       }
       for (int f = gg; f < np; f += G) {
         uint16_t s[kSlices];
-        tc::Wide x = tc::wide_of(xE[(long long)fns[f] * ld2 + col0 + gn]);
-        x.e -= sig[f];
-        tc::split4(fe == kZero ? 0LL : tc::q31_wide(x, fe), s);
+        tc::split4(fe == kZero ? 0LL : tc::q31_wide(tc::wide_of(xE[(long long)fns[f] * ld2 + col0 + gn]), fe), s);
         const uint32_t off = tc::kmajor_offset(gn, f, 16 * KEp);
 #pragma unroll
         for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint16_t*>(sm + kXEs + k * kXEslice + off) = s[k];
@@ -561,24 +536,15 @@ static cudaError_t tc_alloc(Ctx& c, int batch) {
     EFE_CUDA_TRY(cudaMemcpy(t.eoff, eo.data(), sizeof(long long) * (c.nc + 1), cudaMemcpyHostToDevice));
     EFE_CUDA_TRY(cudaMalloc(&t.err, sizeof(int)));
     EFE_CUDA_TRY(cudaMemset(t.err, 0, sizeof(int)));
-    std::vector<int> lam((size_t)std::max(c.nE, 1), 0);
-    for (int f = 0; f < c.nE; ++f) {
-      double mx = 0.0;
-      for (int k = 0; k < c.nE; ++k) mx = std::max(mx, std::fabs(c.S[(size_t)f * c.nE + k]));
-      if (mx > 0.0) std::frexp(mx, &lam[f]);
-    }
-    EFE_CUDA_TRY(cudaMalloc(&t.lam, sizeof(int) * lam.size()));
-    EFE_CUDA_TRY(cudaMemcpy(t.lam, lam.data(), sizeof(int) * lam.size(), cudaMemcpyHostToDevice));
   }
   if (t.batch != batch) {
-    cudaFree(t.H); cudaFree(t.rexp); cudaFree(t.E); cudaFree(t.hexp); cudaFree(t.sig);
-    t.H = nullptr; t.rexp = nullptr; t.E = nullptr; t.hexp = nullptr; t.sig = nullptr;
+    cudaFree(t.H); cudaFree(t.rexp); cudaFree(t.E); cudaFree(t.hexp);
+    t.H = nullptr; t.rexp = nullptr; t.E = nullptr; t.hexp = nullptr;
     t.batch = 0;
     EFE_CUDA_TRY(cudaMalloc(&t.H, (size_t)batch * c.nc * kSlices * kSliceBytes));
     EFE_CUDA_TRY(cudaMalloc(&t.rexp, sizeof(int) * (size_t)batch * c.nc * 128));
     EFE_CUDA_TRY(cudaMalloc(&t.E, (size_t)batch * (t.e_total > 0 ? t.e_total : 1) * 2048));
     EFE_CUDA_TRY(cudaMalloc(&t.hexp, sizeof(int) * (size_t)batch * (c.n_pairs > 0 ? c.n_pairs : 1)));
-    EFE_CUDA_TRY(cudaMalloc(&t.sig, sizeof(int) * (size_t)batch * (c.n_pairs > 0 ? c.n_pairs : 1)));
     t.batch = batch;
     c.ws_gen++;   // captured graphs hold the old pointers
   }
@@ -589,13 +555,12 @@ template <int P1, int NQ1>
 static cudaError_t tc_build_impl(Ctx& c, int batch, cudaStream_t s) {
   EFE_CUDA_TRY(tc_alloc(c, batch));
   constexpr int NN = P1 * P1 * P1, S3 = NQ1 * NQ1 * NQ1, PP = P1 * P1;
-  const size_t sm = sizeof(double) * (S3 + PP * NQ1 + PP * NQ1 * NQ1 + PP * PP * NQ1 + NN * NN + 128) + sizeof(int) * (128 + 48 + 48);
+  const size_t sm = sizeof(double) * (S3 + PP * NQ1 + PP * NQ1 * NQ1 + PP * PP * NQ1 + NN * NN + 128) + sizeof(int) * (128 + 48);
   auto f = k_tc_build<P1, NQ1>;
   EFE_CUDA_TRY(set_smem_tc(f, sm));
   dim3 grid(c.nc, batch);
   f<<<grid, 256, sm, s>>>(c.tab, c.mesh, c.op.W64, c.op.kin, c.n_pairs > 0 ? c.d_pair_start : nullptr, c.op.E64,
-                          c.n_pairs, c.d_Dsc, c.tc.eoff, c.tc.e_total, c.d_pair_fn, c.tc.lam, c.tc.H, c.tc.rexp,
-                          c.tc.E, c.tc.hexp, c.tc.sig);
+                          c.n_pairs, c.d_Dsc, c.tc.eoff, c.tc.e_total, c.tc.H, c.tc.rexp, c.tc.E, c.tc.hexp);
   note_launch();
   return cudaGetLastError();
 }
@@ -624,7 +589,7 @@ static cudaError_t tc_apply_impl(Ctx& c, const double* X, double* Y, long long n
   if (e0) EFE_CUDA_TRY(cudaEventRecord(e0, s));
   f<<<grid, kApplyThreads, kApplySmem, s>>>(c.mesh, X, Y, ld2, cols, nm, batch, c.d_Dsc, c.tc.H, c.tc.rexp, c.tc.E, c.tc.e_total,
                                   c.tc.eoff, c.tc.hexp, c.n_pairs > 0 ? c.d_pair_start : nullptr, c.d_pair_fn,
-                                  c.n_pairs, c.d_xE, c.d_yE, c.tc.sig, c.tc.err, c.apply_gate);
+                                  c.n_pairs, c.d_xE, c.d_yE, c.tc.err, c.apply_gate);
   note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   if (e1) EFE_CUDA_TRY(cudaEventRecord(e1, s));
@@ -652,7 +617,6 @@ cudaError_t launch_tc_apply(Ctx& c, const double* X, double* Y, long long n_cols
 
 void tc_free(TcState& t) {
   cudaFree(t.H); cudaFree(t.rexp); cudaFree(t.E); cudaFree(t.hexp); cudaFree(t.eoff); cudaFree(t.err);
-  cudaFree(t.lam); cudaFree(t.sig);
   t = TcState{};
 }
 
