@@ -97,21 +97,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
   return false;
 }
 
-// --- accumulator loads: warp w reads lanes 32 (w % 4) .. + 31, 16 consecutive columns ---
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
+// --- accumulator loads: warp w reads lanes 32 (w % 4) .. + 31, 8 consecutive columns ---
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -224,10 +210,6 @@ __device__ __forceinline__ double double_of_fixed(long long I, int e) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | (u & 0xFFFFFFFFFFFFFull)));
 }
 
-// 2^n as a double for |n| <= 1022
-__device__ __forceinline__ double pow2(int n) {
-  return __longlong_as_double((long long)(n + 1023) << 52);
-}
 // exponent e with |x| < 2^e for the largest |x| whose biased exponent is be (be > 0)
 __device__ __forceinline__ int scale_exp(int be) { return be - 1022; }
 __device__ __forceinline__ int biased_exp(double x) {
