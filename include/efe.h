@@ -215,7 +215,14 @@ efe_status efe_set_potential(efe_ctx* ctx, const double* v_dev, int32_t batch, d
  * the first n_cols columns are used, n_cols = n_orb_per_member * batch of that
  * operator.  The four steps run on the device: gather (with M^-1/2), cell
  * contraction (kinetic + v-weighted mass), scatter-add (with M^-1/2) and the
- * enrichment coupling.  X and Y must not overlap. */
+ * enrichment coupling.  X and Y must not overlap.  precision: any efe_precision.
+ * EFE_TC needs degree <= 4, at most 48 enrichment functions touching one cell and
+ * at most 96 real columns per member (else EFE_ERR_ARG with a message); its first
+ * use on a context whose options did not ask for it builds the slices of the
+ * current operator (the context keeps them in step with later operator builds).
+ * A tensor-core completion wait that gives up (bounded, seconds) records a
+ * sticky error that the next efe_magnus_step with info_host reports as
+ * EFE_ERR_TIMEOUT. */
 efe_status efe_apply_H(efe_ctx* ctx, const double* X_dev, double* Y_dev, int64_t n_cols, int64_t ld,
                        int32_t precision, void* stream);
 
