@@ -528,7 +528,8 @@ static efe_status magnus_impl(Ctx& c, double* psi, double t, double dt, const ef
     if (c.tc.err) {
       int h = 0;
       TRY_CUDA(c, cudaMemcpy(&h, c.tc.err, sizeof(int), cudaMemcpyDeviceToHost), "tensor-core status");
-      if (h) {
+      if (h) {   // reported once; the context stays usable for the next step
+        TRY_CUDA(c, cudaMemset(c.tc.err, 0, sizeof(int)), "tensor-core status");
         c.err = "a tensor-core completion wait gave up";
         return EFE_ERR_TIMEOUT;
       }

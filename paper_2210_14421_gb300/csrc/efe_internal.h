@@ -95,6 +95,7 @@ struct TcState {
   long long* eoff = nullptr;      // [nc + 1] prefix sums of the padded function counts
   long long e_total = 0;
   int* err = nullptr;             // set by a tensor-core wait that gave up
+  int n_sm = 0;                   // SMs of the context's device (persistent grid)
 };
 
 // Per-launch timing of the cell-apply kernel (enabled by efe_profile).

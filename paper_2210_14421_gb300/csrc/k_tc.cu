@@ -576,11 +576,9 @@ static cudaError_t tc_apply_impl(Ctx& c, const double* X, double* Y, long long n
     EFE_CUDA_TRY(cudaMemsetAsync(c.d_yE, 0, sizeof(double) * c.nE * ld2, s));
     EFE_CUDA_TRY(launch_enr_pre(c, X, ld2, ncols2, s));
   }
-  int dev = 0, nsm = 0;
-  EFE_CUDA_TRY(cudaGetDevice(&dev));
-  EFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (c.tc.n_sm == 0) EFE_CUDA_TRY(cudaDeviceGetAttribute(&c.tc.n_sm, cudaDevAttrMultiProcessorCount, c.device));
   const long long nwork = (long long)c.nc * batch;
-  const unsigned grid = (unsigned)(nwork < nsm ? nwork : nsm);
+  const unsigned grid = (unsigned)(nwork < c.tc.n_sm ? nwork : c.tc.n_sm);
   auto f = k_tc_apply<P1>;
   EFE_CUDA_TRY(set_smem_tc(f, kApplySmem));
   const int nm = (cols + 15) & ~15;
