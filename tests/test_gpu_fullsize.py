@@ -1,0 +1,76 @@
+"""The Na8-like workload at its full size (31^3 graded cells of degree 4,
+1.95M classical nodes, 48 enrichment functions, 44 orbitals), in the launch
+configuration the benchmark times: properties that hold at any size, since
+the oracle cannot assemble Hbar at this size.
+
+* Hbar is Hermitian: <X, Hbar Y> = <Hbar X, Y> for every precision, to its
+  rounding (FP64 ~1e-16, float32 pairs ~1e-13, tensor-core split ~1e-8 per
+  apply; the bounds sit about 100x above).
+* The reduced-precision applies agree with the FP64 apply to their own
+  accuracy.
+* A Magnus step conserves every column's norm (the Lanczos exponential of a
+  Hermitian operator with an orthonormal basis)."""
+import numpy as np
+import pytest
+
+import efe_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx_na8():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2210_14421_gb300 import EFE_PAIR, Context
+    wl = W.na8(k_max=64)   # the benchmark's configuration: float32 pairs, converged Lanczos (k = 57)
+    ctx = Context(wl, precision=EFE_PAIR, cg_tol=1e-10, cg_max_it=20000)
+    yield wl, ctx
+    ctx.close()
+    torch.cuda.empty_cache()
+
+
+def _rand(n, k, seed):
+    rng = np.random.default_rng(seed)
+    return torch.from_numpy(rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k))).cuda()
+
+
+def test_full_size_apply_hermitian_and_consistent(ctx_na8):
+    from paper_2210_14421_gb300 import EFE_FP64, EFE_PAIR, EFE_TC
+    wl, ctx = ctx_na8
+    _, quad = ctx.coords()
+    v = (-1.0 / (1.0 + (quad ** 2).sum(-1)))[None].contiguous()
+    ctx.set_potential(v)
+    n, k = ctx.n_dof, ctx.n_cols
+    X, Y = _rand(n, k, 31), _rand(n, k, 32)
+    out = {}
+    for name, prec, tol in (("fp64", EFE_FP64, 1e-12), ("pair", EFE_PAIR, 1e-11), ("tc", EFE_TC, 1e-6)):
+        HX, HY = torch.empty_like(X), torch.empty_like(Y)
+        ctx.apply_H(X, HX, prec)
+        ctx.apply_H(Y, HY, prec)
+        lhs = torch.sum(X.conj() * HY, dim=0)
+        rhs = torch.sum(HX.conj() * Y, dim=0)
+        scale = torch.linalg.norm(HX, dim=0) * torch.linalg.norm(Y, dim=0)
+        asym = torch.max(torch.abs(lhs - rhs) / scale).item()
+        assert asym < tol, (name, asym)
+        out[name] = HX
+    ref = torch.abs(out["fp64"]).max()
+    assert (torch.abs(out["pair"] - out["fp64"]).max() / ref).item() < 1e-11
+    assert (torch.abs(out["tc"] - out["fp64"]).max() / ref).item() < 1e-6
+
+
+def test_full_size_step_conserves_norms(ctx_na8):
+    wl, ctx = ctx_na8
+    psi = torch.zeros((ctx.n_dof, wl.n_orb), dtype=torch.complex128, device="cuda")
+    ctx.init_orbitals(psi)
+    n0 = torch.linalg.norm(psi, dim=0)
+    ctx.kick(psi, wl.fields)
+    mu = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+    ctx.magnus_step(psi, 0.0, wl.dt, wl.fields, mu)
+    n1 = torch.linalg.norm(psi, dim=0)
+    assert torch.max(torch.abs(n1 - n0) / n0).item() < 1e-8
+    assert torch.isfinite(mu).all()
