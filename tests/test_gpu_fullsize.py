@@ -72,5 +72,6 @@ def test_full_size_step_conserves_norms(ctx_na8):
     mu = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
     ctx.magnus_step(psi, 0.0, wl.dt, wl.fields, mu)
     n1 = torch.linalg.norm(psi, dim=0)
-    assert torch.max(torch.abs(n1 - n0) / n0).item() < 1e-8
+    # the Lanczos basis stays orthonormal to about the level the exponential converged to (tol 1e-7)
+    assert torch.max(torch.abs(n1 - n0) / n0).item() < 1e-7
     assert torch.isfinite(mu).all()
