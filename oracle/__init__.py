@@ -21,8 +21,8 @@ operators H, M, orthogonalisation and the Loewdin transform, Eqs. PsiEFE,
           EFESplit, EFEOrtho, Hmn, M, TDKSDiscrete2, MSquareRoot.
 xc        Slater exchange + Perdew-Wang 1992 correlation (local density).
 poisson   Hartree potential, Eqs. Hartree_possion and DiscretePoisson.
-electrostatic  nuclear potential of smeared charges in the enriched basis,
-          Eqs. PhiEFE and DiscretePoisson.
+electrostatic  nuclear and Hartree potentials in the enriched basis, Eqs.
+          PhiEFE and DiscretePoisson.
 krylov    adaptive Lanczos exponential, Eqs. AdaptiveKrylov, AdaptiveKrylovErr.
 tdks      density, dipole, fields, second-order Magnus predictor-corrector
           step (Eq. ApproxMagnus), delta kick, ground state.

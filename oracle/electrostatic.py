@@ -1,5 +1,5 @@
-"""Nuclear electrostatic potential in the enriched finite element basis (Eqs.
-PhiEFE, DiscretePoisson).
+"""Electrostatic potentials (nuclear and Hartree) in the enriched finite element
+basis (Eqs. PhiEFE, DiscretePoisson).
 
 Test infrastructure only (see `oracle/__init__.py`).
 
@@ -25,6 +25,9 @@ Readings (the paper leaves b and the atomic potential to its references):
   E3  Cell integrals use Gauss-Legendre n^3 rules on sub^3 sub-cells of every
       cell: the Gaussian core is narrower than the cells around a nucleus (the
       paper's adaptive quadrature is a later item).
+  H1  for the Hartree potential, the atomic part is the Hartree potential of
+      the isolated neutral atom whose density fills the shells of its
+      wavefunction enrichment functions (class RadialAtom).
 """
 from __future__ import annotations
 
@@ -97,33 +100,35 @@ def smeared_charge(Z, R, sigma: float, pts: np.ndarray) -> np.ndarray:
     return b
 
 
-def atomic_part(z: float, center, sigma: float, r0: float, s: float, pts: np.ndarray):
-    """Values (npts,) and gradients (npts, 3) of N^{A,phi} = f(r) u(r),
-    f = -z erf(r / (sqrt2 sigma)) / r (reading E2)."""
-    d = pts - np.asarray(center)[None, :]
-    r = np.sqrt(np.sum(d * d, axis=1))
+def nuclear_radial(z: float, sigma: float):
+    """r -> (f, df/dr) for f = -z erf(r / (sqrt2 sigma)) / r, the potential of one
+    smeared nucleus (readings E1, E2; df/dr -> 0 as r -> 0)."""
     a = 1.0 / (math.sqrt(2.0) * sigma)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        f = np.where(r > 0, -z * erf(a * r) / r, -z * 2.0 * a / math.sqrt(math.pi))
-        # f'(r) = -z [2 a exp(-a^2 r^2) / (sqrt(pi) r) - erf(a r) / r^2], -> 0 as r -> 0
-        df = np.where(r > 1e-8, -z * (2.0 * a * np.exp(-(a * r) ** 2) / (math.sqrt(math.pi) * r) - erf(a * r) / r ** 2),
-                      0.0)
-        rhat = np.where(r[:, None] > 0, d / r[:, None], 0.0)
-    u, du = cutoff(r, r0, s)
-    return f * u, ((df * u + f * du))[:, None] * rhat
+
+    def f(r):
+        r = np.asarray(r, float)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            v = np.where(r > 0, -z * erf(a * r) / r, -z * 2.0 * a / math.sqrt(math.pi))
+            dv = np.where(r > 1e-8, -z * (2.0 * a * np.exp(-(a * r) ** 2) / (math.sqrt(math.pi) * r)
+                                          - erf(a * r) / r ** 2), 0.0)
+        return v, dv
+    return f
 
 
-class NuclearEFE:
-    """The enriched Poisson problem for the nuclear potential of smeared point
-    charges on a mesh (Eqs. PhiEFE, DiscretePoisson with readings E1-E3).
-    enrich=False gives the classical-only solve on the same mesh and rule."""
+class EnrichedPoisson:
+    """A phi = d in the classical basis plus one orthogonalised enrichment
+    function per atom (Eqs. PhiEFE, DiscretePoisson): atomic parts
+    potentials[I](r) -> (f, df/dr) times the cutoff u, the load d = int charge N,
+    Dirichlet data on the classical boundary nodes.  enrich=False gives the
+    classical-only solve on the same mesh and rule."""
 
-    def __init__(self, mesh, Z, R, sigma: float, r0: float, s: float, sub: int = 2, n: int = None,
-                 enrich: bool = True):
-        self.mesh, self.Z, self.R, self.sigma = mesh, list(Z), [np.asarray(x, float) for x in R], sigma
+    def __init__(self, mesh, centers, potentials, charge, dirichlet, r0: float, s: float, sub: int = 2,
+                 n: int = None, enrich: bool = True):
+        self.mesh, self.R = mesh, [np.asarray(x, float) for x in centers]
+        self.potentials, self.charge, self.dirichlet = list(potentials), charge, dirichlet
         self.r0, self.s = r0, s
         self.rule = CompositeRule(mesh, sub, n or mesh.nq1)
-        self.nE = len(self.Z) if enrich else 0
+        self.nE = len(self.R) if enrich else 0
         n_h = mesh.n_nodes
         M = mesh.lumped_mass()
         Minv = np.where(mesh.interior, 1.0 / M, 0.0)
@@ -132,10 +137,10 @@ class NuclearEFE:
         for c in range(mesh.n_cells):
             pts, w, Bc, _ = self.rule.cell(mesh, c)
             for I in range(self.nE):
-                va, _ = atomic_part(self.Z[I], self.R[I], sigma, r0, s, pts)
+                va, _ = self._atomic(I, pts)
                 np.add.at(bA[I], mesh.conn[c], Bc.T @ (w * va))
         self.C = bA * Minv[None, :]
-        # assembly of A (classical, classical-enriched, enriched) and of d = int b N
+        # assembly of A (classical, classical-enriched, enriched) and of d = int charge N
         rows, cols, vals = [], [], []
         ACE = np.zeros((n_h, self.nE))
         AEE = np.zeros((self.nE, self.nE))
@@ -149,7 +154,7 @@ class NuclearEFE:
             rows.append(np.repeat(idx, len(idx)))
             cols.append(np.tile(idx, len(idx)))
             vals.append(Kc.ravel())
-            b = smeared_charge(self.Z, self.R, sigma, pts)
+            b = charge(pts)
             dC[idx] += Bc.T @ (w * b)
             if self.nE:
                 vE, gE = self._enriched_at(c, pts, Bc, G)
@@ -160,6 +165,16 @@ class NuclearEFE:
         self.Acc = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n_h, n_h))
         self.ACE, self.AEE, self.dC, self.dE = ACE, AEE, dC, dE
 
+    def _atomic(self, I: int, pts):
+        """Values and gradients of the atomic part N^{A,phi}_I = f(r) u(r)."""
+        d = pts - self.R[I][None, :]
+        r = np.sqrt(np.sum(d * d, axis=1))
+        f, df = self.potentials[I](r)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            rhat = np.where(r[:, None] > 0, d / r[:, None], 0.0)
+        u, du = cutoff(r, self.r0, self.s)
+        return f * u, (df * u + f * du)[:, None] * rhat
+
     def _enriched_at(self, c: int, pts, Bc, G):
         """Values (nq, nE) and gradients [3 x (nq, nE)] of the orthogonalised
         enrichment functions on cell c."""
@@ -167,7 +182,7 @@ class NuclearEFE:
         v = np.zeros((len(pts), self.nE))
         g = [np.zeros((len(pts), self.nE)) for _ in range(3)]
         for I in range(self.nE):
-            va, ga = atomic_part(self.Z[I], self.R[I], self.sigma, self.r0, self.s, pts)
+            va, ga = self._atomic(I, pts)
             cI = self.C[I, idx]
             v[:, I] = va - Bc @ cI
             for a in range(3):
@@ -193,7 +208,7 @@ class NuclearEFE:
         I = np.where(m.interior)[0]
         Bn = np.where(m.boundary)[0]
         if phiB is None:
-            phiB = smeared_potential(self.Z, self.R, self.sigma, m.nodes[Bn])
+            phiB = self.dirichlet(m.nodes[Bn])
         dC = self.dC if dC is None else dC
         dE = self.dE if dE is None else dE
         AIB = self.Acc[I][:, Bn]
@@ -215,3 +230,99 @@ class NuclearEFE:
             vE, _ = self._enriched_at(c, pts, Bc, G)
             val = val + vE @ phiE
         return pts, val
+
+
+class NuclearEFE(EnrichedPoisson):
+    """The nuclear potential of smeared point charges (readings E1-E3)."""
+
+    def __init__(self, mesh, Z, R, sigma: float, r0: float, s: float, sub: int = 2, n: int = None,
+                 enrich: bool = True):
+        self.Z, self.sigma = list(Z), sigma
+        super().__init__(mesh, R, [nuclear_radial(z, sigma) for z in self.Z],
+                         lambda p: smeared_charge(self.Z, R, sigma, p),
+                         lambda p: smeared_potential(self.Z, R, sigma, p), r0, s, sub, n, enrich)
+
+
+# ---------------------------------------------------------------------------
+# Hartree potential with atomic Hartree potentials as enrichment (Eq. PhiEFE,
+# "the electrostatic potential ... of an isolated atom": Hartree part).
+# Reading H1: the isolated neutral atom's density fills the shells of its
+# wavefunction enrichment functions (same n, l, radial shape and zeta) in the
+# order of n, then l, two electrons per orbital: rho_I(r) = sum_nl occ_nl
+# R_nl(r)^2 / (4 pi int R_nl^2 r^2 dr).  Its Hartree potential is the spherical
+# solution v(r) = (4 pi / r) int_0^r rho s^2 ds + 4 pi int_r^inf rho s ds, with
+# dv/dr = -Q(r) / r^2, Q the enclosed charge, on a radial grid.
+# ---------------------------------------------------------------------------
+class RadialAtom:
+    """Density and Hartree potential of one isolated atom (reading H1), tabulated
+    on r = rmax t^2 with n points uniform in t (cumulative trapezoid integrals in t)."""
+
+    def __init__(self, shells, n_el: float, rmax: float = 60.0, n: int = 24001):
+        from .enrich import radial
+        tt = np.linspace(0.0, 1.0, n)
+        r = rmax * tt * tt            # dense near the nucleus, where the core shells vary fastest
+        rho = np.zeros_like(r)
+        left = float(n_el)
+        for (kind, nn, l, zeta) in sorted(shells, key=lambda x: (x[1], x[2])):
+            occ = min(left, 2.0 * (2 * l + 1))
+            if occ <= 0:
+                break
+            f, _ = radial(kind, nn, l, zeta, r)
+            R = f * r ** l
+            norm = _trapezoid_total(R * R * r * r, r)
+            rho += occ * R * R / (4.0 * math.pi * norm)
+            left -= occ
+        self.r, self.rho = r, rho
+        q = 4.0 * math.pi * _cum_trapezoid(rho * r * r, r)          # enclosed charge Q(r)
+        outer = 4.0 * math.pi * (_trapezoid_total(rho * r, r) - _cum_trapezoid(rho * r, r))
+        with np.errstate(invalid="ignore", divide="ignore"):
+            self.v = np.where(r > 0, q / r, 0.0) + outer
+        self.v[0] = 4.0 * math.pi * _trapezoid_total(rho * r, r)
+        self.q = q
+        self.n_el = q[-1]
+
+    def density(self, r):
+        return np.interp(r, self.r, self.rho, right=0.0)
+
+    def potential(self, r):
+        """v(r) and dv/dr = -Q(r) / r^2 (v -> Q/r beyond the table)."""
+        r = np.asarray(r, float)
+        v = np.where(r <= self.r[-1], np.interp(r, self.r, self.v), self.n_el / np.maximum(r, 1e-300))
+        Q = np.interp(r, self.r, self.q, right=self.n_el)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            dv = np.where(r > 0, -Q / (r * r), 0.0)
+        return v, dv
+
+
+def _cum_trapezoid(y, x):
+    """Cumulative integral of y dr on the grid r = rmax t^2: the trapezoid rule
+    in t with dr = 2 rmax t dt (uniform in t)."""
+    t = np.sqrt(x / x[-1])
+    g = y * 2.0 * x[-1] * t
+    out = np.zeros_like(y)
+    out[1:] = np.cumsum(0.5 * (g[1:] + g[:-1]) * np.diff(t))
+    return out
+
+
+def _trapezoid_total(y, x):
+    return float(_cum_trapezoid(y, x)[-1])
+
+
+class HartreeEFE(EnrichedPoisson):
+    """The Hartree potential of a density given as a function of position, with
+    the atoms' Hartree potentials (reading H1) as enrichment; Dirichlet data
+    from `dirichlet` (default: the superposition of the atomic potentials, the
+    exact solution when the density is the superposition of atomic densities)."""
+
+    def __init__(self, mesh, atoms, centers, density, r0: float, s: float, dirichlet=None, sub: int = 2,
+                 n: int = None, enrich: bool = True):
+        self.atoms = list(atoms)
+        centers = [np.asarray(x, float) for x in centers]
+        if dirichlet is None:
+            def dirichlet(p):
+                v = np.zeros(len(p))
+                for A, R in zip(self.atoms, centers):
+                    v += A.potential(np.linalg.norm(p - R[None, :], axis=1))[0]
+                return v
+        super().__init__(mesh, centers, [A.potential for A in self.atoms], density, dirichlet, r0, s, sub, n,
+                         enrich)
