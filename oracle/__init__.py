@@ -23,6 +23,7 @@ xc        Slater exchange + Perdew-Wang 1992 correlation (local density).
 poisson   Hartree potential, Eqs. Hartree_possion and DiscretePoisson.
 electrostatic  nuclear and Hartree potentials in the enriched basis, Eqs.
           PhiEFE and DiscretePoisson.
+quadrature  adaptive cell quadrature for the enrichment integrals.
 krylov    adaptive Lanczos exponential, Eqs. AdaptiveKrylov, AdaptiveKrylovErr.
 tdks      density, dipole, fields, second-order Magnus predictor-corrector
           step (Eq. ApproxMagnus), delta kick, ground state.

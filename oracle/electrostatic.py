@@ -123,11 +123,12 @@ class EnrichedPoisson:
     classical-only solve on the same mesh and rule."""
 
     def __init__(self, mesh, centers, potentials, charge, dirichlet, r0: float, s: float, sub: int = 2,
-                 n: int = None, enrich: bool = True):
+                 n: int = None, enrich: bool = True, rule=None):
         self.mesh, self.R = mesh, [np.asarray(x, float) for x in centers]
         self.potentials, self.charge, self.dirichlet = list(potentials), charge, dirichlet
         self.r0, self.s = r0, s
-        self.rule = CompositeRule(mesh, sub, n or mesh.nq1)
+        # cell rule: uniform sub-cells (reading E3) unless given (e.g. quadrature.AdaptiveRule)
+        self.rule = rule if rule is not None else CompositeRule(mesh, sub, n or mesh.nq1)
         self.nE = len(self.R) if enrich else 0
         n_h = mesh.n_nodes
         M = mesh.lumped_mass()
@@ -236,11 +237,11 @@ class NuclearEFE(EnrichedPoisson):
     """The nuclear potential of smeared point charges (readings E1-E3)."""
 
     def __init__(self, mesh, Z, R, sigma: float, r0: float, s: float, sub: int = 2, n: int = None,
-                 enrich: bool = True):
+                 enrich: bool = True, rule=None):
         self.Z, self.sigma = list(Z), sigma
         super().__init__(mesh, R, [nuclear_radial(z, sigma) for z in self.Z],
                          lambda p: smeared_charge(self.Z, R, sigma, p),
-                         lambda p: smeared_potential(self.Z, R, sigma, p), r0, s, sub, n, enrich)
+                         lambda p: smeared_potential(self.Z, R, sigma, p), r0, s, sub, n, enrich, rule)
 
 
 # ---------------------------------------------------------------------------
