@@ -24,6 +24,7 @@ poisson   Hartree potential, Eqs. Hartree_possion and DiscretePoisson.
 electrostatic  nuclear and Hartree potentials in the enriched basis, Eqs.
           PhiEFE and DiscretePoisson.
 quadrature  adaptive cell quadrature for the enrichment integrals.
+octree    locally refined mesh with hanging-node constraints.
 krylov    adaptive Lanczos exponential, Eqs. AdaptiveKrylov, AdaptiveKrylovErr.
 tdks      density, dipole, fields, second-order Magnus predictor-corrector
           step (Eq. ApproxMagnus), delta kick, ground state.

@@ -1,0 +1,150 @@
+"""A locally refined hexahedral mesh with hanging-node constraints (the paper's
+adaptive mesh: an octree whose non-conforming faces are made conforming by
+constraints on the finer side; Sec. "Enriched finite element basis", mesh
+adaption).
+
+Test infrastructure only (see `oracle/__init__.py`).
+
+Reading O1 (the paper uses the octree of its references): one refinement
+level over a uniform coarse grid — a chosen set of coarse cells is split into
+2 x 2 x 2 children, so neighbouring leaves differ by at most one level — with
+degree-p Lagrange functions on GLL nodes in every leaf.  Coincident nodes of
+leaves are one node.  A node of a fine leaf that lies on the boundary of a
+coarse leaf without being one of its nodes is hanging: its value is the coarse
+leaf's interpolant there, u(x_h) = sum_j N^C_j(x_h) u_j over the coarse leaf's
+nodes, which are never hanging (one level).  The constrained space is
+u_all = P u_free; operators are P^T K P.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .basis import gauss_legendre, gauss_lobatto, lagrange
+
+
+class OctreeMesh:
+    def __init__(self, lo, hi, nc: int, p: int, refine, n_quad: int = None):
+        lo, hi = np.asarray(lo, float), np.asarray(hi, float)
+        self.lo, self.hi, self.p = lo, hi, p
+        self.xi, _ = gauss_lobatto(p)
+        hc = (hi - lo) / nc
+        refine = set(tuple(r) for r in refine)
+        leaves = []     # (x0, h, coarse flag)
+        for k in range(nc):
+            for j in range(nc):
+                for i in range(nc):
+                    x0 = lo + np.array([i, j, k]) * hc
+                    if (i, j, k) in refine:
+                        for c in range(8):
+                            b = np.array([(c >> a) & 1 for a in range(3)])
+                            leaves.append((x0 + 0.5 * b * hc, 0.5 * hc, False))
+                    else:
+                        leaves.append((x0, hc.copy(), True))
+        self.leaves = leaves
+        p1 = p + 1
+        i3, i2, i1 = np.meshgrid(np.arange(p1), np.arange(p1), np.arange(p1), indexing="ij")
+        self.loc = np.stack([i1.ravel(), i2.ravel(), i3.ravel()], axis=1)
+        # nodes of every leaf, merged by position
+        scale = 1.0 / (np.min(hc) * 1e-9)
+        key_of, coords, conn = {}, [], []
+        for x0, h, _ in leaves:
+            X = x0[None, :] + 0.5 * (self.xi[self.loc] + 1.0) * h[None, :]
+            ids = []
+            for x in X:
+                key = tuple(np.rint(x * scale).astype(np.int64))
+                if key not in key_of:
+                    key_of[key] = len(coords)
+                    coords.append(x)
+                ids.append(key_of[key])
+            conn.append(ids)
+        self.nodes = np.array(coords)
+        self.conn = np.array(conn)
+        self.n_all = len(coords)
+        # hanging nodes: on the closed box of a coarse leaf, not one of its nodes
+        hang = {}
+        tol = 1e-9 * np.min(hc)
+        for li, (x0, h, coarse) in enumerate(leaves):
+            if not coarse:
+                continue
+            own = set(self.conn[li])
+            inside = np.all((self.nodes >= x0[None, :] - tol) & (self.nodes <= x0[None, :] + h[None, :] + tol), axis=1)
+            for n in np.where(inside)[0]:
+                if n in own or n in hang:
+                    continue
+                ref = 2.0 * (self.nodes[n] - x0) / h - 1.0
+                L = [lagrange(self.xi, np.array([ref[a]]))[0][0] for a in range(3)]
+                w = L[0][self.loc[:, 0]] * L[1][self.loc[:, 1]] * L[2][self.loc[:, 2]]
+                keep = np.abs(w) > 1e-14
+                hang[n] = (self.conn[li][keep], w[keep])
+        self.hanging = hang
+        free = [n for n in range(self.n_all) if n not in hang]
+        self.free = np.array(free)
+        col = {n: i for i, n in enumerate(free)}
+        rows, cols, vals = [], [], []
+        for n in range(self.n_all):
+            if n in hang:
+                masters, w = hang[n]
+                for mm, ww in zip(masters, w):
+                    rows.append(n)
+                    cols.append(col[mm])
+                    vals.append(ww)
+            else:
+                rows.append(n)
+                cols.append(col[n])
+                vals.append(1.0)
+        self.P = sp.csr_matrix((vals, (rows, cols)), shape=(self.n_all, len(free)))
+        # quadrature tables
+        nq1 = n_quad or p + 2
+        xg, wg = gauss_legendre(nq1)
+        L1, dL1 = lagrange(self.xi, xg)
+        k3, k2, k1 = np.meshgrid(np.arange(nq1), np.arange(nq1), np.arange(nq1), indexing="ij")
+        Q = np.stack([k1.ravel(), k2.ravel(), k3.ravel()], axis=1)
+        lc = self.loc
+        tab = lambda f0, f1, f2: f0[Q[:, 0][:, None], lc[:, 0][None, :]] * f1[Q[:, 1][:, None], lc[:, 1][None, :]] \
+            * f2[Q[:, 2][:, None], lc[:, 2][None, :]]
+        self.B = tab(L1, L1, L1)
+        self.Dref = [tab(dL1, L1, L1), tab(L1, dL1, L1), tab(L1, L1, dL1)]
+        self.xq_ref = xg[Q]
+        self.wq = wg[Q[:, 0]] * wg[Q[:, 1]] * wg[Q[:, 2]]
+        on_bnd = np.any((np.abs(self.nodes - lo[None, :]) < tol) | (np.abs(self.nodes - hi[None, :]) < tol), axis=1)
+        self.boundary_free = on_bnd[self.free]
+
+    def stiffness_and_load(self, f):
+        """K = P^T K_all P with K_all = int grad N . grad N over the leaves, and
+        F = P^T int f N (Gauss-Legendre (p+2)^3 per leaf)."""
+        rows, cols, vals = [], [], []
+        F = np.zeros(self.n_all)
+        for li, (x0, h, _) in enumerate(self.leaves):
+            idx = self.conn[li]
+            G = [self.Dref[a] * (2.0 / h[a]) for a in range(3)]
+            w = self.wq * np.prod(h) / 8.0
+            Kc = sum(G[a].T @ (w[:, None] * G[a]) for a in range(3))
+            rows.append(np.repeat(idx, len(idx)))
+            cols.append(np.tile(idx, len(idx)))
+            vals.append(Kc.ravel())
+            pts = x0[None, :] + 0.5 * (self.xq_ref + 1.0) * h[None, :]
+            np.add.at(F, idx, self.B.T @ (w * f(pts)))
+        K_all = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                              shape=(self.n_all, self.n_all))
+        return (self.P.T @ K_all @ self.P).tocsr(), self.P.T @ F
+
+    def solve_poisson(self, f, g):
+        """-lap u = f with u = g on the boundary, in the constrained space: free
+        values (n_free,) and all node values (n_all,)."""
+        K, F = self.stiffness_and_load(f)
+        B = np.where(self.boundary_free)[0]
+        I = np.where(~self.boundary_free)[0]
+        u = np.zeros(len(self.free))
+        u[B] = g(self.nodes[self.free[B]])
+        u[I] = spla.spsolve(K[I][:, I].tocsc(), F[I] - K[I][:, B] @ u[B])
+        return u, self.P @ u
+
+    def evaluate(self, u_all, li: int, pts):
+        """Values at physical points inside leaf li."""
+        x0, h, _ = self.leaves[li]
+        ref = 2.0 * (np.asarray(pts) - x0[None, :]) / h[None, :] - 1.0
+        L = [lagrange(self.xi, ref[:, a])[0] for a in range(3)]
+        B = L[0][:, self.loc[:, 0]] * L[1][:, self.loc[:, 1]] * L[2][:, self.loc[:, 2]]
+        return B @ u_all[self.conn[li]]
