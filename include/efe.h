@@ -306,7 +306,8 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
  * each operation, in reverse order) of n_steps calls of efe_magnus_step's
  * predictor-corrector step (Eq. ApproxMagnus with the mid-point density of
  * the predictor, field at t_n + dt/2, t_n = n dt), with float64 applies (float32
- * pairs when the context's precision is EFE_PAIR) and float64 elsewhere:
+ * pairs when the context's precision is EFE_PAIR; float64 for EFE_MIXED and
+ * EFE_TC contexts) and float64 elsewhere:
  *   J = (1/|W|) sum_{n in W} d . mu(rho_n),   W = [window_first, window_last],
  *   grad = dJ / d(amp, omega, sigma)   (omega entry 0 for EFE_FIELD_GAUSS).
  * The derivative of each exponential exp(-i dt Hbar) is its Frechet derivative,
