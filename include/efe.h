@@ -333,6 +333,33 @@ efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_st
                               int32_t window_last, int32_t checkpoint_every, int32_t n_quad_s, double* J_host,
                               double* grad_host, void* stream);
 
+/* Nuclear potential in the electrostatically enriched basis (Eqs. PhiEFE,
+ * DiscretePoisson; the paper's electrostatic enrichment of the nuclear
+ * potential).  Replaces the context's nuclear potential -sum Z/|x - R| at the
+ * quadrature points by the finite element solution for Gaussian-smeared
+ * nuclei: charge b = -sum_J Z_J g_sigma(|x - R_J|) (normalised Gaussians of
+ * width sigma), phi^h = sum_j N_j phi_j + sum_J Ntil_J phi^E_J with one
+ * enrichment function per atom, the atom's smeared-nucleus potential
+ * -Z_J erf(r / (sqrt2 sigma)) / r truncated by the smooth cutoff (r0, s) and
+ * orthogonalised against the classical functions in the GLL-lumped inner
+ * product, stiffness (1/4pi) int grad . grad, and the smeared-nucleus
+ * potential as Dirichlet data on the boundary nodes.  Cell integrals of the
+ * atomic parts and of the charge use a composite Gauss-Legendre rule of sub^3
+ * sub-cells with n_quad^3 points each (n_quad 0: p + 2); the Galerkin system is
+ * solved exactly (to rounding) around the direct Poisson solver by block
+ * elimination of the n_atoms enrichment unknowns.  vN_dev (nullable): device
+ * [n_cells][n_q] doubles receiving the new potential at the quadrature points;
+ * phiE_host (nullable): host [n_atoms] enrichment coefficients.  Later steps,
+ * kicks and adjoints use the new potential; the propagation state is
+ * invalidated (the next efe_magnus_step recomputes rho).  Allocates device
+ * memory for the call (about 4 n_atoms + 10 vectors of n_nodes doubles) and
+ * synchronises `stream`.  Errors: EFE_ERR_ARG (sigma <= 0, s <= 0, r0 <= s,
+ * sub outside [1, 8], n_quad outside [p + 1, 8] and not 0, a support sphere of
+ * radius r0 reaching the domain boundary), EFE_ERR_NOT_SPD (the eliminated
+ * block not positive definite), EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+efe_status efe_nuclear_enriched(efe_ctx* ctx, double sigma, double r0, double s, int32_t sub, int32_t n_quad,
+                                double* vN_dev, double* phiE_host, void* stream);
+
 /* Spectra of dipole traces (Sec. Results: the absorption spectrum of the weak
  * perturbation study and the power spectrum of the high-harmonic study); no
  * context needed.  Samples at t_n = n dt, n = 0 .. n_t - 1, on the device;

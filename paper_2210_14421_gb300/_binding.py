@@ -24,7 +24,7 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_apply_H", "efe_magnus_step", "efe_reset_state", "efe_density_vxc", "efe_hartree", "efe_dipole",
             "efe_kick", "efe_init_orbitals", "efe_profile", "efe_profile_read", "efe_selftest",
             "efe_apply_H_noalloc", "efe_tuning", "efe_adjoint_dipole",
-            "efe_absorption_spectrum", "efe_power_spectrum"]
+            "efe_absorption_spectrum", "efe_power_spectrum", "efe_nuclear_enriched"]
 
 
 class MeshDesc(C.Structure):
@@ -103,6 +103,7 @@ def lib(path: str = LIB_PATH):
     L.efe_power_spectrum.argtypes = [vp, i64, i64, dbl, vp, i64, dbl, vp, vp]
     L.efe_adjoint_dipole.argtypes = [vp, vp, i32, dbl, C.POINTER(Field), pdbl, i32, i32, i32, i32, C.POINTER(dbl),
                                      pdbl, vp]
+    L.efe_nuclear_enriched.argtypes = [vp, dbl, dbl, dbl, i32, i32, vp, pdbl, vp]
     for name in EXPORTED:
         if name != "efe_last_error":
             getattr(L, name).restype = C.c_int
@@ -290,6 +291,17 @@ class Context:
 
     def dipole(self, rho, mu):
         self._check(lib().efe_dipole(self.h, _ptr(rho), _ptr(mu), _stream()))
+
+    def nuclear_enriched(self, sigma: float, r0: float, s: float, sub: int = 2, n_quad: int = 0):
+        """Installs the nuclear potential of Gaussian-smeared nuclei solved in the
+        electrostatically enriched basis; returns it at the quadrature points
+        (device float64 [n_cells, n_q]) and the enrichment coefficients (numpy [n_atoms])."""
+        import torch
+        vN = torch.empty((self.n_cells, self.n_q), dtype=torch.float64, device="cuda")
+        phiE = np.zeros(len(self.wl.Z))
+        self._check(lib().efe_nuclear_enriched(self.h, float(sigma), float(r0), float(s), int(sub), int(n_quad),
+                                               _ptr(vN), _dptr(phiE), _stream()))
+        return vN, phiE
 
     def kick(self, psi, fields):
         st = lib().efe_kick(self.h, _ptr(psi), fields_array(fields), _stream())

@@ -688,6 +688,18 @@ efe_status efe_dipole(efe_ctx* ctx, const double* rho_dev, double* mu_dev, void*
   return EFE_OK;
 }
 
+efe_status efe_nuclear_enriched(efe_ctx* ctx, double sigma, double r0, double s, int32_t sub, int32_t n_quad,
+                                double* vN_dev, double* phiE_host, void* stream) {
+  CHECK_CTX(ctx);
+  Ctx& c = ctx->c;
+  cudaStream_t st = as_stream(stream);
+  efe_status r = nuclear_enriched(c, sigma, r0, s, sub, n_quad, phiE_host, st);
+  if (r != EFE_OK) return r;
+  if (vN_dev)
+    TRY_CUDA(c, cudaMemcpyAsync(vN_dev, c.d_vN, sizeof(double) * c.nc * c.nq, cudaMemcpyDeviceToDevice, st), "copy");
+  return EFE_OK;
+}
+
 efe_status efe_kick(efe_ctx* ctx, double* psi_bar_dev, const efe_field* fields_host, void* stream) {
   CHECK_CTX(ctx);
   Ctx& c = ctx->c;

@@ -278,7 +278,11 @@ cudaError_t launch_axpby(double* y, const double* a, const double* b, double ca,
 // fast-diagonalisation Hartree solve (k_poisson.cu)
 cudaError_t setup_fdm(Ctx& c);
 cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, cudaStream_t s,
-                      bool homogeneous = false);
+                      bool homogeneous = false, const double* phiB = nullptr);
+// nuclear potential of smeared nuclei in the electrostatically enriched basis (k_electro.cu):
+// replaces d_vN; phiE_host [n_atoms] receives the enrichment coefficients (nullable)
+efe_status nuclear_enriched(Ctx& c, double sigma, double r0, double s, int sub, int n_quad, double* phiE_host,
+                            cudaStream_t st);
 // context workspaces for C complex columns of leading dimension ld; the operator of v (api.cu)
 efe_status ensure_ws(Ctx& c, long long C, long long ld);
 efe_status build_op(Ctx& c, const double* v, int batch, double kin, cudaStream_t s);

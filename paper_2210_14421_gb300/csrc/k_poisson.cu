@@ -212,8 +212,11 @@ cudaError_t setup_fdm(Ctx& c) {
 }
 
 // phi (n_h x nb) <- solution of the Dirichlet problem for the load vector d;
-// Ap is scratch (n_h x nb).
-cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, cudaStream_t s, bool homogeneous) {
+// Ap is scratch (n_h x nb).  Boundary data: zero if homogeneous, else phiB
+// (n_h, nb == 1) when given, else the context's Hartree data.
+cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, cudaStream_t s, bool homogeneous,
+                      const double* phiB) {
+  if (phiB && nb != 1) return cudaErrorInvalidValue;
   const double scale = 1.0 / (2.0 * 3.14159265358979323846);
   const int nx = c.fdm_n[0], ny = c.fdm_n[1], nz = c.fdm_n[2];
   const long long n = (long long)nx * ny * nz;
@@ -222,7 +225,7 @@ cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, 
   const double *Vx = c.d_fdmV[0], *Vy = c.d_fdmV[1], *Vz = c.d_fdmV[2];
   // Ap = A phi_B (output on interior nodes only)
   EFE_CUDA_TRY(cudaMemsetAsync(Ap, 0, sizeof(double) * c.n_h * nb, s));
-  if (!homogeneous) EFE_CUDA_TRY(launch_laplace(c, c.d_phiB_nb, Ap, nb, 0, scale, s));
+  if (!homogeneous) EFE_CUDA_TRY(launch_laplace(c, phiB ? phiB : c.d_phiB_nb, Ap, nb, 0, scale, s));
   const unsigned g1 = (unsigned)((n * nb + 255) / 256);
   k_fdm_gather<<<g1, 256, 0, s>>>(d, Ap, c.Nx, c.Ny, nx, ny, nz, nb, t0);
   note_launch();
@@ -246,7 +249,7 @@ cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, 
                                       nz, s)));                                                         // y
     EFE_CUDA_TRY((dgemm<false, true>(ny * nz, nx, nx, b, nx, 0, Vx, nx, 0, a, nx, 0, 1, s)));           // x
   }
-  k_fdm_scatter<<<(unsigned)((c.n_h * nb + 255) / 256), 256, 0, s>>>(t0, homogeneous ? nullptr : c.d_phiB, c.n_h,
+  k_fdm_scatter<<<(unsigned)((c.n_h * nb + 255) / 256), 256, 0, s>>>(t0, homogeneous ? nullptr : (phiB ? phiB : c.d_phiB), c.n_h,
                                                                     c.Nx, c.Ny, nx, ny, nz, nb, phi);
   note_launch();
   return cudaGetLastError();

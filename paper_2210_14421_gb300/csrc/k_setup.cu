@@ -5,6 +5,7 @@
 #include <cmath>
 
 #include "efe_internal.h"
+#include "radial.cuh"
 
 namespace efe {
 
@@ -94,18 +95,6 @@ __device__ void solid(int l, int m, double x, double y, double z, double& S, dou
   else if (m == 0) { S = 2 * z * z - x * x - y * y; g[0] = -2 * x; g[1] = -2 * y; g[2] = 4 * z; }
   else if (m == 1) { S = x * z; g[0] = z; g[2] = x; }
   else { S = x * x - y * y; g[0] = 2 * x; g[1] = -2 * y; }
-}
-
-// smooth cutoff u(r) = 1 - S(t), t = (r - r0 + s)/s, S(t) = g(t)/(g(t)+g(1-t)), g = exp(-1/t)
-__device__ void cutoff(double r, double r0, double s, double& u, double& du) {
-  const double t = (r - (r0 - s)) / s;
-  if (t <= 0.0) { u = 1.0; du = 0.0; return; }
-  if (t >= 1.0) { u = 0.0; du = 0.0; return; }
-  const double g1 = exp(-1.0 / t), g2 = exp(-1.0 / (1.0 - t));
-  const double den = g1 + g2;
-  const double dg1 = g1 / (t * t), dg2 = g2 / ((1.0 - t) * (1.0 - t));
-  u = 1.0 - g1 / den;
-  du = -((dg1 * g2 + g1 * dg2) / (den * den)) / s;
 }
 
 // values and gradients of N^A for every (pair, q)

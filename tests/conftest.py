@@ -10,6 +10,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+# GPU test modules of components that have not yet run on a device: they run
+# after the rest of the suite, so that under -x a failure there cannot hide the
+# results of the established tests.
+RUN_LAST = ("test_gpu_electrostatic.py",)
+
+
+def pytest_collection_modifyitems(config, items):
+    items.sort(key=lambda it: os.path.basename(str(it.fspath)) in RUN_LAST)
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the built libefe library")
     config.addinivalue_line("markers", "slow: oracle runs that take tens of seconds")

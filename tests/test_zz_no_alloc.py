@@ -3,8 +3,9 @@
 Callers that cannot allocate device memory while they run (a host framework
 that owns all device memory, or code recorded into a CUDA graph) use the
 allocation-free entry point; it must give the same Y = Hbar X as the regular
-apply.  This file is collected last so a failure here comes after every other
-test has run; it also passes on its own in a fresh process."""
+apply.  This file is collected after the other established GPU tests, so a
+failure here comes after they have run; it also passes on its own in a fresh
+process."""
 import ctypes
 
 import numpy as np
