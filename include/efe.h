@@ -327,7 +327,8 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
  * device memory per call and synchronises `stream`.  Returns EFE_WARN_KRYLOV_CAP
  * (J and grad written) if any exponential stopped at k_max.  Errors: EFE_ERR_ARG
  * (bad sizes, window outside [1, n_steps], n_quad_s outside [1, 64], batch != 1,
- * another functional or step scheme, unsupported field), EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+ * another functional or step scheme, unsupported field, the enriched Hartree
+ * solve installed), EFE_ERR_NOMEM, EFE_ERR_CUDA. */
 efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_steps, double dt,
                               const efe_field* field_host, const double* direction_host, int32_t window_first,
                               int32_t window_last, int32_t checkpoint_every, int32_t n_quad_s, double* J_host,
@@ -359,6 +360,30 @@ efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_st
  * block not positive definite), EFE_ERR_NOMEM, EFE_ERR_CUDA. */
 efe_status efe_nuclear_enriched(efe_ctx* ctx, double sigma, double r0, double s, int32_t sub, int32_t n_quad,
                                 double* vN_dev, double* phiE_host, void* stream);
+
+/* Hartree potential in the electrostatically enriched basis (Eq. PhiEFE for the
+ * Hartree potential, Eq. DiscretePoisson).  Installs, for every later Hartree
+ * solve of the context (efe_hartree and the Magnus steps), one enrichment
+ * function per atom: the Hartree potential of the isolated neutral atom
+ * whose Z electrons fill the shells of the atom's wavefunction enrichment
+ * functions (distinct radial kind, n, l, zeta, filled in the order of n, then
+ * l, two electrons per orbital; tabulated on r = 60 t^2 bohr, t uniform, 24001
+ * points), truncated by the smooth cutoff (r0, s) and orthogonalised against
+ * the classical functions in the GLL-lumped inner product.  The solve keeps
+ * the classical Dirichlet data and load int rho N (quadrature points), adds
+ * the enrichment loads int rho N^A at the quadrature points, and is exact
+ * (to rounding) by block elimination around the direct Poisson solver; the
+ * eliminated n_atoms x n_atoms block and the n_atoms direct solves it needs
+ * are computed here, with cell integrals on a composite Gauss-Legendre rule
+ * of sub^3 sub-cells with n_quad^3 points each (n_quad 0: p + 2).  v_H at
+ * the quadrature points includes the enrichment functions.  Keeps 3 n_atoms
+ * vectors of n_nodes doubles on the device; synchronises `stream`; the
+ * propagation state is invalidated.  efe_adjoint_dipole is not available
+ * once installed.  Errors: EFE_ERR_ARG (the context's Hartree method is not
+ * EFE_HARTREE_FDM; s <= 0, r0 <= s, sub outside [1, 8], n_quad outside
+ * [p + 1, 8] and not 0, a support sphere reaching the domain boundary),
+ * EFE_ERR_NOT_SPD, EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+efe_status efe_hartree_enriched(efe_ctx* ctx, double r0, double s, int32_t sub, int32_t n_quad, void* stream);
 
 /* Spectra of dipole traces (Sec. Results: the absorption spectrum of the weak
  * perturbation study and the power spectrum of the high-harmonic study); no

@@ -98,20 +98,24 @@ class State:
     vhxc_prev: np.ndarray = None   # v_H + v_xc of the previous step (None: no history)
 
 
-def potentials(system: System, rho: np.ndarray, xc_kind: str = "pw92"):
-    """v_H and v_xc for a batch of densities."""
+def potentials(system: System, rho: np.ndarray, xc_kind: str = "pw92", hartree=None):
+    """v_H and v_xc for a batch of densities.  hartree(system, rho_b) -> (classical
+    nodal values, v_H at the quadrature points) replaces the classical Poisson
+    solve (e.g. an enriched solve of module electrostatic)."""
+    solve = hartree or poisson.solve
     vH = np.zeros_like(rho)
     vxc = np.zeros_like(rho)
     phi = np.zeros((rho.shape[0], system.n_h))
     for b in range(rho.shape[0]):
-        phi[b], vH[b] = poisson.solve(system, rho[b])
+        phi[b], vH[b] = solve(system, rho[b])
         vxc[b] = xc.lda(rho[b], xc_kind)[1]
     return vH, vxc, phi
 
 
-def make_state(system: System, psi_bar: np.ndarray, occ: np.ndarray, batch: int, xc_kind: str = "pw92") -> State:
+def make_state(system: System, psi_bar: np.ndarray, occ: np.ndarray, batch: int, xc_kind: str = "pw92",
+               hartree=None) -> State:
     rho = density(system, psi_bar, occ, batch)
-    vH, vxc, phi = potentials(system, rho, xc_kind)
+    vH, vxc, phi = potentials(system, rho, xc_kind, hartree)
     return State(rho=rho, vH=vH, vxc=vxc, phi=phi)
 
 
@@ -131,7 +135,8 @@ def kexp_members(system: System, psi_bar, v_members, n_orb, dt, tol, k_max, fixe
 
 
 def magnus_step(system: System, psi_bar: np.ndarray, state: State, t: float, dt: float, fields, occ,
-                tol: float, k_max: int, fixed_k: int = 0, vN=None, scheme: str = "pc", xc_kind: str = "pw92"):
+                tol: float, k_max: int, fixed_k: int = 0, vN=None, scheme: str = "pc", xc_kind: str = "pw92",
+                hartree=None):
     """One step: predictor-corrector S1..S6 (scheme "pc"), or the
     potential-extrapolation step (scheme "extrapolated"; predictor-corrector
     while the state has no history).  Returns (psi_new, state_new, mu
@@ -151,12 +156,12 @@ def magnus_step(system: System, psi_bar: np.ndarray, state: State, t: float, dt:
         psi_p, k1 = kexp_members(system, psi_bar, v1, n_orb, dt, tol, k_max, fixed_k)
         rho_p = density(system, psi_p, occ, batch)
         rho_mid = 0.5 * (state.rho + rho_p)
-        vH_mid, vxc_mid, _ = potentials(system, rho_mid, xc_kind)
+        vH_mid, vxc_mid, _ = potentials(system, rho_mid, xc_kind, hartree)
         v2 = [vN + vH_mid[b] + vxc_mid[b] + field_potential(system, Emid[b]) for b in range(batch)]
     else:
         raise ValueError("unknown scheme")
     psi_new, k2 = kexp_members(system, psi_bar, v2, n_orb, dt, tol, k_max, fixed_k)
-    new_state = make_state(system, psi_new, occ, batch, xc_kind)
+    new_state = make_state(system, psi_new, occ, batch, xc_kind, hartree)
     new_state.vhxc_prev = vhxc
     mu = np.stack([dipole(system, new_state.rho[b]) for b in range(batch)])
     return psi_new, new_state, mu, {"k_pred": k1, "k_corr": k2}

@@ -24,7 +24,8 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_apply_H", "efe_magnus_step", "efe_reset_state", "efe_density_vxc", "efe_hartree", "efe_dipole",
             "efe_kick", "efe_init_orbitals", "efe_profile", "efe_profile_read", "efe_selftest",
             "efe_apply_H_noalloc", "efe_tuning", "efe_adjoint_dipole",
-            "efe_absorption_spectrum", "efe_power_spectrum", "efe_nuclear_enriched"]
+            "efe_absorption_spectrum", "efe_power_spectrum", "efe_nuclear_enriched",
+            "efe_hartree_enriched"]
 
 
 class MeshDesc(C.Structure):
@@ -104,6 +105,7 @@ def lib(path: str = LIB_PATH):
     L.efe_adjoint_dipole.argtypes = [vp, vp, i32, dbl, C.POINTER(Field), pdbl, i32, i32, i32, i32, C.POINTER(dbl),
                                      pdbl, vp]
     L.efe_nuclear_enriched.argtypes = [vp, dbl, dbl, dbl, i32, i32, vp, pdbl, vp]
+    L.efe_hartree_enriched.argtypes = [vp, dbl, dbl, i32, i32, vp]
     for name in EXPORTED:
         if name != "efe_last_error":
             getattr(L, name).restype = C.c_int
@@ -302,6 +304,11 @@ class Context:
         self._check(lib().efe_nuclear_enriched(self.h, float(sigma), float(r0), float(s), int(sub), int(n_quad),
                                                _ptr(vN), _dptr(phiE), _stream()))
         return vN, phiE
+
+    def hartree_enriched(self, r0: float, s: float, sub: int = 2, n_quad: int = 0):
+        """Installs the enriched Hartree solve (atomic Hartree potentials as enrichment)
+        for every later Hartree solve of the context."""
+        self._check(lib().efe_hartree_enriched(self.h, float(r0), float(s), int(sub), int(n_quad), _stream()))
 
     def kick(self, psi, fields):
         st = lib().efe_kick(self.h, _ptr(psi), fields_array(fields), _stream())

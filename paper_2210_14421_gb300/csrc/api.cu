@@ -59,6 +59,7 @@ Ctx::~Ctx() {
   dfree(d_fdmT);
   dfree(op.W64); dfree(op.W32); dfree(op.E64); dfree(op.E32); dfree(op.W2); dfree(op.E2); dfree(op.HEE);
   tc_free(tc);
+  hen_free(hen);
   dfree(d_rho); dfree(d_vH); dfree(d_vxc); dfree(d_vprev); dfree(d_Q); dfree(d_psi_p); dfree(d_xE); dfree(d_yE);
   dfree(d_lz); dfree(d_lzi); dfree(d_rho2); dfree(d_v); dfree(d_cg); dfree(d_red);
   for (cudaEvent_t e : prof.pool) cudaEventDestroy(e);
@@ -700,6 +701,11 @@ efe_status efe_nuclear_enriched(efe_ctx* ctx, double sigma, double r0, double s,
   return EFE_OK;
 }
 
+efe_status efe_hartree_enriched(efe_ctx* ctx, double r0, double s, int32_t sub, int32_t n_quad, void* stream) {
+  CHECK_CTX(ctx);
+  return hartree_enrich_install(ctx->c, r0, s, sub, n_quad, as_stream(stream));
+}
+
 efe_status efe_kick(efe_ctx* ctx, double* psi_bar_dev, const efe_field* fields_host, void* stream) {
   CHECK_CTX(ctx);
   Ctx& c = ctx->c;
@@ -765,6 +771,10 @@ efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_st
       !std::isfinite(dt) || window_first < 1 || window_last < window_first || window_last > n_steps ||
       checkpoint_every < 1 || n_quad_s < 1 || n_quad_s > 64) {
     c.err = "efe_adjoint_dipole: invalid argument";
+    return EFE_ERR_ARG;
+  }
+  if (c.hen.on) {
+    c.err = "efe_adjoint_dipole: the transposed Hartree map of the enriched solve is not implemented";
     return EFE_ERR_ARG;
   }
   if (c.batch != 1) {

@@ -98,6 +98,30 @@ struct TcState {
   int n_sm = 0;                   // SMs of the context's device (persistent grid)
 };
 
+// Hartree potential in the electrostatically enriched basis (k_electro.cu), installed by
+// efe_hartree_enriched: one enrichment function per atom, the atom's Hartree potential
+// (shell-filled neutral atom, tabulated) times the smooth cutoff; the eliminated block is
+// precomputed so that every solve is the direct Poisson solve plus rank-nA corrections.
+struct HartreeEnr {
+  bool on = false;
+  int nA = 0, n_tab = 0;
+  double r0 = 0, s = 0, rmax = 0;
+  double* C = nullptr;       // [nA][n_h] orthogonalisation coefficients int N^A_J N_i / M_i
+  double* G = nullptr;       // [nA][n_h] int grad N^A_J . grad N_n
+  double* X = nullptr;       // [nA][n_h] A_II^-1 A_IJ
+  double* Sinv = nullptr;    // [nA][nA] (A_EE - A_EI X)^-1
+  double* atoms = nullptr;   // [nA][4] Z, x, y, z
+  double* r = nullptr;       // [n_tab] radial grid
+  double* v = nullptr;       // [nA][n_tab] atomic Hartree potentials
+  double* q = nullptr;       // [nA][n_tab] enclosed charges
+  double* nel = nullptr;     // [nA] electrons per atom
+  int* pair_cell = nullptr;  // (cell, atom) pairs of the supports, for the per-solve loads
+  int* pair_fn = nullptr;
+  long long n_pairs = 0;
+  double* small = nullptr;   // [3][nA][batch] loads int rho N^A, right sides, coefficients
+};
+void hen_free(HartreeEnr& h);
+
 // Per-launch timing of the cell-apply kernel (enabled by efe_profile).
 struct Prof {
   bool on = false;
@@ -167,6 +191,7 @@ struct Ctx {
   // operators
   Operator op;                 // current operator (efe_set_potential / magnus)
   TcState tc;                  // its tensor-core slices, rebuilt with it while tc_on
+  HartreeEnr hen;              // enriched Hartree solve (off unless installed)
   bool tc_on = false;
   // autotuned cell-apply tile width per precision [FP64, MIXED, PAIR]: variant 0 (widest tile
   // fitting two blocks per SM) or 1 (half as wide); -1 until timed
@@ -283,6 +308,12 @@ cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, 
 // replaces d_vN; phiE_host [n_atoms] receives the enrichment coefficients (nullable)
 efe_status nuclear_enriched(Ctx& c, double sigma, double r0, double s, int sub, int n_quad, double* phiE_host,
                             cudaStream_t st);
+// installs the enriched Hartree solve (k_electro.cu)
+efe_status hartree_enrich_install(Ctx& c, double r0, double s, int sub, int n_quad, cudaStream_t st);
+// the enriched Hartree solve for the load d = int rho N ([n_h][batch], assembled): the classical part
+// into c.d_phi, v_H at the quadrature points into vH; Ap, Lz, u: [n_h][batch] scratch
+cudaError_t hartree_enriched_solve(Ctx& c, const double* rho, double* vH, const double* d, double* Ap, double* Lz,
+                                   double* u, cudaStream_t s);
 // context workspaces for C complex columns of leading dimension ld; the operator of v (api.cu)
 efe_status ensure_ws(Ctx& c, long long C, long long ld);
 efe_status build_op(Ctx& c, const double* v, int batch, double kin, cudaStream_t s);

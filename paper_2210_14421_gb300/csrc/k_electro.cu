@@ -48,20 +48,62 @@ __device__ __forceinline__ void nuc_radial(double z, double a, double r, double&
   df = r > 1e-8 ? -z * (2.0 * a * exp(-(a * r) * (a * r)) * rsqpi / r - erf(a * r) / (r * r)) : 0.0;
 }
 
-// Atomic part N^A = f u of the atom at (ax, ay, az) with charge z, and its gradient.
-__device__ __forceinline__ void nuc_atomic(double z, double ax, double ay, double az, double a, double r0, double s,
-                                           double x, double y, double w, double& v, double g[3]) {
-  const double dx = x - ax, dy = y - ay, dz = w - az;
+// Radial parts of the atomic functions.  NucRadial: one smeared nucleus,
+// f = -Z erf(a r) / r.  TabRadial: the Hartree potential of an isolated
+// neutral atom tabulated on r_i = rmax (i / (n - 1))^2, linear interpolation
+// in r between the table points, f = n_el / r and Q = n_el beyond the table;
+// df/dr = -Q(r) / r^2 with Q the enclosed charge.  atoms: [J][4] = Z, x, y, z.
+struct NucRadial {
+  double a;
+  __device__ void operator()(const double* atoms, int J, double r, double& f, double& df) const {
+    nuc_radial(atoms[4 * J], a, r, f, df);
+  }
+};
+
+struct TabRadial {
+  const double* r;     // [n] grid
+  const double* v;     // [nA][n] potential
+  const double* q;     // [nA][n] enclosed charge
+  const double* nel;   // [nA] electrons (Q at the end of the table)
+  int n;
+  double rmax;
+  __device__ void operator()(const double*, int J, double x, double& f, double& df) const {
+    const double rl = r[n - 1];
+    double Q;
+    if (x <= rl) {
+      // interval [r_j, r_j+1] holding x: guess from the grid law, then settle on the table values
+      int j = (int)(sqrt(fmax(x, 0.0) / rmax) * (n - 1));
+      j = min(max(j, 0), n - 2);
+      while (j > 0 && r[j] > x) --j;
+      while (j < n - 2 && r[j + 1] <= x) ++j;
+      const double h = r[j + 1] - r[j];
+      const double* vv = v + (long long)J * n;
+      const double* qq = q + (long long)J * n;
+      f = (vv[j + 1] - vv[j]) / h * (x - r[j]) + vv[j];
+      Q = (qq[j + 1] - qq[j]) / h * (x - r[j]) + qq[j];
+    } else {
+      f = nel[J] / fmax(x, 1e-300);
+      Q = nel[J];
+    }
+    df = x > 0.0 ? -Q / (x * x) : 0.0;
+  }
+};
+
+// Atomic part N^A_J = f u (cutoff r0, s) at (x, y, w) and its gradient.
+template <class Rad>
+__device__ __forceinline__ void atomic_part(const Rad& rad, const double* atoms, int J, double r0, double s, double x,
+                                            double y, double w, double& v, double g[3]) {
+  const double dx = x - atoms[4 * J + 1], dy = y - atoms[4 * J + 2], dz = w - atoms[4 * J + 3];
   const double r = sqrt(dx * dx + dy * dy + dz * dz);
   double f, df, u, du;
-  nuc_radial(z, a, r, f, df);
+  rad(atoms, J, r, f, df);
   cutoff(r, r0, s, u, du);
   v = f * u;
-  const double rad = df * u + f * du;
+  const double radial = df * u + f * du;
   const double inv = r > 0.0 ? 1.0 / r : 0.0;
-  g[0] = rad * dx * inv;
-  g[1] = rad * dy * inv;
-  g[2] = rad * dz * inv;
+  g[0] = radial * dx * inv;
+  g[1] = radial * dy * inv;
+  g[2] = radial * dz * inv;
 }
 
 struct CellGeo {
@@ -81,7 +123,8 @@ __device__ __forceinline__ CellGeo cell_geo(const MeshView& mesh, int c) {
   return g;
 }
 
-// Sum over the block (blockDim.x == kNucThreads); the result is valid in thread 0.
+// Sum over the block (blockDim.x == kNucThreads), returned to every thread;
+// safe to call again right away.
 __device__ double block_sum(double v, double* red) {
   red[threadIdx.x] = v;
   __syncthreads();
@@ -89,17 +132,21 @@ __device__ double block_sum(double v, double* red) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  return red[0];
+  const double out = red[0];
+  __syncthreads();
+  return out;
 }
 
 // Cell integrals with the composite rule (m1 points per axis, tables `rule` =
 // L [m1][P1], dL [m1][P1], xs [m1], ws [m1] on [-1, 1]).  One block per item:
 // for fn[k] = J >= 0, over cell cells[k]
 //   bA[J][g] += int N^A_J N_g,  G[J][g] += int grad N^A_J . grad N_g,  ba[J] += int b N^A_J;
-// for fn[k] < 0 the charge load dC[g] += int b N_g.
+// for fn[k] < 0 the charge load dC[g] += int b N_g (b from the smeared nuclei;
+// with norm = 0 the charge terms vanish, as for the Hartree enrichment).
+template <class Rad>
 __global__ void __launch_bounds__(kNucThreads)
 k_nuc_cells(const MeshView mesh, const double* __restrict__ rule, int m1, const int* __restrict__ cells,
-            const int* __restrict__ fn, const double* __restrict__ atoms, int n_atoms, double a, double norm,
+            const int* __restrict__ fn, const double* __restrict__ atoms, int n_atoms, const Rad rad, double norm,
             double inv2s2, double r0, double s, double* __restrict__ bA, double* __restrict__ G,
             double* __restrict__ ba, double* __restrict__ dC) {
   extern __shared__ double sh[];
@@ -140,7 +187,7 @@ k_nuc_cells(const MeshView mesh, const double* __restrict__ rule, int m1, const 
         v = w * b;
       } else {
         double na, gn[3];
-        nuc_atomic(atoms[4 * J], atoms[4 * J + 1], atoms[4 * J + 2], atoms[4 * J + 3], a, r0, s, x, y, zc, na, gn);
+        atomic_part(rad, atoms, J, r0, s, x, y, zc, na, gn);
         v = w * na;
         g[0] = w * gn[0];
         g[1] = w * gn[1];
@@ -193,10 +240,11 @@ k_nuc_cells(const MeshView mesh, const double* __restrict__ rule, int m1, const 
 }
 
 // AA[J][K] (and AA[K][J]) += int grad N^A_J . grad N^A_K over cell cells[k], J = fa[k] <= K = fb[k].
+template <class Rad>
 __global__ void __launch_bounds__(kNucThreads)
 k_nuc_aa(const MeshView mesh, const double* __restrict__ rule, int m1, const int* __restrict__ cells,
-         const int* __restrict__ fa, const int* __restrict__ fb, const double* __restrict__ atoms, double a, double r0,
-         double s, int nA, double* __restrict__ AA) {
+         const int* __restrict__ fa, const int* __restrict__ fb, const double* __restrict__ atoms, const Rad rad,
+         double r0, double s, int nA, double* __restrict__ AA) {
   __shared__ double red[kNucThreads];
   const int P1 = mesh.p + 1;
   const double* xs = rule + 2 * m1 * P1;
@@ -213,8 +261,8 @@ k_nuc_aa(const MeshView mesh, const double* __restrict__ rule, int m1, const int
     const double zc = cg.oz + 0.5 * (xs[q3] + 1.0) * cg.hz;
     const double w = ws[q1] * ws[q2] * ws[q3] * detJ;
     double va, ga[3], vb, gb[3];
-    nuc_atomic(atoms[4 * J], atoms[4 * J + 1], atoms[4 * J + 2], atoms[4 * J + 3], a, r0, s, x, y, zc, va, ga);
-    nuc_atomic(atoms[4 * K], atoms[4 * K + 1], atoms[4 * K + 2], atoms[4 * K + 3], a, r0, s, x, y, zc, vb, gb);
+    atomic_part(rad, atoms, J, r0, s, x, y, zc, va, ga);
+    atomic_part(rad, atoms, K, r0, s, x, y, zc, vb, gb);
     acc += w * (ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2]);
   }
   const double tot = block_sum(acc, red);
@@ -284,22 +332,120 @@ __global__ void k_nuc_combine(const double* __restrict__ z, const double* __rest
 }
 
 // vN[m] += sum_J xE[J] N^A_J(x_m) at the quadrature points
+template <class Rad>
 __global__ void k_nuc_add_atomic(const double* __restrict__ xq, long long npts, const double* __restrict__ atoms,
-                                 int nA, double a, double r0, double s, const double* __restrict__ xE,
+                                 int nA, const Rad rad, double r0, double s, const double* __restrict__ xE,
                                  double* __restrict__ vN) {
   const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (m >= npts) return;
   double v = 0.0;
   for (int J = 0; J < nA; ++J) {
     double na, g[3];
-    nuc_atomic(atoms[4 * J], atoms[4 * J + 1], atoms[4 * J + 2], atoms[4 * J + 3], a, r0, s, xq[3 * m],
-               xq[3 * m + 1], xq[3 * m + 2], na, g);
+    atomic_part(rad, atoms, J, r0, s, xq[3 * m], xq[3 * m + 1], xq[3 * m + 2], na, g);
     v += xE[J] * na;
   }
   vN[m] += v;
 }
 
-// distance from a point to an axis-aligned box
+
+// ---------------------------------------------------------------------------- enriched Hartree solve
+// Per-solve kernels; members m < nb of the batch, nodal vectors [n_h][nb], quadrature
+// fields [nb][n_cells][nq].
+
+// dA[J][m] += sum_q w|J| rho_m N^A_J at the quadrature points of the pair's cell
+template <class Rad>
+__global__ void __launch_bounds__(kNucThreads)
+k_hen_load(const int* __restrict__ cells, const int* __restrict__ fn, int nq, int nc, int nb,
+           const double* __restrict__ xq, const double* __restrict__ wJ, const double* __restrict__ rho,
+           const double* __restrict__ atoms, const Rad rad, double r0, double s, double* __restrict__ dA) {
+  __shared__ double wa[kMaxNQ1 * kMaxNQ1 * kMaxNQ1];
+  __shared__ double red[kNucThreads];
+  const int c = cells[blockIdx.x], J = fn[blockIdx.x];
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    const long long m = (long long)c * nq + q;
+    double na, g[3];
+    atomic_part(rad, atoms, J, r0, s, xq[3 * m], xq[3 * m + 1], xq[3 * m + 2], na, g);
+    wa[q] = wJ[m] * na;
+  }
+  __syncthreads();
+  for (int b = 0; b < nb; ++b) {
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) acc += wa[q] * rho[((long long)b * nc + c) * nq + q];
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(&dA[J * nb + b], tot);
+  }
+}
+
+// rhs[J][m] = dA[J][m] - C_J . d_m - k G_J . z_m + C_J . Lz_m   (one block per (J, m))
+__global__ void __launch_bounds__(kNucThreads)
+k_hen_rhs(const double* __restrict__ C, const double* __restrict__ G, const double* __restrict__ d,
+          const double* __restrict__ z, const double* __restrict__ Lz, const double* __restrict__ dA, long long n_h,
+          int nb, double k, double* __restrict__ rhs) {
+  __shared__ double red[kNucThreads];
+  const int J = blockIdx.x / nb, b = blockIdx.x % nb;
+  const double* cj = C + (long long)J * n_h;
+  const double* gj = G + (long long)J * n_h;
+  double ad = 0.0, az = 0.0, al = 0.0;
+  for (long long g = threadIdx.x; g < n_h; g += blockDim.x) {
+    const long long i = g * nb + b;
+    ad += cj[g] * d[i];
+    az += gj[g] * z[i];
+    al += cj[g] * Lz[i];
+  }
+  const double sd = block_sum(ad, red);
+  const double sz = block_sum(az, red);
+  const double sl = block_sum(al, red);
+  if (threadIdx.x == 0) rhs[blockIdx.x] = dA[blockIdx.x] - sd - k * sz + sl;
+}
+
+// xE[J][m] = sum_K Sinv[J][K] rhs[K][m]
+__global__ void k_hen_coef(const double* __restrict__ Sinv, const double* __restrict__ rhs, int nA, int nb,
+                           double* __restrict__ xE) {
+  for (int i = threadIdx.x; i < nA * nb; i += blockDim.x) {
+    const int J = i / nb, b = i % nb;
+    double v = 0.0;
+    for (int K = 0; K < nA; ++K) v += Sinv[J * nA + K] * rhs[K * nb + b];
+    xE[i] = v;
+  }
+}
+
+// phi = z - sum_J xE_J X_J (in place), u = phi - sum_J xE_J C_J
+__global__ void k_hen_combine(double* __restrict__ phi, double* __restrict__ u, const double* __restrict__ X,
+                              const double* __restrict__ C, const double* __restrict__ xE, long long n_h, int nA,
+                              int nb) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n_h * nb) return;
+  const long long g = idx / nb;
+  const int b = (int)(idx % nb);
+  double p = phi[idx], cc = 0.0;
+  for (int J = 0; J < nA; ++J) {
+    const double e = xE[J * nb + b];
+    p -= e * X[(long long)J * n_h + g];
+    cc += e * C[(long long)J * n_h + g];
+  }
+  phi[idx] = p;
+  u[idx] = p - cc;
+}
+
+// vH[m][pt] += sum_J xE[J][m] N^A_J(x_pt)
+template <class Rad>
+__global__ void k_hen_add(const double* __restrict__ xq, long long npts, int nb, const double* __restrict__ atoms,
+                          int nA, const Rad rad, double r0, double s, const double* __restrict__ xE,
+                          double* __restrict__ vH) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= npts * nb) return;
+  const int b = (int)(idx / npts);
+  const long long m = idx % npts;
+  double v = 0.0;
+  for (int J = 0; J < nA; ++J) {
+    double na, g[3];
+    atomic_part(rad, atoms, J, r0, s, xq[3 * m], xq[3 * m + 1], xq[3 * m + 2], na, g);
+    v += xE[J * nb + b] * na;
+  }
+  vH[idx] += v;
+}
+
+// ---------------------------------------------------------------------------- host side
 double box_distance(const double lo[3], const double hi[3], const double* R) {
   double d2 = 0.0;
   for (int a = 0; a < 3; ++a) {
@@ -326,38 +472,41 @@ struct Bufs {
   }
 };
 
-}  // namespace
+#define ENR_CK(x, what)                                                      \
+  do {                                                                       \
+    cudaError_t _e = (x);                                                    \
+    if (_e != cudaSuccess) {                                                 \
+      c.err = std::string(what) + ": " + cudaGetErrorString(_e);             \
+      return _e == cudaErrorMemoryAllocation ? EFE_ERR_NOMEM : EFE_ERR_CUDA; \
+    }                                                                        \
+  } while (0)
 
-efe_status nuclear_enriched(Ctx& c, double sigma, double r0, double s, int sub, int n_quad, double* phiE_host,
-                            cudaStream_t st) {
+// Checks shared by both problems: atoms present, 0 < s < r0, rule sizes, every
+// support ball inside the box (the enrichment functions vanish on the boundary).
+bool enr_args_ok(Ctx& c, double r0, double s, int sub, int& n_quad) {
   if (n_quad == 0) n_quad = c.p + 2;
-  if (!(sigma > 0.0) || !(s > 0.0) || !(r0 > s) || sub < 1 || sub > 8 || n_quad < c.p + 1 || n_quad > 8 ||
-      c.P1 > kMaxP1) {
-    c.err = "nuclear enrichment: need sigma > 0, 0 < s < r0, sub in [1, 8], n_quad in [p + 1, 8]";
-    return EFE_ERR_ARG;
+  if (c.n_atoms < 1) {
+    c.err = "electrostatic enrichment: the context has no atoms";
+    return false;
   }
-  const int nA = c.n_atoms;
-  if (nA < 1) {
-    c.err = "nuclear enrichment: the context has no atoms";
-    return EFE_ERR_ARG;
+  if (!(s > 0.0) || !(r0 > s) || sub < 1 || sub > 8 || n_quad < c.p + 1 || n_quad > 8 || c.P1 > kMaxP1) {
+    c.err = "electrostatic enrichment: need 0 < s < r0, sub in [1, 8], n_quad in [p + 1, 8]";
+    return false;
   }
   const double lo[3] = {c.xb.front(), c.yb.front(), c.zb.front()};
   const double hi[3] = {c.xb.back(), c.yb.back(), c.zb.back()};
-  for (int J = 0; J < nA; ++J)
+  for (int J = 0; J < c.n_atoms; ++J)
     for (int a = 0; a < 3; ++a)
       if (c.R[3 * J + a] - lo[a] < r0 || hi[a] - c.R[3 * J + a] < r0) {
-        c.err = "nuclear enrichment: every support (radius r0) must lie inside the box";
-        return EFE_ERR_ARG;
+        c.err = "electrostatic enrichment: every support (radius r0) must lie inside the box";
+        return false;
       }
-#define NUC_CK(x, what)                                                 \
-  do {                                                                  \
-    cudaError_t _e = (x);                                               \
-    if (_e != cudaSuccess) {                                            \
-      c.err = std::string(what) + ": " + cudaGetErrorString(_e);        \
-      return _e == cudaErrorMemoryAllocation ? EFE_ERR_NOMEM : EFE_ERR_CUDA; \
-    }                                                                   \
-  } while (0)
-  // composite 1D rule on [-1, 1] and the cell basis's Lagrange tables at its points
+  return true;
+}
+
+// Composite Gauss-Legendre rule on [-1, 1] (sub pieces of n_quad points) and the
+// cell basis's Lagrange tables there: L [m1][P1], dL [m1][P1], xs [m1], ws [m1].
+std::vector<double> composite_rule(const Ctx& c, int sub, int n_quad) {
   const int m1 = sub * n_quad, P1 = c.P1;
   std::vector<double> xg(n_quad), wg(n_quad), gll(P1), gllw(P1);
   gauss_legendre(n_quad, xg.data(), wg.data());
@@ -373,9 +522,17 @@ efe_status nuclear_enriched(Ctx& c, double sigma, double r0, double s, int sub, 
     }
   }
   lagrange_tables(P1, gll.data(), m1, xs, rule.data(), rule.data() + m1 * P1);
-  // work lists: (cell, atom) pairs of the supports, cells carrying charge, (cell, atom, atom) of overlaps
-  const double reach = 40.0 * sigma;   // exp(-(40)^2 / 2) underflows: no charge beyond
-  std::vector<int> it_cell, it_fn, aa_cell, aa_a, aa_b;
+  return rule;
+}
+
+// Work lists: (cell, atom) pairs whose cell meets the atom's support ball, cells
+// within `reach` of a nucleus as charge items (fn = -1; reach 0: none), and
+// (cell, atom, atom) overlaps with the first atom <= the second.
+struct Lists {
+  std::vector<int> it_cell, it_fn, pr_cell, pr_fn, aa_cell, aa_a, aa_b;
+};
+
+void work_lists(const Ctx& c, double r0, double reach, Lists& L) {
   std::vector<int> local;
   for (int cz = 0; cz < c.ncz; ++cz)
     for (int cy = 0; cy < c.ncy; ++cy)
@@ -385,25 +542,271 @@ efe_status nuclear_enriched(Ctx& c, double sigma, double r0, double s, int sub, 
         const double bhi[3] = {c.xb[cx + 1], c.yb[cy + 1], c.zb[cz + 1]};
         local.clear();
         bool charged = false;
-        for (int J = 0; J < nA; ++J) {
+        for (int J = 0; J < c.n_atoms; ++J) {
           const double d = box_distance(blo, bhi, &c.R[3 * J]);
           if (d < r0) local.push_back(J);
           if (d < reach) charged = true;
         }
         if (charged) {
-          it_cell.push_back(cell);
-          it_fn.push_back(-1);
+          L.it_cell.push_back(cell);
+          L.it_fn.push_back(-1);
         }
         for (size_t i = 0; i < local.size(); ++i) {
-          it_cell.push_back(cell);
-          it_fn.push_back(local[i]);
+          L.it_cell.push_back(cell);
+          L.it_fn.push_back(local[i]);
+          L.pr_cell.push_back(cell);
+          L.pr_fn.push_back(local[i]);
           for (size_t j = i; j < local.size(); ++j) {
-            aa_cell.push_back(cell);
-            aa_a.push_back(local[i]);
-            aa_b.push_back(local[j]);
+            L.aa_cell.push_back(cell);
+            L.aa_a.push_back(local[i]);
+            L.aa_b.push_back(local[j]);
           }
         }
       }
+}
+
+// Blocks of one enrichment (module comment): C (d_C), G (d_G), A_IJ (d_LC),
+// X_J = A_II^-1 A_IJ (d_X), each [nA][n_h], and on the host S = A_EE - A_EI X.
+// With a charge (norm > 0) also d = int b N (d_dC) and, on the host,
+// dE = int b N^A - C . d.  Synchronises st.
+template <class Rad>
+efe_status enr_blocks(Ctx& c, const Rad& rad, const double* d_at, double r0, double s, int sub, int n_quad,
+                      double norm, double inv2s2, double reach, const Lists& L, double* d_C, double* d_G,
+                      double* d_LC, double* d_X, double* d_dC, std::vector<double>& S, std::vector<double>& dE,
+                      cudaStream_t st) {
+  const int nA = c.n_atoms, P1 = c.P1, m1 = sub * n_quad;
+  const long long n_h = c.n_h;
+  const size_t vecs = (size_t)nA * n_h;
+  const std::vector<double> rule = composite_rule(c, sub, n_quad);
+  Bufs B;
+  double *d_rule, *d_ba, *d_AA, *d_dots, *d_Ap;
+  int *d_ic, *d_if, *d_ac, *d_aa, *d_ab;
+  ENR_CK(B.alloc(d_rule, rule.size()), "allocating");
+  ENR_CK(B.alloc(d_ba, nA), "allocating");
+  ENR_CK(B.alloc(d_AA, (size_t)nA * nA), "allocating");
+  ENR_CK(B.alloc(d_dots, (size_t)3 * nA * nA + nA), "allocating");
+  ENR_CK(B.alloc(d_Ap, (size_t)n_h), "allocating");
+  ENR_CK(B.alloc(d_ic, L.it_cell.size()), "allocating");
+  ENR_CK(B.alloc(d_if, L.it_fn.size()), "allocating");
+  ENR_CK(B.alloc(d_ac, L.aa_cell.size()), "allocating");
+  ENR_CK(B.alloc(d_aa, L.aa_a.size()), "allocating");
+  ENR_CK(B.alloc(d_ab, L.aa_b.size()), "allocating");
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+  };
+  ENR_CK(up(d_rule, rule.data(), sizeof(double) * rule.size()), "copy");
+  ENR_CK(up(d_ic, L.it_cell.data(), sizeof(int) * L.it_cell.size()), "copy");
+  ENR_CK(up(d_if, L.it_fn.data(), sizeof(int) * L.it_fn.size()), "copy");
+  ENR_CK(up(d_ac, L.aa_cell.data(), sizeof(int) * L.aa_cell.size()), "copy");
+  ENR_CK(up(d_aa, L.aa_a.data(), sizeof(int) * L.aa_a.size()), "copy");
+  ENR_CK(up(d_ab, L.aa_b.data(), sizeof(int) * L.aa_b.size()), "copy");
+  for (double* v : {d_C, d_G, d_LC}) ENR_CK(cudaMemsetAsync(v, 0, sizeof(double) * vecs, st), "clear");
+  ENR_CK(cudaMemsetAsync(d_ba, 0, sizeof(double) * nA, st), "clear");
+  ENR_CK(cudaMemsetAsync(d_AA, 0, sizeof(double) * nA * nA, st), "clear");
+  if (d_dC) ENR_CK(cudaMemsetAsync(d_dC, 0, sizeof(double) * n_h, st), "clear");
+  // cell integrals (bA into d_C, then scaled in place)
+  if (!L.it_cell.empty()) {
+    const size_t sm = sizeof(double) * (2 * (size_t)m1 * P1 + 2 * m1 + 5 * kNucThreads);
+    k_nuc_cells<Rad><<<(unsigned)L.it_cell.size(), kNucThreads, sm, st>>>(c.mesh, d_rule, m1, d_ic, d_if, d_at, nA,
+                                                                          rad, norm, inv2s2, r0, s, d_C, d_G, d_ba,
+                                                                          d_dC);
+    note_launch();
+    ENR_CK(cudaGetLastError(), "cell integrals");
+  }
+  if (!L.aa_cell.empty()) {
+    k_nuc_aa<Rad><<<(unsigned)L.aa_cell.size(), kNucThreads, 0, st>>>(c.mesh, d_rule, m1, d_ac, d_aa, d_ab, d_at,
+                                                                       rad, r0, s, nA, d_AA);
+    note_launch();
+    ENR_CK(cudaGetLastError(), "atomic stiffness");
+  }
+  const double k4 = 1.0 / (4.0 * kPi), lap = 1.0 / (2.0 * kPi);   // launch_laplace applies lap * (1/2) K
+  k_nuc_orth<<<nblk((long long)vecs), 256, 0, st>>>(d_C, c.d_Dsc, n_h, nA);
+  note_launch();
+  ENR_CK(cudaGetLastError(), "orthogonalisation");
+  for (int J = 0; J < nA; ++J)
+    ENR_CK(launch_laplace(c, d_C + (size_t)J * n_h, d_LC + (size_t)J * n_h, 1, 1, lap, st), "stiffness");
+  double* CG = d_dots;            // [nA][nA] C_J . G_K
+  double* CLC = CG + nA * nA;     // [nA][nA] C_J . (k K C_K)
+  double* AX = CLC + nA * nA;     // [nA][nA] A_IJ . X_K
+  double* CdC = AX + nA * nA;     // [nA]     C_J . d
+  auto dots = [&](const double* A, const double* Bv, int na, int nb, double* out) {
+    k_nuc_dots<<<(unsigned)(na * nb), kNucThreads, 0, st>>>(A, n_h, Bv, n_h, n_h, nb, out);
+    note_launch();
+    return cudaGetLastError();
+  };
+  ENR_CK(dots(d_C, d_G, nA, nA, CG), "dots");
+  ENR_CK(dots(d_C, d_LC, nA, nA, CLC), "dots");
+  if (d_dC) ENR_CK(dots(d_C, d_dC, nA, 1, CdC), "dots");
+  k_nuc_ace<<<nblk((long long)vecs), 256, 0, st>>>(d_G, c.d_Dsc, n_h, nA, k4, d_LC);
+  note_launch();
+  ENR_CK(cudaGetLastError(), "coupling");
+  for (int J = 0; J < nA; ++J)
+    ENR_CK(fdm_solve(c, d_LC + (size_t)J * n_h, d_Ap, d_X + (size_t)J * n_h, 1, st, true), "direct solve");
+  ENR_CK(dots(d_LC, d_X, nA, nA, AX), "dots");
+  std::vector<double> hd((size_t)3 * nA * nA + nA, 0.0), hAA((size_t)nA * nA), hba(nA);
+  ENR_CK(cudaMemcpyAsync(hd.data(), d_dots, sizeof(double) * (3 * (size_t)nA * nA + (d_dC ? nA : 0)),
+                         cudaMemcpyDeviceToHost, st), "copy");
+  ENR_CK(cudaMemcpyAsync(hAA.data(), d_AA, sizeof(double) * hAA.size(), cudaMemcpyDeviceToHost, st), "copy");
+  ENR_CK(cudaMemcpyAsync(hba.data(), d_ba, sizeof(double) * nA, cudaMemcpyDeviceToHost, st), "copy");
+  ENR_CK(cudaStreamSynchronize(st), "set-up");
+  const double* hCG = hd.data();
+  const double* hCLC = hCG + nA * nA;
+  const double* hAX = hCLC + nA * nA;
+  const double* hCdC = hAX + nA * nA;
+  S.assign((size_t)nA * nA, 0.0);
+  for (int J = 0; J < nA; ++J)
+    for (int K = 0; K < nA; ++K) {
+      const double aee = k4 * (hAA[J * nA + K] - hCG[K * nA + J] - hCG[J * nA + K]) + hCLC[J * nA + K];
+      S[J * nA + K] = aee - hAX[J * nA + K];
+    }
+  for (int J = 0; J < nA; ++J)
+    for (int K = 0; K < J; ++K) S[J * nA + K] = S[K * nA + J] = 0.5 * (S[J * nA + K] + S[K * nA + J]);
+  dE.assign(nA, 0.0);
+  if (d_dC)
+    for (int J = 0; J < nA; ++J) dE[J] = hba[J] - hCdC[J];
+  return EFE_OK;
+}
+
+// Cholesky factor of the symmetric n x n matrix S (lower, row-major); false if not positive definite.
+bool cholesky(const std::vector<double>& S, int n, std::vector<double>& L) {
+  L.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double v = S[i * n + j];
+      for (int k = 0; k < j; ++k) v -= L[i * n + k] * L[j * n + k];
+      if (i == j) {
+        if (!(v > 0.0)) return false;
+        L[i * n + i] = std::sqrt(v);
+      } else {
+        L[i * n + j] = v / L[j * n + j];
+      }
+    }
+  return true;
+}
+
+// x = (L L^T)^-1 b
+void chol_solve(const std::vector<double>& L, int n, const double* b, double* x) {
+  for (int i = 0; i < n; ++i) {
+    double v = b[i];
+    for (int k = 0; k < i; ++k) v -= L[i * n + k] * x[k];
+    x[i] = v / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double v = x[i];
+    for (int k = i + 1; k < n; ++k) v -= L[k * n + i] * x[k];
+    x[i] = v / L[i * n + i];
+  }
+}
+
+// ---- radial functions of the wavefunction enrichment (host), for the atomic densities
+double laguerre_h(int k, int a, double x) {
+  if (k < 0) return 0.0;
+  double out = 0.0, fact = 1.0, xp = 1.0;
+  for (int i = 0; i <= k; ++i) {
+    double binom = 1.0;   // C(k + a, k - i)
+    for (int j = 1; j <= k - i; ++j) binom = binom * (a + i + j) / j;
+    out += ((i & 1) ? -1.0 : 1.0) * binom * xp / fact;
+    xp *= x;
+    fact *= (i + 1);
+  }
+  return out;
+}
+
+// R_nl(r) = f(r) r^l for the radial kinds of efe_enrich_fn
+double radial_value(int kind, int n, int l, double zeta, double r) {
+  double f;
+  if (kind == EFE_RADIAL_SLATER) {
+    const int p = n - 1 - l;
+    f = (p > 0 ? std::pow(r, (double)p) : 1.0) * std::exp(-zeta * r);
+  } else if (kind == EFE_RADIAL_HYDROGENIC) {
+    f = std::pow(zeta, (double)l) * laguerre_h(n - l - 1, 2 * l + 1, 2.0 * zeta * r / n) * std::exp(-zeta * r / n);
+  } else {
+    f = std::exp(-zeta * r * r);
+  }
+  return f * (l > 0 ? std::pow(r, (double)l) : 1.0);
+}
+
+// Cumulative integral of y dr on the grid r = rmax t^2 (trapezoid rule in t, dr = 2 rmax t dt).
+std::vector<double> cum_t2(const std::vector<double>& y, const std::vector<double>& r) {
+  const size_t n = r.size();
+  const double rl = r[n - 1];
+  std::vector<double> t(n), g(n), out(n, 0.0);
+  for (size_t i = 0; i < n; ++i) {
+    t[i] = std::sqrt(r[i] / rl);
+    g[i] = y[i] * 2.0 * rl * t[i];
+  }
+  for (size_t i = 1; i < n; ++i) out[i] = out[i - 1] + 0.5 * (g[i] + g[i - 1]) * (t[i] - t[i - 1]);
+  return out;
+}
+
+// The atomic Hartree potentials (one isolated neutral atom per nucleus): the shells of
+// the atom's wavefunction enrichment functions (distinct radial kind, n, l, zeta, in the
+// order of n, then l) are filled with Z electrons, two per orbital, in that order;
+// rho(r) = sum occ R_nl^2 / (4 pi int R_nl^2 r^2 dr), Q(r) = 4 pi int_0^r rho s^2 ds,
+// v(r) = Q(r) / r + 4 pi int_r^inf rho s ds, tabulated on r_i = rmax t_i^2 with t uniform
+// on [0, 1] (nt points): rg [nt], V and Q [nA][nt], nel [nA] = Q at the end of the table.
+void atom_tables(const Ctx& c, int nt, double rmax, std::vector<double>& rg, std::vector<double>& V,
+                 std::vector<double>& Q, std::vector<double>& nel) {
+  const int nA = c.n_atoms;
+  rg.assign(nt, 0.0);
+  for (int i = 0; i < nt; ++i) {
+    const double t = i == nt - 1 ? 1.0 : i * (1.0 / (nt - 1));
+    rg[i] = rmax * t * t;
+  }
+  V.assign((size_t)nA * nt, 0.0);
+  Q.assign((size_t)nA * nt, 0.0);
+  nel.assign(nA, 0.0);
+  for (int J = 0; J < nA; ++J) {
+    struct Shell { int kind, n, l; double zeta; };
+    std::vector<Shell> sh;
+    for (const efe_enrich_fn& f : c.fns) {
+      if (f.atom != J) continue;
+      bool seen = false;
+      for (const Shell& x : sh)
+        if (x.kind == f.radial && x.n == f.n && x.l == f.l && x.zeta == f.zeta) seen = true;
+      if (!seen) sh.push_back(Shell{f.radial, f.n, f.l, f.zeta});
+    }
+    std::stable_sort(sh.begin(), sh.end(), [](const Shell& a, const Shell& b) {
+      return a.n != b.n ? a.n < b.n : a.l < b.l;
+    });
+    std::vector<double> rho(nt, 0.0), R(nt), y(nt);
+    double left = c.Z[J];
+    for (const Shell& x : sh) {
+      const double occ = std::min(left, 2.0 * (2 * x.l + 1));
+      if (occ <= 0.0) break;
+      for (int i = 0; i < nt; ++i) {
+        R[i] = radial_value(x.kind, x.n, x.l, x.zeta, rg[i]);
+        y[i] = R[i] * R[i] * rg[i] * rg[i];
+      }
+      const double nrm = cum_t2(y, rg)[nt - 1];
+      for (int i = 0; i < nt; ++i) rho[i] += occ * R[i] * R[i] / (4.0 * kPi * nrm);
+      left -= occ;
+    }
+    for (int i = 0; i < nt; ++i) y[i] = rho[i] * rg[i] * rg[i];
+    const std::vector<double> q = cum_t2(y, rg);
+    for (int i = 0; i < nt; ++i) y[i] = rho[i] * rg[i];
+    const std::vector<double> o = cum_t2(y, rg);
+    for (int i = 0; i < nt; ++i) {
+      Q[(size_t)J * nt + i] = 4.0 * kPi * q[i];
+      const double outer = 4.0 * kPi * (o[nt - 1] - o[i]);
+      V[(size_t)J * nt + i] = (rg[i] > 0.0 ? 4.0 * kPi * q[i] / rg[i] : 0.0) + outer;
+    }
+    V[(size_t)J * nt] = 4.0 * kPi * o[nt - 1];
+    nel[J] = Q[(size_t)J * nt + nt - 1];
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------- nuclear potential
+efe_status nuclear_enriched(Ctx& c, double sigma, double r0, double s, int sub, int n_quad, double* phiE_host,
+                            cudaStream_t st) {
+  if (!(sigma > 0.0)) {
+    c.err = "nuclear enrichment: need sigma > 0";
+    return EFE_ERR_ARG;
+  }
+  if (!enr_args_ok(c, r0, s, sub, n_quad)) return EFE_ERR_ARG;
+  const int nA = c.n_atoms;
   std::vector<double> at(4 * (size_t)nA);
   for (int J = 0; J < nA; ++J) {
     at[4 * J] = c.Z[J];
@@ -412,162 +815,190 @@ efe_status nuclear_enriched(Ctx& c, double sigma, double r0, double s, int sub, 
   const long long n_h = c.n_h;
   const size_t vecs = (size_t)nA * n_h;
   Bufs B;
-  double *d_rule, *d_at, *d_bA, *d_G, *d_ba, *d_dC, *d_AA, *d_LC, *d_X, *d_z, *d_Lz, *d_u, *d_Ap, *d_phiB, *d_nodes;
-  double *d_dots, *d_xE;
-  int *d_ic, *d_if, *d_ac, *d_aa, *d_ab;
-  NUC_CK(B.alloc(d_rule, rule.size()), "allocating");
-  NUC_CK(B.alloc(d_at, at.size()), "allocating");
-  NUC_CK(B.alloc(d_bA, vecs), "allocating");
-  NUC_CK(B.alloc(d_G, vecs), "allocating");
-  NUC_CK(B.alloc(d_LC, vecs), "allocating");
-  NUC_CK(B.alloc(d_X, vecs), "allocating");
-  NUC_CK(B.alloc(d_ba, nA), "allocating");
-  NUC_CK(B.alloc(d_AA, (size_t)nA * nA), "allocating");
-  NUC_CK(B.alloc(d_dots, (size_t)5 * nA * nA + 3 * nA), "allocating");
-  NUC_CK(B.alloc(d_xE, nA), "allocating");
-  for (double** v : {&d_dC, &d_z, &d_Lz, &d_u, &d_Ap, &d_phiB}) NUC_CK(B.alloc(*v, (size_t)n_h), "allocating");
-  NUC_CK(B.alloc(d_nodes, (size_t)3 * n_h), "allocating");
-  NUC_CK(B.alloc(d_ic, it_cell.size()), "allocating");
-  NUC_CK(B.alloc(d_if, it_fn.size()), "allocating");
-  NUC_CK(B.alloc(d_ac, aa_cell.size()), "allocating");
-  NUC_CK(B.alloc(d_aa, aa_a.size()), "allocating");
-  NUC_CK(B.alloc(d_ab, aa_b.size()), "allocating");
-  auto up = [&](void* dst, const void* src, size_t bytes) {
-    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
-  };
-  NUC_CK(up(d_rule, rule.data(), sizeof(double) * rule.size()), "copy");
-  NUC_CK(up(d_at, at.data(), sizeof(double) * at.size()), "copy");
-  NUC_CK(up(d_ic, it_cell.data(), sizeof(int) * it_cell.size()), "copy");
-  NUC_CK(up(d_if, it_fn.data(), sizeof(int) * it_fn.size()), "copy");
-  NUC_CK(up(d_ac, aa_cell.data(), sizeof(int) * aa_cell.size()), "copy");
-  NUC_CK(up(d_aa, aa_a.data(), sizeof(int) * aa_a.size()), "copy");
-  NUC_CK(up(d_ab, aa_b.data(), sizeof(int) * aa_b.size()), "copy");
-  for (double* v : {d_bA, d_G, d_LC})
-    NUC_CK(cudaMemsetAsync(v, 0, sizeof(double) * vecs, st), "clear");
-  NUC_CK(cudaMemsetAsync(d_ba, 0, sizeof(double) * nA, st), "clear");
-  NUC_CK(cudaMemsetAsync(d_AA, 0, sizeof(double) * nA * nA, st), "clear");
-  NUC_CK(cudaMemsetAsync(d_dC, 0, sizeof(double) * n_h, st), "clear");
-  NUC_CK(cudaMemsetAsync(d_Lz, 0, sizeof(double) * n_h, st), "clear");
-  // cell integrals of the atomic parts and of the charge
+  double *d_at, *d_C, *d_G, *d_LC, *d_X, *d_dC, *d_z, *d_Lz, *d_u, *d_Ap, *d_phiB, *d_nodes, *d_dots, *d_xE;
+  ENR_CK(B.alloc(d_at, at.size()), "allocating");
+  for (double** v : {&d_C, &d_G, &d_LC, &d_X}) ENR_CK(B.alloc(*v, vecs), "allocating");
+  for (double** v : {&d_dC, &d_z, &d_Lz, &d_u, &d_Ap, &d_phiB}) ENR_CK(B.alloc(*v, (size_t)n_h), "allocating");
+  ENR_CK(B.alloc(d_nodes, (size_t)3 * n_h), "allocating");
+  ENR_CK(B.alloc(d_dots, (size_t)2 * nA), "allocating");
+  ENR_CK(B.alloc(d_xE, nA), "allocating");
+  ENR_CK(cudaMemcpyAsync(d_at, at.data(), sizeof(double) * at.size(), cudaMemcpyHostToDevice, st), "copy");
   const double a = 1.0 / (std::sqrt(2.0) * sigma);
   const double norm = std::pow(2.0 * kPi * sigma * sigma, -1.5);
   const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
-  if (!it_cell.empty()) {
-    const size_t sm = sizeof(double) * (2 * (size_t)m1 * P1 + 2 * m1 + 5 * kNucThreads);
-    k_nuc_cells<<<(unsigned)it_cell.size(), kNucThreads, sm, st>>>(c.mesh, d_rule, m1, d_ic, d_if, d_at, nA, a, norm,
-                                                                    inv2s2, r0, s, d_bA, d_G, d_ba, d_dC);
-    note_launch();
-    NUC_CK(cudaGetLastError(), "cell integrals");
-  }
-  if (!aa_cell.empty()) {
-    k_nuc_aa<<<(unsigned)aa_cell.size(), kNucThreads, 0, st>>>(c.mesh, d_rule, m1, d_ac, d_aa, d_ab, d_at, a, r0, s,
-                                                                nA, d_AA);
-    note_launch();
-    NUC_CK(cudaGetLastError(), "atomic stiffness");
-  }
-  // orthogonalisation coefficients C (in place of bA), k K C_J, the dots of the enriched block
-  const double k4 = 1.0 / (4.0 * kPi), lap = 1.0 / (2.0 * kPi);   // launch_laplace applies lap * (1/2) K
-  double* d_C = d_bA;
-  k_nuc_orth<<<nblk((long long)vecs), 256, 0, st>>>(d_C, c.d_Dsc, n_h, nA);
-  note_launch();
-  NUC_CK(cudaGetLastError(), "orthogonalisation");
-  for (int J = 0; J < nA; ++J)
-    NUC_CK(launch_laplace(c, d_C + (size_t)J * n_h, d_LC + (size_t)J * n_h, 1, 1, lap, st), "stiffness");
-  double* CG = d_dots;                 // [nA][nA] C_J . G_K
-  double* CLC = CG + nA * nA;          // [nA][nA] C_J . (k K C_K)
-  double* AX = CLC + nA * nA;          // [nA][nA] A_IJ . X_K
-  double* CdC = AX + nA * nA;          // [nA]     C_J . d
-  double* Gz = CdC + nA;               // [nA]     G_J . z
-  double* CLz = Gz + nA;               // [nA]     C_J . (k K z)
-  auto dots = [&](const double* A, const double* Bv, int na, int nb, double* out) {
-    k_nuc_dots<<<(unsigned)(na * nb), kNucThreads, 0, st>>>(A, n_h, Bv, n_h, n_h, nb, out);
-    note_launch();
-    return cudaGetLastError();
-  };
-  NUC_CK(dots(d_C, d_G, nA, nA, CG), "dots");
-  NUC_CK(dots(d_C, d_LC, nA, nA, CLC), "dots");
-  NUC_CK(dots(d_C, d_dC, nA, 1, CdC), "dots");
-  // A_IJ (in place of k K C_J), X_J = A_II^-1 A_IJ
-  k_nuc_ace<<<nblk((long long)vecs), 256, 0, st>>>(d_G, c.d_Dsc, n_h, nA, k4, d_LC);
-  note_launch();
-  NUC_CK(cudaGetLastError(), "coupling");
-  for (int J = 0; J < nA; ++J)
-    NUC_CK(fdm_solve(c, d_LC + (size_t)J * n_h, d_Ap, d_X + (size_t)J * n_h, 1, st, true), "direct solve");
-  NUC_CK(dots(d_LC, d_X, nA, nA, AX), "dots");
+  const NucRadial nrad{a};
+  Lists L;
+  work_lists(c, r0, 40.0 * sigma, L);   // exp(-40^2 / 2) underflows: no charge beyond 40 sigma
+  std::vector<double> S, dE;
+  efe_status e = enr_blocks(c, nrad, d_at, r0, s, sub, n_quad, norm, inv2s2, 40.0 * sigma, L, d_C, d_G, d_LC, d_X,
+                            d_dC, S, dE, st);
+  if (e != EFE_OK) return e;
   // classical solve with the smeared-nucleus boundary data
-  NUC_CK(launch_coords(c, d_nodes, nullptr, st), "node coordinates");
+  const double k4 = 1.0 / (4.0 * kPi), lap = 1.0 / (2.0 * kPi);
+  ENR_CK(launch_coords(c, d_nodes, nullptr, st), "node coordinates");
   k_nuc_bc<<<nblk(n_h), 256, 0, st>>>(d_nodes, c.d_Dsc, n_h, d_at, nA, a, d_phiB);
   note_launch();
-  NUC_CK(cudaGetLastError(), "boundary data");
-  NUC_CK(fdm_solve(c, d_dC, d_Ap, d_z, 1, st, false, d_phiB), "direct solve");
-  NUC_CK(launch_laplace(c, d_z, d_Lz, 1, 0, lap, st), "stiffness");
-  NUC_CK(dots(d_G, d_z, nA, 1, Gz), "dots");
-  NUC_CK(dots(d_C, d_Lz, nA, 1, CLz), "dots");
-  // the enriched block on the host: S phi^E = rhs
-  std::vector<double> hd((size_t)3 * nA * nA + 3 * nA), hAA((size_t)nA * nA), hba(nA);
-  NUC_CK(cudaMemcpyAsync(hd.data(), d_dots, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost, st), "copy");
-  NUC_CK(cudaMemcpyAsync(hAA.data(), d_AA, sizeof(double) * hAA.size(), cudaMemcpyDeviceToHost, st), "copy");
-  NUC_CK(cudaMemcpyAsync(hba.data(), d_ba, sizeof(double) * nA, cudaMemcpyDeviceToHost, st), "copy");
-  NUC_CK(cudaStreamSynchronize(st), "set-up");
-  const double* hCG = hd.data();
-  const double* hCLC = hCG + nA * nA;
-  const double* hAX = hCLC + nA * nA;
-  const double* hCdC = hAX + nA * nA;
-  const double* hGz = hCdC + nA;
-  const double* hCLz = hGz + nA;
-  std::vector<double> S((size_t)nA * nA), rhs(nA), x(nA);
-  for (int J = 0; J < nA; ++J) {
-    for (int K = 0; K < nA; ++K) {
-      const double aee = k4 * (hAA[J * nA + K] - hCG[K * nA + J] - hCG[J * nA + K]) + hCLC[J * nA + K];
-      S[J * nA + K] = aee - hAX[J * nA + K];
-    }
-    rhs[J] = (hba[J] - hCdC[J]) - k4 * hGz[J] + hCLz[J];
+  ENR_CK(cudaGetLastError(), "boundary data");
+  ENR_CK(fdm_solve(c, d_dC, d_Ap, d_z, 1, st, false, d_phiB), "direct solve");
+  ENR_CK(cudaMemsetAsync(d_Lz, 0, sizeof(double) * n_h, st), "clear");
+  ENR_CK(launch_laplace(c, d_z, d_Lz, 1, 0, lap, st), "stiffness");
+  k_nuc_dots<<<(unsigned)nA, kNucThreads, 0, st>>>(d_G, n_h, d_z, n_h, n_h, 1, d_dots);
+  note_launch();
+  k_nuc_dots<<<(unsigned)nA, kNucThreads, 0, st>>>(d_C, n_h, d_Lz, n_h, n_h, 1, d_dots + nA);
+  note_launch();
+  ENR_CK(cudaGetLastError(), "dots");
+  std::vector<double> hd(2 * (size_t)nA);
+  ENR_CK(cudaMemcpyAsync(hd.data(), d_dots, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost, st), "copy");
+  ENR_CK(cudaStreamSynchronize(st), "set-up");
+  // S phi^E = d_E - A_EB phi_B - A_EI z on the host
+  std::vector<double> rhs(nA), x(nA), Lc;
+  for (int J = 0; J < nA; ++J) rhs[J] = dE[J] - k4 * hd[J] + hd[nA + J];
+  if (!cholesky(S, nA, Lc)) {
+    c.err = "nuclear enrichment: Schur complement not positive definite";
+    return EFE_ERR_NOT_SPD;
   }
-  for (int J = 0; J < nA; ++J)
-    for (int K = 0; K < J; ++K) S[J * nA + K] = S[K * nA + J] = 0.5 * (S[J * nA + K] + S[K * nA + J]);
-  // Cholesky S = L L^T, then the two triangular solves
-  std::vector<double> Lc((size_t)nA * nA, 0.0);
-  for (int i = 0; i < nA; ++i)
-    for (int j = 0; j <= i; ++j) {
-      double v = S[i * nA + j];
-      for (int k = 0; k < j; ++k) v -= Lc[i * nA + k] * Lc[j * nA + k];
-      if (i == j) {
-        if (!(v > 0.0)) {
-          c.err = "nuclear enrichment: Schur complement not positive definite";
-          return EFE_ERR_NOT_SPD;
-        }
-        Lc[i * nA + i] = std::sqrt(v);
-      } else {
-        Lc[i * nA + j] = v / Lc[j * nA + j];
-      }
-    }
-  for (int i = 0; i < nA; ++i) {
-    double v = rhs[i];
-    for (int k = 0; k < i; ++k) v -= Lc[i * nA + k] * x[k];
-    x[i] = v / Lc[i * nA + i];
-  }
-  for (int i = nA - 1; i >= 0; --i) {
-    double v = x[i];
-    for (int k = i + 1; k < nA; ++k) v -= Lc[k * nA + i] * x[k];
-    x[i] = v / Lc[i * nA + i];
-  }
+  chol_solve(Lc, nA, rhs.data(), x.data());
   // v_N at the quadrature points
-  NUC_CK(up(d_xE, x.data(), sizeof(double) * nA), "copy");
+  ENR_CK(cudaMemcpyAsync(d_xE, x.data(), sizeof(double) * nA, cudaMemcpyHostToDevice, st), "copy");
   k_nuc_combine<<<nblk(n_h), 256, 0, st>>>(d_z, d_X, d_C, d_xE, n_h, nA, d_u);
   note_launch();
-  NUC_CK(cudaGetLastError(), "combine");
-  NUC_CK(launch_interp(c, d_u, c.d_vN, 1, st), "interpolation");
+  ENR_CK(cudaGetLastError(), "combine");
+  ENR_CK(launch_interp(c, d_u, c.d_vN, 1, st), "interpolation");
   const long long npts = (long long)c.nc * c.nq;
-  k_nuc_add_atomic<<<nblk(npts), 256, 0, st>>>(c.d_xq, npts, d_at, nA, a, r0, s, d_xE, c.d_vN);
+  k_nuc_add_atomic<<<nblk(npts), 256, 0, st>>>(c.d_xq, npts, d_at, nA, nrad, r0, s, d_xE, c.d_vN);
   note_launch();
-  NUC_CK(cudaGetLastError(), "enrichment values");
-  NUC_CK(cudaStreamSynchronize(st), "set-up");
-#undef NUC_CK
+  ENR_CK(cudaGetLastError(), "enrichment values");
+  ENR_CK(cudaStreamSynchronize(st), "set-up");
   if (phiE_host)
     for (int J = 0; J < nA; ++J) phiE_host[J] = x[J];
   c.state_valid = false;
   c.has_prev = false;
   return EFE_OK;
 }
+
+// ---------------------------------------------------------------------------- Hartree potential
+void hen_free(HartreeEnr& h) {
+  for (double** p : {&h.C, &h.G, &h.X, &h.Sinv, &h.atoms, &h.r, &h.v, &h.q, &h.nel, &h.small}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  for (int** p : {&h.pair_cell, &h.pair_fn}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  h.on = false;
+}
+
+// Installs the enriched Hartree solve: atomic tables, the enrichment blocks and the
+// inverse of the eliminated block.
+efe_status hartree_enrich_install(Ctx& c, double r0, double s, int sub, int n_quad, cudaStream_t st) {
+  if (c.hartree_method != EFE_HARTREE_FDM) {
+    c.err = "enriched Hartree solve: needs the direct (fast-diagonalisation) Hartree method";
+    return EFE_ERR_ARG;
+  }
+  if (!enr_args_ok(c, r0, s, sub, n_quad)) return EFE_ERR_ARG;
+  const int nA = c.n_atoms, nt = 24001;
+  const double rmax = 60.0;
+  std::vector<double> rg, V, Q, nel;
+  atom_tables(c, nt, rmax, rg, V, Q, nel);
+  hen_free(c.hen);
+  HartreeEnr& h = c.hen;
+  h.nA = nA;
+  h.n_tab = nt;
+  h.rmax = rmax;
+  h.r0 = r0;
+  h.s = s;
+  std::vector<double> at(4 * (size_t)nA);
+  for (int J = 0; J < nA; ++J) {
+    at[4 * J] = c.Z[J];
+    for (int a = 0; a < 3; ++a) at[4 * J + 1 + a] = c.R[3 * J + a];
+  }
+  const long long n_h = c.n_h;
+  const size_t vecs = (size_t)nA * n_h;
+  auto dal = [](double*& p, size_t n) { return cudaMalloc(&p, sizeof(double) * std::max<size_t>(n, 1)); };
+  ENR_CK(dal(h.C, vecs), "allocating");
+  ENR_CK(dal(h.G, vecs), "allocating");
+  ENR_CK(dal(h.X, vecs), "allocating");
+  ENR_CK(dal(h.Sinv, (size_t)nA * nA), "allocating");
+  ENR_CK(dal(h.atoms, at.size()), "allocating");
+  ENR_CK(dal(h.r, nt), "allocating");
+  ENR_CK(dal(h.v, V.size()), "allocating");
+  ENR_CK(dal(h.q, Q.size()), "allocating");
+  ENR_CK(dal(h.nel, nA), "allocating");
+  ENR_CK(dal(h.small, (size_t)3 * nA * c.batch), "allocating");
+  ENR_CK(cudaMemcpyAsync(h.atoms, at.data(), sizeof(double) * at.size(), cudaMemcpyHostToDevice, st), "copy");
+  ENR_CK(cudaMemcpyAsync(h.r, rg.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, st), "copy");
+  ENR_CK(cudaMemcpyAsync(h.v, V.data(), sizeof(double) * V.size(), cudaMemcpyHostToDevice, st), "copy");
+  ENR_CK(cudaMemcpyAsync(h.q, Q.data(), sizeof(double) * Q.size(), cudaMemcpyHostToDevice, st), "copy");
+  ENR_CK(cudaMemcpyAsync(h.nel, nel.data(), sizeof(double) * nA, cudaMemcpyHostToDevice, st), "copy");
+  const TabRadial trad{h.r, h.v, h.q, h.nel, nt, rmax};
+  Lists L;
+  work_lists(c, r0, 0.0, L);
+  Bufs B;
+  double* d_LC;
+  ENR_CK(B.alloc(d_LC, vecs), "allocating");
+  std::vector<double> S, dE;
+  efe_status e = enr_blocks(c, trad, h.atoms, r0, s, sub, n_quad, 0.0, 0.0, 0.0, L, h.C, h.G, d_LC, h.X, nullptr,
+                            S, dE, st);
+  if (e != EFE_OK) return e;
+  std::vector<double> Lc, Sinv((size_t)nA * nA), col(nA), x(nA);
+  if (!cholesky(S, nA, Lc)) {
+    c.err = "enriched Hartree solve: Schur complement not positive definite";
+    return EFE_ERR_NOT_SPD;
+  }
+  for (int K = 0; K < nA; ++K) {
+    std::fill(col.begin(), col.end(), 0.0);
+    col[K] = 1.0;
+    chol_solve(Lc, nA, col.data(), x.data());
+    for (int J = 0; J < nA; ++J) Sinv[J * nA + K] = x[J];
+  }
+  ENR_CK(cudaMemcpyAsync(h.Sinv, Sinv.data(), sizeof(double) * Sinv.size(), cudaMemcpyHostToDevice, st), "copy");
+  h.n_pairs = (long long)L.pr_cell.size();
+  ENR_CK(cudaMalloc(&h.pair_cell, sizeof(int) * std::max<size_t>(L.pr_cell.size(), 1)), "allocating");
+  ENR_CK(cudaMalloc(&h.pair_fn, sizeof(int) * std::max<size_t>(L.pr_fn.size(), 1)), "allocating");
+  ENR_CK(cudaMemcpyAsync(h.pair_cell, L.pr_cell.data(), sizeof(int) * L.pr_cell.size(), cudaMemcpyHostToDevice, st),
+         "copy");
+  ENR_CK(cudaMemcpyAsync(h.pair_fn, L.pr_fn.data(), sizeof(int) * L.pr_fn.size(), cudaMemcpyHostToDevice, st), "copy");
+  ENR_CK(cudaStreamSynchronize(st), "set-up");
+  h.on = true;
+  c.state_valid = false;
+  c.has_prev = false;
+  return EFE_OK;
+}
+
+cudaError_t hartree_enriched_solve(Ctx& c, const double* rho, double* vH, const double* d, double* Ap, double* Lz,
+                                   double* u, cudaStream_t s) {
+  HartreeEnr& h = c.hen;
+  const int nb = c.batch, nA = h.nA;
+  const long long n_h = c.n_h, N = n_h * nb;
+  const double k4 = 1.0 / (4.0 * kPi), lap = 1.0 / (2.0 * kPi);
+  const TabRadial trad{h.r, h.v, h.q, h.nel, h.n_tab, h.rmax};
+  double* dA = h.small;
+  double* rhs = dA + nA * nb;
+  double* xE = rhs + nA * nb;
+  EFE_CUDA_TRY(fdm_solve(c, d, Ap, c.d_phi, nb, s));   // z, with the Hartree Dirichlet data
+  EFE_CUDA_TRY(cudaMemsetAsync(Lz, 0, sizeof(double) * N, s));
+  EFE_CUDA_TRY(launch_laplace(c, c.d_phi, Lz, nb, 0, lap, s));
+  EFE_CUDA_TRY(cudaMemsetAsync(dA, 0, sizeof(double) * nA * nb, s));
+  if (h.n_pairs > 0) {
+    k_hen_load<TabRadial><<<(unsigned)h.n_pairs, kNucThreads, 0, s>>>(h.pair_cell, h.pair_fn, c.nq, c.nc, nb, c.d_xq,
+                                                                      c.d_wJ, rho, h.atoms, trad, h.r0, h.s, dA);
+    note_launch();
+  }
+  k_hen_rhs<<<(unsigned)(nA * nb), kNucThreads, 0, s>>>(h.C, h.G, d, c.d_phi, Lz, dA, n_h, nb, k4, rhs);
+  note_launch();
+  k_hen_coef<<<1, 256, 0, s>>>(h.Sinv, rhs, nA, nb, xE);
+  note_launch();
+  k_hen_combine<<<nblk(N), 256, 0, s>>>(c.d_phi, u, h.X, h.C, xE, n_h, nA, nb);
+  note_launch();
+  EFE_CUDA_TRY(cudaGetLastError());
+  EFE_CUDA_TRY(launch_interp(c, u, vH, nb, s));
+  const long long npts = (long long)c.nc * c.nq;
+  k_hen_add<TabRadial><<<nblk(npts * nb), 256, 0, s>>>(c.d_xq, npts, nb, h.atoms, nA, trad, h.r0, h.s, xE, vH);
+  note_launch();
+  return cudaGetLastError();
+}
+
+#undef ENR_CK
 
 }  // namespace efe

@@ -1051,6 +1051,11 @@ efe_status run_hartree(Ctx& c, const double* rho, double* vH, double tol, int ma
   } while (0)
   CK(cudaMemsetAsync(d, 0, sizeof(double) * N, s));
   CK(launch_load_vector(c, rho, d, nb, s));
+  if (c.hartree_method == EFE_HARTREE_FDM && c.hen.on) {
+    CK(hartree_enriched_solve(c, rho, vH, d, Ap, r, z, s));
+    if (iters) *iters = 1;
+    return EFE_OK;
+  }
   if (c.hartree_method == EFE_HARTREE_FDM) {
     CK(fdm_solve(c, d, Ap, c.d_phi, nb, s));
     CK(launch_interp(c, c.d_phi, vH, nb, s));

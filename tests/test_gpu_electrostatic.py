@@ -142,3 +142,154 @@ def test_full_size_enriched_nucleus_properties():
     assert np.all(np.abs(phiE - 1.0) < 0.1), phiE
     ctx.close()
     torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------------------- enriched Hartree solve
+def _shells(wl, J):
+    """The distinct (radial kind, n, l, zeta) of atom J's wavefunction enrichment, in order."""
+    out = []
+    for f in wl.enrich:
+        t = (f.radial, f.n, f.l, f.zeta)
+        if f.atom == J and t not in out:
+            out.append(t)
+    return out
+
+
+def _oracle_hartree(wl, mesh, r0, s):
+    """The oracle's enriched Hartree solve (HartreeEFE, atomic Hartree potentials of
+    the shell-filled atoms as enrichment) on the plain cell rule, whose points are
+    the quadrature points that carry the density, with the Hartree Dirichlet data
+    sum Z / |x - R|: a solver rho_q [n_cells][n_q] -> (phi, v_H [n_cells][n_q])."""
+    from oracle import electrostatic as es
+    atoms = [es.RadialAtom(_shells(wl, J), float(wl.Z[J])) for J in range(len(wl.Z))]
+
+    def dirichlet(p):
+        return sum(z / np.linalg.norm(p - R[None, :], axis=1) for z, R in zip(wl.Z, wl.R))
+
+    P = es.HartreeEFE(mesh, atoms, list(wl.R), lambda p: np.zeros(len(p)), r0=r0, s=s, dirichlet=dirichlet, sub=1,
+                      n=mesh.nq1)
+    tab = []
+    for c in range(mesh.n_cells):
+        pts, w, Bc, G = P.rule.cell(mesh, c)
+        tab.append((w, Bc, P._enriched_at(c, pts, Bc, G)[0]))
+
+    def solve(system, rho_b):
+        dC = np.zeros(mesh.n_nodes)
+        dE = np.zeros(P.nE)
+        for c, (w, Bc, vE) in enumerate(tab):
+            dC[mesh.conn[c]] += Bc.T @ (w * rho_b[c])
+            dE += vE.T @ (w * rho_b[c])
+        phi, phiE = P.solve(dC=dC, dE=dE)
+        return phi, np.array([Bc @ phi[mesh.conn[c]] + vE @ phiE for c, (w, Bc, vE) in enumerate(tab)])
+    return solve
+
+
+def _density(quad, R, b):
+    """A smooth synthetic density at the quadrature points, different per member b."""
+    rho = 0.1 * np.exp(-0.2 * np.sum(quad ** 2, axis=-1))
+    for c in R:
+        rho = rho + (2.0 + 0.3 * b) * np.exp(-1.3 * np.sum((quad - c) ** 2, axis=-1))
+    return rho
+
+
+HARTREE_CASES = {
+    "small2_p3_batch2": lambda: W.small_cluster(n_atoms=2, cells_per_axis=5, degree=3, n_quad=5, n_orb=3, batch=2),
+    "h2_p4": lambda: W.h2(),
+}
+
+
+@pytest.mark.parametrize("name", list(HARTREE_CASES))
+def test_hartree_enriched_matches_oracle(name):
+    """v_H of the enriched solve for a synthetic density per batch member against
+    the oracle's HartreeEFE (1e-10)."""
+    from oracle.mesh import Mesh
+    from paper_2210_14421_gb300 import Context
+    wl = HARTREE_CASES[name]()
+    mesh = Mesh(wl.xb, wl.yb, wl.zb, wl.degree, wl.n_quad)
+    solve = _oracle_hartree(wl, mesh, 3.0, 1.5)
+    ctx = Context(wl)
+    _, quad = ctx.coords()
+    q = quad.cpu().numpy()
+    rho = np.stack([_density(q, wl.R, b) for b in range(wl.batch)])
+    ctx.hartree_enriched(3.0, 1.5, sub=1, n_quad=wl.n_quad)
+    r = torch.from_numpy(np.ascontiguousarray(rho)).cuda()
+    vH = torch.empty_like(r)
+    ctx.hartree(r, vH)
+    got = vH.cpu().numpy()
+    for b in range(wl.batch):
+        _, ref = solve(None, rho[b])
+        assert np.max(np.abs(got[b] - ref)) <= 1e-10 * np.max(np.abs(ref)), (name, b)
+    ctx.close()
+
+
+def test_steps_with_enriched_hartree_match_oracle():
+    """Kick + 2 predictor-corrector steps (fixed Krylov dimension) with the enriched
+    Hartree solve in every density update: orbitals and dipoles to 1e-10."""
+    from oracle import operators, tdks
+    from paper_2210_14421_gb300 import Context
+    wl = W.small_cluster(n_atoms=2, cells_per_axis=5, degree=3, n_quad=5, n_orb=3)
+    S = operators.System(wl)
+    solve = _oracle_hartree(wl, S.mesh, 3.0, 1.5)
+    psi0 = S.initial_orbitals()
+    psi = tdks.kick(S, psi0, wl.fields, wl.n_orb, tol=1e-14, k_max=8)
+    st = tdks.make_state(S, psi, wl.occ, wl.batch, hartree=solve)
+    mus = []
+    for n in range(2):
+        psi, st, mu, _ = tdks.magnus_step(S, psi, st, n * wl.dt, wl.dt, wl.fields, wl.occ, 1e-14, 8, fixed_k=8,
+                                          hartree=solve)
+        mus.append(mu)
+    ctx = Context(wl, fixed_k=8, krylov_tol=1e-14, k_max=8)
+    ctx.hartree_enriched(3.0, 1.5, sub=1, n_quad=wl.n_quad)
+    g = torch.from_numpy(np.ascontiguousarray(psi0)).cuda()
+    ctx.kick(g, wl.fields)
+    m = torch.zeros((wl.batch, 3), dtype=torch.float64, device="cuda")
+    got_mu = []
+    for n in range(2):
+        ctx.magnus_step(g, n * wl.dt, wl.dt, wl.fields, m)
+        got_mu.append(m.cpu().numpy().copy())
+    assert np.linalg.norm(g.cpu().numpy() - psi) <= 1e-10 * np.linalg.norm(psi)
+    ref_mu = np.array(mus)
+    assert np.max(np.abs(np.array(got_mu) - ref_mu)) <= 1e-10 * max(np.max(np.abs(ref_mu)), 1e-3)
+    ctx.close()
+
+
+def test_hartree_enriched_rejections():
+    """The enriched solve needs the direct Hartree method; once installed, the
+    adjoint (whose transposed Hartree map is classical) refuses the context."""
+    from paper_2210_14421_gb300 import EFE_HARTREE_PCG, Context, EfeError
+    wl = W.h2()
+    ctx = Context(wl, hartree_method=EFE_HARTREE_PCG)
+    with pytest.raises(EfeError):
+        ctx.hartree_enriched(3.0, 1.5)
+    ctx.close()
+    ctx = Context(wl)
+    with pytest.raises(EfeError):
+        ctx.hartree_enriched(9.0, 1.5)   # support reaching the boundary
+    ctx.hartree_enriched(3.0, 1.5)
+    psi0 = torch.zeros((ctx.n_dof, ctx.n_cols), dtype=torch.complex128, device="cuda")
+    ctx.init_orbitals(psi0)
+    field = W.Field(kind=W.FIELD_GAUSS, amp=0.02, omega=0.0, t0=0.15, sigma=0.25, direction=(1.0, 0.0, 0.0))
+    with pytest.raises(EfeError):
+        ctx.adjoint_dipole(psi0, 2, wl.dt, field, (1.0, 0.0, 0.0), (1, 2))
+    ctx.close()
+
+
+def test_full_size_step_with_enriched_hartree():
+    """Na8 at full size with the enriched Hartree solve installed (r0 = 4, 2^3
+    sub-cells): a kicked predictor-corrector step in float32 pairs conserves
+    every column's norm to the Lanczos tolerance and gives a finite dipole."""
+    from paper_2210_14421_gb300 import EFE_PAIR, Context
+    wl = W.na8(k_max=64)
+    ctx = Context(wl, precision=EFE_PAIR)
+    ctx.hartree_enriched(4.0, 2.0, sub=2)
+    psi = torch.zeros((ctx.n_dof, wl.n_orb), dtype=torch.complex128, device="cuda")
+    ctx.init_orbitals(psi)
+    ctx.kick(psi, wl.fields)
+    n0 = torch.linalg.norm(psi, dim=0)
+    mu = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+    ctx.magnus_step(psi, 0.0, wl.dt, wl.fields, mu)
+    n1 = torch.linalg.norm(psi, dim=0)
+    assert torch.max(torch.abs(n1 - n0) / n0).item() < 1e-7
+    assert torch.isfinite(mu).all()
+    ctx.close()
+    torch.cuda.empty_cache()
