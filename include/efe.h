@@ -345,8 +345,14 @@ efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_st
  * orthogonalised against the classical functions in the GLL-lumped inner
  * product, stiffness (1/4pi) int grad . grad, and the smeared-nucleus
  * potential as Dirichlet data on the boundary nodes.  Cell integrals of the
- * atomic parts and of the charge use a composite Gauss-Legendre rule of sub^3
- * sub-cells with n_quad^3 points each (n_quad 0: p + 2); the Galerkin system is
+ * atomic parts and of the charge use n_quad^3 Gauss-Legendre points (n_quad 0:
+ * p + 2) on each of a cell's boxes: with adapt_tol = 0, sub^3 equal boxes; with
+ * adapt_tol > 0, the adaptive rule (the paper's adaptive quadrature for the
+ * enrichment): a box's estimate of the trial integrals (the smeared charge and
+ * every atomic part) is compared with the sum over its eight half-size
+ * children, whose boxes are kept where every trial integral agrees to
+ * adapt_tol (absolute) and refined the same way otherwise, down to adapt_depth
+ * levels below the cell (sub is then ignored).  The Galerkin system is
  * solved exactly (to rounding) around the direct Poisson solver by block
  * elimination of the n_atoms enrichment unknowns.  vN_dev (nullable): device
  * [n_cells][n_q] doubles receiving the new potential at the quadrature points;
@@ -355,11 +361,13 @@ efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_st
  * invalidated (the next efe_magnus_step recomputes rho).  Allocates device
  * memory for the call (about 4 n_atoms + 10 vectors of n_nodes doubles) and
  * synchronises `stream`.  Errors: EFE_ERR_ARG (sigma <= 0, s <= 0, r0 <= s,
- * sub outside [1, 8], n_quad outside [p + 1, 8] and not 0, a support sphere of
- * radius r0 reaching the domain boundary), EFE_ERR_NOT_SPD (the eliminated
- * block not positive definite), EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+ * sub outside [1, 8], n_quad outside [p + 1, 8] and not 0, adapt_tol < 0,
+ * adapt_depth outside [0, 8], a support sphere of radius r0 reaching the domain
+ * boundary), EFE_ERR_NOT_SPD (the eliminated block not positive definite),
+ * EFE_ERR_NOMEM, EFE_ERR_CUDA. */
 efe_status efe_nuclear_enriched(efe_ctx* ctx, double sigma, double r0, double s, int32_t sub, int32_t n_quad,
-                                double* vN_dev, double* phiE_host, void* stream);
+                                double adapt_tol, int32_t adapt_depth, double* vN_dev, double* phiE_host,
+                                void* stream);
 
 /* Hartree potential in the electrostatically enriched basis (Eq. PhiEFE for the
  * Hartree potential, Eq. DiscretePoisson).  Installs, for every later Hartree

@@ -104,7 +104,7 @@ def lib(path: str = LIB_PATH):
     L.efe_power_spectrum.argtypes = [vp, i64, i64, dbl, vp, i64, dbl, vp, vp]
     L.efe_adjoint_dipole.argtypes = [vp, vp, i32, dbl, C.POINTER(Field), pdbl, i32, i32, i32, i32, C.POINTER(dbl),
                                      pdbl, vp]
-    L.efe_nuclear_enriched.argtypes = [vp, dbl, dbl, dbl, i32, i32, vp, pdbl, vp]
+    L.efe_nuclear_enriched.argtypes = [vp, dbl, dbl, dbl, i32, i32, dbl, i32, vp, pdbl, vp]
     L.efe_hartree_enriched.argtypes = [vp, dbl, dbl, i32, i32, vp]
     for name in EXPORTED:
         if name != "efe_last_error":
@@ -294,15 +294,17 @@ class Context:
     def dipole(self, rho, mu):
         self._check(lib().efe_dipole(self.h, _ptr(rho), _ptr(mu), _stream()))
 
-    def nuclear_enriched(self, sigma: float, r0: float, s: float, sub: int = 2, n_quad: int = 0):
+    def nuclear_enriched(self, sigma: float, r0: float, s: float, sub: int = 2, n_quad: int = 0,
+                         adapt_tol: float = 0.0, adapt_depth: int = 4):
         """Installs the nuclear potential of Gaussian-smeared nuclei solved in the
-        electrostatically enriched basis; returns it at the quadrature points
+        electrostatically enriched basis (cell integrals on sub^3 boxes, or on the
+        adaptive rule when adapt_tol > 0); returns it at the quadrature points
         (device float64 [n_cells, n_q]) and the enrichment coefficients (numpy [n_atoms])."""
         import torch
         vN = torch.empty((self.n_cells, self.n_q), dtype=torch.float64, device="cuda")
         phiE = np.zeros(len(self.wl.Z))
         self._check(lib().efe_nuclear_enriched(self.h, float(sigma), float(r0), float(s), int(sub), int(n_quad),
-                                               _ptr(vN), _dptr(phiE), _stream()))
+                                               float(adapt_tol), int(adapt_depth), _ptr(vN), _dptr(phiE), _stream()))
         return vN, phiE
 
     def hartree_enriched(self, r0: float, s: float, sub: int = 2, n_quad: int = 0):

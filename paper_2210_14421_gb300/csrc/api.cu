@@ -690,11 +690,12 @@ efe_status efe_dipole(efe_ctx* ctx, const double* rho_dev, double* mu_dev, void*
 }
 
 efe_status efe_nuclear_enriched(efe_ctx* ctx, double sigma, double r0, double s, int32_t sub, int32_t n_quad,
-                                double* vN_dev, double* phiE_host, void* stream) {
+                                double adapt_tol, int32_t adapt_depth, double* vN_dev, double* phiE_host,
+                                void* stream) {
   CHECK_CTX(ctx);
   Ctx& c = ctx->c;
   cudaStream_t st = as_stream(stream);
-  efe_status r = nuclear_enriched(c, sigma, r0, s, sub, n_quad, phiE_host, st);
+  efe_status r = nuclear_enriched(c, sigma, r0, s, sub, n_quad, adapt_tol, adapt_depth, phiE_host, st);
   if (r != EFE_OK) return r;
   if (vN_dev)
     TRY_CUDA(c, cudaMemcpyAsync(vN_dev, c.d_vN, sizeof(double) * c.nc * c.nq, cudaMemcpyDeviceToDevice, st), "copy");

@@ -306,8 +306,8 @@ cudaError_t fdm_solve(Ctx& c, const double* d, double* Ap, double* phi, int nb, 
                       bool homogeneous = false, const double* phiB = nullptr);
 // nuclear potential of smeared nuclei in the electrostatically enriched basis (k_electro.cu):
 // replaces d_vN; phiE_host [n_atoms] receives the enrichment coefficients (nullable)
-efe_status nuclear_enriched(Ctx& c, double sigma, double r0, double s, int sub, int n_quad, double* phiE_host,
-                            cudaStream_t st);
+efe_status nuclear_enriched(Ctx& c, double sigma, double r0, double s, int sub, int n_quad, double adapt_tol,
+                            int adapt_depth, double* phiE_host, cudaStream_t st);
 // installs the enriched Hartree solve (k_electro.cu)
 efe_status hartree_enrich_install(Ctx& c, double r0, double s, int sub, int n_quad, cudaStream_t st);
 // the enriched Hartree solve for the load d = int rho N ([n_h][batch], assembled): the classical part

@@ -26,6 +26,7 @@
 // Set-up work, run once: plain loops, no tuning.
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include <vector>
 
 #include "efe_internal.h"
@@ -137,89 +138,126 @@ __device__ double block_sum(double v, double* red) {
   return out;
 }
 
-// Cell integrals with the composite rule (m1 points per axis, tables `rule` =
-// L [m1][P1], dL [m1][P1], xs [m1], ws [m1] on [-1, 1]).  One block per item:
-// for fn[k] = J >= 0, over cell cells[k]
+// Cell rules as lists of boxes: a box is [lo, hi]^3 in the cell's reference
+// coordinates [-1, 1]^3 with the n^3 Gauss-Legendre rule on it (the uniform
+// composite rule: sub^3 equal boxes; the adaptive rule: the boxes of the
+// recursive refinement).  BoxRule holds, per box, the 1D Lagrange tables of the
+// cell basis at its points (L, dL [3][n][P1]), the physical points (px [3][n])
+// and the 1D weights including the Jacobian (pw [3][n]).
+struct BoxTables {
+  double L[3][8 * kMaxP1], dL[3][8 * kMaxP1], px[3][8], pw[3][8];
+};
+
+// Lagrange basis function i of the nodes and its derivative at x.
+__device__ __forceinline__ double lagrange1(const double* nodes, int P1, int i, double x, double& d) {
+  double v = 1.0;
+  for (int j = 0; j < P1; ++j)
+    if (j != i) v *= (x - nodes[j]) / (nodes[i] - nodes[j]);
+  d = 0.0;
+  for (int a = 0; a < P1; ++a) {
+    if (a == i) continue;
+    double t = 1.0 / (nodes[i] - nodes[a]);
+    for (int j = 0; j < P1; ++j)
+      if (j != i && j != a) t *= (x - nodes[j]) / (nodes[i] - nodes[j]);
+    d += t;
+  }
+  return v;
+}
+
+// Fills the tables of box `box` (6 doubles: lo[3], hi[3]) for a cell with origin o and sizes h.
+__device__ void box_tables(BoxTables& T, const double* box, const double* gll, int P1, const double* xg,
+                           const double* wg, int n, const double o[3], const double h[3]) {
+  for (int t = threadIdx.x; t < 3 * n * P1; t += blockDim.x) {
+    const int a = t / (n * P1), j = (t / P1) % n, i = t % P1;
+    const double mid = 0.5 * (box[a] + box[3 + a]), half = 0.5 * (box[3 + a] - box[a]);
+    double d;
+    T.L[a][j * P1 + i] = lagrange1(gll, P1, i, mid + xg[j] * half, d);
+    T.dL[a][j * P1 + i] = d;
+  }
+  for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
+    const int a = t / n, j = t % n;
+    const double mid = 0.5 * (box[a] + box[3 + a]), half = 0.5 * (box[3 + a] - box[a]);
+    T.px[a][j] = o[a] + 0.5 * (mid + xg[j] * half + 1.0) * h[a];
+    T.pw[a][j] = wg[j] * half * 0.5 * h[a];
+  }
+}
+
+// Cell integrals on the item's boxes.  One block per item k: for fn[k] = J >= 0,
+// over cell cells[k]
 //   bA[J][g] += int N^A_J N_g,  G[J][g] += int grad N^A_J . grad N_g,  ba[J] += int b N^A_J;
 // for fn[k] < 0 the charge load dC[g] += int b N_g (b from the smeared nuclei;
-// with norm = 0 the charge terms vanish, as for the Hartree enrichment).
+// with norm = 0 the charge terms vanish, as for the Hartree enrichment).  The
+// cell's boxes are boxes[cb[c] .. cb[c + 1]) (cb indexed by cell).
 template <class Rad>
 __global__ void __launch_bounds__(kNucThreads)
-k_nuc_cells(const MeshView mesh, const double* __restrict__ rule, int m1, const int* __restrict__ cells,
-            const int* __restrict__ fn, const double* __restrict__ atoms, int n_atoms, const Rad rad, double norm,
-            double inv2s2, double r0, double s, double* __restrict__ bA, double* __restrict__ G,
-            double* __restrict__ ba, double* __restrict__ dC) {
-  extern __shared__ double sh[];
+k_nuc_cells(const MeshView mesh, const double* __restrict__ gll, const double* __restrict__ xg,
+            const double* __restrict__ wg, int n, const long long* __restrict__ cb, const double* __restrict__ boxes,
+            const int* __restrict__ cells, const int* __restrict__ fn, const double* __restrict__ atoms, int n_atoms,
+            const Rad rad, double norm, double inv2s2, double r0, double s, double* __restrict__ bA,
+            double* __restrict__ G, double* __restrict__ ba, double* __restrict__ dC) {
+  __shared__ BoxTables T;
+  __shared__ double fv[kNucThreads], gx[kNucThreads], gy[kNucThreads], gz[kNucThreads], red[kNucThreads];
   const int P1 = mesh.p + 1, nn = P1 * P1 * P1;
-  double* L = sh;
-  double* dL = L + m1 * P1;
-  double* xs = dL + m1 * P1;
-  double* ws = xs + m1;
-  double* fv = ws + m1;
-  double* gx = fv + kNucThreads;
-  double* gy = gx + kNucThreads;
-  double* gz = gy + kNucThreads;
-  double* red = gz + kNucThreads;
-  for (int i = threadIdx.x; i < 2 * m1 * P1 + 2 * m1; i += blockDim.x) sh[i] = rule[i];
   const int c = cells[blockIdx.x], J = fn[blockIdx.x];
   const CellGeo cg = cell_geo(mesh, c);
+  const double o[3] = {cg.ox, cg.oy, cg.oz}, h[3] = {cg.hx, cg.hy, cg.hz};
   const double sc0 = 2.0 / cg.hx, sc1 = 2.0 / cg.hy, sc2 = 2.0 / cg.hz;
-  const double detJ = cg.hx * cg.hy * cg.hz / 8.0;
-  const int npts = m1 * m1 * m1;
+  const int npts = n * n * n;
   double accB[2] = {0.0, 0.0}, accG[2] = {0.0, 0.0};
   double bacc = 0.0;
-  __syncthreads();
-  for (int q0 = 0; q0 < npts; q0 += kNucThreads) {
-    const int q = q0 + threadIdx.x;
-    double v = 0.0, g[3] = {0.0, 0.0, 0.0};
-    if (q < npts) {
-      const int q1 = q % m1, q2 = (q / m1) % m1, q3 = q / (m1 * m1);
-      const double x = cg.ox + 0.5 * (xs[q1] + 1.0) * cg.hx;
-      const double y = cg.oy + 0.5 * (xs[q2] + 1.0) * cg.hy;
-      const double zc = cg.oz + 0.5 * (xs[q3] + 1.0) * cg.hz;
-      const double w = ws[q1] * ws[q2] * ws[q3] * detJ;
-      double b = 0.0;
-      for (int t = 0; t < n_atoms; ++t) {
-        const double dx = x - atoms[4 * t + 1], dy = y - atoms[4 * t + 2], dz = zc - atoms[4 * t + 3];
-        b -= atoms[4 * t] * norm * exp(-(dx * dx + dy * dy + dz * dz) * inv2s2);
-      }
-      if (J < 0) {
-        v = w * b;
-      } else {
-        double na, gn[3];
-        atomic_part(rad, atoms, J, r0, s, x, y, zc, na, gn);
-        v = w * na;
-        g[0] = w * gn[0];
-        g[1] = w * gn[1];
-        g[2] = w * gn[2];
-        bacc += w * b * na;
-      }
-    }
-    fv[threadIdx.x] = v;
-    gx[threadIdx.x] = g[0];
-    gy[threadIdx.x] = g[1];
-    gz[threadIdx.x] = g[2];
+  for (long long bx = cb[c]; bx < cb[c + 1]; ++bx) {
+    box_tables(T, boxes + 6 * bx, gll, P1, xg, wg, n, o, h);
     __syncthreads();
-    const int cnt = min(kNucThreads, npts - q0);
+    for (int q0 = 0; q0 < npts; q0 += kNucThreads) {
+      const int q = q0 + threadIdx.x;
+      double v = 0.0, g[3] = {0.0, 0.0, 0.0};
+      if (q < npts) {
+        const int q1 = q % n, q2 = (q / n) % n, q3 = q / (n * n);
+        const double x = T.px[0][q1], y = T.px[1][q2], zc = T.px[2][q3];
+        const double w = T.pw[0][q1] * T.pw[1][q2] * T.pw[2][q3];
+        double b = 0.0;
+        for (int t = 0; t < n_atoms; ++t) {
+          const double dx = x - atoms[4 * t + 1], dy = y - atoms[4 * t + 2], dz = zc - atoms[4 * t + 3];
+          b -= atoms[4 * t] * norm * exp(-(dx * dx + dy * dy + dz * dz) * inv2s2);
+        }
+        if (J < 0) {
+          v = w * b;
+        } else {
+          double na, gn[3];
+          atomic_part(rad, atoms, J, r0, s, x, y, zc, na, gn);
+          v = w * na;
+          g[0] = w * gn[0];
+          g[1] = w * gn[1];
+          g[2] = w * gn[2];
+          bacc += w * b * na;
+        }
+      }
+      fv[threadIdx.x] = v;
+      gx[threadIdx.x] = g[0];
+      gy[threadIdx.x] = g[1];
+      gz[threadIdx.x] = g[2];
+      __syncthreads();
+      const int cnt = min(kNucThreads, npts - q0);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int l = threadIdx.x + j * kNucThreads;
-      if (l >= nn) continue;
-      const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
-      double ab = 0.0, ag = 0.0;
-      for (int qq = 0; qq < cnt; ++qq) {
-        const int qa = q0 + qq;
-        const int q1 = qa % m1, q2 = (qa / m1) % m1, q3 = qa / (m1 * m1);
-        const double l1 = L[q1 * P1 + i1], l2 = L[q2 * P1 + i2], l3 = L[q3 * P1 + i3];
-        ab += fv[qq] * l1 * l2 * l3;
-        if (J >= 0)
-          ag += sc0 * gx[qq] * dL[q1 * P1 + i1] * l2 * l3 + sc1 * gy[qq] * l1 * dL[q2 * P1 + i2] * l3 +
-                sc2 * gz[qq] * l1 * l2 * dL[q3 * P1 + i3];
+      for (int j = 0; j < 2; ++j) {
+        const int l = threadIdx.x + j * kNucThreads;
+        if (l >= nn) continue;
+        const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
+        double ab = 0.0, ag = 0.0;
+        for (int qq = 0; qq < cnt; ++qq) {
+          const int qa = q0 + qq;
+          const int q1 = qa % n, q2 = (qa / n) % n, q3 = qa / (n * n);
+          const double l1 = T.L[0][q1 * P1 + i1], l2 = T.L[1][q2 * P1 + i2], l3 = T.L[2][q3 * P1 + i3];
+          ab += fv[qq] * l1 * l2 * l3;
+          if (J >= 0)
+            ag += sc0 * gx[qq] * T.dL[0][q1 * P1 + i1] * l2 * l3 + sc1 * gy[qq] * l1 * T.dL[1][q2 * P1 + i2] * l3 +
+                  sc2 * gz[qq] * l1 * l2 * T.dL[2][q3 * P1 + i3];
+        }
+        accB[j] += ab;
+        accG[j] += ag;
       }
-      accB[j] += ab;
-      accG[j] += ag;
+      __syncthreads();
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
@@ -239,31 +277,35 @@ k_nuc_cells(const MeshView mesh, const double* __restrict__ rule, int m1, const 
   }
 }
 
-// AA[J][K] (and AA[K][J]) += int grad N^A_J . grad N^A_K over cell cells[k], J = fa[k] <= K = fb[k].
+// AA[J][K] (and AA[K][J]) += int grad N^A_J . grad N^A_K over the boxes of cell cells[k],
+// J = fa[k] <= K = fb[k].
 template <class Rad>
 __global__ void __launch_bounds__(kNucThreads)
-k_nuc_aa(const MeshView mesh, const double* __restrict__ rule, int m1, const int* __restrict__ cells,
+k_nuc_aa(const MeshView mesh, const double* __restrict__ xg, const double* __restrict__ wg, int n,
+         const long long* __restrict__ cb, const double* __restrict__ boxes, const int* __restrict__ cells,
          const int* __restrict__ fa, const int* __restrict__ fb, const double* __restrict__ atoms, const Rad rad,
          double r0, double s, int nA, double* __restrict__ AA) {
   __shared__ double red[kNucThreads];
-  const int P1 = mesh.p + 1;
-  const double* xs = rule + 2 * m1 * P1;
-  const double* ws = xs + m1;
   const int c = cells[blockIdx.x], J = fa[blockIdx.x], K = fb[blockIdx.x];
   const CellGeo cg = cell_geo(mesh, c);
-  const double detJ = cg.hx * cg.hy * cg.hz / 8.0;
-  const int npts = m1 * m1 * m1;
+  const double o[3] = {cg.ox, cg.oy, cg.oz}, h[3] = {cg.hx, cg.hy, cg.hz};
+  const int npts = n * n * n;
   double acc = 0.0;
-  for (int q = threadIdx.x; q < npts; q += blockDim.x) {
-    const int q1 = q % m1, q2 = (q / m1) % m1, q3 = q / (m1 * m1);
-    const double x = cg.ox + 0.5 * (xs[q1] + 1.0) * cg.hx;
-    const double y = cg.oy + 0.5 * (xs[q2] + 1.0) * cg.hy;
-    const double zc = cg.oz + 0.5 * (xs[q3] + 1.0) * cg.hz;
-    const double w = ws[q1] * ws[q2] * ws[q3] * detJ;
-    double va, ga[3], vb, gb[3];
-    atomic_part(rad, atoms, J, r0, s, x, y, zc, va, ga);
-    atomic_part(rad, atoms, K, r0, s, x, y, zc, vb, gb);
-    acc += w * (ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2]);
+  for (long long bx = cb[c]; bx < cb[c + 1]; ++bx) {
+    const double* box = boxes + 6 * bx;
+    for (int q = threadIdx.x; q < npts; q += blockDim.x) {
+      const int qi[3] = {q % n, (q / n) % n, q / (n * n)};
+      double x[3], w = 1.0;
+      for (int a = 0; a < 3; ++a) {
+        const double mid = 0.5 * (box[a] + box[3 + a]), half = 0.5 * (box[3 + a] - box[a]);
+        x[a] = o[a] + 0.5 * (mid + xg[qi[a]] * half + 1.0) * h[a];
+        w *= wg[qi[a]] * half * 0.5 * h[a];
+      }
+      double va, ga[3], vb, gb[3];
+      atomic_part(rad, atoms, J, r0, s, x[0], x[1], x[2], va, ga);
+      atomic_part(rad, atoms, K, r0, s, x[0], x[1], x[2], vb, gb);
+      acc += w * (ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2]);
+    }
   }
   const double tot = block_sum(acc, red);
   if (threadIdx.x == 0) {
@@ -504,27 +546,6 @@ bool enr_args_ok(Ctx& c, double r0, double s, int sub, int& n_quad) {
   return true;
 }
 
-// Composite Gauss-Legendre rule on [-1, 1] (sub pieces of n_quad points) and the
-// cell basis's Lagrange tables there: L [m1][P1], dL [m1][P1], xs [m1], ws [m1].
-std::vector<double> composite_rule(const Ctx& c, int sub, int n_quad) {
-  const int m1 = sub * n_quad, P1 = c.P1;
-  std::vector<double> xg(n_quad), wg(n_quad), gll(P1), gllw(P1);
-  gauss_legendre(n_quad, xg.data(), wg.data());
-  gauss_lobatto(c.p, gll.data(), gllw.data());
-  std::vector<double> rule((size_t)2 * m1 * P1 + 2 * m1);
-  double* xs = rule.data() + 2 * m1 * P1;
-  double* ws = xs + m1;
-  for (int k = 0; k < sub; ++k) {
-    const double a0 = -1.0 + 2.0 * k / sub, b0 = -1.0 + 2.0 * (k + 1) / sub;
-    for (int j = 0; j < n_quad; ++j) {
-      xs[k * n_quad + j] = 0.5 * (b0 - a0) * xg[j] + 0.5 * (a0 + b0);
-      ws[k * n_quad + j] = 0.5 * (b0 - a0) * wg[j];
-    }
-  }
-  lagrange_tables(P1, gll.data(), m1, xs, rule.data(), rule.data() + m1 * P1);
-  return rule;
-}
-
 // Work lists: (cell, atom) pairs whose cell meets the atom's support ball, cells
 // within `reach` of a nucleus as charge items (fn = -1; reach 0: none), and
 // (cell, atom, atom) overlaps with the first atom <= the second.
@@ -565,23 +586,198 @@ void work_lists(const Ctx& c, double r0, double reach, Lists& L) {
       }
 }
 
+// A cell rule: n^3 Gauss-Legendre points on each of a cell's boxes (reference
+// coordinates, lo[3] then hi[3]); boxes of cell c: boxes[6 cb[c] .. 6 cb[c + 1]).
+// Only the cells of the work lists carry boxes (elsewhere every integrand vanishes).
+struct BoxRule {
+  int n = 0;
+  std::vector<long long> cb;
+  std::vector<double> boxes;
+};
+
+std::vector<char> listed_cells(const Ctx& c, const Lists& L) {
+  std::vector<char> on(c.nc, 0);
+  for (int x : L.it_cell) on[x] = 1;
+  for (int x : L.aa_cell) on[x] = 1;
+  return on;
+}
+
+// The uniform composite rule: sub^3 equal boxes per listed cell.
+BoxRule uniform_rule(const Ctx& c, const Lists& L, int sub, int n) {
+  BoxRule R;
+  R.n = n;
+  const std::vector<char> on = listed_cells(c, L);
+  R.cb.assign(c.nc + 1, 0);
+  for (int cell = 0; cell < c.nc; ++cell) {
+    R.cb[cell + 1] = R.cb[cell];
+    if (!on[cell]) continue;
+    for (int k3 = 0; k3 < sub; ++k3)
+      for (int k2 = 0; k2 < sub; ++k2)
+        for (int k1 = 0; k1 < sub; ++k1) {
+          const int k[3] = {k1, k2, k3};
+          for (int a = 0; a < 3; ++a) R.boxes.push_back(-1.0 + 2.0 * k[a] / sub);
+          for (int a = 0; a < 3; ++a) R.boxes.push_back(-1.0 + 2.0 * (k[a] + 1) / sub);
+          ++R.cb[cell + 1];
+        }
+  }
+  return R;
+}
+
+// The adaptive rule (reading Q1): a box's n^3 estimate of the trial integrals
+// against the sum of the same rule on its eight half-size children; where every
+// trial integral agrees to tol the children are kept, else each child is refined
+// the same way, down to max_depth levels.  Trial integrands of the nuclear
+// enrichment: the smeared charge b and the atomic part N^A_J of every atom
+// (those that vanish on a cell contribute zero to both estimates and are skipped,
+// as are the charges of nuclei beyond 40 sigma).
+struct NucTrial {
+  const Ctx* c;
+  double a, norm, inv2s2, r0, s;
+  std::vector<int> local, nearb;   // atoms whose support / charge reaches the cell
+  void eval(const double x[3], double* out) const {
+    double b = 0.0;
+    for (int t : nearb) {
+      const double dx = x[0] - c->R[3 * t], dy = x[1] - c->R[3 * t + 1], dz = x[2] - c->R[3 * t + 2];
+      b -= c->Z[t] * norm * std::exp(-(dx * dx + dy * dy + dz * dz) * inv2s2);
+    }
+    out[0] = b;
+    for (size_t k = 0; k < local.size(); ++k) {
+      const int J = local[k];
+      const double dx = x[0] - c->R[3 * J], dy = x[1] - c->R[3 * J + 1], dz = x[2] - c->R[3 * J + 2];
+      const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+      const double f = r > 0.0 ? -c->Z[J] * std::erf(a * r) / r : -c->Z[J] * 2.0 * a / std::sqrt(kPi);
+      double u, du;
+      cutoff(r, r0, s, u, du);
+      out[1 + k] = f * u;
+    }
+  }
+};
+
+void box_integrals(const NucTrial& T, const double lo[3], const double hi[3], const double o[3], const double h[3],
+                   const std::vector<double>& xg, const std::vector<double>& wg, double* acc, double* val) {
+  const int n = (int)xg.size(), m = 1 + (int)T.local.size();
+  for (int i = 0; i < m; ++i) acc[i] = 0.0;
+  double mid[3], half[3];
+  for (int a = 0; a < 3; ++a) {
+    mid[a] = 0.5 * (lo[a] + hi[a]);
+    half[a] = 0.5 * (hi[a] - lo[a]);
+  }
+  for (int k3 = 0; k3 < n; ++k3)
+    for (int k2 = 0; k2 < n; ++k2)
+      for (int k1 = 0; k1 < n; ++k1) {
+        const int k[3] = {k1, k2, k3};
+        double x[3], w = 1.0;
+        for (int a = 0; a < 3; ++a) {
+          x[a] = o[a] + 0.5 * (mid[a] + xg[k[a]] * half[a] + 1.0) * h[a];
+          w *= wg[k[a]] * half[a] * 0.5 * h[a];
+        }
+        T.eval(x, val);
+        for (int i = 0; i < m; ++i) acc[i] += w * val[i];
+      }
+}
+
+void adapt_box(const NucTrial& T, const double lo[3], const double hi[3], int depth, int max_depth, double tol,
+               const double o[3], const double h[3], const std::vector<double>& xg, const std::vector<double>& wg,
+               std::vector<double>& out) {
+  const int m = 1 + (int)T.local.size();
+  std::vector<double> coarse(m), fine(m, 0.0), part(m), val(m);
+  box_integrals(T, lo, hi, o, h, xg, wg, coarse.data(), val.data());
+  double clo[8][3], chi[8][3];
+  for (int i = 0; i < 8; ++i)
+    for (int a = 0; a < 3; ++a) {
+      const double mid = 0.5 * (lo[a] + hi[a]);
+      const bool up = (i >> a) & 1;
+      clo[i][a] = up ? mid : lo[a];
+      chi[i][a] = up ? hi[a] : mid;
+    }
+  for (int i = 0; i < 8; ++i) {
+    box_integrals(T, clo[i], chi[i], o, h, xg, wg, part.data(), val.data());
+    for (int j = 0; j < m; ++j) fine[j] += part[j];
+  }
+  bool ok = depth >= max_depth;
+  if (!ok) {
+    ok = true;
+    for (int j = 0; j < m; ++j)
+      if (!(std::fabs(fine[j] - coarse[j]) <= tol)) ok = false;
+  }
+  if (ok) {
+    for (int i = 0; i < 8; ++i) {
+      out.insert(out.end(), clo[i], clo[i] + 3);
+      out.insert(out.end(), chi[i], chi[i] + 3);
+    }
+    return;
+  }
+  for (int i = 0; i < 8; ++i) adapt_box(T, clo[i], chi[i], depth + 1, max_depth, tol, o, h, xg, wg, out);
+}
+
+BoxRule adaptive_rule(const Ctx& c, const Lists& L, int n, double tol, int max_depth, double sigma, double r0,
+                      double s) {
+  BoxRule R;
+  R.n = n;
+  std::vector<double> xg(n), wg(n);
+  gauss_legendre(n, xg.data(), wg.data());
+  const std::vector<char> on = listed_cells(c, L);
+  std::vector<int> cells;
+  for (int cell = 0; cell < c.nc; ++cell)
+    if (on[cell]) cells.push_back(cell);
+  std::vector<std::vector<double>> per(cells.size());
+  const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  auto work = [&](unsigned tid) {
+    for (size_t i = tid; i < cells.size(); i += nt) {
+      const int cell = cells[i];
+      const int cx = cell % c.ncx, cy = (cell / c.ncx) % c.ncy, cz = cell / (c.ncx * c.ncy);
+      const double o[3] = {c.xb[cx], c.yb[cy], c.zb[cz]};
+      const double h[3] = {c.xb[cx + 1] - c.xb[cx], c.yb[cy + 1] - c.yb[cy], c.zb[cz + 1] - c.zb[cz]};
+      const double bhi[3] = {o[0] + h[0], o[1] + h[1], o[2] + h[2]};
+      NucTrial T{&c, 1.0 / (std::sqrt(2.0) * sigma), std::pow(2.0 * kPi * sigma * sigma, -1.5),
+                 1.0 / (2.0 * sigma * sigma), r0, s, {}, {}};
+      for (int J = 0; J < c.n_atoms; ++J) {
+        const double d = box_distance(o, bhi, &c.R[3 * J]);
+        if (d < r0) T.local.push_back(J);
+        if (d < 40.0 * sigma) T.nearb.push_back(J);
+      }
+      const double lo[3] = {-1.0, -1.0, -1.0}, hi[3] = {1.0, 1.0, 1.0};
+      adapt_box(T, lo, hi, 0, max_depth, tol, o, h, xg, wg, per[i]);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (unsigned t = 0; t < nt; ++t) pool.emplace_back(work, t);
+  for (auto& t : pool) t.join();
+  R.cb.assign(c.nc + 1, 0);
+  size_t i = 0;
+  for (int cell = 0; cell < c.nc; ++cell) {
+    R.cb[cell + 1] = R.cb[cell];
+    if (i < cells.size() && cells[i] == cell) {
+      R.cb[cell + 1] += (long long)(per[i].size() / 6);
+      R.boxes.insert(R.boxes.end(), per[i].begin(), per[i].end());
+      ++i;
+    }
+  }
+  return R;
+}
+
 // Blocks of one enrichment (module comment): C (d_C), G (d_G), A_IJ (d_LC),
 // X_J = A_II^-1 A_IJ (d_X), each [nA][n_h], and on the host S = A_EE - A_EI X.
 // With a charge (norm > 0) also d = int b N (d_dC) and, on the host,
 // dE = int b N^A - C . d.  Synchronises st.
 template <class Rad>
-efe_status enr_blocks(Ctx& c, const Rad& rad, const double* d_at, double r0, double s, int sub, int n_quad,
-                      double norm, double inv2s2, double reach, const Lists& L, double* d_C, double* d_G,
+efe_status enr_blocks(Ctx& c, const Rad& rad, const double* d_at, double r0, double s, const BoxRule& rule,
+                      double norm, double inv2s2, const Lists& L, double* d_C, double* d_G,
                       double* d_LC, double* d_X, double* d_dC, std::vector<double>& S, std::vector<double>& dE,
                       cudaStream_t st) {
-  const int nA = c.n_atoms, P1 = c.P1, m1 = sub * n_quad;
+  const int nA = c.n_atoms, P1 = c.P1, n = rule.n;
   const long long n_h = c.n_h;
   const size_t vecs = (size_t)nA * n_h;
-  const std::vector<double> rule = composite_rule(c, sub, n_quad);
+  std::vector<double> tabs(P1 + 2 * n), gllw(P1);   // GLL nodes, GL points, GL weights
+  gauss_lobatto(c.p, tabs.data(), gllw.data());
+  gauss_legendre(n, tabs.data() + P1, tabs.data() + P1 + n);
   Bufs B;
-  double *d_rule, *d_ba, *d_AA, *d_dots, *d_Ap;
+  double *d_tabs, *d_boxes, *d_ba, *d_AA, *d_dots, *d_Ap;
+  long long* d_cb;
   int *d_ic, *d_if, *d_ac, *d_aa, *d_ab;
-  ENR_CK(B.alloc(d_rule, rule.size()), "allocating");
+  ENR_CK(B.alloc(d_tabs, tabs.size()), "allocating");
+  ENR_CK(B.alloc(d_boxes, rule.boxes.size()), "allocating");
+  ENR_CK(B.alloc(d_cb, rule.cb.size()), "allocating");
   ENR_CK(B.alloc(d_ba, nA), "allocating");
   ENR_CK(B.alloc(d_AA, (size_t)nA * nA), "allocating");
   ENR_CK(B.alloc(d_dots, (size_t)3 * nA * nA + nA), "allocating");
@@ -594,7 +790,9 @@ efe_status enr_blocks(Ctx& c, const Rad& rad, const double* d_at, double r0, dou
   auto up = [&](void* dst, const void* src, size_t bytes) {
     return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
   };
-  ENR_CK(up(d_rule, rule.data(), sizeof(double) * rule.size()), "copy");
+  ENR_CK(up(d_tabs, tabs.data(), sizeof(double) * tabs.size()), "copy");
+  ENR_CK(up(d_boxes, rule.boxes.data(), sizeof(double) * rule.boxes.size()), "copy");
+  ENR_CK(up(d_cb, rule.cb.data(), sizeof(long long) * rule.cb.size()), "copy");
   ENR_CK(up(d_ic, L.it_cell.data(), sizeof(int) * L.it_cell.size()), "copy");
   ENR_CK(up(d_if, L.it_fn.data(), sizeof(int) * L.it_fn.size()), "copy");
   ENR_CK(up(d_ac, L.aa_cell.data(), sizeof(int) * L.aa_cell.size()), "copy");
@@ -605,17 +803,19 @@ efe_status enr_blocks(Ctx& c, const Rad& rad, const double* d_at, double r0, dou
   ENR_CK(cudaMemsetAsync(d_AA, 0, sizeof(double) * nA * nA, st), "clear");
   if (d_dC) ENR_CK(cudaMemsetAsync(d_dC, 0, sizeof(double) * n_h, st), "clear");
   // cell integrals (bA into d_C, then scaled in place)
+  const double* d_gll = d_tabs;
+  const double* d_xg = d_tabs + P1;
+  const double* d_wg = d_tabs + P1 + n;
   if (!L.it_cell.empty()) {
-    const size_t sm = sizeof(double) * (2 * (size_t)m1 * P1 + 2 * m1 + 5 * kNucThreads);
-    k_nuc_cells<Rad><<<(unsigned)L.it_cell.size(), kNucThreads, sm, st>>>(c.mesh, d_rule, m1, d_ic, d_if, d_at, nA,
-                                                                          rad, norm, inv2s2, r0, s, d_C, d_G, d_ba,
-                                                                          d_dC);
+    k_nuc_cells<Rad><<<(unsigned)L.it_cell.size(), kNucThreads, 0, st>>>(c.mesh, d_gll, d_xg, d_wg, n, d_cb, d_boxes,
+                                                                         d_ic, d_if, d_at, nA, rad, norm, inv2s2, r0,
+                                                                         s, d_C, d_G, d_ba, d_dC);
     note_launch();
     ENR_CK(cudaGetLastError(), "cell integrals");
   }
   if (!L.aa_cell.empty()) {
-    k_nuc_aa<Rad><<<(unsigned)L.aa_cell.size(), kNucThreads, 0, st>>>(c.mesh, d_rule, m1, d_ac, d_aa, d_ab, d_at,
-                                                                       rad, r0, s, nA, d_AA);
+    k_nuc_aa<Rad><<<(unsigned)L.aa_cell.size(), kNucThreads, 0, st>>>(c.mesh, d_xg, d_wg, n, d_cb, d_boxes, d_ac,
+                                                                       d_aa, d_ab, d_at, rad, r0, s, nA, d_AA);
     note_launch();
     ENR_CK(cudaGetLastError(), "atomic stiffness");
   }
@@ -799,12 +999,13 @@ void atom_tables(const Ctx& c, int nt, double rmax, std::vector<double>& rg, std
 }  // namespace
 
 // ---------------------------------------------------------------------------- nuclear potential
-efe_status nuclear_enriched(Ctx& c, double sigma, double r0, double s, int sub, int n_quad, double* phiE_host,
-                            cudaStream_t st) {
-  if (!(sigma > 0.0)) {
-    c.err = "nuclear enrichment: need sigma > 0";
+efe_status nuclear_enriched(Ctx& c, double sigma, double r0, double s, int sub, int n_quad, double adapt_tol,
+                            int adapt_depth, double* phiE_host, cudaStream_t st) {
+  if (!(sigma > 0.0) || !(adapt_tol >= 0.0) || adapt_depth < 0 || adapt_depth > 8) {
+    c.err = "nuclear enrichment: need sigma > 0, adapt_tol >= 0, adapt_depth in [0, 8]";
     return EFE_ERR_ARG;
   }
+  if (adapt_tol > 0.0) sub = 1;
   if (!enr_args_ok(c, r0, s, sub, n_quad)) return EFE_ERR_ARG;
   const int nA = c.n_atoms;
   std::vector<double> at(4 * (size_t)nA);
@@ -830,7 +1031,9 @@ efe_status nuclear_enriched(Ctx& c, double sigma, double r0, double s, int sub, 
   Lists L;
   work_lists(c, r0, 40.0 * sigma, L);   // exp(-40^2 / 2) underflows: no charge beyond 40 sigma
   std::vector<double> S, dE;
-  efe_status e = enr_blocks(c, nrad, d_at, r0, s, sub, n_quad, norm, inv2s2, 40.0 * sigma, L, d_C, d_G, d_LC, d_X,
+  const BoxRule rule = adapt_tol > 0.0 ? adaptive_rule(c, L, n_quad, adapt_tol, adapt_depth, sigma, r0, s)
+                                       : uniform_rule(c, L, sub, n_quad);
+  efe_status e = enr_blocks(c, nrad, d_at, r0, s, rule, norm, inv2s2, L, d_C, d_G, d_LC, d_X,
                             d_dC, S, dE, st);
   if (e != EFE_OK) return e;
   // classical solve with the smeared-nucleus boundary data
@@ -938,7 +1141,8 @@ efe_status hartree_enrich_install(Ctx& c, double r0, double s, int sub, int n_qu
   double* d_LC;
   ENR_CK(B.alloc(d_LC, vecs), "allocating");
   std::vector<double> S, dE;
-  efe_status e = enr_blocks(c, trad, h.atoms, r0, s, sub, n_quad, 0.0, 0.0, 0.0, L, h.C, h.G, d_LC, h.X, nullptr,
+  const BoxRule rule = uniform_rule(c, L, sub, n_quad);
+  efe_status e = enr_blocks(c, trad, h.atoms, r0, s, rule, 0.0, 0.0, L, h.C, h.G, d_LC, h.X, nullptr,
                             S, dE, st);
   if (e != EFE_OK) return e;
   std::vector<double> Lc, Sinv((size_t)nA * nA), col(nA), x(nA);

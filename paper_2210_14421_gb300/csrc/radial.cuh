@@ -7,7 +7,7 @@
 namespace efe {
 
 // smooth cutoff u(r) = 1 - S(t), t = (r - r0 + s)/s, S(t) = g(t)/(g(t)+g(1-t)), g = exp(-1/t)
-__device__ __forceinline__ void cutoff(double r, double r0, double s, double& u, double& du) {
+__host__ __device__ __forceinline__ void cutoff(double r, double r0, double s, double& u, double& du) {
   const double t = (r - (r0 - s)) / s;
   if (t <= 0.0) { u = 1.0; du = 0.0; return; }
   if (t >= 1.0) { u = 0.0; du = 0.0; return; }

@@ -69,6 +69,51 @@ def test_nuclear_enriched_matches_oracle(name):
     ctx.close()
 
 
+def _nuclear_trial(wl, sigma, r0, s):
+    """Trial integrands of the adaptive rule: the smeared charge and every atom's
+    truncated smeared-nucleus potential."""
+    from oracle import electrostatic as es
+    from oracle.enrich import cutoff
+    Z, R = list(wl.Z), [np.asarray(r) for r in wl.R]
+    rad = [es.nuclear_radial(z, sigma) for z in Z]
+
+    def trial(p):
+        cols = [es.smeared_charge(Z, R, sigma, p)]
+        for J in range(len(Z)):
+            r = np.linalg.norm(p - R[J][None, :], axis=1)
+            f, _ = rad[J](r)
+            u, _ = cutoff(r, r0, s)
+            cols.append(f * u)
+        return np.stack(cols, axis=1)
+    return trial
+
+
+def test_nuclear_enriched_adaptive_rule_matches_oracle():
+    """The adaptive cell rule (recursive octant refinement until the trial
+    integrals agree to 1e-6, at most 3 levels): potential and coefficients
+    against NuclearEFE on the oracle's AdaptiveRule with the same trial
+    integrands (1e-10)."""
+    from oracle import electrostatic as es, quadrature as qd
+    from oracle.mesh import Mesh
+    from paper_2210_14421_gb300 import Context
+    wl = W.small_cluster(n_atoms=2, cells_per_axis=5, degree=3, n_quad=5, n_orb=3)
+    sigma, r0, s, tol, depth = 0.3, 3.0, 1.5, 1e-6, 3
+    m = Mesh(wl.xb, wl.yb, wl.zb, wl.degree, wl.n_quad)
+    rule = qd.AdaptiveRule(m, _nuclear_trial(wl, sigma, r0, s), wl.n_quad, tol, depth)
+    P = es.NuclearEFE(m, list(wl.Z), list(wl.R), sigma, r0=r0, s=s, rule=rule)
+    phi, phiE = P.solve()
+    gl = es.CompositeRule(m, 1, m.nq1)
+    ref = np.empty((m.n_cells, m.nq))
+    for c in range(m.n_cells):
+        pts, _, Bc, G = gl.cell(m, c)
+        ref[c] = Bc @ phi[m.conn[c]] + P._enriched_at(c, pts, Bc, G)[0] @ phiE
+    ctx = Context(wl)
+    vN, got_E = ctx.nuclear_enriched(sigma, r0, s, n_quad=wl.n_quad, adapt_tol=tol, adapt_depth=depth)
+    assert np.max(np.abs(vN.cpu().numpy() - ref)) <= 1e-10 * np.max(np.abs(ref))
+    assert np.max(np.abs(got_E - phiE)) <= 1e-10 * np.max(np.abs(phiE))
+    ctx.close()
+
+
 def test_steps_with_enriched_nucleus_match_oracle():
     """Kick + 2 predictor-corrector steps (fixed Krylov dimension) with the
     enriched nuclear potential installed: orbitals and dipoles to 1e-10."""
@@ -113,6 +158,10 @@ def test_nuclear_enriched_rejects_bad_arguments():
                  (0.25, 9.0, 1.5, 2, 0)):    # support reaching the boundary (atoms 7.3 bohr inside)
         with pytest.raises(EfeError):
             ctx.nuclear_enriched(*args[:3], sub=args[3], n_quad=args[4])
+    with pytest.raises(EfeError):
+        ctx.nuclear_enriched(0.25, 3.0, 1.5, adapt_tol=-1.0)
+    with pytest.raises(EfeError):
+        ctx.nuclear_enriched(0.25, 3.0, 1.5, adapt_tol=1e-6, adapt_depth=9)
     ctx.close()
 
 
