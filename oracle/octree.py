@@ -130,6 +130,29 @@ class OctreeMesh:
                               shape=(self.n_all, self.n_all))
         return (self.P.T @ K_all @ self.P).tocsr(), self.P.T @ F
 
+    def quad_points(self):
+        """Physical Gauss-Legendre points of every leaf, (n_leaves, nq, 3), in the
+        order of self.wq (first axis fastest)."""
+        return np.stack([x0[None, :] + 0.5 * (self.xq_ref + 1.0) * h[None, :] for x0, h, _ in self.leaves])
+
+    def hamiltonian(self, vq, kin: float = 1.0):
+        """P^T (kin (1/2) K_all + V_all) P with V_all = sum over leaves of
+        int v N_m N_n, v given at every leaf's Gauss-Legendre points
+        (n_leaves, nq) (the operator of Eq. Hmn on the locally refined mesh,
+        constrained space)."""
+        rows, cols, vals = [], [], []
+        for li, (x0, h, _) in enumerate(self.leaves):
+            idx = self.conn[li]
+            G = [self.Dref[a] * (2.0 / h[a]) for a in range(3)]
+            w = self.wq * np.prod(h) / 8.0
+            Hc = kin * 0.5 * sum(G[a].T @ (w[:, None] * G[a]) for a in range(3)) + self.B.T @ ((w * vq[li])[:, None] * self.B)
+            rows.append(np.repeat(idx, len(idx)))
+            cols.append(np.tile(idx, len(idx)))
+            vals.append(Hc.ravel())
+        H_all = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                              shape=(self.n_all, self.n_all))
+        return (self.P.T @ H_all @ self.P).tocsr()
+
     def solve_poisson(self, f, g):
         """-lap u = f with u = g on the boundary, in the constrained space: free
         values (n_free,) and all node values (n_all,)."""

@@ -90,3 +90,23 @@ def test_local_refinement_resolves_a_local_feature():
     assert res["local"][0] <= 1.05 * res["fine"][0], res
     assert res["local"][1] < 0.4 * res["fine"][1]
     assert res["local"][0] * 10 < res["coarse"][0]
+
+
+def test_hamiltonian_potential_part_integrates_and_is_symmetric():
+    """The octree Hamiltonian's potential part against closed forms: with
+    kin = 0 and v = c, <1, H 1> = c |box| (the constant is in the constrained
+    space and the consistent mass integrates it exactly); with v = x,
+    <1, H 1> = int x = |box| x_centre; H is symmetric; the kinetic part
+    annihilates constants."""
+    m = OctreeMesh([0, 0, 0], [3, 2, 2], 3, 3, [(1, 0, 0), (2, 1, 1)])
+    xq = m.quad_points()
+    one = np.ones(len(m.free))
+    vol = 3.0 * 2.0 * 2.0
+    H = m.hamiltonian(np.full(xq.shape[:2], 0.7), kin=0.0)
+    assert abs(one @ (H @ one) - 0.7 * vol) < 1e-12 * vol
+    H = m.hamiltonian(xq[:, :, 0], kin=0.0)
+    assert abs(one @ (H @ one) - 1.5 * vol) < 1e-12 * vol
+    H = m.hamiltonian(xq[:, :, 1] ** 2 - xq[:, :, 2], kin=1.0)
+    assert abs(H - H.T).max() < 1e-13 * abs(H).max()
+    K = m.hamiltonian(np.zeros(xq.shape[:2]), kin=1.0)
+    assert np.abs(K @ one).max() < 1e-12 * abs(K).max()
