@@ -393,6 +393,44 @@ efe_status efe_nuclear_enriched(efe_ctx* ctx, double sigma, double r0, double s,
  * EFE_ERR_NOT_SPD, EFE_ERR_NOMEM, EFE_ERR_CUDA. */
 efe_status efe_hartree_enriched(efe_ctx* ctx, double r0, double s, int32_t sub, int32_t n_quad, void* stream);
 
+/* Locally refined mesh with hanging-node constraints (the paper's adaptively
+ * refined finite element mesh, Sec. "Enriched finite element basis"): one
+ * refinement level over a uniform nc^3 grid of the box [lo, hi] (host
+ * double[3] each); the n_refine coarse cells (i, j, k) listed in refine_host
+ * (int32[n_refine][3]) are split into 2 x 2 x 2 leaves.  Every leaf carries
+ * degree-p Lagrange functions on GLL nodes (p in [1, 5]) and an n_quad^3
+ * Gauss-Legendre rule (n_quad in [p + 1, 8]).  A fine-leaf node on the closed
+ * box of a coarse leaf that is not one of its nodes hangs: its value is the
+ * coarse leaf's interpolant there, u_all = P u_free.  The handle owns the mesh
+ * and P on the device.  Errors: EFE_ERR_ARG (sizes, a refined cell outside
+ * the grid), EFE_ERR_NOMEM, EFE_ERR_CUDA; message by efe_octree_last_error(NULL). */
+typedef struct efe_octree efe_octree;
+efe_status efe_octree_setup(const double* lo_host, const double* hi_host, int32_t nc, int32_t degree, int32_t n_quad,
+                            const int32_t* refine_host, int32_t n_refine, efe_octree** out);
+efe_status efe_octree_destroy(efe_octree* oct);
+const char* efe_octree_last_error(const efe_octree* oct);
+/* Counts: free (unconstrained) nodes, all nodes, leaves, quadrature points per
+ * leaf, hanging nodes (any pointer may be NULL). */
+efe_status efe_octree_sizes(const efe_octree* oct, int64_t* n_free, int64_t* n_all, int64_t* n_leaves, int64_t* n_q,
+                            int64_t* n_hanging);
+/* Host copies: free-node coordinates [n_free][3], the leaves' Gauss-Legendre
+ * points [n_leaves][n_q][3] (first axis fastest), boundary flags [n_free]
+ * (1 on the domain boundary); any pointer may be NULL. */
+efe_status efe_octree_coords(const efe_octree* oct, double* free_xyz_host, double* quad_xyz_host,
+                             uint8_t* boundary_host);
+/* Y = P^T (kin (1/2) K + V) P X in the constrained space (Eq. Hmn on the
+ * locally refined mesh): K the stiffness int grad N . grad N, V the potential
+ * matrix int v N N with v given at every leaf's Gauss-Legendre points (vq_dev:
+ * device [n_leaves][n_q]).  X_dev, Y_dev: device [n_free][n_cols] doubles
+ * (real columns, 1 <= n_cols <= 65535).  mask_boundary != 0 applies the
+ * Dirichlet restriction: boundary entries of X read as 0 and boundary rows of
+ * Y are 0.  Three stages (gather through P, per-leaf operator scatter-added
+ * over all nodes, scatter through P^T); stream-ordered; the first call with
+ * more columns than before allocates scratch (2 n_all n_cols doubles).
+ * Errors: EFE_ERR_ARG, EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+efe_status efe_octree_apply(efe_octree* oct, const double* vq_dev, double kin, const double* X_dev, double* Y_dev,
+                            int64_t n_cols, int32_t mask_boundary, void* stream);
+
 /* Spectra of dipole traces (Sec. Results: the absorption spectrum of the weak
  * perturbation study and the power spectrum of the high-harmonic study); no
  * context needed.  Samples at t_n = n dt, n = 0 .. n_t - 1, on the device;

@@ -25,7 +25,8 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_kick", "efe_init_orbitals", "efe_profile", "efe_profile_read", "efe_selftest",
             "efe_apply_H_noalloc", "efe_tuning", "efe_adjoint_dipole",
             "efe_absorption_spectrum", "efe_power_spectrum", "efe_nuclear_enriched",
-            "efe_hartree_enriched"]
+            "efe_hartree_enriched", "efe_octree_setup", "efe_octree_destroy", "efe_octree_last_error",
+            "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply"]
 
 
 class MeshDesc(C.Structure):
@@ -106,8 +107,15 @@ def lib(path: str = LIB_PATH):
                                      pdbl, vp]
     L.efe_nuclear_enriched.argtypes = [vp, dbl, dbl, dbl, i32, i32, dbl, i32, vp, pdbl, vp]
     L.efe_hartree_enriched.argtypes = [vp, dbl, dbl, i32, i32, vp]
+    L.efe_octree_setup.argtypes = [pdbl, pdbl, i32, i32, i32, C.POINTER(i32), i32, C.POINTER(vp)]
+    L.efe_octree_destroy.argtypes = [vp]
+    L.efe_octree_last_error.argtypes = [vp]
+    L.efe_octree_last_error.restype = C.c_char_p
+    L.efe_octree_sizes.argtypes = [vp] + [C.POINTER(i64)] * 5
+    L.efe_octree_coords.argtypes = [vp, pdbl, pdbl, C.POINTER(C.c_uint8)]
+    L.efe_octree_apply.argtypes = [vp, vp, dbl, vp, vp, i64, i32, vp]
     for name in EXPORTED:
-        if name != "efe_last_error":
+        if name not in ("efe_last_error", "efe_octree_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -354,3 +362,53 @@ class Context:
         self._check(lib().efe_init_orbitals(self.h, _ptr(psi), int(G), _dptr(cen), _dptr(ex), _dptr(co), _dptr(en),
                                             _stream()))
         return psi
+
+
+class Octree:
+    """Owns one efe_octree (locally refined mesh with hanging-node constraints)."""
+
+    def __init__(self, lo, hi, nc: int, degree: int, n_quad: int, refine=()):
+        L = lib()
+        lo = np.ascontiguousarray(lo, dtype=np.float64)
+        hi = np.ascontiguousarray(hi, dtype=np.float64)
+        ref = np.ascontiguousarray(np.asarray(list(refine), dtype=np.int32).reshape(-1, 3))
+        h = C.c_void_p()
+        st = L.efe_octree_setup(_dptr(lo), _dptr(hi), int(nc), int(degree), int(n_quad),
+                                ref.ctypes.data_as(C.POINTER(C.c_int32)), int(len(ref)), C.byref(h))
+        if st != EFE_OK:
+            raise EfeError(st, L.efe_octree_last_error(None).decode())
+        self.h = h
+        v = [C.c_int64() for _ in range(5)]
+        L.efe_octree_sizes(self.h, *[C.byref(x) for x in v])
+        self.n_free, self.n_all, self.n_leaves, self.n_q, self.n_hanging = (x.value for x in v)
+
+    def coords(self):
+        """(free-node coordinates [n_free, 3], quadrature points [n_leaves, n_q, 3],
+        boundary flags [n_free]) as numpy arrays."""
+        fx = np.zeros((self.n_free, 3))
+        qx = np.zeros((self.n_leaves, self.n_q, 3))
+        bd = np.zeros(self.n_free, dtype=np.uint8)
+        st = lib().efe_octree_coords(self.h, _dptr(fx), _dptr(qx), bd.ctypes.data_as(C.POINTER(C.c_uint8)))
+        if st != EFE_OK:
+            raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
+        return fx, qx, bd.astype(bool)
+
+    def apply(self, vq, X, Y, kin: float = 1.0, mask_boundary: bool = False):
+        """Y = P^T (kin K/2 + V) P X; vq device [n_leaves, n_q], X, Y device [n_free, n_cols] float64."""
+        assert X.is_contiguous() and Y.is_contiguous() and vq.is_contiguous()
+        st = lib().efe_octree_apply(self.h, _ptr(vq), float(kin), _ptr(X), _ptr(Y), int(X.shape[1]),
+                                    int(bool(mask_boundary)), _stream())
+        if st != EFE_OK:
+            raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
+        return Y
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().efe_octree_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

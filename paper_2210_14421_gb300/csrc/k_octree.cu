@@ -1,0 +1,498 @@
+// Locally refined mesh with hanging-node constraints (the paper's adaptively
+// refined mesh, Sec. "Enriched finite element basis"): the Hamiltonian of
+// Eq. Hmn applied in the constrained space, Y = P^T (kin (1/2) K + V) P X.
+//
+// The mesh is one refinement level over a uniform coarse grid: chosen coarse
+// cells are split into 2 x 2 x 2 leaves, so neighbouring leaves differ by at
+// most one level.  Every leaf carries degree-p Lagrange functions on GLL nodes;
+// coincident nodes of leaves are one node.  A node of a fine leaf that lies on
+// the closed box of a coarse leaf without being one of its nodes is hanging:
+// its value is the coarse leaf's interpolant there, so u_all = P u_free with P
+// the interpolation weights (rows of hanging nodes) and the identity (rows of
+// free nodes).  The apply is three stages: the gather x_all = P x_free, the
+// per-leaf operator (kinetic by its Kronecker form, potential by sum
+// factorisation at the Gauss-Legendre points) scatter-added into y_all, and
+// the transposed scatter y_free = P^T y_all.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <type_traits>
+#include <vector>
+
+#include "efe_internal.h"
+
+namespace efe {
+
+constexpr int kOctMaxQ1 = 8;
+constexpr int kOctThreads = 128;
+
+// 1D reference tables of the leaves (passed by value): GL values of the GLL
+// Lagrange basis B1[q][i], exact 1D stiffness and mass K1, M1, GL weights.
+struct OctTables {
+  double B1[kOctMaxQ1 * kMaxP1];
+  double K1[kMaxP1 * kMaxP1];
+  double M1[kMaxP1 * kMaxP1];
+  double wg[kOctMaxQ1];
+  int P1, NQ1;
+};
+
+struct Octree {
+  std::string err;
+  int p = 0, P1 = 0, NQ1 = 0, nn = 0, nq = 0;
+  long long n_leaves = 0, n_all = 0, n_free = 0, n_hang = 0;
+  OctTables tab{};
+  std::vector<double> free_xyz, quad_xyz;   // host copies for efe_octree_coords
+  std::vector<double> all_xyz;              // coordinates of all nodes
+  std::vector<long long> rs;                // host copy of P (CSR over all nodes)
+  std::vector<int> col;
+  std::vector<double> val;
+  double* d_geo = nullptr;                  // [n_leaves][6] origin, size
+  int* d_conn = nullptr;                    // [n_leaves][nn] node ids
+  long long* d_rs = nullptr;                // [n_all + 1] row starts of P
+  int* d_col = nullptr;                     // free index per entry
+  double* d_val = nullptr;                  // weight per entry
+  unsigned char* d_bnd = nullptr;           // [n_free] 1 on the domain boundary
+  double* d_xall = nullptr;                 // [n_all][cols] scratch
+  double* d_yall = nullptr;
+  long long ws_cols = 0;
+  ~Octree() {
+    for (void* q : {(void*)d_geo, (void*)d_conn, (void*)d_rs, (void*)d_col, (void*)d_val, (void*)d_bnd,
+                    (void*)d_xall, (void*)d_yall})
+      if (q) cudaFree(q);
+  }
+};
+
+namespace {
+
+// x_all[n][c] = sum_k val_k x_free[col_k][c] over row n of P (boundary free values as 0 when masked)
+__global__ void k_oct_expand(const long long* __restrict__ rs, const int* __restrict__ col,
+                             const double* __restrict__ val, const unsigned char* __restrict__ bnd,
+                             const double* __restrict__ xf, long long n_all, int ncols, int mask,
+                             double* __restrict__ xa) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n_all * ncols) return;
+  const long long n = idx / ncols;
+  const int c = (int)(idx % ncols);
+  double v = 0.0;
+  for (long long k = rs[n]; k < rs[n + 1]; ++k) {
+    const int f = col[k];
+    if (mask && bnd[f]) continue;
+    v += val[k] * xf[(long long)f * ncols + c];
+  }
+  xa[idx] = v;
+}
+
+// y_free[col_k][c] += val_k y_all[n][c] over row n of P (boundary rows skipped when masked)
+__global__ void k_oct_reduce(const long long* __restrict__ rs, const int* __restrict__ col,
+                             const double* __restrict__ val, const unsigned char* __restrict__ bnd,
+                             const double* __restrict__ ya, long long n_all, int ncols, int mask,
+                             double* __restrict__ yf) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n_all * ncols) return;
+  const long long n = idx / ncols;
+  const int c = (int)(idx % ncols);
+  const double y = ya[idx];
+  for (long long k = rs[n]; k < rs[n + 1]; ++k) {
+    const int f = col[k];
+    if (mask && bnd[f]) continue;
+    atomicAdd(&yf[(long long)f * ncols + c], val[k] * y);
+  }
+}
+
+// One block per (leaf, column): y_all += (kin (1/2) K_leaf + V_leaf) x_leaf, v at the leaf's GL points.
+__global__ void __launch_bounds__(kOctThreads)
+k_oct_apply(const OctTables T, const double* __restrict__ geo, const int* __restrict__ conn,
+            const double* __restrict__ vq, double kin, const double* __restrict__ xa, int ncols,
+            double* __restrict__ ya) {
+  __shared__ double x[kMaxP1 * kMaxP1 * kMaxP1];
+  __shared__ double A[kOctMaxQ1 * kMaxP1 * kMaxP1];
+  __shared__ double Bq[kOctMaxQ1 * kOctMaxQ1 * kMaxP1];
+  __shared__ double Cq[kOctMaxQ1 * kOctMaxQ1 * kOctMaxQ1];
+  const int P1 = T.P1, Q = T.NQ1, nn = P1 * P1 * P1, nq = Q * Q * Q;
+  const long long leaf = blockIdx.x;
+  const int c = blockIdx.y;
+  const double hx = geo[6 * leaf + 3], hy = geo[6 * leaf + 4], hz = geo[6 * leaf + 5];
+  const int* cl = conn + leaf * nn;
+  for (int l = threadIdx.x; l < nn; l += blockDim.x) x[l] = xa[(long long)cl[l] * ncols + c];
+  __syncthreads();
+  // potential: values at the GL points (axis 1, 2, 3), times w |J| v, back (axis 3, 2, 1)
+  for (int t = threadIdx.x; t < Q * P1 * P1; t += blockDim.x) {   // A[q1][i2][i3]
+    const int q1 = t % Q, i2 = (t / Q) % P1, i3 = t / (Q * P1);
+    double s = 0.0;
+    for (int i1 = 0; i1 < P1; ++i1) s += T.B1[q1 * P1 + i1] * x[i1 + P1 * (i2 + P1 * i3)];
+    A[t] = s;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < Q * Q * P1; t += blockDim.x) {    // Bq[q1][q2][i3]
+    const int q1 = t % Q, q2 = (t / Q) % Q, i3 = t / (Q * Q);
+    double s = 0.0;
+    for (int i2 = 0; i2 < P1; ++i2) s += T.B1[q2 * P1 + i2] * A[q1 + Q * (i2 + P1 * i3)];
+    Bq[t] = s;
+  }
+  __syncthreads();
+  const double detJ = hx * hy * hz / 8.0;
+  for (int t = threadIdx.x; t < nq; t += blockDim.x) {            // Cq[q1][q2][q3]
+    const int q1 = t % Q, q2 = (t / Q) % Q, q3 = t / (Q * Q);
+    double s = 0.0;
+    for (int i3 = 0; i3 < P1; ++i3) s += T.B1[q3 * P1 + i3] * Bq[q1 + Q * (q2 + Q * i3)];
+    Cq[t] = s * T.wg[q1] * T.wg[q2] * T.wg[q3] * detJ * vq[leaf * nq + t];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < Q * Q * P1; t += blockDim.x) {    // Bq[q1][q2][i3] = sum_q3
+    const int q1 = t % Q, q2 = (t / Q) % Q, i3 = t / (Q * Q);
+    double s = 0.0;
+    for (int q3 = 0; q3 < Q; ++q3) s += T.B1[q3 * P1 + i3] * Cq[q1 + Q * (q2 + Q * q3)];
+    Bq[t] = s;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < Q * P1 * P1; t += blockDim.x) {   // A[q1][i2][i3] = sum_q2
+    const int q1 = t % Q, i2 = (t / Q) % P1, i3 = t / (Q * P1);
+    double s = 0.0;
+    for (int q2 = 0; q2 < Q; ++q2) s += T.B1[q2 * P1 + i2] * Bq[q1 + Q * (q2 + Q * i3)];
+    A[t] = s;
+  }
+  __syncthreads();
+  // kinetic (Kronecker form) plus the last potential axis, scatter-added
+  const double ax = kin * hy * hz / (4.0 * hx), ay = kin * hx * hz / (4.0 * hy), az = kin * hx * hy / (4.0 * hz);
+  for (int l = threadIdx.x; l < nn; l += blockDim.x) {
+    const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
+    double y = 0.0;
+    for (int q1 = 0; q1 < Q; ++q1) y += T.B1[q1 * P1 + i1] * A[q1 + Q * (i2 + P1 * i3)];
+    double k = 0.0;
+    for (int j3 = 0; j3 < P1; ++j3)
+      for (int j2 = 0; j2 < P1; ++j2)
+        for (int j1 = 0; j1 < P1; ++j1) {
+          const double a1 = T.K1[i1 * P1 + j1] * T.M1[i2 * P1 + j2] * T.M1[i3 * P1 + j3];
+          const double a2 = T.M1[i1 * P1 + j1] * T.K1[i2 * P1 + j2] * T.M1[i3 * P1 + j3];
+          const double a3 = T.M1[i1 * P1 + j1] * T.M1[i2 * P1 + j2] * T.K1[i3 * P1 + j3];
+          k += (ax * a1 + ay * a2 + az * a3) * x[j1 + P1 * (j2 + P1 * j3)];
+        }
+    atomicAdd(&ya[(long long)cl[l] * ncols + c], y + k);
+  }
+}
+
+unsigned oblk(long long n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+// Builds the mesh, the constraints and the tables (host), then copies them to the device.
+static efe_status octree_build(Octree& o, const double* lo, const double* hi, int nc, int p, int n_quad,
+                               const int32_t* refine, int n_refine) {
+  if (nc < 1 || p < 1 || p + 1 > kMaxP1 || n_quad < p + 1 || n_quad > kOctMaxQ1 || n_refine < 0 ||
+      (n_refine > 0 && !refine)) {
+    o.err = "octree: need nc >= 1, degree in [1, 5], n_quad in [p + 1, 8]";
+    return EFE_ERR_ARG;
+  }
+  for (int a = 0; a < 3; ++a)
+    if (!(hi[a] > lo[a])) {
+      o.err = "octree: empty box";
+      return EFE_ERR_ARG;
+    }
+  std::vector<char> ref((size_t)nc * nc * nc, 0);
+  for (int r = 0; r < n_refine; ++r) {
+    const int i = refine[3 * r], j = refine[3 * r + 1], k = refine[3 * r + 2];
+    if (i < 0 || j < 0 || k < 0 || i >= nc || j >= nc || k >= nc) {
+      o.err = "octree: refined cell outside the coarse grid";
+      return EFE_ERR_ARG;
+    }
+    ref[i + (size_t)nc * (j + (size_t)nc * k)] = 1;
+  }
+  o.p = p;
+  o.P1 = p + 1;
+  o.NQ1 = n_quad;
+  o.nn = o.P1 * o.P1 * o.P1;
+  o.nq = n_quad * n_quad * n_quad;
+  const int P1 = o.P1, nn = o.nn;
+  double hc[3], hmin = 1e300;
+  for (int a = 0; a < 3; ++a) {
+    hc[a] = (hi[a] - lo[a]) / nc;
+    hmin = std::min(hmin, hc[a]);
+  }
+  // leaves: coarse cells in x-fastest order, a refined cell as its 8 children (bit a of the child: upper half on axis a)
+  struct Leaf { double x0[3], h[3]; bool coarse; };
+  std::vector<Leaf> leaves;
+  std::vector<long long> coarse_leaf((size_t)nc * nc * nc, -1);   // leaf of an unrefined coarse cell
+  for (int k = 0; k < nc; ++k)
+    for (int j = 0; j < nc; ++j)
+      for (int i = 0; i < nc; ++i) {
+        const int ijk[3] = {i, j, k};
+        Leaf L;
+        for (int a = 0; a < 3; ++a) L.x0[a] = lo[a] + ijk[a] * hc[a];
+        if (ref[i + (size_t)nc * (j + (size_t)nc * k)]) {
+          for (int ch = 0; ch < 8; ++ch) {
+            Leaf S;
+            for (int a = 0; a < 3; ++a) {
+              S.x0[a] = L.x0[a] + 0.5 * ((ch >> a) & 1) * hc[a];
+              S.h[a] = 0.5 * hc[a];
+            }
+            S.coarse = false;
+            leaves.push_back(S);
+          }
+        } else {
+          for (int a = 0; a < 3; ++a) L.h[a] = hc[a];
+          L.coarse = true;
+          coarse_leaf[i + (size_t)nc * (j + (size_t)nc * k)] = (long long)leaves.size();
+          leaves.push_back(L);
+        }
+      }
+  std::vector<double> xi(P1), wl(P1);
+  gauss_lobatto(p, xi.data(), wl.data());
+  // nodes merged by position (integer keys on a lattice much finer than any node spacing)
+  const double scale = 1.0 / (hmin * 1e-9);
+  std::map<std::array<long long, 3>, int> key_of;
+  std::vector<double> xyz;
+  std::vector<int> conn(leaves.size() * (size_t)nn);
+  std::vector<char> fine_node;
+  for (size_t li = 0; li < leaves.size(); ++li)
+    for (int l = 0; l < nn; ++l) {
+      const int loc[3] = {l % P1, (l / P1) % P1, l / (P1 * P1)};
+      double X[3];
+      std::array<long long, 3> key;
+      for (int a = 0; a < 3; ++a) {
+        X[a] = leaves[li].x0[a] + 0.5 * (xi[loc[a]] + 1.0) * leaves[li].h[a];
+        key[a] = std::llround(X[a] * scale);
+      }
+      auto it = key_of.find(key);
+      int id;
+      if (it == key_of.end()) {
+        id = (int)(xyz.size() / 3);
+        key_of.emplace(key, id);
+        xyz.insert(xyz.end(), X, X + 3);
+        fine_node.push_back(0);
+      } else {
+        id = it->second;
+      }
+      if (!leaves[li].coarse) fine_node[id] = 1;
+      conn[li * nn + l] = id;
+    }
+  const long long n_all = (long long)(xyz.size() / 3);
+  // hanging nodes: nodes of fine leaves on the closed box of a coarse leaf that are not its nodes
+  const double tol = 1e-9 * hmin;
+  std::vector<std::vector<std::pair<int, double>>> hang((size_t)n_all);
+  std::vector<char> is_hang((size_t)n_all, 0);
+  std::vector<double> L1(P1), dL1(P1);
+  for (long long nd = 0; nd < n_all; ++nd) {
+    if (!fine_node[nd]) continue;
+    const double* X = &xyz[3 * nd];
+    // the coarse cells whose closed box holds X
+    int lo_i[3], hi_i[3];
+    for (int a = 0; a < 3; ++a) {
+      lo_i[a] = std::max(0, (int)std::floor((X[a] - lo[a] - tol) / hc[a]));
+      hi_i[a] = std::min(nc - 1, (int)std::floor((X[a] - lo[a] + tol) / hc[a]));
+    }
+    for (int k = lo_i[2]; k <= hi_i[2] && !is_hang[nd]; ++k)
+      for (int j = lo_i[1]; j <= hi_i[1] && !is_hang[nd]; ++j)
+        for (int i = lo_i[0]; i <= hi_i[0] && !is_hang[nd]; ++i) {
+          const long long lc = coarse_leaf[i + (size_t)nc * (j + (size_t)nc * k)];
+          if (lc < 0) continue;   // refined cell
+          const size_t li = (size_t)lc;
+          const Leaf& C = leaves[li];
+          bool inside = true, own = false;
+          for (int a = 0; a < 3; ++a)
+            if (X[a] < C.x0[a] - tol || X[a] > C.x0[a] + C.h[a] + tol) inside = false;
+          for (int l = 0; l < nn && inside; ++l)
+            if (conn[li * nn + l] == nd) own = true;
+          if (!inside || own) continue;
+          std::vector<double> Lv[3];
+          for (int a = 0; a < 3; ++a) {
+            const double r = 2.0 * (X[a] - C.x0[a]) / C.h[a] - 1.0;
+            lagrange_tables(P1, xi.data(), 1, &r, L1.data(), dL1.data());
+            Lv[a] = L1;
+          }
+          for (int l = 0; l < nn; ++l) {
+            const double w = Lv[0][l % P1] * Lv[1][(l / P1) % P1] * Lv[2][l / (P1 * P1)];
+            if (std::fabs(w) > 1e-14) hang[nd].push_back({conn[li * nn + l], w});
+          }
+          is_hang[nd] = 1;
+        }
+  }
+  // free numbering and P in CSR over all nodes
+  std::vector<int> free_of((size_t)n_all, -1);
+  long long n_free = 0;
+  for (long long nd = 0; nd < n_all; ++nd)
+    if (!is_hang[nd]) free_of[nd] = (int)n_free++;
+  std::vector<long long>& rs = o.rs;
+  std::vector<int>& col = o.col;
+  std::vector<double>& val = o.val;
+  rs.assign((size_t)n_all + 1, 0);
+  col.clear();
+  val.clear();
+  for (long long nd = 0; nd < n_all; ++nd) {
+    if (is_hang[nd]) {
+      for (auto& mw : hang[nd]) {
+        if (is_hang[mw.first]) {
+          o.err = "octree: a master node is hanging (more than one level between neighbours)";
+          return EFE_ERR_ARG;
+        }
+        col.push_back(free_of[mw.first]);
+        val.push_back(mw.second);
+      }
+    } else {
+      col.push_back(free_of[nd]);
+      val.push_back(1.0);
+    }
+    rs[nd + 1] = (long long)col.size();
+  }
+  std::vector<unsigned char> bnd((size_t)n_free, 0);
+  o.free_xyz.assign((size_t)3 * n_free, 0.0);
+  for (long long nd = 0; nd < n_all; ++nd) {
+    if (is_hang[nd]) continue;
+    const long long f = free_of[nd];
+    for (int a = 0; a < 3; ++a) {
+      o.free_xyz[3 * f + a] = xyz[3 * nd + a];
+      if (std::fabs(xyz[3 * nd + a] - lo[a]) < tol || std::fabs(xyz[3 * nd + a] - hi[a]) < tol) bnd[f] = 1;
+    }
+  }
+  // tables
+  std::vector<double> xg(n_quad), wg(n_quad), B(n_quad * P1), D(n_quad * P1);
+  gauss_legendre(n_quad, xg.data(), wg.data());
+  lagrange_tables(P1, xi.data(), n_quad, xg.data(), B.data(), D.data());
+  o.tab.P1 = P1;
+  o.tab.NQ1 = n_quad;
+  for (int q = 0; q < n_quad; ++q) {
+    o.tab.wg[q] = wg[q];
+    for (int i = 0; i < P1; ++i) o.tab.B1[q * P1 + i] = B[q * P1 + i];
+  }
+  for (int i = 0; i < P1; ++i)
+    for (int j = 0; j < P1; ++j) {
+      double k = 0.0, m = 0.0;
+      for (int q = 0; q < n_quad; ++q) {
+        k += wg[q] * D[q * P1 + i] * D[q * P1 + j];
+        m += wg[q] * B[q * P1 + i] * B[q * P1 + j];
+      }
+      o.tab.K1[i * P1 + j] = k;
+      o.tab.M1[i * P1 + j] = m;
+    }
+  std::vector<double> geo(6 * leaves.size());
+  o.quad_xyz.assign(leaves.size() * (size_t)o.nq * 3, 0.0);
+  for (size_t li = 0; li < leaves.size(); ++li) {
+    for (int a = 0; a < 3; ++a) {
+      geo[6 * li + a] = leaves[li].x0[a];
+      geo[6 * li + 3 + a] = leaves[li].h[a];
+    }
+    for (int q = 0; q < o.nq; ++q) {
+      const int qi[3] = {q % n_quad, (q / n_quad) % n_quad, q / (n_quad * n_quad)};
+      for (int a = 0; a < 3; ++a)
+        o.quad_xyz[(li * o.nq + q) * 3 + a] = leaves[li].x0[a] + 0.5 * (xg[qi[a]] + 1.0) * leaves[li].h[a];
+    }
+  }
+  o.all_xyz = xyz;
+  o.n_leaves = (long long)leaves.size();
+  o.n_all = n_all;
+  o.n_free = n_free;
+  o.n_hang = n_all - n_free;
+  auto up = [](auto*& dst, const auto& v) -> cudaError_t {
+    using T = typename std::remove_reference<decltype(v)>::type::value_type;
+    cudaError_t e = cudaMalloc((void**)&dst, sizeof(T) * std::max<size_t>(v.size(), 1));
+    if (e != cudaSuccess) return e;
+    return v.empty() ? cudaSuccess : cudaMemcpy(dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+  };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = up(o.d_geo, geo);
+  if (e == cudaSuccess) e = up(o.d_conn, conn);
+  if (e == cudaSuccess) e = up(o.d_rs, rs);
+  if (e == cudaSuccess) e = up(o.d_col, col);
+  if (e == cudaSuccess) e = up(o.d_val, val);
+  if (e == cudaSuccess) e = up(o.d_bnd, bnd);
+  if (e != cudaSuccess) {
+    o.err = std::string("octree set-up: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? EFE_ERR_NOMEM : EFE_ERR_CUDA;
+  }
+  return EFE_OK;
+}
+
+}  // namespace efe
+
+struct efe_octree {
+  efe::Octree o;
+};
+
+static thread_local std::string g_oct_err;
+
+extern "C" {
+
+efe_status efe_octree_setup(const double* lo_host, const double* hi_host, int32_t nc, int32_t degree, int32_t n_quad,
+                            const int32_t* refine_host, int32_t n_refine, efe_octree** out) {
+  if (!out || !lo_host || !hi_host) return EFE_ERR_ARG;
+  *out = nullptr;
+  efe_octree* h = new efe_octree();
+  efe_status st = efe::octree_build(h->o, lo_host, hi_host, nc, degree, n_quad, refine_host, n_refine);
+  if (st != EFE_OK) {
+    g_oct_err = h->o.err;
+    delete h;
+    return st;
+  }
+  *out = h;
+  return EFE_OK;
+}
+
+efe_status efe_octree_destroy(efe_octree* oct) {
+  delete oct;
+  return EFE_OK;
+}
+
+const char* efe_octree_last_error(const efe_octree* oct) { return oct ? oct->o.err.c_str() : g_oct_err.c_str(); }
+
+efe_status efe_octree_sizes(const efe_octree* oct, int64_t* n_free, int64_t* n_all, int64_t* n_leaves, int64_t* n_q,
+                            int64_t* n_hanging) {
+  if (!oct) return EFE_ERR_ARG;
+  const efe::Octree& o = oct->o;
+  if (n_free) *n_free = o.n_free;
+  if (n_all) *n_all = o.n_all;
+  if (n_leaves) *n_leaves = o.n_leaves;
+  if (n_q) *n_q = o.nq;
+  if (n_hanging) *n_hanging = o.n_hang;
+  return EFE_OK;
+}
+
+efe_status efe_octree_coords(const efe_octree* oct, double* free_xyz_host, double* quad_xyz_host,
+                             uint8_t* boundary_host) {
+  if (!oct) return EFE_ERR_ARG;
+  const efe::Octree& o = oct->o;
+  if (free_xyz_host) std::copy(o.free_xyz.begin(), o.free_xyz.end(), free_xyz_host);
+  if (quad_xyz_host) std::copy(o.quad_xyz.begin(), o.quad_xyz.end(), quad_xyz_host);
+  if (boundary_host && cudaMemcpy(boundary_host, o.d_bnd, (size_t)o.n_free, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return EFE_ERR_CUDA;
+  return EFE_OK;
+}
+
+efe_status efe_octree_apply(efe_octree* oct, const double* vq_dev, double kin, const double* X_dev, double* Y_dev,
+                            int64_t n_cols, int32_t mask_boundary, void* stream) {
+  if (!oct || !vq_dev || !X_dev || !Y_dev || n_cols < 1 || n_cols > 65535) return EFE_ERR_ARG;
+  efe::Octree& o = oct->o;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (o.ws_cols < n_cols) {
+    if (o.d_xall) cudaFree(o.d_xall);
+    if (o.d_yall) cudaFree(o.d_yall);
+    o.d_xall = o.d_yall = nullptr;
+    o.ws_cols = 0;
+    if (cudaMalloc(&o.d_xall, sizeof(double) * o.n_all * n_cols) != cudaSuccess ||
+        cudaMalloc(&o.d_yall, sizeof(double) * o.n_all * n_cols) != cudaSuccess) {
+      o.err = "octree apply: out of device memory";
+      return EFE_ERR_NOMEM;
+    }
+    o.ws_cols = n_cols;
+  }
+  const int nc = (int)n_cols;
+  const long long N = o.n_all * n_cols;
+  efe::k_oct_expand<<<efe::oblk(N), 256, 0, s>>>(o.d_rs, o.d_col, o.d_val, o.d_bnd, X_dev, o.n_all, nc,
+                                                 mask_boundary, o.d_xall);
+  efe::note_launch();
+  cudaMemsetAsync(o.d_yall, 0, sizeof(double) * N, s);
+  dim3 grid((unsigned)o.n_leaves, (unsigned)nc);
+  efe::k_oct_apply<<<grid, efe::kOctThreads, 0, s>>>(o.tab, o.d_geo, o.d_conn, vq_dev, kin, o.d_xall, nc, o.d_yall);
+  efe::note_launch();
+  cudaMemsetAsync(Y_dev, 0, sizeof(double) * o.n_free * n_cols, s);
+  efe::k_oct_reduce<<<efe::oblk(N), 256, 0, s>>>(o.d_rs, o.d_col, o.d_val, o.d_bnd, o.d_yall, o.n_all, nc,
+                                                 mask_boundary, Y_dev);
+  efe::note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    o.err = std::string("octree apply: ") + cudaGetErrorString(e);
+    return EFE_ERR_CUDA;
+  }
+  return EFE_OK;
+}
+
+}  // extern "C"

@@ -13,7 +13,7 @@ if ROOT not in sys.path:
 # GPU test modules of components that have not yet run on a device: they run
 # after the rest of the suite, so that under -x a failure there cannot hide the
 # results of the established tests.
-RUN_LAST = ("test_gpu_electrostatic.py",)
+RUN_LAST = ("test_gpu_electrostatic.py", "test_gpu_octree.py")
 
 
 def pytest_collection_modifyitems(config, items):

@@ -1,0 +1,108 @@
+"""The constrained Hamiltonian apply on the locally refined mesh
+(efe_octree_apply: gather through the hanging-node constraints P, per-leaf
+kinetic and potential operator, scatter through P^T) against the oracle's
+P^T H P (oracle.octree.OctreeMesh.hamiltonian), and its properties on a larger
+mesh."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+# (lo, hi, nc, degree, n_quad, refined cells): degrees 2, 3, 5; one refined cell,
+# neighbouring refined cells, a refined 2^3 block; non-cubic boxes
+MESHES = {
+    "p3_three": ([0, 0, 0], [3, 3, 3], 3, 3, 5, [(1, 1, 1), (2, 1, 1), (0, 0, 0)]),
+    "p3_box": ([0, 0, 0], [3, 2, 2], 3, 3, 5, [(1, 0, 0), (2, 1, 1)]),
+    "p2_block": ([-1, 0, 0.5], [2, 2, 2.5], 4, 2, 4, [(i, j, k) for i in (1, 2) for j in (1, 2) for k in (1, 2)]),
+    "p5_corner": ([0, 0, 0], [2, 2, 2], 2, 5, 7, [(0, 0, 0)]),
+}
+
+
+def _key(x):
+    return [tuple(r) for r in np.round(np.asarray(x) * 1e6).astype(np.int64)]
+
+
+@pytest.mark.parametrize("mask", [False, True])
+@pytest.mark.parametrize("name", list(MESHES))
+def test_octree_apply_matches_oracle(name, mask):
+    from oracle.octree import OctreeMesh
+    from paper_2210_14421_gb300 import Octree
+    lo, hi, nc, p, nq, ref = MESHES[name]
+    m = OctreeMesh(lo, hi, nc, p, ref, n_quad=nq)
+    o = Octree(lo, hi, nc, p, nq, ref)
+    assert o.n_all == m.n_all and o.n_free == len(m.free) and o.n_hanging == len(m.hanging)
+    fx, qx, bnd = o.coords()
+    assert np.allclose(qx, m.quad_points(), rtol=0, atol=1e-13)
+    pos = {k: j for j, k in enumerate(_key(m.nodes[m.free]))}
+    perm = np.array([pos[k] for k in _key(fx)])          # GPU free node -> oracle free index
+    assert np.array_equal(bnd, m.boundary_free[perm])
+    rng = np.random.default_rng(7)
+    vq = np.sin(qx[:, :, 0]) + qx[:, :, 1] ** 2 - 0.3 * qx[:, :, 2]
+    X = rng.standard_normal((o.n_free, 3))
+    H = m.hamiltonian(vq, kin=0.8)
+    Xo = np.zeros((len(m.free), 3))
+    Xo[perm] = X
+    if mask:
+        I = ~m.boundary_free
+        ref_y = np.zeros_like(Xo)
+        ref_y[I] = H[I][:, I] @ Xo[I]
+        scale = abs(H[I][:, I]) @ np.abs(Xo[I])
+    else:
+        ref_y = H @ Xo
+        scale = abs(H) @ np.abs(Xo)
+    Y = torch.zeros((o.n_free, 3), dtype=torch.float64, device="cuda")
+    o.apply(torch.from_numpy(np.ascontiguousarray(vq)).cuda(), torch.from_numpy(X).cuda(), Y, kin=0.8,
+            mask_boundary=mask)
+    got = Y.cpu().numpy()
+    ref_g = ref_y[perm]
+    assert np.max(np.abs(got - ref_g) - 1e-12 * scale[perm] - 1e-300) <= 0.0, name
+    o.close()
+
+
+def test_octree_rejects_bad_meshes():
+    from paper_2210_14421_gb300 import EfeError, Octree
+    with pytest.raises(EfeError):
+        Octree([0, 0, 0], [1, 1, 1], 2, 3, 3, [])          # n_quad < p + 1
+    with pytest.raises(EfeError):
+        Octree([0, 0, 0], [1, 1, 1], 2, 3, 5, [(2, 0, 0)])  # refined cell outside the grid
+    with pytest.raises(EfeError):
+        Octree([0, 0, 0], [0, 1, 1], 2, 3, 5, [])          # empty box
+
+
+def test_octree_larger_mesh_properties():
+    """16^3 coarse cells of degree 4 with a refined 4^3 block (the local refinement
+    around a nucleus): the operator is symmetric, the kinetic part annihilates
+    constants, and <1, V 1> = c |box| for a constant potential (the constrained
+    space holds the constants and the leaf rules integrate them exactly)."""
+    from paper_2210_14421_gb300 import Octree
+    ref = [(i, j, k) for i in range(6, 10) for j in range(6, 10) for k in range(6, 10)]
+    o = Octree([-8, -8, -8], [8, 8, 8], 16, 4, 6, ref)
+    assert o.n_hanging > 0
+    _, qx, _ = o.coords()
+    rng = np.random.default_rng(3)
+    vq = torch.from_numpy(-1.0 / np.sqrt(1.0 + np.sum(qx ** 2, axis=2))).cuda()
+    X = torch.from_numpy(rng.standard_normal((o.n_free, 2))).cuda()
+    Y = torch.zeros_like(X)
+    o.apply(vq, X, Y, kin=1.0)
+    lhs = (X[:, 0] * Y[:, 1]).sum().item()
+    rhs = (Y[:, 0] * X[:, 1]).sum().item()
+    assert abs(lhs - rhs) <= 1e-11 * (torch.linalg.norm(X) * torch.linalg.norm(Y)).item()
+    one = torch.ones((o.n_free, 1), dtype=torch.float64, device="cuda")
+    K1 = torch.zeros_like(one)
+    o.apply(torch.zeros_like(vq), one, K1, kin=1.0)
+    assert torch.max(torch.abs(K1)).item() < 1e-10
+    V1 = torch.zeros_like(one)
+    o.apply(torch.full_like(vq, 0.7), one, V1, kin=0.0)
+    assert abs(V1.sum().item() - 0.7 * 16.0 ** 3) < 1e-9 * 16.0 ** 3
+    o.close()
