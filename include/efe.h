@@ -409,6 +409,15 @@ efe_status efe_octree_setup(const double* lo_host, const double* hi_host, int32_
                             const int32_t* refine_host, int32_t n_refine, efe_octree** out);
 efe_status efe_octree_destroy(efe_octree* oct);
 const char* efe_octree_last_error(const efe_octree* oct);
+/* The same mesh described on the host only (no device work, no handle): the
+ * constraint matrix P in CSR over all nodes (row_start [n_all + 1], col
+ * [nnz] free-node indices, val [nnz] weights; a free node's row is its own
+ * index with weight 1), node coordinates all_xyz [n_all][3] and free_xyz
+ * [n_free][3].  Call with NULL arrays to read n_all, n_free and nnz first. */
+efe_status efe_octree_constraints(const double* lo_host, const double* hi_host, int32_t nc, int32_t degree,
+                                  int32_t n_quad, const int32_t* refine_host, int32_t n_refine, int64_t* n_all,
+                                  int64_t* n_free, int64_t* nnz, int64_t* row_start, int32_t* col, double* val,
+                                  double* all_xyz, double* free_xyz);
 /* Counts: free (unconstrained) nodes, all nodes, leaves, quadrature points per
  * leaf, hanging nodes (any pointer may be NULL). */
 efe_status efe_octree_sizes(const efe_octree* oct, int64_t* n_free, int64_t* n_all, int64_t* n_leaves, int64_t* n_q,

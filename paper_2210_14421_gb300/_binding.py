@@ -26,7 +26,7 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_apply_H_noalloc", "efe_tuning", "efe_adjoint_dipole",
             "efe_absorption_spectrum", "efe_power_spectrum", "efe_nuclear_enriched",
             "efe_hartree_enriched", "efe_octree_setup", "efe_octree_destroy", "efe_octree_last_error",
-            "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply"]
+            "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply", "efe_octree_constraints"]
 
 
 class MeshDesc(C.Structure):
@@ -114,6 +114,9 @@ def lib(path: str = LIB_PATH):
     L.efe_octree_sizes.argtypes = [vp] + [C.POINTER(i64)] * 5
     L.efe_octree_coords.argtypes = [vp, pdbl, pdbl, C.POINTER(C.c_uint8)]
     L.efe_octree_apply.argtypes = [vp, vp, dbl, vp, vp, i64, i32, vp]
+    L.efe_octree_constraints.argtypes = [pdbl, pdbl, i32, i32, i32, C.POINTER(i32), i32, C.POINTER(i64),
+                                         C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), pdbl, pdbl,
+                                         pdbl]
     for name in EXPORTED:
         if name not in ("efe_last_error", "efe_octree_last_error"):
             getattr(L, name).restype = C.c_int
@@ -395,7 +398,11 @@ class Octree:
 
     def apply(self, vq, X, Y, kin: float = 1.0, mask_boundary: bool = False):
         """Y = P^T (kin K/2 + V) P X; vq device [n_leaves, n_q], X, Y device [n_free, n_cols] float64."""
-        assert X.is_contiguous() and Y.is_contiguous() and vq.is_contiguous()
+        import torch
+        for t in (vq, X, Y):
+            assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+        assert vq.numel() == self.n_leaves * self.n_q
+        assert X.dim() == 2 and X.shape[0] == self.n_free and tuple(Y.shape) == tuple(X.shape)
         st = lib().efe_octree_apply(self.h, _ptr(vq), float(kin), _ptr(X), _ptr(Y), int(X.shape[1]),
                                     int(bool(mask_boundary)), _stream())
         if st != EFE_OK:
@@ -412,3 +419,29 @@ class Octree:
             self.close()
         except Exception:
             pass
+
+
+def octree_constraints(lo, hi, nc: int, degree: int, n_quad: int, refine=()):
+    """Host-only description of a locally refined mesh: (row_start, col, val) of the
+    constraint matrix P over all nodes, all-node and free-node coordinates."""
+    L = lib()
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    ref = np.ascontiguousarray(np.asarray(list(refine), dtype=np.int32).reshape(-1, 3))
+    rp = ref.ctypes.data_as(C.POINTER(C.c_int32))
+    na, nf, nz = C.c_int64(), C.c_int64(), C.c_int64()
+    args = (_dptr(lo), _dptr(hi), int(nc), int(degree), int(n_quad), rp, int(len(ref)))
+    st = L.efe_octree_constraints(*args, C.byref(na), C.byref(nf), C.byref(nz), None, None, None, None, None)
+    if st != EFE_OK:
+        raise EfeError(st, L.efe_octree_last_error(None).decode())
+    rs = np.zeros(na.value + 1, dtype=np.int64)
+    col = np.zeros(nz.value, dtype=np.int32)
+    val = np.zeros(nz.value)
+    axyz = np.zeros((na.value, 3))
+    fxyz = np.zeros((nf.value, 3))
+    st = L.efe_octree_constraints(*args, C.byref(na), C.byref(nf), C.byref(nz),
+                                  rs.ctypes.data_as(C.POINTER(C.c_int64)), col.ctypes.data_as(C.POINTER(C.c_int32)),
+                                  _dptr(val), _dptr(axyz), _dptr(fxyz))
+    if st != EFE_OK:
+        raise EfeError(st, L.efe_octree_last_error(None).decode())
+    return rs, col, val, axyz, fxyz

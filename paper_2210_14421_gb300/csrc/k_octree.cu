@@ -44,6 +44,9 @@ struct Octree {
   OctTables tab{};
   std::vector<double> free_xyz, quad_xyz;   // host copies for efe_octree_coords
   std::vector<double> all_xyz;              // coordinates of all nodes
+  std::vector<double> geo;                  // host copies of the device arrays
+  std::vector<int> conn;
+  std::vector<unsigned char> bnd;
   std::vector<long long> rs;                // host copy of P (CSR over all nodes)
   std::vector<int> col;
   std::vector<double> val;
@@ -177,8 +180,9 @@ unsigned oblk(long long n) { return (unsigned)((n + 255) / 256); }
 }  // namespace
 
 // Builds the mesh, the constraints and the tables (host), then copies them to the device.
-static efe_status octree_build(Octree& o, const double* lo, const double* hi, int nc, int p, int n_quad,
-                               const int32_t* refine, int n_refine) {
+// Host side of the set-up: leaves, nodes, constraints, tables (no device work).
+static efe_status octree_host(Octree& o, const double* lo, const double* hi, int nc, int p, int n_quad,
+                              const int32_t* refine, int n_refine) {
   if (nc < 1 || p < 1 || p + 1 > kMaxP1 || n_quad < p + 1 || n_quad > kOctMaxQ1 || n_refine < 0 ||
       (n_refine > 0 && !refine)) {
     o.err = "octree: need nc >= 1, degree in [1, 5], n_quad in [p + 1, 8]";
@@ -382,6 +386,23 @@ static efe_status octree_build(Octree& o, const double* lo, const double* hi, in
   o.n_all = n_all;
   o.n_free = n_free;
   o.n_hang = n_all - n_free;
+  o.geo = std::move(geo);
+  o.conn = std::move(conn);
+  o.bnd = std::move(bnd);
+  return EFE_OK;
+}
+
+// Host set-up, then the device copies.
+static efe_status octree_build(Octree& o, const double* lo, const double* hi, int nc, int p, int n_quad,
+                               const int32_t* refine, int n_refine) {
+  efe_status st = octree_host(o, lo, hi, nc, p, n_quad, refine, n_refine);
+  if (st != EFE_OK) return st;
+  const std::vector<double>& geo = o.geo;
+  const std::vector<int>& conn = o.conn;
+  const std::vector<long long>& rs = o.rs;
+  const std::vector<int>& col = o.col;
+  const std::vector<double>& val = o.val;
+  const std::vector<unsigned char>& bnd = o.bnd;
   auto up = [](auto*& dst, const auto& v) -> cudaError_t {
     using T = typename std::remove_reference<decltype(v)>::type::value_type;
     cudaError_t e = cudaMalloc((void**)&dst, sizeof(T) * std::max<size_t>(v.size(), 1));
@@ -424,6 +445,28 @@ efe_status efe_octree_setup(const double* lo_host, const double* hi_host, int32_
     return st;
   }
   *out = h;
+  return EFE_OK;
+}
+
+efe_status efe_octree_constraints(const double* lo_host, const double* hi_host, int32_t nc, int32_t degree,
+                                  int32_t n_quad, const int32_t* refine_host, int32_t n_refine, int64_t* n_all,
+                                  int64_t* n_free, int64_t* nnz, int64_t* row_start, int32_t* col, double* val,
+                                  double* all_xyz, double* free_xyz) {
+  if (!lo_host || !hi_host) return EFE_ERR_ARG;
+  efe::Octree o;
+  efe_status st = efe::octree_host(o, lo_host, hi_host, nc, degree, n_quad, refine_host, n_refine);
+  if (st != EFE_OK) {
+    g_oct_err = o.err;
+    return st;
+  }
+  if (n_all) *n_all = o.n_all;
+  if (n_free) *n_free = o.n_free;
+  if (nnz) *nnz = (int64_t)o.col.size();
+  if (row_start) std::copy(o.rs.begin(), o.rs.end(), row_start);
+  if (col) std::copy(o.col.begin(), o.col.end(), col);
+  if (val) std::copy(o.val.begin(), o.val.end(), val);
+  if (all_xyz) std::copy(o.all_xyz.begin(), o.all_xyz.end(), all_xyz);
+  if (free_xyz) std::copy(o.free_xyz.begin(), o.free_xyz.end(), free_xyz);
   return EFE_OK;
 }
 
