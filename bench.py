@@ -60,6 +60,9 @@ def parse_args(argv=None):
     ap.add_argument("--adj-steps", type=int, default=6)
     ap.add_argument("--adj-cells", type=int, default=27)
     ap.add_argument("--cells", type=int, default=31, help="cells per axis (31 = the Na8-like workload)")
+    ap.add_argument("--next-rows", action="store_true",
+                    help="child mode: time the electrostatic enrichment and locally refined mesh paths, print JSON")
+    ap.add_argument("--no-next-rows", action="store_true", help="skip the child run of --next-rows")
     ap.add_argument("--k-max", type=int, default=64,
                     help="Lanczos cap; the Na8-like spectrum (-257..+2500 Ha) at dt = 0.05 needs k = 57 (FP64, "
                          "pair) to 58 (float32) for eps_k <= 1e-7. Below that the exponential is unconverged and "
@@ -354,6 +357,10 @@ def run_efe(args):
     import numpy as np
     import torch
 
+    next_rows = None
+    if int(os.environ.get("WORLD_SIZE", "1")) == 1 and not args.no_next_rows:
+        next_rows = next_rows_child(args)   # before this process creates its CUDA context
+
     import __graft_entry__ as g
     from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED, EFE_PAIR, EFE_TC, Context, fields_array
 
@@ -608,6 +615,8 @@ def run_efe(args):
     if rank == 0 and not args.no_cpu_baseline:
         k_hint = max([i["k_corr"] for i in infos] or [wl.k_max])
         line["cpu_baseline"] = cpu_baseline(workload(args.cells, 0), k_hint)
+    if next_rows is not None:
+        line["next_rows"] = next_rows
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -615,6 +624,105 @@ def run_efe(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def run_next_rows(args):
+    """Set-up and per-solve cost of the electrostatic enrichment on the Na8-like
+    workload (nuclear potential with the uniform and the adaptive cell rule,
+    enriched Hartree solve against the classical one) and the constrained
+    Hamiltonian apply on a locally refined mesh.  One JSON object on stdout."""
+    import numpy as np
+    import torch
+    from scipy.special import erf
+    import __graft_entry__ as g
+    g.build()
+    from paper_2210_14421_gb300 import Context, Octree
+    torch.cuda.set_device(0)
+    out = {}
+    wl = workload(args.cells, 0)
+    ctx = Context(wl, cg_tol=1e-10, cg_max_it=20000)
+    _, quad = ctx.coords()
+    x = quad.cpu().numpy().reshape(-1, 3)
+    sigma = 0.25
+    exact = np.zeros(len(x))
+    for z, R in zip(wl.Z, wl.R):
+        r = np.linalg.norm(x - R[None, :], axis=1)
+        exact -= z * erf(r / (np.sqrt(2.0) * sigma)) / r
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    (vN, phiE), t_u = timed(lambda: ctx.nuclear_enriched(sigma, 4.0, 2.0, sub=2))
+    err_u = float(np.max(np.abs(vN.cpu().numpy().ravel() - exact)) / np.max(np.abs(exact)))
+    (vA, phiA), t_a = timed(lambda: ctx.nuclear_enriched(sigma, 4.0, 2.0, n_quad=6, adapt_tol=1e-6, adapt_depth=3))
+    err_a = float(np.max(np.abs(vA.cpu().numpy().ravel() - exact)) / np.max(np.abs(exact)))
+    out["nuclear_enrichment"] = {
+        "sigma": sigma, "r0": 4.0, "s": 2.0,
+        "uniform_2x2x2": {"setup_s": round(t_u, 3), "max_rel_err_vs_closed_form": err_u,
+                          "phiE_range": [float(phiE.min()), float(phiE.max())]},
+        "adaptive_tol1e-6_depth3": {"setup_s": round(t_a, 3), "max_rel_err_vs_closed_form": err_a,
+                                    "phiE_range": [float(phiA.min()), float(phiA.max())]}}
+    rho = np.zeros(len(x))
+    for R in wl.R:
+        rho += 0.5 * np.exp(-np.sum((x - R[None, :]) ** 2, axis=1))
+    rho_t = torch.from_numpy(rho.reshape(1, ctx.n_cells, ctx.n_q)).cuda()
+    vH = torch.empty_like(rho_t)
+
+    def solves(k=5):
+        ctx.hartree(rho_t, vH)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            ctx.hartree(rho_t, vH)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / k
+
+    t_cls = solves()
+    _, t_inst = timed(lambda: ctx.hartree_enriched(4.0, 2.0, sub=2))
+    t_enr = solves()
+    out["hartree_enrichment"] = {"install_s": round(t_inst, 3), "classical_solve_ms": round(1e3 * t_cls, 2),
+                                 "enriched_solve_ms": round(1e3 * t_enr, 2), "r0": 4.0, "s": 2.0}
+    ctx.close()
+    torch.cuda.empty_cache()
+    ref = [(i, j, k) for i in range(9, 15) for j in range(9, 15) for k in range(9, 15)]
+    o, t_oct = timed(lambda: Octree([-12, -12, -12], [12, 12, 12], 24, 4, 6, ref))
+    _, qx, _ = o.coords()
+    vq = torch.from_numpy(-1.0 / np.sqrt(1.0 + np.sum(qx ** 2, axis=2))).cuda()
+    X = torch.randn((o.n_free, 88), dtype=torch.float64, device="cuda")
+    Y = torch.zeros_like(X)
+    o.apply(vq, X, Y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        o.apply(vq, X, Y)
+    e1.record()
+    torch.cuda.synchronize()
+    out["octree_apply"] = {"mesh": "24^3 coarse cells of degree 4 on a 24-bohr cube, central 6^3 refined",
+                           "n_free": o.n_free, "n_hanging": o.n_hanging, "n_leaves": o.n_leaves, "cols": 88,
+                           "setup_s": round(t_oct, 3), "ms_per_apply": round(e0.elapsed_time(e1) / 5, 3)}
+    o.close()
+    print(json.dumps(out))
+    return 0
+
+
+def next_rows_child(args):
+    """Runs --next-rows in a child process (its own CUDA context, a time limit), so
+    that the headline measurement never depends on it."""
+    import subprocess
+    cmd = [sys.executable, os.path.abspath(__file__), "--next-rows", "--cells", str(args.cells)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=300)
+    except subprocess.TimeoutExpired:
+        return {"error": "timed out after 300 s"}
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    if r.returncode != 0 or not lines:
+        tail = (r.stderr or r.stdout).strip().splitlines()[-3:]
+        return {"error": "exit %d: %s" % (r.returncode, " | ".join(tail))}
+    return json.loads(lines[-1])
 
 
 def run_adjoint(args):
@@ -691,6 +799,8 @@ def main():
         return run_reference(args)
     if args.adjoint:
         return run_adjoint(args)
+    if args.next_rows:
+        return run_next_rows(args)
     return run_efe(args)
 
 
