@@ -327,8 +327,9 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
  * device memory per call and synchronises `stream`.  Returns EFE_WARN_KRYLOV_CAP
  * (J and grad written) if any exponential stopped at k_max.  Errors: EFE_ERR_ARG
  * (bad sizes, window outside [1, n_steps], n_quad_s outside [1, 64], batch != 1,
- * another functional or step scheme, unsupported field, the enriched Hartree
- * solve installed), EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+ * another functional or step scheme, unsupported field), EFE_ERR_NOMEM,
+ * EFE_ERR_CUDA.  With the enriched Hartree solve installed (efe_hartree_enriched)
+ * the Hartree map and its transpose are the enriched ones. */
 efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_steps, double dt,
                               const efe_field* field_host, const double* direction_host, int32_t window_first,
                               int32_t window_last, int32_t checkpoint_every, int32_t n_quad_s, double* J_host,
@@ -386,8 +387,8 @@ efe_status efe_nuclear_enriched(efe_ctx* ctx, double sigma, double r0, double s,
  * of sub^3 sub-cells with n_quad^3 points each (n_quad 0: p + 2).  v_H at
  * the quadrature points includes the enrichment functions.  Keeps 3 n_atoms
  * vectors of n_nodes doubles on the device; synchronises `stream`; the
- * propagation state is invalidated.  efe_adjoint_dipole is not available
- * once installed.  Errors: EFE_ERR_ARG (the context's Hartree method is not
+ * propagation state is invalidated.  efe_adjoint_dipole then transposes the
+ * enriched map (rho -> v_H) in its reverse sweep.  Errors: EFE_ERR_ARG (the context's Hartree method is not
  * EFE_HARTREE_FDM; s <= 0, r0 <= s, sub outside [1, 8], n_quad outside
  * [p + 1, 8] and not 0, a support sphere reaching the domain boundary),
  * EFE_ERR_NOT_SPD, EFE_ERR_NOMEM, EFE_ERR_CUDA. */

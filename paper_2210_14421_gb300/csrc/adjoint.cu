@@ -424,10 +424,16 @@ class Sweep {
     double* Ap = c_.d_cg + 2 * c_.n_h;
     k_div_w<<<nb256(nqt_), 256, 0, s_>>>(g, c_.d_wJ, tq2_, 1.0, nqt_);
     note_launch();
-    ck(c_, cudaMemsetAsync(d, 0, sizeof(double) * c_.n_h, s_), "memset");
-    ck(c_, launch_load_vector(c_, tq2_, d, 1, s_), "load vector");
-    ck(c_, fdm_solve(c_, d, Ap, phi, 1, s_, true), "Hartree transpose");
-    ck(c_, launch_interp(c_, phi, tq2_, 1, s_), "interpolation");
+    if (c_.hen.on) {   // enriched Hartree solve: its own transpose
+      double* w = c_.d_cg;
+      ck(c_, hartree_enriched_vt(c_, tq2_, tq2_, w, w + c_.n_h, w + 2 * c_.n_h, w + 3 * c_.n_h, w + 4 * c_.n_h,
+                                 w + 5 * c_.n_h, s_), "enriched Hartree transpose");
+    } else {
+      ck(c_, cudaMemsetAsync(d, 0, sizeof(double) * c_.n_h, s_), "memset");
+      ck(c_, launch_load_vector(c_, tq2_, d, 1, s_), "load vector");
+      ck(c_, fdm_solve(c_, d, Ap, phi, 1, s_, true), "Hartree transpose");
+      ck(c_, launch_interp(c_, phi, tq2_, 1, s_), "interpolation");
+    }
     k_vt_finish<<<nb256(nqt_), 256, 0, s_>>>(tq2_, c_.d_wJ, rho, g, out, nqt_);
     note_launch();
   }

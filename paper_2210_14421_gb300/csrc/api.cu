@@ -774,10 +774,6 @@ efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_st
     c.err = "efe_adjoint_dipole: invalid argument";
     return EFE_ERR_ARG;
   }
-  if (c.hen.on) {
-    c.err = "efe_adjoint_dipole: the transposed Hartree map of the enriched solve is not implemented";
-    return EFE_ERR_ARG;
-  }
   if (c.batch != 1) {
     c.err = "efe_adjoint_dipole needs a context with batch = 1";
     return EFE_ERR_ARG;

@@ -314,6 +314,10 @@ efe_status hartree_enrich_install(Ctx& c, double r0, double s, int sub, int n_qu
 // into c.d_phi, v_H at the quadrature points into vH; Ap, Lz, u: [n_h][batch] scratch
 cudaError_t hartree_enriched_solve(Ctx& c, const double* rho, double* vH, const double* d, double* Ap, double* Lz,
                                    double* u, cudaStream_t s);
+// its transpose for the adjoint (batch 1): out = I (Z h - W^T t) + sum_J t_J N^A_J for gw = g / w
+// (out may alias gw; the caller multiplies by w); s1..s6 [n_h] scratch
+cudaError_t hartree_enriched_vt(Ctx& c, const double* gw, double* out, double* s1, double* s2, double* s3, double* s4,
+                                double* s5, double* s6, cudaStream_t s);
 // context workspaces for C complex columns of leading dimension ld; the operator of v (api.cu)
 efe_status ensure_ws(Ctx& c, long long C, long long ld);
 efe_status build_op(Ctx& c, const double* v, int batch, double kin, cudaStream_t s);

@@ -487,6 +487,61 @@ __global__ void k_hen_add(const double* __restrict__ xq, long long npts, int nb,
   vH[idx] += v;
 }
 
+// Transposed enriched Hartree map (the adjoint's v_H'(rho)^T): helpers.
+// out[J] = (X_J + C_J) . h   (one block per atom)
+__global__ void __launch_bounds__(kNucThreads)
+k_hen_xc_dot(const double* __restrict__ X, const double* __restrict__ C, const double* __restrict__ h, long long n_h,
+             double* __restrict__ out) {
+  __shared__ double red[kNucThreads];
+  const int J = blockIdx.x;
+  const double* xj = X + (long long)J * n_h;
+  const double* cj = C + (long long)J * n_h;
+  double acc = 0.0;
+  for (long long g = threadIdx.x; g < n_h; g += blockDim.x) acc += (xj[g] + cj[g]) * h[g];
+  const double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) out[J] = tot;
+}
+
+// t = Sinv (sN - sX)
+__global__ void k_hen_tcoef(const double* __restrict__ Sinv, const double* __restrict__ sN,
+                            const double* __restrict__ sX, int nA, double* __restrict__ t) {
+  for (int J = threadIdx.x; J < nA; J += blockDim.x) {
+    double v = 0.0;
+    for (int K = 0; K < nA; ++K) v += Sinv[J * nA + K] * (sN[K] - sX[K]);
+    t[J] = v;
+  }
+}
+
+// ct = sum_J t_J C_J;  r0 = sum_J t_J G_J
+__global__ void k_hen_comb_t(const double* __restrict__ C, const double* __restrict__ G, const double* __restrict__ t,
+                             long long n_h, int nA, double* __restrict__ ct, double* __restrict__ gt) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= n_h) return;
+  double a = 0.0, b = 0.0;
+  for (int J = 0; J < nA; ++J) {
+    a += t[J] * C[(long long)J * n_h + g];
+    b += t[J] * G[(long long)J * n_h + g];
+  }
+  ct[g] = a;
+  gt[g] = b;
+}
+
+// r = k gt - Kc at interior nodes, 0 on the boundary (in place on gt)
+__global__ void k_hen_rvec(double* __restrict__ gt, const double* __restrict__ Kc, const double* __restrict__ Dsc,
+                           long long n_h, double k) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= n_h) return;
+  gt[g] = Dsc[g] != 0.0 ? k * gt[g] - Kc[g] : 0.0;
+}
+
+// y = Zh - ct - Zr
+__global__ void k_hen_yvec(const double* __restrict__ Zh, const double* __restrict__ ct, const double* __restrict__ Zr,
+                           long long n_h, double* __restrict__ y) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= n_h) return;
+  y[g] = Zh[g] - ct[g] - Zr[g];
+}
+
 // ---------------------------------------------------------------------------- host side
 double box_distance(const double lo[3], const double hi[3], const double* R) {
   double d2 = 0.0;
@@ -1199,6 +1254,60 @@ cudaError_t hartree_enriched_solve(Ctx& c, const double* rho, double* vH, const 
   EFE_CUDA_TRY(launch_interp(c, u, vH, nb, s));
   const long long npts = (long long)c.nc * c.nq;
   k_hen_add<TabRadial><<<nblk(npts * nb), 256, 0, s>>>(c.d_xq, npts, nb, h.atoms, nA, trad, h.r0, h.s, xE, vH);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// The transpose of the enriched Hartree map rho -> v_H (batch 1), as the adjoint
+// needs it.  With d = L rho (load), z = Z d (homogeneous direct solve),
+// d_E = A rho (enrichment loads), rhs = A rho - W L rho with
+// W d = C d + k G (Z d) - C (k K Z d), phi^E = Sinv rhs and
+// v_H = I (z - (X + C)^T phi^E) + N^T phi^E (I: interpolation, N: atomic values),
+//   v_H^T g = L^T (Z h - W^T t) + A^T t,   h = I^T g,   t = Sinv (N g - (X + C) h),
+//   W^T t = C^T t + Z (k G^T t - k K C^T t),   L^T = w I,   (A^T t)_q = w_q sum_J t_J N^A_J(q).
+// gw: g / w at the quadrature points (input); out: I (Z h - W^T t) + sum_J t_J N^A_J, to be
+// multiplied by w by the caller (may alias gw); s1..s6: [n_h] scratch.
+cudaError_t hartree_enriched_vt(Ctx& c, const double* gw, double* out, double* s1, double* s2, double* s3, double* s4,
+                                double* s5, double* s6, cudaStream_t s) {
+  HartreeEnr& h = c.hen;
+  const int nA = h.nA;
+  const long long n_h = c.n_h;
+  const double k4 = 1.0 / (4.0 * kPi), lap = 1.0 / (2.0 * kPi);
+  const TabRadial trad{h.r, h.v, h.q, h.nel, h.n_tab, h.rmax};
+  double* sN = h.small;
+  double* sX = sN + nA;
+  double* t = sX + nA;
+  // h = I^T g = load(g / w);  Zh
+  EFE_CUDA_TRY(cudaMemsetAsync(s1, 0, sizeof(double) * n_h, s));
+  EFE_CUDA_TRY(launch_load_vector(c, gw, s1, 1, s));
+  EFE_CUDA_TRY(fdm_solve(c, s1, s2, s3, 1, s, true));
+  // N g (the enrichment loads of g / w) and (X + C) . h, then t
+  EFE_CUDA_TRY(cudaMemsetAsync(sN, 0, sizeof(double) * nA, s));
+  if (h.n_pairs > 0) {
+    k_hen_load<TabRadial><<<(unsigned)h.n_pairs, kNucThreads, 0, s>>>(h.pair_cell, h.pair_fn, c.nq, c.nc, 1, c.d_xq,
+                                                                      c.d_wJ, gw, h.atoms, trad, h.r0, h.s, sN);
+    note_launch();
+  }
+  k_hen_xc_dot<<<(unsigned)nA, kNucThreads, 0, s>>>(h.X, h.C, s1, n_h, sX);
+  note_launch();
+  k_hen_tcoef<<<1, 256, 0, s>>>(h.Sinv, sN, sX, nA, t);
+  note_launch();
+  // W^T t = ct + Z (k gt - k K ct)
+  k_hen_comb_t<<<nblk(n_h), 256, 0, s>>>(h.C, h.G, t, n_h, nA, s4, s5);
+  note_launch();
+  EFE_CUDA_TRY(cudaMemsetAsync(s6, 0, sizeof(double) * n_h, s));
+  EFE_CUDA_TRY(launch_laplace(c, s4, s6, 1, 1, lap, s));
+  k_hen_rvec<<<nblk(n_h), 256, 0, s>>>(s5, s6, c.d_Dsc, n_h, k4);
+  note_launch();
+  EFE_CUDA_TRY(cudaGetLastError());
+  EFE_CUDA_TRY(fdm_solve(c, s5, s2, s6, 1, s, true));
+  // y = Zh - W^T t, then out = I y + sum_J t_J N^A_J
+  k_hen_yvec<<<nblk(n_h), 256, 0, s>>>(s3, s4, s6, n_h, s1);
+  note_launch();
+  EFE_CUDA_TRY(cudaGetLastError());
+  EFE_CUDA_TRY(launch_interp(c, s1, out, 1, s));
+  const long long npts = (long long)c.nc * c.nq;
+  k_hen_add<TabRadial><<<nblk(npts), 256, 0, s>>>(c.d_xq, npts, 1, h.atoms, nA, trad, h.r0, h.s, t, out);
   note_launch();
   return cudaGetLastError();
 }

@@ -303,8 +303,7 @@ def test_steps_with_enriched_hartree_match_oracle():
 
 
 def test_hartree_enriched_rejections():
-    """The enriched solve needs the direct Hartree method; once installed, the
-    adjoint (whose transposed Hartree map is classical) refuses the context."""
+    """The enriched solve needs the direct Hartree method and supports inside the box."""
     from paper_2210_14421_gb300 import EFE_HARTREE_PCG, Context, EfeError
     wl = W.h2()
     ctx = Context(wl, hartree_method=EFE_HARTREE_PCG)
@@ -314,12 +313,39 @@ def test_hartree_enriched_rejections():
     ctx = Context(wl)
     with pytest.raises(EfeError):
         ctx.hartree_enriched(9.0, 1.5)   # support reaching the boundary
-    ctx.hartree_enriched(3.0, 1.5)
-    psi0 = torch.zeros((ctx.n_dof, ctx.n_cols), dtype=torch.complex128, device="cuda")
-    ctx.init_orbitals(psi0)
-    field = W.Field(kind=W.FIELD_GAUSS, amp=0.02, omega=0.0, t0=0.15, sigma=0.25, direction=(1.0, 0.0, 0.0))
-    with pytest.raises(EfeError):
-        ctx.adjoint_dipole(psi0, 2, wl.dt, field, (1.0, 0.0, 0.0), (1, 2))
+    ctx.close()
+
+
+def test_adjoint_with_enriched_hartree_matches_finite_differences():
+    """The adjoint's reverse sweep through the enriched Hartree map (its transpose
+    by the same block elimination) against central differences (h = 1e-4 |theta|)
+    of the CUDA forward run with the enriched solve."""
+    import dataclasses
+    from paper_2210_14421_gb300 import Context
+    from oracle import operators
+    wl = W.small_cluster(n_atoms=2, cells_per_axis=3, degree=3, n_quad=5, L=10.0, n_orb=2)
+    field = W.Field(kind=W.FIELD_GAUSS, amp=0.02, omega=0.0, t0=0.15, sigma=0.25, direction=(0.0, 0.6, 0.8))
+    dt, n, window, d = 0.04, 4, (3, 4), (0.0, 0.6, 0.8)
+    psi0 = operators.System(wl).initial_orbitals()
+    psi0 /= np.linalg.norm(psi0, axis=0)
+    ctx = Context(wl, krylov_tol=1e-13, k_max=40)
+    ctx.hartree_enriched(3.0, 1.5, sub=1, n_quad=wl.n_quad)
+    g0 = torch.from_numpy(np.ascontiguousarray(psi0)).cuda()
+
+    def run(f, n_s=6):
+        return ctx.adjoint_dipole(g0, n, dt, f, d, window, checkpoint_every=2, n_quad_s=n_s)
+
+    J, g = run(field)
+    for k, name in enumerate(["amp", "omega", "sigma"]):
+        val = getattr(field, name)
+        if val == 0.0:
+            assert g[k] == 0.0
+            continue
+        h = 1e-4 * abs(val)
+        Jp, _ = run(dataclasses.replace(field, **{name: val + h}), n_s=1)
+        Jm, _ = run(dataclasses.replace(field, **{name: val - h}), n_s=1)
+        fd = (Jp - Jm) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-6 * abs(fd) + 1e-13, (name, g[k], fd)
     ctx.close()
 
 
