@@ -118,7 +118,7 @@ struct HartreeEnr {
   int* pair_cell = nullptr;  // (cell, atom) pairs of the supports, for the per-solve loads
   int* pair_fn = nullptr;
   long long n_pairs = 0;
-  double* small = nullptr;   // [3][nA][batch] loads int rho N^A, right sides, coefficients
+  double* small = nullptr;   // [6][nA][batch] loads int rho N^A, right sides, coefficients, 3 partial dots
 };
 void hen_free(HartreeEnr& h);
 

@@ -418,17 +418,21 @@ k_hen_load(const int* __restrict__ cells, const int* __restrict__ fn, int nq, in
   }
 }
 
-// rhs[J][m] = dA[J][m] - C_J . d_m - k G_J . z_m + C_J . Lz_m   (one block per (J, m))
+// Partial dots of the right sides, spread over gridDim.y slices of the nodes:
+// sums[0][J][m] += C_J . d_m, sums[1][J][m] += G_J . z_m, sums[2][J][m] += C_J . Lz_m
+// (blockIdx.x = (J, m); the caller zeroes sums)
 __global__ void __launch_bounds__(kNucThreads)
-k_hen_rhs(const double* __restrict__ C, const double* __restrict__ G, const double* __restrict__ d,
-          const double* __restrict__ z, const double* __restrict__ Lz, const double* __restrict__ dA, long long n_h,
-          int nb, double k, double* __restrict__ rhs) {
+k_hen_dots(const double* __restrict__ C, const double* __restrict__ G, const double* __restrict__ d,
+           const double* __restrict__ z, const double* __restrict__ Lz, long long n_h, int nb, int nAnb,
+           double* __restrict__ sums) {
   __shared__ double red[kNucThreads];
   const int J = blockIdx.x / nb, b = blockIdx.x % nb;
   const double* cj = C + (long long)J * n_h;
   const double* gj = G + (long long)J * n_h;
+  const long long chunk = (n_h + gridDim.y - 1) / gridDim.y;
+  const long long g0 = (long long)blockIdx.y * chunk, g1 = min(n_h, g0 + chunk);
   double ad = 0.0, az = 0.0, al = 0.0;
-  for (long long g = threadIdx.x; g < n_h; g += blockDim.x) {
+  for (long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
     const long long i = g * nb + b;
     ad += cj[g] * d[i];
     az += gj[g] * z[i];
@@ -437,7 +441,18 @@ k_hen_rhs(const double* __restrict__ C, const double* __restrict__ G, const doub
   const double sd = block_sum(ad, red);
   const double sz = block_sum(az, red);
   const double sl = block_sum(al, red);
-  if (threadIdx.x == 0) rhs[blockIdx.x] = dA[blockIdx.x] - sd - k * sz + sl;
+  if (threadIdx.x == 0) {
+    atomicAdd(&sums[blockIdx.x], sd);
+    atomicAdd(&sums[nAnb + blockIdx.x], sz);
+    atomicAdd(&sums[2 * nAnb + blockIdx.x], sl);
+  }
+}
+
+// rhs[J][m] = dA[J][m] - C_J . d_m - k G_J . z_m + C_J . Lz_m
+__global__ void k_hen_rhs(const double* __restrict__ dA, const double* __restrict__ sums, int nAnb, double k,
+                          double* __restrict__ rhs) {
+  for (int i = threadIdx.x; i < nAnb; i += blockDim.x)
+    rhs[i] = dA[i] - sums[i] - k * sums[nAnb + i] + sums[2 * nAnb + i];
 }
 
 // xE[J][m] = sum_K Sinv[J][K] rhs[K][m]
@@ -1183,7 +1198,7 @@ efe_status hartree_enrich_install(Ctx& c, double r0, double s, int sub, int n_qu
   ENR_CK(dal(h.v, V.size()), "allocating");
   ENR_CK(dal(h.q, Q.size()), "allocating");
   ENR_CK(dal(h.nel, nA), "allocating");
-  ENR_CK(dal(h.small, (size_t)3 * nA * c.batch), "allocating");
+  ENR_CK(dal(h.small, (size_t)6 * nA * c.batch), "allocating");
   ENR_CK(cudaMemcpyAsync(h.atoms, at.data(), sizeof(double) * at.size(), cudaMemcpyHostToDevice, st), "copy");
   ENR_CK(cudaMemcpyAsync(h.r, rg.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, st), "copy");
   ENR_CK(cudaMemcpyAsync(h.v, V.data(), sizeof(double) * V.size(), cudaMemcpyHostToDevice, st), "copy");
@@ -1244,7 +1259,11 @@ cudaError_t hartree_enriched_solve(Ctx& c, const double* rho, double* vH, const 
                                                                       c.d_wJ, rho, h.atoms, trad, h.r0, h.s, dA);
     note_launch();
   }
-  k_hen_rhs<<<(unsigned)(nA * nb), kNucThreads, 0, s>>>(h.C, h.G, d, c.d_phi, Lz, dA, n_h, nb, k4, rhs);
+  double* sums = h.small + 3 * nA * nb;   // [3][nA][nb]
+  EFE_CUDA_TRY(cudaMemsetAsync(sums, 0, sizeof(double) * 3 * nA * nb, s));
+  k_hen_dots<<<dim3((unsigned)(nA * nb), 64), kNucThreads, 0, s>>>(h.C, h.G, d, c.d_phi, Lz, n_h, nb, nA * nb, sums);
+  note_launch();
+  k_hen_rhs<<<1, 256, 0, s>>>(dA, sums, nA * nb, k4, rhs);
   note_launch();
   k_hen_coef<<<1, 256, 0, s>>>(h.Sinv, rhs, nA, nb, xE);
   note_launch();
