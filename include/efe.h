@@ -441,6 +441,24 @@ efe_status efe_octree_coords(const efe_octree* oct, double* free_xyz_host, doubl
 efe_status efe_octree_apply(efe_octree* oct, const double* vq_dev, double kin, const double* X_dev, double* Y_dev,
                             int64_t n_cols, int32_t mask_boundary, void* stream);
 
+/* Host-only diagnostics of the electrostatic enrichment (no context, no device
+ * work).  efe_atom_hartree_table: the atomic Hartree potentials that
+ * efe_hartree_enriched uses, for atoms with charges Z_host [n_atoms] and the
+ * wavefunction enrichment functions fns_host [n_fn]: r_host [n_tab] (r =
+ * rmax t^2, t uniform on [0, 1]), v_host and q_host [n_atoms][n_tab] (potential
+ * and enclosed charge), nel_host [n_atoms] (any output may be NULL).
+ * efe_adaptive_cell_boxes: the boxes of efe_nuclear_enriched's adaptive rule
+ * for one cell (origin_host, size_host: double[3]; atoms_host [n_atoms][4] =
+ * Z, x, y, z), in the cell's reference coordinates [-1, 1]^3 as lo[3], hi[3]
+ * per box; *n_boxes receives the count, boxes_host (NULL to query) needs
+ * capacity >= the count.  Errors: EFE_ERR_ARG. */
+efe_status efe_atom_hartree_table(const efe_enrich_fn* fns_host, int32_t n_fn, const double* Z_host, int32_t n_atoms,
+                                  int32_t n_tab, double rmax, double* r_host, double* v_host, double* q_host,
+                                  double* nel_host);
+efe_status efe_adaptive_cell_boxes(const double* origin_host, const double* size_host, const double* atoms_host,
+                                   int32_t n_atoms, double sigma, double r0, double s, int32_t n_quad, double tol,
+                                   int32_t max_depth, int64_t* n_boxes, double* boxes_host, int64_t capacity);
+
 /* Spectra of dipole traces (Sec. Results: the absorption spectrum of the weak
  * perturbation study and the power spectrum of the high-harmonic study); no
  * context needed.  Samples at t_n = n dt, n = 0 .. n_t - 1, on the device;

@@ -26,7 +26,8 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_apply_H_noalloc", "efe_tuning", "efe_adjoint_dipole",
             "efe_absorption_spectrum", "efe_power_spectrum", "efe_nuclear_enriched",
             "efe_hartree_enriched", "efe_octree_setup", "efe_octree_destroy", "efe_octree_last_error",
-            "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply", "efe_octree_constraints"]
+            "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply", "efe_octree_constraints",
+            "efe_atom_hartree_table", "efe_adaptive_cell_boxes"]
 
 
 class MeshDesc(C.Structure):
@@ -117,6 +118,9 @@ def lib(path: str = LIB_PATH):
     L.efe_octree_constraints.argtypes = [pdbl, pdbl, i32, i32, i32, C.POINTER(i32), i32, C.POINTER(i64),
                                          C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), pdbl, pdbl,
                                          pdbl]
+    L.efe_atom_hartree_table.argtypes = [C.POINTER(EnrichFn), i32, pdbl, i32, i32, dbl, pdbl, pdbl, pdbl, pdbl]
+    L.efe_adaptive_cell_boxes.argtypes = [pdbl, pdbl, pdbl, i32, dbl, dbl, dbl, i32, dbl, i32, C.POINTER(i64), pdbl,
+                                          i64]
     for name in EXPORTED:
         if name not in ("efe_last_error", "efe_octree_last_error"):
             getattr(L, name).restype = C.c_int
@@ -445,3 +449,43 @@ def octree_constraints(lo, hi, nc: int, degree: int, n_quad: int, refine=()):
     if st != EFE_OK:
         raise EfeError(st, L.efe_octree_last_error(None).decode())
     return rs, col, val, axyz, fxyz
+
+
+def atom_hartree_table(enrich, Z, n_tab: int = 24001, rmax: float = 60.0):
+    """Host-only: the atomic Hartree potentials of the enriched Hartree solve for
+    atoms with charges Z and wavefunction enrichment functions `enrich`
+    (efe_workloads.EnrichFn list): (r [n_tab], v [n_atoms, n_tab], Q [n_atoms, n_tab], n_el [n_atoms])."""
+    L = lib()
+    Z = np.ascontiguousarray(Z, dtype=np.float64)
+    fns = (EnrichFn * max(len(enrich), 1))()
+    for i, f in enumerate(enrich):
+        fns[i] = EnrichFn(int(f.atom), int(f.n), int(f.l), int(f.m), int(f.radial), float(f.zeta))
+    r = np.zeros(n_tab)
+    v = np.zeros((len(Z), n_tab))
+    q = np.zeros((len(Z), n_tab))
+    nel = np.zeros(len(Z))
+    st = L.efe_atom_hartree_table(fns, len(enrich), _dptr(Z), len(Z), int(n_tab), float(rmax), _dptr(r), _dptr(v),
+                                  _dptr(q), _dptr(nel))
+    if st != EFE_OK:
+        raise EfeError(st, "efe_atom_hartree_table: invalid argument")
+    return r, v, q, nel
+
+
+def adaptive_cell_boxes(origin, size, Z, R, sigma, r0, s, n_quad, tol, max_depth):
+    """Host-only: the boxes (reference coordinates, [n, 6] = lo, hi) of the adaptive
+    cell rule of efe_nuclear_enriched for one cell."""
+    L = lib()
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    h = np.ascontiguousarray(size, dtype=np.float64)
+    at = np.ascontiguousarray(np.column_stack([np.asarray(Z, float), np.asarray(R, float).reshape(-1, 3)]))
+    n = C.c_int64()
+    args = (_dptr(o), _dptr(h), _dptr(at), len(Z), float(sigma), float(r0), float(s), int(n_quad), float(tol),
+            int(max_depth), C.byref(n))
+    st = L.efe_adaptive_cell_boxes(*args, None, 0)
+    if st != EFE_OK:
+        raise EfeError(st, "efe_adaptive_cell_boxes: invalid argument")
+    boxes = np.zeros((n.value, 6))
+    st = L.efe_adaptive_cell_boxes(*args, _dptr(boxes), int(n.value))
+    if st != EFE_OK:
+        raise EfeError(st, "efe_adaptive_cell_boxes: invalid argument")
+    return boxes

@@ -701,21 +701,22 @@ BoxRule uniform_rule(const Ctx& c, const Lists& L, int sub, int n) {
 // (those that vanish on a cell contribute zero to both estimates and are skipped,
 // as are the charges of nuclei beyond 40 sigma).
 struct NucTrial {
-  const Ctx* c;
+  const double* R;   // [nA][3]
+  const double* Z;   // [nA]
   double a, norm, inv2s2, r0, s;
   std::vector<int> local, nearb;   // atoms whose support / charge reaches the cell
   void eval(const double x[3], double* out) const {
     double b = 0.0;
     for (int t : nearb) {
-      const double dx = x[0] - c->R[3 * t], dy = x[1] - c->R[3 * t + 1], dz = x[2] - c->R[3 * t + 2];
-      b -= c->Z[t] * norm * std::exp(-(dx * dx + dy * dy + dz * dz) * inv2s2);
+      const double dx = x[0] - R[3 * t], dy = x[1] - R[3 * t + 1], dz = x[2] - R[3 * t + 2];
+      b -= Z[t] * norm * std::exp(-(dx * dx + dy * dy + dz * dz) * inv2s2);
     }
     out[0] = b;
     for (size_t k = 0; k < local.size(); ++k) {
       const int J = local[k];
-      const double dx = x[0] - c->R[3 * J], dy = x[1] - c->R[3 * J + 1], dz = x[2] - c->R[3 * J + 2];
+      const double dx = x[0] - R[3 * J], dy = x[1] - R[3 * J + 1], dz = x[2] - R[3 * J + 2];
       const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
-      const double f = r > 0.0 ? -c->Z[J] * std::erf(a * r) / r : -c->Z[J] * 2.0 * a / std::sqrt(kPi);
+      const double f = r > 0.0 ? -Z[J] * std::erf(a * r) / r : -Z[J] * 2.0 * a / std::sqrt(kPi);
       double u, du;
       cutoff(r, r0, s, u, du);
       out[1 + k] = f * u;
@@ -780,6 +781,22 @@ void adapt_box(const NucTrial& T, const double lo[3], const double hi[3], int de
   for (int i = 0; i < 8; ++i) adapt_box(T, clo[i], chi[i], depth + 1, max_depth, tol, o, h, xg, wg, out);
 }
 
+// The adaptive boxes of one cell (origin o, sizes h) for atoms R [nA][3], Z [nA].
+void adaptive_cell(const double o[3], const double h[3], const double* R, const double* Z, int nA, double sigma,
+                   double r0, double s, const std::vector<double>& xg, const std::vector<double>& wg, double tol,
+                   int max_depth, std::vector<double>& out) {
+  const double bhi[3] = {o[0] + h[0], o[1] + h[1], o[2] + h[2]};
+  NucTrial T{R, Z, 1.0 / (std::sqrt(2.0) * sigma), std::pow(2.0 * kPi * sigma * sigma, -1.5),
+             1.0 / (2.0 * sigma * sigma), r0, s, {}, {}};
+  for (int J = 0; J < nA; ++J) {
+    const double d = box_distance(o, bhi, &R[3 * J]);
+    if (d < r0) T.local.push_back(J);
+    if (d < 40.0 * sigma) T.nearb.push_back(J);
+  }
+  const double lo[3] = {-1.0, -1.0, -1.0}, hi[3] = {1.0, 1.0, 1.0};
+  adapt_box(T, lo, hi, 0, max_depth, tol, o, h, xg, wg, out);
+}
+
 BoxRule adaptive_rule(const Ctx& c, const Lists& L, int n, double tol, int max_depth, double sigma, double r0,
                       double s) {
   BoxRule R;
@@ -798,16 +815,7 @@ BoxRule adaptive_rule(const Ctx& c, const Lists& L, int n, double tol, int max_d
       const int cx = cell % c.ncx, cy = (cell / c.ncx) % c.ncy, cz = cell / (c.ncx * c.ncy);
       const double o[3] = {c.xb[cx], c.yb[cy], c.zb[cz]};
       const double h[3] = {c.xb[cx + 1] - c.xb[cx], c.yb[cy + 1] - c.yb[cy], c.zb[cz + 1] - c.zb[cz]};
-      const double bhi[3] = {o[0] + h[0], o[1] + h[1], o[2] + h[2]};
-      NucTrial T{&c, 1.0 / (std::sqrt(2.0) * sigma), std::pow(2.0 * kPi * sigma * sigma, -1.5),
-                 1.0 / (2.0 * sigma * sigma), r0, s, {}, {}};
-      for (int J = 0; J < c.n_atoms; ++J) {
-        const double d = box_distance(o, bhi, &c.R[3 * J]);
-        if (d < r0) T.local.push_back(J);
-        if (d < 40.0 * sigma) T.nearb.push_back(J);
-      }
-      const double lo[3] = {-1.0, -1.0, -1.0}, hi[3] = {1.0, 1.0, 1.0};
-      adapt_box(T, lo, hi, 0, max_depth, tol, o, h, xg, wg, per[i]);
+      adaptive_cell(o, h, c.R.data(), c.Z.data(), c.n_atoms, sigma, r0, s, xg, wg, tol, max_depth, per[i]);
     }
   };
   std::vector<std::thread> pool;
@@ -1015,9 +1023,8 @@ std::vector<double> cum_t2(const std::vector<double>& y, const std::vector<doubl
 // rho(r) = sum occ R_nl^2 / (4 pi int R_nl^2 r^2 dr), Q(r) = 4 pi int_0^r rho s^2 ds,
 // v(r) = Q(r) / r + 4 pi int_r^inf rho s ds, tabulated on r_i = rmax t_i^2 with t uniform
 // on [0, 1] (nt points): rg [nt], V and Q [nA][nt], nel [nA] = Q at the end of the table.
-void atom_tables(const Ctx& c, int nt, double rmax, std::vector<double>& rg, std::vector<double>& V,
-                 std::vector<double>& Q, std::vector<double>& nel) {
-  const int nA = c.n_atoms;
+void atom_tables(int nA, const double* Zs, const std::vector<efe_enrich_fn>& fns, int nt, double rmax,
+                 std::vector<double>& rg, std::vector<double>& V, std::vector<double>& Q, std::vector<double>& nel) {
   rg.assign(nt, 0.0);
   for (int i = 0; i < nt; ++i) {
     const double t = i == nt - 1 ? 1.0 : i * (1.0 / (nt - 1));
@@ -1029,7 +1036,7 @@ void atom_tables(const Ctx& c, int nt, double rmax, std::vector<double>& rg, std
   for (int J = 0; J < nA; ++J) {
     struct Shell { int kind, n, l; double zeta; };
     std::vector<Shell> sh;
-    for (const efe_enrich_fn& f : c.fns) {
+    for (const efe_enrich_fn& f : fns) {
       if (f.atom != J) continue;
       bool seen = false;
       for (const Shell& x : sh)
@@ -1040,7 +1047,7 @@ void atom_tables(const Ctx& c, int nt, double rmax, std::vector<double>& rg, std
       return a.n != b.n ? a.n < b.n : a.l < b.l;
     });
     std::vector<double> rho(nt, 0.0), R(nt), y(nt);
-    double left = c.Z[J];
+    double left = Zs[J];
     for (const Shell& x : sh) {
       const double occ = std::min(left, 2.0 * (2 * x.l + 1));
       if (occ <= 0.0) break;
@@ -1173,7 +1180,7 @@ efe_status hartree_enrich_install(Ctx& c, double r0, double s, int sub, int n_qu
   const int nA = c.n_atoms, nt = 24001;
   const double rmax = 60.0;
   std::vector<double> rg, V, Q, nel;
-  atom_tables(c, nt, rmax, rg, V, Q, nel);
+  atom_tables(nA, c.Z.data(), c.fns, nt, rmax, rg, V, Q, nel);
   hen_free(c.hen);
   HartreeEnr& h = c.hen;
   h.nA = nA;
@@ -1334,3 +1341,46 @@ cudaError_t hartree_enriched_vt(Ctx& c, const double* gw, double* out, double* s
 #undef ENR_CK
 
 }  // namespace efe
+
+// ---------------------------------------------------------------------------- host-only diagnostics
+extern "C" {
+
+efe_status efe_atom_hartree_table(const efe_enrich_fn* fns_host, int32_t n_fn, const double* Z_host, int32_t n_atoms,
+                                  int32_t n_tab, double rmax, double* r_host, double* v_host, double* q_host,
+                                  double* nel_host) {
+  if (!Z_host || n_atoms < 1 || n_fn < 0 || (n_fn > 0 && !fns_host) || n_tab < 2 || !(rmax > 0.0)) return EFE_ERR_ARG;
+  for (int i = 0; i < n_fn; ++i)
+    if (fns_host[i].atom < 0 || fns_host[i].atom >= n_atoms) return EFE_ERR_ARG;
+  std::vector<efe_enrich_fn> fns(fns_host, fns_host + n_fn);
+  std::vector<double> rg, V, Q, nel;
+  efe::atom_tables(n_atoms, Z_host, fns, n_tab, rmax, rg, V, Q, nel);
+  if (r_host) std::copy(rg.begin(), rg.end(), r_host);
+  if (v_host) std::copy(V.begin(), V.end(), v_host);
+  if (q_host) std::copy(Q.begin(), Q.end(), q_host);
+  if (nel_host) std::copy(nel.begin(), nel.end(), nel_host);
+  return EFE_OK;
+}
+
+efe_status efe_adaptive_cell_boxes(const double* origin_host, const double* size_host, const double* atoms_host,
+                                   int32_t n_atoms, double sigma, double r0, double s, int32_t n_quad, double tol,
+                                   int32_t max_depth, int64_t* n_boxes, double* boxes_host, int64_t capacity) {
+  if (!origin_host || !size_host || (n_atoms > 0 && !atoms_host) || n_atoms < 0 || !(sigma > 0.0) || !(s > 0.0) ||
+      !(r0 > s) || n_quad < 1 || n_quad > 8 || !(tol > 0.0) || max_depth < 0 || max_depth > 8 || !n_boxes)
+    return EFE_ERR_ARG;
+  std::vector<double> R(3 * (size_t)n_atoms), Z(n_atoms);
+  for (int J = 0; J < n_atoms; ++J) {
+    Z[J] = atoms_host[4 * J];
+    for (int a = 0; a < 3; ++a) R[3 * J + a] = atoms_host[4 * J + 1 + a];
+  }
+  std::vector<double> xg(n_quad), wg(n_quad), out;
+  efe::gauss_legendre(n_quad, xg.data(), wg.data());
+  efe::adaptive_cell(origin_host, size_host, R.data(), Z.data(), n_atoms, sigma, r0, s, xg, wg, tol, max_depth, out);
+  *n_boxes = (int64_t)(out.size() / 6);
+  if (boxes_host) {
+    if (capacity < *n_boxes) return EFE_ERR_ARG;
+    std::copy(out.begin(), out.end(), boxes_host);
+  }
+  return EFE_OK;
+}
+
+}  // extern "C"
