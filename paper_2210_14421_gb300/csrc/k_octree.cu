@@ -10,8 +10,8 @@
 // its value is the coarse leaf's interpolant there, so u_all = P u_free with P
 // the interpolation weights (rows of hanging nodes) and the identity (rows of
 // free nodes).  The apply is three stages: the gather x_all = P x_free, the
-// per-leaf operator (kinetic by its Kronecker form, potential by sum
-// factorisation at the Gauss-Legendre points) scatter-added into y_all, and
+// per-leaf operator (kinetic and potential by sum factorisation, the
+// potential at the Gauss-Legendre points) scatter-added into y_all, and
 // the transposed scatter y_free = P^T y_all.
 #include <algorithm>
 #include <array>
@@ -112,6 +112,8 @@ k_oct_apply(const OctTables T, const double* __restrict__ geo, const int* __rest
   __shared__ double A[kOctMaxQ1 * kMaxP1 * kMaxP1];
   __shared__ double Bq[kOctMaxQ1 * kOctMaxQ1 * kMaxP1];
   __shared__ double Cq[kOctMaxQ1 * kOctMaxQ1 * kOctMaxQ1];
+  __shared__ double ka[kMaxP1 * kMaxP1 * kMaxP1], kb[kMaxP1 * kMaxP1 * kMaxP1];
+  __shared__ double kc[kMaxP1 * kMaxP1 * kMaxP1], kd[kMaxP1 * kMaxP1 * kMaxP1], ke[kMaxP1 * kMaxP1 * kMaxP1];
   const int P1 = T.P1, Q = T.NQ1, nn = P1 * P1 * P1, nq = Q * Q * Q;
   const long long leaf = blockIdx.x;
   const int c = blockIdx.y;
@@ -156,22 +158,47 @@ k_oct_apply(const OctTables T, const double* __restrict__ geo, const int* __rest
     A[t] = s;
   }
   __syncthreads();
-  // kinetic (Kronecker form) plus the last potential axis, scatter-added
+  // kinetic by sum factorisation: with a = M1 x, b = K1 x along axis 3, then c = M1 a, d = K1 a,
+  // e = M1 b along axis 2, y = ax K1 c + ay M1 d + az M1 e along axis 1 (ax = kin hy hz / (4 hx), ...)
+  for (int l = threadIdx.x; l < nn; l += blockDim.x) {   // a, b [i1][i2][i3] from x along axis 3
+    const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
+    double sa = 0.0, sb = 0.0;
+    for (int j3 = 0; j3 < P1; ++j3) {
+      const double v = x[i1 + P1 * (i2 + P1 * j3)];
+      sa += T.M1[i3 * P1 + j3] * v;
+      sb += T.K1[i3 * P1 + j3] * v;
+    }
+    ka[l] = sa;
+    kb[l] = sb;
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < nn; l += blockDim.x) {   // c, d, e along axis 2
+    const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
+    double sc = 0.0, sd = 0.0, se = 0.0;
+    for (int j2 = 0; j2 < P1; ++j2) {
+      const int m = i1 + P1 * (j2 + P1 * i3);
+      sc += T.M1[i2 * P1 + j2] * ka[m];
+      sd += T.K1[i2 * P1 + j2] * ka[m];
+      se += T.M1[i2 * P1 + j2] * kb[m];
+    }
+    kc[l] = sc;
+    kd[l] = sd;
+    ke[l] = se;
+  }
+  __syncthreads();
   const double ax = kin * hy * hz / (4.0 * hx), ay = kin * hx * hz / (4.0 * hy), az = kin * hx * hy / (4.0 * hz);
-  for (int l = threadIdx.x; l < nn; l += blockDim.x) {
+  for (int l = threadIdx.x; l < nn; l += blockDim.x) {   // axis 1, plus the last potential axis; scatter-add
     const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
     double y = 0.0;
     for (int q1 = 0; q1 < Q; ++q1) y += T.B1[q1 * P1 + i1] * A[q1 + Q * (i2 + P1 * i3)];
-    double k = 0.0;
-    for (int j3 = 0; j3 < P1; ++j3)
-      for (int j2 = 0; j2 < P1; ++j2)
-        for (int j1 = 0; j1 < P1; ++j1) {
-          const double a1 = T.K1[i1 * P1 + j1] * T.M1[i2 * P1 + j2] * T.M1[i3 * P1 + j3];
-          const double a2 = T.M1[i1 * P1 + j1] * T.K1[i2 * P1 + j2] * T.M1[i3 * P1 + j3];
-          const double a3 = T.M1[i1 * P1 + j1] * T.M1[i2 * P1 + j2] * T.K1[i3 * P1 + j3];
-          k += (ax * a1 + ay * a2 + az * a3) * x[j1 + P1 * (j2 + P1 * j3)];
-        }
-    atomicAdd(&ya[(long long)cl[l] * ncols + c], y + k);
+    double k1 = 0.0, k2 = 0.0, k3 = 0.0;
+    for (int j1 = 0; j1 < P1; ++j1) {
+      const int m = j1 + P1 * (i2 + P1 * i3);
+      k1 += T.K1[i1 * P1 + j1] * kc[m];
+      k2 += T.M1[i1 * P1 + j1] * kd[m];
+      k3 += T.M1[i1 * P1 + j1] * ke[m];
+    }
+    atomicAdd(&ya[(long long)cl[l] * ncols + c], y + ax * k1 + ay * k2 + az * k3);
   }
 }
 
