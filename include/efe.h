@@ -440,6 +440,18 @@ efe_status efe_octree_coords(const efe_octree* oct, double* free_xyz_host, doubl
  * Errors: EFE_ERR_ARG, EFE_ERR_NOMEM, EFE_ERR_CUDA. */
 efe_status efe_octree_apply(efe_octree* oct, const double* vq_dev, double kin, const double* X_dev, double* Y_dev,
                             int64_t n_cols, int32_t mask_boundary, void* stream);
+/* The Poisson problem on the locally refined mesh (the operator of the Hartree
+ * solve, Eqs. Hartree_possion and DiscretePoisson, without the 1/4pi that the
+ * caller folds into f): -lap u = f with u = g on the boundary, i.e.
+ * K_II u_I = F_I - K_IB g_B in the constrained space, F = P^T int f N with f at
+ * every leaf's Gauss-Legendre points (f_q_dev: device [n_leaves][n_q]); g_free_dev
+ * and u_dev: device [n_free] (g read on the boundary free nodes only).
+ * Conjugate gradients on the constrained stiffness to |r| <= tol |r_0|, at most
+ * max_it iterations (*iters_host receives the count); synchronises `stream`
+ * every iteration.  Errors: EFE_ERR_ARG, EFE_ERR_CG_NOCONV (u holds the last
+ * iterate), EFE_ERR_NOT_SPD, EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+efe_status efe_octree_poisson(efe_octree* oct, const double* f_q_dev, const double* g_free_dev, double* u_dev,
+                              double tol, int32_t max_it, int32_t* iters_host, void* stream);
 
 /* Host-only diagnostics of the electrostatic enrichment (no context, no device
  * work).  efe_atom_hartree_table: the atomic Hartree potentials that

@@ -27,7 +27,7 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_absorption_spectrum", "efe_power_spectrum", "efe_nuclear_enriched",
             "efe_hartree_enriched", "efe_octree_setup", "efe_octree_destroy", "efe_octree_last_error",
             "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply", "efe_octree_constraints",
-            "efe_atom_hartree_table", "efe_adaptive_cell_boxes"]
+            "efe_atom_hartree_table", "efe_adaptive_cell_boxes", "efe_octree_poisson"]
 
 
 class MeshDesc(C.Structure):
@@ -118,6 +118,7 @@ def lib(path: str = LIB_PATH):
     L.efe_octree_constraints.argtypes = [pdbl, pdbl, i32, i32, i32, C.POINTER(i32), i32, C.POINTER(i64),
                                          C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), pdbl, pdbl,
                                          pdbl]
+    L.efe_octree_poisson.argtypes = [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), vp]
     L.efe_atom_hartree_table.argtypes = [C.POINTER(EnrichFn), i32, pdbl, i32, i32, dbl, pdbl, pdbl, pdbl, pdbl]
     L.efe_adaptive_cell_boxes.argtypes = [pdbl, pdbl, pdbl, i32, dbl, dbl, dbl, i32, dbl, i32, C.POINTER(i64), pdbl,
                                           i64]
@@ -412,6 +413,21 @@ class Octree:
         if st != EFE_OK:
             raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
         return Y
+
+    def poisson(self, fq, g, tol: float = 1e-12, max_it: int = 10000):
+        """-lap u = f (f at the leaves' GL points, device [n_leaves, n_q]) with u = g on the
+        boundary (g device [n_free]); returns (u device [n_free], CG iterations)."""
+        import torch
+        for t in (fq, g):
+            assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+        assert fq.numel() == self.n_leaves * self.n_q and g.numel() == self.n_free
+        u = torch.zeros(self.n_free, dtype=torch.float64, device="cuda")
+        its = C.c_int32()
+        st = lib().efe_octree_poisson(self.h, _ptr(fq), _ptr(g), _ptr(u), float(tol), int(max_it), C.byref(its),
+                                      _stream())
+        if st != EFE_OK:
+            raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
+        return u, its.value
 
     def close(self):
         if getattr(self, "h", None):

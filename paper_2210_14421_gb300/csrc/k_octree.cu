@@ -121,7 +121,10 @@ k_oct_apply(const OctTables T, const double* __restrict__ geo, const int* __rest
   const int* cl = conn + leaf * nn;
   for (int l = threadIdx.x; l < nn; l += blockDim.x) x[l] = xa[(long long)cl[l] * ncols + c];
   __syncthreads();
-  // potential: values at the GL points (axis 1, 2, 3), times w |J| v, back (axis 3, 2, 1)
+  // potential (skipped when vq is NULL: v = 0): values at the GL points (axis 1, 2, 3), times
+  // w |J| v, back (axis 3, 2, 1)
+  const bool pot = vq != nullptr;   // uniform over the block
+  if (pot) {
   for (int t = threadIdx.x; t < Q * P1 * P1; t += blockDim.x) {   // A[q1][i2][i3]
     const int q1 = t % Q, i2 = (t / Q) % P1, i3 = t / (Q * P1);
     double s = 0.0;
@@ -158,6 +161,7 @@ k_oct_apply(const OctTables T, const double* __restrict__ geo, const int* __rest
     A[t] = s;
   }
   __syncthreads();
+  }
   // kinetic by sum factorisation: with a = M1 x, b = K1 x along axis 3, then c = M1 a, d = K1 a,
   // e = M1 b along axis 2, y = ax K1 c + ay M1 d + az M1 e along axis 1 (ax = kin hy hz / (4 hx), ...)
   for (int l = threadIdx.x; l < nn; l += blockDim.x) {   // a, b [i1][i2][i3] from x along axis 3
@@ -190,7 +194,8 @@ k_oct_apply(const OctTables T, const double* __restrict__ geo, const int* __rest
   for (int l = threadIdx.x; l < nn; l += blockDim.x) {   // axis 1, plus the last potential axis; scatter-add
     const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
     double y = 0.0;
-    for (int q1 = 0; q1 < Q; ++q1) y += T.B1[q1 * P1 + i1] * A[q1 + Q * (i2 + P1 * i3)];
+    if (pot)
+      for (int q1 = 0; q1 < Q; ++q1) y += T.B1[q1 * P1 + i1] * A[q1 + Q * (i2 + P1 * i3)];
     double k1 = 0.0, k2 = 0.0, k3 = 0.0;
     for (int j1 = 0; j1 < P1; ++j1) {
       const int m = j1 + P1 * (i2 + P1 * i3);
@@ -203,6 +208,67 @@ k_oct_apply(const OctTables T, const double* __restrict__ geo, const int* __rest
 }
 
 unsigned oblk(long long n) { return (unsigned)((n + 255) / 256); }
+
+// *out += a . b (the caller zeroes *out)
+__global__ void __launch_bounds__(256) k_oct_dot(const double* __restrict__ a, const double* __restrict__ b,
+                                                 long long n, double* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    acc += a[i] * b[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, red[0]);
+}
+
+// gB = g on the boundary free nodes, 0 inside; ones = 1
+__global__ void k_oct_bc(const double* __restrict__ g, const unsigned char* __restrict__ bnd, long long n,
+                         double* __restrict__ gB, double* __restrict__ ones) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  gB[i] = bnd[i] ? g[i] : 0.0;
+  ones[i] = 1.0;
+}
+
+// r = p = F - y inside, 0 on the boundary; u = 0
+__global__ void k_oct_cg_start(const double* __restrict__ F, const double* __restrict__ y,
+                               const unsigned char* __restrict__ bnd, long long n, double* __restrict__ r,
+                               double* __restrict__ p, double* __restrict__ u) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = bnd[i] ? 0.0 : F[i] - y[i];
+  r[i] = v;
+  p[i] = v;
+  u[i] = 0.0;
+}
+
+// u += alpha p, r -= alpha Ap
+__global__ void k_oct_cg_step(double* __restrict__ u, double* __restrict__ r, const double* __restrict__ p,
+                              const double* __restrict__ Ap, double alpha, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  u[i] += alpha * p[i];
+  r[i] -= alpha * Ap[i];
+}
+
+// p = r + beta p
+__global__ void k_oct_cg_dir(double* __restrict__ p, const double* __restrict__ r, double beta, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  p[i] = r[i] + beta * p[i];
+}
+
+// u = g on the boundary free nodes
+__global__ void k_oct_cg_finish(double* __restrict__ u, const double* __restrict__ g,
+                                const unsigned char* __restrict__ bnd, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (bnd[i]) u[i] = g[i];
+}
 
 }  // namespace
 
@@ -452,6 +518,11 @@ static efe_status octree_build(Octree& o, const double* lo, const double* hi, in
 
 }  // namespace efe
 
+namespace efe {
+efe_status octree_apply(Octree& o, const double* vq_dev, double kin, const double* X_dev, double* Y_dev,
+                        long long n_cols, int mask_boundary, cudaStream_t s);
+}  // namespace efe
+
 struct efe_octree {
   efe::Octree o;
 };
@@ -530,8 +601,17 @@ efe_status efe_octree_coords(const efe_octree* oct, double* free_xyz_host, doubl
 efe_status efe_octree_apply(efe_octree* oct, const double* vq_dev, double kin, const double* X_dev, double* Y_dev,
                             int64_t n_cols, int32_t mask_boundary, void* stream) {
   if (!oct || !vq_dev || !X_dev || !Y_dev || n_cols < 1 || n_cols > 65535) return EFE_ERR_ARG;
-  efe::Octree& o = oct->o;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  return efe::octree_apply(oct->o, vq_dev, kin, X_dev, Y_dev, n_cols, mask_boundary,
+                           reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace efe {
+
+// Y = P^T (kin K/2 + V) P X (V = 0 when vq is NULL).
+efe_status octree_apply(Octree& o, const double* vq_dev, double kin, const double* X_dev, double* Y_dev,
+                        long long n_cols, int mask_boundary, cudaStream_t s) {
   if (o.ws_cols < n_cols) {
     if (o.d_xall) cudaFree(o.d_xall);
     if (o.d_yall) cudaFree(o.d_yall);
@@ -563,6 +643,108 @@ efe_status efe_octree_apply(efe_octree* oct, const double* vq_dev, double kin, c
     return EFE_ERR_CUDA;
   }
   return EFE_OK;
+}
+
+// -lap u = f with u = g on the boundary free nodes: K_II u_I = F_I - K_IB g_B, F = P^T int f N
+// (F = P^T V P 1 with v = f: the constants are in the constrained space and the basis sums to 1),
+// by conjugate gradients to |r| <= tol |F_I - K_IB g_B|.
+efe_status octree_poisson(Octree& o, const double* fq, const double* g, double* u, double tol, int max_it,
+                          int* iters, cudaStream_t s) {
+  const long long n = o.n_free;
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * (6 * n + 4)) != cudaSuccess) {
+    o.err = "octree Poisson: out of device memory";
+    return EFE_ERR_NOMEM;
+  }
+  double *gB = buf, *ones = buf + n, *F = buf + 2 * n, *r = buf + 3 * n, *p = buf + 4 * n, *Ap = buf + 5 * n;
+  double* dots = buf + 6 * n;
+  std::vector<double> hd(2);
+  efe_status st = EFE_OK;
+  auto fail = [&](cudaError_t e) {
+    o.err = std::string("octree Poisson: ") + cudaGetErrorString(e);
+    return EFE_ERR_CUDA;
+  };
+  auto dot = [&](const double* a, const double* b, double* out) {
+    k_oct_dot<<<(unsigned)std::min<long long>(oblk(n), 1024), 256, 0, s>>>(a, b, n, out);
+    note_launch();
+  };
+  int it = 0;
+  bool conv = false;
+  do {
+    k_oct_bc<<<oblk(n), 256, 0, s>>>(g, o.d_bnd, n, gB, ones);
+    note_launch();
+    if ((st = octree_apply(o, fq, 0.0, ones, F, 1, 0, s)) != EFE_OK) break;    // F = P^T int f N
+    if ((st = octree_apply(o, nullptr, 2.0, gB, Ap, 1, 0, s)) != EFE_OK) break; // K g_B
+    k_oct_cg_start<<<oblk(n), 256, 0, s>>>(F, Ap, o.d_bnd, n, r, p, u);
+    note_launch();
+    cudaMemsetAsync(dots, 0, sizeof(double) * 2, s);
+    dot(r, r, dots);
+    cudaError_t e = cudaMemcpyAsync(hd.data(), dots, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      st = fail(e);
+      break;
+    }
+    const double rr0 = hd[0];
+    double rr = rr0;
+    conv = rr0 == 0.0;
+    while (!conv && it < max_it) {
+      if ((st = octree_apply(o, nullptr, 2.0, p, Ap, 1, 1, s)) != EFE_OK) break;   // K_II p
+      cudaMemsetAsync(dots, 0, sizeof(double), s);
+      dot(p, Ap, dots);
+      e = cudaMemcpyAsync(hd.data(), dots, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess || !(hd[0] > 0.0)) {
+        if (e != cudaSuccess) st = fail(e);
+        else { o.err = "octree Poisson: the operator is not positive definite"; st = EFE_ERR_NOT_SPD; }
+        break;
+      }
+      const double alpha = rr / hd[0];
+      k_oct_cg_step<<<oblk(n), 256, 0, s>>>(u, r, p, Ap, alpha, n);
+      note_launch();
+      cudaMemsetAsync(dots + 1, 0, sizeof(double), s);
+      dot(r, r, dots + 1);
+      e = cudaMemcpyAsync(hd.data() + 1, dots + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        st = fail(e);
+        break;
+      }
+      const double rr_new = hd[1];
+      ++it;
+      conv = std::sqrt(rr_new) <= tol * std::sqrt(rr0);
+      k_oct_cg_dir<<<oblk(n), 256, 0, s>>>(p, r, rr_new / rr, n);
+      note_launch();
+      rr = rr_new;
+    }
+    if (st != EFE_OK) break;
+    k_oct_cg_finish<<<oblk(n), 256, 0, s>>>(u, g, o.d_bnd, n);
+    note_launch();
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) st = fail(e);
+  } while (false);
+  cudaFree(buf);
+  if (iters) *iters = it;
+  if (st == EFE_OK && !conv) {
+    o.err = "octree Poisson: no convergence within max_it";
+    st = EFE_ERR_CG_NOCONV;
+  }
+  return st;
+}
+
+}  // namespace efe
+
+extern "C" {
+
+efe_status efe_octree_poisson(efe_octree* oct, const double* f_q_dev, const double* g_free_dev, double* u_dev,
+                              double tol, int32_t max_it, int32_t* iters_host, void* stream) {
+  if (!oct || !f_q_dev || !g_free_dev || !u_dev || !(tol > 0.0) || max_it < 1) return EFE_ERR_ARG;
+  int its = 0;
+  efe_status st = efe::octree_poisson(oct->o, f_q_dev, g_free_dev, u_dev, tol, max_it, &its,
+                                      reinterpret_cast<cudaStream_t>(stream));
+  if (iters_host) *iters_host = its;
+  return st;
 }
 
 }  // extern "C"

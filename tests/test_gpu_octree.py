@@ -106,3 +106,32 @@ def test_octree_larger_mesh_properties():
     o.apply(torch.full_like(vq, 0.7), one, V1, kin=0.0)
     assert abs(V1.sum().item() - 0.7 * 16.0 ** 3) < 1e-9 * 16.0 ** 3
     o.close()
+
+
+def test_octree_poisson_matches_oracle():
+    """-lap u = f for a Gaussian bump on a vertex of 1-bohr cells, the eight cells
+    around it refined (the oracle's local-refinement case): the CUDA conjugate
+    gradients against the oracle's sparse direct solve of the same constrained
+    system, node by node (1e-9)."""
+    from oracle.octree import OctreeMesh
+    from paper_2210_14421_gb300 import Octree
+    c0, s0 = np.array([1.0, 1.0, 1.0]), 0.25
+
+    def ex(x):
+        return np.exp(-np.sum((x - c0) ** 2, axis=-1) / (2 * s0 * s0))
+
+    def f(x):
+        r2 = np.sum((x - c0) ** 2, axis=-1)
+        return (3 / s0 ** 2 - r2 / s0 ** 4) * ex(x)
+
+    ref_cells = [(i, j, k) for i in (0, 1) for j in (0, 1) for k in (0, 1)]
+    m = OctreeMesh([0, 0, 0], [3, 3, 3], 3, 3, ref_cells)
+    u_ref, _ = m.solve_poisson(f, ex)
+    o = Octree([0, 0, 0], [3, 3, 3], 3, 3, 5, ref_cells)
+    fx, qx, _ = o.coords()
+    u, its = o.poisson(torch.from_numpy(f(qx)).cuda(), torch.from_numpy(ex(fx)).cuda(), tol=1e-13, max_it=20000)
+    pos = {k: j for j, k in enumerate(_key(m.nodes[m.free]))}
+    perm = np.array([pos[k] for k in _key(fx)])
+    assert its > 0
+    assert np.max(np.abs(u.cpu().numpy() - u_ref[perm])) <= 1e-9 * np.max(np.abs(u_ref))
+    o.close()
