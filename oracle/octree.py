@@ -14,6 +14,12 @@ coarse leaf without being one of its nodes is hanging: its value is the coarse
 leaf's interpolant there, u(x_h) = sum_j N^C_j(x_h) u_j over the coarse leaf's
 nodes, which are never hanging (one level).  The constrained space is
 u_all = P u_free; operators are P^T K P.
+
+Reading O2 (the paper's Loewdin transform needs a diagonal mass; with hanging
+nodes P^T M P is not diagonal): the mass of the constrained space is the
+row-sum lumping of P^T M_GLL P, i.e. P^T m_all with m_all the GLL-lumped
+weights of all nodes; it integrates constants exactly and reduces to the
+rectilinear lumped mass without refinement.
 """
 from __future__ import annotations
 
@@ -129,6 +135,27 @@ class OctreeMesh:
         K_all = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                               shape=(self.n_all, self.n_all))
         return (self.P.T @ K_all @ self.P).tocsr(), self.P.T @ F
+
+    def lumped_mass(self):
+        """Diagonal mass of the constrained space (reading O2): the row sums of
+        P^T M_GLL P, M_GLL the GLL-lumped mass of all nodes (Sec. "Spectral finite
+        elements": diagonal mass from GLL collocation); since every row of P sums
+        to one these are P^T m_all."""
+        _, w = gauss_lobatto(self.p)
+        w3 = w[self.loc[:, 0]] * w[self.loc[:, 1]] * w[self.loc[:, 2]]
+        m_all = np.zeros(self.n_all)
+        for li, (x0, h, _) in enumerate(self.leaves):
+            np.add.at(m_all, self.conn[li], w3 * np.prod(h) / 8.0)
+        return self.P.T @ m_all
+
+    def hbar(self, vq, kin: float = 1.0):
+        """The Loewdin-scaled Hamiltonian on the interior free nodes,
+        D H_II D with D = M^-1/2 of lumped_mass (Eq. TDKSDiscrete2 on the
+        locally refined mesh)."""
+        I = np.where(~self.boundary_free)[0]
+        d = 1.0 / np.sqrt(self.lumped_mass()[I])
+        H = self.hamiltonian(vq, kin)[I][:, I]
+        return sp.diags(d) @ H @ sp.diags(d)
 
     def quad_points(self):
         """Physical Gauss-Legendre points of every leaf, (n_leaves, nq, 3), in the
