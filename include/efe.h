@@ -432,9 +432,12 @@ efe_status efe_octree_coords(const efe_octree* oct, double* free_xyz_host, doubl
  * locally refined mesh): K the stiffness int grad N . grad N, V the potential
  * matrix int v N N with v given at every leaf's Gauss-Legendre points (vq_dev:
  * device [n_leaves][n_q]).  X_dev, Y_dev: device [n_free][n_cols] doubles
- * (real columns, 1 <= n_cols <= 65535).  mask_boundary != 0 applies the
+ * (real columns, 1 <= n_cols <= 65535).  mask_boundary 1 applies the
  * Dirichlet restriction: boundary entries of X read as 0 and boundary rows of
- * Y are 0.  Three stages (gather through P, per-leaf operator scatter-added
+ * Y are 0; mask_boundary 2 gives the Loewdin-scaled operator on top of it,
+ * Y = D P^T (kin K/2 + V) P D X (Eq. TDKSDiscrete2) with D = mask / sqrt(m),
+ * m the lumped mass of the constrained space: the row sums of P^T M_GLL P,
+ * i.e. P^T m_all with m_all the GLL-lumped weights of all nodes.  Three stages (gather through P, per-leaf operator scatter-added
  * over all nodes, scatter through P^T); stream-ordered; the first call with
  * more columns than before allocates scratch (2 n_all n_cols doubles).
  * Errors: EFE_ERR_ARG, EFE_ERR_NOMEM, EFE_ERR_CUDA. */

@@ -401,15 +401,18 @@ class Octree:
             raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
         return fx, qx, bd.astype(bool)
 
-    def apply(self, vq, X, Y, kin: float = 1.0, mask_boundary: bool = False):
-        """Y = P^T (kin K/2 + V) P X; vq device [n_leaves, n_q], X, Y device [n_free, n_cols] float64."""
+    def apply(self, vq, X, Y, kin: float = 1.0, mask_boundary: bool = False, lowdin: bool = False):
+        """Y = P^T (kin K/2 + V) P X (lowdin: D P^T (kin K/2 + V) P D X on the interior, D the
+        inverse square root of the lumped constrained mass); vq device [n_leaves, n_q],
+        X, Y device [n_free, n_cols] float64."""
         import torch
         for t in (vq, X, Y):
             assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
         assert vq.numel() == self.n_leaves * self.n_q
         assert X.dim() == 2 and X.shape[0] == self.n_free and tuple(Y.shape) == tuple(X.shape)
-        st = lib().efe_octree_apply(self.h, _ptr(vq), float(kin), _ptr(X), _ptr(Y), int(X.shape[1]),
-                                    int(bool(mask_boundary)), _stream())
+        mode = 2 if lowdin else int(bool(mask_boundary))
+        st = lib().efe_octree_apply(self.h, _ptr(vq), float(kin), _ptr(X), _ptr(Y), int(X.shape[1]), mode,
+                                    _stream())
         if st != EFE_OK:
             raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
         return Y

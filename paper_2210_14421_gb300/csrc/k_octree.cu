@@ -47,6 +47,7 @@ struct Octree {
   std::vector<double> geo;                  // host copies of the device arrays
   std::vector<int> conn;
   std::vector<unsigned char> bnd;
+  std::vector<double> D;                    // [n_free] mask / sqrt(lumped constrained mass)
   std::vector<long long> rs;                // host copy of P (CSR over all nodes)
   std::vector<int> col;
   std::vector<double> val;
@@ -56,12 +57,13 @@ struct Octree {
   int* d_col = nullptr;                     // free index per entry
   double* d_val = nullptr;                  // weight per entry
   unsigned char* d_bnd = nullptr;           // [n_free] 1 on the domain boundary
+  double* d_D = nullptr;                    // [n_free] Loewdin scaling
   double* d_xall = nullptr;                 // [n_all][cols] scratch
   double* d_yall = nullptr;
   long long ws_cols = 0;
   ~Octree() {
     for (void* q : {(void*)d_geo, (void*)d_conn, (void*)d_rs, (void*)d_col, (void*)d_val, (void*)d_bnd,
-                    (void*)d_xall, (void*)d_yall})
+                    (void*)d_D, (void*)d_xall, (void*)d_yall})
       if (q) cudaFree(q);
   }
 };
@@ -69,10 +71,11 @@ struct Octree {
 namespace {
 
 // x_all[n][c] = sum_k val_k x_free[col_k][c] over row n of P (boundary free values as 0 when masked)
+// (with scale: x_free scaled by scale[f] first, the Loewdin D that is 0 on the boundary)
 __global__ void k_oct_expand(const long long* __restrict__ rs, const int* __restrict__ col,
                              const double* __restrict__ val, const unsigned char* __restrict__ bnd,
-                             const double* __restrict__ xf, long long n_all, int ncols, int mask,
-                             double* __restrict__ xa) {
+                             const double* __restrict__ scale, const double* __restrict__ xf, long long n_all,
+                             int ncols, int mask, double* __restrict__ xa) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= n_all * ncols) return;
   const long long n = idx / ncols;
@@ -81,16 +84,17 @@ __global__ void k_oct_expand(const long long* __restrict__ rs, const int* __rest
   for (long long k = rs[n]; k < rs[n + 1]; ++k) {
     const int f = col[k];
     if (mask && bnd[f]) continue;
-    v += val[k] * xf[(long long)f * ncols + c];
+    v += val[k] * (scale ? scale[f] : 1.0) * xf[(long long)f * ncols + c];
   }
   xa[idx] = v;
 }
 
 // y_free[col_k][c] += val_k y_all[n][c] over row n of P (boundary rows skipped when masked)
+// (with scale: each contribution scaled by scale[f])
 __global__ void k_oct_reduce(const long long* __restrict__ rs, const int* __restrict__ col,
                              const double* __restrict__ val, const unsigned char* __restrict__ bnd,
-                             const double* __restrict__ ya, long long n_all, int ncols, int mask,
-                             double* __restrict__ yf) {
+                             const double* __restrict__ scale, const double* __restrict__ ya, long long n_all,
+                             int ncols, int mask, double* __restrict__ yf) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= n_all * ncols) return;
   const long long n = idx / ncols;
@@ -99,7 +103,7 @@ __global__ void k_oct_reduce(const long long* __restrict__ rs, const int* __rest
   for (long long k = rs[n]; k < rs[n + 1]; ++k) {
     const int f = col[k];
     if (mask && bnd[f]) continue;
-    atomicAdd(&yf[(long long)f * ncols + c], val[k] * y);
+    atomicAdd(&yf[(long long)f * ncols + c], val[k] * (scale ? scale[f] : 1.0) * y);
   }
 }
 
@@ -441,6 +445,20 @@ static efe_status octree_host(Octree& o, const double* lo, const double* hi, int
       if (std::fabs(xyz[3 * nd + a] - lo[a]) < tol || std::fabs(xyz[3 * nd + a] - hi[a]) < tol) bnd[f] = 1;
     }
   }
+  // lumped mass of the constrained space: P^T m_all, m_all the GLL-lumped weights of all nodes
+  {
+    std::vector<double> m_all((size_t)n_all, 0.0);
+    for (size_t li = 0; li < leaves.size(); ++li) {
+      const double J = leaves[li].h[0] * leaves[li].h[1] * leaves[li].h[2] / 8.0;
+      for (int l = 0; l < nn; ++l)
+        m_all[conn[li * nn + l]] += wl[l % P1] * wl[(l / P1) % P1] * wl[l / (P1 * P1)] * J;
+    }
+    std::vector<double> m_c((size_t)n_free, 0.0);
+    for (long long nd = 0; nd < n_all; ++nd)
+      for (long long k = rs[nd]; k < rs[nd + 1]; ++k) m_c[col[k]] += val[k] * m_all[nd];
+    o.D.assign((size_t)n_free, 0.0);
+    for (long long f = 0; f < n_free; ++f) o.D[f] = bnd[f] ? 0.0 : 1.0 / std::sqrt(m_c[f]);
+  }
   // tables
   std::vector<double> xg(n_quad), wg(n_quad), B(n_quad * P1), D(n_quad * P1);
   gauss_legendre(n_quad, xg.data(), wg.data());
@@ -509,6 +527,7 @@ static efe_status octree_build(Octree& o, const double* lo, const double* hi, in
   if (e == cudaSuccess) e = up(o.d_col, col);
   if (e == cudaSuccess) e = up(o.d_val, val);
   if (e == cudaSuccess) e = up(o.d_bnd, bnd);
+  if (e == cudaSuccess) e = up(o.d_D, o.D);
   if (e != cudaSuccess) {
     o.err = std::string("octree set-up: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? EFE_ERR_NOMEM : EFE_ERR_CUDA;
@@ -600,7 +619,8 @@ efe_status efe_octree_coords(const efe_octree* oct, double* free_xyz_host, doubl
 
 efe_status efe_octree_apply(efe_octree* oct, const double* vq_dev, double kin, const double* X_dev, double* Y_dev,
                             int64_t n_cols, int32_t mask_boundary, void* stream) {
-  if (!oct || !vq_dev || !X_dev || !Y_dev || n_cols < 1 || n_cols > 65535) return EFE_ERR_ARG;
+  if (!oct || !vq_dev || !X_dev || !Y_dev || n_cols < 1 || n_cols > 65535 || mask_boundary < 0 || mask_boundary > 2)
+    return EFE_ERR_ARG;
   return efe::octree_apply(oct->o, vq_dev, kin, X_dev, Y_dev, n_cols, mask_boundary,
                            reinterpret_cast<cudaStream_t>(stream));
 }
@@ -626,16 +646,18 @@ efe_status octree_apply(Octree& o, const double* vq_dev, double kin, const doubl
   }
   const int nc = (int)n_cols;
   const long long N = o.n_all * n_cols;
-  efe::k_oct_expand<<<efe::oblk(N), 256, 0, s>>>(o.d_rs, o.d_col, o.d_val, o.d_bnd, X_dev, o.n_all, nc,
-                                                 mask_boundary, o.d_xall);
+  const double* scale = mask_boundary == 2 ? o.d_D : nullptr;   // Loewdin: D = mask / sqrt(m_c) both sides
+  const int mask = mask_boundary != 0;
+  efe::k_oct_expand<<<efe::oblk(N), 256, 0, s>>>(o.d_rs, o.d_col, o.d_val, o.d_bnd, scale, X_dev, o.n_all, nc,
+                                                 mask, o.d_xall);
   efe::note_launch();
   cudaMemsetAsync(o.d_yall, 0, sizeof(double) * N, s);
   dim3 grid((unsigned)o.n_leaves, (unsigned)nc);
   efe::k_oct_apply<<<grid, efe::kOctThreads, 0, s>>>(o.tab, o.d_geo, o.d_conn, vq_dev, kin, o.d_xall, nc, o.d_yall);
   efe::note_launch();
   cudaMemsetAsync(Y_dev, 0, sizeof(double) * o.n_free * n_cols, s);
-  efe::k_oct_reduce<<<efe::oblk(N), 256, 0, s>>>(o.d_rs, o.d_col, o.d_val, o.d_bnd, o.d_yall, o.n_all, nc,
-                                                 mask_boundary, Y_dev);
+  efe::k_oct_reduce<<<efe::oblk(N), 256, 0, s>>>(o.d_rs, o.d_col, o.d_val, o.d_bnd, scale, o.d_yall, o.n_all, nc,
+                                                 mask, Y_dev);
   efe::note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

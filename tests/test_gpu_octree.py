@@ -135,3 +135,32 @@ def test_octree_poisson_matches_oracle():
     assert its > 0
     assert np.max(np.abs(u.cpu().numpy() - u_ref[perm])) <= 1e-9 * np.max(np.abs(u_ref))
     o.close()
+
+
+@pytest.mark.parametrize("name", ["p3_box", "p5_corner"])
+def test_octree_loewdin_apply_matches_oracle(name):
+    """The Loewdin-scaled operator D P^T H P D on the interior free nodes (D from
+    the lumped constrained mass) against the oracle's OctreeMesh.hbar."""
+    from oracle.octree import OctreeMesh
+    from paper_2210_14421_gb300 import Octree
+    lo, hi, nc, p, nq, ref = MESHES[name]
+    m = OctreeMesh(lo, hi, nc, p, ref, n_quad=nq)
+    o = Octree(lo, hi, nc, p, nq, ref)
+    fx, qx, _ = o.coords()
+    pos = {k: j for j, k in enumerate(_key(m.nodes[m.free]))}
+    perm = np.array([pos[k] for k in _key(fx)])
+    vq = 0.5 * np.sum(qx ** 2, axis=2)
+    X = np.random.default_rng(11).standard_normal((o.n_free, 2))
+    Xo = np.zeros_like(X)
+    Xo[perm] = X
+    I = np.where(~m.boundary_free)[0]
+    Hb = m.hbar(vq, kin=1.0)
+    ref_y = np.zeros_like(Xo)
+    ref_y[I] = Hb @ Xo[I]
+    scale = np.zeros_like(Xo)
+    scale[I] = abs(Hb) @ np.abs(Xo[I])
+    Y = torch.zeros((o.n_free, 2), dtype=torch.float64, device="cuda")
+    o.apply(torch.from_numpy(np.ascontiguousarray(vq)).cuda(), torch.from_numpy(X).cuda(), Y, kin=1.0, lowdin=True)
+    got = Y.cpu().numpy()
+    assert np.max(np.abs(got - ref_y[perm]) - 1e-12 * scale[perm] - 1e-300) <= 0.0
+    o.close()
