@@ -157,6 +157,19 @@ class OctreeMesh:
         H = self.hamiltonian(vq, kin)[I][:, I]
         return sp.diags(d) @ H @ sp.diags(d)
 
+    def density(self, psi_bar, occ):
+        """rho at every leaf's Gauss-Legendre points, (n_leaves, nq), for orbitals
+        psi_bar (n_free, n_orb) complex in the Loewdin basis: psi = D psi_bar with
+        D = mask / sqrt(lumped_mass), rho = sum_a occ_a |sum_i N_i psi_a,i|^2
+        (Eq. rho on the locally refined mesh)."""
+        d = np.where(self.boundary_free, 0.0, 1.0 / np.sqrt(self.lumped_mass()))
+        psi_all = self.P @ (d[:, None] * psi_bar)
+        rho = np.zeros((len(self.leaves), len(self.wq)))
+        for li in range(len(self.leaves)):
+            vals = self.B @ psi_all[self.conn[li]]
+            rho[li] = np.abs(vals) ** 2 @ np.asarray(occ, float)
+        return rho
+
     def quad_points(self):
         """Physical Gauss-Legendre points of every leaf, (n_leaves, nq, 3), in the
         order of self.wq (first axis fastest)."""

@@ -137,3 +137,21 @@ def test_constrained_lumped_mass_and_loewdin_hamiltonian():
         assert abs(Hb - Hb.T).max() < 1e-13 * abs(Hb).max()
         lam.append(spla.eigsh(Hb, k=1, sigma=0, which="LM")[0][0])
     assert abs(lam[1] - 1.5) < 5e-5 and abs(lam[1] - 1.5) < abs(lam[0] - 1.5) / 5, lam
+
+
+def test_density_integrates_to_the_mass_quadratic_form():
+    """int rho = sum_a occ_a psi_a^H (P^T M P) psi_a with psi = D psi_bar, the
+    consistent mass taken from the Hamiltonian's potential part with v = 1 and
+    kin = 0 (an independent assembly); rho >= 0."""
+    m = OctreeMesh([0, 0, 0], [3, 2, 2], 3, 3, [(1, 0, 0), (2, 1, 1)])
+    rng = np.random.default_rng(5)
+    psi_bar = rng.standard_normal((len(m.free), 2)) + 1j * rng.standard_normal((len(m.free), 2))
+    occ = np.array([2.0, 1.0])
+    rho = m.density(psi_bar, occ)
+    assert rho.min() >= 0.0
+    w = np.stack([m.wq * np.prod(h) / 8.0 for _, h, _ in m.leaves])
+    d = np.where(m.boundary_free, 0.0, 1.0 / np.sqrt(m.lumped_mass()))
+    psi = d[:, None] * psi_bar
+    Mc = m.hamiltonian(np.ones(w.shape), kin=0.0)
+    ref = sum(occ[a] * np.real(np.conj(psi[:, a]) @ (Mc @ psi[:, a])) for a in range(2))
+    assert abs(np.sum(w * rho) - ref) < 1e-12 * ref
