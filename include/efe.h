@@ -455,6 +455,15 @@ efe_status efe_octree_apply(efe_octree* oct, const double* vq_dev, double kin, c
  * iterate), EFE_ERR_NOT_SPD, EFE_ERR_NOMEM, EFE_ERR_CUDA. */
 efe_status efe_octree_poisson(efe_octree* oct, const double* f_q_dev, const double* g_free_dev, double* u_dev,
                               double tol, int32_t max_it, int32_t* iters_host, void* stream);
+/* The density at every leaf's Gauss-Legendre points (the density of Sec. TDKS on
+ * the locally refined mesh) for orbitals in the Loewdin basis: psi = D psi_bar
+ * with D = mask / sqrt(m) (m the lumped constrained mass), rho = sum_a occ_a
+ * |sum_i N_i psi_a,i|^2.  psi_bar_dev: device complex128 [n_free][n_orb]
+ * (interleaved real and imaginary parts); occ_host: host [n_orb]; rho_dev:
+ * device [n_leaves][n_q].  Synchronises `stream`.  Errors: EFE_ERR_ARG,
+ * EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+efe_status efe_octree_density(efe_octree* oct, const double* psi_bar_dev, int32_t n_orb, const double* occ_host,
+                              double* rho_dev, void* stream);
 
 /* Host-only diagnostics of the electrostatic enrichment (no context, no device
  * work).  efe_atom_hartree_table: the atomic Hartree potentials that

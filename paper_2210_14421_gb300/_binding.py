@@ -27,7 +27,8 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_absorption_spectrum", "efe_power_spectrum", "efe_nuclear_enriched",
             "efe_hartree_enriched", "efe_octree_setup", "efe_octree_destroy", "efe_octree_last_error",
             "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply", "efe_octree_constraints",
-            "efe_atom_hartree_table", "efe_adaptive_cell_boxes", "efe_octree_poisson"]
+            "efe_atom_hartree_table", "efe_adaptive_cell_boxes", "efe_octree_poisson",
+            "efe_octree_density"]
 
 
 class MeshDesc(C.Structure):
@@ -119,6 +120,7 @@ def lib(path: str = LIB_PATH):
                                          C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), pdbl, pdbl,
                                          pdbl]
     L.efe_octree_poisson.argtypes = [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), vp]
+    L.efe_octree_density.argtypes = [vp, vp, i32, pdbl, vp, vp]
     L.efe_atom_hartree_table.argtypes = [C.POINTER(EnrichFn), i32, pdbl, i32, i32, dbl, pdbl, pdbl, pdbl, pdbl]
     L.efe_adaptive_cell_boxes.argtypes = [pdbl, pdbl, pdbl, i32, dbl, dbl, dbl, i32, dbl, i32, C.POINTER(i64), pdbl,
                                           i64]
@@ -431,6 +433,20 @@ class Octree:
         if st != EFE_OK:
             raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
         return u, its.value
+
+    def density(self, psi_bar, occ):
+        """rho at the leaves' GL points (device [n_leaves, n_q]) of Loewdin-basis orbitals
+        psi_bar (device complex128 [n_free, n_orb])."""
+        import torch
+        assert psi_bar.is_cuda and psi_bar.dtype == torch.complex128 and psi_bar.is_contiguous()
+        assert psi_bar.dim() == 2 and psi_bar.shape[0] == self.n_free
+        occ = np.ascontiguousarray(occ, dtype=np.float64)
+        assert len(occ) == psi_bar.shape[1]
+        rho = torch.zeros((self.n_leaves, self.n_q), dtype=torch.float64, device="cuda")
+        st = lib().efe_octree_density(self.h, _ptr(psi_bar), int(psi_bar.shape[1]), _dptr(occ), _ptr(rho), _stream())
+        if st != EFE_OK:
+            raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
+        return rho
 
     def close(self):
         if getattr(self, "h", None):

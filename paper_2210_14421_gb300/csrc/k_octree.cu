@@ -211,6 +211,50 @@ k_oct_apply(const OctTables T, const double* __restrict__ geo, const int* __rest
   }
 }
 
+// rho[leaf][q] = sum_a occ_a |psi_a(x_q)|^2 from x_all [n_all][2 n_orb] (re, im per orbital), one
+// block per leaf: each component interpolated to the GL points by three sum-factorisation passes.
+__global__ void __launch_bounds__(kOctThreads)
+k_oct_density(const OctTables T, const int* __restrict__ conn, const double* __restrict__ xa, int n_orb,
+              const double* __restrict__ occ, double* __restrict__ rho) {
+  __shared__ double x[kMaxP1 * kMaxP1 * kMaxP1];
+  __shared__ double A[kOctMaxQ1 * kMaxP1 * kMaxP1];
+  __shared__ double Bq[kOctMaxQ1 * kOctMaxQ1 * kMaxP1];
+  __shared__ double acc[kOctMaxQ1 * kOctMaxQ1 * kOctMaxQ1];
+  const int P1 = T.P1, Q = T.NQ1, nn = P1 * P1 * P1, nq = Q * Q * Q;
+  const long long leaf = blockIdx.x;
+  const int* cl = conn + leaf * nn;
+  const int ncols = 2 * n_orb;
+  for (int t = threadIdx.x; t < nq; t += blockDim.x) acc[t] = 0.0;
+  for (int col = 0; col < ncols; ++col) {
+    __syncthreads();
+    for (int l = threadIdx.x; l < nn; l += blockDim.x) x[l] = xa[(long long)cl[l] * ncols + col];
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q * P1 * P1; t += blockDim.x) {
+      const int q1 = t % Q, i2 = (t / Q) % P1, i3 = t / (Q * P1);
+      double s = 0.0;
+      for (int i1 = 0; i1 < P1; ++i1) s += T.B1[q1 * P1 + i1] * x[i1 + P1 * (i2 + P1 * i3)];
+      A[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q * Q * P1; t += blockDim.x) {
+      const int q1 = t % Q, q2 = (t / Q) % Q, i3 = t / (Q * Q);
+      double s = 0.0;
+      for (int i2 = 0; i2 < P1; ++i2) s += T.B1[q2 * P1 + i2] * A[q1 + Q * (i2 + P1 * i3)];
+      Bq[t] = s;
+    }
+    __syncthreads();
+    const double o = occ[col / 2];
+    for (int t = threadIdx.x; t < nq; t += blockDim.x) {
+      const int q1 = t % Q, q2 = (t / Q) % Q, q3 = t / (Q * Q);
+      double s = 0.0;
+      for (int i3 = 0; i3 < P1; ++i3) s += T.B1[q3 * P1 + i3] * Bq[q1 + Q * (q2 + Q * i3)];
+      acc[t] += o * s * s;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nq; t += blockDim.x) rho[leaf * nq + t] = acc[t];
+}
+
 unsigned oblk(long long n) { return (unsigned)((n + 255) / 256); }
 
 // *out += a . b (the caller zeroes *out)
@@ -767,6 +811,51 @@ efe_status efe_octree_poisson(efe_octree* oct, const double* f_q_dev, const doub
                                       reinterpret_cast<cudaStream_t>(stream));
   if (iters_host) *iters_host = its;
   return st;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+efe_status efe_octree_density(efe_octree* oct, const double* psi_bar_dev, int32_t n_orb, const double* occ_host,
+                              double* rho_dev, void* stream) {
+  if (!oct || !psi_bar_dev || !occ_host || !rho_dev || n_orb < 1 || 2 * n_orb > 65535) return EFE_ERR_ARG;
+  efe::Octree& o = oct->o;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const long long nc2 = 2LL * n_orb;
+  if (o.ws_cols < nc2) {
+    if (o.d_xall) cudaFree(o.d_xall);
+    if (o.d_yall) cudaFree(o.d_yall);
+    o.d_xall = o.d_yall = nullptr;
+    o.ws_cols = 0;
+    if (cudaMalloc(&o.d_xall, sizeof(double) * o.n_all * nc2) != cudaSuccess ||
+        cudaMalloc(&o.d_yall, sizeof(double) * o.n_all * nc2) != cudaSuccess) {
+      o.err = "octree density: out of device memory";
+      return EFE_ERR_NOMEM;
+    }
+    o.ws_cols = nc2;
+  }
+  double* d_occ = nullptr;
+  if (cudaMalloc(&d_occ, sizeof(double) * n_orb) != cudaSuccess) {
+    o.err = "octree density: out of device memory";
+    return EFE_ERR_NOMEM;
+  }
+  cudaMemcpyAsync(d_occ, occ_host, sizeof(double) * n_orb, cudaMemcpyHostToDevice, s);
+  const long long N = o.n_all * nc2;
+  efe::k_oct_expand<<<efe::oblk(N), 256, 0, s>>>(o.d_rs, o.d_col, o.d_val, o.d_bnd, o.d_D, psi_bar_dev, o.n_all,
+                                                 (int)nc2, 1, o.d_xall);
+  efe::note_launch();
+  efe::k_oct_density<<<(unsigned)o.n_leaves, efe::kOctThreads, 0, s>>>(o.tab, o.d_conn, o.d_xall, n_orb, d_occ,
+                                                                       rho_dev);
+  efe::note_launch();
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaFree(d_occ);
+  if (e != cudaSuccess) {
+    o.err = std::string("octree density: ") + cudaGetErrorString(e);
+    return EFE_ERR_CUDA;
+  }
+  return EFE_OK;
 }
 
 }  // extern "C"

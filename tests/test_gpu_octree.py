@@ -164,3 +164,26 @@ def test_octree_loewdin_apply_matches_oracle(name):
     got = Y.cpu().numpy()
     assert np.max(np.abs(got - ref_y[perm]) - 1e-12 * scale[perm] - 1e-300) <= 0.0
     o.close()
+
+
+@pytest.mark.parametrize("name", ["p3_box", "p5_corner", "p2_block"])
+def test_octree_density_matches_oracle(name):
+    """rho at the leaves' Gauss-Legendre points from Loewdin-basis orbitals against
+    OctreeMesh.density (1e-12 relative)."""
+    from oracle.octree import OctreeMesh
+    from paper_2210_14421_gb300 import Octree
+    lo, hi, nc, p, nq, ref = MESHES[name]
+    m = OctreeMesh(lo, hi, nc, p, ref, n_quad=nq)
+    o = Octree(lo, hi, nc, p, nq, ref)
+    fx, _, _ = o.coords()
+    pos = {k: j for j, k in enumerate(_key(m.nodes[m.free]))}
+    perm = np.array([pos[k] for k in _key(fx)])
+    rng = np.random.default_rng(3)
+    psi = rng.standard_normal((o.n_free, 3)) + 1j * rng.standard_normal((o.n_free, 3))
+    occ = np.array([2.0, 2.0, 1.0])
+    rho = o.density(torch.from_numpy(psi).cuda(), occ).cpu().numpy()
+    po = np.zeros_like(psi)
+    po[perm] = psi
+    ref_rho = m.density(po, occ)
+    assert np.max(np.abs(rho - ref_rho)) <= 1e-12 * np.max(np.abs(ref_rho))
+    o.close()
