@@ -704,6 +704,25 @@ def run_next_rows(args):
     out["octree_apply"] = {"mesh": "24^3 coarse cells of degree 4 on a 24-bohr cube, central 6^3 refined",
                            "n_free": o.n_free, "n_hanging": o.n_hanging, "n_leaves": o.n_leaves, "cols": 88,
                            "setup_s": round(t_oct, 3), "ms_per_apply": round(e0.elapsed_time(e1) / 5, 3)}
+    try:
+        Yl = torch.zeros_like(X)
+        o.apply(vq, X, Yl, lowdin=True)
+        e0.record()
+        for _ in range(5):
+            o.apply(vq, X, Yl, lowdin=True)
+        e1.record()
+        torch.cuda.synchronize()
+        out["octree_apply"]["ms_per_loewdin_apply"] = round(e0.elapsed_time(e1) / 5, 3)
+        psi = torch.randn((o.n_free, 44), dtype=torch.complex128, device="cuda")
+        (_, t_rho) = timed(lambda: o.density(psi, np.full(44, 2.0)))
+        out["octree_density"] = {"orbitals": 44, "ms": round(1e3 * t_rho, 2)}
+        fx, _, _ = o.coords()
+        g_b = torch.from_numpy(np.zeros(o.n_free)).cuda()
+        fq = torch.from_numpy(np.exp(-np.sum(qx ** 2, axis=2))).cuda()
+        ((u, its), t_p) = timed(lambda: o.poisson(fq, g_b, tol=1e-10, max_it=20000))
+        out["octree_poisson"] = {"cg_iterations": its, "s": round(t_p, 3), "tol": 1e-10}
+    except Exception as e:   # keep the numbers above
+        out["octree_error"] = str(e)[:200]
     o.close()
     print(json.dumps(out))
     return 0
