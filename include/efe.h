@@ -449,7 +449,8 @@ efe_status efe_octree_apply(efe_octree* oct, const double* vq_dev, double kin, c
  * K_II u_I = F_I - K_IB g_B in the constrained space, F = P^T int f N with f at
  * every leaf's Gauss-Legendre points (f_q_dev: device [n_leaves][n_q]); g_free_dev
  * and u_dev: device [n_free] (g read on the boundary free nodes only).
- * Conjugate gradients on the constrained stiffness to |r| <= tol |r_0|, at most
+ * Conjugate gradients on the constrained stiffness, Jacobi-preconditioned by its
+ * diagonal (assembled at set-up), to |r| <= tol |r_0|, at most
  * max_it iterations (*iters_host receives the count); synchronises `stream`
  * every iteration.  Errors: EFE_ERR_ARG, EFE_ERR_CG_NOCONV (u holds the last
  * iterate), EFE_ERR_NOT_SPD, EFE_ERR_NOMEM, EFE_ERR_CUDA. */

@@ -48,6 +48,7 @@ struct Octree {
   std::vector<int> conn;
   std::vector<unsigned char> bnd;
   std::vector<double> D;                    // [n_free] mask / sqrt(lumped constrained mass)
+  std::vector<double> Kdiag;                // [n_free] diagonal of P^T K P (Jacobi preconditioner)
   std::vector<long long> rs;                // host copy of P (CSR over all nodes)
   std::vector<int> col;
   std::vector<double> val;
@@ -58,12 +59,13 @@ struct Octree {
   double* d_val = nullptr;                  // weight per entry
   unsigned char* d_bnd = nullptr;           // [n_free] 1 on the domain boundary
   double* d_D = nullptr;                    // [n_free] Loewdin scaling
+  double* d_Kdiag = nullptr;                // [n_free] diagonal of the constrained stiffness
   double* d_xall = nullptr;                 // [n_all][cols] scratch
   double* d_yall = nullptr;
   long long ws_cols = 0;
   ~Octree() {
     for (void* q : {(void*)d_geo, (void*)d_conn, (void*)d_rs, (void*)d_col, (void*)d_val, (void*)d_bnd,
-                    (void*)d_D, (void*)d_xall, (void*)d_yall})
+                    (void*)d_D, (void*)d_Kdiag, (void*)d_xall, (void*)d_yall})
       if (q) cudaFree(q);
   }
 };
@@ -282,16 +284,26 @@ __global__ void k_oct_bc(const double* __restrict__ g, const unsigned char* __re
   ones[i] = 1.0;
 }
 
-// r = p = F - y inside, 0 on the boundary; u = 0
+// r = F - y inside, 0 on the boundary; z = p = r / diag; u = 0
 __global__ void k_oct_cg_start(const double* __restrict__ F, const double* __restrict__ y,
-                               const unsigned char* __restrict__ bnd, long long n, double* __restrict__ r,
-                               double* __restrict__ p, double* __restrict__ u) {
+                               const unsigned char* __restrict__ bnd, const double* __restrict__ diag, long long n,
+                               double* __restrict__ r, double* __restrict__ z, double* __restrict__ p,
+                               double* __restrict__ u) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double v = bnd[i] ? 0.0 : F[i] - y[i];
   r[i] = v;
-  p[i] = v;
+  z[i] = bnd[i] ? 0.0 : v / diag[i];
+  p[i] = z[i];
   u[i] = 0.0;
+}
+
+// z = r / diag inside (0 on the boundary)
+__global__ void k_oct_precond(const double* __restrict__ r, const double* __restrict__ diag,
+                              const unsigned char* __restrict__ bnd, long long n, double* __restrict__ z) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  z[i] = bnd[i] ? 0.0 : r[i] / diag[i];
 }
 
 // u += alpha p, r -= alpha Ap
@@ -303,7 +315,7 @@ __global__ void k_oct_cg_step(double* __restrict__ u, double* __restrict__ r, co
   r[i] -= alpha * Ap[i];
 }
 
-// p = r + beta p
+// p = z + beta p
 __global__ void k_oct_cg_dir(double* __restrict__ p, const double* __restrict__ r, double beta, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -523,6 +535,36 @@ static efe_status octree_host(Octree& o, const double* lo, const double* hi, int
       o.tab.K1[i * P1 + j] = k;
       o.tab.M1[i * P1 + j] = m;
     }
+  // diagonal of the constrained stiffness P^T K P: per leaf, sum over local pairs whose P rows share a free index
+  o.Kdiag.assign((size_t)n_free, 0.0);
+  {
+    std::vector<std::vector<std::pair<int, double>>> rows(nn);
+    for (size_t li = 0; li < leaves.size(); ++li) {
+      const double hx = leaves[li].h[0], hy = leaves[li].h[1], hz = leaves[li].h[2];
+      const double ax = hy * hz / (2.0 * hx), ay = hx * hz / (2.0 * hy), az = hx * hy / (2.0 * hz);
+      for (int l = 0; l < nn; ++l) {
+        rows[l].clear();
+        const int nd = conn[li * nn + l];
+        for (long long k = rs[nd]; k < rs[nd + 1]; ++k) rows[l].push_back({col[k], val[k]});
+      }
+      auto Ke = [&](int l, int m) {
+        const int i1 = l % P1, i2 = (l / P1) % P1, i3 = l / (P1 * P1);
+        const int j1 = m % P1, j2 = (m / P1) % P1, j3 = m / (P1 * P1);
+        const double* K1 = o.tab.K1;
+        const double* M1 = o.tab.M1;
+        return ax * K1[i1 * P1 + j1] * M1[i2 * P1 + j2] * M1[i3 * P1 + j3] +
+               ay * M1[i1 * P1 + j1] * K1[i2 * P1 + j2] * M1[i3 * P1 + j3] +
+               az * M1[i1 * P1 + j1] * M1[i2 * P1 + j2] * K1[i3 * P1 + j3];
+      };
+      // group the leaf's (local node, weight) pairs by free index: diag[f] += sum over pairs of w w' K_e
+      std::map<int, std::vector<std::pair<int, double>>> by_f;
+      for (int l = 0; l < nn; ++l)
+        for (const auto& a : rows[l]) by_f[a.first].push_back({l, a.second});
+      for (const auto& kv : by_f)
+        for (const auto& a : kv.second)
+          for (const auto& b : kv.second) o.Kdiag[kv.first] += a.second * b.second * Ke(a.first, b.first);
+    }
+  }
   std::vector<double> geo(6 * leaves.size());
   o.quad_xyz.assign(leaves.size() * (size_t)o.nq * 3, 0.0);
   for (size_t li = 0; li < leaves.size(); ++li) {
@@ -572,6 +614,7 @@ static efe_status octree_build(Octree& o, const double* lo, const double* hi, in
   if (e == cudaSuccess) e = up(o.d_val, val);
   if (e == cudaSuccess) e = up(o.d_bnd, bnd);
   if (e == cudaSuccess) e = up(o.d_D, o.D);
+  if (e == cudaSuccess) e = up(o.d_Kdiag, o.Kdiag);
   if (e != cudaSuccess) {
     o.err = std::string("octree set-up: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? EFE_ERR_NOMEM : EFE_ERR_CUDA;
@@ -713,17 +756,19 @@ efe_status octree_apply(Octree& o, const double* vq_dev, double kin, const doubl
 
 // -lap u = f with u = g on the boundary free nodes: K_II u_I = F_I - K_IB g_B, F = P^T int f N
 // (F = P^T V P 1 with v = f: the constants are in the constrained space and the basis sums to 1),
-// by conjugate gradients to |r| <= tol |F_I - K_IB g_B|.
+// by conjugate gradients with the Jacobi preconditioner (the diagonal of P^T K P) to
+// |r| <= tol |F_I - K_IB g_B|.
 efe_status octree_poisson(Octree& o, const double* fq, const double* g, double* u, double tol, int max_it,
                           int* iters, cudaStream_t s) {
   const long long n = o.n_free;
   double* buf = nullptr;
-  if (cudaMalloc(&buf, sizeof(double) * (6 * n + 4)) != cudaSuccess) {
+  if (cudaMalloc(&buf, sizeof(double) * (7 * n + 4)) != cudaSuccess) {
     o.err = "octree Poisson: out of device memory";
     return EFE_ERR_NOMEM;
   }
   double *gB = buf, *ones = buf + n, *F = buf + 2 * n, *r = buf + 3 * n, *p = buf + 4 * n, *Ap = buf + 5 * n;
-  double* dots = buf + 6 * n;
+  double* z = buf + 6 * n;
+  double* dots = buf + 7 * n;
   std::vector<double> hd(2);
   efe_status st = EFE_OK;
   auto fail = [&](cudaError_t e) {
@@ -741,18 +786,20 @@ efe_status octree_poisson(Octree& o, const double* fq, const double* g, double* 
     note_launch();
     if ((st = octree_apply(o, fq, 0.0, ones, F, 1, 0, s)) != EFE_OK) break;    // F = P^T int f N
     if ((st = octree_apply(o, nullptr, 2.0, gB, Ap, 1, 0, s)) != EFE_OK) break; // K g_B
-    k_oct_cg_start<<<oblk(n), 256, 0, s>>>(F, Ap, o.d_bnd, n, r, p, u);
+    k_oct_cg_start<<<oblk(n), 256, 0, s>>>(F, Ap, o.d_bnd, o.d_Kdiag, n, r, z, p, u);
     note_launch();
-    cudaMemsetAsync(dots, 0, sizeof(double) * 2, s);
+    cudaMemsetAsync(dots, 0, sizeof(double) * 4, s);
     dot(r, r, dots);
-    cudaError_t e = cudaMemcpyAsync(hd.data(), dots, sizeof(double), cudaMemcpyDeviceToHost, s);
+    dot(r, z, dots + 2);
+    hd.resize(4);
+    cudaError_t e = cudaMemcpyAsync(hd.data(), dots, sizeof(double) * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
       st = fail(e);
       break;
     }
     const double rr0 = hd[0];
-    double rr = rr0;
+    double rz = hd[2];
     conv = rr0 == 0.0;
     while (!conv && it < max_it) {
       if ((st = octree_apply(o, nullptr, 2.0, p, Ap, 1, 1, s)) != EFE_OK) break;   // K_II p
@@ -765,23 +812,26 @@ efe_status octree_poisson(Octree& o, const double* fq, const double* g, double* 
         else { o.err = "octree Poisson: the operator is not positive definite"; st = EFE_ERR_NOT_SPD; }
         break;
       }
-      const double alpha = rr / hd[0];
+      const double alpha = rz / hd[0];
       k_oct_cg_step<<<oblk(n), 256, 0, s>>>(u, r, p, Ap, alpha, n);
       note_launch();
-      cudaMemsetAsync(dots + 1, 0, sizeof(double), s);
+      k_oct_precond<<<oblk(n), 256, 0, s>>>(r, o.d_Kdiag, o.d_bnd, n, z);
+      note_launch();
+      cudaMemsetAsync(dots + 1, 0, sizeof(double) * 3, s);
       dot(r, r, dots + 1);
-      e = cudaMemcpyAsync(hd.data() + 1, dots + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
+      dot(r, z, dots + 3);
+      e = cudaMemcpyAsync(hd.data() + 1, dots + 1, sizeof(double) * 3, cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) {
         st = fail(e);
         break;
       }
-      const double rr_new = hd[1];
+      const double rr_new = hd[1], rz_new = hd[3];
       ++it;
       conv = std::sqrt(rr_new) <= tol * std::sqrt(rr0);
-      k_oct_cg_dir<<<oblk(n), 256, 0, s>>>(p, r, rr_new / rr, n);
+      k_oct_cg_dir<<<oblk(n), 256, 0, s>>>(p, z, rz_new / rz, n);
       note_launch();
-      rr = rr_new;
+      rz = rz_new;
     }
     if (st != EFE_OK) break;
     k_oct_cg_finish<<<oblk(n), 256, 0, s>>>(u, g, o.d_bnd, n);
