@@ -10,9 +10,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-# GPU test modules of components that have not yet run on a device: they run
-# after the rest of the suite, so that under -x a failure there cannot hide the
-# results of the established tests.
+# GPU test modules of the newest components run after the rest of the suite, so
+# that under -x a failure there cannot hide the results of the established tests.
 RUN_LAST = ("test_gpu_electrostatic.py", "test_gpu_octree.py")
 
 
