@@ -465,6 +465,17 @@ efe_status efe_octree_poisson(efe_octree* oct, const double* f_q_dev, const doub
  * EFE_ERR_NOMEM, EFE_ERR_CUDA. */
 efe_status efe_octree_density(efe_octree* oct, const double* psi_bar_dev, int32_t n_orb, const double* occ_host,
                               double* rho_dev, void* stream);
+/* psi_bar <- exp(-i dt Hbar) psi_bar on the locally refined mesh, Hbar the
+ * Loewdin-scaled operator of efe_octree_apply (mode 2) with kin and v at the
+ * leaves' Gauss-Legendre points (vq_dev [n_leaves][n_q]): per complex column,
+ * k Lanczos steps of the three-term recurrence (Eq. AdaptiveKrylov with a fixed
+ * Krylov dimension), the exponential of the k x k tridiagonal matrix from its
+ * eigendecomposition, psi_bar = |psi_bar| Q_k y.  psi_bar_dev: device complex128
+ * [n_free][n_cols], in place (boundary rows set to 0).  Allocates (k + 1) n_free
+ * n_cols complex scratch per call; synchronises `stream` every step.  Errors:
+ * EFE_ERR_ARG (k outside [1, 64]), EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+efe_status efe_octree_kexp(efe_octree* oct, const double* vq_dev, double kin, double* psi_bar_dev, int32_t n_cols,
+                           double dt, int32_t k, void* stream);
 
 /* Host-only diagnostics of the electrostatic enrichment (no context, no device
  * work).  efe_atom_hartree_table: the atomic Hartree potentials that

@@ -28,7 +28,7 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_hartree_enriched", "efe_octree_setup", "efe_octree_destroy", "efe_octree_last_error",
             "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply", "efe_octree_constraints",
             "efe_atom_hartree_table", "efe_adaptive_cell_boxes", "efe_octree_poisson",
-            "efe_octree_density"]
+            "efe_octree_density", "efe_octree_kexp"]
 
 
 class MeshDesc(C.Structure):
@@ -121,6 +121,7 @@ def lib(path: str = LIB_PATH):
                                          pdbl]
     L.efe_octree_poisson.argtypes = [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), vp]
     L.efe_octree_density.argtypes = [vp, vp, i32, pdbl, vp, vp]
+    L.efe_octree_kexp.argtypes = [vp, vp, dbl, vp, i32, dbl, i32, vp]
     L.efe_atom_hartree_table.argtypes = [C.POINTER(EnrichFn), i32, pdbl, i32, i32, dbl, pdbl, pdbl, pdbl, pdbl]
     L.efe_adaptive_cell_boxes.argtypes = [pdbl, pdbl, pdbl, i32, dbl, dbl, dbl, i32, dbl, i32, C.POINTER(i64), pdbl,
                                           i64]
@@ -447,6 +448,19 @@ class Octree:
         if st != EFE_OK:
             raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
         return rho
+
+    def kexp(self, vq, psi_bar, dt: float, k: int, kin: float = 1.0):
+        """psi_bar <- exp(-i dt Hbar) psi_bar in place (device complex128 [n_free, n_cols]),
+        k Lanczos steps per column."""
+        import torch
+        assert psi_bar.is_cuda and psi_bar.dtype == torch.complex128 and psi_bar.is_contiguous()
+        assert psi_bar.dim() == 2 and psi_bar.shape[0] == self.n_free
+        assert vq.is_cuda and vq.dtype == torch.float64 and vq.is_contiguous() and vq.numel() == self.n_leaves * self.n_q
+        st = lib().efe_octree_kexp(self.h, _ptr(vq), float(kin), _ptr(psi_bar), int(psi_bar.shape[1]), float(dt),
+                                   int(k), _stream())
+        if st != EFE_OK:
+            raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
+        return psi_bar
 
     def close(self):
         if getattr(self, "h", None):

@@ -259,6 +259,71 @@ k_oct_density(const OctTables T, const int* __restrict__ conn, const double* __r
 
 unsigned oblk(long long n) { return (unsigned)((n + 255) / 256); }
 
+// Per complex column c of [n][2C] arrays (re, im interleaved): out[c] += Re sum_i conj(a_ic) b_ic over the
+// block's slice of rows (blockIdx.x = column, gridDim.y slices; the caller zeroes out)
+__global__ void __launch_bounds__(256) k_oct_cdot(const double* __restrict__ a, const double* __restrict__ b,
+                                                  long long n, int C, double* __restrict__ out) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  const long long chunk = (n + gridDim.y - 1) / gridDim.y;
+  const long long i0 = (long long)blockIdx.y * chunk, i1 = min(n, i0 + chunk);
+  double acc = 0.0;
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const long long o = i * 2 * C + 2 * c;
+    acc += a[o] * b[o] + a[o + 1] * b[o + 1];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(&out[c], red[0]);
+}
+
+// boundary rows of a [n][2C] array set to 0 (the Dirichlet space)
+__global__ void k_oct_zero_bnd(double* __restrict__ x, const unsigned char* __restrict__ bnd, long long n, int C) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n * 2 * C) return;
+  if (bnd[idx / (2 * C)]) x[idx] = 0.0;
+}
+
+// y[:, c] = s[c] x[:, c] (complex column c, real scalar; y may be x)
+__global__ void k_oct_cscale(const double* x, const double* __restrict__ sc, long long n, int C, double* y) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n * 2 * C) return;
+  y[idx] = sc[(idx % (2 * C)) / 2] * x[idx];
+}
+
+// w[:, c] -= a[c] q[:, c] + b[c] qm[:, c]   (qm may be NULL)
+__global__ void k_oct_lz_update(double* __restrict__ w, const double* __restrict__ q, const double* __restrict__ qm,
+                                const double* __restrict__ a, const double* __restrict__ b, long long n, int C) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n * 2 * C) return;
+  const int c = (int)((idx % (2 * C)) / 2);
+  double v = w[idx] - a[c] * q[idx];
+  if (qm) v -= b[c] * qm[idx];
+  w[idx] = v;
+}
+
+// psi[:, c] = sum_j y[c][j] Q_j[:, c] with complex y ([C][k][2]); Q_j = Q + j n 2C
+__global__ void k_oct_lz_combine(const double* __restrict__ Q, const double* __restrict__ y, int k, long long n, int C,
+                                 double* __restrict__ psi) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n * C) return;
+  const long long i = idx / C;
+  const int c = (int)(idx % C);
+  double re = 0.0, im = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double* q = Q + (long long)j * n * 2 * C + i * 2 * C + 2 * c;
+    const double yr = y[(c * k + j) * 2], yi = y[(c * k + j) * 2 + 1];
+    re += yr * q[0] - yi * q[1];
+    im += yr * q[1] + yi * q[0];
+  }
+  psi[i * 2 * C + 2 * c] = re;
+  psi[i * 2 * C + 2 * c + 1] = im;
+}
+
 // *out += a . b (the caller zeroes *out)
 __global__ void __launch_bounds__(256) k_oct_dot(const double* __restrict__ a, const double* __restrict__ b,
                                                  long long n, double* __restrict__ out) {
@@ -906,6 +971,122 @@ efe_status efe_octree_density(efe_octree* oct, const double* psi_bar_dev, int32_
     return EFE_ERR_CUDA;
   }
   return EFE_OK;
+}
+
+}  // extern "C"
+
+namespace efe {
+
+// psi <- exp(-i dt Hbar) psi per complex column by k Lanczos steps (Eqs. AdaptiveKrylov with a fixed
+// Krylov dimension): Hbar = D P^T H P D (octree_apply mode 2), three-term recurrence, the exponential
+// of the tridiagonal matrix by its eigendecomposition on the host, psi = |psi| Q_k y.
+efe_status octree_kexp(Octree& o, const double* vq, double kin, double* psi, int C, double dt, int k, cudaStream_t s) {
+  const long long n = o.n_free, N2 = n * 2 * C;
+  double* Q = nullptr;
+  double* small = nullptr;   // nrm[C], a[C], b[C], scratch[C], y[C][k][2]
+  if (cudaMalloc(&Q, sizeof(double) * N2 * (k + 1)) != cudaSuccess ||
+      cudaMalloc(&small, sizeof(double) * (4 * C + 2 * (size_t)C * k)) != cudaSuccess) {
+    if (Q) cudaFree(Q);
+    o.err = "octree exponential: out of device memory";
+    return EFE_ERR_NOMEM;
+  }
+  double *nrm = small, *a = small + C, *b = small + 2 * C, *tmp = small + 3 * C, *ydev = small + 4 * C;
+  std::vector<double> h_nrm(C), h_a((size_t)C * k), h_b((size_t)C * k), hv(C);
+  efe_status st = EFE_OK;
+  const dim3 dg((unsigned)C, 64);
+  auto cdot = [&](const double* x, const double* y, double* out) {
+    cudaMemsetAsync(out, 0, sizeof(double) * C, s);
+    k_oct_cdot<<<dg, 256, 0, s>>>(x, y, n, C, out);
+    note_launch();
+  };
+  auto to_host = [&](const double* d, std::vector<double>& h) {
+    cudaError_t e = cudaMemcpyAsync(h.data(), d, sizeof(double) * C, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+  };
+  do {
+    // q_0 = psi / |psi| (boundary rows of psi zeroed first: they are not part of the space)
+    k_oct_zero_bnd<<<oblk(N2), 256, 0, s>>>(psi, o.d_bnd, n, C);
+    note_launch();
+    cdot(psi, psi, nrm);
+    if (to_host(nrm, h_nrm) != cudaSuccess) { st = EFE_ERR_CUDA; break; }
+    for (int c = 0; c < C; ++c) {
+      h_nrm[c] = std::sqrt(h_nrm[c]);
+      hv[c] = h_nrm[c] > 0.0 ? 1.0 / h_nrm[c] : 0.0;
+    }
+    cudaMemcpyAsync(tmp, hv.data(), sizeof(double) * C, cudaMemcpyHostToDevice, s);
+    k_oct_cscale<<<oblk(N2), 256, 0, s>>>(psi, tmp, n, C, Q);
+    note_launch();
+    for (int j = 0; j < k && st == EFE_OK; ++j) {
+      double* qj = Q + (long long)j * N2;
+      double* w = Q + (long long)(j + 1) * N2;
+      if ((st = octree_apply(o, vq, kin, qj, w, 2 * C, 2, s)) != EFE_OK) break;
+      cdot(qj, w, a);
+      if (to_host(a, hv) != cudaSuccess) { st = EFE_ERR_CUDA; break; }
+      for (int c = 0; c < C; ++c) h_a[(size_t)c * k + j] = hv[c];
+      k_oct_lz_update<<<oblk(N2), 256, 0, s>>>(w, qj, j > 0 ? Q + (long long)(j - 1) * N2 : nullptr, a, b, n, C);
+      note_launch();
+      cdot(w, w, tmp);
+      if (to_host(tmp, hv) != cudaSuccess) { st = EFE_ERR_CUDA; break; }
+      for (int c = 0; c < C; ++c) {
+        const double beta = std::sqrt(std::max(hv[c], 0.0));
+        h_b[(size_t)c * k + j] = beta;
+        hv[c] = beta > 1e-300 ? 1.0 / beta : 0.0;   // invariant subspace: the rest of the basis is zero
+      }
+      std::vector<double> bj(C);
+      for (int c = 0; c < C; ++c) bj[c] = h_b[(size_t)c * k + j];
+      cudaMemcpyAsync(b, bj.data(), sizeof(double) * C, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(tmp, hv.data(), sizeof(double) * C, cudaMemcpyHostToDevice, s);
+      if (j + 1 < k) {
+        k_oct_cscale<<<oblk(N2), 256, 0, s>>>(w, tmp, n, C, w);
+        note_launch();
+      }
+    }
+    if (st != EFE_OK) break;
+    // y = |psi| V exp(-i dt Lambda) V^T e_1 for the k x k tridiagonal matrix of each column
+    std::vector<double> y((size_t)C * k * 2);
+    for (int c = 0; c < C; ++c) {
+      std::vector<double> T((size_t)k * k, 0.0), V, lam;
+      for (int i = 0; i < k; ++i) {
+        T[(size_t)i * k + i] = h_a[(size_t)c * k + i];
+        if (i + 1 < k) T[(size_t)i * k + i + 1] = T[(size_t)(i + 1) * k + i] = h_b[(size_t)c * k + i];
+      }
+      if (!jacobi_eigen(k, T, V, lam)) {
+        o.err = "octree exponential: tridiagonal eigensolver did not converge";
+        st = EFE_ERR_CUDA;
+        break;
+      }
+      for (int i = 0; i < k; ++i) {
+        double re = 0.0, im = 0.0;
+        for (int m = 0; m < k; ++m) {
+          const double v0 = V[(size_t)0 * k + m], vi = V[(size_t)i * k + m];
+          re += vi * std::cos(-dt * lam[m]) * v0;
+          im += vi * std::sin(-dt * lam[m]) * v0;
+        }
+        y[((size_t)c * k + i) * 2] = h_nrm[c] * re;
+        y[((size_t)c * k + i) * 2 + 1] = h_nrm[c] * im;
+      }
+    }
+    if (st != EFE_OK) break;
+    cudaMemcpyAsync(ydev, y.data(), sizeof(double) * y.size(), cudaMemcpyHostToDevice, s);
+    k_oct_lz_combine<<<oblk(n * C), 256, 0, s>>>(Q, ydev, k, n, C, psi);
+    note_launch();
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) st = EFE_ERR_CUDA;
+  } while (false);
+  if (st == EFE_ERR_CUDA && o.err.empty()) o.err = "octree exponential: CUDA error";
+  cudaFree(Q);
+  cudaFree(small);
+  return st;
+}
+
+}  // namespace efe
+
+extern "C" {
+
+efe_status efe_octree_kexp(efe_octree* oct, const double* vq_dev, double kin, double* psi_bar_dev, int32_t n_cols,
+                           double dt, int32_t k, void* stream) {
+  if (!oct || !vq_dev || !psi_bar_dev || n_cols < 1 || 2 * n_cols > 65535 || k < 1 || k > 64) return EFE_ERR_ARG;
+  return efe::octree_kexp(oct->o, vq_dev, kin, psi_bar_dev, n_cols, dt, k, reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -187,3 +187,33 @@ def test_octree_density_matches_oracle(name):
     ref_rho = m.density(po, occ)
     assert np.max(np.abs(rho - ref_rho)) <= 1e-12 * np.max(np.abs(ref_rho))
     o.close()
+
+
+def test_octree_krylov_exponential_matches_oracle():
+    """psi <- exp(-i dt Hbar) psi on the locally refined mesh (harmonic potential,
+    fixed Krylov dimension 8) against the oracle's Lanczos exponential of
+    OctreeMesh.hbar (1e-10 relative); norms conserved."""
+    from oracle import krylov
+    from oracle.octree import OctreeMesh
+    from paper_2210_14421_gb300 import Octree
+    lo, hi, nc, p, nq, ref = [-5, -5, -5], [5, 5, 5], 3, 3, 5, [(1, 1, 1)]
+    m = OctreeMesh(lo, hi, nc, p, ref, n_quad=nq)
+    o = Octree(lo, hi, nc, p, nq, ref)
+    fx, qx, bnd = o.coords()
+    pos = {k: j for j, k in enumerate(_key(m.nodes[m.free]))}
+    perm = np.array([pos[k] for k in _key(fx)])
+    vq = 0.5 * np.sum(qx ** 2, axis=2)
+    rng = np.random.default_rng(9)
+    psi = rng.standard_normal((o.n_free, 2)) + 1j * rng.standard_normal((o.n_free, 2))
+    psi[bnd] = 0.0
+    po = np.zeros_like(psi)
+    po[perm] = psi
+    I = np.where(~m.boundary_free)[0]
+    ref_out, _, _ = krylov.expm_block(m.hbar(vq, 1.0), po[I], 0.05, 1e-14, 8, fixed_k=8)
+    g = torch.from_numpy(np.ascontiguousarray(psi)).cuda()
+    o.kexp(torch.from_numpy(np.ascontiguousarray(vq)).cuda(), g, 0.05, 8)
+    got = np.zeros_like(po)
+    got[perm] = g.cpu().numpy()
+    assert np.max(np.abs(got[I] - ref_out)) <= 1e-10 * np.max(np.abs(ref_out))
+    assert abs(np.linalg.norm(got) - np.linalg.norm(psi)) <= 1e-12 * np.linalg.norm(psi)
+    o.close()
