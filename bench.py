@@ -716,6 +716,8 @@ def run_next_rows(args):
         psi = torch.randn((o.n_free, 44), dtype=torch.complex128, device="cuda")
         (_, t_rho) = timed(lambda: o.density(psi, np.full(44, 2.0)))
         out["octree_density"] = {"orbitals": 44, "ms": round(1e3 * t_rho, 2)}
+        (_, t_kx) = timed(lambda: o.kexp(vq, psi, 0.05, 16))
+        out["octree_kexp"] = {"orbitals": 44, "krylov_dim": 16, "dt": 0.05, "s": round(t_kx, 3)}
         fx, _, _ = o.coords()
         g_b = torch.from_numpy(np.zeros(o.n_free)).cuda()
         fq = torch.from_numpy(np.exp(-np.sum(qx ** 2, axis=2))).cuda()
