@@ -465,6 +465,13 @@ efe_status efe_octree_poisson(efe_octree* oct, const double* f_q_dev, const doub
  * EFE_ERR_NOMEM, EFE_ERR_CUDA. */
 efe_status efe_octree_density(efe_octree* oct, const double* psi_bar_dev, int32_t n_orb, const double* occ_host,
                               double* rho_dev, void* stream);
+/* Values at every leaf's Gauss-Legendre points of n_cols real nodal columns of
+ * the constrained space (u_all = P u, then the leaf interpolants; e.g. the
+ * Hartree potential from efe_octree_poisson): u_free_dev device [n_free][n_cols],
+ * out_q_dev device [n_cols][n_leaves][n_q].  Stream-ordered.  Errors:
+ * EFE_ERR_ARG, EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+efe_status efe_octree_interp(efe_octree* oct, const double* u_free_dev, int32_t n_cols, double* out_q_dev,
+                             void* stream);
 /* psi_bar <- exp(-i dt Hbar) psi_bar on the locally refined mesh, Hbar the
  * Loewdin-scaled operator of efe_octree_apply (mode 2) with kin and v at the
  * leaves' Gauss-Legendre points (vq_dev [n_leaves][n_q]): per complex column,

@@ -28,7 +28,7 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_hartree_enriched", "efe_octree_setup", "efe_octree_destroy", "efe_octree_last_error",
             "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply", "efe_octree_constraints",
             "efe_atom_hartree_table", "efe_adaptive_cell_boxes", "efe_octree_poisson",
-            "efe_octree_density", "efe_octree_kexp"]
+            "efe_octree_density", "efe_octree_kexp", "efe_octree_interp"]
 
 
 class MeshDesc(C.Structure):
@@ -122,6 +122,7 @@ def lib(path: str = LIB_PATH):
     L.efe_octree_poisson.argtypes = [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), vp]
     L.efe_octree_density.argtypes = [vp, vp, i32, pdbl, vp, vp]
     L.efe_octree_kexp.argtypes = [vp, vp, dbl, vp, i32, dbl, i32, vp]
+    L.efe_octree_interp.argtypes = [vp, vp, i32, vp, vp]
     L.efe_atom_hartree_table.argtypes = [C.POINTER(EnrichFn), i32, pdbl, i32, i32, dbl, pdbl, pdbl, pdbl, pdbl]
     L.efe_adaptive_cell_boxes.argtypes = [pdbl, pdbl, pdbl, i32, dbl, dbl, dbl, i32, dbl, i32, C.POINTER(i64), pdbl,
                                           i64]
@@ -448,6 +449,18 @@ class Octree:
         if st != EFE_OK:
             raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
         return rho
+
+    def interp(self, u):
+        """Values at the leaves' GL points (device [n_cols, n_leaves, n_q]) of real nodal columns
+        u (device float64 [n_free] or [n_free, n_cols])."""
+        import torch
+        assert u.is_cuda and u.dtype == torch.float64 and u.is_contiguous() and u.shape[0] == self.n_free
+        nc = 1 if u.dim() == 1 else int(u.shape[1])
+        out = torch.empty((nc, self.n_leaves, self.n_q), dtype=torch.float64, device="cuda")
+        st = lib().efe_octree_interp(self.h, _ptr(u), nc, _ptr(out), _stream())
+        if st != EFE_OK:
+            raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
+        return out
 
     def kexp(self, vq, psi_bar, dt: float, k: int, kin: float = 1.0):
         """psi_bar <- exp(-i dt Hbar) psi_bar in place (device complex128 [n_free, n_cols]),

@@ -257,6 +257,44 @@ k_oct_density(const OctTables T, const int* __restrict__ conn, const double* __r
   for (int t = threadIdx.x; t < nq; t += blockDim.x) rho[leaf * nq + t] = acc[t];
 }
 
+// out[c][leaf][q] = sum_l N_l(x_q) x_all[conn[leaf][l]][c]: values at the leaves' GL points of ncols
+// real nodal columns (one block per leaf, three sum-factorisation passes per column)
+__global__ void __launch_bounds__(kOctThreads)
+k_oct_interp(const OctTables T, const int* __restrict__ conn, const double* __restrict__ xa, int ncols,
+             long long n_leaves, double* __restrict__ out) {
+  __shared__ double x[kMaxP1 * kMaxP1 * kMaxP1];
+  __shared__ double A[kOctMaxQ1 * kMaxP1 * kMaxP1];
+  __shared__ double Bq[kOctMaxQ1 * kOctMaxQ1 * kMaxP1];
+  const int P1 = T.P1, Q = T.NQ1, nn = P1 * P1 * P1, nq = Q * Q * Q;
+  const long long leaf = blockIdx.x;
+  const int* cl = conn + leaf * nn;
+  for (int col = 0; col < ncols; ++col) {
+    __syncthreads();
+    for (int l = threadIdx.x; l < nn; l += blockDim.x) x[l] = xa[(long long)cl[l] * ncols + col];
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q * P1 * P1; t += blockDim.x) {
+      const int q1 = t % Q, i2 = (t / Q) % P1, i3 = t / (Q * P1);
+      double s = 0.0;
+      for (int i1 = 0; i1 < P1; ++i1) s += T.B1[q1 * P1 + i1] * x[i1 + P1 * (i2 + P1 * i3)];
+      A[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q * Q * P1; t += blockDim.x) {
+      const int q1 = t % Q, q2 = (t / Q) % Q, i3 = t / (Q * Q);
+      double s = 0.0;
+      for (int i2 = 0; i2 < P1; ++i2) s += T.B1[q2 * P1 + i2] * A[q1 + Q * (i2 + P1 * i3)];
+      Bq[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nq; t += blockDim.x) {
+      const int q1 = t % Q, q2 = (t / Q) % Q, q3 = t / (Q * Q);
+      double s = 0.0;
+      for (int i3 = 0; i3 < P1; ++i3) s += T.B1[q3 * P1 + i3] * Bq[q1 + Q * (q2 + Q * i3)];
+      out[((long long)col * n_leaves + leaf) * nq + t] = s;
+    }
+  }
+}
+
 unsigned oblk(long long n) { return (unsigned)((n + 255) / 256); }
 
 // Per complex column c of [n][2C] arrays (re, im interleaved): out[c] += Re sum_i conj(a_ic) b_ic over the
@@ -1087,6 +1125,42 @@ efe_status efe_octree_kexp(efe_octree* oct, const double* vq_dev, double kin, do
                            double dt, int32_t k, void* stream) {
   if (!oct || !vq_dev || !psi_bar_dev || n_cols < 1 || 2 * n_cols > 65535 || k < 1 || k > 64) return EFE_ERR_ARG;
   return efe::octree_kexp(oct->o, vq_dev, kin, psi_bar_dev, n_cols, dt, k, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+extern "C" {
+
+efe_status efe_octree_interp(efe_octree* oct, const double* u_free_dev, int32_t n_cols, double* out_q_dev,
+                             void* stream) {
+  if (!oct || !u_free_dev || !out_q_dev || n_cols < 1 || n_cols > 65535) return EFE_ERR_ARG;
+  efe::Octree& o = oct->o;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (o.ws_cols < n_cols) {
+    if (o.d_xall) cudaFree(o.d_xall);
+    if (o.d_yall) cudaFree(o.d_yall);
+    o.d_xall = o.d_yall = nullptr;
+    o.ws_cols = 0;
+    if (cudaMalloc(&o.d_xall, sizeof(double) * o.n_all * n_cols) != cudaSuccess ||
+        cudaMalloc(&o.d_yall, sizeof(double) * o.n_all * n_cols) != cudaSuccess) {
+      o.err = "octree interpolation: out of device memory";
+      return EFE_ERR_NOMEM;
+    }
+    o.ws_cols = n_cols;
+  }
+  const long long N = o.n_all * n_cols;
+  efe::k_oct_expand<<<efe::oblk(N), 256, 0, s>>>(o.d_rs, o.d_col, o.d_val, o.d_bnd, nullptr, u_free_dev, o.n_all,
+                                                 n_cols, 0, o.d_xall);
+  efe::note_launch();
+  efe::k_oct_interp<<<(unsigned)o.n_leaves, efe::kOctThreads, 0, s>>>(o.tab, o.d_conn, o.d_xall, n_cols, o.n_leaves,
+                                                                      out_q_dev);
+  efe::note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    o.err = std::string("octree interpolation: ") + cudaGetErrorString(e);
+    return EFE_ERR_CUDA;
+  }
+  return EFE_OK;
 }
 
 }  // extern "C"

@@ -217,3 +217,26 @@ def test_octree_krylov_exponential_matches_oracle():
     assert np.max(np.abs(got[I] - ref_out)) <= 1e-10 * np.max(np.abs(ref_out))
     assert abs(np.linalg.norm(got) - np.linalg.norm(psi)) <= 1e-12 * np.linalg.norm(psi)
     o.close()
+
+
+@pytest.mark.parametrize("name", ["p3_box", "p5_corner"])
+def test_octree_interpolation_matches_oracle(name):
+    """Nodal columns of the constrained space at the leaves' Gauss-Legendre points
+    against OctreeMesh.evaluate of P u (1e-12 relative)."""
+    from oracle.octree import OctreeMesh
+    from paper_2210_14421_gb300 import Octree
+    lo, hi, nc, p, nq, ref = MESHES[name]
+    m = OctreeMesh(lo, hi, nc, p, ref, n_quad=nq)
+    o = Octree(lo, hi, nc, p, nq, ref)
+    fx, qx, _ = o.coords()
+    pos = {k: j for j, k in enumerate(_key(m.nodes[m.free]))}
+    perm = np.array([pos[k] for k in _key(fx)])
+    u = np.random.default_rng(2).standard_normal((o.n_free, 2))
+    out = o.interp(torch.from_numpy(u).cuda()).cpu().numpy()
+    uo = np.zeros_like(u)
+    uo[perm] = u
+    for c in range(2):
+        ua = m.P @ uo[:, c]
+        ref_v = np.stack([m.evaluate(ua, li, qx[li]) for li in range(o.n_leaves)])
+        assert np.max(np.abs(out[c] - ref_v)) <= 1e-12 * np.max(np.abs(ref_v))
+    o.close()
