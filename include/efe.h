@@ -502,6 +502,13 @@ efe_status efe_adaptive_cell_boxes(const double* origin_host, const double* size
                                    int32_t n_atoms, double sigma, double r0, double s, int32_t n_quad, double tol,
                                    int32_t max_depth, int64_t* n_boxes, double* boxes_host, int64_t capacity);
 
+/* The LDA at n points without a context (for meshes that have none, such as the
+ * locally refined mesh): v_xc = d(rho e_xc)/d rho and e_xc of Slater exchange
+ * plus the correlation xc (EFE_XC_PW92 or EFE_XC_PZ81), as efe_density_vxc
+ * computes them.  rho_dev: device [n]; vxc_dev, exc_dev: device [n] (nullable).
+ * Stream-ordered.  Errors: EFE_ERR_ARG, EFE_ERR_CUDA. */
+efe_status efe_lda_points(const double* rho_dev, double* vxc_dev, double* exc_dev, int64_t n, int32_t xc, void* stream);
+
 /* Spectra of dipole traces (Sec. Results: the absorption spectrum of the weak
  * perturbation study and the power spectrum of the high-harmonic study); no
  * context needed.  Samples at t_n = n dt, n = 0 .. n_t - 1, on the device;

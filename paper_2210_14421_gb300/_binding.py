@@ -28,7 +28,7 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_hartree_enriched", "efe_octree_setup", "efe_octree_destroy", "efe_octree_last_error",
             "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply", "efe_octree_constraints",
             "efe_atom_hartree_table", "efe_adaptive_cell_boxes", "efe_octree_poisson",
-            "efe_octree_density", "efe_octree_kexp", "efe_octree_interp"]
+            "efe_octree_density", "efe_octree_kexp", "efe_octree_interp", "efe_lda_points"]
 
 
 class MeshDesc(C.Structure):
@@ -123,6 +123,7 @@ def lib(path: str = LIB_PATH):
     L.efe_octree_density.argtypes = [vp, vp, i32, pdbl, vp, vp]
     L.efe_octree_kexp.argtypes = [vp, vp, dbl, vp, i32, dbl, i32, vp]
     L.efe_octree_interp.argtypes = [vp, vp, i32, vp, vp]
+    L.efe_lda_points.argtypes = [vp, vp, vp, i64, i32, vp]
     L.efe_atom_hartree_table.argtypes = [C.POINTER(EnrichFn), i32, pdbl, i32, i32, dbl, pdbl, pdbl, pdbl, pdbl]
     L.efe_adaptive_cell_boxes.argtypes = [pdbl, pdbl, pdbl, i32, dbl, dbl, dbl, i32, dbl, i32, C.POINTER(i64), pdbl,
                                           i64]
@@ -551,3 +552,15 @@ def adaptive_cell_boxes(origin, size, Z, R, sigma, r0, s, n_quad, tol, max_depth
     if st != EFE_OK:
         raise EfeError(st, "efe_adaptive_cell_boxes: invalid argument")
     return boxes
+
+
+def lda_points(rho, xc: int = EFE_XC_PW92):
+    """(v_xc, e_xc) at the points of a device float64 density array (any shape)."""
+    import torch
+    assert rho.is_cuda and rho.dtype == torch.float64 and rho.is_contiguous()
+    vxc = torch.empty_like(rho)
+    exc = torch.empty_like(rho)
+    st = lib().efe_lda_points(_ptr(rho), _ptr(vxc), _ptr(exc), int(rho.numel()), int(xc), _stream())
+    if st != EFE_OK:
+        raise EfeError(st, "efe_lda_points: invalid argument")
+    return vxc, exc

@@ -808,6 +808,21 @@ cudaError_t launch_lda(const Ctx& c, const double* rho, double* vxc, double* exc
   return cudaGetLastError();
 }
 
+}  // namespace efe
+
+// Context-free LDA at n points (the potential assembly of meshes without an efe_ctx,
+// e.g. the locally refined mesh).
+extern "C" efe_status efe_lda_points(const double* rho_dev, double* vxc_dev, double* exc_dev, int64_t n, int32_t xc,
+                                     void* stream) {
+  if (!rho_dev || n < 0 || (xc != EFE_XC_PW92 && xc != EFE_XC_PZ81)) return EFE_ERR_ARG;
+  if (n == 0) return EFE_OK;
+  efe::k_lda<<<efe::nblk(n), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(rho_dev, vxc_dev, exc_dev, n, xc);
+  efe::note_launch();
+  return cudaGetLastError() == cudaSuccess ? EFE_OK : EFE_ERR_CUDA;
+}
+
+namespace efe {
+
 // ---------------------------------------------------------------------------- dipole
 __global__ void k_dipole(const double* __restrict__ rho, const double* __restrict__ wJ, const double* __restrict__ xq,
                          long long npts, double* __restrict__ mu) {

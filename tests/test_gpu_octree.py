@@ -240,3 +240,16 @@ def test_octree_interpolation_matches_oracle(name):
         ref_v = np.stack([m.evaluate(ua, li, qx[li]) for li in range(o.n_leaves)])
         assert np.max(np.abs(out[c] - ref_v)) <= 1e-12 * np.max(np.abs(ref_v))
     o.close()
+
+
+@pytest.mark.parametrize("xc", ["pw92", "pz81"])
+def test_context_free_lda_matches_oracle(xc):
+    """efe_lda_points (the LDA for meshes without a context) against the oracle's
+    LDA on densities spanning the floor and both PZ81 branches (1e-12)."""
+    from oracle import xc as oxc
+    from paper_2210_14421_gb300 import EFE_XC_PW92, EFE_XC_PZ81, lda_points
+    rho = np.concatenate([np.logspace(-16, 3, 400), [0.0, 1e-14, 2e-14]])
+    vxc, exc = lda_points(torch.from_numpy(rho).cuda(), EFE_XC_PW92 if xc == "pw92" else EFE_XC_PZ81)
+    e_ref, v_ref = oxc.lda(rho, xc)[:2]
+    assert np.max(np.abs(vxc.cpu().numpy() - v_ref) - 1e-12 * np.abs(v_ref)) <= 1e-300
+    assert np.max(np.abs(exc.cpu().numpy() - e_ref) - 1e-12 * np.abs(e_ref)) <= 1e-300
