@@ -170,6 +170,53 @@ class OctreeMesh:
             rho[li] = np.abs(vals) ** 2 @ np.asarray(occ, float)
         return rho
 
+    def hartree(self, rho, Z, R):
+        """v_H at every leaf's Gauss-Legendre points: -lap v_H = 4 pi rho (rho at
+        those points, load by the same rule) with the Dirichlet data sum Z / |x - R|
+        (Eqs. Hartree_possion, DiscretePoisson on the locally refined mesh)."""
+        K, _ = self.stiffness_and_load(lambda x: np.zeros(len(x)))
+        F_all = np.zeros(self.n_all)
+        for li, (x0, h, _) in enumerate(self.leaves):
+            w = self.wq * np.prod(h) / 8.0
+            np.add.at(F_all, self.conn[li], self.B.T @ (w * 4.0 * np.pi * rho[li]))
+        F = self.P.T @ F_all
+        xf = self.nodes[self.free]
+        g = sum(z / np.linalg.norm(xf - np.asarray(r)[None, :], axis=1) for z, r in zip(Z, R))
+        B = np.where(self.boundary_free)[0]
+        I = np.where(~self.boundary_free)[0]
+        u = np.zeros(len(self.free))
+        u[B] = g[B]
+        u[I] = spla.spsolve(K[I][:, I].tocsc(), F[I] - K[I][:, B] @ u[B])
+        ua = self.P @ u
+        return np.stack([self.B @ ua[self.conn[li]] for li in range(len(self.leaves))])
+
+    def potential(self, rho, Z, R, E, xc_kind: str = "pw92"):
+        """v = v_N + v_H + v_xc - E . x at every leaf's Gauss-Legendre points."""
+        from .xc import lda
+        xq = self.quad_points()
+        vN = np.zeros(xq.shape[:2])
+        for z, r in zip(Z, R):
+            vN -= z / np.linalg.norm(xq - np.asarray(r)[None, None, :], axis=2)
+        return vN + self.hartree(rho, Z, R) + lda(rho, xc_kind)[1] - xq @ np.asarray(E, float)
+
+    def magnus_step(self, psi_bar, occ, Z, R, dt, k, E):
+        """One predictor-corrector step (Eq. ApproxMagnus) on the locally refined mesh
+        with the field E at the mid-point and a fixed Krylov dimension k:
+        psi_p = exp(-i dt Hbar[v(rho_n)]) psi_n, rho_mid = (rho_n + rho(psi_p)) / 2,
+        psi_n+1 = exp(-i dt Hbar[v(rho_mid)]) psi_n.  psi_bar: (n_free, n_orb) complex,
+        zero on the boundary free nodes."""
+        from .krylov import expm_block
+        I = np.where(~self.boundary_free)[0]
+
+        def kexp(v, psi):
+            out = np.zeros_like(psi)
+            out[I] = expm_block(self.hbar(v), psi[I], dt, 1e-14, k, fixed_k=k)[0]
+            return out
+        rho_n = self.density(psi_bar, occ)
+        psi_p = kexp(self.potential(rho_n, Z, R, E), psi_bar)
+        rho_mid = 0.5 * (rho_n + self.density(psi_p, occ))
+        return kexp(self.potential(rho_mid, Z, R, E), psi_bar)
+
     def quad_points(self):
         """Physical Gauss-Legendre points of every leaf, (n_leaves, nq, 3), in the
         order of self.wq (first axis fastest)."""

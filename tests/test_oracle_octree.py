@@ -155,3 +155,25 @@ def test_density_integrates_to_the_mass_quadratic_form():
     Mc = m.hamiltonian(np.ones(w.shape), kin=0.0)
     ref = sum(occ[a] * np.real(np.conj(psi[:, a]) @ (Mc @ psi[:, a])) for a in range(2))
     assert abs(np.sum(w * rho) - ref) < 1e-12 * ref
+
+
+def test_magnus_step_reduces_to_the_rectilinear_step():
+    """Without refinement the locally refined mesh is the rectilinear mesh: the
+    predictor-corrector step there (classical basis, fixed Krylov dimension 8)
+    equals the rectilinear oracle's step (oracle.tdks) node for node."""
+    import efe_workloads as W
+    from oracle import operators, tdks
+    wl = W.small_cluster(n_atoms=2, cells_per_axis=3, degree=3, n_quad=5, L=10.0, n_orb=2)
+    b = np.linspace(-5, 5, 4)
+    wl = wl.with_(xb=b, yb=b.copy(), zb=b.copy(), enrich=[], enr_coefs=np.zeros((wl.n_orb, 0), dtype=complex))
+    S = operators.System(wl)
+    m = OctreeMesh([-5, -5, -5], [5, 5, 5], 3, 3, [])
+    pos = {tuple(k): i for i, k in enumerate(np.round(S.mesh.nodes * 1e6).astype(np.int64))}
+    idx = np.array([pos[tuple(k)] for k in np.round(m.nodes[m.free] * 1e6).astype(np.int64)])
+    rng = np.random.default_rng(4)
+    psi_r = (rng.standard_normal((S.n_h, 2)) + 1j * rng.standard_normal((S.n_h, 2))) * S.mesh.interior[:, None]
+    field = W.Field(kind=W.FIELD_GAUSS, amp=0.0, omega=0.0, t0=0.0, sigma=1.0, direction=(0.0, 0.0, 1.0))
+    st = tdks.make_state(S, psi_r, wl.occ, 1)
+    out_r = tdks.magnus_step(S, psi_r, st, 0.0, 0.05, [field], wl.occ, 1e-14, 8, fixed_k=8)[0]
+    out_o = m.magnus_step(psi_r[idx], wl.occ, wl.Z, wl.R, 0.05, 8, np.zeros(3))
+    assert np.max(np.abs(out_o - out_r[idx])) < 1e-12 * np.max(np.abs(out_r))
