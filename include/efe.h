@@ -472,6 +472,19 @@ efe_status efe_octree_density(efe_octree* oct, const double* psi_bar_dev, int32_
  * EFE_ERR_ARG, EFE_ERR_NOMEM, EFE_ERR_CUDA. */
 efe_status efe_octree_interp(efe_octree* oct, const double* u_free_dev, int32_t n_cols, double* out_q_dev,
                              void* stream);
+/* One predictor-corrector Magnus step (Eq. ApproxMagnus) on the locally refined
+ * mesh with a fixed Krylov dimension k: psi_p = exp(-i dt Hbar[v(rho_n)]) psi_n,
+ * rho_mid = (rho_n + rho(psi_p)) / 2, psi_n+1 = exp(-i dt Hbar[v(rho_mid)]) psi_n,
+ * v = -sum Z / |x - R| + v_H + v_xc - E . x at the leaves' Gauss-Legendre points
+ * (field_host: double[3], E at the mid-point), v_H from -lap v_H = 4 pi rho with the
+ * Dirichlet data sum Z / |x - R| (efe_octree_poisson to cg_tol), v_xc the LDA xc.
+ * psi_bar_dev: device complex128 [n_free][n_orb] in the Loewdin basis, in place;
+ * occ_host [n_orb]; atoms_host [n_atoms][4] = Z, x, y, z.  Allocates per call and
+ * synchronises `stream`.  Errors: EFE_ERR_ARG, EFE_ERR_CG_NOCONV, EFE_ERR_NOMEM,
+ * EFE_ERR_CUDA. */
+efe_status efe_octree_magnus_step(efe_octree* oct, double* psi_bar_dev, int32_t n_orb, const double* occ_host,
+                                  const double* atoms_host, int32_t n_atoms, const double* field_host, double dt,
+                                  int32_t k, double cg_tol, int32_t xc, void* stream);
 /* psi_bar <- exp(-i dt Hbar) psi_bar on the locally refined mesh, Hbar the
  * Loewdin-scaled operator of efe_octree_apply (mode 2) with kin and v at the
  * leaves' Gauss-Legendre points (vq_dev [n_leaves][n_q]): per complex column,

@@ -28,7 +28,8 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_hartree_enriched", "efe_octree_setup", "efe_octree_destroy", "efe_octree_last_error",
             "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply", "efe_octree_constraints",
             "efe_atom_hartree_table", "efe_adaptive_cell_boxes", "efe_octree_poisson",
-            "efe_octree_density", "efe_octree_kexp", "efe_octree_interp", "efe_lda_points"]
+            "efe_octree_density", "efe_octree_kexp", "efe_octree_interp", "efe_lda_points",
+            "efe_octree_magnus_step"]
 
 
 class MeshDesc(C.Structure):
@@ -124,6 +125,7 @@ def lib(path: str = LIB_PATH):
     L.efe_octree_kexp.argtypes = [vp, vp, dbl, vp, i32, dbl, i32, vp]
     L.efe_octree_interp.argtypes = [vp, vp, i32, vp, vp]
     L.efe_lda_points.argtypes = [vp, vp, vp, i64, i32, vp]
+    L.efe_octree_magnus_step.argtypes = [vp, vp, i32, pdbl, pdbl, i32, pdbl, dbl, i32, dbl, i32, vp]
     L.efe_atom_hartree_table.argtypes = [C.POINTER(EnrichFn), i32, pdbl, i32, i32, dbl, pdbl, pdbl, pdbl, pdbl]
     L.efe_adaptive_cell_boxes.argtypes = [pdbl, pdbl, pdbl, i32, dbl, dbl, dbl, i32, dbl, i32, C.POINTER(i64), pdbl,
                                           i64]
@@ -450,6 +452,21 @@ class Octree:
         if st != EFE_OK:
             raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
         return rho
+
+    def magnus_step(self, psi_bar, occ, Z, R, dt: float, k: int, field=(0.0, 0.0, 0.0), cg_tol: float = 1e-12,
+                    xc: int = EFE_XC_PW92):
+        """One predictor-corrector step of psi_bar (device complex128 [n_free, n_orb], in place)."""
+        import torch
+        assert psi_bar.is_cuda and psi_bar.dtype == torch.complex128 and psi_bar.is_contiguous()
+        assert psi_bar.dim() == 2 and psi_bar.shape[0] == self.n_free
+        occ = np.ascontiguousarray(occ, dtype=np.float64)
+        at = np.ascontiguousarray(np.column_stack([np.asarray(Z, float), np.asarray(R, float).reshape(-1, 3)]))
+        E = np.ascontiguousarray(field, dtype=np.float64)
+        st = lib().efe_octree_magnus_step(self.h, _ptr(psi_bar), int(psi_bar.shape[1]), _dptr(occ), _dptr(at), len(Z),
+                                          _dptr(E), float(dt), int(k), float(cg_tol), int(xc), _stream())
+        if st != EFE_OK:
+            raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
+        return psi_bar
 
     def interp(self, u):
         """Values at the leaves' GL points (device [n_cols, n_leaves, n_q]) of real nodal columns

@@ -295,6 +295,17 @@ k_oct_interp(const OctTables T, const int* __restrict__ conn, const double* __re
   }
 }
 
+// v = vN + vH + vxc + vf (pointwise), rho_mid = (a + b) / 2, y = c x
+__global__ void k_oct_vsum(const double* __restrict__ vN, const double* __restrict__ vH, const double* __restrict__ vxc,
+                           const double* __restrict__ vf, long long n, double* __restrict__ v) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) v[i] = vN[i] + vH[i] + vxc[i] + vf[i];
+}
+__global__ void k_oct_axpby(const double* a, const double* b, double ca, double cb, long long n, double* out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = ca * a[i] + cb * b[i];
+}
+
 unsigned oblk(long long n) { return (unsigned)((n + 255) / 256); }
 
 // Per complex column c of [n][2C] arrays (re, im interleaved): out[c] += Re sum_i conj(a_ic) b_ic over the
@@ -1164,3 +1175,95 @@ efe_status efe_octree_interp(efe_octree* oct, const double* u_free_dev, int32_t 
 }
 
 }  // extern "C"
+
+extern "C" efe_status efe_lda_points(const double* rho_dev, double* vxc_dev, double* exc_dev, int64_t n, int32_t xc,
+                                     void* stream);
+extern "C" efe_status efe_octree_density(efe_octree* oct, const double* psi_bar_dev, int32_t n_orb,
+                                         const double* occ_host, double* rho_dev, void* stream);
+extern "C" efe_status efe_octree_interp(efe_octree* oct, const double* u_free_dev, int32_t n_cols, double* out_q_dev,
+                                        void* stream);
+
+namespace efe {
+
+// One predictor-corrector step (Eq. ApproxMagnus) on the locally refined mesh with the field E at the
+// mid-point and a fixed Krylov dimension: psi_p = exp(-i dt Hbar[v(rho_n)]) psi_n,
+// rho_mid = (rho_n + rho(psi_p)) / 2, psi_n+1 = exp(-i dt Hbar[v(rho_mid)]) psi_n, with
+// v = -sum Z / |x - R| + v_H + v_xc - E . x at the leaves' Gauss-Legendre points and v_H from
+// -lap v_H = 4 pi rho with the Dirichlet data sum Z / |x - R|.
+static efe_status octree_step(efe_octree* oct, double* psi, int n_orb, const double* occ, const double* atoms,
+                              int n_atoms, const double E[3], double dt, int k, double cg_tol, int xc,
+                              cudaStream_t s) {
+  Octree& o = oct->o;
+  const long long nq = o.n_leaves * o.nq, nf = o.n_free, N2 = nf * 2 * n_orb;
+  // host: v_N and the field potential at the points, the Dirichlet data at the free nodes
+  std::vector<double> vNf(2 * (size_t)nq), g((size_t)nf, 0.0);
+  for (long long m = 0; m < nq; ++m) {
+    const double* x = &o.quad_xyz[3 * m];
+    double v = 0.0;
+    for (int a = 0; a < n_atoms; ++a) {
+      const double dx = x[0] - atoms[4 * a + 1], dy = x[1] - atoms[4 * a + 2], dz = x[2] - atoms[4 * a + 3];
+      v -= atoms[4 * a] / std::sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    vNf[m] = v;
+    vNf[nq + m] = -(E[0] * x[0] + E[1] * x[1] + E[2] * x[2]);
+  }
+  for (long long f = 0; f < nf; ++f) {
+    double v = 0.0;
+    for (int a = 0; a < n_atoms; ++a) {
+      const double dx = o.free_xyz[3 * f] - atoms[4 * a + 1], dy = o.free_xyz[3 * f + 1] - atoms[4 * a + 2],
+                   dz = o.free_xyz[3 * f + 2] - atoms[4 * a + 3];
+      v += atoms[4 * a] / std::sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    g[f] = v;
+  }
+  double* buf = nullptr;
+  const size_t nbuf = 8 * (size_t)nq + 2 * (size_t)nf + (size_t)N2;
+  if (cudaMalloc(&buf, sizeof(double) * nbuf) != cudaSuccess) {
+    o.err = "octree step: out of device memory";
+    return EFE_ERR_NOMEM;
+  }
+  double *vN = buf, *vf = buf + nq, *rho_n = buf + 2 * nq, *rho = buf + 3 * nq, *vH = buf + 4 * nq;
+  double *vxc = buf + 5 * nq, *v = buf + 6 * nq, *fq = buf + 7 * nq, *gd = buf + 8 * nq, *u = gd + nf;
+  double* psi_p = u + nf;
+  efe_status st = EFE_OK;
+  auto potential = [&](const double* r) -> efe_status {
+    k_oct_axpby<<<oblk(nq), 256, 0, s>>>(r, r, 4.0 * 3.14159265358979323846, 0.0, nq, fq);
+    note_launch();
+    int its = 0;
+    efe_status e = octree_poisson(o, fq, gd, u, cg_tol, 100000, &its, s);
+    if (e != EFE_OK) return e;
+    if ((e = efe_octree_interp(oct, u, 1, vH, s)) != EFE_OK) return e;
+    if ((e = efe_lda_points(r, vxc, nullptr, nq, xc, s)) != EFE_OK) return e;
+    k_oct_vsum<<<oblk(nq), 256, 0, s>>>(vN, vH, vxc, vf, nq, v);
+    note_launch();
+    return EFE_OK;
+  };
+  do {
+    cudaMemcpyAsync(vN, vNf.data(), sizeof(double) * 2 * nq, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(gd, g.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, s);
+    if ((st = efe_octree_density(oct, psi, n_orb, occ, rho_n, s)) != EFE_OK) break;
+    if ((st = potential(rho_n)) != EFE_OK) break;
+    cudaMemcpyAsync(psi_p, psi, sizeof(double) * N2, cudaMemcpyDeviceToDevice, s);
+    if ((st = octree_kexp(o, v, 1.0, psi_p, n_orb, dt, k, s)) != EFE_OK) break;
+    if ((st = efe_octree_density(oct, psi_p, n_orb, occ, rho, s)) != EFE_OK) break;
+    k_oct_axpby<<<oblk(nq), 256, 0, s>>>(rho_n, rho, 0.5, 0.5, nq, rho);
+    note_launch();
+    if ((st = potential(rho)) != EFE_OK) break;
+    st = octree_kexp(o, v, 1.0, psi, n_orb, dt, k, s);
+  } while (false);
+  cudaStreamSynchronize(s);
+  cudaFree(buf);
+  return st;
+}
+
+}  // namespace efe
+
+extern "C" efe_status efe_octree_magnus_step(efe_octree* oct, double* psi_bar_dev, int32_t n_orb, const double* occ_host,
+                                             const double* atoms_host, int32_t n_atoms, const double* field_host,
+                                             double dt, int32_t k, double cg_tol, int32_t xc, void* stream) {
+  if (!oct || !psi_bar_dev || !occ_host || (n_atoms > 0 && !atoms_host) || n_atoms < 0 || !field_host ||
+      n_orb < 1 || 2 * n_orb > 65535 || k < 1 || k > 64 || !(cg_tol > 0.0))
+    return EFE_ERR_ARG;
+  return efe::octree_step(oct, psi_bar_dev, n_orb, occ_host, atoms_host, n_atoms, field_host, dt, k, cg_tol, xc,
+                          reinterpret_cast<cudaStream_t>(stream));
+}

@@ -253,3 +253,31 @@ def test_context_free_lda_matches_oracle(xc):
     e_ref, v_ref = oxc.lda(rho, xc)[:2]
     assert np.max(np.abs(vxc.cpu().numpy() - v_ref) - 1e-12 * np.abs(v_ref)) <= 1e-300
     assert np.max(np.abs(exc.cpu().numpy() - e_ref) - 1e-12 * np.abs(e_ref)) <= 1e-300
+
+
+def test_octree_magnus_step_matches_oracle():
+    """One predictor-corrector step on the locally refined mesh (two nuclei, a field,
+    Hartree and LDA potentials, Krylov dimension 8) against the oracle's step
+    OctreeMesh.magnus_step (1e-10)."""
+    from oracle.octree import OctreeMesh
+    from paper_2210_14421_gb300 import Octree
+    lo, hi, nc, p, nq, ref = [-5, -5, -5], [5, 5, 5], 3, 3, 5, [(1, 1, 1)]
+    Z, R = [1.0, 1.0], [np.array([-0.7, 0.1, 0.0]), np.array([0.7, -0.1, 0.2])]
+    m = OctreeMesh(lo, hi, nc, p, ref, n_quad=nq)
+    o = Octree(lo, hi, nc, p, nq, ref)
+    fx, _, bnd = o.coords()
+    pos = {k: j for j, k in enumerate(_key(m.nodes[m.free]))}
+    perm = np.array([pos[k] for k in _key(fx)])
+    rng = np.random.default_rng(8)
+    psi = 0.3 * (rng.standard_normal((o.n_free, 2)) + 1j * rng.standard_normal((o.n_free, 2)))
+    psi[bnd] = 0.0
+    po = np.zeros_like(psi)
+    po[perm] = psi
+    occ, E = np.array([2.0, 1.0]), np.array([0.0, 0.0, 0.01])
+    ref_out = m.magnus_step(po, occ, Z, R, 0.05, 8, E)
+    g = torch.from_numpy(np.ascontiguousarray(psi)).cuda()
+    o.magnus_step(g, occ, Z, np.array(R), 0.05, 8, field=E, cg_tol=1e-13)
+    got = np.zeros_like(po)
+    got[perm] = g.cpu().numpy()
+    assert np.max(np.abs(got - ref_out)) <= 1e-10 * np.max(np.abs(ref_out))
+    o.close()
