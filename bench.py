@@ -723,6 +723,10 @@ def run_next_rows(args):
         fq = torch.from_numpy(np.exp(-np.sum(qx ** 2, axis=2))).cuda()
         ((u, its), t_p) = timed(lambda: o.poisson(fq, g_b, tol=1e-10, max_it=20000))
         out["octree_poisson"] = {"cg_iterations": its, "s": round(t_p, 3), "tol": 1e-10}
+        psi_s = (0.01 * torch.randn((o.n_free, 8), dtype=torch.complex128, device="cuda")).contiguous()
+        (_, t_st) = timed(lambda: o.magnus_step(psi_s, np.full(8, 2.0), [1.0, 1.0], np.array([[-0.7, 0, 0], [0.7, 0, 0]]),
+                                                0.05, 12, field=(0.0, 0.0, 0.0), cg_tol=1e-10))
+        out["octree_magnus_step"] = {"orbitals": 8, "krylov_dim": 12, "s": round(t_st, 3)}
     except Exception as e:   # keep the numbers above
         out["octree_error"] = str(e)[:200]
     o.close()
