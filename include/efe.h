@@ -478,10 +478,13 @@ efe_status efe_octree_interp(efe_octree* oct, const double* u_free_dev, int32_t 
  * v = -sum Z / |x - R| + v_H + v_xc - E . x at the leaves' Gauss-Legendre points
  * (field_host: double[3], E at the mid-point), v_H from -lap v_H = 4 pi rho with the
  * Dirichlet data sum Z / |x - R| (efe_octree_poisson to cg_tol), v_xc the LDA xc.
+ * Those Dirichlet data are the electrons' far field only for a neutral system
+ * (sum_a occ_a ||psi_a||^2 = sum Z): a precondition, as on the rectilinear mesh.
  * psi_bar_dev: device complex128 [n_free][n_orb] in the Loewdin basis, in place;
- * occ_host [n_orb]; atoms_host [n_atoms][4] = Z, x, y, z.  Allocates per call and
- * synchronises `stream`.  Errors: EFE_ERR_ARG, EFE_ERR_CG_NOCONV, EFE_ERR_NOMEM,
- * EFE_ERR_CUDA. */
+ * occ_host [n_orb]; atoms_host [n_atoms][4] = Z, x, y, z; dt finite and > 0;
+ * xc EFE_XC_PW92 or EFE_XC_PZ81.  Allocates per call and synchronises `stream`.
+ * Errors: EFE_ERR_ARG (message set), EFE_ERR_CG_NOCONV, EFE_ERR_NOMEM,
+ * EFE_ERR_CUDA (also for a kernel fault surfacing at the final synchronisation). */
 efe_status efe_octree_magnus_step(efe_octree* oct, double* psi_bar_dev, int32_t n_orb, const double* occ_host,
                                   const double* atoms_host, int32_t n_atoms, const double* field_host, double dt,
                                   int32_t k, double cg_tol, int32_t xc, void* stream);

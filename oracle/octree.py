@@ -173,7 +173,9 @@ class OctreeMesh:
     def hartree(self, rho, Z, R):
         """v_H at every leaf's Gauss-Legendre points: -lap v_H = 4 pi rho (rho at
         those points, load by the same rule) with the Dirichlet data sum Z / |x - R|
-        (Eqs. Hartree_possion, DiscretePoisson on the locally refined mesh)."""
+        (Eqs. Hartree_possion, DiscretePoisson on the locally refined mesh).  Those
+        data are the electrons' far field only for a neutral system (total charge of
+        rho equal to sum Z), which callers must supply."""
         K, _ = self.stiffness_and_load(lambda x: np.zeros(len(x)))
         F_all = np.zeros(self.n_all)
         for li, (x0, h, _) in enumerate(self.leaves):

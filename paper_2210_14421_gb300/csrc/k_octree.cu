@@ -1238,12 +1238,14 @@ static efe_status octree_step(efe_octree* oct, double* psi, int n_orb, const dou
     note_launch();
     return EFE_OK;
   };
+  cudaError_t ce = cudaSuccess;
   do {
-    cudaMemcpyAsync(vN, vNf.data(), sizeof(double) * 2 * nq, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(gd, g.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, s);
+    if ((ce = cudaMemcpyAsync(vN, vNf.data(), sizeof(double) * 2 * nq, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (ce = cudaMemcpyAsync(gd, g.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      break;
     if ((st = efe_octree_density(oct, psi, n_orb, occ, rho_n, s)) != EFE_OK) break;
     if ((st = potential(rho_n)) != EFE_OK) break;
-    cudaMemcpyAsync(psi_p, psi, sizeof(double) * N2, cudaMemcpyDeviceToDevice, s);
+    if ((ce = cudaMemcpyAsync(psi_p, psi, sizeof(double) * N2, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) break;
     if ((st = octree_kexp(o, v, 1.0, psi_p, n_orb, dt, k, s)) != EFE_OK) break;
     if ((st = efe_octree_density(oct, psi_p, n_orb, occ, rho, s)) != EFE_OK) break;
     k_oct_axpby<<<oblk(nq), 256, 0, s>>>(rho_n, rho, 0.5, 0.5, nq, rho);
@@ -1251,8 +1253,16 @@ static efe_status octree_step(efe_octree* oct, double* psi, int n_orb, const dou
     if ((st = potential(rho)) != EFE_OK) break;
     st = octree_kexp(o, v, 1.0, psi, n_orb, dt, k, s);
   } while (false);
-  cudaStreamSynchronize(s);
+  // the host vectors vNf and g must outlive the copies, and a kernel fault of the last launches
+  // surfaces only here: both need the synchronisation before the status is final
+  const cudaError_t se = cudaStreamSynchronize(s);
+  if (ce == cudaSuccess) ce = se;
+  if (ce == cudaSuccess) ce = cudaGetLastError();
   cudaFree(buf);
+  if (st == EFE_OK && ce != cudaSuccess) {
+    o.err = std::string("octree step: ") + cudaGetErrorString(ce);
+    st = EFE_ERR_CUDA;
+  }
   return st;
 }
 
@@ -1261,9 +1271,14 @@ static efe_status octree_step(efe_octree* oct, double* psi, int n_orb, const dou
 extern "C" efe_status efe_octree_magnus_step(efe_octree* oct, double* psi_bar_dev, int32_t n_orb, const double* occ_host,
                                              const double* atoms_host, int32_t n_atoms, const double* field_host,
                                              double dt, int32_t k, double cg_tol, int32_t xc, void* stream) {
-  if (!oct || !psi_bar_dev || !occ_host || (n_atoms > 0 && !atoms_host) || n_atoms < 0 || !field_host ||
-      n_orb < 1 || 2 * n_orb > 65535 || k < 1 || k > 64 || !(cg_tol > 0.0))
+  if (!oct) return EFE_ERR_ARG;
+  if (!psi_bar_dev || !occ_host || (n_atoms > 0 && !atoms_host) || n_atoms < 0 || !field_host || n_orb < 1 ||
+      2 * n_orb > 65535 || k < 1 || k > 64 || !(cg_tol > 0.0) || !std::isfinite(dt) || !(dt > 0.0) ||
+      (xc != EFE_XC_PW92 && xc != EFE_XC_PZ81)) {
+    oct->o.err = "efe_octree_magnus_step: bad arguments (null pointer, n_orb outside 1..32767, k outside 1..64, "
+                 "cg_tol <= 0, dt not finite and > 0, or an unknown xc)";
     return EFE_ERR_ARG;
+  }
   return efe::octree_step(oct, psi_bar_dev, n_orb, occ_host, atoms_host, n_atoms, field_host, dt, k, cg_tol, xc,
                           reinterpret_cast<cudaStream_t>(stream));
 }

@@ -11,12 +11,20 @@ if ROOT not in sys.path:
 
 
 # GPU test modules of the newest components run after the rest of the suite, so
-# that under -x a failure there cannot hide the results of the established tests.
+# that under -x a failure there cannot hide the results of the established tests;
+# modules named test_zz_* run after those, last of all.
 RUN_LAST = ("test_gpu_electrostatic.py", "test_gpu_octree.py")
 
 
+def _order(item):
+    name = os.path.basename(str(item.fspath))
+    if name.startswith("test_zz_"):
+        return 2
+    return 1 if name in RUN_LAST else 0
+
+
 def pytest_collection_modifyitems(config, items):
-    items.sort(key=lambda it: os.path.basename(str(it.fspath)) in RUN_LAST)
+    items.sort(key=_order)
 
 
 def pytest_configure(config):

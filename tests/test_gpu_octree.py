@@ -57,7 +57,8 @@ def test_octree_apply_matches_oracle(name, mask):
         I = ~m.boundary_free
         ref_y = np.zeros_like(Xo)
         ref_y[I] = H[I][:, I] @ Xo[I]
-        scale = abs(H[I][:, I]) @ np.abs(Xo[I])
+        scale = np.zeros_like(Xo)                   # full free-node length: indexed by perm below
+        scale[I] = abs(H[I][:, I]) @ np.abs(Xo[I])
     else:
         ref_y = H @ Xo
         scale = abs(H) @ np.abs(Xo)
@@ -269,11 +270,12 @@ def test_octree_magnus_step_matches_oracle():
     pos = {k: j for j, k in enumerate(_key(m.nodes[m.free]))}
     perm = np.array([pos[k] for k in _key(fx)])
     rng = np.random.default_rng(8)
-    psi = 0.3 * (rng.standard_normal((o.n_free, 2)) + 1j * rng.standard_normal((o.n_free, 2)))
+    psi = rng.standard_normal((o.n_free, 2)) + 1j * rng.standard_normal((o.n_free, 2))
     psi[bnd] = 0.0
+    psi /= np.linalg.norm(psi, axis=0)       # neutral: occ . ||psi||^2 = sum Z (the Dirichlet data's premise)
     po = np.zeros_like(psi)
     po[perm] = psi
-    occ, E = np.array([2.0, 1.0]), np.array([0.0, 0.0, 0.01])
+    occ, E = np.array([1.0, 1.0]), np.array([0.0, 0.0, 0.01])
     ref_out = m.magnus_step(po, occ, Z, R, 0.05, 8, E)
     g = torch.from_numpy(np.ascontiguousarray(psi)).cuda()
     o.magnus_step(g, occ, Z, np.array(R), 0.05, 8, field=E, cg_tol=1e-13)
