@@ -89,8 +89,9 @@ struct Operator {
 struct TcState {
   int batch = 0;                  // members the slices are allocated for
   unsigned char* H = nullptr;     // [batch][nc][4 slices][128 x 128 bf16]
-  int* rexp = nullptr;            // [batch][nc][128] row exponents of [H_c E_c]
-  unsigned char* E = nullptr;     // [batch][e_total][2048 B]: E_c then E_c^T slices per cell
+  int* rexp = nullptr;            // [batch][nc][128] row exponents of H_c
+  int* rexpE = nullptr;           // [batch][nc][128] row exponents of E_c
+  unsigned char* E = nullptr;     // [batch][e_total][2048 B]: per cell, [E_c slice i | E_c^T slice i], i = 0..3
   int* hexp = nullptr;            // [batch][n_pairs] row exponents of E_c^T
   long long* eoff = nullptr;      // [nc + 1] prefix sums of the padded function counts
   long long e_total = 0;

@@ -8,39 +8,47 @@
 // VeffDiscrete; P1^3 <= 128 nodes at degree <= 4) and E_c the cell's block of the
 // classical-enriched coupling.  These are dense contractions, so they run on the
 // tensor cores with an exact-product splitting: every float64 operand is scaled by a
-// power of two per row (rows of [H_c E_c], rows of E_c^T) or per column (of
-// [x^C; x^E]), rounded to 31 bits and cut into four bf16 slices of 7 + 8 + 8 + 8
-// bits.  A product of two slices is exact in binary32.  Slice pairs whose indices
-// sum to 0 are accumulated in one tensor-memory accumulator and pairs summing to 1
-// in a second: both sums are exact (at most 2 x 176 terms on a grid of 2^-14 resp.
-// 2^-22, below 2^24 grid steps).  Pairs summing to 2, 3 or 4 go to a third
-// accumulator, whose binary32 rounding is ~2^-39 of the scales; pairs summing to 5
-// or 6 are dropped (each below 2^-38 of the scales).  The result is
-// 2^(row + column exponent) (acc0 + acc1 + acc2), formed in float64.  Per element of
-// y the error is a few 2^-31 of sum_k |A_ik| max_k |x_k|.  Two choices matter here:
-// a pair (k, l) carries up to 2^(2 - 8(k + l)) of the scales whatever the size of
-// its product, and a typical entry is ~2^-7 of its row's largest, so stopping at
-// k + l = 3 would leave binary32-level (2^-30 of the scales) errors; and with one
-// accumulator for every pair past the first, the exact but large cross terms
-// a0 b1 + a1 b0 would round the finer groups away at binary32's relative 2^-24.
+// power of two per row (rows of H_c, rows of E_c, rows of E_c^T) or per column (of
+// x^C, of x^E; each its own), rounded to 31 bits and cut into four bf16 slices on
+// the grids 2^-7, 2^-15, 2^-23, 2^-31.  A product of two slices is exact in
+// binary32.  Slice pairs whose indices sum to 0 are accumulated in one
+// tensor-memory accumulator and pairs summing to 1 in a second: both sums are exact
+// (at most 2 x 128 terms on a grid of 2^-14 resp. 2^-22, below 2^24 grid steps).
+// Pairs summing to 2, 3 or 4 go to a third accumulator, whose binary32 rounding is
+// ~2^-39 of the scales; pairs summing to 5 or 6 are dropped (each below 2^-38 of the
+// scales).  A product is 2^(row + column exponent) (acc0 + acc1 + acc2), formed in
+// 64-bit fixed point and float64 on the integer pipes.  Per element of y the error is
+// a few 2^-31 of sum_k |A_ik| max_k |x_k| for each of the products separately.
+//
+// Separate scales: in cells near a nucleus the enrichment part of an orbital is many
+// orders of magnitude larger than its classical part, so x^C and x^E have their own
+// column exponents (and E_c its own row exponents).  The products therefore have
+// their own accumulators: first the E pass (E_c x^E and E_c^T x^C), whose classical
+// part is carried in registers as 64-bit fixed point, then the H pass (H_c x^C), added
+// to it on the integer pipes before the one float64 value per output is formed.
 //
 // Layout: the A operands (H_c slices, E_c and E_c^T slices) are written when the
 // operator is built, directly in the shared-memory image the MMA reads (no-swizzle
-// K-major core matrices, see tc.cuh), so the apply copies them with plain 16-byte
-// copies.  The apply is a persistent kernel, one CTA of 512 threads per SM:
-//   gather x_bar^C and x^E, x^C = D x_bar^C, per-column exponents, split into 4 slices
-//   (smem); all float64 work is done on the integer pipes from bit patterns (GB300's
-//   float64 pipe is ~1/64 of its float32 pipe).  The output-side D is folded into the
-//   rows of H_c and E_c when they are built.
-//   for slice i of H_c / E_c / E_c^T (copied into smem, next slices prefetched to L2):
-//       one thread issues the MMAs of the pairs (i, j), i + j <= 4, commits to an
-//       mbarrier; all threads wait (bounded)
-//   epilogue: accumulators -> exact 64-bit fixed point -> float64 -> y_bar^C, y^E
-//   (atomic adds)
+// K-major core matrices, see tc.cuh), so the apply streams them into a two-slot ring
+// with bulk asynchronous copies (cp.async.bulk, completion counted on an mbarrier).
+// The apply is persistent, one CTA per SM, warp-specialised:
+//   16 work warps: gather x_bar^C (rows of the cell's nodes) and x^E, x^C = D x_bar^C
+//     in float32 pairs, per-column exponents, digit extraction into 4 bf16 slices
+//     (shared memory); after the MMAs the epilogues: accumulators -> fixed point ->
+//     float64, E_c^T x^C to y^E (atomic adds), y_c staged in shared memory and
+//     scattered row by row (coalesced atomic adds; plain stores for the cell's
+//     interior nodes, which no other cell touches);
+//   1 issuer warp: one thread streams the A slices (E pass: E_c slice i with E_c^T
+//     slice i; H pass: H_c slice i) and issues the MMAs of the slice pairs (i, j),
+//     i + j <= 4, committing to mbarriers that free ring slots and release the
+//     epilogues.  Every wait is bounded: a wait that gives up sets an error flag the
+//     host reads (EFE_ERR_TIMEOUT), waits (bounded) for the copies and MMAs in
+//     flight and frees the tensor memory before returning.
 #include <cstdio>
 #include <vector>
 
 #include "efe_internal.h"
+#include "sumfact.cuh"
 #include "tc.cuh"
 
 namespace efe {
@@ -50,28 +58,60 @@ namespace {
 constexpr int kSlices = 4;
 constexpr int kMaxGroup = 4;                    // slice pairs (i, j) with i + j <= 4 are formed
 constexpr int kK = 128;                         // padded node dimension
-constexpr int kSliceBytes = 128 * kK * 2;       // one 128 x 128 bf16 slice
+constexpr int kSliceBytes = 128 * kK * 2;       // one 128 x 128 bf16 slice of H_c
 constexpr int kMaxKE = 48;                      // enrichment functions per cell
 constexpr int kMaxN = 96;                       // real columns per batch member
 constexpr int kZero = -100000;                  // exponent of an all-zero row or column
 constexpr uint32_t kWaitLimit = 1u << 22;       // mbarrier polls before giving up (seconds)
 
+// the apply kernel: kWork / 32 work warps (a multiple of 4: the tensor-memory lane quarters) and one
+// issuer warp; 13 warps leave 128 registers per thread
+#ifndef EFE_TC_WORK_WARPS
+#define EFE_TC_WORK_WARPS 12
+#endif
+constexpr int kWork = 32 * EFE_TC_WORK_WARPS;
+constexpr int kApplyThreads = kWork + 32;
+constexpr int kWPQ = EFE_TC_WORK_WARPS / 4;                 // work warps per lane quarter
+constexpr int kNQ = (kMaxN / 8 + kWPQ - 1) / kWPQ;          // 8-column chunks per thread in an epilogue
+constexpr int kNK = ((kK / 8) * kMaxN + kWork - 1) / kWork; // gather items per thread
+constexpr int kNSlot = 2;                                   // ring slots for the streamed A operands
 // shared-memory map of the apply kernel (bytes)
-constexpr int kXs = 0;                                   // 4 slices x 128 x 128 (x^C, K-major)
-constexpr int kXEs = kXs + kSlices * kSliceBytes;        // 4 slices x 96 x 48   (x^E, K-major)
-constexpr int kXEslice = kMaxN * kMaxKE * 2;
-constexpr int kAH = kXEs + kSlices * kXEslice;           // H_c slice i
-constexpr int kAEA = kAH + kSliceBytes;                  // E_c slice i      (128 x KEp)
-constexpr int kAET = kAEA + 128 * kMaxKE * 2;            // E_c^T slice i    (KEp x 128)
-constexpr int kMisc = kAET + kMaxKE * kK * 2;
-constexpr int kApplySmem = kMisc + 128 * 8 * 2 + 128 * 4 + (96 + 96 + 128 + 48 + 48) * 4 + 16;
-constexpr int kApplyThreads = 512;
-constexpr int kMaxPer = 26;                     // nodes gathered per thread (even; 512 / 96 >= 5 groups)
+constexpr int kXslice = kMaxN * kK * 2;                     // x^C slice: 96 rows (columns n) x 128 nodes
+constexpr int kXs = 0;                                      // 4 x^C slices; y_c staging after the MMAs
+constexpr int kXEslice = kMaxN * kMaxKE * 2;                // x^E slice: 96 rows x 48 functions
+constexpr int kXEs = kXs + kSlices * kXslice;
+constexpr int kRing = kXEs + kSlices * kXEslice;            // kNSlot x 32 KB
+constexpr int kMisc = kRing + kNSlot * kSliceBytes;
+constexpr int kStageLd = kMaxN + 1;                         // staging row stride (doubles; odd: no bank conflicts)
+static_assert(125 * kStageLd * 8 <= kSlices * kXslice, "y_c staging (at most 125 nodes) must fit the x^C slices");
+// misc block: the metadata of the cell being processed and of the next one (two buffers)
+constexpr int kMgS = kMisc;                                 // long long [2][128] offset of each node's row in X, Y
+constexpr int kMrH = kMgS + 2 * 128 * 8;                    // int [2][128] H_c row exponents
+constexpr int kMrE = kMrH + 2 * 128 * 4;                    // int [2][128] E_c row exponents
+constexpr int kMhx = kMrE + 2 * 128 * 4;                    // int [2][48] E_c^T row exponents
+constexpr int kMfn = kMhx + 2 * kMaxKE * 4;                 // int [2][48] enrichment functions of the cell
+constexpr int kMcC = kMfn + 2 * kMaxKE * 4;                 // int [96] column maxima of |x^C| (binary32 bits)
+constexpr int kMcE = kMcC + kMaxN * 4;                      // int [96] column maxima of |x^E|
+constexpr int kMfC = kMcE + kMaxN * 4;                      // int [96] column exponents of x^C
+constexpr int kMfE = kMfC + kMaxN * 4;                      // int [96] column exponents of x^E
+constexpr int kMbar = kMfE + kMaxN * 4;                     // uint64 [10] mbarriers
+constexpr int kMtm = kMbar + 10 * 8;                        // uint32 tensor-memory base, int abort flag
+constexpr int kApplySmem = kMtm + 16;
+static_assert(kApplySmem <= 232448, "apply kernel exceeds the shared memory of a CTA");
+// mbarrier indices
+enum { kBFull0 = 0, kBEmpty0 = kNSlot, kBXready = 2 * kNSlot, kBAccE, kBDrainedE, kBAccH, kBFin };
+static_assert(kBFin < 10, "mbarrier block too small");
 
 __device__ __forceinline__ long long q31(double v, int e) { return e == kZero ? 0LL : tc::q31_bits(v, e); }
 __device__ __forceinline__ int exp_of_max(double mx) {
   const int be = tc::biased_exp(mx);
   return (be == 0 || be - 1022 < -990) ? kZero : tc::scale_exp(be);
+}
+// column exponent from the binary32 bits of a column's largest |value|: |x| < 2^e
+__device__ __forceinline__ int exp_of_maxbits(int bits) {
+  if (bits <= 0) return kZero;
+  const int e = (bits >> 23) - 126;
+  return e < -125 ? kZero : (e > 126 ? 126 : e);
 }
 // eight consecutive values of one core-matrix row, scaled by 2^-e, stored as four
 // 16-byte slice rows at dst + s * stride
@@ -89,23 +129,41 @@ __device__ __forceinline__ void store_slices8(const double* v, int e, unsigned c
   for (int s = 0; s < kSlices; ++s)
     *reinterpret_cast<uint4*>(dst + s * stride) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
 }
+// eight consecutive values (a_t + b_t) 2^-e of one core-matrix row as four 16-byte slice rows
+__device__ __forceinline__ void store_digits8(const float* a, const float* b, float sc, unsigned char* dst,
+                                              int stride) {
+  uint32_t w[kSlices][4];
+#pragma unroll
+  for (int t = 0; t < 8; t += 2) {
+    uint32_t d0[kSlices], d1[kSlices];
+    tc::digits4(__fmul_rn(a[t], sc), __fmul_rn(b[t], sc), d0);
+    tc::digits4(__fmul_rn(a[t + 1], sc), __fmul_rn(b[t + 1], sc), d1);
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) w[s][t / 2] = tc::pack_hi16(d0[s], d1[s]);
+  }
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s)
+    *reinterpret_cast<uint4*>(dst + s * stride) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+}
 
 }  // namespace
 
 // ----------------------------------------------------------------------------
 // build: dense H_c in float64 by sum factorisation, row exponents, slices of H_c,
-// E_c (rows scaled with H_c's) and E_c^T (rows scaled per function).
+// E_c (rows scaled by their own exponents) and E_c^T (rows scaled per function).
 //   M_c[i][j] = sum_q W_q prod_d B1[q_d][i_d] B1[q_d][j_d]
 //   K_c[i][j] = kx K1 M1 M1 + ky M1 K1 M1 + kz M1 M1 K1        (axis order x, y, z)
-// One block of 256 threads per (cell, member).
+// One block of 256 threads per (cell, member).  The enrichment data of a cell are laid
+// out slice by slice, [E_c slice i | E_c^T slice i] for i = 0..3, so that each stage of
+// the apply's E pass is one contiguous copy.
 // ----------------------------------------------------------------------------
 template <int P1, int NQ1>
 __global__ void __launch_bounds__(256)
 k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ W64, double kin,
            const int* __restrict__ pair_start, const double* __restrict__ E64, long long n_pairs,
            const double* __restrict__ Dsc, const long long* __restrict__ eoff, long long e_total,
-           unsigned char* __restrict__ tcH,
-           int* __restrict__ tcRexp, unsigned char* __restrict__ tcE, int* __restrict__ tcHexp) {
+           unsigned char* __restrict__ tcH, int* __restrict__ tcRexpH, int* __restrict__ tcRexpE,
+           unsigned char* __restrict__ tcE, int* __restrict__ tcHexp) {
   constexpr int NN = P1 * P1 * P1;
   constexpr int S3 = NQ1 * NQ1 * NQ1;
   constexpr int PP = P1 * P1;
@@ -116,8 +174,9 @@ k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const dou
   double* T2 = T1 + PP * NQ1 * NQ1;    // [(a a') PP + (b b')][q3]
   double* H = T2 + PP * PP * NQ1;      // [NN][NN]
   double* Dn = H + NN * NN;           // D = mask / sqrt(M) at the cell's nodes
-  int* rexp = reinterpret_cast<int*>(Dn + 128);
-  int* hexp = rexp + 128;
+  int* rexpH = reinterpret_cast<int*>(Dn + 128);
+  int* rexpE = rexpH + 128;
+  int* hexp = rexpE + 128;
   const int c = blockIdx.x, m = blockIdx.y, tid = threadIdx.x;
   int cx, cy, cz;
   cell_ijk(mesh, c, cx, cy, cz);
@@ -154,7 +213,7 @@ k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const dou
     const double Ka = tab.K1[a * P1 + a2], Kb = tab.K1[b * P1 + b2], Kc = tab.K1[cc * P1 + c2];
     const double Ma = tab.M1[a * P1 + a2], Mb = tab.M1[b * P1 + b2], Mc = tab.M1[cc * P1 + c2];
     acc += kx * Ka * Mb * Mc + ky * Ma * Kb * Mc + kz * Ma * Mb * Kc;
-    H[it] = Dn[i] * acc;   // the output side of the Loewdin scaling, folded in (rows keep one scale)
+    H[it] = Dn[i] * acc * Dn[j];   // both sides of the Loewdin scaling folded in: the apply gathers x_bar
   }
   int p0 = 0, np = 0;
   if (pair_start) {
@@ -163,19 +222,21 @@ k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const dou
   }
   const double* Ec = E64 + ((long long)m * n_pairs + p0) * NN;
   __syncthreads();
-  // row exponents, joint over the row of H_c and the row of E_c (one accumulator)
+  // row exponents: H_c rows and E_c rows each their own
   for (int i = tid; i < 128; i += blockDim.x) {
-    double mx = 0.0;
+    double mh = 0.0, me = 0.0;
     if (i < NN) {
-      for (int j = 0; j < NN; ++j) mx = fmax(mx, fabs(H[i * NN + j]));
-      for (int f = 0; f < np; ++f) mx = fmax(mx, fabs(Dn[i] * Ec[(long long)f * NN + i]));
+      for (int j = 0; j < NN; ++j) mh = fmax(mh, fabs(H[i * NN + j]));
+      for (int f = 0; f < np; ++f) me = fmax(me, fabs(Dn[i] * Ec[(long long)f * NN + i]));
     }
-    rexp[i] = i < NN ? exp_of_max(mx) : kZero;
-    tcRexp[((long long)m * mesh.nc + c) * 128 + i] = rexp[i];
+    rexpH[i] = i < NN ? exp_of_max(mh) : kZero;
+    rexpE[i] = i < NN ? exp_of_max(me) : kZero;
+    tcRexpH[((long long)m * mesh.nc + c) * 128 + i] = rexpH[i];
+    tcRexpE[((long long)m * mesh.nc + c) * 128 + i] = rexpE[i];
   }
   for (int f = tid; f < np; f += blockDim.x) {
     double mx = 0.0;
-    for (int i = 0; i < NN; ++i) mx = fmax(mx, fabs(Ec[(long long)f * NN + i]));
+    for (int i = 0; i < NN; ++i) mx = fmax(mx, fabs(Ec[(long long)f * NN + i] * Dn[i]));
     hexp[f] = exp_of_max(mx);
     tcHexp[(long long)m * n_pairs + p0 + f] = hexp[f];
   }
@@ -192,13 +253,13 @@ k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const dou
       const int k = kc * 8 + t;
       v[t] = (i < NN && k < NN) ? H[i * NN + k] : 0.0;
     }
-    store_slices8(v, rexp[i], Hc + tc::kmajor_offset(i, kc * 8, 2048), kSliceBytes);
+    store_slices8(v, rexpH[i], Hc + tc::kmajor_offset(i, kc * 8, 2048), kSliceBytes);
   }
   if (np > 0) {
     const int KEp = (np + 15) & ~15;
     const long long eb = 256LL * KEp;   // bytes of one 128 x KEp slice
     unsigned char* Eb = tcE + ((long long)m * e_total + eoff[c]) * 2048;
-    // E_c (rows i, K = f), rows scaled with H_c's
+    // E_c (rows i, K = f), rows scaled by rexpE; slice s at Eb + 2 s eb
     const int nfc = KEp / 8;
     for (int it = tid; it < 128 * nfc; it += blockDim.x) {
       const int i8 = it & 7, fc = (it >> 3) % nfc, ig = (it >> 3) / nfc;
@@ -209,9 +270,10 @@ k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const dou
         const int f = fc * 8 + t;
         v[t] = (i < NN && f < np) ? Dn[i] * Ec[(long long)f * NN + i] : 0.0;
       }
-      store_slices8(v, rexp[i], Eb + tc::kmajor_offset(i, fc * 8, 16 * KEp), eb);
+      store_slices8(v, rexpE[i], Eb + tc::kmajor_offset(i, fc * 8, 16 * KEp), 2 * eb);
     }
-    // E_c^T (rows f, K = i), rows scaled by hexp
+    // E_c^T D (rows f, K = i; the input side of the Loewdin scaling folded in), rows scaled by
+    // hexp; slice s at Eb + (2 s + 1) eb
     for (int it = tid; it < KEp * (kK / 8); it += blockDim.x) {
       const int f8 = it & 7, ic = (it >> 3) & 15, fg = it >> 7;
       const int f = fg * 8 + f8;
@@ -219,51 +281,74 @@ k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const dou
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int i = ic * 8 + t;
-        v[t] = (f < np && i < NN) ? Ec[(long long)f * NN + i] : 0.0;
+        v[t] = (f < np && i < NN) ? Ec[(long long)f * NN + i] * Dn[i] : 0.0;
       }
-      store_slices8(v, f < np ? hexp[f] : kZero, Eb + 4 * eb + tc::kmajor_offset(f, ic * 8, 2048), eb);
+      store_slices8(v, f < np ? hexp[f] : kZero, Eb + eb + tc::kmajor_offset(f, ic * 8, 2048), 2 * eb);
+    }
+  }
+}
+
+// x_bar of one cell into registers: item it = tid + k kWork is (chunk it / cols of 8 nodes, column
+// it % cols); gS: offsets of the cell's node rows (column offset of the member included)
+template <int NN>
+__device__ __forceinline__ void gather_rows(const double* __restrict__ X, const long long* gS, int tid, int cols,
+                                            int nitem, double (&v)[kNK][8]) {
+#pragma unroll
+  for (int k = 0; k < kNK; ++k) {
+    const int it = tid + k * kWork;
+    const int ch = it / cols, n = it - (it / cols) * cols;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int l = ch * 8 + t;
+      v[k][t] = (it < nitem && l < NN) ? X[gS[l] + n] : 0.0;
     }
   }
 }
 
 // ----------------------------------------------------------------------------
-// apply (persistent; one CTA per SM)
+// apply (persistent; one CTA per SM; 16 work warps + 1 issuer warp)
 // ----------------------------------------------------------------------------
 template <int P1>
 __global__ void __launch_bounds__(kApplyThreads, 1)
 k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict__ Y, long long ld2, int cols, int nm,
            int batch, const double* __restrict__ Dsc, const unsigned char* __restrict__ tcH,
-           const int* __restrict__ tcRexp, const unsigned char* __restrict__ tcE, long long e_total,
-           const long long* __restrict__ eoff, const int* __restrict__ tcHexp, const int* __restrict__ pair_start,
-           const int* __restrict__ pair_fn, long long n_pairs, const double* __restrict__ xE, double* __restrict__ yE,
-           int* __restrict__ err, const int* __restrict__ gate) {
+           const int* __restrict__ tcRexpH, const int* __restrict__ tcRexpE, const unsigned char* __restrict__ tcE,
+           long long e_total, const long long* __restrict__ eoff, const int* __restrict__ tcHexp,
+           const int* __restrict__ pair_start, const int* __restrict__ pair_fn, long long n_pairs,
+           const double* __restrict__ xE, double* __restrict__ yE, int* __restrict__ err,
+           const int* __restrict__ gate) {
   constexpr int NN = P1 * P1 * P1;
-  constexpr int NT = kApplyThreads;
   extern __shared__ __align__(1024) unsigned char sm[];
-  long long* gS = reinterpret_cast<long long*>(sm + kMisc);   // [128] global node of each cell node
-  unsigned long long* dm = reinterpret_cast<unsigned long long*>(gS + 128);   // [128] significand of D
-  int* de = reinterpret_cast<int*>(dm + 128);                 // [128] exponent of D
-  int* colmax = de + 128;                                     // [96]
-  int* fexp = colmax + 96;                                    // [96] column exponents
-  int* rexp = fexp + 96;                                      // [128] row exponents
-  int* hexp = rexp + 128;                                     // [48] E_c^T row exponents
-  int* fns = hexp + 48;                                       // [48] enrichment functions of the cell
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(fns + 48);
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(mbar + 1);
-  int* abort_flag = reinterpret_cast<int*>(tbase + 1);
+  long long* gS2 = reinterpret_cast<long long*>(sm + kMgS);
+  int* rexpH2 = reinterpret_cast<int*>(sm + kMrH);
+  int* rexpE2 = reinterpret_cast<int*>(sm + kMrE);
+  int* hexp2 = reinterpret_cast<int*>(sm + kMhx);
+  int* fns2 = reinterpret_cast<int*>(sm + kMfn);
+  int* cmaxC = reinterpret_cast<int*>(sm + kMcC);
+  int* cmaxE = reinterpret_cast<int*>(sm + kMcE);
+  int* fC = reinterpret_cast<int*>(sm + kMfC);
+  int* fE = reinterpret_cast<int*>(sm + kMfE);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kMbar);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(sm + kMtm);
+  // abort flag: written only before, and read only after, a barrier of the work warps (so that they
+  // all leave the cell loop at the same barrier); the issuer warp only reads it
+  volatile int* wabort = reinterpret_cast<volatile int*>(sm + kMtm + 4);
+  double* stage = reinterpret_cast<double*>(sm + kXs);
   if (gate && *gate == 0) return;   // every Lanczos column has converged (graph-captured loops)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // gather mapping: thread (group g, column n) owns column n of the nodes
-  // [g per, (g + 1) per); per is even so that node pairs share a 4-byte slot
-  const int G = NT / cols;
-  const int per = 2 * ((NN + 2 * G - 1) / (2 * G));
-  const int gg = tid / cols, gn = tid - gg * cols;
-  const bool active = gg < G;
-  // operand images start zeroed: rows n >= cols and nodes l >= NN of x^C stay zero
-  for (int o = tid * 16; o < kAH; o += NT * 16) *reinterpret_cast<uint4*>(sm + o) = make_uint4(0, 0, 0, 0);
+  // operand images start zeroed: padding rows and nodes l >= NN stay finite
+  for (int o = tid * 16; o < kRing; o += kApplyThreads * 16) *reinterpret_cast<uint4*>(sm + o) = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
-    tc::mbar_init(mbar, 1);
-    *abort_flag = 0;
+    for (int b = 0; b < kNSlot; ++b) {
+      tc::mbar_init(&bar[kBFull0 + b], 1);
+      tc::mbar_init(&bar[kBEmpty0 + b], 1);
+    }
+    tc::mbar_init(&bar[kBXready], 1);
+    tc::mbar_init(&bar[kBAccE], 1);
+    tc::mbar_init(&bar[kBDrainedE], 1);
+    tc::mbar_init(&bar[kBAccH], 1);
+    tc::mbar_init(&bar[kBFin], 1);
+    *wabort = 0;
   }
   if (warp == 0) tc::tmem_alloc(tbase, 512);
   tc::fence_proxy_async();
@@ -271,237 +356,405 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tm = *tbase;
-  uint32_t phase = 0;
-  const uint32_t idm = tc::idesc_bf16(128, nm);
   const long long nwork = (long long)mesh.nc * batch;
-  const uint32_t xs = tc::smem_u32(sm + kXs), xes = tc::smem_u32(sm + kXEs), ah = tc::smem_u32(sm + kAH),
-                 aea = tc::smem_u32(sm + kAEA), aet = tc::smem_u32(sm + kAET);
-  bool aborted = false;
-  for (long long w = blockIdx.x; w < nwork && !aborted; w += gridDim.x) {
-    const int c = (int)(w % mesh.nc), m = (int)(w / mesh.nc);
-    const int col0 = m * cols;
-    int p0 = 0, np = 0;
-    if (pair_start) {
-      p0 = pair_start[c];
-      np = pair_start[c + 1] - p0;
-    }
-    const int KEp = (np + 15) & ~15;
-    const long long eb = 256LL * KEp;
-    const unsigned char* Hc = tcH + ((long long)m * mesh.nc + c) * kSlices * kSliceBytes;
-    const unsigned char* Ec = np > 0 ? tcE + ((long long)m * e_total + eoff[c]) * 2048 : nullptr;
-    auto load_set = [&](int i) {
-      for (int o = tid * 16; o < kSliceBytes; o += NT * 16) tc::cp_async16(sm + kAH + o, Hc + i * kSliceBytes + o);
-      if (np > 0)
-        for (int o = tid * 16; o < eb; o += NT * 16) {
-          tc::cp_async16(sm + kAEA + o, Ec + i * eb + o);
-          tc::cp_async16(sm + kAET + o, Ec + 4 * eb + i * eb + o);
-        }
+  const uint32_t xs = tc::smem_u32(sm + kXs), xes = tc::smem_u32(sm + kXEs), ring = tc::smem_u32(sm + kRing);
+
+  if (warp == kWork / 32) {
+    // ------------------------------------------------------------ issuer warp
+    // The whole warp runs the loops (operands stay warp-uniform); lane 0 waits on the mbarriers and
+    // its verdict is broadcast, lane 0 issues the copies, MMAs and commits.
+    auto wait = [&](uint64_t* b, uint32_t par) {
+      bool ok = true;
+      if (lane == 0) ok = tc::mbar_wait(b, par, kWaitLimit);
+      return __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
     };
-    load_set(0);
-    // the remaining slices of this cell and the first of the next one, into L2
-    for (int o = tid * 128; o < 3 * kSliceBytes; o += NT * 128)
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(Hc + kSliceBytes + o));
-    if (np > 0)
-      for (int o = tid * 128; o < 3 * eb; o += NT * 128) {
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(Ec + eb + o));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(Ec + 5 * eb + o));
+    auto cell_np = [&](long long w) {
+      const int c = (int)(w % mesh.nc);
+      return pair_start ? pair_start[c + 1] - pair_start[c] : 0;
+    };
+    // stage s of a cell: E pass stages 0..3 (cells coupled to enrichment functions), then the H
+    // pass stages; the ring is refilled NSLOT - 1 stages ahead of the MMAs
+    long long cw = blockIdx.x;   // copy cursor: cell and stage
+    int cst = 0, cnp = cw < nwork ? cell_np(cw) : 0;
+    long long issued = 0, consumed = 0;
+    uint32_t fparb = 0, eparb = 0;   // phase parities of the full / empty barriers, bit = slot
+    uint32_t xpar = 0, dpar = 0;
+    auto issue_copy = [&]() -> bool {
+      if (cw >= nwork) return true;
+      const int slot = (int)(issued % kNSlot);
+      if (issued >= kNSlot) {
+        if (!wait(&bar[kBEmpty0 + slot], (eparb >> slot) & 1u)) return false;
+        eparb ^= 1u << slot;
       }
-    if (w + gridDim.x < nwork) {
-      const unsigned char* Hn = tcH + (w + gridDim.x) * kSlices * kSliceBytes;
-      for (int o = tid * 128; o < kSliceBytes; o += NT * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(Hn + o));
-    }
-    int cx, cy, cz;
-    cell_ijk(mesh, c, cx, cy, cz);
-    for (int l = tid; l < 128; l += NT) {
-      if (l < NN) {
-        const long long g = node_index(mesh, cx, cy, cz, l % P1, (l / P1) % P1, l / (P1 * P1));
-        gS[l] = g;
-        const tc::Wide d = tc::wide_of(Dsc[g]);
-        dm[l] = d.m;
-        de[l] = d.e;
+      const int c = (int)(cw % mesh.nc), m = (int)(cw / mesh.nc);
+      const unsigned char* src;
+      uint32_t bytes;
+      if (cnp > 0 && cst < kSlices) {
+        const long long eb = 256LL * ((cnp + 15) & ~15);
+        src = tcE + ((long long)m * e_total + eoff[c]) * 2048 + 2 * cst * eb;
+        bytes = (uint32_t)(2 * eb);
+      } else {
+        const int i = cnp > 0 ? cst - kSlices : cst;
+        src = tcH + ((long long)m * mesh.nc + c) * kSlices * kSliceBytes + (long long)i * kSliceBytes;
+        bytes = kSliceBytes;
       }
-      rexp[l] = tcRexp[((long long)m * mesh.nc + c) * 128 + l];
-    }
-    for (int f = tid; f < np; f += NT) {
-      fns[f] = pair_fn[p0 + f];
-      hexp[f] = tcHexp[(long long)m * n_pairs + p0 + f];
-    }
-    for (int n = tid; n < 96; n += NT) colmax[n] = 0;
-    if (np > 0)
-      for (int o = tid * 16; o < kSlices * kXEslice; o += NT * 16)
-        *reinterpret_cast<uint4*>(sm + kXEs + o) = make_uint4(0, 0, 0, 0);
-    __syncthreads();
-    // gather x_bar^C into registers, every load issued first; x^C = D x_bar^C is formed
-    // (64-bit significand product) on the integer pipes
-    const int l0 = gg * per;
-    double xv[kMaxPer];
-#pragma unroll
-    for (int j = 0; j < kMaxPer; ++j) {
-      xv[j] = 0.0;
-      if (active && j < per && l0 + j < NN) xv[j] = X[gS[l0 + j] * ld2 + col0 + gn];
-    }
-    int kmax = 0;
-#pragma unroll
-    for (int j = 0; j < kMaxPer; ++j)
-      if (active && j < per && l0 + j < NN)
-        kmax = max(kmax, tc::wide_key(tc::wide_mul(tc::wide_of(xv[j]), dm[l0 + j], de[l0 + j])));
-    for (int f = gg; active && f < np; f += G)
-      kmax = max(kmax, tc::wide_key(tc::wide_of(xE[(long long)fns[f] * ld2 + col0 + gn])));
-    if (active) atomicMax(&colmax[gn], kmax);
-    __syncthreads();
-    for (int n = tid; n < 96; n += NT) {
-      const int k = colmax[n];   // floor(log2 max|x|) + 2048
-      fexp[n] = k == 0 ? kZero : k - 2048 + 1;
-    }
-    __syncthreads();
-    // slices of x^C (rows n, K = node), two nodes per 4-byte store, and of x^E
-    if (active) {
-      const int fe = fexp[gn];
-#pragma unroll
-      for (int j = 0; j < kMaxPer; j += 2) {
-        const int l = l0 + j;
-        if (j < per && l < NN) {
-          uint16_t s0[kSlices], s1[kSlices];
-          const tc::Wide x0 = tc::wide_mul(tc::wide_of(xv[j]), dm[l], de[l]);
-          tc::split4(fe == kZero ? 0LL : tc::q31_wide(x0, fe), s0);
-          if (l + 1 < NN) {
-            const tc::Wide x1 = tc::wide_mul(tc::wide_of(xv[j + 1]), dm[l + 1], de[l + 1]);
-            tc::split4(fe == kZero ? 0LL : tc::q31_wide(x1, fe), s1);
-          } else {
-#pragma unroll
-            for (int k = 0; k < kSlices; ++k) s1[k] = 0;
-          }
-          const uint32_t off = tc::kmajor_offset(gn, l, 2048);
-#pragma unroll
-          for (int k = 0; k < kSlices; ++k)
-            *reinterpret_cast<uint32_t*>(sm + kXs + k * kSliceBytes + off) = (uint32_t)s0[k] | ((uint32_t)s1[k] << 16);
+      if (lane == 0) {
+        tc::mbar_expect_tx(&bar[kBFull0 + slot], bytes);
+        tc::bulk_g2s(sm + kRing + slot * kSliceBytes, src, bytes, &bar[kBFull0 + slot]);
+      }
+      ++issued;
+      if (++cst == (cnp > 0 ? 2 * kSlices : kSlices)) {
+        cst = 0;
+        cw += gridDim.x;
+        cnp = cw < nwork ? cell_np(cw) : 0;
+      }
+      return true;
+    };
+    bool ok = true;
+    for (int k = 0; k < kNSlot - 1 && ok; ++k) ok = issue_copy();
+    const uint32_t idH = tc::idesc_bf16(128, nm);
+    // x^C slice j as the B operand of H_c x^C and the A operand of E_c^T x^C: descriptor dX0 + j dXs
+    const uint64_t dX0 = tc::smem_desc(xs, tc::kLBO, 2048);
+    constexpr uint64_t dXs = (uint64_t)(kXslice >> 4);
+    for (long long w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+      const int np = cell_np(w);
+      const int KEp = (np + 15) & ~15;
+      const uint32_t eb = 256u * (uint32_t)KEp;
+      // the next cell's operator data, into L2
+      if (w + gridDim.x < nwork && lane == 0) {
+        const long long w2 = w + gridDim.x;
+        const int c2 = (int)(w2 % mesh.nc), m2 = (int)(w2 / mesh.nc);
+        tc::bulk_prefetch_l2(tcH + ((long long)m2 * mesh.nc + c2) * kSlices * kSliceBytes, kSlices * kSliceBytes);
+        const int np2 = cell_np(w2);
+        if (np2 > 0)
+          tc::bulk_prefetch_l2(tcE + ((long long)m2 * e_total + eoff[c2]) * 2048, (uint32_t)(2048 * ((np2 + 15) & ~15)));
+      }
+      if (!wait(&bar[kBXready], xpar)) { ok = false; break; }
+      xpar ^= 1u;
+      const uint64_t dXE0 = tc::smem_desc(xes, tc::kLBO, 16u * (uint32_t)KEp);   // x^E slice j: + j dXEs
+      constexpr uint64_t dXEs = (uint64_t)(kXEslice >> 4);
+      const uint32_t idT = tc::idesc_bf16(128, KEp > 0 ? KEp : 16);
+      const int ns = np > 0 ? 2 * kSlices : kSlices;
+      for (int st = 0; st < ns && ok; ++st) {
+        if (*wabort) { ok = false; break; }   // a work warp gave up
+        const int slot = (int)(consumed % kNSlot);
+        if (!wait(&bar[kBFull0 + slot], (fparb >> slot) & 1u)) { ok = false; break; }
+        fparb ^= 1u << slot;
+        const bool isE = np > 0 && st < kSlices;
+        const int i = isE ? st : (np > 0 ? st - kSlices : st);
+        if (!isE && i == 0 && np > 0) {
+          // the E pass's classical accumulators must be drained before the H pass reuses them
+          if (!wait(&bar[kBDrainedE], dpar)) { ok = false; break; }
+          dpar ^= 1u;
         }
-      }
-      for (int f = gg; f < np; f += G) {
-        uint16_t s[kSlices];
-        tc::split4(fe == kZero ? 0LL : tc::q31_wide(tc::wide_of(xE[(long long)fns[f] * ld2 + col0 + gn]), fe), s);
-        const uint32_t off = tc::kmajor_offset(gn, f, 16 * KEp);
-#pragma unroll
-        for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint16_t*>(sm + kXEs + k * kXEslice + off) = s[k];
-      }
-    }
-    // the next cell's rows of x_bar, into L2
-    if (w + gridDim.x < nwork) {
-      const long long w2 = w + gridDim.x;
-      const int c2 = (int)(w2 % mesh.nc), m2 = (int)(w2 / mesh.nc);
-      int ex, ey, ez;
-      cell_ijk(mesh, c2, ex, ey, ez);
-      const int lines = (cols * 8 + 127) / 128 + 1;   // 128-byte steps plus the row's last entry
-      for (int it = tid; it < NN * lines; it += NT) {
-        const int l = it / lines, q = it - l * lines;
-        const long long g = node_index(mesh, ex, ey, ez, l % P1, (l / P1) % P1, l / (P1 * P1));
-        const char* row = reinterpret_cast<const char*>(X + g * ld2 + (long long)m2 * cols);
-        const int off = q + 1 < lines ? 128 * q : cols * 8 - 8;
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(row + off));
-      }
-    }
-    tc::cp_async_wait_all();
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    for (int i = 0; i < kSlices; ++i) {
-      if (tid == 0) {
         tc::fence_after_sync();
-        for (int j = 0; j < kSlices && i + j <= kMaxGroup; ++j) {
-          const int gsum = i + j;
-          const uint32_t acc = gsum == 0 ? 0u : gsum == 1 ? 96u : 192u;
-          const uint32_t dacc = tm + acc;
-          const uint32_t dT = tm + 288u + acc / 2;
-          const bool first = i == 0 && j <= 2;   // first pair of each accumulator's group
-          for (int ks = 0; ks < kK / 16; ++ks)
-            tc::mma_bf16(dacc, tc::smem_desc(ah + 256 * ks, tc::kLBO, 2048),
-                         tc::smem_desc(xs + j * kSliceBytes + 256 * ks, tc::kLBO, 2048), idm, !(first && ks == 0));
-          if (np > 0) {
-            const uint32_t sbo = 16 * KEp;
+        const uint32_t a = ring + (uint32_t)slot * kSliceBytes;
+        if (isE) {
+          const uint64_t dEc = tc::smem_desc(a, tc::kLBO, 16u * (uint32_t)KEp);   // E_c slice i (128 x KEp)
+          const uint64_t dEt = tc::smem_desc(a + eb, tc::kLBO, 2048);            // E_c^T slice i (KEp x 128)
+          for (int j = 0; j < kSlices && i + j <= kMaxGroup; ++j) {
+            const int gsum = i + j;
+            const uint32_t acc = gsum == 0 ? 0u : gsum == 1 ? 96u : 192u;
+            const uint32_t first = (i == 0 && j <= 2) ? 1u : 0u;   // first pair of each accumulator's group
+            // E_c x^E: A = E_c slice i, B = x^E slice j (96 x KEp)
             for (int ks = 0; ks < KEp / 16; ++ks)
-              tc::mma_bf16(dacc, tc::smem_desc(aea + 256 * ks, tc::kLBO, sbo),
-                           tc::smem_desc(xes + j * kXEslice + 256 * ks, tc::kLBO, sbo), idm, true);
-            const uint32_t idt = tc::idesc_bf16(128, KEp);
+              tc::mma_bf16_lane0(tm + acc, dEc + 16u * ks, dXE0 + j * dXEs + 16u * ks, idH, (first && ks == 0) ? 0u : 1u);
+            // E_c^T x^C: A = x^C slice j (rows n; rows past 96 read the next region and land in
+            // tensor-memory lanes that are never read), B = E_c^T slice i
             for (int ks = 0; ks < kK / 16; ++ks)
-              tc::mma_bf16(dT, tc::smem_desc(xs + j * kSliceBytes + 256 * ks, tc::kLBO, 2048),
-                           tc::smem_desc(aet + 256 * ks, tc::kLBO, 2048), idt, !(first && ks == 0));
+              tc::mma_bf16_lane0(tm + 288u + acc / 2, dX0 + j * dXs + 16u * ks, dEt + 16u * ks, idT,
+                                 (first && ks == 0) ? 0u : 1u);
+          }
+        } else {
+          const uint64_t dH = tc::smem_desc(a, tc::kLBO, 2048);   // H_c slice i (128 x 128)
+          for (int j = 0; j < kSlices && i + j <= kMaxGroup; ++j) {
+            const int gsum = i + j;
+            const uint32_t acc = gsum == 0 ? 0u : gsum == 1 ? 96u : 192u;
+            const uint32_t first = (i == 0 && j <= 2) ? 1u : 0u;
+            for (int ks = 0; ks < kK / 16; ++ks)
+              tc::mma_bf16_lane0(tm + acc, dH + 16u * ks, dX0 + j * dXs + 16u * ks, idH, (first && ks == 0) ? 0u : 1u);
           }
         }
-        tc::mma_commit(mbar);
+        tc::mma_commit_lane0(&bar[kBEmpty0 + slot]);
+        if (isE && st == kSlices - 1) tc::mma_commit_lane0(&bar[kBAccE]);
+        ++consumed;
+        ok = issue_copy();
       }
-      const bool ok = tc::mbar_wait(mbar, phase, kWaitLimit);
-      phase ^= 1u;
-      if (!ok) {
-        *abort_flag = 1;
-        atomicExch(err, 1);
-      }
-      tc::fence_after_sync();
-      if (i + 1 < kSlices) {
-        load_set(i + 1);
-        tc::cp_async_wait_all();
-        tc::fence_proxy_async();
-      }
-      tc::fence_before_sync();
-      __syncthreads();
-      if (*abort_flag) {
-        aborted = true;
-        break;
-      }
+      if (ok) tc::mma_commit_lane0(&bar[kBAccH]);
     }
-    if (aborted) break;
-    tc::fence_after_sync();
-    // epilogue: warp w reads lanes 32 (w % 4) ..; the four warps of a lane group take
-    // 8-column chunks in turn
-    const int lg = warp & 3, qw = warp >> 2;
-    const int r = 32 * lg + lane;
+    if (!ok && lane == 0) atomicExch(err, 1);
+    // nothing may be in flight when the CTA leaves: every copy issued (bounded waits on the ones not
+    // consumed) and every MMA (one more commit, on a barrier of its own)
+    for (long long s2 = consumed; s2 < issued; ++s2) {
+      const int slot = (int)(s2 % kNSlot);
+      wait(&bar[kBFull0 + slot], (fparb >> slot) & 1u);
+      fparb ^= 1u << slot;
+    }
+    tc::mma_commit_lane0(&bar[kBFin]);
+    wait(&bar[kBFin], 0);
+  } else {
+    // ------------------------------------------------------------ work warps
+    uint32_t apar = 0, hpar = 0;
+    const int lg = warp & 3, qw = warp >> 2;     // tensor-memory lane quarter, column share (0..kWPQ-1)
+    const int r = 32 * lg + lane;                // accumulator row (cell node) of this thread
     const uint32_t lane_addr = (uint32_t)(32 * lg) << 16;
-    const long long gr = r < NN ? gS[r] : 0;
-    const int re = rexp[r];
-    for (int ch = qw; ch * 8 < nm; ch += 4) {
-      const int col = 8 * ch;
-      float a0[8], a1[8], a2[8];
-      tc::tmem_ld8(tm + lane_addr + col, a0);
-      tc::tmem_ld8(tm + lane_addr + 96 + col, a1);
-      tc::tmem_ld8(tm + lane_addr + 192 + col, a2);
-      if (r < NN && re != kZero) {
+    // warp 0 polls an mbarrier (bounded), the other warps wait at the work barrier; a wait that
+    // gave up is recorded before the barrier and read by everyone after it
+    auto wait_all = [&](uint64_t* b, uint32_t par) {
+      if (warp == 0) {
+        const bool okw = __all_sync(0xffffffffu, tc::mbar_wait(b, par, kWaitLimit));
+        if (!okw && lane == 0) {
+          *wabort = 1;
+          atomicExch(err, 1);
+        }
+      }
+      tc::named_sync(1, kWork);
+      tc::fence_after_sync();
+      return *wabort == 0;
+    };
+    // metadata of cell w into buffer b (every work thread takes part; no barrier inside)
+    auto load_meta = [&](long long w, int b) {
+      const int c = (int)(w % mesh.nc), m = (int)(w / mesh.nc);
+      int p0 = 0, np = 0;
+      if (pair_start) {
+        p0 = pair_start[c];
+        np = pair_start[c + 1] - p0;
+      }
+      int cx, cy, cz;
+      cell_ijk(mesh, c, cx, cy, cz);
+      for (int l = tid; l < 128; l += kWork) {
+        if (l < NN)
+          gS2[b * 128 + l] = node_index(mesh, cx, cy, cz, l % P1, (l / P1) % P1, l / (P1 * P1)) * ld2 + (long long)m * cols;
+        rexpH2[b * 128 + l] = tcRexpH[((long long)m * mesh.nc + c) * 128 + l];
+        if (np > 0) rexpE2[b * 128 + l] = tcRexpE[((long long)m * mesh.nc + c) * 128 + l];
+      }
+      for (int f = tid; f < np; f += kWork) {
+        fns2[b * kMaxKE + f] = pair_fn[p0 + f];
+        hexp2[b * kMaxKE + f] = tcHexp[(long long)m * n_pairs + p0 + f];
+      }
+    };
+    // gather of x_bar^C (D is folded into the operator): item = (chunk of 8 nodes, column n)
+    const int nitem = (kK / 8) * cols;
+    double v[kNK][8];
+    int buf = 0;
+    if ((long long)blockIdx.x < nwork) {
+      load_meta(blockIdx.x, 0);
+      tc::named_sync(1, kWork);
+    }
+    for (long long w = blockIdx.x; w < nwork; w += gridDim.x) {
+      const int c = (int)(w % mesh.nc), m = (int)(w / mesh.nc);
+      const int col0 = m * cols;
+      const int np = pair_start ? pair_start[c + 1] - pair_start[c] : 0;
+      const int KEp = (np + 15) & ~15;
+      const long long* gS = gS2 + buf * 128;
+      const int* rexpH = rexpH2 + buf * 128;
+      const int* rexpE = rexpE2 + buf * 128;
+      const int* hexp = hexp2 + buf * kMaxKE;
+      const int* fns = fns2 + buf * kMaxKE;
+      gather_rows<NN>(X, gS, tid, cols, nitem, v);   // rows prefetched into L2 one cell ahead
+      for (int n = tid; n < kMaxN; n += kWork) {
+        cmaxC[n] = 0;
+        cmaxE[n] = 0;
+      }
+      tc::named_sync(1, kWork);
+      // x^C as float32 pairs (ph, pl); column maxima of |ph|
+      float ph[kNK][8], pl[kNK][8];
+#pragma unroll
+      for (int k = 0; k < kNK; ++k) {
+        const int it = tid + k * kWork;
+        const int n = it - (it / cols) * cols;
+        float mx = 0.0f;
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
-          const int n = col + t;
-          if (n >= cols) break;
-          const int fe = fexp[n];
-          if (fe == kZero) continue;
-          // acc0 and acc1 are exact on the 2^-46 grid, acc2 to its last bit above it
-          const long long I = tc::fixed_of_float(a0[t], 46) + tc::fixed_of_float(a1[t], 46) +
-                              tc::fixed_of_float(a2[t], 46);
-          if (I != 0) atomicAdd(&Y[gr * ld2 + col0 + n], tc::double_of_fixed(I, re + fe - 46));
+          const df32 x = split_f64(v[k][t]);
+          ph[k][t] = x.h;
+          pl[k][t] = x.l;
+          mx = fmaxf(mx, fabsf(x.h));
+        }
+        if (it < nitem && mx > 0.0f) atomicMax(&cmaxC[n], __float_as_int(mx));
+      }
+      // x^E column maxima (values reloaded for the split below)
+      const int nitemE = (KEp / 8) * cols;
+      for (int it = tid; it < nitemE; it += kWork) {
+        const int ch = it / cols, n = it - ch * cols;
+        float mx = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int f = ch * 8 + t;
+          if (f < np) mx = fmaxf(mx, fabsf(split_f64(xE[(long long)fns[f] * ld2 + col0 + n]).h));
+        }
+        if (mx > 0.0f) atomicMax(&cmaxE[n], __float_as_int(mx));
+      }
+      tc::named_sync(1, kWork);
+      for (int n = tid; n < kMaxN; n += kWork) {
+        fC[n] = exp_of_maxbits(cmaxC[n]);
+        fE[n] = exp_of_maxbits(cmaxE[n]);
+      }
+      // slices of x^C (rows n, K = node) and of x^E (rows n, K = function)
+#pragma unroll
+      for (int k = 0; k < kNK; ++k) {
+        const int it = tid + k * kWork;
+        if (it < nitem) {
+          const int ch = it / cols, n = it - ch * cols;
+          const int fe = exp_of_maxbits(cmaxC[n]);
+          const float sc = fe == kZero ? 0.0f : tc::exp2_neg(fe);
+          store_digits8(ph[k], pl[k], sc, sm + kXs + tc::kmajor_offset(n, ch * 8, 2048), kXslice);
         }
       }
-    }
-    if (np > 0) {
-      const int n = r;
-      const int fe = n < cols ? fexp[n] : kZero;
-      for (int ch = qw; ch * 8 < KEp; ch += 4) {
-        float t0[8], t1[8], t2[8];
-        tc::tmem_ld8(tm + lane_addr + 288 + 8 * ch, t0);
-        tc::tmem_ld8(tm + lane_addr + 336 + 8 * ch, t1);
-        tc::tmem_ld8(tm + lane_addr + 384 + 8 * ch, t2);
-        if (fe != kZero) {
+      for (int it = tid; it < nitemE; it += kWork) {
+        const int ch = it / cols, n = it - ch * cols;
+        const int fe = exp_of_maxbits(cmaxE[n]);
+        const float sc = fe == kZero ? 0.0f : tc::exp2_neg(fe);
+        float a[8], b[8];
 #pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const int f = 8 * ch + t;
-            if (f >= np) break;
-            if (hexp[f] == kZero) continue;
-            const long long I = tc::fixed_of_float(t0[t], 46) + tc::fixed_of_float(t1[t], 46) +
-                                tc::fixed_of_float(t2[t], 46);
-            if (I != 0) atomicAdd(&yE[(long long)fns[f] * ld2 + col0 + n], tc::double_of_fixed(I, fe + hexp[f] - 46));
+        for (int t = 0; t < 8; ++t) {
+          const int f = ch * 8 + t;
+          const df32 x = f < np ? split_f64(xE[(long long)fns[f] * ld2 + col0 + n]) : df32(0.0f, 0.0f);
+          a[t] = x.h;
+          b[t] = x.l;
+        }
+        store_digits8(a, b, sc, sm + kXEs + tc::kmajor_offset(n, ch * 8, 16 * KEp), kXEslice);
+      }
+      tc::fence_proxy_async();
+      tc::named_sync(1, kWork);
+      if (tid == 0) tc::mbar_arrive(&bar[kBXready]);
+      // while the tensor cores run: the metadata of this CTA's next cell, and its rows of x_bar into
+      // L2 (one bulk prefetch per node row)
+      const long long wn = w + gridDim.x;
+      if (wn < nwork) load_meta(wn, buf ^ 1);
+      if (wn < nwork && tid < NN) {
+        const long long w2 = wn;
+        const int c2 = (int)(w2 % mesh.nc), m2 = (int)(w2 / mesh.nc);
+        int ex, ey, ez;
+        cell_ijk(mesh, c2, ex, ey, ez);
+        const long long g = node_index(mesh, ex, ey, ez, tid % P1, (tid / P1) % P1, tid / (P1 * P1));
+        tc::bulk_prefetch_l2(X + g * ld2 + (long long)m2 * cols, (uint32_t)(cols * 8));
+      }
+      // units of the output (row r, column n): the larger of the units of H_c x^C and E_c x^E;
+      // each part is scaled onto them by 2^kH, 2^kE <= 1
+      const int reH = r < NN ? rexpH[r] : kZero;
+      const int reE = (r < NN && np > 0) ? rexpE[r] : kZero;
+      auto down = [](int k) { return k < -125 ? 0.0f : tc::exp2_pos(k); };
+      // ---- E pass epilogue: E_c^T x^C to y^E; then E_c x^E as a pair (s, t) in the output's
+      // units, parked in tensor-memory columns 288 + 16 ch (s) and 296 + 16 ch (t) of chunk ch
+      // (free once E_c^T x^C has been read: the H pass writes columns 0..287 only)
+      if (np > 0) {
+        const bool okE = wait_all(&bar[kBAccE], apar);
+        apar ^= 1u;
+        if (okE) {
+          // E_c^T x^C: accumulator row = column n of this member, column = function f
+          const int n = r;
+          const int fe = n < cols ? fC[n] : kZero;
+          for (int ch = qw; ch * 8 < KEp; ch += kWPQ) {
+            float t0[8], t1[8], t2[8];
+            const uint32_t ta = tm + lane_addr + 288 + 8 * ch;
+            tc::tmem_ld8x3(ta, ta + 48, ta + 96, t0, t1, t2);
+            if (fe != kZero) {
+#pragma unroll
+              for (int t = 0; t < 8; ++t) {
+                const int f = 8 * ch + t;
+                if (f >= np) break;
+                if (hexp[f] == kZero) continue;
+                float s, u;
+                tc::sum3_pair(t0[t], t1[t], t2[t], s, u);
+                if (s != 0.0f) atomicAdd(&yE[(long long)fns[f] * ld2 + col0 + n], tc::double_of_pair(s, u, fe + hexp[f]));
+              }
+            }
+          }
+        }
+        tc::fence_before_sync();
+        tc::named_sync(1, kWork);   // every warp has read E_c^T x^C before its columns are reused
+        tc::fence_after_sync();
+        if (okE) {
+#pragma unroll
+          for (int q = 0; q < kNQ; ++q) {
+            const int ch = qw + kWPQ * q;
+            if (ch * 8 < nm) {
+              float a0[8], a1[8], a2[8], sE[8], tE[8];
+              const uint32_t t0 = tm + lane_addr + 8 * ch;
+              tc::tmem_ld8x3(t0, t0 + 96, t0 + 192, a0, a1, a2);
+#pragma unroll
+              for (int t = 0; t < 8; ++t) {
+                const int n = 8 * ch + t;
+                const int eH = (reH == kZero || fC[n] == kZero) ? kZero : reH + fC[n];
+                const int eE = (reE == kZero || fE[n] == kZero) ? kZero : reE + fE[n];
+                float s, u;
+                tc::sum3_pair(a0[t], a1[t], a2[t], s, u);
+                const float sc = eE == kZero ? 0.0f : down(eE - (eH > eE ? eH : eE));
+                sE[t] = __fmul_rn(s, sc);
+                tE[t] = __fmul_rn(u, sc);
+              }
+              tc::tmem_st8x2(tm + lane_addr + 288 + 16 * ch, tm + lane_addr + 296 + 16 * ch, sE, tE);
+            }
+          }
+        }
+        tc::fence_before_sync();
+        tc::named_sync(1, kWork);
+        if (tid == 0) tc::mbar_arrive(&bar[kBDrainedE]);
+        if (*wabort) break;
+      }
+      // ---- H pass epilogue: H_c x^C (+ the E part) -> y_c (staged in shared memory)
+      const bool okH = wait_all(&bar[kBAccH], hpar);
+      hpar ^= 1u;
+      if (okH) {
+#pragma unroll
+        for (int q = 0; q < kNQ; ++q) {
+          const int ch = qw + kWPQ * q;
+          if (ch * 8 < nm) {
+            float a0[8], a1[8], a2[8], sE[8], tE[8];
+            const uint32_t t0 = tm + lane_addr + 8 * ch;
+            tc::tmem_ld8x3(t0, t0 + 96, t0 + 192, a0, a1, a2);
+            if (np > 0) tc::tmem_ld8x2(tm + lane_addr + 288 + 16 * ch, tm + lane_addr + 296 + 16 * ch, sE, tE);
+            if (r < NN) {
+#pragma unroll
+              for (int t = 0; t < 8; ++t) {
+                const int n = 8 * ch + t;
+                if (n < cols) {
+                  const int eH = (reH == kZero || fC[n] == kZero) ? kZero : reH + fC[n];
+                  double y = 0.0;
+                  float s, u;
+                  if (np == 0) {
+                    if (eH != kZero) {
+                      tc::sum3_pair(a0[t], a1[t], a2[t], s, u);
+                      y = tc::double_of_pair(s, u, eH);
+                    }
+                  } else {
+                    const int eE = (reE == kZero || fE[n] == kZero) ? kZero : reE + fE[n];
+                    const int eO = eH > eE ? eH : eE;
+                    if (eO != kZero) {
+                      const float sc = eH == kZero ? 0.0f : down(eH - eO);
+                      tc::sum5_pair(__fmul_rn(a0[t], sc), __fmul_rn(a1[t], sc), __fmul_rn(a2[t], sc), sE[t], tE[t],
+                                    s, u);
+                      y = tc::double_of_pair(s, u, eO);
+                    }
+                  }
+                  stage[r * kStageLd + n] = y;
+                }
+              }
+            }
           }
         }
       }
+      tc::fence_before_sync();
+      tc::named_sync(1, kWork);
+      if (*wabort) break;
+      // scatter: one node row per warp, consecutive columns per lane
+      for (int l = warp; l < NN; l += kWork / 32) {
+        const int a = l % P1, b = (l / P1) % P1, cc = l / (P1 * P1);
+        const bool interior = a > 0 && a < P1 - 1 && b > 0 && b < P1 - 1 && cc > 0 && cc < P1 - 1;
+        double* yrow = Y + gS[l];
+        for (int n = lane; n < cols; n += 32) {
+          const double y = stage[l * kStageLd + n];
+          if (interior)
+            yrow[n] = y;
+          else if ((__double_as_longlong(y) << 1) != 0)
+            atomicAdd(&yrow[n], y);
+        }
+      }
+      tc::named_sync(1, kWork);   // staging (the x^C slices) free for the next cell
+      buf ^= 1;
     }
-    tc::fence_before_sync();
-    __syncthreads();
   }
-  if (aborted && tid == 0) tc::mbar_wait(mbar, phase, kWaitLimit);   // MMAs still in flight
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -538,11 +791,12 @@ static cudaError_t tc_alloc(Ctx& c, int batch) {
     EFE_CUDA_TRY(cudaMemset(t.err, 0, sizeof(int)));
   }
   if (t.batch != batch) {
-    cudaFree(t.H); cudaFree(t.rexp); cudaFree(t.E); cudaFree(t.hexp);
-    t.H = nullptr; t.rexp = nullptr; t.E = nullptr; t.hexp = nullptr;
+    cudaFree(t.H); cudaFree(t.rexp); cudaFree(t.rexpE); cudaFree(t.E); cudaFree(t.hexp);
+    t.H = nullptr; t.rexp = nullptr; t.rexpE = nullptr; t.E = nullptr; t.hexp = nullptr;
     t.batch = 0;
     EFE_CUDA_TRY(cudaMalloc(&t.H, (size_t)batch * c.nc * kSlices * kSliceBytes));
     EFE_CUDA_TRY(cudaMalloc(&t.rexp, sizeof(int) * (size_t)batch * c.nc * 128));
+    EFE_CUDA_TRY(cudaMalloc(&t.rexpE, sizeof(int) * (size_t)batch * c.nc * 128));
     EFE_CUDA_TRY(cudaMalloc(&t.E, (size_t)batch * (t.e_total > 0 ? t.e_total : 1) * 2048));
     EFE_CUDA_TRY(cudaMalloc(&t.hexp, sizeof(int) * (size_t)batch * (c.n_pairs > 0 ? c.n_pairs : 1)));
     t.batch = batch;
@@ -555,12 +809,14 @@ template <int P1, int NQ1>
 static cudaError_t tc_build_impl(Ctx& c, int batch, cudaStream_t s) {
   EFE_CUDA_TRY(tc_alloc(c, batch));
   constexpr int NN = P1 * P1 * P1, S3 = NQ1 * NQ1 * NQ1, PP = P1 * P1;
-  const size_t sm = sizeof(double) * (S3 + PP * NQ1 + PP * NQ1 * NQ1 + PP * PP * NQ1 + NN * NN + 128) + sizeof(int) * (128 + 48);
+  const size_t sm = sizeof(double) * (S3 + PP * NQ1 + PP * NQ1 * NQ1 + PP * PP * NQ1 + NN * NN + 128) +
+                    sizeof(int) * (128 + 128 + 48);
   auto f = k_tc_build<P1, NQ1>;
   EFE_CUDA_TRY(set_smem_tc(f, sm));
   dim3 grid(c.nc, batch);
   f<<<grid, 256, sm, s>>>(c.tab, c.mesh, c.op.W64, c.op.kin, c.n_pairs > 0 ? c.d_pair_start : nullptr, c.op.E64,
-                          c.n_pairs, c.d_Dsc, c.tc.eoff, c.tc.e_total, c.tc.H, c.tc.rexp, c.tc.E, c.tc.hexp);
+                          c.n_pairs, c.d_Dsc, c.tc.eoff, c.tc.e_total, c.tc.H, c.tc.rexp, c.tc.rexpE, c.tc.E,
+                          c.tc.hexp);
   note_launch();
   return cudaGetLastError();
 }
@@ -585,9 +841,10 @@ static cudaError_t tc_apply_impl(Ctx& c, const double* X, double* Y, long long n
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!c.apply_gate) prof_pair(c, e0, e1);
   if (e0) EFE_CUDA_TRY(cudaEventRecord(e0, s));
-  f<<<grid, kApplyThreads, kApplySmem, s>>>(c.mesh, X, Y, ld2, cols, nm, batch, c.d_Dsc, c.tc.H, c.tc.rexp, c.tc.E, c.tc.e_total,
-                                  c.tc.eoff, c.tc.hexp, c.n_pairs > 0 ? c.d_pair_start : nullptr, c.d_pair_fn,
-                                  c.n_pairs, c.d_xE, c.d_yE, c.tc.err, c.apply_gate);
+  f<<<grid, kApplyThreads, kApplySmem, s>>>(c.mesh, X, Y, ld2, cols, nm, batch, c.d_Dsc, c.tc.H, c.tc.rexp,
+                                            c.tc.rexpE, c.tc.E, c.tc.e_total, c.tc.eoff, c.tc.hexp,
+                                            c.n_pairs > 0 ? c.d_pair_start : nullptr, c.d_pair_fn, c.n_pairs, c.d_xE,
+                                            c.d_yE, c.tc.err, c.apply_gate);
   note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   if (e1) EFE_CUDA_TRY(cudaEventRecord(e1, s));
@@ -614,7 +871,8 @@ cudaError_t launch_tc_apply(Ctx& c, const double* X, double* Y, long long n_cols
 }
 
 void tc_free(TcState& t) {
-  cudaFree(t.H); cudaFree(t.rexp); cudaFree(t.E); cudaFree(t.hexp); cudaFree(t.eoff); cudaFree(t.err);
+  cudaFree(t.H); cudaFree(t.rexp); cudaFree(t.rexpE); cudaFree(t.E); cudaFree(t.hexp); cudaFree(t.eoff);
+  cudaFree(t.err);
   t = TcState{};
 }
 

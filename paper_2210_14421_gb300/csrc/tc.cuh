@@ -70,6 +70,28 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate)
       : "memory");
 }
+// the same, executed by a converged warp and issued by its lane 0 (the predicate is formed inside the
+// instruction block, so the operands stay warp-uniform; lane 0 also commits, see mma_commit_lane0)
+__device__ __forceinline__ void mma_bf16_lane0(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred e, p;\n\t.reg .u32 l;\n\t"
+      "mov.u32 l, %%laneid;\n\t"
+      "setp.eq.u32 e, l, 0;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit_lane0(uint64_t* mbar) {
+  asm volatile(
+      "{\n\t.reg .pred e;\n\t.reg .u32 l;\n\t"
+      "mov.u32 l, %%laneid;\n\t"
+      "setp.eq.u32 e, l, 0;\n\t"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}\n" ::"r"(
+          smem_u32(mbar))
+      : "memory");
+}
 // arrive on the mbarrier once every MMA issued so far by this thread has completed
 __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
@@ -108,6 +130,112 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// three 8-column loads, one wait
+__device__ __forceinline__ void tmem_ld8x3(uint32_t t0, uint32_t t1, uint32_t t2, float* a, float* b, float* c) {
+  uint32_t r[24];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(t0)
+               : "memory");
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(t1)
+               : "memory");
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+               : "r"(t2)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    a[i] = __uint_as_float(r[i]);
+    b[i] = __uint_as_float(r[8 + i]);
+    c[i] = __uint_as_float(r[16 + i]);
+  }
+}
+
+// two 8-column stores (lanes of this warp's quarter), then the wait for them
+__device__ __forceinline__ void tmem_st8x2(uint32_t t0, uint32_t t1, const float* a, const float* b) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(t0),
+               "r"(__float_as_uint(a[0])), "r"(__float_as_uint(a[1])), "r"(__float_as_uint(a[2])),
+               "r"(__float_as_uint(a[3])), "r"(__float_as_uint(a[4])), "r"(__float_as_uint(a[5])),
+               "r"(__float_as_uint(a[6])), "r"(__float_as_uint(a[7]))
+               : "memory");
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(t1),
+               "r"(__float_as_uint(b[0])), "r"(__float_as_uint(b[1])), "r"(__float_as_uint(b[2])),
+               "r"(__float_as_uint(b[3])), "r"(__float_as_uint(b[4])), "r"(__float_as_uint(b[5])),
+               "r"(__float_as_uint(b[6])), "r"(__float_as_uint(b[7]))
+               : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// two 8-column loads and one wait
+__device__ __forceinline__ void tmem_ld8x2(uint32_t t0, uint32_t t1, float* a, float* b) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(t0)
+               : "memory");
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(t1)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    a[i] = __uint_as_float(r[i]);
+    b[i] = __uint_as_float(r[8 + i]);
+  }
+}
+
+// --- mbarrier arrivals, bulk (non-tensor) copies global -> shared, L2 prefetch ---
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+// arrive and add `bytes` to the transaction count the current phase waits for
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+// `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to this CTA's shared memory,
+// completing as transactions on `mbar`
+__device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(sdst)),
+               "l"(gsrc), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_prefetch_l2(const void* g, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"(bytes) : "memory");
+}
+// barrier `id` (1..15) among n threads of whole warps (the warps that execute it)
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// --- splitting on the FP32 pipe ---
+// alpha = a + b (|a| < 1, |b| <= ulp(a)) cut into four values r_k on the grids 2^-7, 2^-15,
+// 2^-23 and 2^-31 by round-to-nearest digit extraction: each step adds and removes
+// 1.5 * 2^(23 - q), which rounds to the grid 2^-q, and the remainder is exact; |r_0| <= 1,
+// |r_k| <= 2^(-8k) for k >= 1, so every r_k has at most 8 significant bits and its bf16
+// pattern is the upper half of its binary32 pattern.  |alpha - sum r_k| <= 2^-32 + 2^-33.
+__device__ __forceinline__ void digits4(float a, float b, uint32_t bits[4]) {
+  const float r0 = __fsub_rn(__fadd_rn(a, 98304.0f), 98304.0f);
+  float t = __fadd_rn(__fsub_rn(a, r0), b);
+  const float r1 = __fsub_rn(__fadd_rn(t, 384.0f), 384.0f);
+  t = __fsub_rn(t, r1);
+  const float r2 = __fsub_rn(__fadd_rn(t, 1.5f), 1.5f);
+  t = __fsub_rn(t, r2);
+  const float r3 = __fsub_rn(__fadd_rn(t, 0.005859375f), 0.005859375f);
+  bits[0] = __float_as_uint(r0);
+  bits[1] = __float_as_uint(r1);
+  bits[2] = __float_as_uint(r2);
+  bits[3] = __float_as_uint(r3);
+}
+// two bf16 patterns (the upper halves of two binary32 patterns) in one 32-bit word, lo first
+__device__ __forceinline__ uint32_t pack_hi16(uint32_t lo, uint32_t hi) { return __byte_perm(lo, hi, 0x7632); }
+// 2^-e as a binary32 for -126 <= e <= 126
+__device__ __forceinline__ float exp2_neg(int e) { return __uint_as_float((uint32_t)(127 - e) << 23); }
 
 // --- Ampere-style asynchronous 16-byte copies global -> shared ---
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
@@ -209,6 +337,67 @@ __device__ __forceinline__ double double_of_fixed(long long I, int e) {
   u = p > 52 ? (u >> (p - 52)) : (u << (52 - p));
   return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | (u & 0xFFFFFFFFFFFFFull)));
 }
+
+// I1 2^e1 + I2 2^e2 as a double: the addend with the smaller exponent is shifted onto the other's
+// grid (an error below one unit of that grid); |I1|, |I2| < 2^55
+__device__ __forceinline__ double double_of_fixed2(long long I1, int e1, long long I2, int e2) {
+  if (I2 == 0) return double_of_fixed(I1, e1);
+  if (I1 == 0) return double_of_fixed(I2, e2);
+  if (e1 < e2) {
+    const long long ti = I1;
+    I1 = I2;
+    I2 = ti;
+    const int te = e1;
+    e1 = e2;
+    e2 = te;
+  }
+  const int d = e1 - e2;
+  return double_of_fixed(I1 + (d < 63 ? (I2 >> d) : (I2 < 0 ? -1LL : 0LL)), e1);
+}
+
+// --- float-pair epilogue arithmetic ---
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// a0 + a1 + a2 (+ c0 + c1) as a normalised pair (s, t), |t| <= ulp(s) / 2; the rounding of the
+// small terms' sum is far below the last bit of s
+__device__ __forceinline__ void sum3_pair(float a0, float a1, float a2, float& s, float& t) {
+  float s1, e1, s2, e2;
+  two_sum_f(a0, a1, s1, e1);
+  two_sum_f(s1, a2, s2, e2);
+  two_sum_f(s2, __fadd_rn(e1, e2), s, t);
+}
+__device__ __forceinline__ void sum5_pair(float a0, float a1, float a2, float c0, float c1, float& s, float& t) {
+  float s1, e1, s2, e2, s3, e3;
+  two_sum_f(a0, c0, s1, e1);
+  two_sum_f(s1, a1, s2, e2);
+  two_sum_f(s2, a2, s3, e3);
+  two_sum_f(s3, __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, c1)), s, t);
+}
+// (s + t) 2^E as a double from integer operations only, for a normalised pair (|t| <= ulp(s) / 2):
+// the pattern of s 2^E, plus t counted in units of the double's last place (for t against the
+// sign of s across a power of two the result is within a few units of the last place)
+__device__ __forceinline__ double double_of_pair(float s, float t, int E) {
+  const uint32_t us = __float_as_uint(s);
+  const int bs = (int)((us >> 23) & 0xFFu);
+  if (bs == 0) return 0.0;
+  const int ed = bs + 896 + E;
+  if (ed <= 0 || ed >= 2047) return 0.0;
+  unsigned long long mag = ((unsigned long long)ed << 52) | ((unsigned long long)(us & 0x7FFFFFu) << 29);
+  const uint32_t ut = __float_as_uint(t);
+  const int bt = (int)((ut >> 23) & 0xFFu);
+  if (bt != 0) {
+    const unsigned long long mt = (ut & 0x7FFFFFu) | 0x800000u;
+    const int sh = bt - bs + 29;   // t / ulp = mt 2^(bt - bs + 29), bt <= bs - 24
+    const unsigned long long q = sh >= 0 ? (mt << sh) : (sh > -25 ? (mt >> -sh) : 0ull);
+    mag = ((ut ^ us) >> 31) ? mag - q : mag + q;
+  }
+  return __longlong_as_double((long long)((((unsigned long long)us >> 31) << 63) | mag));
+}
+// 2^k as a binary32 for -126 <= k <= 127
+__device__ __forceinline__ float exp2_pos(int k) { return __uint_as_float((uint32_t)(127 + k) << 23); }
 
 // exponent e with |x| < 2^e for the largest |x| whose biased exponent is be (be > 0)
 __device__ __forceinline__ int scale_exp(int be) { return be - 1022; }
