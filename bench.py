@@ -10,17 +10,18 @@ kick 1e-3 along x.  Inputs are synthetic and seeded (efe_workloads.na8); the
 orbital block (1.35 GB) is larger than L2, so no flush is needed between
 steps.  One JSON line is printed by rank 0.
 
-The headline precision is "pair": the sum-factorised cell contraction and the
-enrichment coupling on the FP32 pipe in pairs of binary32 (error-free products
-and sums, ~2^-44), the rest in FP64; its dipole error against the FP64 path is
-measured in the same run (bound 1e-5 a.u.), with both runs at one fixed Krylov
-dimension and with each at its own adaptive one.  Beside it: "tc" (dense cell
-matrices and enrichment coupling on the tensor cores, every operand split into
-four bf16 slices of a 31-bit fixed-point value, exact slice products, float32
-accumulation) and "mixed" (plain binary32), each with its own time per step and
-dipole error.
+The headline precision is "tc": the dense cell contraction and the enrichment
+coupling on the tensor cores, every operand split into four bf16 slices of a
+31-bit fixed-point value with its own power-of-two scale, exact slice
+products, float32 tensor-memory accumulation; the Lanczos recurrence,
+tridiagonal exponential, Hartree solve, LDA, norms and dipole in FP64.  Its
+dipole error against the FP64 path is measured in the same run (bound 1e-5
+a.u.), with both runs at one fixed Krylov dimension and with each at its own
+adaptive one.  Beside it: "pair" (the sum-factorised contraction in float32
+pairs on the FP32 pipe) and FP64, each with its own time per step and dipole
+error.
 
-  python bench.py [--gpus N --steps K --warmup W] [--precision pair|tc|mixed|fp64]
+  python bench.py [--gpus N --steps K --warmup W] [--precision tc|pair|mixed|fp64]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
 """
 from __future__ import annotations
@@ -49,7 +50,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="efe", choices=["efe", "reference"])
-    ap.add_argument("--precision", default="pair", choices=["pair", "tc", "mixed", "fp64"])
+    ap.add_argument("--precision", default="tc", choices=["tc", "pair", "mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64 steps reported beside the main number")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--graph-steps", type=int, default=3, help="extra steps timed in CUDA-graph mode")
@@ -63,6 +64,10 @@ def parse_args(argv=None):
     ap.add_argument("--next-rows", action="store_true",
                     help="child mode: time the electrostatic enrichment and locally refined mesh paths, print JSON")
     ap.add_argument("--no-next-rows", action="store_true", help="skip the child run of --next-rows")
+    ap.add_argument("--apply-only", action="store_true",
+                    help="time --steps cell applies (Y = Hbar X, random X, the nuclear potential) of the workload "
+                         "at --cells and --precision after --warmup untimed ones, one JSON line; the target of the "
+                         "kernel profiles")
     ap.add_argument("--k-max", type=int, default=64,
                     help="Lanczos cap; the Na8-like spectrum (-257..+2500 Ha) at dt = 0.05 needs k = 57 (FP64, "
                          "pair) to 58 (float32) for eps_k <= 1e-7. Below that the exponential is unconverged and "
@@ -138,6 +143,12 @@ def job_throughput(world, steps, ms):
 
 
 # ---------------------------------------------------------------------------- helpers
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each cell kernel on the
+# 15^3-cell crop of the Na8-like mesh, from ncu (profiles/), and that launch's algorithmic bytes:
+# (measured, algorithmic).  Entries are removed when the kernel changes.
+TRAFFIC = {"k_tc_apply<5>": (1155091472.0, 803952832.0)}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -156,77 +167,153 @@ def workload(cells, rank):
 
 
 def apply_model(ctx, wl, precision):
-    """Algorithmic work of one cell-apply launch (the dominant kernel).
-    bytes: read X and write Y once (complex128), the quadrature weights, the
-    coupling blocks and D; flops: the sum-factorised cell operator
-    (7 (p+1)^4 FMA kinetic + 2 (nq (p+1)^3 + nq^2 (p+1)^2 + nq^3 (p+1)) + nq^3
-    potential per real column) plus 2 (p+1)^3 FMA per real column per
-    cell-function pair of the enrichment coupling; dense-equivalent flops
-    N_c 2 N_n^2 cols for the H.X rate."""
+    """Algorithmic work of one cell-apply launch (the dominant kernel), the same for every
+    precision: flops = N_c 2 N_n^2 cols (the dense cell contraction H_c x^C) + 4 N_n n_pairs cols
+    (the coupling E_c x^E and E_c^T x^C), cols = 2 n_orb batch real columns; bytes = X read and Y
+    written once (complex128) plus the operator data the kernel streams (tc: the four bf16
+    slices of every 128 x 128 cell matrix and of each cell's E_c and E_c^T blocks; the
+    sum-factorised kernels: w|J|v at the quadrature points and the coupling blocks).  Also the
+    work the kernel actually issues: the 13 bf16 slice-pair products (tc) or the FP32-pipe
+    pair-arithmetic terms (pair)."""
     p1, nq1 = wl.degree + 1, wl.n_quad
+    nn = p1 ** 3
     R = 2 * wl.n_orb * wl.batch
+    flops = ctx.n_cells * 2.0 * nn * nn * R + 4.0 * nn * ctx.n_pairs * R
     if precision == "tc":
-        # dense form on the tensor cores: X read and Y written once, the four bf16 slices of
-        # every 128 x 128 cell matrix and of the cell's E_c and E_c^T blocks (125 values per
-        # cell-function pair each); flops: the 13 slice-pair products of the dense cell
-        # product H_c x^C, of E_c x^E and of E_c^T x^C (bf16 products, f32 accumulation)
-        nn = p1 ** 3
         bytes_ = 2 * ctx.n_dof * R * 8 + ctx.n_cells * 4 * 128 * 128 * 2 + ctx.n_pairs * 2 * 4 * nn * 2
-        flops = 13 * 2.0 * R * (ctx.n_cells * nn * nn + 2 * nn * ctx.n_pairs)
-        dense = ctx.n_cells * 2.0 * nn ** 2 * R
-        return bytes_, flops, dense
+        issued = 13 * 2.0 * R * (ctx.n_cells * 128 * 128 + 2 * 128 * ctx.n_pairs)
+        return bytes_, flops, issued
     ts = 4 if precision == "mixed" else 8   # bytes per stored operator value (float, float pair, double)
     bytes_ = 2 * ctx.n_dof * R * 8 + ctx.n_cells * nq1 ** 3 * ts + ctx.n_pairs * p1 ** 3 * ts + ctx.n_nodes * 8
     fma_cell = 7 * p1 ** 4 + 2 * (nq1 * p1 ** 3 + nq1 ** 2 * p1 ** 2 + nq1 ** 3 * p1) + nq1 ** 3
-    flops = 2.0 * (ctx.n_cells * fma_cell * R + 2 * p1 ** 3 * ctx.n_pairs * R)
-    dense = ctx.n_cells * 2.0 * (p1 ** 3) ** 2 * R
-    return bytes_, flops, dense
+    issued = 2.0 * (ctx.n_cells * fma_cell * R + 2 * p1 ** 3 * ctx.n_pairs * R)
+    return bytes_, flops, issued
 
 
-def cpu_baseline(wl_full, k_hint, budget_s=25.0):
-    """The FP64 oracle as it stands, timed on the host cores on a bounded sample:
-    one predictor-corrector step on a crop of the same mesh (n^3 cells around
-    the first atom, all orbitals, the enrichment functions of the atoms inside
-    the crop, the same Krylov tolerance), scaled to the full mesh by the cell
-    count."""
-    import numpy as np
-    from oracle import operators, tdks
+def pipe_peaks_measured():
+    """Measured peaks of the pipes the cell kernels run on, on this device: the float32 and
+    float64 FMA pipes (the library's own probe kernels, efe_pipe_peaks) and the TF32 tensor
+    rate of a cuBLAS GEMM (8192^3 float32 with TF32 math, best of 5, CUDA events)."""
+    import torch
+    from paper_2210_14421_gb300 import pipe_peaks
+    fp32, fp64 = pipe_peaks()
+    out = {"fp32_fma_tflops": round(fp32, 2), "fp64_fma_tflops": round(fp64, 3)}
+    try:
+        old = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True
+        n = 8192
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        best = None
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        torch.backends.cuda.matmul.allow_tf32 = old
+        out["tf32_gemm_tflops"] = round(2.0 * n ** 3 / (best * 1e-3) / 1e12, 1)
+        del a, b
+        torch.cuda.empty_cache()
+    except Exception as e:   # keep the FMA probes
+        out["tf32_gemm_error"] = str(e)[:120]
+    out["how"] = ("efe_pipe_peaks: 8 independent FMA chains per thread, 8 x 256 threads per SM, one timed "
+                  "launch after a warm-up; TF32: torch.matmul 8192^3 float32, allow_tf32, best of 5")
+    return out
+
+
+def blas_info():
+    """The oracle's BLAS (numpy's build configuration) and its thread count."""
+    name = "unknown"
+    try:
+        import numpy as np
+        cfg = np.__config__.CONFIG.get("Build Dependencies", {}).get("blas", {})
+        name = "%s %s" % (cfg.get("name", "?"), cfg.get("version", ""))
+    except Exception:
+        pass
+    threads = None
     try:
         from threadpoolctl import threadpool_info
-        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+        threads = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
     except Exception:
-        cores = os.cpu_count() or 1
-    n = 4
-    while True:
-        sub = []
-        centre = np.asarray(wl_full.R[0])
-        for a, b in enumerate((wl_full.xb, wl_full.yb, wl_full.zb)):
-            mid = int(np.searchsorted(b, centre[a])) - 1
-            lo = min(max(0, mid - n // 2), len(b) - 1 - n)
-            sub.append(b[lo:lo + n + 1].copy())
-        lo_c = np.array([b[0] for b in sub])
-        hi_c = np.array([b[-1] for b in sub])
-        # the enrichment functions of the atoms inside the crop
-        keep = [f for f in wl_full.enrich
-                if np.all(np.asarray(wl_full.R[f.atom]) > lo_c) and np.all(np.asarray(wl_full.R[f.atom]) < hi_c)]
-        idx = [wl_full.enrich.index(f) for f in keep]
-        wl = wl_full.with_(xb=sub[0], yb=sub[1], zb=sub[2], enrich=keep, enr_coefs=wl_full.enr_coefs[:, idx])
-        S = operators.System(wl)
-        psi = S.initial_orbitals()
-        psi = tdks.kick(S, psi, wl.fields, wl.n_orb, tol=wl.krylov_tol, k_max=wl.k_max)
-        st = tdks.make_state(S, psi, wl.occ, 1)
-        t0 = time.perf_counter()
-        tdks.magnus_step(S, psi, st, 0.0, wl.dt, wl.fields, wl.occ, wl.krylov_tol, wl.k_max)
-        dt = time.perf_counter() - t0
-        if dt > budget_s / 4 or n >= 8:
+        for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+            if os.environ.get(var, "").isdigit():
+                threads = int(os.environ[var])
+                break
+    return name.strip(), int(threads or os.cpu_count() or 1)
+
+
+def oracle_crop_step(wl_full, n):
+    """Seconds of one oracle predictor-corrector step (FP64, host cores) on an n^3-cell crop of
+    the workload's mesh around its first atom (all orbitals, the enrichment functions of the
+    atoms inside the crop, the same Krylov tolerance), and the crop's cell count."""
+    import numpy as np
+    from oracle import operators, tdks
+    sub = []
+    centre = np.asarray(wl_full.R[0])
+    for a, b in enumerate((wl_full.xb, wl_full.yb, wl_full.zb)):
+        mid = int(np.searchsorted(b, centre[a])) - 1
+        lo = min(max(0, mid - n // 2), len(b) - 1 - n)
+        sub.append(b[lo:lo + n + 1].copy())
+    lo_c = np.array([b[0] for b in sub])
+    hi_c = np.array([b[-1] for b in sub])
+    keep = [f for f in wl_full.enrich
+            if np.all(np.asarray(wl_full.R[f.atom]) > lo_c) and np.all(np.asarray(wl_full.R[f.atom]) < hi_c)]
+    idx = [wl_full.enrich.index(f) for f in keep]
+    wl = wl_full.with_(xb=sub[0], yb=sub[1], zb=sub[2], enrich=keep, enr_coefs=wl_full.enr_coefs[:, idx])
+    S = operators.System(wl)
+    psi = S.initial_orbitals()
+    psi = tdks.kick(S, psi, wl.fields, wl.n_orb, tol=wl.krylov_tol, k_max=wl.k_max)
+    st = tdks.make_state(S, psi, wl.occ, 1)
+    t0 = time.perf_counter()
+    tdks.magnus_step(S, psi, st, 0.0, wl.dt, wl.fields, wl.occ, wl.krylov_tol, wl.k_max)
+    return time.perf_counter() - t0, S.mesh.n_cells, len(keep)
+
+
+def fit_exponent(cells, secs):
+    """Least-squares fit of log t = a + b log N_cells; returns (b, rms residual of log t)."""
+    import numpy as np
+    x, y = np.log(np.asarray(cells, float)), np.log(np.asarray(secs, float))
+    A = np.stack([np.ones_like(x), x], axis=1)
+    coef, *_ = np.linalg.lstsq(A, y, rcond=None)
+    res = y - A @ coef
+    return float(coef[1]), float(np.sqrt(np.mean(res ** 2)))
+
+
+def cpu_baseline(wl_full, crops=(4, 6, 8), budget_s=50.0):
+    """The FP64 oracle as it stands, timed on the host cores on a bounded sample of the
+    workload: one predictor-corrector step on n^3-cell crops of the same mesh (n = 4, 6, 8 while
+    the budget lasts), a fit t = a N_cells^b over the crops, and the full mesh's time per step
+    extrapolated from the largest crop with that exponent (the oracle's cost is not linear in
+    the cell count: its sparse Hartree factorisation and Krylov dimensions grow with the crop)."""
+    blas, threads = blas_info()
+    cells, secs, nfun = [], [], []
+    spent = 0.0
+    for k, n in enumerate(crops):
+        # the next crop's time, estimated with an exponent of 1.5 in the cell count
+        if cells and spent + secs[-1] * (n / crops[k - 1]) ** 4.5 > budget_s:
             break
-        n += 2
-    scale = wl_full.n_cells / S.mesh.n_cells
-    sec_per_step = dt * scale
-    return {"value": 1.0 / sec_per_step, "unit": "steps/s", "cores": int(cores), "kind": "oracle",
-            "sample": "one predictor-corrector step on a %dx%dx%d-cell crop of the same mesh (%d of %d cells, all "
-                      "%d orbitals, the %d enrichment functions of the atoms inside it), %.2f s, scaled by "
-                      "the cell count" % (n, n, n, S.mesh.n_cells, wl_full.n_cells, wl.n_orb, len(wl.enrich), dt)}
+        t, nc, nf = oracle_crop_step(wl_full, n)
+        cells.append(nc)
+        secs.append(t)
+        nfun.append(nf)
+        spent += t
+    if len(cells) >= 2:
+        b, resid = fit_exponent(cells, secs)
+    else:
+        b, resid = 1.0, None
+    sec_full = secs[-1] * (wl_full.n_cells / cells[-1]) ** b
+    return {"value": 1.0 / sec_full, "unit": "steps/s", "cores": threads, "kind": "oracle", "blas": blas,
+            "sample": "one predictor-corrector step of the FP64 oracle on each of the %s-cell crops of the same mesh "
+                      "(all %d orbitals, the enrichment functions inside each crop: %s), %s s; fit t ~ N_cells^%.2f "
+                      "(rms log residual %s), extrapolated from the largest crop to the %d cells"
+                      % ("/".join("%d" % c for c in cells), wl_full.n_orb, "/".join(map(str, nfun)),
+                         "/".join("%.2f" % t for t in secs), b, "%.3f" % resid if resid is not None else "n/a",
+                         wl_full.n_cells),
+            "fit": {"cells": cells, "seconds": [round(t, 3) for t in secs], "exponent": round(b, 3),
+                    "rms_log_residual": resid}}
 
 
 def prepare_state(ctx, wl, tau=0.02, passes=(4, 2, 2, 2, 2, 2, 2, 2), mix=0.5):
@@ -330,26 +417,48 @@ def prepare_state(ctx, wl, tau=0.02, passes=(4, 2, 2, 2, 2, 2, 2, 2), mix=0.5):
 
 # ---------------------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The FP64 oracle on the host cores (rank 0 only): W untimed and K timed samples, each one
+    oracle predictor-corrector step on the 4^3-cell crop of the workload's mesh; the exponent of
+    the cost in the cell count is fitted first from the 4^3 and 6^3 crops, and every sample is
+    reported in the GPU arm's unit (steps/s of the full workload) through that fit.  ms_per_step
+    is the measured time of a sample, so steps x ms_per_step is the run's own timed region."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     wl = workload(args.cells, 0)
-    # each timed unit is one oracle sample step (bounded so the run ends in minutes)
-    vals = []
-    info = None
-    for i in range(max(1, min(args.steps, 3))):
-        info = cpu_baseline(wl, None, budget_s=20.0)
-        vals.append(info["value"])
-    value = statistics.median(vals)
+    blas, threads = blas_info()
+    t4, c4, _ = oracle_crop_step(wl, 4)
+    t6, c6, _ = oracle_crop_step(wl, 6)
+    b, _ = fit_exponent([c4, c6], [t4, t6])
+    for _ in range(args.warmup):
+        oracle_crop_step(wl, 4)
+    secs = []
+    for _ in range(args.steps):
+        t, _, _ = oracle_crop_step(wl, 4)
+        secs.append(t)
+    sample_s = statistics.median(secs)
+    value = 1.0 / (sample_s * (wl.n_cells / c4) ** b)
+    sample = ("one predictor-corrector step of the FP64 oracle on the %d-cell crop (4^3) of the same mesh, all %d "
+              "orbitals; full-mesh time per step = sample x (%d / %d)^%.2f (exponent fitted on the 4^3 and 6^3 crops, "
+              "%.2f and %.2f s)" % (c4, wl.n_orb, wl.n_cells, c4, b, t4, t6))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
-            "steps": len(vals), "warmup": 0, "ms_per_step": 1000.0 / value, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": 1, "flush": "inputs larger than L2"},
-            "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"], "value": value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 * sum(secs) / len(secs), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded efe_workloads.na8)", "config": bench_config(wl, args.gpus),
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "blas": blas, "sample": sample, "value": value,
                              "unit": "steps/s"},
+            "ms_per_full_step_extrapolated": round(1000.0 / value, 1),
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def bench_config(wl, world):
+    """The workload description both arms print (the same dict)."""
+    return {"workload": WORKLOAD, "global_batch": world, "n_cells": int(wl.n_cells), "n_orb": int(wl.n_orb),
+            "degree": int(wl.degree), "n_enrich": int(len(wl.enrich)), "krylov_tol": wl.krylov_tol,
+            "dt": wl.dt, "parallelism": "independent problem per GPU" if world > 1 else "1 GPU",
+            "flush": "inputs larger than L2 (orbital block %.2f GB)" % (wl.n_dof * wl.n_orb * 16 / 1e9)}
 
 
 # ---------------------------------------------------------------------------- GPU arm
@@ -427,66 +536,54 @@ def run_efe(args):
     value = job_throughput(world, args.steps, ms)
 
     # dominant kernel: cell apply, timed by CUDA events on its stream inside the timed region
-    bytes_, flops, dense = apply_model(ctx, wl, args.precision)
+    bytes_, flops, issued = apply_model(ctx, wl, args.precision)
     t_apply = prof["apply_ms"] / max(prof["apply_launches"], 1) / 1000.0
     peaks, src = measured_peaks()
+    pipes = pipe_peaks_measured() if rank == 0 else {}
     gbs = bytes_ / t_apply / 1e9
-    sm_mhz = (ck or {}).get("sm_mhz") or 1900.0
-    fp_lanes = 2 if args.precision == "fp64" else 128   # FP64 FMA / FP32 lanes per clock per SM
-    alu_peak = 152 * fp_lanes * 2 * sm_mhz * 1e6 / 1e12
-    if args.precision == "pair":
-        # each pair fma is 12 FP32-pipe instructions (1 mul, 3 fma, 8 add) = 15 flops; the pipe's peak
-        # for that mix is 15 flops per 12 lane-cycles
-        flops *= 15.0 / 2.0
-        alu_peak = 152 * 128 * (15.0 / 12.0) * sm_mhz * 1e6 / 1e12
     tfl = flops / t_apply / 1e12
-    # dram__bytes_read.sum + dram__bytes_write.sum of one k_cell_apply<df32,5,6,ENR,8> launch on the
-    # 15^3-cell crop (438.96 MB against 348.27 MB algorithmic), scaled to this launch by its algorithmic
-    # bytes; only for the pair kernel that capture measured
-    traffic = (round(bytes_ * 438.959616 / 348.26868, -6)
-               if args.precision == "pair" and wl.degree == 4 else None)
     hbm_frac = gbs / peaks["hbm_gbs"]
-    alu_frac = tfl / alu_peak
+    kernel = ("k_tc_apply<5>" if args.precision == "tc" else
+              "k_cell_apply<%s,5,6,ENR>" % {"mixed": "float", "pair": "df32", "fp64": "double"}[args.precision])
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel on the 15^3-cell crop of
+    # the same mesh (ncu, profiles/), against that launch's algorithmic bytes; scaled to this launch by
+    # its algorithmic bytes.  None where no capture of the kernel as it stands exists.
+    captured = TRAFFIC.get(kernel) if wl.degree == 4 else None
+    traffic = round(bytes_ * captured[0] / captured[1], -6) if captured else None
     if args.precision == "tc":
-        # bf16 slice products on the tensor cores, timed inside a long step: the sustained peak
+        # the dense contraction runs on the bf16 tensor pipe, timed inside a long step: the sustained peak
         tpk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-        roof = {"bound": "tensor", "achieved": round(tfl, 2), "peak": tpk, "unit": "TFLOP/s",
-                "frac": round(tfl / tpk, 4), "traffic": None,
+        roof = {"bound": "tensor", "achieved": round(tfl, 3), "peak": tpk, "unit": "TFLOP/s",
+                "frac": round(tfl / tpk, 5), "traffic": traffic,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (%s)" % src,
-                "hbm_frac_of_measured": round(hbm_frac, 4)}
-    elif alu_frac >= hbm_frac:
-        roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
-                "frac": round(alu_frac, 4), "traffic": traffic,
-                "peak_source": ("152 SMs x 128 FP32 lanes x 15/12 flop per lane-cycle (pair-fma instruction mix) x "
-                                "%.0f MHz (median SM clock sampled in the timed region)" % sm_mhz)
-                               if args.precision == "pair" else
-                               "152 SMs x %d %s FMA/clk x 2 x %.0f MHz (median SM clock sampled in the timed region)"
-                               % (fp_lanes, "FP32" if fp_lanes == 128 else "FP64", sm_mhz),
+                "issued_slice_product_tflops": round(issued / t_apply / 1e12, 2),
+                "issued_frac": round(issued / t_apply / 1e12 / tpk, 4),
                 "hbm_frac_of_measured": round(hbm_frac, 4)}
     else:
-        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(hbm_frac, 4), "traffic": traffic, "peak_source": src, "alu_frac": round(alu_frac, 4)}
-    roof.update({"kernel": "k_tc_apply<5>" if args.precision == "tc" else
-                 "k_cell_apply<%s,5,6,ENR>" % {"mixed": "float", "pair": "df32", "fp64": "double"}[args.precision],
-                 "launches": prof["apply_launches"], "avg_ms": round(t_apply * 1000.0, 4),
-                 "algorithmic_bytes": int(bytes_), "algorithmic_flops": flops})
-    hx_tflops = dense / t_apply / 1e12
+        pk = pipes.get("fp64_fma_tflops" if args.precision == "fp64" else "fp32_fma_tflops")
+        roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": pk, "unit": "TFLOP/s",
+                "frac": round(tfl / pk, 5) if pk else None, "traffic": traffic,
+                "peak_source": "efe_pipe_peaks: measured %s FMA pipe of this device" %
+                               ("FP64" if args.precision == "fp64" else "FP32"),
+                "issued_tflops": round(issued / t_apply / 1e12, 3), "hbm_frac_of_measured": round(hbm_frac, 4)}
+    roof.update({"kernel": kernel, "launches": prof["apply_launches"], "avg_ms": round(t_apply * 1000.0, 4),
+                 "algorithmic_bytes": int(bytes_), "algorithmic_flops": flops,
+                 "flops_def": "N_c 2 N_n^2 cols + 4 N_n n_pairs cols (dense cell contraction + enrichment coupling)"})
 
+    cfg = bench_config(wl, world)
+    cfg.update({"precision": args.precision, "n_nodes": ctx.n_nodes, "n_pairs": ctx.n_pairs, "k_max": wl.k_max})
     line = {"metric": METRIC, "value": round(value, 4), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": {"mixed": "f32-contraction/f64", "pair": "f32-pair-contraction/f64", "fp64": "f64",
                       "tc": "bf16x4-split-tensor-contraction/f64"}[args.precision],
             "data": "synthetic (seeded efe_workloads.na8)",
-            "config": {"workload": WORKLOAD, "precision": args.precision, "global_batch": world,
-                       "n_cells": ctx.n_cells, "n_nodes": ctx.n_nodes, "n_enrich": ctx.n_enrich,
-                       "n_pairs": ctx.n_pairs, "n_orb": wl.n_orb, "krylov_tol": wl.krylov_tol, "k_max": wl.k_max,
-                       "parallelism": "independent problem per GPU" if world > 1 else "1 GPU",
-                       "flush": "inputs larger than L2 (orbital block %.2f GB)" % (ctx.n_dof * ctx.n_cols * 16 / 1e9)},
+            "config": cfg,
             "roofline": roof,
-            "hx": {"tflops_dense_equivalent": round(hx_tflops, 3),
-                   "note": "N_c * 2 N_n^2 * cols per H.X over the cell-apply time; the kernel does the "
-                           "sum-factorised equivalent"},
+            "hx": {"tflops": round(tfl, 3),
+                   "note": "algorithmic flops of one H.X (dense cell contraction + coupling) over the cell-apply "
+                           "time; the same count for every precision"},
+            "pipe_peaks": pipes,
             "gpu_launches": prof["launches"], "clocks": ck,
             "krylov": {"k_pred": [i["k_pred"] for i in infos], "k_corr": [i["k_corr"] for i in infos],
                        "eps_max": [i["eps_max"] for i in infos], "cap_hits": [i["cap"] for i in infos],
@@ -613,8 +710,7 @@ def run_efe(args):
                               "note": "Lanczos loops captured as CUDA graphs (k_max iterations, no host sync)"}
         ctxg.close()
     if rank == 0 and not args.no_cpu_baseline:
-        k_hint = max([i["k_corr"] for i in infos] or [wl.k_max])
-        line["cpu_baseline"] = cpu_baseline(workload(args.cells, 0), k_hint)
+        line["cpu_baseline"] = cpu_baseline(workload(args.cells, 0))
     if next_rows is not None:
         line["next_rows"] = next_rows
     if rank == 0:
@@ -818,8 +914,49 @@ def run_adjoint(args):
     return 0
 
 
+def run_apply_only(args):
+    """CUDA-event times of single cell applies (with the enrichment pre/post steps) on the
+    workload at --cells, against an FP64 apply of the same random block."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED, EFE_PAIR, EFE_TC, Context
+    torch.cuda.set_device(0)
+    prec = {"mixed": EFE_MIXED, "pair": EFE_PAIR, "fp64": EFE_FP64, "tc": EFE_TC}[args.precision]
+    wl = workload(args.cells, 0)
+    ctx = Context(wl)
+    _, quad = ctx.coords()
+    vN = torch.zeros(quad.shape[:2], dtype=torch.float64, device="cuda")
+    for Z, R in zip(wl.Z, wl.R):
+        vN -= float(Z) / torch.sqrt(((quad - torch.tensor(R, dtype=torch.float64, device="cuda")) ** 2).sum(dim=2))
+    ctx.set_potential(vN[None].contiguous())
+    gen = torch.Generator(device="cuda").manual_seed(2210)
+    X = torch.randn((ctx.n_dof, ctx.n_cols), dtype=torch.complex128, device="cuda", generator=gen)
+    Y, Y64 = torch.empty_like(X), torch.empty_like(X)
+    ctx.apply_H(X, Y64, precision=EFE_FP64)
+    for _ in range(args.warmup):
+        ctx.apply_H(X, Y, precision=prec)
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.apply_H(X, Y, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    bytes_, flops, issued = apply_model(ctx, wl, args.precision)
+    print(json.dumps({"mode": "apply-only", "precision": args.precision, "cells": ctx.n_cells, "n_pairs": ctx.n_pairs,
+                      "n_dof": ctx.n_dof, "cols": 2 * ctx.n_cols, "ms": [round(x, 4) for x in ms],
+                      "algorithmic_bytes": int(bytes_), "algorithmic_flops": flops,
+                      "max_rel_diff_vs_fp64": ((Y - Y64).abs().max() / Y64.abs().max()).item()}))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.apply_only:
+        return run_apply_only(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.adjoint:

@@ -573,6 +573,15 @@ efe_status efe_tuning(efe_ctx* ctx, int32_t precision, int32_t force_variant, in
  * round-to-nearest ties).  *mismatches_host receives the count (0 expected).
  * Synchronises the device. */
 efe_status efe_selftest(int64_t n, int64_t* mismatches_host);
+
+/* Diagnostics (not part of the method): measured throughput of the float32 and
+ * float64 fused-multiply-add pipes of the current device in TFLOP/s (2 flops per
+ * FMA; eight independent chains per thread, eight blocks of 256 threads per SM,
+ * CUDA events around one launch after a warm-up).  These are the peaks the
+ * roofline fractions of the float32-pair and float64 cell kernels are stated
+ * against.  Allocates and frees a small device buffer and synchronises the device.
+ * Errors: EFE_ERR_ARG (null pointer), EFE_ERR_CUDA. */
+efe_status efe_pipe_peaks(double* fp32_tflops_host, double* fp64_tflops_host);
 efe_status efe_profile_read(efe_ctx* ctx, int64_t* launches, int64_t* apply_launches, double* apply_ms);
 
 #ifdef __cplusplus

@@ -29,7 +29,7 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply", "efe_octree_constraints",
             "efe_atom_hartree_table", "efe_adaptive_cell_boxes", "efe_octree_poisson",
             "efe_octree_density", "efe_octree_kexp", "efe_octree_interp", "efe_lda_points",
-            "efe_octree_magnus_step"]
+            "efe_octree_magnus_step", "efe_pipe_peaks"]
 
 
 class MeshDesc(C.Structure):
@@ -102,6 +102,7 @@ def lib(path: str = LIB_PATH):
     L.efe_init_orbitals.argtypes = [vp, vp, i32, pdbl, pdbl, pdbl, pdbl, vp]
     L.efe_profile.argtypes = [vp, i32]
     L.efe_selftest.argtypes = [i64, C.POINTER(i64)]
+    L.efe_pipe_peaks.argtypes = [pdbl, pdbl]
     L.efe_tuning.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.efe_profile_read.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl)]
     L.efe_absorption_spectrum.argtypes = [vp, i64, i64, i64, dbl, vp, dbl, vp, i64, dbl, vp, vp]
@@ -143,6 +144,15 @@ def selftest(n: int = 1 << 24) -> int:
     if st != EFE_OK:
         raise EfeError(st, lib().efe_last_error(None).decode())
     return m.value
+
+
+def pipe_peaks():
+    """Measured float32 and float64 FMA-pipe throughput of the current device (TFLOP/s)."""
+    a, b = C.c_double(), C.c_double()
+    st = lib().efe_pipe_peaks(C.byref(a), C.byref(b))
+    if st != EFE_OK:
+        raise EfeError(st, "efe_pipe_peaks failed")
+    return a.value, b.value
 
 
 class EfeError(RuntimeError):
