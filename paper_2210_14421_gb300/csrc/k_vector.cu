@@ -19,7 +19,7 @@ static unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) /
 
 // Lanczos scalar layout in Ctx::d_lz for C complex columns.
 struct LzView {
-  double *nrm, *alpha, *beta, *yre, *yim, *eps, *red, *red2, *dt, *invb;
+  double *nrm, *alpha, *beta, *yre, *yim, *eps, *red, *red2, *dt, *dts_in;
   df32* wp;   // [kMaxK][C][2] combination weights nrm y_j as float32 pairs (re, im)
   int *active, *kused, *cap, *n_active;
 };
@@ -35,8 +35,8 @@ static LzView lz_view(const Ctx& c, long long C) {
   v.red = v.eps + C;
   v.red2 = v.red + C;
   v.dt = v.red2 + C;
-  v.invb = v.dt + C;
-  v.wp = reinterpret_cast<df32*>(v.invb + C);
+  v.dts_in = v.dt + C;
+  v.wp = reinterpret_cast<df32*>(v.dts_in + C);
   int* ib = c.d_lzi;
   v.active = ib;
   v.kused = ib + C;
@@ -128,30 +128,43 @@ __global__ void k_lz_dot(const double* __restrict__ Qj, const double* __restrict
   block_col_reduce(acc, f.col, f.ok, C, sred, out);
 }
 
-// W -= alpha Qj + beta_prev Qjm1 ; red2[col] += |W|^2
-__global__ void k_lz_update(double* __restrict__ W, const double* __restrict__ Qj, const double* __restrict__ Qjm1,
-                            long long n_rows, int C, const int* __restrict__ active, const double* __restrict__ alpha,
-                            const double* __restrict__ beta_prev, double* __restrict__ out) {
+// The basis is stored unnormalised: V_0 = Q_0 and V_{j+1} = w_j, the Lanczos residual of
+// iteration j, so V_j = s_j Q_j with s_0 = 1 and s_j = beta_{j-1}; no scaling pass is needed.
+// Iteration j, after the apply W = Hbar V_j and the dot red = <V_j, W> = s_j^2 alpha_j:
+//   w = (W - alpha_j V_j) / s_j - beta_{j-1} V_{j-1} / s_{j-1},   red2[col] += |w|^2,
+// written over W (it becomes V_{j+1}).  Columns that have stopped get zeros, so the applies of
+// later iterations (graph mode runs all k_max) see a zero vector.
+__device__ __forceinline__ double lz_norm_of_basis(const double* beta, int j, int C, int col) {
+  return j <= 0 ? 1.0 : beta[(long long)(j - 1) * C + col];
+}
+__global__ void k_lz_update(double* __restrict__ W, const double* __restrict__ Vj, const double* __restrict__ Vjm1,
+                            long long n_rows, int C, const int* __restrict__ active, const double* __restrict__ dotv,
+                            const double* __restrict__ beta, int j, double* __restrict__ out) {
   extern __shared__ double sred[];
   FlatIter f = flat_iter(C);
   double acc = 0.0;
   if (f.ok && active[f.col]) {
-    const double a = alpha[f.col];
-    const double b = Qjm1 ? beta_prev[f.col] : 0.0;
+    const double sj = lz_norm_of_basis(beta, j, C, f.col);
+    const double c1 = 1.0 / sj;
+    const double c2 = dotv[f.col] / (sj * sj) * c1;   // alpha_j / s_j
+    const double c3 = Vjm1 ? beta[(long long)(j - 1) * C + f.col] / lz_norm_of_basis(beta, j - 1, C, f.col) : 0.0;
     for (long long r = f.row0; r < n_rows; r += f.rstride) {
       const long long o = r * 2 * C + 2 * f.col;
       double2 w = *reinterpret_cast<double2*>(W + o);
-      const double2 q = *reinterpret_cast<const double2*>(Qj + o);
-      w.x -= a * q.x;
-      w.y -= a * q.y;
-      if (Qjm1) {
-        const double2 p = *reinterpret_cast<const double2*>(Qjm1 + o);
-        w.x -= b * p.x;
-        w.y -= b * p.y;
+      const double2 q = *reinterpret_cast<const double2*>(Vj + o);
+      w.x = c1 * w.x - c2 * q.x;
+      w.y = c1 * w.y - c2 * q.y;
+      if (Vjm1) {
+        const double2 p = *reinterpret_cast<const double2*>(Vjm1 + o);
+        w.x -= c3 * p.x;
+        w.y -= c3 * p.y;
       }
       *reinterpret_cast<double2*>(W + o) = w;
       acc += w.x * w.x + w.y * w.y;
     }
+  } else if (f.ok) {
+    for (long long r = f.row0; r < n_rows; r += f.rstride)
+      *reinterpret_cast<double2*>(W + r * 2 * C + 2 * f.col) = make_double2(0.0, 0.0);
   }
   block_col_reduce(acc, f.col, f.ok, C, sred, out);
 }
@@ -310,7 +323,8 @@ __global__ void k_lz_tri(LzView v, int C, int j, int k_max, int fixed_k, double 
   __shared__ int sK;
   TriScratch t{be + kMaxK, be + 2 * kMaxK + 2, be + 3 * kMaxK + 4, sc, &sK};
   if (lane == 0) {
-    v.alpha[(long long)j * C + col] = v.red[col];
+    const double sj = lz_norm_of_basis(v.beta, j, C, col);
+    v.alpha[(long long)j * C + col] = v.red[col] / (sj * sj);
     v.beta[(long long)j * C + col] = sqrt(v.red2[col]);
   }
   __syncwarp();
@@ -339,7 +353,6 @@ __global__ void k_lz_tri(LzView v, int C, int j, int k_max, int fixed_k, double 
     v.active[col] = 0;
     v.kused[col] = m;
   } else {
-    v.invb[col] = 1.0 / b_j;
     atomicAdd(v.n_active, 1);
   }
 }
@@ -366,25 +379,18 @@ __global__ void k_lz_eval(LzView v, int C, const double* __restrict__ dts) {
   tri_exp_warp(al, be, m, dts[col], t, v, col, C);
 }
 
-// Q_{j+1} = W / beta_j for columns still running, zero for finished ones
-__global__ void k_lz_scale(double* __restrict__ W, long long n_rows, int C, const int* __restrict__ active,
-                           const double* __restrict__ invb) {
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= n_rows * C) return;
-  const int col = (int)(idx % C);
-  double2* p = reinterpret_cast<double2*>(W) + idx;
-  if (active[col]) {
-    const double s = invb[col];
-    double2 w = *p;
-    w.x *= s;
-    w.y *= s;
-    *p = w;
-  } else {
-    *p = make_double2(0.0, 0.0);
-  }
+// y_j <- y_j / s_j for j < kused: the weights of the unnormalised basis vectors V_j = s_j Q_j
+__global__ void k_lz_wscale(LzView v, int C, int K) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= K * C) return;
+  const int j = i / C, col = i % C;
+  if (j >= v.kused[col]) return;
+  const double inv = 1.0 / lz_norm_of_basis(v.beta, j, C, col);
+  v.yre[i] *= inv;
+  v.yim[i] *= inv;
 }
 
-// out = nrm * sum_{j < kused} y_j Q_j.  One thread per complex entry; the basis
+// out = nrm * sum_{j < kused} y_j V_j (weights already divided by s_j).  One thread per complex entry; the basis
 // vectors are read eight at a time (independent loads in flight) with
 // streaming hints, since each is touched once.
 __global__ void __launch_bounds__(256) k_lz_combine(const double* __restrict__ Q, long long qstride,
@@ -479,6 +485,8 @@ __global__ void __launch_bounds__(256) k_lz_combine_pair(const double* __restric
 // The Krylov combination in the precision of the run: float64 for EFE_FP64, float32 pairs otherwise.
 static cudaError_t launch_combine(const Ctx& c, const LzView& v, long long n, long long C, double* out, long long ld2,
                                   int precision, cudaStream_t s) {
+  k_lz_wscale<<<nblk((long long)c.k_max * C), 256, 0, s>>>(v, (int)C, c.k_max);
+  note_launch();
   if (precision == EFE_FP64) {
     k_lz_combine<<<nblk(n * C), 256, 0, s>>>(c.d_Q, n * 2 * C, n, (int)C, v, out, ld2);
     note_launch();
@@ -542,7 +550,7 @@ static cudaError_t kexp_body(Ctx& c, const double* in, double* out, int precisio
   note_launch();
   k_lz_init<<<nblk(n * C), 256, 0, s>>>(in, c.d_Q, n, (int)C, ld2, v.red);
   note_launch();
-  k_lz_state<<<nblk(C), 256, 0, s>>>(v, (int)C, v.invb);
+  k_lz_state<<<nblk(C), 256, 0, s>>>(v, (int)C, v.dts_in);
   note_launch();
   EFE_CUDA_TRY(cudaGetLastError());
   c.apply_gate = eager ? nullptr : v.n_active;
@@ -556,12 +564,10 @@ static cudaError_t kexp_body(Ctx& c, const double* in, double* out, int precisio
     k_lz_dot<<<rg, 256, rs, s>>>(Qj, W, n, (int)C, v.active, v.red);
     note_launch();
     k_lz_update<<<rg, 256, rs, s>>>(W, Qj, j > 0 ? c.d_Q + (j - 1) * qstride : nullptr, n, (int)C, v.active, v.red,
-                                    j > 0 ? v.beta + (long long)(j - 1) * C : nullptr, v.red2);
+                                    v.beta, j, v.red2);
     note_launch();
     k_lz_tri<<<(unsigned)C, 32, sizeof(double) * (4 * kMaxK + 4 + kMaxBessel), s>>>(v, (int)C, j, c.k_max, c.fixed_k,
                                                                             c.krylov_tol);
-    note_launch();
-    k_lz_scale<<<nblk(n * C), 256, 0, s>>>(W, n, (int)C, v.active, v.invb);
     note_launch();
     EFE_CUDA_TRY(cudaGetLastError());
     if (eager) {
@@ -583,8 +589,8 @@ cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h
                           int* cap_hits, double* eps_max, cudaStream_t s, bool need_stats) {
   const long long C = (long long)c.n_orb * c.op.batch;
   LzView v = lz_view(c, C);
-  // per-column time steps; they reach k_lz_state through invb (outside any graph)
-  EFE_CUDA_TRY(cudaMemcpyAsync(v.invb, h_dts, sizeof(double) * C, cudaMemcpyHostToDevice, s));
+  // per-column time steps; they reach k_lz_state through dts_in (outside any graph)
+  EFE_CUDA_TRY(cudaMemcpyAsync(v.dts_in, h_dts, sizeof(double) * C, cudaMemcpyHostToDevice, s));
   bool done = false;
   if (c.use_graphs) {
     Ctx::KexpGraph key{in, out, precision, C, c.op.kin, c.ws_gen, nullptr};
@@ -644,8 +650,8 @@ cudaError_t run_kexp_recombine(Ctx& c, double* out, const double* h_dts, cudaStr
   const long long C = (long long)c.n_orb * c.op.batch;
   const long long n = c.n_dof;
   LzView v = lz_view(c, C);
-  EFE_CUDA_TRY(cudaMemcpyAsync(v.invb, h_dts, sizeof(double) * C, cudaMemcpyHostToDevice, s));
-  k_lz_eval<<<(unsigned)C, 32, sizeof(double) * (4 * kMaxK + 4 + kMaxBessel), s>>>(v, (int)C, v.invb);
+  EFE_CUDA_TRY(cudaMemcpyAsync(v.dts_in, h_dts, sizeof(double) * C, cudaMemcpyHostToDevice, s));
+  k_lz_eval<<<(unsigned)C, 32, sizeof(double) * (4 * kMaxK + 4 + kMaxBessel), s>>>(v, (int)C, v.dts_in);
   note_launch();
   return launch_combine(c, v, n, C, out, 2 * C, c.precision == EFE_FP64 ? EFE_FP64 : EFE_PAIR, s);
 }
