@@ -113,8 +113,12 @@ def potentials(system: System, rho: np.ndarray, xc_kind: str = "pw92", hartree=N
 
 
 def make_state(system: System, psi_bar: np.ndarray, occ: np.ndarray, batch: int, xc_kind: str = "pw92",
-               hartree=None) -> State:
+               hartree=None, reduce=None) -> State:
+    """reduce(rho) -> rho summed over processes, when the orbitals are split among them
+    (rho is a sum over orbitals; None: all orbitals are here)."""
     rho = density(system, psi_bar, occ, batch)
+    if reduce is not None:
+        rho = reduce(rho)
     vH, vxc, phi = potentials(system, rho, xc_kind, hartree)
     return State(rho=rho, vH=vH, vxc=vxc, phi=phi)
 
@@ -136,11 +140,14 @@ def kexp_members(system: System, psi_bar, v_members, n_orb, dt, tol, k_max, fixe
 
 def magnus_step(system: System, psi_bar: np.ndarray, state: State, t: float, dt: float, fields, occ,
                 tol: float, k_max: int, fixed_k: int = 0, vN=None, scheme: str = "pc", xc_kind: str = "pw92",
-                hartree=None):
+                hartree=None, reduce=None):
     """One step: predictor-corrector S1..S6 (scheme "pc"), or the
     potential-extrapolation step (scheme "extrapolated"; predictor-corrector
     while the state has no history).  Returns (psi_new, state_new, mu
-    (batch, 3), info dict)."""
+    (batch, 3), info dict).  With the orbitals split among processes, psi_bar
+    and occ are this process's and reduce(rho) sums a density over the
+    processes (each orbital's exponential is independent of the others)."""
+    red = (lambda r: r) if reduce is None else reduce
     batch = len(fields)
     n_orb = len(occ)
     if vN is None:
@@ -154,14 +161,14 @@ def magnus_step(system: System, psi_bar: np.ndarray, state: State, t: float, dt:
     elif scheme in ("pc", "extrapolated"):
         v1 = [vN + vhxc[b] + field_potential(system, Emid[b]) for b in range(batch)]
         psi_p, k1 = kexp_members(system, psi_bar, v1, n_orb, dt, tol, k_max, fixed_k)
-        rho_p = density(system, psi_p, occ, batch)
+        rho_p = red(density(system, psi_p, occ, batch))
         rho_mid = 0.5 * (state.rho + rho_p)
         vH_mid, vxc_mid, _ = potentials(system, rho_mid, xc_kind, hartree)
         v2 = [vN + vH_mid[b] + vxc_mid[b] + field_potential(system, Emid[b]) for b in range(batch)]
     else:
         raise ValueError("unknown scheme")
     psi_new, k2 = kexp_members(system, psi_bar, v2, n_orb, dt, tol, k_max, fixed_k)
-    new_state = make_state(system, psi_new, occ, batch, xc_kind, hartree)
+    new_state = make_state(system, psi_new, occ, batch, xc_kind, hartree, reduce)
     new_state.vhxc_prev = vhxc
     mu = np.stack([dipole(system, new_state.rho[b]) for b in range(batch)])
     return psi_new, new_state, mu, {"k_pred": k1, "k_corr": k2}
