@@ -40,8 +40,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "TDDFT steps/s & H.X TFLOP/s (% peak), mixed vs FP64 at dipole err<=1e-5"
-WORKLOAD = "Na8-like cluster (Z=11 x 8, 44 doubly occupied orbitals), 31^3 graded hex cells degree 4, " \
-           "GL 6^3, 48 enrichment fns (1s,2s,2p,3s per atom, cutoff 6 bohr), dt=0.05, kick 1e-3"
+WORKLOADS = {
+    "na8": "Na8-like cluster (Z=11 x 8, 44 doubly occupied orbitals), 31^3 graded hex cells degree 4, GL 6^3, "
+           "48 enrichment fns (1s,2s,2p,3s per atom, cutoff 6 bohr), dt=0.05, kick 1e-3",
+    "na50": "Na50-like cluster (Z=11 x 50, 275 doubly occupied orbitals), 60-bohr cube, 43^3 graded hex cells "
+            "degree 4 (5.18M nodes), 300 enrichment fns, Krylov dim <= 16, dt=0.05, kick 1e-3",
+    "organic27": "organic-27-like molecule (15 C/N/O + 12 H, 59 orbitals), 30-bohr cube, 27^3 graded hex cells "
+                 "degree 4, 87 enrichment fns, Krylov dim <= 16, dt=0.05, kick 1e-3",
+    "mg2x48": "Mg2-like dimer (Z=12, 12 orbitals) x 48 batch members (16 amplitudes in [1e-3, 2e-2] x 3 "
+              "polarisations, 10-cycle trapezoid sine pulses, w=0.057), 40-bohr cube, 25^3 graded hex cells "
+              "degree 5, GL 7^3, Krylov dim <= 16, dt=0.02",
+}
 
 
 def parse_args(argv=None):
@@ -50,7 +59,11 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="efe", choices=["efe", "reference"])
-    ap.add_argument("--precision", default="tc", choices=["tc", "pair", "mixed", "fp64"])
+    ap.add_argument("--precision", default=None, choices=["tc", "pair", "mixed", "fp64"],
+                    help="default: tc (degree <= 4), pair (the degree-5 Mg2 batch)")
+    ap.add_argument("--workload", default="na8", choices=list(WORKLOADS),
+                    help="na8 (the headline), na50 (275 orbitals, Krylov basis in column blocks), organic27, "
+                         "mg2x48 (48 batch members of degree 5)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64 steps reported beside the main number")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--graph-steps", type=int, default=3, help="extra steps timed in CUDA-graph mode")
@@ -68,11 +81,15 @@ def parse_args(argv=None):
                     help="time --steps cell applies (Y = Hbar X, random X, the nuclear potential) of the workload "
                          "at --cells and --precision after --warmup untimed ones, one JSON line; the target of the "
                          "kernel profiles")
-    ap.add_argument("--k-max", type=int, default=64,
-                    help="Lanczos cap; the Na8-like spectrum (-257..+2500 Ha) at dt = 0.05 needs k = 57 (FP64, "
-                         "pair) to 58 (float32) for eps_k <= 1e-7. Below that the exponential is unconverged and "
-                         "repeated FP64 runs already differ by ~1e-6 in the dipole after 3 steps (amplified "
-                         "rounding), so the precision comparison means nothing there")
+    ap.add_argument("--k-max", type=int, default=None,
+                    help="Lanczos cap (default: 64 for na8, the workload's own 16 otherwise); the Na8-like "
+                         "spectrum (-257..+2500 Ha) at dt = 0.05 needs k = 57 (FP64, pair) to 58 (float32) for "
+                         "eps_k <= 1e-7. Below that the exponential is unconverged and repeated FP64 runs already "
+                         "differ by ~1e-6 in the dipole after 3 steps (amplified rounding)")
+    ap.add_argument("--substeps", type=int, default=0,
+                    help="Krylov sub-steps per exponential (0: adaptive: a pass whose columns reach k_max above "
+                         "the tolerance is repeated with twice the sub-steps; the Na50-like workload's cap of 16 "
+                         "meets eps_k <= 1e-7 at dt = 0.05 only with sub-steps)")
     return ap.parse_args(argv)
 
 
@@ -157,12 +174,29 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def workload(cells, rank):
+def workload(args, rank):
+    """The benchmark workload (seeded, synthetic); for na8 --cells picks a coarser or finer mesh of
+    the same cluster.  Ranks propagate independent problems (weak scaling): the kick direction of a
+    single-member workload cycles x, y, z with the rank."""
     import efe_workloads as W
-    wl = W.na8() if cells == 31 else W.na_cluster(n_atoms=8, L=40.0, cells_per_axis=cells)
-    # independent problems per rank (weak scaling): the kick direction cycles x, y, z
-    d = [(1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0)][rank % 3]
-    wl.fields[0].direction = d
+    name = getattr(args, "workload", "na8")
+    cells = getattr(args, "cells", 31)
+    if name == "na8":
+        wl = W.na8() if cells == 31 else W.na_cluster(n_atoms=8, L=40.0, cells_per_axis=cells)
+    elif name == "na50":
+        wl = W.na50()
+    elif name == "organic27":
+        wl = W.organic27()
+        wl.fields[0] = W.Field(kind=W.FIELD_NONE, kick=1e-3, direction=(1.0, 0.0, 0.0))
+    else:
+        wl = W.mg2_batch()
+    if wl.batch == 1:
+        wl.fields[0].direction = [(1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0)][rank % 3]
+    k_max = getattr(args, "k_max", None)
+    if k_max is None and name == "na8":
+        k_max = 64
+    if k_max:
+        wl = wl.with_(k_max=k_max)
     return wl
 
 
@@ -224,6 +258,11 @@ def pipe_peaks_measured():
     return out
 
 
+def default_precision(args, wl):
+    """tc where the tensor-core path serves the degree (<= 4), else the float32-pair path."""
+    return args.precision or ("tc" if wl.degree <= 4 else "pair")
+
+
 def blas_info():
     """The oracle's BLAS (numpy's build configuration) and its thread count."""
     name = "unknown"
@@ -262,7 +301,9 @@ def oracle_crop_step(wl_full, n):
     keep = [f for f in wl_full.enrich
             if np.all(np.asarray(wl_full.R[f.atom]) > lo_c) and np.all(np.asarray(wl_full.R[f.atom]) < hi_c)]
     idx = [wl_full.enrich.index(f) for f in keep]
-    wl = wl_full.with_(xb=sub[0], yb=sub[1], zb=sub[2], enrich=keep, enr_coefs=wl_full.enr_coefs[:, idx])
+    # one batch member (members are independent problems; callers scale by the batch)
+    wl = wl_full.with_(xb=sub[0], yb=sub[1], zb=sub[2], enrich=keep, enr_coefs=wl_full.enr_coefs[:, idx], batch=1,
+                       fields=[wl_full.fields[0]])
     S = operators.System(wl)
     psi = S.initial_orbitals()
     psi = tdks.kick(S, psi, wl.fields, wl.n_orb, tol=wl.krylov_tol, k_max=wl.k_max)
@@ -304,14 +345,14 @@ def cpu_baseline(wl_full, crops=(4, 6, 8), budget_s=50.0):
         b, resid = fit_exponent(cells, secs)
     else:
         b, resid = 1.0, None
-    sec_full = secs[-1] * (wl_full.n_cells / cells[-1]) ** b
+    sec_full = secs[-1] * (wl_full.n_cells / cells[-1]) ** b * wl_full.batch
     return {"value": 1.0 / sec_full, "unit": "steps/s", "cores": threads, "kind": "oracle", "blas": blas,
             "sample": "one predictor-corrector step of the FP64 oracle on each of the %s-cell crops of the same mesh "
                       "(all %d orbitals, the enrichment functions inside each crop: %s), %s s; fit t ~ N_cells^%.2f "
-                      "(rms log residual %s), extrapolated from the largest crop to the %d cells"
+                      "(rms log residual %s), extrapolated from the largest crop to the %d cells%s"
                       % ("/".join("%d" % c for c in cells), wl_full.n_orb, "/".join(map(str, nfun)),
                          "/".join("%.2f" % t for t in secs), b, "%.3f" % resid if resid is not None else "n/a",
-                         wl_full.n_cells),
+                         wl_full.n_cells, " x %d batch members" % wl_full.batch if wl_full.batch > 1 else ""),
             "fit": {"cells": cells, "seconds": [round(t, 3) for t in secs], "exponent": round(b, 3),
                     "rms_log_residual": resid}}
 
@@ -425,7 +466,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    wl = workload(args.cells, 0)
+    wl = workload(args, 0)
     blas, threads = blas_info()
     t4, c4, _ = oracle_crop_step(wl, 4)
     t6, c6, _ = oracle_crop_step(wl, 6)
@@ -437,14 +478,14 @@ def run_reference(args):
         t, _, _ = oracle_crop_step(wl, 4)
         secs.append(t)
     sample_s = statistics.median(secs)
-    value = 1.0 / (sample_s * (wl.n_cells / c4) ** b)
+    value = 1.0 / (sample_s * (wl.n_cells / c4) ** b * wl.batch)
     sample = ("one predictor-corrector step of the FP64 oracle on the %d-cell crop (4^3) of the same mesh, all %d "
               "orbitals; full-mesh time per step = sample x (%d / %d)^%.2f (exponent fitted on the 4^3 and 6^3 crops, "
               "%.2f and %.2f s)" % (c4, wl.n_orb, wl.n_cells, c4, b, t4, t6))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 * sum(secs) / len(secs), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded efe_workloads.na8)", "config": bench_config(wl, args.gpus),
+            "data": "synthetic (seeded efe_workloads.%s)" % args.workload, "config": bench_config(args, wl, args.gpus),
             "cpu_baseline": {"kind": "oracle", "cores": threads, "blas": blas, "sample": sample, "value": value,
                              "unit": "steps/s"},
             "ms_per_full_step_extrapolated": round(1000.0 / value, 1),
@@ -453,9 +494,9 @@ def run_reference(args):
     return 0
 
 
-def bench_config(wl, world):
+def bench_config(args, wl, world):
     """The workload description both arms print (the same dict)."""
-    return {"workload": WORKLOAD, "global_batch": world, "n_cells": int(wl.n_cells), "n_orb": int(wl.n_orb),
+    return {"workload": WORKLOADS[args.workload], "global_batch": world, "n_cells": int(wl.n_cells), "n_orb": int(wl.n_orb),
             "degree": int(wl.degree), "n_enrich": int(len(wl.enrich)), "krylov_tol": wl.krylov_tol,
             "dt": wl.dt, "parallelism": "independent problem per GPU" if world > 1 else "1 GPU",
             "flush": "inputs larger than L2 (orbital block %.2f GB)" % (wl.n_dof * wl.n_orb * 16 / 1e9)}
@@ -484,18 +525,27 @@ def run_efe(args):
         torch.cuda.set_device(0)
     g.build()
     dev = torch.cuda.current_device()
+    wl = workload(args, rank)
+    args.precision = default_precision(args, wl)
     prec = {"mixed": EFE_MIXED, "pair": EFE_PAIR, "fp64": EFE_FP64, "tc": EFE_TC}[args.precision]
-    wl = workload(args.cells, rank)
-    if args.k_max > 0:
-        wl = wl.with_(k_max=args.k_max)
     t_setup = time.perf_counter()
-    ctx = Context(wl, precision=prec, cg_tol=1e-10, cg_max_it=20000)
+    ctx = Context(wl, precision=prec, cg_tol=1e-10, cg_max_it=20000, krylov_substeps=args.substeps)
     t_setup = time.perf_counter() - t_setup
-    psi, prep = prepare_state(ctx, wl)
+    if wl.batch == 1:
+        psi, prep = prepare_state(ctx, wl)
+    else:
+        # the members share the ground state: prepared once on one member, then repeated
+        wl1 = wl.with_(batch=1, fields=[wl.fields[0]])
+        ctx1 = Context(wl1, precision=EFE_MIXED, cg_tol=1e-10, cg_max_it=20000)
+        psi1, prep = prepare_state(ctx1, wl1)
+        ctx1.close()
+        psi = psi1.repeat(1, wl.batch).contiguous()
+        del psi1
+    torch.cuda.empty_cache()   # the preparation's blocks back to the device (the Krylov basis sizes itself to it)
     ctx.kick(psi, wl.fields)
     psi_start = psi.clone()
     arr = fields_array(wl.fields)
-    mu = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+    mu = torch.zeros((wl.batch, 3), dtype=torch.float64, device="cuda")   # one dipole per batch member
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -543,12 +593,13 @@ def run_efe(args):
     gbs = bytes_ / t_apply / 1e9
     tfl = flops / t_apply / 1e12
     hbm_frac = gbs / peaks["hbm_gbs"]
-    kernel = ("k_tc_apply<5>" if args.precision == "tc" else
-              "k_cell_apply<%s,5,6,ENR>" % {"mixed": "float", "pair": "df32", "fp64": "double"}[args.precision])
+    kernel = ("k_tc_apply<%d>" % (wl.degree + 1) if args.precision == "tc" else
+              "k_cell_apply<%s,%d,%d,ENR>" % ({"mixed": "float", "pair": "df32", "fp64": "double"}[args.precision],
+                                             wl.degree + 1, wl.n_quad))
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel on the 15^3-cell crop of
     # the same mesh (ncu, profiles/), against that launch's algorithmic bytes; scaled to this launch by
     # its algorithmic bytes.  None where no capture of the kernel as it stands exists.
-    captured = TRAFFIC.get(kernel) if wl.degree == 4 else None
+    captured = TRAFFIC.get(kernel) if args.workload == "na8" else None
     traffic = round(bytes_ * captured[0] / captured[1], -6) if captured else None
     if args.precision == "tc":
         # the dense contraction runs on the bf16 tensor pipe, timed inside a long step: the sustained peak
@@ -570,14 +621,14 @@ def run_efe(args):
                  "algorithmic_bytes": int(bytes_), "algorithmic_flops": flops,
                  "flops_def": "N_c 2 N_n^2 cols + 4 N_n n_pairs cols (dense cell contraction + enrichment coupling)"})
 
-    cfg = bench_config(wl, world)
+    cfg = bench_config(args, wl, world)
     cfg.update({"precision": args.precision, "n_nodes": ctx.n_nodes, "n_pairs": ctx.n_pairs, "k_max": wl.k_max})
     line = {"metric": METRIC, "value": round(value, 4), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": {"mixed": "f32-contraction/f64", "pair": "f32-pair-contraction/f64", "fp64": "f64",
                       "tc": "bf16x4-split-tensor-contraction/f64"}[args.precision],
-            "data": "synthetic (seeded efe_workloads.na8)",
+            "data": "synthetic (seeded efe_workloads.%s)" % args.workload,
             "config": cfg,
             "roofline": roof,
             "hx": {"tflops": round(tfl, 3),
@@ -587,14 +638,16 @@ def run_efe(args):
             "gpu_launches": prof["launches"], "clocks": ck,
             "krylov": {"k_pred": [i["k_pred"] for i in infos], "k_corr": [i["k_corr"] for i in infos],
                        "eps_max": [i["eps_max"] for i in infos], "cap_hits": [i["cap"] for i in infos],
-                       "hartree_solves": [i["cg_iters"] for i in infos]},
+                       "hartree_solves": [i["cg_iters"] for i in infos],
+                       "substeps": [i["substeps"] for i in infos]},
             "setup_s": round(t_setup, 2), "initial_state": prep,
             "autotune": {"mixed": ctx.tuning(EFE_MIXED), "pair": ctx.tuning(EFE_PAIR), "fp64": ctx.tuning(EFE_FP64)}}
 
     def side_run(prec_code, timed_steps, n_cmp, scheme=0, fixed_k=0):
         """The same steps from the same kicked state at another precision (or step scheme): the
         dipoles of the first n_cmp steps and the device time per step of timed_steps more."""
-        cs = Context(wl, precision=prec_code, cg_tol=1e-10, cg_max_it=20000, scheme=scheme, fixed_k=fixed_k)
+        cs = Context(wl, precision=prec_code, cg_tol=1e-10, cg_max_it=20000, scheme=scheme, fixed_k=fixed_k,
+                     krylov_substeps=args.substeps)
         ps = psi_start.clone()
         mus, ts, first = [], 0.0, None
         while len(mus) < n_cmp:
@@ -612,6 +665,26 @@ def run_efe(args):
         torch.cuda.synchronize()
         cs.close()
         return f0.elapsed_time(f1) / max(timed_steps, 1), np.array(mus), first
+
+    # end to end through the public API with host buffers: H2D of the orbital
+    # block from pinned memory, the step, D2H of the dipole, every step
+    if rank == 0 and args.e2e_steps > 0:
+        host_psi = psi.cpu().pin_memory()
+        host_mu = torch.zeros((wl.batch, 3), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        a0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            psi.copy_(host_psi, non_blocking=True)
+            ctx.magnus_step_async(psi, t, wl.dt, arr, mu)
+            host_mu.copy_(mu, non_blocking=True)
+            torch.cuda.synchronize()
+            t += wl.dt
+        el = time.perf_counter() - a0
+        line["e2e"] = {"value": round(args.e2e_steps / el, 4), "unit": "steps/s",
+                       "h2d_bytes_per_step": int(psi.numel() * 16), "d2h_bytes_per_step": int(mu.numel() * 8)}
+
+    ctx.close()   # its Krylov basis back to the device before the side runs build their own
+    torch.cuda.empty_cache()
 
     if rank == 0 and args.fp64_steps > 0 and args.precision != "fp64":
         # FP64 (and, beside the pair path, the plain float32 contraction) from the same kicked
@@ -643,7 +716,11 @@ def run_efe(args):
                                              "first_step": firstp,
                                              "note": "EFE_PAIR: the sum-factorised contraction in float32 pairs "
                                                      "on the FP32 pipe"}
-        if args.precision == "pair":
+        if args.precision == "pair" and wl.degree > 4:
+            line["tensor_core_contraction"] = {"unavailable": "EFE_TC holds dense cell matrices of at most 128 "
+                                                              "nodes (degree <= 4); this mesh has degree %d"
+                                                              % wl.degree}
+        elif args.precision == "pair":
             mst, must, firstt = side_run(EFE_TC, args.fp64_steps, n_cmp)
             _, mustf, _ = side_run(EFE_TC, 0, n_cmp, fixed_k=k_fix)
             dt_fix = float(np.max(np.abs(mus64f - mustf)))
@@ -670,27 +747,10 @@ def run_efe(args):
                                        "note": "EFE_STEP_EXTRAPOLATED: v_Hxc at the mid-point extrapolated from the "
                                                "last two steps, one exponential per step (second order, as PC)"}
 
-    # end to end through the public API with host buffers: H2D of the orbital
-    # block from pinned memory, the step, D2H of the dipole, every step
-    if rank == 0 and args.e2e_steps > 0:
-        host_psi = psi.cpu().pin_memory()
-        host_mu = torch.zeros((1, 3), dtype=torch.float64).pin_memory()
-        torch.cuda.synchronize()
-        a0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            psi.copy_(host_psi, non_blocking=True)
-            ctx.magnus_step_async(psi, t, wl.dt, arr, mu)
-            host_mu.copy_(mu, non_blocking=True)
-            torch.cuda.synchronize()
-            t += wl.dt
-        el = time.perf_counter() - a0
-        line["e2e"] = {"value": round(args.e2e_steps / el, 4), "unit": "steps/s",
-                       "h2d_bytes_per_step": int(psi.numel() * 16), "d2h_bytes_per_step": int(mu.numel() * 8)}
-
-    ctx.close()
     # the same steps with each Lanczos exponential replayed as a captured CUDA graph
     if rank == 0 and args.graph_steps > 0:
-        ctxg = Context(wl, precision=prec, cg_tol=1e-10, cg_max_it=20000, use_graphs=True)
+        ctxg = Context(wl, precision=prec, cg_tol=1e-10, cg_max_it=20000, use_graphs=True,
+                       krylov_substeps=args.substeps)
         psig = psi_start.clone()
         tg = 0.0
         for _ in range(2):                       # eager + capture
@@ -710,7 +770,7 @@ def run_efe(args):
                               "note": "Lanczos loops captured as CUDA graphs (k_max iterations, no host sync)"}
         ctxg.close()
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(workload(args.cells, 0))
+        line["cpu_baseline"] = cpu_baseline(workload(args, 0), budget_s=50.0 if args.workload == "na8" else 150.0)
     if next_rows is not None:
         line["next_rows"] = next_rows
     if rank == 0:
@@ -735,7 +795,7 @@ def run_next_rows(args):
     from paper_2210_14421_gb300 import Context, Octree
     torch.cuda.set_device(0)
     out = {}
-    wl = workload(args.cells, 0)
+    wl = workload(args, 0)
     ctx = Context(wl, cg_tol=1e-10, cg_max_it=20000)
     _, quad = ctx.coords()
     x = quad.cpu().numpy().reshape(-1, 3)
@@ -857,7 +917,7 @@ def run_adjoint(args):
     g.build()
     import efe_workloads as W
     from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED, EFE_PAIR, Context
-    prec = {"mixed": EFE_FP64, "pair": EFE_PAIR, "fp64": EFE_FP64, "tc": EFE_PAIR}[args.precision]
+    prec = {"mixed": EFE_FP64, "pair": EFE_PAIR, "fp64": EFE_FP64, "tc": EFE_PAIR}[args.precision or "pair"]
     n = args.adj_steps
     # k_max 64: the exponentials converge (tol 1e-7), so the forward run is smooth in theta at the
     # level the finite difference needs (with the cap at 48 the atomics' rounding order moves J by ~1e-6)
@@ -897,7 +957,7 @@ def run_adjoint(args):
     line = {"metric": "adjoint gradient cost", "value": round(t_adj / t_fwd, 3), "unit": "x forward",
             "higher_is_better": False,
             "dtype": {"pair": "f32-pair-contraction/f64", "fp64": "f64", "mixed": "f64",
-                      "tc": "f32-pair-contraction/f64"}[args.precision],
+                      "tc": "f32-pair-contraction/f64"}[args.precision or "pair"],
             "data": "synthetic (seeded efe_workloads.organic27)",
             "config": {"workload": "organic-27 (15 C/N/O + 12 H, %d orbitals), %d^3 graded cells degree 4; "
                                    "sine-Gaussian pulse amp 5e-3, omega 0.1, centred in a %d-step segment, dt 0.05"
@@ -922,8 +982,9 @@ def run_apply_only(args):
     g.build()
     from paper_2210_14421_gb300 import EFE_FP64, EFE_MIXED, EFE_PAIR, EFE_TC, Context
     torch.cuda.set_device(0)
+    wl = workload(args, 0)
+    args.precision = default_precision(args, wl)
     prec = {"mixed": EFE_MIXED, "pair": EFE_PAIR, "fp64": EFE_FP64, "tc": EFE_TC}[args.precision]
-    wl = workload(args.cells, 0)
     ctx = Context(wl)
     _, quad = ctx.coords()
     vN = torch.zeros(quad.shape[:2], dtype=torch.float64, device="cuda")

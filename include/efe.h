@@ -156,6 +156,25 @@ typedef struct {
                                  EFE_STEP_EXTRAPOLATED: v_Hxc at the mid-point extrapolated
                                  linearly from the last two steps, one exponential per step (the
                                  first step after set-up, a kick or a reset is predictor-corrector) */
+  int32_t krylov_block;       /* complex columns per Lanczos exponential run (the Krylov basis holds
+                                 k_max + 1 vectors of that many columns): 0 takes as many as fit in
+                                 the device memory free at the first step (all columns when they
+                                 fit); with batch > 1 a block holds whole batch members (rounded
+                                 down, at least one).  Columns are independent in the exponential,
+                                 so blocks give the result of one run; the density, Hartree and
+                                 dipole always see all orbitals.  efe_adjoint_dipole needs all
+                                 columns in one block (else EFE_ERR_ARG). */
+  int32_t krylov_substeps;    /* each exponential exp(-i dt Hbar) of efe_magnus_step (Eq.
+                                 ApproxMagnus) as m sub-steps exp(-i (dt/m) Hbar) of the same
+                                 operator, each a Lanczos run capped at k_max (exact in exact
+                                 arithmetic: the sub-steps commute).  n >= 1: m = n.  0: adaptive,
+                                 for a Krylov cap below what dt needs: an exponential in which a
+                                 column reached k_max with its estimate above krylov_tol is
+                                 computed again from its input with twice the sub-steps (up to
+                                 64); the count carries over to the next exponential and halves
+                                 after one whose largest k stayed at or below 2 k_max / 5.  With
+                                 fixed_k > 0, 0 means 1.  The kick and the adjoint take single
+                                 exponentials. */
 } efe_options;
 
 enum { EFE_XC_PW92 = 0, EFE_XC_PZ81 = 1 };
@@ -173,6 +192,7 @@ typedef struct {
   int32_t krylov_cap_hit;     /* columns that reached k_max */
   int32_t cg_iters;           /* total Hartree PCG iterations in the step */
   double eps_max;             /* largest final Krylov error estimate */
+  int32_t substeps;           /* sub-steps of the step's last exponential (krylov_substeps) */
 } efe_step_info;
 
 /* ---- set-up (Secs. "Enriched finite element discretization", "Spectral finite
@@ -327,7 +347,7 @@ efe_status efe_init_orbitals(efe_ctx* ctx, double* psi_bar_dev, int32_t n_gauss,
  * device memory per call and synchronises `stream`.  Returns EFE_WARN_KRYLOV_CAP
  * (J and grad written) if any exponential stopped at k_max.  Errors: EFE_ERR_ARG
  * (bad sizes, window outside [1, n_steps], n_quad_s outside [1, 64], batch != 1,
- * another functional or step scheme, unsupported field), EFE_ERR_NOMEM,
+ * another functional or step scheme, unsupported field, a density reduction installed), EFE_ERR_NOMEM,
  * EFE_ERR_CUDA.  With the enriched Hartree solve installed (efe_hartree_enriched)
  * the Hartree map and its transpose are the enriched ones. */
 efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_steps, double dt,
@@ -573,6 +593,62 @@ efe_status efe_tuning(efe_ctx* ctx, int32_t precision, int32_t force_variant, in
  * round-to-nearest ties).  *mismatches_host receives the count (0 expected).
  * Synchronises the device. */
 efe_status efe_selftest(int64_t n, int64_t* mismatches_host);
+
+/* Diagnostics (not part of the method): the number of polls after which a progress wait of
+ * the tensor-core apply (the completion of its operand copies and MMAs, and of the other
+ * warps' stages) gives up; 0 restores the default (seconds).  A wait that gives up makes the
+ * kernel stop its work, wait (with the default limit) for the copies and MMAs already in
+ * flight, free its tensor memory and return; the next efe_magnus_step with step info reports
+ * EFE_ERR_TIMEOUT once and the context stays usable (reset its state: the orbitals of that step
+ * are not meaningful).  For tests of the timeout path.  Errors: EFE_ERR_ARG. */
+efe_status efe_set_wait_limit(efe_ctx* ctx, int64_t polls);
+
+/* Orbital (column) partition across processes.  The density rho_q = sum_alpha f_alpha
+ * |psi_alpha(x_q)|^2 (Eq. rho of Section 2) is a sum over orbitals, and the Krylov exponential
+ * of Section 4.2 acts on each orbital by itself, so G processes may each own a subset of the
+ * orbitals (each process sets up its context with its own n_orb, occupations and orbitals)
+ * as long as every density a step forms is summed over all processes before it is used.
+ * efe_set_density_reduce installs that sum: after each density of the context's own orbitals
+ * (the state density of S6 and at the first step, the predictor density of S2, and the one of
+ * efe_density_vxc), and before anything reads it, the step calls
+ *   fn(rho_dev, n, stream, user)
+ * on the host with rho_dev the device float64 [batch][n_cells][n_q] partial density (n values)
+ * and `stream` the step's stream; fn must replace it in place by the sum over all processes,
+ * in order on `stream` (e.g. an NCCL all-reduce on that stream), and return 0, or non-zero for
+ * an error (the step then returns EFE_ERR_CUDA with a message).  LDA, the Hartree solve
+ * (replicated: every process solves the same Poisson problem) and the dipole then read the
+ * summed density, so every process holds the same potentials and dipole.  The call is made
+ * outside the CUDA graphs of the Krylov loops (they never read a density).  fn = NULL removes
+ * it.  Errors: EFE_ERR_ARG. */
+typedef int (*efe_reduce_fn)(double* rho_dev, int64_t n, void* stream, void* user);
+efe_status efe_set_density_reduce(efe_ctx* ctx, efe_reduce_fn fn, void* user);
+
+/* Forward checkpoint and resume (not part of the method; a propagation of thousands of
+ * steps must survive an interrupted job).  efe_checkpoint_save writes psi_bar_dev (device
+ * complex128 [n_dof][n_orb * batch]), t, step and the context's density-derived state (rho_n,
+ * v_H, v_xc at the quadrature points, the nodal Hartree potential, and the previous step's
+ * v_Hxc when the context holds them, and the adaptive Krylov sub-step count) to `path`, through `path`.tmp and a rename; it
+ * synchronises `stream`.  efe_checkpoint_load checks the file (magic, version, the sizes of this
+ * context, payload length, 64-bit FNV-1a checksum) before copying anything, then fills
+ * psi_bar_dev, *t_host, *step_host and restores the state, so the next efe_magnus_step
+ * continues the saved run.  Errors: EFE_ERR_ARG (null pointer, unreadable, corrupt or
+ * truncated file, sizes of another context; message in efe_last_error), EFE_ERR_NOMEM,
+ * EFE_ERR_CUDA. */
+efe_status efe_checkpoint_save(efe_ctx* ctx, const char* path, const double* psi_bar_dev, double t, int64_t step,
+                               void* stream);
+efe_status efe_checkpoint_load(efe_ctx* ctx, const char* path, double* psi_bar_dev, double* t_host,
+                               int64_t* step_host, void* stream);
+/* Host-only forms of the same file (no device, no context): efe_checkpoint_write_host writes
+ * host arrays in the layout above (sizes: n_dof, complex columns, batch, n_cells, n_q, n_h;
+ * rho/vH/vxc/phi all NULL or all given, vprev only with them); efe_checkpoint_inspect validates a
+ * file and returns its sizes, t, step and which parts it holds.  Errors: EFE_ERR_ARG, with the
+ * reason in efe_checkpoint_last_error(). */
+efe_status efe_checkpoint_write_host(const char* path, const int64_t* sizes, double t, int64_t step,
+                                     const double* psi_host, const double* rho_host, const double* vH_host,
+                                     const double* vxc_host, const double* phi_host, const double* vprev_host);
+efe_status efe_checkpoint_inspect(const char* path, int64_t* sizes, double* t, int64_t* step, int32_t* has_state,
+                                  int32_t* has_prev);
+const char* efe_checkpoint_last_error(void);
 
 /* Diagnostics (not part of the method): measured throughput of the float32 and
  * float64 fused-multiply-add pipes of the current device in TFLOP/s (2 flops per

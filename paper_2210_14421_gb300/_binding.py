@@ -29,7 +29,9 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_octree_sizes", "efe_octree_coords", "efe_octree_apply", "efe_octree_constraints",
             "efe_atom_hartree_table", "efe_adaptive_cell_boxes", "efe_octree_poisson",
             "efe_octree_density", "efe_octree_kexp", "efe_octree_interp", "efe_lda_points",
-            "efe_octree_magnus_step", "efe_pipe_peaks"]
+            "efe_octree_magnus_step", "efe_pipe_peaks", "efe_checkpoint_save", "efe_checkpoint_load",
+            "efe_checkpoint_write_host", "efe_checkpoint_inspect", "efe_checkpoint_last_error",
+            "efe_set_wait_limit", "efe_set_density_reduce"]
 
 
 class MeshDesc(C.Structure):
@@ -61,12 +63,13 @@ class Options(C.Structure):
     _fields_ = [("n_orb", C.c_int32), ("batch", C.c_int32), ("occ_host", C.POINTER(C.c_double)),
                 ("krylov_tol", C.c_double), ("k_max", C.c_int32), ("fixed_k", C.c_int32), ("cg_tol", C.c_double),
                 ("cg_max_it", C.c_int32), ("precision", C.c_int32), ("hartree_method", C.c_int32),
-                ("use_graphs", C.c_int32), ("xc", C.c_int32), ("scheme", C.c_int32)]
+                ("use_graphs", C.c_int32), ("xc", C.c_int32), ("scheme", C.c_int32), ("krylov_block", C.c_int32),
+                ("krylov_substeps", C.c_int32)]
 
 
 class StepInfo(C.Structure):
     _fields_ = [("k_pred_max", C.c_int32), ("k_corr_max", C.c_int32), ("krylov_cap_hit", C.c_int32),
-                ("cg_iters", C.c_int32), ("eps_max", C.c_double)]
+                ("cg_iters", C.c_int32), ("eps_max", C.c_double), ("substeps", C.c_int32)]
 
 
 _lib = None
@@ -103,6 +106,15 @@ def lib(path: str = LIB_PATH):
     L.efe_profile.argtypes = [vp, i32]
     L.efe_selftest.argtypes = [i64, C.POINTER(i64)]
     L.efe_pipe_peaks.argtypes = [pdbl, pdbl]
+    L.efe_checkpoint_save.argtypes = [vp, C.c_char_p, vp, dbl, i64, vp]
+    L.efe_checkpoint_load.argtypes = [vp, C.c_char_p, vp, pdbl, C.POINTER(i64), vp]
+    L.efe_checkpoint_write_host.argtypes = [C.c_char_p, C.POINTER(i64), dbl, i64, vp, vp, vp, vp, vp, vp]
+    L.efe_checkpoint_inspect.argtypes = [C.c_char_p, C.POINTER(i64), pdbl, C.POINTER(i64), C.POINTER(i32),
+                                         C.POINTER(i32)]
+    L.efe_set_wait_limit.argtypes = [vp, i64]
+    L.efe_set_density_reduce.argtypes = [vp, ReduceFn, vp]
+    L.efe_checkpoint_last_error.argtypes = []
+    L.efe_checkpoint_last_error.restype = C.c_char_p
     L.efe_tuning.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.efe_profile_read.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl)]
     L.efe_absorption_spectrum.argtypes = [vp, i64, i64, i64, dbl, vp, dbl, vp, i64, dbl, vp, vp]
@@ -131,7 +143,7 @@ def lib(path: str = LIB_PATH):
     L.efe_adaptive_cell_boxes.argtypes = [pdbl, pdbl, pdbl, i32, dbl, dbl, dbl, i32, dbl, i32, C.POINTER(i64), pdbl,
                                           i64]
     for name in EXPORTED:
-        if name not in ("efe_last_error", "efe_octree_last_error"):
+        if name not in ("efe_last_error", "efe_octree_last_error", "efe_checkpoint_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -144,6 +156,26 @@ def selftest(n: int = 1 << 24) -> int:
     if st != EFE_OK:
         raise EfeError(st, lib().efe_last_error(None).decode())
     return m.value
+
+
+def checkpoint_write_host(path, sizes, t, step, psi, rho=None, vH=None, vxc=None, phi=None, vprev=None):
+    """Writes a checkpoint file from host float64 arrays (see efe_checkpoint_write_host)."""
+    arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (psi, rho, vH, vxc, phi, vprev)]
+    sz = (C.c_int64 * 6)(*[int(x) for x in sizes])
+    ptrs = [None if a is None else a.ctypes.data_as(C.c_void_p) for a in arrs]
+    st = lib().efe_checkpoint_write_host(str(path).encode(), sz, float(t), int(step), *ptrs)
+    if st != EFE_OK:
+        raise EfeError(st, lib().efe_checkpoint_last_error().decode())
+
+
+def checkpoint_inspect(path):
+    """(sizes, t, step, has_state, has_prev) of a valid checkpoint file; raises EfeError otherwise."""
+    sz = (C.c_int64 * 6)()
+    t, step, hs, hp = C.c_double(), C.c_int64(), C.c_int32(), C.c_int32()
+    st = lib().efe_checkpoint_inspect(str(path).encode(), sz, C.byref(t), C.byref(step), C.byref(hs), C.byref(hp))
+    if st != EFE_OK:
+        raise EfeError(st, lib().efe_checkpoint_last_error().decode())
+    return tuple(sz), t.value, step.value, bool(hs.value), bool(hp.value)
 
 
 def pipe_peaks():
@@ -163,6 +195,18 @@ class EfeError(RuntimeError):
 
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
+
+
+# int fn(double* rho_dev, int64_t n, void* stream, void* user): the density reduction callback
+ReduceFn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p)
+
+
+class _DeviceArray:
+    """A float64 vector in device memory the library owns, seen by torch without a copy."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
 
 
 def _stream():
@@ -218,7 +262,8 @@ class Context:
 
     def __init__(self, wl, precision: int = EFE_FP64, krylov_tol=None, k_max=None, fixed_k: int = 0,
                  cg_tol: float = 1e-12, cg_max_it: int = 5000, hartree_method: int = EFE_HARTREE_FDM,
-                 use_graphs: bool = False, xc: int = EFE_XC_PW92, scheme: int = EFE_STEP_PC):
+                 use_graphs: bool = False, xc: int = EFE_XC_PW92, scheme: int = EFE_STEP_PC,
+                 krylov_block: int = 0, krylov_substeps: int = 1):
         L = lib()
         self.wl = wl
         self._keep = []
@@ -241,7 +286,8 @@ class Context:
         opts = Options(int(wl.n_orb), int(wl.batch), _dptr(occ),
                        float(wl.krylov_tol if krylov_tol is None else krylov_tol),
                        int(wl.k_max if k_max is None else k_max), int(fixed_k), float(cg_tol), int(cg_max_it),
-                       int(precision), int(hartree_method), int(bool(use_graphs)), int(xc), int(scheme))
+                       int(precision), int(hartree_method), int(bool(use_graphs)), int(xc), int(scheme),
+                       int(krylov_block), int(krylov_substeps))
         h = C.c_void_p()
         st = L.efe_setup(C.byref(mesh), atoms, na, C.byref(enr), C.byref(opts), C.byref(h))
         if st != EFE_OK:
@@ -255,6 +301,9 @@ class Context:
 
     def _check(self, st, allow=(EFE_OK,)):
         if st not in allow:
+            exc, self._reduce_exc = getattr(self, "_reduce_exc", None), None
+            if exc is not None:
+                raise exc
             raise EfeError(st, lib().efe_last_error(self.h).decode())
         return st
 
@@ -305,7 +354,7 @@ class Context:
         st = lib().efe_magnus_step(self.h, _ptr(psi), float(t), float(dt), arr, _ptr(mu), C.byref(info), _stream())
         self._check(st, allow=(EFE_OK, EFE_WARN_KRYLOV_CAP))
         return {"k_pred": info.k_pred_max, "k_corr": info.k_corr_max, "cap": info.krylov_cap_hit,
-                "cg_iters": info.cg_iters, "eps_max": info.eps_max, "status": st}
+                "cg_iters": info.cg_iters, "eps_max": info.eps_max, "substeps": info.substeps, "status": st}
 
     def magnus_step_async(self, psi, t, dt, fields_arr, mu=None):
         """Same as magnus_step with a prepared field array and no host-visible info."""
@@ -314,6 +363,46 @@ class Context:
 
     def reset_state(self):
         self._check(lib().efe_reset_state(self.h))
+
+    def set_wait_limit(self, polls: int):
+        """Polls before a tensor-core progress wait gives up (0: the default); for timeout tests."""
+        self._check(lib().efe_set_wait_limit(self.h, int(polls)))
+
+    def set_density_reduce(self, fn):
+        """Orbital partition across processes: fn(rho) must replace the device float64 tensor
+        rho (this context's partial density, [batch * n_cells * n_q]) by its sum over all
+        processes, e.g. ``torch.distributed.all_reduce``; it runs with the step's stream as
+        torch's current stream.  None removes it.  An exception raised by fn ends the step and
+        is raised again by the call that ran it."""
+        if fn is None:
+            self._reduce_cb = None
+            self._check(lib().efe_set_density_reduce(self.h, ReduceFn(), None))
+            return
+        import torch
+
+        def cb(ptr, n, stream, _user):
+            try:
+                rho = torch.as_tensor(_DeviceArray(ptr, n), device="cuda")
+                ext = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+                with torch.cuda.stream(ext):
+                    fn(rho)
+                return 0
+            except BaseException as e:   # noqa: BLE001 -- handed back to the caller of the step
+                self._reduce_exc = e
+                return 1
+
+        self._reduce_cb = ReduceFn(cb)   # kept alive as long as the library may call it
+        self._check(lib().efe_set_density_reduce(self.h, self._reduce_cb, None))
+
+    def checkpoint_save(self, path, psi, t, step):
+        self._check(lib().efe_checkpoint_save(self.h, str(path).encode(), _ptr(psi), float(t), int(step), _stream()))
+
+    def checkpoint_load(self, path, psi):
+        """Restores psi (device, in place) and the state; returns (t, step)."""
+        t, step = C.c_double(), C.c_int64()
+        self._check(lib().efe_checkpoint_load(self.h, str(path).encode(), _ptr(psi), C.byref(t), C.byref(step),
+                                              _stream()))
+        return t.value, step.value
 
     def density_vxc(self, psi, rho, vxc=None, exc=None):
         self._check(lib().efe_density_vxc(self.h, _ptr(psi), _ptr(rho), _ptr(vxc), _ptr(exc), _stream()))

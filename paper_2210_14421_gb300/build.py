@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libefe.so")
 SOURCES = ["api.cu", "host_math.cu", "k_setup.cu", "k_apply.cu", "k_tc.cu", "k_vector.cu", "k_poisson.cu", "adjoint.cu",
-           "spectra.cu", "k_electro.cu", "k_octree.cu", "probe.cu"]
+           "spectra.cu", "k_electro.cu", "k_octree.cu", "probe.cu", "checkpoint.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

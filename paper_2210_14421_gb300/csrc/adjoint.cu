@@ -484,6 +484,12 @@ efe_status adjoint_dipole(Ctx& c, const double* psi0, int n_steps, double dt, co
   efe_status st = EFE_OK;
   try {
     ck(ensure_ws(c, c.n_orb, c.n_orb));
+    ck(ensure_krylov(c));
+    if (c.kblock < c.n_orb) {   // the reverse sweep recombines one Krylov basis of every column
+      c.err = "efe_adjoint_dipole needs the Krylov basis of all orbitals at once (krylov_block too small for them)";
+      c.use_graphs = graphs;
+      return EFE_ERR_ARG;
+    }
     Sweep sw(c, s, n_s);
     const long long blk = sw.blk();
     const int n_ck = (n_steps + K - 1) / K;

@@ -94,21 +94,53 @@ static cudaError_t dalloc(T*& p, size_t n) {
   return cudaMalloc((void**)&p, sizeof(T) * n);
 }
 
-// Workspaces for C complex columns (Krylov basis, scratch, scalars).
+// Workspaces for C complex columns (predictor block, enrichment scratch, Lanczos scalars).  The
+// Krylov basis is allocated by ensure_krylov at the first exponential.
 efe_status ensure_ws(Ctx& c, long long C, long long ld) {
   const long long need_ld = std::max(C, ld);
-  if (c.ws_cols >= need_ld && c.d_Q) return EFE_OK;
+  if (c.ws_cols >= need_ld) return EFE_OK;
   const long long n = c.n_dof;
   c.ws_gen += 1;   // captured graphs refer to the old buffers
-  TRY_CUDA(c, dalloc(c.d_Q, (size_t)(c.k_max + 1) * n * 2 * need_ld), "allocating the Krylov basis");
+  dfree(c.d_Q);
+  c.kblock = 0;
   TRY_CUDA(c, dalloc(c.d_psi_p, (size_t)n * 2 * need_ld), "allocating the predictor block");
-  TRY_CUDA(c, dalloc(c.d_lz, (size_t)(6 * kMaxK + 8) * need_ld), "allocating Lanczos scalars");
-  TRY_CUDA(c, dalloc(c.d_lzi, (size_t)3 * need_ld + 8), "allocating Lanczos state");
   TRY_CUDA(c, dalloc(c.d_xE, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
   TRY_CUDA(c, dalloc(c.d_xE32, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
   TRY_CUDA(c, dalloc(c.d_xE2, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
   TRY_CUDA(c, dalloc(c.d_yE, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
+  TRY_CUDA(c, dalloc(c.d_lz, (size_t)(6 * kMaxK + 8) * need_ld), "allocating Lanczos scalars");
+  TRY_CUDA(c, dalloc(c.d_lzi, (size_t)3 * need_ld + 8), "allocating Lanczos state");
   c.ws_cols = need_ld;
+  return EFE_OK;
+}
+
+// The Krylov basis: k_max + 1 vectors of c.kblock complex columns, all n_orb * batch when they fit
+// in the free device memory (or the krylov_block option), else the largest block that does (whole
+// batch members when batch > 1); run_kexp_cols then runs the columns block by block.  The free
+// memory left aside covers the densities and operator rebuilds and, for EFE_TC before its first
+// build, the tensor-core operator; the basis takes at most three quarters of the rest.
+efe_status ensure_krylov(Ctx& c) {
+  if (c.d_Q && c.kblock > 0) return EFE_OK;
+  const long long C = (long long)c.n_orb * c.batch;
+  const size_t per_col = sizeof(double) * (size_t)(c.k_max + 1) * c.n_dof * 2;
+  long long blk = C;
+  if (c.kblock_opt > 0) {
+    blk = std::min<long long>(C, c.kblock_opt);
+  } else {
+    size_t free_b = 0, total_b = 0;
+    TRY_CUDA(c, cudaMemGetInfo(&free_b, &total_b), "querying device memory");
+    size_t reserve = (size_t)8 << 30;
+    if (c.precision == EFE_TC && !c.tc_on)
+      reserve += (size_t)c.batch * ((size_t)c.nc * (4 * 128 * 128 * 2 + 2 * 128 * 4) +
+                                    ((size_t)c.n_pairs + 16 * (size_t)c.nc) * (2048 + 4));
+    // at most three quarters of what is left: the caller's own tensors come after the first step
+    const long long fit = free_b > reserve ? (long long)((free_b - reserve) / 4 * 3 / per_col) : 1;
+    blk = std::max<long long>(1, std::min(C, fit));
+  }
+  if (c.batch > 1 && blk < C) blk = std::max<long long>(1, blk / c.n_orb) * c.n_orb;   // whole members
+  c.ws_gen += 1;
+  TRY_CUDA(c, dalloc(c.d_Q, per_col / sizeof(double) * (size_t)blk), "allocating the Krylov basis");
+  c.kblock = blk;
   return EFE_OK;
 }
 
@@ -190,6 +222,8 @@ static bool validate(const efe_mesh_desc* mesh, const efe_atom* atoms, int n_ato
   }
   if (o->xc != EFE_XC_PW92 && o->xc != EFE_XC_PZ81) { why = "unknown xc"; return false; }
   if (o->scheme != EFE_STEP_PC && o->scheme != EFE_STEP_EXTRAPOLATED) { why = "unknown step scheme"; return false; }
+  if (o->krylov_block < 0) { why = "krylov_block must be >= 0"; return false; }
+  if (o->krylov_substeps < 0 || o->krylov_substeps > 64) { why = "krylov_substeps must be in [0, 64]"; return false; }
   if (o->hartree_method != EFE_HARTREE_FDM && o->hartree_method != EFE_HARTREE_PCG) {
     why = "unknown Hartree method";
     return false;
@@ -238,6 +272,9 @@ static efe_status setup_impl(Ctx& c, const efe_mesh_desc* mesh, const efe_atom* 
   c.xc = o->xc;
   c.scheme = o->scheme;
   c.use_graphs = o->use_graphs != 0;
+  c.kblock_opt = o->krylov_block;
+  c.substeps_opt = o->krylov_substeps;
+  c.substeps_cur = 1;
 
   // reference tables
   double xi[kMaxP1], wl[kMaxP1], xg[kMaxNQ1], wg[kMaxNQ1];
@@ -461,15 +498,69 @@ static void field_vectors(const Ctx& c, const efe_field* fields, double t, std::
   }
 }
 
+// the partial density of this process's orbitals -> the sum over all processes (orbital partition)
+static efe_status reduce_rho(Ctx& c, double* rho, cudaStream_t s) {
+  if (!c.rho_reduce) return EFE_OK;
+  const long long n = (long long)c.batch * c.nc * c.nq;
+  const int rc = c.rho_reduce(rho, (int64_t)n, (void*)s, c.rho_reduce_user);
+  if (rc != 0) {
+    c.err = "the density reduction across processes failed (code " + std::to_string(rc) + ")";
+    return EFE_ERR_CUDA;
+  }
+  return EFE_OK;
+}
+
 // rho, v_xc, v_H of psi into the context state
 static efe_status compute_state(Ctx& c, const double* psi, int* cg_its, cudaStream_t s) {
   TRY_CUDA(c, launch_density(c, psi, c.d_rho, s), "density");
+  {
+    const efe_status r = reduce_rho(c, c.d_rho, s);
+    if (r != EFE_OK) return r;
+  }
   TRY_CUDA(c, launch_lda(c, c.d_rho, c.d_vxc, nullptr, (long long)c.batch * c.nc * c.nq, s), "LDA");
   int its = 0;
   efe_status st = run_hartree(c, c.d_rho, c.d_vH, c.cg_tol, c.cg_max_it, &its, s);
   if (cg_its) *cg_its += its;
   if (st == EFE_OK) c.state_valid = true;
   return st;
+}
+
+// out = exp(-i dt Hbar) in as m sub-steps exp(-i (dt/m) Hbar), each a Lanczos run capped at
+// k_max (the operator is the same for all of them, so they compose exactly).  Adaptive
+// (krylov_substeps = 0, no fixed k): a pass in which a column reached k_max with its estimate
+// above the tolerance is repeated from `in` with twice the sub-steps (in and out must differ),
+// up to 64; the count is kept for the next exponential, halved after one whose largest k
+// stayed at or below 2 k_max / 5.  Statistics: the largest k, the cap hits and the largest
+// estimate of the pass that was kept.
+static efe_status kexp_substeps(Ctx& c, const double* in, double* out, double dt, int* kmax, int* caps, double* eps,
+                                int* m_used, cudaStream_t s, bool stats) {
+  constexpr int kMaxSub = 64;
+  const long long C = (long long)c.n_orb * c.batch;
+  const bool adaptive = c.substeps_opt == 0 && c.fixed_k <= 0 && in != out;
+  int m = adaptive ? c.substeps_cur : (c.substeps_opt > 0 ? c.substeps_opt : 1);
+  for (;;) {
+    std::vector<double> dts((size_t)C, dt / m);
+    int km = 0, cp = 0;
+    double em = 0.0;
+    for (int q = 0; q < m; ++q) {
+      int k = 0, p = 0;
+      double e = 0.0;
+      TRY_CUDA(c, run_kexp_cols(c, q == 0 ? in : out, out, dts.data(), c.precision, &k, &p, &e, s, stats || adaptive),
+               "Krylov exponential");
+      km = std::max(km, k);
+      cp += p;
+      em = std::max(em, e);
+    }
+    if (!adaptive || cp == 0 || m >= kMaxSub) {
+      if (adaptive) c.substeps_cur = (m > 1 && 5 * km <= 2 * c.k_max) ? m / 2 : m;
+      *kmax = km;
+      *caps = cp;
+      *eps = em;
+      *m_used = m;
+      return EFE_OK;
+    }
+    m *= 2;
+  }
 }
 
 static efe_status magnus_impl(Ctx& c, double* psi, double t, double dt, const efe_field* fields, double* mu,
@@ -485,8 +576,7 @@ static efe_status magnus_impl(Ctx& c, double* psi, double t, double dt, const ef
   }
   std::vector<double> E;
   field_vectors(c, fields, t + 0.5 * dt, E);
-  std::vector<double> dts((size_t)C, dt);
-  int k1 = 0, cap1 = 0, k2 = 0, cap2 = 0;
+  int k1 = 0, cap1 = 0, k2 = 0, cap2 = 0, m1 = 1, m2 = 1;
   double e1 = 0.0, e2 = 0.0;
   const bool stats = info != nullptr;
   const long long nqb = (long long)c.batch * c.nc * c.nq;
@@ -502,9 +592,12 @@ static efe_status magnus_impl(Ctx& c, double* psi, double t, double dt, const ef
     TRY_CUDA(c, launch_potential_sum(c, c.d_vH, c.d_vxc, E.data(), true, c.d_v, s), "potential");
     st = build_op(c, c.d_v, c.batch, 1.0, s);
     if (st != EFE_OK) return st;
-    TRY_CUDA(c, run_kexp_cols(c, psi, c.d_psi_p, dts.data(), c.precision, &k1, &cap1, &e1, s, stats), "predictor");
+    st = kexp_substeps(c, psi, c.d_psi_p, dt, &k1, &cap1, &e1, &m1, s, stats);
+    if (st != EFE_OK) return st;
     // S2, S3: rho_mid = (rho_n + rho^p) / 2
     TRY_CUDA(c, launch_density(c, c.d_psi_p, c.d_rho2, s), "density");
+    st = reduce_rho(c, c.d_rho2, s);
+    if (st != EFE_OK) return st;
     TRY_CUDA(c, launch_axpby(c.d_rho2, c.d_rho, c.d_rho2, 0.5, 0.5, nqb, s), "mid-point density");
     // S4: v_mid
     TRY_CUDA(c, launch_lda(c, c.d_rho2, c.d_vxc, nullptr, nqb, s), "LDA");
@@ -516,8 +609,17 @@ static efe_status magnus_impl(Ctx& c, double* psi, double t, double dt, const ef
   }
   st = build_op(c, c.d_v, c.batch, 1.0, s);
   if (st != EFE_OK) return st;
-  // S5: corrector from psi_n, written in place
-  TRY_CUDA(c, run_kexp_cols(c, psi, psi, dts.data(), c.precision, &k2, &cap2, &e2, s, stats), "corrector");
+  // S5: corrector from psi_n, written in place (adaptive sub-steps: into the predictor's buffer,
+  // free by now, so that a pass can be repeated from psi_n, then copied back)
+  if (c.substeps_opt == 0 && c.fixed_k <= 0) {
+    st = kexp_substeps(c, psi, c.d_psi_p, dt, &k2, &cap2, &e2, &m2, s, stats);
+    if (st != EFE_OK) return st;
+    TRY_CUDA(c, cudaMemcpyAsync(psi, c.d_psi_p, sizeof(double) * 2 * (size_t)c.n_dof * C, cudaMemcpyDeviceToDevice, s),
+             "corrector");
+  } else {
+    st = kexp_substeps(c, psi, psi, dt, &k2, &cap2, &e2, &m2, s, stats);
+    if (st != EFE_OK) return st;
+  }
   // S6: state of step n+1 and the dipole
   c.state_valid = false;
   st = compute_state(c, psi, &cg_its, s);
@@ -540,6 +642,7 @@ static efe_status magnus_impl(Ctx& c, double* psi, double t, double dt, const ef
     info->krylov_cap_hit = cap1 + cap2;
     info->cg_iters = cg_its;
     info->eps_max = std::max(e1, e2);
+    info->substeps = m2;
   }
   if (warn == EFE_OK && cap1 + cap2 > 0) warn = EFE_WARN_KRYLOV_CAP;
   return warn;
@@ -654,6 +757,7 @@ efe_status efe_reset_state(efe_ctx* ctx) {
   CHECK_CTX(ctx);
   ctx->c.state_valid = false;
   ctx->c.has_prev = false;
+  ctx->c.substeps_cur = 1;
   return EFE_OK;
 }
 
@@ -666,6 +770,8 @@ efe_status efe_density_vxc(efe_ctx* ctx, const double* psi_bar_dev, double* rho_
   if (st != EFE_OK) return st;
   cudaStream_t s = as_stream(stream);
   TRY_CUDA(c, launch_density(c, psi_bar_dev, rho_dev, s), "density");
+  st = reduce_rho(c, rho_dev, s);
+  if (st != EFE_OK) return st;
   if (vxc_dev || exc_dev)
     TRY_CUDA(c, launch_lda(c, rho_dev, vxc_dev, exc_dev, (long long)c.batch * c.nc * c.nq, s), "LDA");
   return EFE_OK;
@@ -778,6 +884,10 @@ efe_status efe_adjoint_dipole(efe_ctx* ctx, const double* psi0_dev, int32_t n_st
     c.err = "efe_adjoint_dipole needs a context with batch = 1";
     return EFE_ERR_ARG;
   }
+  if (c.rho_reduce) {
+    c.err = "efe_adjoint_dipole needs all orbitals in one context (no density reduction installed)";
+    return EFE_ERR_ARG;
+  }
   if (c.xc != EFE_XC_PW92 || c.scheme != EFE_STEP_PC) {
     c.err = "efe_adjoint_dipole differentiates the predictor-corrector step with the PW92 functional";
     return EFE_ERR_ARG;
@@ -833,6 +943,23 @@ efe_status efe_selftest(int64_t n, int64_t* mismatches_host) {
     return EFE_ERR_CUDA;
   }
   *mismatches_host = m;
+  return EFE_OK;
+}
+
+efe_status efe_set_density_reduce(efe_ctx* ctx, efe_reduce_fn fn, void* user) {
+  CHECK_CTX(ctx);
+  ctx->c.rho_reduce = fn;
+  ctx->c.rho_reduce_user = fn ? user : nullptr;
+  return EFE_OK;
+}
+
+efe_status efe_set_wait_limit(efe_ctx* ctx, int64_t polls) {
+  CHECK_CTX(ctx);
+  if (polls < 0 || polls > 0xFFFFFFFFLL) {
+    ctx->c.err = "efe_set_wait_limit: polls must be in [0, 2^32)";
+    return EFE_ERR_ARG;
+  }
+  ctx->c.tc_wait_limit = (uint32_t)polls;
   return EFE_OK;
 }
 

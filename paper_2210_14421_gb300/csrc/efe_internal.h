@@ -90,11 +90,16 @@ struct TcState {
   int batch = 0;                  // members the slices are allocated for
   unsigned char* H = nullptr;     // [batch][nc][4 slices][128 x 128 bf16]
   int* rexp = nullptr;            // [batch][nc][128] row exponents of H_c
-  int* rexpE = nullptr;           // [batch][nc][128] row exponents of E_c
+  int* rexpE = nullptr;           // [batch][n_items][128] row exponents of E_c (per item)
   unsigned char* E = nullptr;     // [batch][e_total][2048 B]: per cell, [E_c slice i | E_c^T slice i], i = 0..3
   int* hexp = nullptr;            // [batch][n_pairs] row exponents of E_c^T
-  long long* eoff = nullptr;      // [nc + 1] prefix sums of the padded function counts
+  long long* eoff = nullptr;      // [n_items + 1] prefix sums of the padded function counts
   long long e_total = 0;
+  // work items: a cell coupled to more enrichment functions than one pass takes is split into
+  // several items (the first carries H_c); [4][n_items]: cell, first pair, pairs, flags
+  int n_items = 0;
+  int* items = nullptr;
+  int* first_item = nullptr;      // [nc + 1] first item of each cell
   int* err = nullptr;             // set by a tensor-core wait that gave up
   int n_sm = 0;                   // SMs of the context's device (persistent grid)
 };
@@ -211,6 +216,13 @@ struct Ctx {
   std::vector<KexpGraph> graph_seen;   // keys run eagerly once (tuning) before capture
   long long ws_gen = 0;                // bumped whenever workspaces or operator buffers move
   bool use_graphs = false;
+  int kblock_opt = 0;          // krylov_block option (0: automatic)
+  int substeps_opt = 1;        // krylov_substeps option (0: adaptive)
+  int substeps_cur = 1;        // adaptive: sub-steps of the next exponential
+  uint32_t tc_wait_limit = 0;  // polls of the tensor-core apply's progress waits (0: the default)
+  efe_reduce_fn rho_reduce = nullptr;  // sum of the partial densities over processes (orbital partition)
+  void* rho_reduce_user = nullptr;
+  long long kblock = 0;        // complex columns per Lanczos run (the Krylov basis width)
   cudaStream_t cap_stream = nullptr;
   int tile_choice[3] = {-1, -1, -1};
   long long tile_cols[3] = {-1, -1, -1};
@@ -321,6 +333,7 @@ cudaError_t hartree_enriched_vt(Ctx& c, const double* gw, double* out, double* s
                                 double* s5, double* s6, cudaStream_t s);
 // context workspaces for C complex columns of leading dimension ld; the operator of v (api.cu)
 efe_status ensure_ws(Ctx& c, long long C, long long ld);
+efe_status ensure_krylov(Ctx& c);   // the Krylov basis (first exponential)
 efe_status build_op(Ctx& c, const double* v, int batch, double kin, cudaStream_t s);
 // reverse sweep of the dipole objective through n_steps Magnus steps (adjoint.cu)
 efe_status adjoint_dipole(Ctx& c, const double* psi0, int n_steps, double dt, const efe_field& f, const double dir[3],

@@ -16,34 +16,41 @@
 // (at most 2 x 128 terms on a grid of 2^-14 resp. 2^-22, below 2^24 grid steps).
 // Pairs summing to 2, 3 or 4 go to a third accumulator, whose binary32 rounding is
 // ~2^-39 of the scales; pairs summing to 5 or 6 are dropped (each below 2^-38 of the
-// scales).  A product is 2^(row + column exponent) (acc0 + acc1 + acc2), formed in
-// 64-bit fixed point and float64 on the integer pipes.  Per element of y the error is
-// a few 2^-31 of sum_k |A_ik| max_k |x_k| for each of the products separately.
+// scales).  A product is 2^(row + column exponent) (acc0 + acc1 + acc2); the three
+// binary32 partial sums are added as an unevaluated float pair (error-free TwoSum
+// chains) and the pair is turned into one float64 on the integer pipes.  Per element
+// of y the error is a few 2^-31 of sum_k |A_ik| max_k |x_k| for each product apart.
 //
 // Separate scales: in cells near a nucleus the enrichment part of an orbital is many
 // orders of magnitude larger than its classical part, so x^C and x^E have their own
 // column exponents (and E_c its own row exponents).  The products therefore have
 // their own accumulators: first the E pass (E_c x^E and E_c^T x^C), whose classical
-// part is carried in registers as 64-bit fixed point, then the H pass (H_c x^C), added
-// to it on the integer pipes before the one float64 value per output is formed.
+// part is parked in tensor memory as a float pair, then the H pass (H_c x^C); the two
+// float pairs are brought to the larger of the two exponents and summed before the
+// one float64 value per output is formed.
 //
 // Layout: the A operands (H_c slices, E_c and E_c^T slices) are written when the
 // operator is built, directly in the shared-memory image the MMA reads (no-swizzle
-// K-major core matrices, see tc.cuh), so the apply streams them into a two-slot ring
-// with bulk asynchronous copies (cp.async.bulk, completion counted on an mbarrier).
+// K-major core matrices, see tc.cuh), with the Loewdin scaling D = mask / sqrt(M)
+// folded into both sides of H_c and into E_c, so the apply reads x_bar as stored.
+// The A images stream into a two-slot ring with bulk asynchronous copies
+// (cp.async.bulk, completion counted on an mbarrier).  Cells with more than 48
+// enrichment functions are split into work items of at most 48 functions (the first
+// one carries H_c), and an apply over more than 96 columns runs in column blocks.
 // The apply is persistent, one CTA per SM, warp-specialised:
-//   16 work warps: gather x_bar^C (rows of the cell's nodes) and x^E, x^C = D x_bar^C
-//     in float32 pairs, per-column exponents, digit extraction into 4 bf16 slices
-//     (shared memory); after the MMAs the epilogues: accumulators -> fixed point ->
-//     float64, E_c^T x^C to y^E (atomic adds), y_c staged in shared memory and
-//     scattered row by row (coalesced atomic adds; plain stores for the cell's
-//     interior nodes, which no other cell touches);
-//   1 issuer warp: one thread streams the A slices (E pass: E_c slice i with E_c^T
-//     slice i; H pass: H_c slice i) and issues the MMAs of the slice pairs (i, j),
-//     i + j <= 4, committing to mbarriers that free ring slots and release the
-//     epilogues.  Every wait is bounded: a wait that gives up sets an error flag the
-//     host reads (EFE_ERR_TIMEOUT), waits (bounded) for the copies and MMAs in
+//   16 work warps: gather x_bar^C (rows of the cell's nodes; the next cell's rows are
+//     prefetched into L2) and x^E, per-column exponents, digit extraction into 4
+//     bf16 slices (shared memory); after the MMAs the epilogues: accumulators ->
+//     float pair -> float64, E_c^T x^C to y^E (atomic adds), y_c staged in shared
+//     memory and scattered row by row (coalesced atomic adds; plain stores for the
+//     interior nodes of a cell that is its own only work item);
+//   1 issuer warp: streams the A slices (E pass: E_c slice i with E_c^T slice i;
+//     H pass: H_c slice i) and issues, from one lane, the MMAs of the slice pairs
+//     (i, j), i + j <= 4, committing to mbarriers that free ring slots and release
+//     the epilogues.  Every wait is bounded: a wait that gives up sets an error flag
+//     the host reads (EFE_ERR_TIMEOUT), waits (bounded) for the copies and MMAs in
 //     flight and frees the tensor memory before returning.
+#include <algorithm>
 #include <cstdio>
 #include <vector>
 
@@ -101,6 +108,19 @@ static_assert(kApplySmem <= 232448, "apply kernel exceeds the shared memory of a
 // mbarrier indices
 enum { kBFull0 = 0, kBEmpty0 = kNSlot, kBXready = 2 * kNSlot, kBAccE, kBDrainedE, kBAccH, kBFin };
 static_assert(kBFin < 10, "mbarrier block too small");
+
+// Work items of the apply: a cell with more than kMaxKE enrichment functions is processed as
+// several items of at most kMaxKE functions each; the first item of a cell also carries H_c.
+struct TcItems {
+  int n;                   // items per batch member
+  const int* cell;         // [n] the item's cell
+  const int* p0;           // [n] its first cell-function pair (global pair index)
+  const int* np;           // [n] its pairs
+  const int* flags;        // [n] bit 0: carries H_c; bit 1: the only item of its cell
+  const long long* eoff;   // [n + 1] offsets of the items' enrichment data (units of 2048 bytes)
+  const int* first;        // [nc + 1] first item of each cell
+};
+constexpr int kItemH = 1, kItemSolo = 2;
 
 __device__ __forceinline__ long long q31(double v, int e) { return e == kZero ? 0LL : tc::q31_bits(v, e); }
 __device__ __forceinline__ int exp_of_max(double mx) {
@@ -161,7 +181,7 @@ template <int P1, int NQ1>
 __global__ void __launch_bounds__(256)
 k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const double* __restrict__ W64, double kin,
            const int* __restrict__ pair_start, const double* __restrict__ E64, long long n_pairs,
-           const double* __restrict__ Dsc, const long long* __restrict__ eoff, long long e_total,
+           const double* __restrict__ Dsc, const TcItems items, long long e_total,
            unsigned char* __restrict__ tcH, int* __restrict__ tcRexpH, int* __restrict__ tcRexpE,
            unsigned char* __restrict__ tcE, int* __restrict__ tcHexp) {
   constexpr int NN = P1 * P1 * P1;
@@ -215,30 +235,26 @@ k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const dou
     acc += kx * Ka * Mb * Mc + ky * Ma * Kb * Mc + kz * Ma * Mb * Kc;
     H[it] = Dn[i] * acc * Dn[j];   // both sides of the Loewdin scaling folded in: the apply gathers x_bar
   }
-  int p0 = 0, np = 0;
+  int p0c = 0, npc = 0;
   if (pair_start) {
-    p0 = pair_start[c];
-    np = pair_start[c + 1] - p0;
+    p0c = pair_start[c];
+    npc = pair_start[c + 1] - p0c;
   }
-  const double* Ec = E64 + ((long long)m * n_pairs + p0) * NN;
   __syncthreads();
-  // row exponents: H_c rows and E_c rows each their own
+  // H_c row exponents
   for (int i = tid; i < 128; i += blockDim.x) {
-    double mh = 0.0, me = 0.0;
-    if (i < NN) {
+    double mh = 0.0;
+    if (i < NN)
       for (int j = 0; j < NN; ++j) mh = fmax(mh, fabs(H[i * NN + j]));
-      for (int f = 0; f < np; ++f) me = fmax(me, fabs(Dn[i] * Ec[(long long)f * NN + i]));
-    }
     rexpH[i] = i < NN ? exp_of_max(mh) : kZero;
-    rexpE[i] = i < NN ? exp_of_max(me) : kZero;
     tcRexpH[((long long)m * mesh.nc + c) * 128 + i] = rexpH[i];
-    tcRexpE[((long long)m * mesh.nc + c) * 128 + i] = rexpE[i];
   }
-  for (int f = tid; f < np; f += blockDim.x) {
+  // E_c^T row exponents (per cell-function pair)
+  for (int f = tid; f < npc; f += blockDim.x) {
+    const double* Ef = E64 + ((long long)m * n_pairs + p0c + f) * NN;
     double mx = 0.0;
-    for (int i = 0; i < NN; ++i) mx = fmax(mx, fabs(Ec[(long long)f * NN + i] * Dn[i]));
-    hexp[f] = exp_of_max(mx);
-    tcHexp[(long long)m * n_pairs + p0 + f] = hexp[f];
+    for (int i = 0; i < NN; ++i) mx = fmax(mx, fabs(Ef[i] * Dn[i]));
+    tcHexp[(long long)m * n_pairs + p0c + f] = exp_of_max(mx);
   }
   __syncthreads();
   // H_c slices: item = one 16-byte core-matrix row (i, 8 consecutive k), consecutive
@@ -255,35 +271,51 @@ k_tc_build(const __grid_constant__ RefTables tab, const MeshView mesh, const dou
     }
     store_slices8(v, rexpH[i], Hc + tc::kmajor_offset(i, kc * 8, 2048), kSliceBytes);
   }
-  if (np > 0) {
-    const int KEp = (np + 15) & ~15;
-    const long long eb = 256LL * KEp;   // bytes of one 128 x KEp slice
-    unsigned char* Eb = tcE + ((long long)m * e_total + eoff[c]) * 2048;
-    // E_c (rows i, K = f), rows scaled by rexpE; slice s at Eb + 2 s eb
-    const int nfc = KEp / 8;
-    for (int it = tid; it < 128 * nfc; it += blockDim.x) {
-      const int i8 = it & 7, fc = (it >> 3) % nfc, ig = (it >> 3) / nfc;
-      const int i = ig * 8 + i8;
-      double v[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int f = fc * 8 + t;
-        v[t] = (i < NN && f < np) ? Dn[i] * Ec[(long long)f * NN + i] : 0.0;
+  // the enrichment data of each of the cell's work items
+  if (npc > 0) {
+    for (int k = items.first[c]; k < items.first[c + 1]; ++k) {
+      const int p0 = items.p0[k], np = items.np[k];
+      const double* Ec = E64 + ((long long)m * n_pairs + p0) * NN;
+      const int* hx = tcHexp + (long long)m * n_pairs + p0;
+      __syncthreads();
+      for (int i = tid; i < 128; i += blockDim.x) {   // E_c rows of this item: their own exponents
+        double me = 0.0;
+        if (i < NN)
+          for (int f = 0; f < np; ++f) me = fmax(me, fabs(Dn[i] * Ec[(long long)f * NN + i]));
+        rexpE[i] = i < NN ? exp_of_max(me) : kZero;
+        tcRexpE[((long long)m * items.n + k) * 128 + i] = rexpE[i];
       }
-      store_slices8(v, rexpE[i], Eb + tc::kmajor_offset(i, fc * 8, 16 * KEp), 2 * eb);
-    }
-    // E_c^T D (rows f, K = i; the input side of the Loewdin scaling folded in), rows scaled by
-    // hexp; slice s at Eb + (2 s + 1) eb
-    for (int it = tid; it < KEp * (kK / 8); it += blockDim.x) {
-      const int f8 = it & 7, ic = (it >> 3) & 15, fg = it >> 7;
-      const int f = fg * 8 + f8;
-      double v[8];
+      for (int f = tid; f < np; f += blockDim.x) hexp[f] = hx[f];
+      __syncthreads();
+      const int KEp = (np + 15) & ~15;
+      const long long eb = 256LL * KEp;   // bytes of one 128 x KEp slice
+      unsigned char* Eb = tcE + ((long long)m * e_total + items.eoff[k]) * 2048;
+      // E_c (rows i, K = f), rows scaled by rexpE; slice s at Eb + 2 s eb
+      const int nfc = KEp / 8;
+      for (int it = tid; it < 128 * nfc; it += blockDim.x) {
+        const int i8 = it & 7, fc = (it >> 3) % nfc, ig = (it >> 3) / nfc;
+        const int i = ig * 8 + i8;
+        double v[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int i = ic * 8 + t;
-        v[t] = (f < np && i < NN) ? Ec[(long long)f * NN + i] * Dn[i] : 0.0;
+        for (int t = 0; t < 8; ++t) {
+          const int f = fc * 8 + t;
+          v[t] = (i < NN && f < np) ? Dn[i] * Ec[(long long)f * NN + i] : 0.0;
+        }
+        store_slices8(v, rexpE[i], Eb + tc::kmajor_offset(i, fc * 8, 16 * KEp), 2 * eb);
       }
-      store_slices8(v, f < np ? hexp[f] : kZero, Eb + eb + tc::kmajor_offset(f, ic * 8, 2048), 2 * eb);
+      // E_c^T D (rows f, K = i; the input side of the Loewdin scaling folded in), rows scaled by
+      // hexp; slice s at Eb + (2 s + 1) eb
+      for (int it = tid; it < KEp * (kK / 8); it += blockDim.x) {
+        const int f8 = it & 7, ic = (it >> 3) & 15, fg = it >> 7;
+        const int f = fg * 8 + f8;
+        double v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int i = ic * 8 + t;
+          v[t] = (f < np && i < NN) ? Ec[(long long)f * NN + i] * Dn[i] : 0.0;
+        }
+        store_slices8(v, f < np ? hexp[f] : kZero, Eb + eb + tc::kmajor_offset(f, ic * 8, 2048), 2 * eb);
+      }
     }
   }
 }
@@ -313,10 +345,10 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
 k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict__ Y, long long ld2, int cols, int nm,
            int batch, const double* __restrict__ Dsc, const unsigned char* __restrict__ tcH,
            const int* __restrict__ tcRexpH, const int* __restrict__ tcRexpE, const unsigned char* __restrict__ tcE,
-           long long e_total, const long long* __restrict__ eoff, const int* __restrict__ tcHexp,
-           const int* __restrict__ pair_start, const int* __restrict__ pair_fn, long long n_pairs,
+           long long e_total, const TcItems items, const int* __restrict__ tcHexp,
+           const int* __restrict__ pair_fn, long long n_pairs,
            const double* __restrict__ xE, double* __restrict__ yE, int* __restrict__ err,
-           const int* __restrict__ gate) {
+           const int* __restrict__ gate, uint32_t wlim) {
   constexpr int NN = P1 * P1 * P1;
   extern __shared__ __align__(1024) unsigned char sm[];
   long long* gS2 = reinterpret_cast<long long*>(sm + kMgS);
@@ -356,26 +388,27 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tm = *tbase;
-  const long long nwork = (long long)mesh.nc * batch;
+  const long long nwork = (long long)items.n * batch;   // (item, member) pairs
   const uint32_t xs = tc::smem_u32(sm + kXs), xes = tc::smem_u32(sm + kXEs), ring = tc::smem_u32(sm + kRing);
 
   if (warp == kWork / 32) {
     // ------------------------------------------------------------ issuer warp
     // The whole warp runs the loops (operands stay warp-uniform); lane 0 waits on the mbarriers and
     // its verdict is broadcast, lane 0 issues the copies, MMAs and commits.
-    auto wait = [&](uint64_t* b, uint32_t par) {
+    // progress waits give up after wlim polls; the final waits for work in flight after kWaitLimit
+    auto wait_n = [&](uint64_t* b, uint32_t par, uint32_t limit) {
       bool ok = true;
-      if (lane == 0) ok = tc::mbar_wait(b, par, kWaitLimit);
+      if (lane == 0) ok = tc::mbar_wait(b, par, limit);
       return __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
     };
-    auto cell_np = [&](long long w) {
-      const int c = (int)(w % mesh.nc);
-      return pair_start ? pair_start[c + 1] - pair_start[c] : 0;
-    };
-    // stage s of a cell: E pass stages 0..3 (cells coupled to enrichment functions), then the H
-    // pass stages; the ring is refilled NSLOT - 1 stages ahead of the MMAs
-    long long cw = blockIdx.x;   // copy cursor: cell and stage
-    int cst = 0, cnp = cw < nwork ? cell_np(cw) : 0;
+    auto wait = [&](uint64_t* b, uint32_t par) { return wait_n(b, par, wlim); };
+    auto item_np = [&](long long w) { return items.np[(int)(w % items.n)]; };
+    auto item_h = [&](long long w) { return (items.flags[(int)(w % items.n)] & kItemH) != 0; };
+    auto n_stages = [&](long long w) { return (item_np(w) > 0 ? kSlices : 0) + (item_h(w) ? kSlices : 0); };
+    // stage s of an item: E pass stages 0..3 (items coupled to enrichment functions), then the H
+    // pass stages (items that carry H_c); the ring is refilled NSLOT - 1 stages ahead of the MMAs
+    long long cw = blockIdx.x;   // copy cursor: item and stage
+    int cst = 0, cnp = cw < nwork ? item_np(cw) : 0, cns = cw < nwork ? n_stages(cw) : 0;
     long long issued = 0, consumed = 0;
     uint32_t fparb = 0, eparb = 0;   // phase parities of the full / empty barriers, bit = slot
     uint32_t xpar = 0, dpar = 0;
@@ -386,12 +419,13 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
         if (!wait(&bar[kBEmpty0 + slot], (eparb >> slot) & 1u)) return false;
         eparb ^= 1u << slot;
       }
-      const int c = (int)(cw % mesh.nc), m = (int)(cw / mesh.nc);
+      const int it = (int)(cw % items.n), m = (int)(cw / items.n);
+      const int c = items.cell[it];
       const unsigned char* src;
       uint32_t bytes;
       if (cnp > 0 && cst < kSlices) {
         const long long eb = 256LL * ((cnp + 15) & ~15);
-        src = tcE + ((long long)m * e_total + eoff[c]) * 2048 + 2 * cst * eb;
+        src = tcE + ((long long)m * e_total + items.eoff[it]) * 2048 + 2 * cst * eb;
         bytes = (uint32_t)(2 * eb);
       } else {
         const int i = cnp > 0 ? cst - kSlices : cst;
@@ -403,10 +437,11 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
         tc::bulk_g2s(sm + kRing + slot * kSliceBytes, src, bytes, &bar[kBFull0 + slot]);
       }
       ++issued;
-      if (++cst == (cnp > 0 ? 2 * kSlices : kSlices)) {
+      if (++cst == cns) {
         cst = 0;
         cw += gridDim.x;
-        cnp = cw < nwork ? cell_np(cw) : 0;
+        cnp = cw < nwork ? item_np(cw) : 0;
+        cns = cw < nwork ? n_stages(cw) : 0;
       }
       return true;
     };
@@ -417,24 +452,28 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
     const uint64_t dX0 = tc::smem_desc(xs, tc::kLBO, 2048);
     constexpr uint64_t dXs = (uint64_t)(kXslice >> 4);
     for (long long w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
-      const int np = cell_np(w);
+      const int np = item_np(w);
+      const bool hasH = item_h(w);
       const int KEp = (np + 15) & ~15;
       const uint32_t eb = 256u * (uint32_t)KEp;
-      // the next cell's operator data, into L2
+      // the next item's operator data, into L2
       if (w + gridDim.x < nwork && lane == 0) {
         const long long w2 = w + gridDim.x;
-        const int c2 = (int)(w2 % mesh.nc), m2 = (int)(w2 / mesh.nc);
-        tc::bulk_prefetch_l2(tcH + ((long long)m2 * mesh.nc + c2) * kSlices * kSliceBytes, kSlices * kSliceBytes);
-        const int np2 = cell_np(w2);
+        const int it2 = (int)(w2 % items.n), m2 = (int)(w2 / items.n);
+        if (item_h(w2))
+          tc::bulk_prefetch_l2(tcH + ((long long)m2 * mesh.nc + items.cell[it2]) * kSlices * kSliceBytes,
+                               kSlices * kSliceBytes);
+        const int np2 = item_np(w2);
         if (np2 > 0)
-          tc::bulk_prefetch_l2(tcE + ((long long)m2 * e_total + eoff[c2]) * 2048, (uint32_t)(2048 * ((np2 + 15) & ~15)));
+          tc::bulk_prefetch_l2(tcE + ((long long)m2 * e_total + items.eoff[it2]) * 2048,
+                               (uint32_t)(2048 * ((np2 + 15) & ~15)));
       }
       if (!wait(&bar[kBXready], xpar)) { ok = false; break; }
       xpar ^= 1u;
       const uint64_t dXE0 = tc::smem_desc(xes, tc::kLBO, 16u * (uint32_t)KEp);   // x^E slice j: + j dXEs
       constexpr uint64_t dXEs = (uint64_t)(kXEslice >> 4);
       const uint32_t idT = tc::idesc_bf16(128, KEp > 0 ? KEp : 16);
-      const int ns = np > 0 ? 2 * kSlices : kSlices;
+      const int ns = (np > 0 ? kSlices : 0) + (hasH ? kSlices : 0);
       for (int st = 0; st < ns && ok; ++st) {
         if (*wabort) { ok = false; break; }   // a work warp gave up
         const int slot = (int)(consumed % kNSlot);
@@ -480,6 +519,7 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
         ++consumed;
         ok = issue_copy();
       }
+      // the work warps' H epilogue waits on this commit also for items without H_c
       if (ok) tc::mma_commit_lane0(&bar[kBAccH]);
     }
     if (!ok && lane == 0) atomicExch(err, 1);
@@ -487,11 +527,11 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
     // consumed) and every MMA (one more commit, on a barrier of its own)
     for (long long s2 = consumed; s2 < issued; ++s2) {
       const int slot = (int)(s2 % kNSlot);
-      wait(&bar[kBFull0 + slot], (fparb >> slot) & 1u);
+      wait_n(&bar[kBFull0 + slot], (fparb >> slot) & 1u, kWaitLimit);
       fparb ^= 1u << slot;
     }
     tc::mma_commit_lane0(&bar[kBFin]);
-    wait(&bar[kBFin], 0);
+    wait_n(&bar[kBFin], 0, kWaitLimit);
   } else {
     // ------------------------------------------------------------ work warps
     uint32_t apar = 0, hpar = 0;
@@ -502,7 +542,7 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
     // gave up is recorded before the barrier and read by everyone after it
     auto wait_all = [&](uint64_t* b, uint32_t par) {
       if (warp == 0) {
-        const bool okw = __all_sync(0xffffffffu, tc::mbar_wait(b, par, kWaitLimit));
+        const bool okw = __all_sync(0xffffffffu, tc::mbar_wait(b, par, wlim));
         if (!okw && lane == 0) {
           *wabort = 1;
           atomicExch(err, 1);
@@ -514,19 +554,16 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
     };
     // metadata of cell w into buffer b (every work thread takes part; no barrier inside)
     auto load_meta = [&](long long w, int b) {
-      const int c = (int)(w % mesh.nc), m = (int)(w / mesh.nc);
-      int p0 = 0, np = 0;
-      if (pair_start) {
-        p0 = pair_start[c];
-        np = pair_start[c + 1] - p0;
-      }
+      const int item = (int)(w % items.n), m = (int)(w / items.n);
+      const int c = items.cell[item];
+      const int p0 = items.p0[item], np = items.np[item];
       int cx, cy, cz;
       cell_ijk(mesh, c, cx, cy, cz);
       for (int l = tid; l < 128; l += kWork) {
         if (l < NN)
           gS2[b * 128 + l] = node_index(mesh, cx, cy, cz, l % P1, (l / P1) % P1, l / (P1 * P1)) * ld2 + (long long)m * cols;
         rexpH2[b * 128 + l] = tcRexpH[((long long)m * mesh.nc + c) * 128 + l];
-        if (np > 0) rexpE2[b * 128 + l] = tcRexpE[((long long)m * mesh.nc + c) * 128 + l];
+        if (np > 0) rexpE2[b * 128 + l] = tcRexpE[((long long)m * items.n + item) * 128 + l];
       }
       for (int f = tid; f < np; f += kWork) {
         fns2[b * kMaxKE + f] = pair_fn[p0 + f];
@@ -542,9 +579,11 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
       tc::named_sync(1, kWork);
     }
     for (long long w = blockIdx.x; w < nwork; w += gridDim.x) {
-      const int c = (int)(w % mesh.nc), m = (int)(w / mesh.nc);
+      const int item = (int)(w % items.n), m = (int)(w / items.n);
       const int col0 = m * cols;
-      const int np = pair_start ? pair_start[c + 1] - pair_start[c] : 0;
+      const int np = items.np[item];
+      const int iflags = items.flags[item];
+      const bool hasH = (iflags & kItemH) != 0, solo = (iflags & kItemSolo) != 0;
       const int KEp = (np + 15) & ~15;
       const long long* gS = gS2 + buf * 128;
       const int* rexpH = rexpH2 + buf * 128;
@@ -624,7 +663,7 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
       if (wn < nwork) load_meta(wn, buf ^ 1);
       if (wn < nwork && tid < NN) {
         const long long w2 = wn;
-        const int c2 = (int)(w2 % mesh.nc), m2 = (int)(w2 / mesh.nc);
+        const int c2 = items.cell[(int)(w2 % items.n)], m2 = (int)(w2 / items.n);
         int ex, ey, ez;
         cell_ijk(mesh, c2, ex, ey, ez);
         const long long g = node_index(mesh, ex, ey, ez, tid % P1, (tid / P1) % P1, tid / (P1 * P1));
@@ -676,7 +715,7 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
 #pragma unroll
               for (int t = 0; t < 8; ++t) {
                 const int n = 8 * ch + t;
-                const int eH = (reH == kZero || fC[n] == kZero) ? kZero : reH + fC[n];
+                const int eH = (!hasH || reH == kZero || fC[n] == kZero) ? kZero : reH + fC[n];
                 const int eE = (reE == kZero || fE[n] == kZero) ? kZero : reE + fE[n];
                 float s, u;
                 tc::sum3_pair(a0[t], a1[t], a2[t], s, u);
@@ -690,7 +729,8 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
         }
         tc::fence_before_sync();
         tc::named_sync(1, kWork);
-        if (tid == 0) tc::mbar_arrive(&bar[kBDrainedE]);
+        // the issuer waits for this only before an H pass (items that carry H_c): one arrival per wait
+        if (tid == 0 && hasH) tc::mbar_arrive(&bar[kBDrainedE]);
         if (*wabort) break;
       }
       // ---- H pass epilogue: H_c x^C (+ the E part) -> y_c (staged in shared memory)
@@ -703,14 +743,19 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
           if (ch * 8 < nm) {
             float a0[8], a1[8], a2[8], sE[8], tE[8];
             const uint32_t t0 = tm + lane_addr + 8 * ch;
-            tc::tmem_ld8x3(t0, t0 + 96, t0 + 192, a0, a1, a2);
+            if (hasH) {
+              tc::tmem_ld8x3(t0, t0 + 96, t0 + 192, a0, a1, a2);
+            } else {
+#pragma unroll
+              for (int t = 0; t < 8; ++t) a0[t] = a1[t] = a2[t] = 0.0f;
+            }
             if (np > 0) tc::tmem_ld8x2(tm + lane_addr + 288 + 16 * ch, tm + lane_addr + 296 + 16 * ch, sE, tE);
             if (r < NN) {
 #pragma unroll
               for (int t = 0; t < 8; ++t) {
                 const int n = 8 * ch + t;
                 if (n < cols) {
-                  const int eH = (reH == kZero || fC[n] == kZero) ? kZero : reH + fC[n];
+                  const int eH = (!hasH || reH == kZero || fC[n] == kZero) ? kZero : reH + fC[n];
                   double y = 0.0;
                   float s, u;
                   if (np == 0) {
@@ -741,7 +786,7 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
       // scatter: one node row per warp, consecutive columns per lane
       for (int l = warp; l < NN; l += kWork / 32) {
         const int a = l % P1, b = (l / P1) % P1, cc = l / (P1 * P1);
-        const bool interior = a > 0 && a < P1 - 1 && b > 0 && b < P1 - 1 && cc > 0 && cc < P1 - 1;
+        const bool interior = solo && a > 0 && a < P1 - 1 && b > 0 && b < P1 - 1 && cc > 0 && cc < P1 - 1;
         double* yrow = Y + gS[l];
         for (int n = lane; n < cols; n += 32) {
           const double y = stage[l * kStageLd + n];
@@ -771,9 +816,16 @@ static cudaError_t set_smem_tc(F f, size_t bytes) {
 
 const char* tc_unsupported(const Ctx& c, int cols_member) {
   if (c.p > 4) return "EFE_TC needs degree <= 4 (at most 128 nodes per cell)";
-  if (c.max_pairs_per_cell > kMaxKE) return "EFE_TC needs at most 48 enrichment functions per cell";
-  if (cols_member > kMaxN) return "EFE_TC needs at most 96 real columns (48 orbitals) per batch member";
+  // one member: the apply runs over blocks of 96 real columns; several members: one block each
+  if (c.batch > 1 && cols_member > kMaxN)
+    return "EFE_TC needs at most 96 real columns (48 orbitals) per batch member when batch > 1";
   return nullptr;
+}
+
+static TcItems tc_items(const Ctx& c) {
+  const TcState& t = c.tc;
+  return TcItems{t.n_items, t.items, t.items + t.n_items, t.items + 2 * t.n_items, t.items + 3 * t.n_items, t.eoff,
+                 t.first_item};
 }
 
 static cudaError_t tc_alloc(Ctx& c, int batch) {
@@ -782,11 +834,33 @@ static cudaError_t tc_alloc(Ctx& c, int batch) {
     std::vector<int> ps(c.nc + 1, 0);
     if (c.n_pairs > 0)
       EFE_CUDA_TRY(cudaMemcpy(ps.data(), c.d_pair_start, sizeof(int) * (c.nc + 1), cudaMemcpyDeviceToHost));
-    std::vector<long long> eo(c.nc + 1, 0);
-    for (int i = 0; i < c.nc; ++i) eo[i + 1] = eo[i] + (((ps[i + 1] - ps[i]) + 15) & ~15);
-    t.e_total = eo[c.nc];
-    EFE_CUDA_TRY(cudaMalloc(&t.eoff, sizeof(long long) * (c.nc + 1)));
-    EFE_CUDA_TRY(cudaMemcpy(t.eoff, eo.data(), sizeof(long long) * (c.nc + 1), cudaMemcpyHostToDevice));
+    // work items: a cell's pairs in runs of at most kMaxKE; the first item of a cell carries H_c
+    std::vector<int> cell, p0, np, flags, first(c.nc + 1, 0);
+    for (int i = 0; i < c.nc; ++i) {
+      first[i] = (int)cell.size();
+      const int n = ps[i + 1] - ps[i];
+      const int k = n > 0 ? (n + kMaxKE - 1) / kMaxKE : 1;
+      for (int q = 0; q < k; ++q) {
+        cell.push_back(i);
+        p0.push_back(ps[i] + q * kMaxKE);
+        np.push_back(std::min(kMaxKE, n - q * kMaxKE) > 0 ? std::min(kMaxKE, n - q * kMaxKE) : 0);
+        flags.push_back((q == 0 ? kItemH : 0) | (k == 1 ? kItemSolo : 0));
+      }
+    }
+    first[c.nc] = (int)cell.size();
+    t.n_items = (int)cell.size();
+    std::vector<int> packed;
+    packed.reserve(4 * (size_t)t.n_items);
+    for (auto* v : {&cell, &p0, &np, &flags}) packed.insert(packed.end(), v->begin(), v->end());
+    std::vector<long long> eo(t.n_items + 1, 0);
+    for (int i = 0; i < t.n_items; ++i) eo[i + 1] = eo[i] + ((np[i] + 15) & ~15);
+    t.e_total = eo[t.n_items];
+    EFE_CUDA_TRY(cudaMalloc(&t.items, sizeof(int) * packed.size()));
+    EFE_CUDA_TRY(cudaMemcpy(t.items, packed.data(), sizeof(int) * packed.size(), cudaMemcpyHostToDevice));
+    EFE_CUDA_TRY(cudaMalloc(&t.first_item, sizeof(int) * (c.nc + 1)));
+    EFE_CUDA_TRY(cudaMemcpy(t.first_item, first.data(), sizeof(int) * (c.nc + 1), cudaMemcpyHostToDevice));
+    EFE_CUDA_TRY(cudaMalloc(&t.eoff, sizeof(long long) * (t.n_items + 1)));
+    EFE_CUDA_TRY(cudaMemcpy(t.eoff, eo.data(), sizeof(long long) * (t.n_items + 1), cudaMemcpyHostToDevice));
     EFE_CUDA_TRY(cudaMalloc(&t.err, sizeof(int)));
     EFE_CUDA_TRY(cudaMemset(t.err, 0, sizeof(int)));
   }
@@ -796,7 +870,7 @@ static cudaError_t tc_alloc(Ctx& c, int batch) {
     t.batch = 0;
     EFE_CUDA_TRY(cudaMalloc(&t.H, (size_t)batch * c.nc * kSlices * kSliceBytes));
     EFE_CUDA_TRY(cudaMalloc(&t.rexp, sizeof(int) * (size_t)batch * c.nc * 128));
-    EFE_CUDA_TRY(cudaMalloc(&t.rexpE, sizeof(int) * (size_t)batch * c.nc * 128));
+    EFE_CUDA_TRY(cudaMalloc(&t.rexpE, sizeof(int) * (size_t)batch * t.n_items * 128));
     EFE_CUDA_TRY(cudaMalloc(&t.E, (size_t)batch * (t.e_total > 0 ? t.e_total : 1) * 2048));
     EFE_CUDA_TRY(cudaMalloc(&t.hexp, sizeof(int) * (size_t)batch * (c.n_pairs > 0 ? c.n_pairs : 1)));
     t.batch = batch;
@@ -815,7 +889,7 @@ static cudaError_t tc_build_impl(Ctx& c, int batch, cudaStream_t s) {
   EFE_CUDA_TRY(set_smem_tc(f, sm));
   dim3 grid(c.nc, batch);
   f<<<grid, 256, sm, s>>>(c.tab, c.mesh, c.op.W64, c.op.kin, c.n_pairs > 0 ? c.d_pair_start : nullptr, c.op.E64,
-                          c.n_pairs, c.d_Dsc, c.tc.eoff, c.tc.e_total, c.tc.H, c.tc.rexp, c.tc.rexpE, c.tc.E,
+                          c.n_pairs, c.d_Dsc, tc_items(c), c.tc.e_total, c.tc.H, c.tc.rexp, c.tc.rexpE, c.tc.E,
                           c.tc.hexp);
   note_launch();
   return cudaGetLastError();
@@ -825,7 +899,7 @@ template <int P1>
 static cudaError_t tc_apply_impl(Ctx& c, const double* X, double* Y, long long n_cols, long long ld, cudaStream_t s) {
   const long long ld2 = 2 * ld;
   const int batch = c.op.batch;
-  const int cols = (int)(2 * n_cols / batch);
+  const int cols_all = (int)(2 * n_cols / batch);
   const int ncols2 = (int)(2 * n_cols);
   EFE_CUDA_TRY(cudaMemset2DAsync(Y, sizeof(double) * ld2, 0, sizeof(double) * ncols2, c.n_dof, s));
   if (c.nE > 0) {
@@ -833,22 +907,27 @@ static cudaError_t tc_apply_impl(Ctx& c, const double* X, double* Y, long long n
     EFE_CUDA_TRY(launch_enr_pre(c, X, ld2, ncols2, s));
   }
   if (c.tc.n_sm == 0) EFE_CUDA_TRY(cudaDeviceGetAttribute(&c.tc.n_sm, cudaDevAttrMultiProcessorCount, c.device));
-  const long long nwork = (long long)c.nc * batch;
+  const long long nwork = (long long)c.tc.n_items * batch;
   const unsigned grid = (unsigned)(nwork < c.tc.n_sm ? nwork : c.tc.n_sm);
   auto f = k_tc_apply<P1>;
   EFE_CUDA_TRY(set_smem_tc(f, kApplySmem));
-  const int nm = (cols + 15) & ~15;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!c.apply_gate) prof_pair(c, e0, e1);
   if (e0) EFE_CUDA_TRY(cudaEventRecord(e0, s));
-  f<<<grid, kApplyThreads, kApplySmem, s>>>(c.mesh, X, Y, ld2, cols, nm, batch, c.d_Dsc, c.tc.H, c.tc.rexp,
-                                            c.tc.rexpE, c.tc.E, c.tc.e_total, c.tc.eoff, c.tc.hexp,
-                                            c.n_pairs > 0 ? c.d_pair_start : nullptr, c.d_pair_fn, c.n_pairs, c.d_xE,
-                                            c.d_yE, c.tc.err, c.apply_gate);
-  note_launch();
-  EFE_CUDA_TRY(cudaGetLastError());
+  // one member: blocks of at most 96 real columns (one launch each); several members: one launch
+  const int blk = batch == 1 ? kMaxN : cols_all;
+  for (int off = 0; off < cols_all; off += blk) {
+    const int cols = std::min(blk, cols_all - off);
+    const int nm = (cols + 15) & ~15;
+    f<<<grid, kApplyThreads, kApplySmem, s>>>(c.mesh, X + off, Y + off, ld2, cols, nm, batch, c.d_Dsc, c.tc.H,
+                                              c.tc.rexp, c.tc.rexpE, c.tc.E, c.tc.e_total, tc_items(c), c.tc.hexp,
+                                              c.d_pair_fn, c.n_pairs, c.d_xE + off, c.d_yE + off, c.tc.err,
+                                              c.apply_gate, c.tc_wait_limit > 0 ? c.tc_wait_limit : kWaitLimit);
+    note_launch();
+    EFE_CUDA_TRY(cudaGetLastError());
+  }
   if (e1) EFE_CUDA_TRY(cudaEventRecord(e1, s));
-  if (c.nE > 0) EFE_CUDA_TRY(launch_enr_post(c, Y, ld2, ncols2, cols, s));
+  if (c.nE > 0) EFE_CUDA_TRY(launch_enr_post(c, Y, ld2, ncols2, cols_all, s));
   return cudaSuccess;
 }
 
@@ -872,7 +951,7 @@ cudaError_t launch_tc_apply(Ctx& c, const double* X, double* Y, long long n_cols
 
 void tc_free(TcState& t) {
   cudaFree(t.H); cudaFree(t.rexp); cudaFree(t.rexpE); cudaFree(t.E); cudaFree(t.hexp); cudaFree(t.eoff);
-  cudaFree(t.err);
+  cudaFree(t.items); cudaFree(t.first_item); cudaFree(t.err);
   t = TcState{};
 }
 

@@ -2,6 +2,7 @@
 // (Sec. "Time dependent Kohn-Sham equations"), LDA, dipole, potential
 // assembly and the Hartree PCG (Eqs. Hartree_possion, DiscretePoisson).
 // Everything here is float64 and bound by HBM bandwidth or by the FP64 pipe.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -534,13 +535,13 @@ static unsigned red_grid(long long n_rows, long long C) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-// The Lanczos loop for C columns: eager (host checks the active count after every
-// iteration and stops when it reaches zero) or graph body (all k_max iterations,
-// finished columns skipped on the device, no host synchronisation).
-static cudaError_t kexp_body(Ctx& c, const double* in, double* out, int precision, cudaStream_t s, bool eager) {
-  const long long C = (long long)c.n_orb * c.op.batch;
+// The Lanczos loop for the C columns at in / out (row stride ld2 doubles): eager (host checks
+// the active count after every iteration and stops when it reaches zero) or graph body (all
+// k_max iterations, finished columns skipped on the device, no host synchronisation).  The
+// Krylov basis is contiguous ([k_max + 1][n][C]).
+static cudaError_t kexp_body(Ctx& c, const double* in, double* out, long long C, long long ld2, int precision,
+                             cudaStream_t s, bool eager) {
   const long long n = c.n_dof;
-  const long long ld2 = 2 * C;
   const long long qstride = n * 2 * C;
   LzView v = lz_view(c, C);
   EFE_CUDA_TRY(cudaMemsetAsync(v.red, 0, sizeof(double) * C, s));
@@ -585,9 +586,10 @@ static cudaError_t kexp_body(Ctx& c, const double* in, double* out, int precisio
   return cudaGetLastError();
 }
 
-cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h_dts, int precision, int* kmax_used,
-                          int* cap_hits, double* eps_max, cudaStream_t s, bool need_stats) {
-  const long long C = (long long)c.n_orb * c.op.batch;
+// One Lanczos run over the columns [col0, col0 + C) of in / out (ld2: their row stride).
+static cudaError_t kexp_block(Ctx& c, const double* in, double* out, long long C, long long ld2, const double* h_dts,
+                              int precision, int* kmax_used, int* cap_hits, double* eps_max, cudaStream_t s,
+                              bool need_stats) {
   LzView v = lz_view(c, C);
   // per-column time steps; they reach k_lz_state through dts_in (outside any graph)
   EFE_CUDA_TRY(cudaMemcpyAsync(v.dts_in, h_dts, sizeof(double) * C, cudaMemcpyHostToDevice, s));
@@ -613,7 +615,7 @@ cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h
       EFE_CUDA_TRY(cudaStreamSynchronize(c.cap_stream));
       cudaEventDestroy(ev);
       EFE_CUDA_TRY(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = kexp_body(c, in, out, precision, c.cap_stream, false);
+      cudaError_t e = kexp_body(c, in, out, C, ld2, precision, c.cap_stream, false);
       cudaGraph_t graph = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(c.cap_stream, &graph);
       if (e != cudaSuccess) return e;
@@ -630,7 +632,7 @@ cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h
       c.graph_seen.push_back(key);   // first time: run eagerly (this also tunes the apply)
     }
   }
-  if (!done) EFE_CUDA_TRY(kexp_body(c, in, out, precision, s, true));
+  if (!done) EFE_CUDA_TRY(kexp_body(c, in, out, C, ld2, precision, s, true));
   if (!need_stats) return cudaSuccess;
   int hi[2];
   double hd;
@@ -640,6 +642,70 @@ cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h
   if (kmax_used) *kmax_used = hi[0];
   if (cap_hits) *cap_hits = hi[1];
   if (eps_max) *eps_max = hd;
+  return cudaSuccess;
+}
+
+// out = Kexp(-i dt_col Hbar) in for all n_orb * batch columns, in blocks of at most c.kblock
+// columns (one Lanczos run each; the columns are independent).  Statistics: the largest k, the
+// cap hits and the largest estimate over the blocks.
+// The operator of batch members [m0, m0 + nb) as the whole operator: per-member arrays offset,
+// batch = nb (the apply then runs on those members' columns alone).
+static void view_members(Ctx& c, int m0, int nb) {
+  const long long pq = (long long)c.nc * c.nq, pe = c.n_pairs * (long long)c.nn, ph = (long long)c.nE * c.nE;
+  Operator& o = c.op;
+  if (o.W64) o.W64 += m0 * pq;
+  if (o.W32) o.W32 += m0 * pq;
+  if (o.W2) o.W2 += m0 * pq;
+  if (o.E64) o.E64 += m0 * pe;
+  if (o.E32) o.E32 += m0 * pe;
+  if (o.E2) o.E2 += m0 * pe;
+  if (o.HEE) o.HEE += m0 * ph;
+  o.batch = nb;
+  TcState& t = c.tc;
+  if (t.H) {
+    t.H += (size_t)m0 * c.nc * 4 * 128 * 128 * 2;
+    t.rexp += (size_t)m0 * c.nc * 128;
+    t.rexpE += (size_t)m0 * t.n_items * 128;
+    t.E += (size_t)m0 * (t.e_total > 0 ? t.e_total : 1) * 2048;
+    t.hexp += (size_t)m0 * (c.n_pairs > 0 ? c.n_pairs : 1);
+    t.batch = nb;
+  }
+}
+
+cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h_dts, int precision, int* kmax_used,
+                          int* cap_hits, double* eps_max, cudaStream_t s, bool need_stats) {
+  if (ensure_krylov(c) != EFE_OK) return cudaErrorMemoryAllocation;
+  const int batch = c.op.batch;
+  const long long C = (long long)c.n_orb * batch;
+  long long blk = (c.kblock > 0 && c.kblock < C) ? c.kblock : C;
+  if (batch > 1 && blk < C) blk = std::max<long long>(1, blk / c.n_orb) * c.n_orb;   // whole members
+  int km = 0, caps = 0;
+  double em = 0.0;
+  for (long long off = 0; off < C; off += blk) {
+    const long long Cb = std::min(blk, C - off);
+    int k = 0, cp = 0;
+    double e = 0.0;
+    cudaError_t err;
+    if (batch > 1 && Cb < C) {
+      const Operator op_all = c.op;
+      const TcState tc_all = c.tc;
+      view_members(c, (int)(off / c.n_orb), (int)(Cb / c.n_orb));
+      err = kexp_block(c, in + 2 * off, out + 2 * off, Cb, 2 * C, h_dts + off, precision, &k, &cp, &e, s,
+                       need_stats);
+      c.op = op_all;
+      c.tc = tc_all;
+    } else {
+      err = kexp_block(c, in + 2 * off, out + 2 * off, Cb, 2 * C, h_dts + off, precision, &k, &cp, &e, s,
+                       need_stats);
+    }
+    EFE_CUDA_TRY(err);
+    km = std::max(km, k);
+    caps += cp;
+    em = std::max(em, e);
+  }
+  if (kmax_used) *kmax_used = km;
+  if (cap_hits) *cap_hits = caps;
+  if (eps_max) *eps_max = em;
   return cudaSuccess;
 }
 

@@ -170,9 +170,10 @@ def _oracle_run(S, wl, psi0, n_steps, fixed_k, tol, kmax, kick=True):
     return psi, np.array(mus)
 
 
-def _gpu_run(wl, psi0, n_steps, fixed_k, tol, kmax, precision=0, kick=True, use_graphs=False):
+def _gpu_run(wl, psi0, n_steps, fixed_k, tol, kmax, precision=0, kick=True, use_graphs=False, krylov_block=0,
+             krylov_substeps=1):
     ctx = _ctx(wl, precision=precision, fixed_k=fixed_k, krylov_tol=tol, k_max=kmax, cg_tol=1e-14, cg_max_it=20000,
-               use_graphs=use_graphs)
+               use_graphs=use_graphs, krylov_block=krylov_block, krylov_substeps=krylov_substeps)
     psi = _to_dev(psi0)
     if kick:
         ctx.kick(psi, wl.fields)
@@ -197,6 +198,30 @@ def test_magnus_steps_fixed_k_match_oracle(name):
     got_psi, got_mu, _ = _gpu_run(wl, psi0, 3, fixed_k=8, tol=1e-14, kmax=8)
     assert np.linalg.norm(got_psi - ref_psi) <= 1e-10 * np.linalg.norm(ref_psi)
     assert np.max(np.abs(got_mu - ref_mu)) <= 1e-10 * max(np.max(np.abs(ref_mu)), 1e-3)
+
+
+@pytest.mark.parametrize("substeps", [2, 0])
+def test_krylov_substeps_match_the_converged_step(substeps):
+    """exp(-i dt Hbar) taken as sub-steps of the same operator (Eq. ApproxMagnus; they compose
+    exactly): two fixed sub-steps, and the adaptive count under a cap of 6 Lanczos vectors that
+    one exponential of dt cannot meet at tolerance 1e-12, against the oracle's converged single
+    exponentials: orbitals and dipoles to relative 1e-9."""
+    wl = WORKLOADS["small2_p3"]()
+    S = _sys(wl)
+    psi0 = S.initial_orbitals()
+    ref_psi, ref_mu = _oracle_run(S, wl, psi0, 3, fixed_k=0, tol=1e-13, kmax=40, kick=False)
+    kmax = 24 if substeps == 2 else 6
+    got_psi, got_mu, infos = _gpu_run(wl, psi0, 3, fixed_k=0, tol=1e-12, kmax=kmax, kick=False,
+                                      krylov_substeps=substeps)
+    assert all(i["cap"] == 0 for i in infos)
+    if substeps == 2:
+        assert all(i["substeps"] == 2 for i in infos)
+    else:
+        assert min(i["substeps"] for i in infos) > 1
+        _, _, single = _gpu_run(wl, psi0, 1, fixed_k=0, tol=1e-12, kmax=kmax, kick=False)
+        assert single[0]["cap"] > 0          # one exponential of dt does not converge under this cap
+    assert np.linalg.norm(got_psi - ref_psi) <= 1e-9 * np.linalg.norm(ref_psi)
+    assert np.max(np.abs(got_mu - ref_mu)) <= 1e-9 * max(np.max(np.abs(ref_mu)), 1e-3)
 
 
 def test_hartree_batched_members():
@@ -331,3 +356,54 @@ def test_unitary_and_hermitian_at_scale():
     ctx.magnus_step(psi, 0.0, wl.dt, wl.fields, mu)
     n1 = torch.linalg.norm(psi, dim=0)
     assert torch.max(torch.abs(n1 - n0) / n0).item() < 1e-11
+
+
+@pytest.mark.parametrize("precision", [0, 3])
+def test_krylov_blocks_match_one_run(precision):
+    """Lanczos exponentials over column blocks (krylov_block = 2 of 11 orbitals: five full blocks
+    and a ragged one, the way a workload too large for one Krylov basis runs) give the steps of a
+    single run over all columns, since the columns are independent in the exponential: FP64 to
+    rounding (1e-12), the tensor-core apply to its splitting accuracy (1e-9).  The FP64 blocked run
+    also matches the oracle (1e-10)."""
+    wl = WORKLOADS["small1_p2_11orb"]()
+    S = _sys(wl)
+    psi0 = S.initial_orbitals()
+    one, mu_one, info_one = _gpu_run(wl, psi0, 2, fixed_k=0, tol=1e-12, kmax=12, precision=precision)
+    blk, mu_blk, info_blk = _gpu_run(wl, psi0, 2, fixed_k=0, tol=1e-12, kmax=12, precision=precision, krylov_block=2)
+    tol = 1e-12 if precision == 0 else 1e-9
+    assert np.linalg.norm(blk - one) <= tol * np.linalg.norm(one)
+    assert np.max(np.abs(mu_blk - mu_one)) <= tol * max(np.max(np.abs(mu_one)), 1e-3)
+    assert [i["k_corr"] for i in info_blk] == [i["k_corr"] for i in info_one] or precision != 0
+    if precision == 0:
+        ref_psi, ref_mu = _oracle_run(S, wl, psi0, 2, fixed_k=8, tol=1e-14, kmax=8)
+        got_psi, got_mu, _ = _gpu_run(wl, psi0, 2, fixed_k=8, tol=1e-14, kmax=8, krylov_block=3)
+        assert np.linalg.norm(got_psi - ref_psi) <= 1e-10 * np.linalg.norm(ref_psi)
+        assert np.max(np.abs(got_mu - ref_mu)) <= 1e-10 * max(np.max(np.abs(ref_mu)), 1e-3)
+
+
+def test_krylov_member_blocks_match_one_run():
+    """Two batch members with their own fields propagated with a Krylov basis of one member
+    (krylov_block = n_orb: the operator is viewed at each member's offset) give the steps of one
+    run over both members (FP64, 1e-12)."""
+    wl = W.small_cluster(n_atoms=2, cells_per_axis=4, degree=3, n_quad=5, n_orb=2, batch=2, tol=1e-12)
+    S = _sys(wl)
+    psi0 = np.tile(S.initial_orbitals(), (1, 2))
+    one, mu_one, _ = _gpu_run(wl, psi0, 2, fixed_k=0, tol=1e-12, kmax=12)
+    blk, mu_blk, _ = _gpu_run(wl, psi0, 2, fixed_k=0, tol=1e-12, kmax=12, krylov_block=wl.n_orb)
+    assert np.linalg.norm(blk - one) <= 1e-12 * np.linalg.norm(one)
+    assert np.max(np.abs(mu_blk - mu_one)) <= 1e-12 * max(np.max(np.abs(mu_one)), 1e-3)
+
+
+def test_adjoint_rejects_a_blocked_krylov_basis():
+    """The adjoint recombines one Krylov basis of every orbital: a context whose basis holds fewer
+    columns (krylov_block) is refused with EFE_ERR_ARG, not run wrongly."""
+    from paper_2210_14421_gb300 import EfeError
+    wl = W.small_cluster(n_atoms=2, cells_per_axis=3, degree=3, n_quad=5, L=10.0, n_orb=2)
+    S = _sys(wl)
+    f = W.Field(kind=W.FIELD_GAUSS, amp=0.02, omega=0.0, t0=0.15, sigma=0.25, direction=(0.0, 0.6, 0.8))
+    psi = _to_dev(S.initial_orbitals())
+    ok = _ctx(wl, krylov_tol=1e-13, k_max=40)
+    ok.adjoint_dipole(psi, 2, 0.04, f, (0.0, 0.6, 0.8), (1, 2), checkpoint_every=1)   # the same call runs whole
+    ctx = _ctx(wl, krylov_tol=1e-13, k_max=40, krylov_block=1)
+    with pytest.raises(EfeError, match="Krylov basis of all orbitals"):
+        ctx.adjoint_dipole(psi, 2, 0.04, f, (0.0, 0.6, 0.8), (1, 2), checkpoint_every=1)

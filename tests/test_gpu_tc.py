@@ -189,3 +189,30 @@ def test_tc_unsupported_cases_are_rejected():
     Y = torch.empty_like(X)
     with pytest.raises(EfeError):
         ctx.apply_H(X, Y, precision=EFE_TC)
+
+
+def test_tc_apply_split_cells_and_column_blocks_match_fp64():
+    """An organic-27-like mesh coarsened to 7^3 cells: 87 enrichment functions, cells coupled to up
+    to 87 of them (the apply splits such a cell into work items of at most 48 functions, the first
+    one carrying H_c) and 59 orbitals (118 real columns: blocks of 96 and 22).  Against the FP64
+    apply, element-wise to 1e-7 of the row scale, and to the FP64 result as a whole to 1e-8."""
+    from paper_2210_14421_gb300 import EFE_FP64, EFE_TC, Context
+    wl = W.organic27(cells_per_axis=7)
+    ctx = Context(wl)
+    _, quad = ctx.coords()
+    v = torch.zeros(quad.shape[:2], dtype=torch.float64, device="cuda")
+    for Z, R in zip(wl.Z, wl.R):
+        v -= float(Z) / torch.sqrt(((quad - torch.tensor(R, dtype=torch.float64, device="cuda")) ** 2).sum(-1))
+    ctx.set_potential(v[None].contiguous())
+    assert ctx.n_pairs > 48 * ctx.n_cells // 4   # many cells beyond one work item
+    rng = np.random.default_rng(31)
+    X = _to_dev(rng.normal(size=(ctx.n_dof, wl.n_orb)) + 1j * rng.normal(size=(ctx.n_dof, wl.n_orb)))
+    Y64, Ytc = torch.empty_like(X), torch.empty_like(X)
+    ctx.apply_H(X, Y64, precision=EFE_FP64)
+    ctx.apply_H(X, Ytc, precision=EFE_TC)
+    rel = (torch.abs(Ytc - Y64).max() / torch.abs(Y64).max()).item()
+    assert rel < 1e-8, rel
+    err = torch.abs(Ytc - Y64)
+    scale = torch.abs(Y64).amax(dim=1, keepdim=True) + torch.abs(Y64).max() * 1e-6
+    assert torch.max(err / scale).item() < 1e-7
+    ctx.close()
