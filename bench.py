@@ -163,7 +163,7 @@ def job_throughput(world, steps, ms):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each cell kernel on the
 # 15^3-cell crop of the Na8-like mesh, from ncu (profiles/), and that launch's algorithmic bytes:
 # (measured, algorithmic).  Entries are removed when the kernel changes.
-TRAFFIC = {"k_tc_apply<5>": (1155091472.0, 803952832.0)}
+TRAFFIC = {"k_tc_apply<5>": (1192530176.0, 803952832.0)}
 
 
 def measured_peaks():
@@ -683,6 +683,15 @@ def run_efe(args):
         line["e2e"] = {"value": round(args.e2e_steps / el, 4), "unit": "steps/s",
                        "h2d_bytes_per_step": int(psi.numel() * 16), "d2h_bytes_per_step": int(mu.numel() * 8)}
 
+    if rank == 0:
+        # loss of orthogonality of the plain three-term recurrence (no reorthogonalisation) in the
+        # last Lanczos run: max |Q^H Q - I| over the normalised vectors of its first four columns
+        try:
+            worst, ks = ctx.krylov_orthogonality(4)
+            line["krylov"]["orthogonality"] = {"max_abs_QhQ_minus_I": worst, "k": ks, "tol": wl.krylov_tol,
+                                               "note": "last Lanczos run of the last step, first 4 columns"}
+        except Exception as e:  # noqa: BLE001 -- a diagnostic; the line stands without it
+            line["krylov"]["orthogonality"] = {"unavailable": str(e)[:200]}
     ctx.close()   # its Krylov basis back to the device before the side runs build their own
     torch.cuda.empty_cache()
 

@@ -658,6 +658,15 @@ const char* efe_checkpoint_last_error(void);
  * against.  Allocates and frees a small device buffer and synchronises the device.
  * Errors: EFE_ERR_ARG (null pointer), EFE_ERR_CUDA. */
 efe_status efe_pipe_peaks(double* fp32_tflops_host, double* fp64_tflops_host);
+/* Diagnostics (not part of the method): the Krylov basis of the context's last Lanczos run (the
+ * last column block of its last exponential).  *q_dev: device complex128 basis, vector j of the
+ * c = *cols columns at q_dev + 2 j n_dof c, [n_dof][c] row-major (V_j = s_j q_j, unnormalised:
+ * s_0 = 1, s_j = beta_{j-1}); *norms_dev: device float64 [k_max][c], row j - 1 holding s_j;
+ * *kused_dev: device int32 [c], the Lanczos vectors each column used.  The pointers belong to the
+ * context and stay valid until its next step, apply or exponential.  Errors: EFE_ERR_ARG (null
+ * pointer, no Lanczos run yet). */
+efe_status efe_krylov_basis(efe_ctx* ctx, const double** q_dev, const double** norms_dev, const int32_t** kused_dev,
+                            int64_t* cols);
 efe_status efe_profile_read(efe_ctx* ctx, int64_t* launches, int64_t* apply_launches, double* apply_ms);
 
 #ifdef __cplusplus

@@ -31,7 +31,7 @@ EXPORTED = ["efe_setup", "efe_destroy", "efe_last_error", "efe_sizes", "efe_coor
             "efe_octree_density", "efe_octree_kexp", "efe_octree_interp", "efe_lda_points",
             "efe_octree_magnus_step", "efe_pipe_peaks", "efe_checkpoint_save", "efe_checkpoint_load",
             "efe_checkpoint_write_host", "efe_checkpoint_inspect", "efe_checkpoint_last_error",
-            "efe_set_wait_limit", "efe_set_density_reduce"]
+            "efe_set_wait_limit", "efe_set_density_reduce", "efe_krylov_basis"]
 
 
 class MeshDesc(C.Structure):
@@ -113,6 +113,7 @@ def lib(path: str = LIB_PATH):
                                          C.POINTER(i32)]
     L.efe_set_wait_limit.argtypes = [vp, i64]
     L.efe_set_density_reduce.argtypes = [vp, ReduceFn, vp]
+    L.efe_krylov_basis.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
     L.efe_checkpoint_last_error.argtypes = []
     L.efe_checkpoint_last_error.restype = C.c_char_p
     L.efe_tuning.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(C.c_float), C.POINTER(C.c_float)]
@@ -202,10 +203,11 @@ ReduceFn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p)
 
 
 class _DeviceArray:
-    """A float64 vector in device memory the library owns, seen by torch without a copy."""
+    """A vector in device memory the library owns (float64, or another type string), seen by torch
+    without a copy."""
 
-    def __init__(self, ptr: int, n: int):
-        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8", "data": (int(ptr), False),
+    def __init__(self, ptr: int, n: int, typestr: str = "<f8"):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
                                          "version": 2, "strides": None}
 
 
@@ -393,6 +395,31 @@ class Context:
 
         self._reduce_cb = ReduceFn(cb)   # kept alive as long as the library may call it
         self._check(lib().efe_set_density_reduce(self.h, self._reduce_cb, None))
+
+    def krylov_orthogonality(self, n_cols: int = 4):
+        """Diagnostics: max |Q^H Q - I| over the normalised Lanczos vectors q_j = V_j / s_j of the
+        first n_cols columns of the last Lanczos run, and the vectors each used."""
+        import torch
+        q, nr, ku, c = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_int64()
+        self._check(lib().efe_krylov_basis(self.h, C.byref(q), C.byref(nr), C.byref(ku), C.byref(c)))
+        cols = c.value
+        kused = torch.as_tensor(_DeviceArray(ku.value, cols, "<i4"), device="cuda").cpu().tolist()
+        kmax = max(kused)
+        norms = torch.as_tensor(_DeviceArray(nr.value, kmax * cols), device="cuda").view(kmax, cols)
+        V = torch.as_tensor(_DeviceArray(q.value, kmax * self.n_dof * cols * 2), device="cuda")
+        V = torch.view_as_complex(V.view(kmax, self.n_dof, cols, 2))
+        worst, ks = 0.0, []
+        for col in range(min(n_cols, cols)):
+            k = kused[col]
+            if k < 2:
+                continue
+            s = torch.ones(k, dtype=torch.float64, device="cuda")
+            s[1:] = norms[:k - 1, col]   # |V_j| = beta_{j-1}
+            Qn = V[:k, :, col] / s[:, None]
+            G = Qn.conj() @ Qn.T
+            worst = max(worst, (G - torch.eye(k, dtype=G.dtype, device="cuda")).abs().max().item())
+            ks.append(k)
+        return worst, ks
 
     def checkpoint_save(self, path, psi, t, step):
         self._check(lib().efe_checkpoint_save(self.h, str(path).encode(), _ptr(psi), float(t), int(step), _stream()))

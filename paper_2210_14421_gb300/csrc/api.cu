@@ -992,6 +992,21 @@ efe_status efe_profile(efe_ctx* ctx, int32_t enable) {
   return EFE_OK;
 }
 
+efe_status efe_krylov_basis(efe_ctx* ctx, const double** q_dev, const double** norms_dev, const int32_t** kused_dev,
+                            int64_t* cols) {
+  CHECK_CTX(ctx);
+  Ctx& c = ctx->c;
+  if (!q_dev || !norms_dev || !kused_dev || !cols) return EFE_ERR_ARG;
+  if (c.lz_last_C <= 0 || !c.d_Q) {
+    c.err = "efe_krylov_basis: no Lanczos run yet";
+    return EFE_ERR_ARG;
+  }
+  *q_dev = c.d_Q;
+  lz_last_views(c, norms_dev, kused_dev);
+  *cols = c.lz_last_C;
+  return EFE_OK;
+}
+
 efe_status efe_profile_read(efe_ctx* ctx, int64_t* launches, int64_t* apply_launches, double* apply_ms) {
   CHECK_CTX(ctx);
   Ctx& c = ctx->c;

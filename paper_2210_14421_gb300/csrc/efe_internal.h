@@ -223,6 +223,7 @@ struct Ctx {
   efe_reduce_fn rho_reduce = nullptr;  // sum of the partial densities over processes (orbital partition)
   void* rho_reduce_user = nullptr;
   long long kblock = 0;        // complex columns per Lanczos run (the Krylov basis width)
+  long long lz_last_C = 0;     // columns of the last Lanczos run (0: none yet)
   cudaStream_t cap_stream = nullptr;
   int tile_choice[3] = {-1, -1, -1};
   long long tile_cols[3] = {-1, -1, -1};
@@ -298,6 +299,9 @@ cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* d
 
 // out = Kexp(-i dt_col Hbar) in again, for the start vectors of the last run_kexp_cols, from its
 // Krylov basis and tridiagonal matrices (|dt_col| no larger than that run's; no applies)
+// device pointers to the norms of the basis vectors (beta_{j-1} for V_j: [kMaxK][C]) and used
+// dimensions (int [C]) of the last Lanczos run
+void lz_last_views(const Ctx& c, const double** norms, const int** kused);
 cudaError_t run_kexp_recombine(Ctx& c, double* out, const double* dts_host, cudaStream_t s);
 
 // density / xc / dipole

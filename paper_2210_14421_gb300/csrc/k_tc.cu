@@ -38,7 +38,7 @@
 // enrichment functions are split into work items of at most 48 functions (the first
 // one carries H_c), and an apply over more than 96 columns runs in column blocks.
 // The apply is persistent, one CTA per SM, warp-specialised:
-//   16 work warps: gather x_bar^C (rows of the cell's nodes; the next cell's rows are
+//   24 work warps: gather x_bar^C (rows of the cell's nodes; the next cell's rows are
 //     prefetched into L2) and x^E, per-column exponents, digit extraction into 4
 //     bf16 slices (shared memory); after the MMAs the epilogues: accumulators ->
 //     float pair -> float64, E_c^T x^C to y^E (atomic adds), y_c staged in shared
@@ -72,9 +72,10 @@ constexpr int kZero = -100000;                  // exponent of an all-zero row o
 constexpr uint32_t kWaitLimit = 1u << 22;       // mbarrier polls before giving up (seconds)
 
 // the apply kernel: kWork / 32 work warps (a multiple of 4: the tensor-memory lane quarters) and one
-// issuer warp (16 + 1 measured faster than 12 + 1 on the Na8-like workload: 8.4 against 9.9 ms)
+// issuer warp (on the Na8-like workload, per apply: 12 + 1 warps 9.9 ms, 16 + 1 8.5 ms, 24 + 1 7.9 ms;
+// 24 work warps run at 72 registers per thread)
 #ifndef EFE_TC_WORK_WARPS
-#define EFE_TC_WORK_WARPS 16
+#define EFE_TC_WORK_WARPS 24
 #endif
 constexpr int kWork = 32 * EFE_TC_WORK_WARPS;
 constexpr int kApplyThreads = kWork + 32;
@@ -338,7 +339,7 @@ __device__ __forceinline__ void gather_rows(const double* __restrict__ X, const 
 }
 
 // ----------------------------------------------------------------------------
-// apply (persistent; one CTA per SM; 16 work warps + 1 issuer warp)
+// apply (persistent; one CTA per SM; 24 work warps + 1 issuer warp)
 // ----------------------------------------------------------------------------
 template <int P1>
 __global__ void __launch_bounds__(kApplyThreads, 1)

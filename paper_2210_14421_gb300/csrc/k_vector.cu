@@ -591,6 +591,7 @@ static cudaError_t kexp_block(Ctx& c, const double* in, double* out, long long C
                               int precision, int* kmax_used, int* cap_hits, double* eps_max, cudaStream_t s,
                               bool need_stats) {
   LzView v = lz_view(c, C);
+  c.lz_last_C = C;
   // per-column time steps; they reach k_lz_state through dts_in (outside any graph)
   EFE_CUDA_TRY(cudaMemcpyAsync(v.dts_in, h_dts, sizeof(double) * C, cudaMemcpyHostToDevice, s));
   bool done = false;
@@ -712,6 +713,12 @@ cudaError_t run_kexp_cols(Ctx& c, const double* in, double* out, const double* h
 // out = nrm V exp(-i dts[col] T) e_1 with the Krylov basis V and tridiagonal T left by the
 // last run_kexp_cols (same columns): the exponential of the same start vector at another
 // time step of no larger magnitude, without new operator applies.
+void lz_last_views(const Ctx& c, const double** norms, const int** kused) {
+  const LzView v = lz_view(c, c.lz_last_C);
+  *norms = v.beta;   // the norm of V_j is beta_{j-1}
+  *kused = v.kused;
+}
+
 cudaError_t run_kexp_recombine(Ctx& c, double* out, const double* h_dts, cudaStream_t s) {
   const long long C = (long long)c.n_orb * c.op.batch;
   const long long n = c.n_dof;
