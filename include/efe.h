@@ -493,7 +493,8 @@ efe_status efe_octree_density(efe_octree* oct, const double* psi_bar_dev, int32_
 efe_status efe_octree_interp(efe_octree* oct, const double* u_free_dev, int32_t n_cols, double* out_q_dev,
                              void* stream);
 /* One predictor-corrector Magnus step (Eq. ApproxMagnus) on the locally refined
- * mesh with a fixed Krylov dimension k: psi_p = exp(-i dt Hbar[v(rho_n)]) psi_n,
+ * mesh, each exponential as in efe_octree_kexp (Krylov dimension k, or adaptive up to
+ * k with krylov_tol > 0): psi_p = exp(-i dt Hbar[v(rho_n)]) psi_n,
  * rho_mid = (rho_n + rho(psi_p)) / 2, psi_n+1 = exp(-i dt Hbar[v(rho_mid)]) psi_n,
  * v = -sum Z / |x - R| + v_H + v_xc - E . x at the leaves' Gauss-Legendre points
  * (field_host: double[3], E at the mid-point), v_H from -lap v_H = 4 pi rho with the
@@ -507,18 +508,23 @@ efe_status efe_octree_interp(efe_octree* oct, const double* u_free_dev, int32_t 
  * EFE_ERR_CUDA (also for a kernel fault surfacing at the final synchronisation). */
 efe_status efe_octree_magnus_step(efe_octree* oct, double* psi_bar_dev, int32_t n_orb, const double* occ_host,
                                   const double* atoms_host, int32_t n_atoms, const double* field_host, double dt,
-                                  int32_t k, double cg_tol, int32_t xc, void* stream);
+                                  int32_t k, double krylov_tol, double cg_tol, int32_t xc, void* stream);
 /* psi_bar <- exp(-i dt Hbar) psi_bar on the locally refined mesh, Hbar the
  * Loewdin-scaled operator of efe_octree_apply (mode 2) with kin and v at the
  * leaves' Gauss-Legendre points (vq_dev [n_leaves][n_q]): per complex column,
- * k Lanczos steps of the three-term recurrence (Eq. AdaptiveKrylov with a fixed
- * Krylov dimension), the exponential of the k x k tridiagonal matrix from its
- * eigendecomposition, psi_bar = |psi_bar| Q_k y.  psi_bar_dev: device complex128
+ * Lanczos steps of the three-term recurrence (Eq. AdaptiveKrylov), the exponential
+ * of the m x m tridiagonal matrix from its eigendecomposition, psi_bar =
+ * |psi_bar| Q_m y.  tol <= 0: m = k for every column; tol > 0: each column stops at
+ * the first m <= k whose estimate |dt| beta_m |psi| |[exp(-i dt T_m) e_1]_m| (Eq.
+ * AdaptiveKrylovErr) is at most tol, or whose recurrence breaks down.  *k_used_host
+ * (may be NULL) receives the largest m.  psi_bar_dev: device complex128
  * [n_free][n_cols], in place (boundary rows set to 0).  Allocates (k + 1) n_free
- * n_cols complex scratch per call; synchronises `stream` every step.  Errors:
- * EFE_ERR_ARG (k outside [1, 64]), EFE_ERR_NOMEM, EFE_ERR_CUDA. */
+ * n_cols complex scratch per call; synchronises `stream` every step.  Returns
+ * EFE_WARN_KRYLOV_CAP (result written) if a column reached k with its estimate above
+ * tol.  Errors: EFE_ERR_ARG (k outside [1, 64], tol not finite), EFE_ERR_NOMEM,
+ * EFE_ERR_CUDA. */
 efe_status efe_octree_kexp(efe_octree* oct, const double* vq_dev, double kin, double* psi_bar_dev, int32_t n_cols,
-                           double dt, int32_t k, void* stream);
+                           double dt, int32_t k, double tol, int32_t* k_used_host, void* stream);
 
 /* Host-only diagnostics of the electrostatic enrichment (no context, no device
  * work).  efe_atom_hartree_table: the atomic Hartree potentials that

@@ -136,10 +136,10 @@ def lib(path: str = LIB_PATH):
                                          pdbl]
     L.efe_octree_poisson.argtypes = [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), vp]
     L.efe_octree_density.argtypes = [vp, vp, i32, pdbl, vp, vp]
-    L.efe_octree_kexp.argtypes = [vp, vp, dbl, vp, i32, dbl, i32, vp]
+    L.efe_octree_kexp.argtypes = [vp, vp, dbl, vp, i32, dbl, i32, dbl, C.POINTER(i32), vp]
     L.efe_octree_interp.argtypes = [vp, vp, i32, vp, vp]
     L.efe_lda_points.argtypes = [vp, vp, vp, i64, i32, vp]
-    L.efe_octree_magnus_step.argtypes = [vp, vp, i32, pdbl, pdbl, i32, pdbl, dbl, i32, dbl, i32, vp]
+    L.efe_octree_magnus_step.argtypes = [vp, vp, i32, pdbl, pdbl, i32, pdbl, dbl, i32, dbl, dbl, i32, vp]
     L.efe_atom_hartree_table.argtypes = [C.POINTER(EnrichFn), i32, pdbl, i32, i32, dbl, pdbl, pdbl, pdbl, pdbl]
     L.efe_adaptive_cell_boxes.argtypes = [pdbl, pdbl, pdbl, i32, dbl, dbl, dbl, i32, dbl, i32, C.POINTER(i64), pdbl,
                                           i64]
@@ -580,8 +580,9 @@ class Octree:
         return rho
 
     def magnus_step(self, psi_bar, occ, Z, R, dt: float, k: int, field=(0.0, 0.0, 0.0), cg_tol: float = 1e-12,
-                    xc: int = EFE_XC_PW92):
-        """One predictor-corrector step of psi_bar (device complex128 [n_free, n_orb], in place)."""
+                    xc: int = EFE_XC_PW92, krylov_tol: float = 0.0):
+        """One predictor-corrector step of psi_bar (device complex128 [n_free, n_orb], in place);
+        krylov_tol > 0: adaptive Krylov dimension up to k."""
         import torch
         assert psi_bar.is_cuda and psi_bar.dtype == torch.complex128 and psi_bar.is_contiguous()
         assert psi_bar.dim() == 2 and psi_bar.shape[0] == self.n_free
@@ -589,7 +590,8 @@ class Octree:
         at = np.ascontiguousarray(np.column_stack([np.asarray(Z, float), np.asarray(R, float).reshape(-1, 3)]))
         E = np.ascontiguousarray(field, dtype=np.float64)
         st = lib().efe_octree_magnus_step(self.h, _ptr(psi_bar), int(psi_bar.shape[1]), _dptr(occ), _dptr(at), len(Z),
-                                          _dptr(E), float(dt), int(k), float(cg_tol), int(xc), _stream())
+                                          _dptr(E), float(dt), int(k), float(krylov_tol), float(cg_tol), int(xc),
+                                          _stream())
         if st != EFE_OK:
             raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
         return psi_bar
@@ -606,18 +608,20 @@ class Octree:
             raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
         return out
 
-    def kexp(self, vq, psi_bar, dt: float, k: int, kin: float = 1.0):
-        """psi_bar <- exp(-i dt Hbar) psi_bar in place (device complex128 [n_free, n_cols]),
-        k Lanczos steps per column."""
+    def kexp(self, vq, psi_bar, dt: float, k: int, kin: float = 1.0, tol: float = 0.0):
+        """psi_bar <- exp(-i dt Hbar) psi_bar in place (device complex128 [n_free, n_cols]): k Lanczos
+        steps per column, or (tol > 0) each column up to k until its estimate meets tol.  Returns the
+        largest Krylov dimension used."""
         import torch
         assert psi_bar.is_cuda and psi_bar.dtype == torch.complex128 and psi_bar.is_contiguous()
         assert psi_bar.dim() == 2 and psi_bar.shape[0] == self.n_free
         assert vq.is_cuda and vq.dtype == torch.float64 and vq.is_contiguous() and vq.numel() == self.n_leaves * self.n_q
+        ku = C.c_int32()
         st = lib().efe_octree_kexp(self.h, _ptr(vq), float(kin), _ptr(psi_bar), int(psi_bar.shape[1]), float(dt),
-                                   int(k), _stream())
-        if st != EFE_OK:
+                                   int(k), float(tol), C.byref(ku), _stream())
+        if st not in (EFE_OK, EFE_WARN_KRYLOV_CAP):
             raise EfeError(st, lib().efe_octree_last_error(self.h).decode())
-        return psi_bar
+        return ku.value
 
     def close(self):
         if getattr(self, "h", None):

@@ -356,8 +356,9 @@ __global__ void k_oct_lz_update(double* __restrict__ w, const double* __restrict
 }
 
 // psi[:, c] = sum_j y[c][j] Q_j[:, c] with complex y ([C][k][2]); Q_j = Q + j n 2C
-__global__ void k_oct_lz_combine(const double* __restrict__ Q, const double* __restrict__ y, int k, long long n, int C,
-                                 double* __restrict__ psi) {
+// psi = sum_{j < k} y_j Q_j per column, y [C][ks][2] (only the first k basis vectors were formed)
+__global__ void k_oct_lz_combine(const double* __restrict__ Q, const double* __restrict__ y, int k, int ks, long long n,
+                                 int C, double* __restrict__ psi) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= n * C) return;
   const long long i = idx / C;
@@ -365,7 +366,7 @@ __global__ void k_oct_lz_combine(const double* __restrict__ Q, const double* __r
   double re = 0.0, im = 0.0;
   for (int j = 0; j < k; ++j) {
     const double* q = Q + (long long)j * n * 2 * C + i * 2 * C + 2 * c;
-    const double yr = y[(c * k + j) * 2], yi = y[(c * k + j) * 2 + 1];
+    const double yr = y[(c * ks + j) * 2], yi = y[(c * ks + j) * 2 + 1];
     re += yr * q[0] - yi * q[1];
     im += yr * q[1] + yi * q[0];
   }
@@ -1026,10 +1027,35 @@ efe_status efe_octree_density(efe_octree* oct, const double* psi_bar_dev, int32_
 
 namespace efe {
 
-// psi <- exp(-i dt Hbar) psi per complex column by k Lanczos steps (Eqs. AdaptiveKrylov with a fixed
-// Krylov dimension): Hbar = D P^T H P D (octree_apply mode 2), three-term recurrence, the exponential
-// of the tridiagonal matrix by its eigendecomposition on the host, psi = |psi| Q_k y.
-efe_status octree_kexp(Octree& o, const double* vq, double kin, double* psi, int C, double dt, int k, cudaStream_t s) {
+// y = exp(-i dt T_m) e_1 for the m x m tridiagonal matrix (diagonal a, off-diagonal b) of one column
+// by its eigendecomposition; false if the eigensolver did not converge
+static bool tri_exp_host(int m, const double* a, const double* b, double dt, std::vector<double>& yre,
+                         std::vector<double>& yim) {
+  std::vector<double> T((size_t)m * m, 0.0), V, lam;
+  for (int i = 0; i < m; ++i) {
+    T[(size_t)i * m + i] = a[i];
+    if (i + 1 < m) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = b[i];
+  }
+  if (!jacobi_eigen(m, T, V, lam)) return false;
+  yre.assign(m, 0.0);
+  yim.assign(m, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int q = 0; q < m; ++q) {
+      const double v0 = V[(size_t)0 * m + q], vi = V[(size_t)i * m + q];
+      yre[i] += vi * std::cos(-dt * lam[q]) * v0;
+      yim[i] += vi * std::sin(-dt * lam[q]) * v0;
+    }
+  return true;
+}
+
+// psi <- exp(-i dt Hbar) psi per complex column by Lanczos steps (Eqs. AdaptiveKrylov,
+// AdaptiveKrylovErr): Hbar = D P^T H P D (octree_apply mode 2), three-term recurrence, the exponential
+// of the tridiagonal matrix by its eigendecomposition on the host, psi = |psi| Q_m y.  tol <= 0: every
+// column takes k steps; tol > 0: a column stops at the first m <= k whose estimate
+// eps_m = |dt| beta_m |psi| |[exp(-i dt T_m) e_1]_m| is at most tol (or whose recurrence breaks
+// down), the others at k (counted in *caps); *k_used receives the largest m.
+efe_status octree_kexp(Octree& o, const double* vq, double kin, double* psi, int C, double dt, int k, double tol,
+                       int* k_used, int* caps, cudaStream_t s) {
   const long long n = o.n_free, N2 = n * 2 * C;
   double* Q = nullptr;
   double* small = nullptr;   // nrm[C], a[C], b[C], scratch[C], y[C][k][2]
@@ -1066,7 +1092,11 @@ efe_status octree_kexp(Octree& o, const double* vq, double kin, double* psi, int
     cudaMemcpyAsync(tmp, hv.data(), sizeof(double) * C, cudaMemcpyHostToDevice, s);
     k_oct_cscale<<<oblk(N2), 256, 0, s>>>(psi, tmp, n, C, Q);
     note_launch();
-    for (int j = 0; j < k && st == EFE_OK; ++j) {
+    // per column: the Lanczos dimension it stops at (0: still running) and its y at that point
+    std::vector<int> mc(C, 0);
+    std::vector<std::vector<double>> yre_c(C), yim_c(C);
+    int n_run = C;
+    for (int j = 0; j < k && st == EFE_OK && n_run > 0; ++j) {
       double* qj = Q + (long long)j * N2;
       double* w = Q + (long long)(j + 1) * N2;
       if ((st = octree_apply(o, vq, kin, qj, w, 2 * C, 2, s)) != EFE_OK) break;
@@ -1082,6 +1112,28 @@ efe_status octree_kexp(Octree& o, const double* vq, double kin, double* psi, int
         h_b[(size_t)c * k + j] = beta;
         hv[c] = beta > 1e-300 ? 1.0 / beta : 0.0;   // invariant subspace: the rest of the basis is zero
       }
+      if (tol > 0.0) {
+        // the estimate of each running column at m = j + 1
+        for (int c = 0; c < C && st == EFE_OK; ++c) {
+          if (mc[c] != 0) continue;
+          const int m = j + 1;
+          const double bm = h_b[(size_t)c * k + j];
+          std::vector<double> yr, yi;
+          if (!tri_exp_host(m, &h_a[(size_t)c * k], &h_b[(size_t)c * k], dt, yr, yi)) {
+            o.err = "octree exponential: tridiagonal eigensolver did not converge";
+            st = EFE_ERR_CUDA;
+            break;
+          }
+          const double eps = std::fabs(dt) * bm * h_nrm[c] * std::hypot(yr[m - 1], yi[m - 1]);
+          if (eps <= tol || bm <= 1e-300 || h_nrm[c] == 0.0) {
+            mc[c] = m;
+            yre_c[c] = yr;
+            yim_c[c] = yi;
+            --n_run;
+          }
+        }
+        if (st != EFE_OK) break;
+      }
       std::vector<double> bj(C);
       for (int c = 0; c < C; ++c) bj[c] = h_b[(size_t)c * k + j];
       cudaMemcpyAsync(b, bj.data(), sizeof(double) * C, cudaMemcpyHostToDevice, s);
@@ -1092,33 +1144,31 @@ efe_status octree_kexp(Octree& o, const double* vq, double kin, double* psi, int
       }
     }
     if (st != EFE_OK) break;
-    // y = |psi| V exp(-i dt Lambda) V^T e_1 for the k x k tridiagonal matrix of each column
-    std::vector<double> y((size_t)C * k * 2);
+    // y = |psi| exp(-i dt T_m) e_1 for each column's m x m tridiagonal matrix (zero past m), columns
+    // that did not stop taking m = k
+    std::vector<double> y((size_t)C * k * 2, 0.0);
+    int kmax = 0, ncap = 0;
     for (int c = 0; c < C; ++c) {
-      std::vector<double> T((size_t)k * k, 0.0), V, lam;
-      for (int i = 0; i < k; ++i) {
-        T[(size_t)i * k + i] = h_a[(size_t)c * k + i];
-        if (i + 1 < k) T[(size_t)i * k + i + 1] = T[(size_t)(i + 1) * k + i] = h_b[(size_t)c * k + i];
-      }
-      if (!jacobi_eigen(k, T, V, lam)) {
-        o.err = "octree exponential: tridiagonal eigensolver did not converge";
-        st = EFE_ERR_CUDA;
-        break;
-      }
-      for (int i = 0; i < k; ++i) {
-        double re = 0.0, im = 0.0;
-        for (int m = 0; m < k; ++m) {
-          const double v0 = V[(size_t)0 * k + m], vi = V[(size_t)i * k + m];
-          re += vi * std::cos(-dt * lam[m]) * v0;
-          im += vi * std::sin(-dt * lam[m]) * v0;
+      if (mc[c] == 0) {
+        mc[c] = k;
+        if (tol > 0.0) ++ncap;
+        if (!tri_exp_host(k, &h_a[(size_t)c * k], &h_b[(size_t)c * k], dt, yre_c[c], yim_c[c])) {
+          o.err = "octree exponential: tridiagonal eigensolver did not converge";
+          st = EFE_ERR_CUDA;
+          break;
         }
-        y[((size_t)c * k + i) * 2] = h_nrm[c] * re;
-        y[((size_t)c * k + i) * 2 + 1] = h_nrm[c] * im;
+      }
+      kmax = std::max(kmax, mc[c]);
+      for (int i = 0; i < mc[c]; ++i) {
+        y[((size_t)c * k + i) * 2] = h_nrm[c] * yre_c[c][i];
+        y[((size_t)c * k + i) * 2 + 1] = h_nrm[c] * yim_c[c][i];
       }
     }
     if (st != EFE_OK) break;
+    if (k_used) *k_used = kmax;
+    if (caps) *caps = ncap;
     cudaMemcpyAsync(ydev, y.data(), sizeof(double) * y.size(), cudaMemcpyHostToDevice, s);
-    k_oct_lz_combine<<<oblk(n * C), 256, 0, s>>>(Q, ydev, k, n, C, psi);
+    k_oct_lz_combine<<<oblk(n * C), 256, 0, s>>>(Q, ydev, kmax, k, n, C, psi);
     note_launch();
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) st = EFE_ERR_CUDA;
   } while (false);
@@ -1133,9 +1183,15 @@ efe_status octree_kexp(Octree& o, const double* vq, double kin, double* psi, int
 extern "C" {
 
 efe_status efe_octree_kexp(efe_octree* oct, const double* vq_dev, double kin, double* psi_bar_dev, int32_t n_cols,
-                           double dt, int32_t k, void* stream) {
-  if (!oct || !vq_dev || !psi_bar_dev || n_cols < 1 || 2 * n_cols > 65535 || k < 1 || k > 64) return EFE_ERR_ARG;
-  return efe::octree_kexp(oct->o, vq_dev, kin, psi_bar_dev, n_cols, dt, k, reinterpret_cast<cudaStream_t>(stream));
+                           double dt, int32_t k, double tol, int32_t* k_used_host, void* stream) {
+  if (!oct || !vq_dev || !psi_bar_dev || n_cols < 1 || 2 * n_cols > 65535 || k < 1 || k > 64 || !std::isfinite(tol))
+    return EFE_ERR_ARG;
+  int ku = 0, caps = 0;
+  const efe_status st = efe::octree_kexp(oct->o, vq_dev, kin, psi_bar_dev, n_cols, dt, k, tol, &ku, &caps,
+                                         reinterpret_cast<cudaStream_t>(stream));
+  if (k_used_host) *k_used_host = ku;
+  if (st == EFE_OK && caps > 0) return EFE_WARN_KRYLOV_CAP;
+  return st;
 }
 
 }  // extern "C"
@@ -1191,7 +1247,7 @@ namespace efe {
 // v = -sum Z / |x - R| + v_H + v_xc - E . x at the leaves' Gauss-Legendre points and v_H from
 // -lap v_H = 4 pi rho with the Dirichlet data sum Z / |x - R|.
 static efe_status octree_step(efe_octree* oct, double* psi, int n_orb, const double* occ, const double* atoms,
-                              int n_atoms, const double E[3], double dt, int k, double cg_tol, int xc,
+                              int n_atoms, const double E[3], double dt, int k, double ktol, double cg_tol, int xc,
                               cudaStream_t s) {
   Octree& o = oct->o;
   const long long nq = o.n_leaves * o.nq, nf = o.n_free, N2 = nf * 2 * n_orb;
@@ -1246,12 +1302,12 @@ static efe_status octree_step(efe_octree* oct, double* psi, int n_orb, const dou
     if ((st = efe_octree_density(oct, psi, n_orb, occ, rho_n, s)) != EFE_OK) break;
     if ((st = potential(rho_n)) != EFE_OK) break;
     if ((ce = cudaMemcpyAsync(psi_p, psi, sizeof(double) * N2, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) break;
-    if ((st = octree_kexp(o, v, 1.0, psi_p, n_orb, dt, k, s)) != EFE_OK) break;
+    if ((st = octree_kexp(o, v, 1.0, psi_p, n_orb, dt, k, ktol, nullptr, nullptr, s)) != EFE_OK) break;
     if ((st = efe_octree_density(oct, psi_p, n_orb, occ, rho, s)) != EFE_OK) break;
     k_oct_axpby<<<oblk(nq), 256, 0, s>>>(rho_n, rho, 0.5, 0.5, nq, rho);
     note_launch();
     if ((st = potential(rho)) != EFE_OK) break;
-    st = octree_kexp(o, v, 1.0, psi, n_orb, dt, k, s);
+    st = octree_kexp(o, v, 1.0, psi, n_orb, dt, k, ktol, nullptr, nullptr, s);
   } while (false);
   // the host vectors vNf and g must outlive the copies, and a kernel fault of the last launches
   // surfaces only here: both need the synchronisation before the status is final
@@ -1270,15 +1326,16 @@ static efe_status octree_step(efe_octree* oct, double* psi, int n_orb, const dou
 
 extern "C" efe_status efe_octree_magnus_step(efe_octree* oct, double* psi_bar_dev, int32_t n_orb, const double* occ_host,
                                              const double* atoms_host, int32_t n_atoms, const double* field_host,
-                                             double dt, int32_t k, double cg_tol, int32_t xc, void* stream) {
+                                             double dt, int32_t k, double krylov_tol, double cg_tol, int32_t xc,
+                                             void* stream) {
   if (!oct) return EFE_ERR_ARG;
   if (!psi_bar_dev || !occ_host || (n_atoms > 0 && !atoms_host) || n_atoms < 0 || !field_host || n_orb < 1 ||
       2 * n_orb > 65535 || k < 1 || k > 64 || !(cg_tol > 0.0) || !std::isfinite(dt) || !(dt > 0.0) ||
-      (xc != EFE_XC_PW92 && xc != EFE_XC_PZ81)) {
+      !std::isfinite(krylov_tol) || (xc != EFE_XC_PW92 && xc != EFE_XC_PZ81)) {
     oct->o.err = "efe_octree_magnus_step: bad arguments (null pointer, n_orb outside 1..32767, k outside 1..64, "
-                 "cg_tol <= 0, dt not finite and > 0, or an unknown xc)";
+                 "cg_tol <= 0, dt not finite and > 0, krylov_tol not finite, or an unknown xc)";
     return EFE_ERR_ARG;
   }
-  return efe::octree_step(oct, psi_bar_dev, n_orb, occ_host, atoms_host, n_atoms, field_host, dt, k, cg_tol, xc,
-                          reinterpret_cast<cudaStream_t>(stream));
+  return efe::octree_step(oct, psi_bar_dev, n_orb, occ_host, atoms_host, n_atoms, field_host, dt, k, krylov_tol,
+                          cg_tol, xc, reinterpret_cast<cudaStream_t>(stream));
 }

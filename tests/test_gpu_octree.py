@@ -220,6 +220,41 @@ def test_octree_krylov_exponential_matches_oracle():
     o.close()
 
 
+def test_octree_adaptive_krylov_dimension():
+    """The adaptive form (Eqs. AdaptiveKrylov, AdaptiveKrylovErr): each column stops at the first
+    dimension whose estimate meets the tolerance.  Against the oracle's Lanczos exponential of
+    OctreeMesh.hbar converged to 1e-13: within 10x the tolerance (1e-9) of the orbital's norm,
+    with fewer vectors than the cap; a cap far below what the tolerance needs is reported, not
+    raised."""
+    from oracle import krylov
+    from oracle.octree import OctreeMesh
+    from paper_2210_14421_gb300 import Octree
+    lo, hi, nc, p, nq, ref = [-5, -5, -5], [5, 5, 5], 3, 3, 5, [(1, 1, 1)]
+    m = OctreeMesh(lo, hi, nc, p, ref, n_quad=nq)
+    o = Octree(lo, hi, nc, p, nq, ref)
+    fx, qx, bnd = o.coords()
+    pos = {k: j for j, k in enumerate(_key(m.nodes[m.free]))}
+    perm = np.array([pos[k] for k in _key(fx)])
+    vq = 0.5 * np.sum(qx ** 2, axis=2)
+    rng = np.random.default_rng(12)
+    psi = rng.standard_normal((o.n_free, 2)) + 1j * rng.standard_normal((o.n_free, 2))
+    psi[bnd] = 0.0
+    po = np.zeros_like(psi)
+    po[perm] = psi
+    I = np.where(~m.boundary_free)[0]
+    ref_out, ks, _ = krylov.expm_block(m.hbar(vq, 1.0), po[I], 0.05, 1e-13, 64)
+    vd = torch.from_numpy(np.ascontiguousarray(vq)).cuda()
+    g = torch.from_numpy(np.ascontiguousarray(psi)).cuda()
+    ku = o.kexp(vd, g, 0.05, 64, tol=1e-9)
+    assert 1 < ku < 64
+    got = np.zeros_like(po)
+    got[perm] = g.cpu().numpy()
+    assert np.max(np.linalg.norm(got[I] - ref_out, axis=0) / np.linalg.norm(psi, axis=0)) <= 1e-8
+    g2 = torch.from_numpy(np.ascontiguousarray(psi)).cuda()
+    assert o.kexp(vd, g2, 0.05, 3, tol=1e-14) == 3        # the cap, reported by the status
+    o.close()
+
+
 @pytest.mark.parametrize("name", ["p3_box", "p5_corner"])
 def test_octree_interpolation_matches_oracle(name):
     """Nodal columns of the constrained space at the leaves' Gauss-Legendre points
