@@ -13,9 +13,12 @@ Per column, in the paper's order:
   result = ||psi|| Q_k y.
 Readings: T_k of Eq. AdaptiveKrylov is that of A~ = -i dt Hbar, so its
 (k+1, k) entry has magnitude |dt| * beta_k, which is where the |dt| in eps_k
-comes from; the paper is silent on reorthogonalisation, so the plain three-term
-recurrence is used; with fixed_k > 0 exactly fixed_k steps are taken (used by
-tests that must not depend on where a threshold falls).
+comes from; the paper is silent on reorthogonalisation: by default the plain
+three-term recurrence is used, and with reorth=True every new w is made
+orthogonal to q_1 .. q_j by classical Gram-Schmidt applied twice (CGS2:
+w <- w - Q (Q^H w), two times) before beta_j = ||w|| is taken, alpha_j and the
+recurrence itself unchanged; with fixed_k > 0 exactly fixed_k steps are taken
+(used by tests that must not depend on where a threshold falls).
 """
 from __future__ import annotations
 
@@ -32,8 +35,10 @@ def tridiag_expm_e1(alpha, beta, dt):
     return U @ (np.exp(-1j * dt * lam) * U[0, :])
 
 
-def expm_column(matvec, psi: np.ndarray, dt: float, tol: float, k_max: int, fixed_k: int = 0):
-    """Returns (exp(-i dt Hbar) psi approximation, k used, eps_k, hit_cap)."""
+def expm_column(matvec, psi: np.ndarray, dt: float, tol: float, k_max: int, fixed_k: int = 0, reorth: bool = False,
+                return_basis: bool = False):
+    """Returns (exp(-i dt Hbar) psi approximation, k used, eps_k, hit_cap), and the normalised
+    Lanczos vectors q_1 .. q_k (columns) as a fifth item with return_basis."""
     nrm = np.linalg.norm(psi)
     if nrm == 0.0:
         return psi.copy(), 0, 0.0, False
@@ -49,6 +54,10 @@ def expm_column(matvec, psi: np.ndarray, dt: float, tol: float, k_max: int, fixe
         w = matvec(q)
         a = float(np.real(np.vdot(q, w)))
         w = w - a * q - beta_prev * q_prev
+        if reorth:
+            Qm = np.stack(Q, axis=1)
+            for _ in range(2):
+                w = w - Qm @ (Qm.conj().T @ w)
         b = float(np.linalg.norm(w))
         alphas.append(a)
         betas.append(b)
@@ -66,17 +75,20 @@ def expm_column(matvec, psi: np.ndarray, dt: float, tol: float, k_max: int, fixe
         q = w / b
         Q.append(q)
     k = len(alphas)
-    out = nrm * (np.stack(Q[:k], axis=1) @ y)
+    Qk = np.stack(Q[:k], axis=1)
+    out = nrm * (Qk @ y)
+    if return_basis:
+        return out, k, eps, hit_cap, Qk
     return out, k, eps, hit_cap
 
 
-def expm_block(Hbar, psi: np.ndarray, dt: float, tol: float, k_max: int, fixed_k: int = 0):
+def expm_block(Hbar, psi: np.ndarray, dt: float, tol: float, k_max: int, fixed_k: int = 0, reorth: bool = False):
     """Columns propagated independently; returns (result, ks, eps)."""
     out = np.empty_like(psi)
     ks, eps = [], []
     mv = (lambda v: Hbar @ v) if not callable(Hbar) else Hbar
     for col in range(psi.shape[1]):
-        r, k, e, _ = expm_column(mv, psi[:, col], dt, tol, k_max, fixed_k)
+        r, k, e, _ = expm_column(mv, psi[:, col], dt, tol, k_max, fixed_k, reorth)
         out[:, col] = r
         ks.append(k)
         eps.append(e)

@@ -127,26 +127,27 @@ def field_potential(system: System, E: np.ndarray) -> np.ndarray:
     return -np.einsum("cqa,a->cq", system.mesh.xq, E)
 
 
-def kexp_members(system: System, psi_bar, v_members, n_orb, dt, tol, k_max, fixed_k=0, kin=1.0):
+def kexp_members(system: System, psi_bar, v_members, n_orb, dt, tol, k_max, fixed_k=0, kin=1.0, reorth=False):
     out = np.empty_like(psi_bar)
     ks = []
     for b, vq in enumerate(v_members):
         H = system.hbar(vq, kin)
         sl = slice(b * n_orb, (b + 1) * n_orb)
-        out[:, sl], k, _ = krylov.expm_block(H, psi_bar[:, sl], dt, tol, k_max, fixed_k)
+        out[:, sl], k, _ = krylov.expm_block(H, psi_bar[:, sl], dt, tol, k_max, fixed_k, reorth)
         ks.append(k)
     return out, np.concatenate(ks)
 
 
 def magnus_step(system: System, psi_bar: np.ndarray, state: State, t: float, dt: float, fields, occ,
                 tol: float, k_max: int, fixed_k: int = 0, vN=None, scheme: str = "pc", xc_kind: str = "pw92",
-                hartree=None, reduce=None):
+                hartree=None, reduce=None, reorth=False):
     """One step: predictor-corrector S1..S6 (scheme "pc"), or the
     potential-extrapolation step (scheme "extrapolated"; predictor-corrector
     while the state has no history).  Returns (psi_new, state_new, mu
     (batch, 3), info dict).  With the orbitals split among processes, psi_bar
     and occ are this process's and reduce(rho) sums a density over the
-    processes (each orbital's exponential is independent of the others)."""
+    processes (each orbital's exponential is independent of the others).  reorth: the
+    Lanczos recurrence of every exponential with CGS2 reorthogonalisation."""
     red = (lambda r: r) if reduce is None else reduce
     batch = len(fields)
     n_orb = len(occ)
@@ -160,14 +161,14 @@ def magnus_step(system: System, psi_bar: np.ndarray, state: State, t: float, dt:
         k1 = np.zeros(0, dtype=int)
     elif scheme in ("pc", "extrapolated"):
         v1 = [vN + vhxc[b] + field_potential(system, Emid[b]) for b in range(batch)]
-        psi_p, k1 = kexp_members(system, psi_bar, v1, n_orb, dt, tol, k_max, fixed_k)
+        psi_p, k1 = kexp_members(system, psi_bar, v1, n_orb, dt, tol, k_max, fixed_k, reorth=reorth)
         rho_p = red(density(system, psi_p, occ, batch))
         rho_mid = 0.5 * (state.rho + rho_p)
         vH_mid, vxc_mid, _ = potentials(system, rho_mid, xc_kind, hartree)
         v2 = [vN + vH_mid[b] + vxc_mid[b] + field_potential(system, Emid[b]) for b in range(batch)]
     else:
         raise ValueError("unknown scheme")
-    psi_new, k2 = kexp_members(system, psi_bar, v2, n_orb, dt, tol, k_max, fixed_k)
+    psi_new, k2 = kexp_members(system, psi_bar, v2, n_orb, dt, tol, k_max, fixed_k, reorth=reorth)
     new_state = make_state(system, psi_new, occ, batch, xc_kind, hartree, reduce)
     new_state.vhxc_prev = vhxc
     mu = np.stack([dipole(system, new_state.rho[b]) for b in range(batch)])

@@ -50,3 +50,19 @@ def test_exponential_meets_the_tolerance_despite_lost_orthogonality():
     exact = np.exp(-1j * dt * lam) * b
     assert np.linalg.norm(y - exact) <= tol             # measured 1.3e-9
     assert abs(np.linalg.norm(y) - 1.0) <= tol
+
+
+def test_reorthogonalised_basis_is_orthogonal_and_agrees():
+    """The CGS2 option (the reading that reorthogonalises every new Lanczos vector against all
+    earlier ones, twice): on the same operator its basis is orthogonal to rounding, against a
+    loss of order one without it, and both exponentials meet the exact one within the tolerance."""
+    lam, b = _case()
+    dt, tol = 0.05, 1e-7
+    mv = lambda v: lam * v
+    exact = np.exp(-1j * dt * lam) * b
+    y0, k0, _, _, Q0 = krylov.expm_column(mv, b, dt, tol, 64, return_basis=True)
+    y1, k1, e1, cap1, Q1 = krylov.expm_column(mv, b, dt, tol, 64, reorth=True, return_basis=True)
+    assert not cap1 and e1 <= tol
+    assert np.max(np.abs(Q1.conj().T @ Q1 - np.eye(k1))) <= 1e-12
+    assert np.max(np.abs(Q0.conj().T @ Q0 - np.eye(k0))) > 0.1
+    assert np.linalg.norm(y1 - exact) <= tol and np.linalg.norm(y0 - exact) <= tol
