@@ -643,11 +643,11 @@ def run_efe(args):
             "setup_s": round(t_setup, 2), "initial_state": prep,
             "autotune": {"mixed": ctx.tuning(EFE_MIXED), "pair": ctx.tuning(EFE_PAIR), "fp64": ctx.tuning(EFE_FP64)}}
 
-    def side_run(prec_code, timed_steps, n_cmp, scheme=0, fixed_k=0, substeps=None):
+    def side_run(prec_code, timed_steps, n_cmp, scheme=0, fixed_k=0, substeps=None, reorth=False):
         """The same steps from the same kicked state at another precision (or step scheme): the
         dipoles of the first n_cmp steps and the device time per step of timed_steps more."""
         cs = Context(wl, precision=prec_code, cg_tol=1e-10, cg_max_it=20000, scheme=scheme, fixed_k=fixed_k,
-                     krylov_substeps=args.substeps if substeps is None else substeps)
+                     krylov_substeps=args.substeps if substeps is None else substeps, krylov_reorth=reorth)
         ps = psi_start.clone()
         mus, ts, first = [], 0.0, None
         while len(mus) < n_cmp:
@@ -753,6 +753,16 @@ def run_efe(args):
         # from the predictor-corrector run over the same first steps
         mse, muse, _ = side_run(prec, args.fp64_steps, n_cmp, scheme=1)
         dse = float(np.max(np.abs(muse - np.array(mus_mixed[:n_cmp]))))
+        # the same steps with CGS2 reorthogonalisation in every Lanczos iteration: its cost, and how
+        # far the plain recurrence's loss of orthogonality moves the dipole
+        msr, musr, firstr = side_run(prec, args.fp64_steps, n_cmp, reorth=True)
+        dsr = float(np.max(np.abs(musr - np.array(mus_mixed[:n_cmp]))))
+        line["krylov_reorth"] = {"steps_per_s": round(1000.0 / msr, 4), "ms_per_step": round(msr, 1),
+                                 "steps": args.fp64_steps, "dipole_diff_vs_plain": dsr, "compared_steps": n_cmp,
+                                 "first_step": firstr,
+                                 "note": "krylov_reorth=1: classical Gram-Schmidt twice against all earlier Lanczos "
+                                         "vectors in every iteration; the headline runs the plain three-term "
+                                         "recurrence"}
         line["extrapolated_scheme"] = {"steps_per_s": round(1000.0 / mse, 4), "ms_per_step": round(mse, 1),
                                        "steps": args.fp64_steps, "dipole_diff_vs_pc": dse, "compared_steps": n_cmp,
                                        "note": "EFE_STEP_EXTRAPOLATED: v_Hxc at the mid-point extrapolated from the "

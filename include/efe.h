@@ -175,6 +175,10 @@ typedef struct {
                                  after one whose largest k stayed at or below 2 k_max / 5.  With
                                  fixed_k > 0, 0 means 1.  The kick and the adjoint take single
                                  exponentials. */
+  int32_t krylov_reorth;      /* 1: every new Lanczos vector is made orthogonal to all earlier ones
+                                 of its column by classical Gram-Schmidt applied twice before
+                                 beta_j is taken (the paper is silent; 2 (j + 1) extra passes over
+                                 the basis at iteration j); 0: the plain three-term recurrence. */
 } efe_options;
 
 enum { EFE_XC_PW92 = 0, EFE_XC_PZ81 = 1 };

@@ -64,7 +64,7 @@ class Options(C.Structure):
                 ("krylov_tol", C.c_double), ("k_max", C.c_int32), ("fixed_k", C.c_int32), ("cg_tol", C.c_double),
                 ("cg_max_it", C.c_int32), ("precision", C.c_int32), ("hartree_method", C.c_int32),
                 ("use_graphs", C.c_int32), ("xc", C.c_int32), ("scheme", C.c_int32), ("krylov_block", C.c_int32),
-                ("krylov_substeps", C.c_int32)]
+                ("krylov_substeps", C.c_int32), ("krylov_reorth", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -265,7 +265,7 @@ class Context:
     def __init__(self, wl, precision: int = EFE_FP64, krylov_tol=None, k_max=None, fixed_k: int = 0,
                  cg_tol: float = 1e-12, cg_max_it: int = 5000, hartree_method: int = EFE_HARTREE_FDM,
                  use_graphs: bool = False, xc: int = EFE_XC_PW92, scheme: int = EFE_STEP_PC,
-                 krylov_block: int = 0, krylov_substeps: int = 1):
+                 krylov_block: int = 0, krylov_substeps: int = 1, krylov_reorth: bool = False):
         L = lib()
         self.wl = wl
         self._keep = []
@@ -289,7 +289,7 @@ class Context:
                        float(wl.krylov_tol if krylov_tol is None else krylov_tol),
                        int(wl.k_max if k_max is None else k_max), int(fixed_k), float(cg_tol), int(cg_max_it),
                        int(precision), int(hartree_method), int(bool(use_graphs)), int(xc), int(scheme),
-                       int(krylov_block), int(krylov_substeps))
+                       int(krylov_block), int(krylov_substeps), int(bool(krylov_reorth)))
         h = C.c_void_p()
         st = L.efe_setup(C.byref(mesh), atoms, na, C.byref(enr), C.byref(opts), C.byref(h))
         if st != EFE_OK:

@@ -108,7 +108,7 @@ efe_status ensure_ws(Ctx& c, long long C, long long ld) {
   TRY_CUDA(c, dalloc(c.d_xE32, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
   TRY_CUDA(c, dalloc(c.d_xE2, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
   TRY_CUDA(c, dalloc(c.d_yE, (size_t)std::max(c.nE, 1) * 2 * need_ld), "allocating enrichment scratch");
-  TRY_CUDA(c, dalloc(c.d_lz, (size_t)(6 * kMaxK + 8) * need_ld), "allocating Lanczos scalars");
+  TRY_CUDA(c, dalloc(c.d_lz, (size_t)(8 * kMaxK + 8) * need_ld), "allocating Lanczos scalars");
   TRY_CUDA(c, dalloc(c.d_lzi, (size_t)3 * need_ld + 8), "allocating Lanczos state");
   c.ws_cols = need_ld;
   return EFE_OK;
@@ -224,6 +224,7 @@ static bool validate(const efe_mesh_desc* mesh, const efe_atom* atoms, int n_ato
   if (o->scheme != EFE_STEP_PC && o->scheme != EFE_STEP_EXTRAPOLATED) { why = "unknown step scheme"; return false; }
   if (o->krylov_block < 0) { why = "krylov_block must be >= 0"; return false; }
   if (o->krylov_substeps < 0 || o->krylov_substeps > 64) { why = "krylov_substeps must be in [0, 64]"; return false; }
+  if (o->krylov_reorth != 0 && o->krylov_reorth != 1) { why = "krylov_reorth must be 0 or 1"; return false; }
   if (o->hartree_method != EFE_HARTREE_FDM && o->hartree_method != EFE_HARTREE_PCG) {
     why = "unknown Hartree method";
     return false;
@@ -274,6 +275,7 @@ static efe_status setup_impl(Ctx& c, const efe_mesh_desc* mesh, const efe_atom* 
   c.use_graphs = o->use_graphs != 0;
   c.kblock_opt = o->krylov_block;
   c.substeps_opt = o->krylov_substeps;
+  c.reorth = o->krylov_reorth != 0;
   c.substeps_cur = 1;
 
   // reference tables

@@ -218,6 +218,7 @@ struct Ctx {
   bool use_graphs = false;
   int kblock_opt = 0;          // krylov_block option (0: automatic)
   int substeps_opt = 1;        // krylov_substeps option (0: adaptive)
+  bool reorth = false;         // krylov_reorth: CGS2 reorthogonalisation in the Lanczos loop
   int substeps_cur = 1;        // adaptive: sub-steps of the next exponential
   uint32_t tc_wait_limit = 0;  // polls of the tensor-core apply's progress waits (0: the default)
   efe_reduce_fn rho_reduce = nullptr;  // sum of the partial densities over processes (orbital partition)

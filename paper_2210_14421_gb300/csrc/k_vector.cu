@@ -21,7 +21,8 @@ static unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) /
 // Lanczos scalar layout in Ctx::d_lz for C complex columns.
 struct LzView {
   double *nrm, *alpha, *beta, *yre, *yim, *eps, *red, *red2, *dt, *dts_in;
-  df32* wp;   // [kMaxK][C][2] combination weights nrm y_j as float32 pairs (re, im)
+  df32* wp;     // [kMaxK][C][2] combination weights nrm y_j as float32 pairs (re, im)
+  double* hre;  // [kMaxK][2][C] reorthogonalisation coefficients <V_i, W> (re, im)
   int *active, *kused, *cap, *n_active;
 };
 static LzView lz_view(const Ctx& c, long long C) {
@@ -38,6 +39,7 @@ static LzView lz_view(const Ctx& c, long long C) {
   v.dt = v.red2 + C;
   v.dts_in = v.dt + C;
   v.wp = reinterpret_cast<df32*>(v.dts_in + C);
+  v.hre = reinterpret_cast<double*>(v.wp + 2 * kMaxK * C);
   int* ib = c.d_lzi;
   v.active = ib;
   v.kused = ib + C;
@@ -168,6 +170,71 @@ __global__ void k_lz_update(double* __restrict__ W, const double* __restrict__ V
       *reinterpret_cast<double2*>(W + r * 2 * C + 2 * f.col) = make_double2(0.0, 0.0);
   }
   block_col_reduce(acc, f.col, f.ok, C, sred, out);
+}
+
+// Reorthogonalisation (option krylov_reorth, classical Gram-Schmidt applied twice): the new
+// Lanczos vector W (= V_{j+1}) loses its components along q_0 .. q_j, q_i = V_i / s_i.
+// k_lz_mdot: h[i][col] = <V_i, W> (complex, i <= j), eight basis vectors per pass over W.
+__global__ void k_lz_mdot(const double* __restrict__ W, const double* __restrict__ Q, long long qstride,
+                          long long n_rows, int C, const int* __restrict__ active, int j, double* __restrict__ h) {
+  extern __shared__ double sred[];
+  FlatIter f = flat_iter(C);
+  const bool on = f.ok && active[f.col];
+  for (int i0 = 0; i0 <= j; i0 += 8) {
+    double re[8], im[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) re[t] = im[t] = 0.0;
+    if (on)
+      for (long long r = f.row0; r < n_rows; r += f.rstride) {
+        const long long o = r * 2 * C + 2 * f.col;
+        const double2 w = *reinterpret_cast<const double2*>(W + o);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          if (i0 + t <= j) {
+            const double2 q = *reinterpret_cast<const double2*>(Q + (long long)(i0 + t) * qstride + o);
+            re[t] += q.x * w.x + q.y * w.y;   // conj(q) w
+            im[t] += q.x * w.y - q.y * w.x;
+          }
+        }
+      }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (i0 + t > j) break;
+      block_col_reduce(re[t], f.col, on, C, sred, h + (long long)(2 * (i0 + t)) * C);
+      __syncthreads();
+      block_col_reduce(im[t], f.col, on, C, sred, h + (long long)(2 * (i0 + t) + 1) * C);
+      __syncthreads();
+    }
+  }
+}
+// W <- W - sum_{i <= j} (h_i / s_i^2) V_i, and out[col] += |W|^2
+__global__ void k_lz_maxpy(double* __restrict__ W, const double* __restrict__ Q, long long qstride, long long n_rows,
+                           int C, const int* __restrict__ active, int j, const double* __restrict__ h,
+                           const double* __restrict__ beta, double* __restrict__ out) {
+  extern __shared__ double sred[];
+  FlatIter f = flat_iter(C);
+  double acc = 0.0;
+  if (f.ok && active[f.col]) {
+    double cr[kMaxK], ci[kMaxK];
+    for (int i = 0; i <= j; ++i) {
+      const double si = lz_norm_of_basis(beta, i, C, f.col);
+      const double inv = 1.0 / (si * si);
+      cr[i] = h[(long long)(2 * i) * C + f.col] * inv;
+      ci[i] = h[(long long)(2 * i + 1) * C + f.col] * inv;
+    }
+    for (long long r = f.row0; r < n_rows; r += f.rstride) {
+      const long long o = r * 2 * C + 2 * f.col;
+      double2 w = *reinterpret_cast<double2*>(W + o);
+      for (int i = 0; i <= j; ++i) {
+        const double2 q = *reinterpret_cast<const double2*>(Q + (long long)i * qstride + o);
+        w.x -= cr[i] * q.x - ci[i] * q.y;
+        w.y -= cr[i] * q.y + ci[i] * q.x;
+      }
+      *reinterpret_cast<double2*>(W + o) = w;
+      acc += w.x * w.x + w.y * w.y;
+    }
+  }
+  block_col_reduce(acc, f.col, f.ok && active[f.col], C, sred, out);
 }
 
 // y = exp(-i dt T) e_1 for the real symmetric m x m tridiagonal T (diagonal al,
@@ -567,6 +634,16 @@ static cudaError_t kexp_body(Ctx& c, const double* in, double* out, long long C,
     k_lz_update<<<rg, 256, rs, s>>>(W, Qj, j > 0 ? c.d_Q + (j - 1) * qstride : nullptr, n, (int)C, v.active, v.red,
                                     v.beta, j, v.red2);
     note_launch();
+    if (c.reorth) {
+      for (int pass = 0; pass < 2; ++pass) {
+        EFE_CUDA_TRY(cudaMemsetAsync(v.hre, 0, sizeof(double) * 2 * (j + 1) * C, s));
+        EFE_CUDA_TRY(cudaMemsetAsync(v.red2, 0, sizeof(double) * C, s));
+        k_lz_mdot<<<rg, 256, rs, s>>>(W, c.d_Q, qstride, n, (int)C, v.active, j, v.hre);
+        note_launch();
+        k_lz_maxpy<<<rg, 256, rs, s>>>(W, c.d_Q, qstride, n, (int)C, v.active, j, v.hre, v.beta, v.red2);
+        note_launch();
+      }
+    }
     k_lz_tri<<<(unsigned)C, 32, sizeof(double) * (4 * kMaxK + 4 + kMaxBessel), s>>>(v, (int)C, j, c.k_max, c.fixed_k,
                                                                             c.krylov_tol);
     note_launch();

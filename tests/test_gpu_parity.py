@@ -155,7 +155,7 @@ def test_density_lda_hartree_dipole(name, method):
     assert np.allclose(mu.cpu().numpy()[0], mu_ref, rtol=1e-12, atol=1e-12)
 
 
-def _oracle_run(S, wl, psi0, n_steps, fixed_k, tol, kmax, kick=True):
+def _oracle_run(S, wl, psi0, n_steps, fixed_k, tol, kmax, kick=True, reorth=False):
     from oracle import tdks
     psi = psi0
     if kick:
@@ -165,7 +165,7 @@ def _oracle_run(S, wl, psi0, n_steps, fixed_k, tol, kmax, kick=True):
     vN = tdks.nuclear_potential(S)
     for n in range(n_steps):
         psi, st, mu, info = tdks.magnus_step(S, psi, st, n * wl.dt, wl.dt, wl.fields, wl.occ, tol, kmax,
-                                             fixed_k=fixed_k, vN=vN)
+                                             fixed_k=fixed_k, vN=vN, reorth=reorth)
         mus.append(mu)
     return psi, np.array(mus)
 
@@ -222,6 +222,30 @@ def test_krylov_substeps_match_the_converged_step(substeps):
         assert single[0]["cap"] > 0          # one exponential of dt does not converge under this cap
     assert np.linalg.norm(got_psi - ref_psi) <= 1e-9 * np.linalg.norm(ref_psi)
     assert np.max(np.abs(got_mu - ref_mu)) <= 1e-9 * max(np.max(np.abs(ref_mu)), 1e-3)
+
+
+def test_reorthogonalised_steps_match_oracle():
+    """krylov_reorth (classical Gram-Schmidt twice in every Lanczos iteration): 2 steps at fixed
+    k = 14 against the oracle's reorthogonalised steps (orbitals and dipoles to relative 1e-10),
+    and the basis of the last Lanczos run orthogonal to 1e-11."""
+    from paper_2210_14421_gb300 import Context
+    wl = WORKLOADS["small2_p3"]()
+    S = _sys(wl)
+    psi0 = S.initial_orbitals()
+    ref_psi, ref_mu = _oracle_run(S, wl, psi0, 2, fixed_k=14, tol=1e-14, kmax=14, kick=False, reorth=True)
+    ctx = Context(wl, fixed_k=14, krylov_tol=1e-14, k_max=14, cg_tol=1e-14, cg_max_it=20000, krylov_reorth=True)
+    psi = _to_dev(psi0)
+    mu = torch.zeros((wl.batch, 3), dtype=torch.float64, device="cuda")
+    mus = []
+    for n in range(2):
+        ctx.magnus_step(psi, n * wl.dt, wl.dt, wl.fields, mu)
+        mus.append(mu.cpu().numpy().copy())
+    got = psi.cpu().numpy()
+    assert np.linalg.norm(got - ref_psi) <= 1e-10 * np.linalg.norm(ref_psi)
+    assert np.max(np.abs(np.array(mus) - ref_mu)) <= 1e-10 * max(np.max(np.abs(ref_mu)), 1e-3)
+    loss, ks = ctx.krylov_orthogonality(3)
+    assert ks and loss <= 1e-11
+    ctx.close()
 
 
 def test_hartree_batched_members():
