@@ -395,7 +395,7 @@ k_tc_apply(const MeshView mesh, const double* __restrict__ X, double* __restrict
   if (warp == kWork / 32) {
     // ------------------------------------------------------------ issuer warp
     // The whole warp runs the loops (operands stay warp-uniform); lane 0 waits on the mbarriers and
-    // its verdict is broadcast, lane 0 issues the copies, MMAs and commits.
+    // its result is broadcast, lane 0 issues the copies, MMAs and commits.
     // progress waits give up after wlim polls; the final waits for work in flight after kWaitLimit
     auto wait_n = [&](uint64_t* b, uint32_t par, uint32_t limit) {
       bool ok = true;
