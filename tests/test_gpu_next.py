@@ -91,6 +91,7 @@ def test_extrapolated_scheme_matches_oracle(name):
     ref_psi, ref_mu = _oracle_run(S, wl, psi0, 4, 8, "extrapolated", "pw92")
     got_psi, got_mu, infos = _gpu_run(wl, psi0, 4, 8, EFE_STEP_EXTRAPOLATED, EFE_XC_PW92)
     assert np.linalg.norm(got_psi - ref_psi) <= 1e-10 * np.linalg.norm(ref_psi)
+    assert np.max(np.abs(got_psi - ref_psi)) <= 1e-10 * np.max(np.abs(ref_psi))   # element-wise
     assert np.max(np.abs(got_mu - ref_mu)) <= 1e-10 * max(np.max(np.abs(ref_mu)), 1e-3)
     assert infos[0]["k_pred"] == 8 and all(i["k_pred"] == 0 for i in infos[1:])
 
@@ -104,6 +105,7 @@ def test_pz81_steps_match_oracle():
     ref_psi, ref_mu = _oracle_run(S, wl, psi0, 3, 8, "pc", "pz81")
     got_psi, got_mu, _ = _gpu_run(wl, psi0, 3, 8, EFE_STEP_PC, EFE_XC_PZ81)
     assert np.linalg.norm(got_psi - ref_psi) <= 1e-10 * np.linalg.norm(ref_psi)
+    assert np.max(np.abs(got_psi - ref_psi)) <= 1e-10 * np.max(np.abs(ref_psi))   # element-wise
     assert np.max(np.abs(got_mu - ref_mu)) <= 1e-10 * max(np.max(np.abs(ref_mu)), 1e-3)
 
 

@@ -197,6 +197,7 @@ def test_magnus_steps_fixed_k_match_oracle(name):
     ref_psi, ref_mu = _oracle_run(S, wl, psi0, 3, fixed_k=8, tol=1e-14, kmax=8)
     got_psi, got_mu, _ = _gpu_run(wl, psi0, 3, fixed_k=8, tol=1e-14, kmax=8)
     assert np.linalg.norm(got_psi - ref_psi) <= 1e-10 * np.linalg.norm(ref_psi)
+    assert np.max(np.abs(got_psi - ref_psi)) <= 1e-10 * np.max(np.abs(ref_psi))   # element-wise
     assert np.max(np.abs(got_mu - ref_mu)) <= 1e-10 * max(np.max(np.abs(ref_mu)), 1e-3)
 
 
@@ -221,6 +222,7 @@ def test_krylov_substeps_match_the_converged_step(substeps):
         _, _, single = _gpu_run(wl, psi0, 1, fixed_k=0, tol=1e-12, kmax=kmax, kick=False)
         assert single[0]["cap"] > 0          # one exponential of dt does not converge under this cap
     assert np.linalg.norm(got_psi - ref_psi) <= 1e-9 * np.linalg.norm(ref_psi)
+    assert np.max(np.abs(got_psi - ref_psi)) <= 1e-9 * np.max(np.abs(ref_psi))   # element-wise
     assert np.max(np.abs(got_mu - ref_mu)) <= 1e-9 * max(np.max(np.abs(ref_mu)), 1e-3)
 
 
@@ -242,6 +244,7 @@ def test_reorthogonalised_steps_match_oracle():
         mus.append(mu.cpu().numpy().copy())
     got = psi.cpu().numpy()
     assert np.linalg.norm(got - ref_psi) <= 1e-10 * np.linalg.norm(ref_psi)
+    assert np.max(np.abs(got - ref_psi)) <= 1e-10 * np.max(np.abs(ref_psi))   # element-wise
     assert np.max(np.abs(np.array(mus) - ref_mu)) <= 1e-10 * max(np.max(np.abs(ref_mu)), 1e-3)
     loss, ks = ctx.krylov_orthogonality(3)
     assert ks and loss <= 1e-11
@@ -310,6 +313,7 @@ def test_graph_mode_matches_eager_and_oracle():
     torch.cuda.synchronize()
     got = psi.cpu().numpy()
     assert np.linalg.norm(got - ref_psi) <= 1e-8 * np.linalg.norm(ref_psi)
+    assert np.max(np.abs(got - ref_psi)) <= 1e-8 * np.max(np.abs(ref_psi))   # element-wise
     assert np.max(np.abs(mu.cpu().numpy() - ref_mu[-1])) <= 1e-8
 
 
@@ -323,6 +327,7 @@ def test_magnus_adaptive_k_and_batch():
     # columns may stop one Lanczos step apart where eps_k sits on the threshold:
     # both results are then within the Krylov tolerance of the exponential
     assert np.linalg.norm(got_psi - ref_psi) <= 1e-8 * np.linalg.norm(ref_psi)
+    assert np.max(np.abs(got_psi - ref_psi)) <= 1e-8 * np.max(np.abs(ref_psi))   # element-wise
     assert np.max(np.abs(got_mu - ref_mu)) <= 1e-8
     assert all(i["k_corr"] <= 16 for i in infos)
     assert np.abs(ref_mu[-1, 0, 0] - ref_mu[-1, 1, 0]) > 0   # members differ
@@ -402,6 +407,7 @@ def test_krylov_blocks_match_one_run(precision):
         ref_psi, ref_mu = _oracle_run(S, wl, psi0, 2, fixed_k=8, tol=1e-14, kmax=8)
         got_psi, got_mu, _ = _gpu_run(wl, psi0, 2, fixed_k=8, tol=1e-14, kmax=8, krylov_block=3)
         assert np.linalg.norm(got_psi - ref_psi) <= 1e-10 * np.linalg.norm(ref_psi)
+        assert np.max(np.abs(got_psi - ref_psi)) <= 1e-10 * np.max(np.abs(ref_psi))   # element-wise
         assert np.max(np.abs(got_mu - ref_mu)) <= 1e-10 * max(np.max(np.abs(ref_mu)), 1e-3)
 
 
