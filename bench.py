@@ -27,6 +27,7 @@ error.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -520,7 +521,8 @@ def run_efe(args):
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        # rank 0 runs the side measurements (several minutes) before the closing barrier
+        dist.init_process_group("nccl", timeout=datetime.timedelta(minutes=30))
     else:
         torch.cuda.set_device(0)
     g.build()
