@@ -30,6 +30,7 @@ tdks      density, dipole, fields, second-order Magnus predictor-corrector
           step (Eq. ApproxMagnus), delta kick, ground state.
 
 Parity status of each function is stated in its docstring; every function is
-pinned by a `-m "not gpu"` test in `tests/test_oracle_*.py` except where the
-docstring says "parity unpinned".
+pinned by a `-m "not gpu"` test in `tests/test_oracle_*.py` (no function is
+"parity unpinned"; values taken from the literature sit in `tests/golden/`
+with their citations).
 """

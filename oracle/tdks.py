@@ -193,11 +193,12 @@ def kick(system: System, psi_bar: np.ndarray, fields, n_orb: int, tol: float = 1
 
 def ground_state(system: System, n_orb: int, occ: np.ndarray, mix: float = 0.3, tol: float = 1e-10,
                  max_iter: int = 200, psi_guess=None):
-    """Self-consistent ground state by dense diagonalisation of Hbar on the
-    interior + enrichment DOFs with linear density mixing (parity unpinned
-    as a procedure: only its result - a stationary state - is tested).  The
-    phase of each orbital is fixed so that its overlap with the guess is
-    real and positive."""
+    """Self-consistent ground state by diagonalisation of Hbar on the
+    interior + enrichment DOFs with linear density mixing.  Pinned by its
+    results: the helium atom's LDA 1s eigenvalue against the tabulated
+    all-electron value (tests/test_oracle_ground_state.py), and the H2 state's
+    stationarity under the Magnus propagation.  The phase of each orbital is
+    fixed so that its overlap with the guess is real and positive."""
     import scipy.sparse.linalg as spla
     keep = np.concatenate([system.mesh.interior, np.ones(system.n_E, dtype=bool)])
     idx = np.where(keep)[0]
