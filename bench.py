@@ -324,10 +324,10 @@ def fit_exponent(cells, secs):
     return float(coef[1]), float(np.sqrt(np.mean(res ** 2)))
 
 
-def cpu_baseline(wl_full, crops=(4, 6, 8), budget_s=50.0):
+def cpu_baseline(wl_full, crops=(4, 5, 6, 8), budget_s=50.0):
     """The FP64 oracle as it stands, timed on the host cores on a bounded sample of the
-    workload: one predictor-corrector step on n^3-cell crops of the same mesh (n = 4, 6, 8 while
-    the budget lasts), a fit t = a N_cells^b over the crops, and the full mesh's time per step
+    workload: one predictor-corrector step on n^3-cell crops of the same mesh (n = 4, 5, 6, 8
+    while the budget lasts), a fit t = a N_cells^b over the crops, and the full mesh's time per step
     extrapolated from the largest crop with that exponent (the oracle's cost is not linear in
     the cell count: its sparse Hartree factorisation and Krylov dimensions grow with the crop)."""
     blas, threads = blas_info()
@@ -461,7 +461,7 @@ def prepare_state(ctx, wl, tau=0.02, passes=(4, 2, 2, 2, 2, 2, 2, 2), mix=0.5):
 def run_reference(args):
     """The FP64 oracle on the host cores (rank 0 only): W untimed and K timed samples, each one
     oracle predictor-corrector step on the 4^3-cell crop of the workload's mesh; the exponent of
-    the cost in the cell count is fitted first from the 4^3 and 6^3 crops, and every sample is
+    the cost in the cell count is fitted first from the 4^3, 5^3 and 6^3 crops, and every sample is
     reported in the GPU arm's unit (steps/s of the full workload) through that fit.  ms_per_step
     is the measured time of a sample, so steps x ms_per_step is the run's own timed region."""
     rank = int(os.environ.get("RANK", "0"))
@@ -469,9 +469,9 @@ def run_reference(args):
         return 0
     wl = workload(args, 0)
     blas, threads = blas_info()
-    t4, c4, _ = oracle_crop_step(wl, 4)
-    t6, c6, _ = oracle_crop_step(wl, 6)
-    b, _ = fit_exponent([c4, c6], [t4, t6])
+    fit = [oracle_crop_step(wl, n)[:2] for n in (4, 5, 6)]
+    (t4, c4), (t5, _), (t6, _) = fit
+    b, resid = fit_exponent([c for _, c in fit], [t for t, _ in fit])
     for _ in range(args.warmup):
         oracle_crop_step(wl, 4)
     secs = []
@@ -481,8 +481,8 @@ def run_reference(args):
     sample_s = statistics.median(secs)
     value = 1.0 / (sample_s * (wl.n_cells / c4) ** b * wl.batch)
     sample = ("one predictor-corrector step of the FP64 oracle on the %d-cell crop (4^3) of the same mesh, all %d "
-              "orbitals; full-mesh time per step = sample x (%d / %d)^%.2f (exponent fitted on the 4^3 and 6^3 crops, "
-              "%.2f and %.2f s)" % (c4, wl.n_orb, wl.n_cells, c4, b, t4, t6))
+              "orbitals; full-mesh time per step = sample x (%d / %d)^%.2f (exponent fitted on the 4^3, 5^3 and 6^3 "
+              "crops, %.2f, %.2f and %.2f s, rms log residual %.3f)" % (c4, wl.n_orb, wl.n_cells, c4, b, t4, t5, t6, resid))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 * sum(secs) / len(secs), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
