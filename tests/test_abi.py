@@ -51,3 +51,15 @@ def test_setup_rejects_bad_arguments_without_gpu_work():
     opts = B.Options(1, 1, B._dptr(occ), 1e-8, 99, 0, 1e-10, 100, 0, 0)                # k_max too large
     st = lib.efe_setup(ctypes.byref(mesh), None, 0, None, ctypes.byref(opts), ctypes.byref(h))
     assert st == B.EFE_ERR_ARG
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library the binding raises: there is no CPU fallback to fall into."""
+    from paper_2210_14421_gb300 import _binding as B
+    saved = B._lib
+    try:
+        B._lib = None
+        with pytest.raises(RuntimeError, match="no CPU fallback"):
+            B.lib(str(tmp_path / "libefe.so"))
+    finally:
+        B._lib = saved
