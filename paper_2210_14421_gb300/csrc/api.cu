@@ -714,7 +714,10 @@ efe_status efe_coords(efe_ctx* ctx, double* node_xyz_dev, double* quad_xyz_dev, 
 
 efe_status efe_set_potential(efe_ctx* ctx, const double* v_dev, int32_t batch, double kin_scale, void* stream) {
   CHECK_CTX(ctx);
-  if (!v_dev || batch < 1) return EFE_ERR_ARG;
+  if (!v_dev || batch < 1) {
+    ctx->c.err = "efe_set_potential: v_dev is NULL or batch < 1";
+    return EFE_ERR_ARG;
+  }
   return build_op(ctx->c, v_dev, batch, kin_scale, as_stream(stream));
 }
 
@@ -751,7 +754,10 @@ efe_status efe_apply_H(efe_ctx* ctx, const double* X_dev, double* Y_dev, int64_t
 efe_status efe_magnus_step(efe_ctx* ctx, double* psi_bar_dev, double t, double dt, const efe_field* fields_host,
                            double* mu_dev, efe_step_info* info_host, void* stream) {
   CHECK_CTX(ctx);
-  if (!psi_bar_dev) return EFE_ERR_ARG;
+  if (!psi_bar_dev || !std::isfinite(t) || !std::isfinite(dt)) {
+    ctx->c.err = "efe_magnus_step: psi_bar_dev is NULL or t, dt not finite";
+    return EFE_ERR_ARG;
+  }
   return magnus_impl(ctx->c, psi_bar_dev, t, dt, fields_host, mu_dev, info_host, as_stream(stream));
 }
 
@@ -767,7 +773,10 @@ efe_status efe_density_vxc(efe_ctx* ctx, const double* psi_bar_dev, double* rho_
                            void* stream) {
   CHECK_CTX(ctx);
   Ctx& c = ctx->c;
-  if (!psi_bar_dev || !rho_dev) return EFE_ERR_ARG;
+  if (!psi_bar_dev || !rho_dev) {
+    c.err = "efe_density_vxc: psi_bar_dev and rho_dev are required";
+    return EFE_ERR_ARG;
+  }
   efe_status st = ensure_ws(c, (long long)c.n_orb * c.batch, (long long)c.n_orb * c.batch);
   if (st != EFE_OK) return st;
   cudaStream_t s = as_stream(stream);
@@ -782,7 +791,10 @@ efe_status efe_density_vxc(efe_ctx* ctx, const double* psi_bar_dev, double* rho_
 efe_status efe_hartree(efe_ctx* ctx, const double* rho_dev, double* vH_dev, double tol, int32_t max_it,
                        int32_t* iters_host, void* stream) {
   CHECK_CTX(ctx);
-  if (!rho_dev || !vH_dev || !(tol > 0.0) || max_it < 1) return EFE_ERR_ARG;
+  if (!rho_dev || !vH_dev || !(tol > 0.0) || max_it < 1) {
+    ctx->c.err = "efe_hartree: rho_dev and vH_dev are required, tol > 0, max_it >= 1";
+    return EFE_ERR_ARG;
+  }
   int its = 0;
   efe_status st = run_hartree(ctx->c, rho_dev, vH_dev, tol, max_it, &its, as_stream(stream));
   if (iters_host) *iters_host = its;
@@ -792,7 +804,10 @@ efe_status efe_hartree(efe_ctx* ctx, const double* rho_dev, double* vH_dev, doub
 
 efe_status efe_dipole(efe_ctx* ctx, const double* rho_dev, double* mu_dev, void* stream) {
   CHECK_CTX(ctx);
-  if (!rho_dev || !mu_dev) return EFE_ERR_ARG;
+  if (!rho_dev || !mu_dev) {
+    ctx->c.err = "efe_dipole: rho_dev and mu_dev are required";
+    return EFE_ERR_ARG;
+  }
   TRY_CUDA(ctx->c, launch_dipole(ctx->c, rho_dev, mu_dev, as_stream(stream)), "dipole");
   return EFE_OK;
 }
@@ -818,7 +833,10 @@ efe_status efe_hartree_enriched(efe_ctx* ctx, double r0, double s, int32_t sub, 
 efe_status efe_kick(efe_ctx* ctx, double* psi_bar_dev, const efe_field* fields_host, void* stream) {
   CHECK_CTX(ctx);
   Ctx& c = ctx->c;
-  if (!psi_bar_dev || !fields_host) return EFE_ERR_ARG;
+  if (!psi_bar_dev || !fields_host) {
+    c.err = "efe_kick: psi_bar_dev and fields_host are required";
+    return EFE_ERR_ARG;
+  }
   const long long C = (long long)c.n_orb * c.batch;
   efe_status st = ensure_ws(c, C, C);
   if (st != EFE_OK) return st;
@@ -969,7 +987,10 @@ efe_status efe_tuning(efe_ctx* ctx, int32_t precision, int32_t force_variant, in
                       float* ms1) {
   CHECK_CTX(ctx);
   Ctx& c = ctx->c;
-  if (precision != EFE_FP64 && precision != EFE_MIXED && precision != EFE_PAIR) return EFE_ERR_ARG;
+  if (precision != EFE_FP64 && precision != EFE_MIXED && precision != EFE_PAIR) {
+    c.err = "efe_tuning: precision must be EFE_FP64, EFE_MIXED or EFE_PAIR";
+    return EFE_ERR_ARG;
+  }
   const int p = precision;
   if (force_variant == 0 || force_variant == 1) {
     c.tile_choice[p] = force_variant;
@@ -998,7 +1019,10 @@ efe_status efe_krylov_basis(efe_ctx* ctx, const double** q_dev, const double** n
                             int64_t* cols) {
   CHECK_CTX(ctx);
   Ctx& c = ctx->c;
-  if (!q_dev || !norms_dev || !kused_dev || !cols) return EFE_ERR_ARG;
+  if (!q_dev || !norms_dev || !kused_dev || !cols) {
+    c.err = "efe_krylov_basis: every output pointer is required";
+    return EFE_ERR_ARG;
+  }
   if (c.lz_last_C <= 0 || !c.d_Q) {
     c.err = "efe_krylov_basis: no Lanczos run yet";
     return EFE_ERR_ARG;

@@ -201,7 +201,10 @@ efe_status efe_checkpoint_write_host(const char* path, const int64_t* sizes, dou
 efe_status efe_checkpoint_inspect(const char* path, int64_t* sizes, double* t, int64_t* step, int32_t* has_state,
                                   int32_t* has_prev) {
   g_ckpt_err.clear();
-  if (!path) return EFE_ERR_ARG;
+  if (!path) {
+    g_ckpt_err = "efe_checkpoint_inspect: path is NULL";
+    return EFE_ERR_ARG;
+  }
   CkptHeader h{};
   std::vector<double> payload;
   if (!read_file(path, h, payload, g_ckpt_err)) return EFE_ERR_ARG;

@@ -69,3 +69,13 @@ def test_incomplete_state_is_refused(B, tmp_path):
         B.checkpoint_write_host(tmp_path / "x.ckpt", SIZES, 0.0, 0, a["psi"], rho=a["rho"])
     with pytest.raises(EfeError, match="previous potential"):
         B.checkpoint_write_host(tmp_path / "y.ckpt", SIZES, 0.0, 0, a["psi"], vprev=a["vprev"])
+
+
+def test_null_path_is_refused_with_a_message(B):
+    import ctypes as C
+    L = B.lib()
+    i64, i32 = C.c_int64, C.c_int32
+    sz, t, step, hs, hp = (i64 * 6)(), C.c_double(), i64(), i32(), i32()
+    st = L.efe_checkpoint_inspect(None, sz, C.byref(t), C.byref(step), C.byref(hs), C.byref(hp))
+    assert st == B.EFE_ERR_ARG
+    assert b"path is NULL" in L.efe_checkpoint_last_error()
