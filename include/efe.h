@@ -282,7 +282,10 @@ efe_status efe_apply_H_noalloc(efe_ctx* ctx, const double* X_dev, double* Y_dev,
  * at t + dt.  info_host: NULL, or filled after synchronising `stream`.
  * The density-derived potentials of step n are kept in the context from the
  * previous step; the first step after efe_setup, efe_kick or efe_reset_state
- * recomputes them from psi_bar. */
+ * recomputes them from psi_bar.  Errors: EFE_ERR_ARG (psi_bar_dev NULL, t or dt
+ * not finite), EFE_ERR_CG_NOCONV (a Hartree PCG solve missed cg_tol; the step
+ * is completed), EFE_ERR_TIMEOUT (see efe_apply_H), EFE_ERR_NOMEM, EFE_ERR_CUDA,
+ * and the warning EFE_WARN_KRYLOV_CAP. */
 efe_status efe_magnus_step(efe_ctx* ctx, double* psi_bar_dev, double t, double dt,
                            const efe_field* fields_host, double* mu_dev, efe_step_info* info_host,
                            void* stream);
