@@ -63,3 +63,36 @@ def test_missing_library_fails_loudly(tmp_path):
             B.lib(str(tmp_path / "libefe.so"))
     finally:
         B._lib = saved
+
+
+def test_plain_c_program_links_and_calls_the_library(tmp_path):
+    """The boundary is a C ABI: a C99 program that includes include/efe.h alone links against
+    libefe.so, takes the address of every declared entry point and makes a host-only call (no
+    device work) whose status and message come back through C."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2210_14421_gb300 import _binding as B
+    libdir = os.path.dirname(B.LIB_PATH)
+    names = _declared()
+    src = tmp_path / "use_efe.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <string.h>\n#include "efe.h"\n'
+        "typedef void (*fn_t)(void);\n"
+        "int main(void) {\n"
+        "  fn_t fns[] = {" + ", ".join("(fn_t)%s" % n for n in names) + "};\n"
+        "  int n = 0;\n"
+        "  for (size_t i = 0; i < sizeof fns / sizeof fns[0]; ++i) n += fns[i] != 0;\n"
+        "  int64_t sizes[6]; double t; int64_t step; int32_t hs, hp;\n"
+        "  efe_status st = efe_checkpoint_inspect(NULL, sizes, &t, &step, &hs, &hp);\n"
+        '  printf("%d %d %s\\n", n, (int)st, efe_checkpoint_last_error());\n'
+        "  return 0;\n}\n")
+    exe = tmp_path / "use_efe"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe), str(B.LIB_PATH), "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split(maxsplit=2)
+    assert int(out[0]) == len(names)
+    assert int(out[1]) == B.EFE_ERR_ARG and "path is NULL" in out[2]
